@@ -1,0 +1,412 @@
+"""Pins for the oracle: each check ties it to something other than its own formulas.
+
+* D-tensors: central finite differences of the previous order; symmetry; tracelessness
+  (1/r is harmonic away from 0).
+* Expansions: for two point clusters the error of the local expansion falls as h^4 (phi) and
+  h^3 (g) when the clusters shrink by h (total order 3 truncation); the angular-momentum
+  correction removes the pair torque to round-off, while without it the torque is O(h^3).
+* Tree: proper nesting (Sec. 2.4), leaves tile the unit box, refinement is flagged-or-required.
+* Lists: every leaf pair is covered exactly once (single-source solves on AMR trees); the
+  solve reduces to the exact direct sum when every pair is near.
+* Whole solve: error against the O(N^2) direct sum is small and falls as theta shrinks; zero
+  net force and torque with the correction on; closed-form potentials of the uniform sphere
+  (paper's residual table as a soft band, Sec. 3.4) and of the n = 1 polytrope.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2101_08226_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+BETA_CUBE = 2.380077363979554  # integral of 1/r over the unit cube from its centre (quadrature)
+
+
+# ------------------------------------------------------------------------------------------
+# expansions
+# ------------------------------------------------------------------------------------------
+def test_dtensors_are_successive_derivatives_of_inverse_distance():
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        R = rng.uniform(-2, 2, 3) + np.array([3.0, 0, 0])
+        D = O.dtensors(R)
+        h = 1e-5
+        for n in range(4):
+            fd = np.empty(D[n + 1].shape)
+            for a in range(3):
+                e = np.zeros(3)
+                e[a] = h
+                Dp, Dm = O.dtensors(R + e)[n], O.dtensors(R - e)[n]
+                fd[..., a] = (np.asarray(Dp) - np.asarray(Dm)) / (2 * h)
+            scale = np.abs(D[n + 1]).max()
+            assert np.abs(fd - D[n + 1]).max() <= 1e-7 * scale, n
+        assert abs(D[0] - 1 / np.linalg.norm(R)) < 1e-15
+
+
+def test_dtensors_symmetric_and_traceless():
+    R = np.array([0.3, -1.7, 2.2])
+    _, D1, D2, D3, D4 = O.dtensors(R)
+    for T in (D2, D3, D4):
+        for perm in [(1, 0) + tuple(range(2, T.ndim))]:
+            assert np.allclose(T, np.transpose(T, perm), atol=0, rtol=1e-14)
+        tr = np.trace(T, axis1=0, axis2=1)
+        assert np.abs(tr).max() <= 1e-13 * np.abs(T).max()
+    assert np.allclose(D3, np.transpose(D3, (2, 1, 0)), rtol=1e-14, atol=0)
+    assert np.allclose(D4, np.transpose(D4, (3, 2, 1, 0)), rtol=1e-14, atol=0)
+
+
+def _clusters(h, seed=1):
+    rng = np.random.default_rng(seed)
+    xa0 = rng.uniform(-1, 1, (20, 3))
+    xb0 = rng.uniform(-1, 1, (25, 3))
+    ma = rng.uniform(0.5, 1.5, 20)
+    mb = rng.uniform(0.5, 1.5, 25)
+    ya0 = rng.uniform(-1, 1, (6, 3))
+    R = np.array([10.0, 3.0, -4.0])
+    return R + h * xa0, ma, h * xb0, mb, R + h * ya0
+
+
+def test_expansion_error_orders():
+    errs = []
+    for h in (0.4, 0.2, 0.1):
+        xa, ma, xb, mb, ya = _clusters(h)
+        momA, momB = O.point_moments(xa, ma), O.point_moments(xb, mb)
+        L, _ = O.m2l(momA, momB)
+        ep = eg = 0.0
+        for y in ya:
+            phi, g = O.local_eval(L, momA[1:4], y)
+            d = y - xb
+            r = np.linalg.norm(d, axis=1)
+            ep = max(ep, abs(phi + (mb / r).sum()))
+            eg = max(eg, np.linalg.norm(g + (mb[:, None] * d / r[:, None] ** 3).sum(0)))
+        errs.append((ep, eg))
+    for (p0, g0), (p1, g1) in zip(errs, errs[1:]):
+        assert 12 < p0 / p1 < 20   # O(h^4): potential exact through total order 3
+        assert 6 < g0 / g1 < 10    # O(h^3): force exact through total order 2
+
+
+def _pair_force_torque(xa, ma, xb, mb, amc):
+    momA, momB = O.point_moments(xa, ma), O.point_moments(xb, mb)
+    LA, acA = O.m2l(momA, momB, amc)
+    LB, acB = O.m2l(momB, momA, amc)
+    F = np.zeros(3)
+    T = np.zeros(3)
+    norm = 0.0
+    for xs, ms, L, ac, mom in ((xa, ma, LA, acA, momA), (xb, mb, LB, acB, momB)):
+        for x, m in zip(xs, ms):
+            _, g = O.local_eval(L, mom[1:4], x)
+            f = m * (g + (ac if amc else 0))
+            F += f
+            T += np.cross(x, f)
+            norm += np.linalg.norm(x) * np.linalg.norm(f)
+    return F, T, norm
+
+
+def test_angular_momentum_correction_cancels_pair_torque():
+    prev = None
+    for h in (0.4, 0.2):
+        xa, ma, xb, mb, _ = _clusters(h, seed=7)
+        F, T, n = _pair_force_torque(xa, ma, xb, mb, True)
+        assert np.abs(F).max() <= 1e-14 * n
+        assert np.abs(T).max() <= 1e-14 * n
+        F0, T0, n0 = _pair_force_torque(xa, ma, xb, mb, False)
+        assert np.abs(F0).max() <= 1e-14 * n0      # linear momentum holds without it too
+        assert np.abs(T0).max() > 1e-8 * n0       # ... angular momentum does not
+        if prev is not None:
+            assert 6 < prev / np.abs(T0).max() < 10  # defect is O(h^3)
+        prev = np.abs(T0).max()
+
+
+def test_cell_multipoles_reproduce_far_field():
+    w = synth.workload_uniform_polytrope(1)
+    t = O.Tree(w.max_level, w.flags)
+    rho = synth.leaf_density(w.field, t.leaves())
+    mom = O.inner_moments(t, rho)          # level-0 cells (all refined)
+    x, m = O.leaf_masses(t, rho)
+    # level-0 cell at local (3,4,2) covers level-1 global cells (6..7, 8..9, 4..5)
+    c = (3 * 8 + 4) * 8 + 2
+    lv = t.leaves()
+    sel = []
+    for s, (lev, i, j, k) in enumerate(lv):
+        for a in range(8):
+            for b in range(8):
+                for cc in range(8):
+                    g = (8 * i + a, 8 * j + b, 8 * k + cc)
+                    if (g[0] // 2, g[1] // 2, g[2] // 2) == (3, 4, 2):
+                        sel.append(s * 512 + (a * 8 + b) * 8 + cc)
+    sel = np.array(sel)
+    assert sel.size == 8
+    np.testing.assert_allclose(mom[c, 0], m[sel].sum(), rtol=1e-14)
+    dirs = np.random.default_rng(3).normal(size=(24, 3))
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    errs = []
+    for D in (0.5, 4.0):
+        e = 0.0
+        for u in dirs:
+            y = mom[c, 1:4] + D * u
+            point = np.zeros(40)
+            point[0] = 1.0
+            point[1:4] = y
+            L, _ = O.m2l(point, mom[c])
+            phi, _ = O.local_eval(L, y, y)
+            exact = -(m[sel] / np.linalg.norm(y - x[sel], axis=1)).sum()
+            e = max(e, abs(phi - exact))
+        errs.append(e)
+    # exact through the 3rd moment: over a factor 8 in distance the worst-direction error falls
+    # by more than 8^4.6 (a wrong 2nd or 3rd moment would leave D^-3 or D^-4: 512 or 4096)
+    assert errs[0] / errs[1] > 1.5e4
+
+
+# ------------------------------------------------------------------------------------------
+# tree and lists
+# ------------------------------------------------------------------------------------------
+def test_uniform_tree_layout():
+    t = O.Tree(2, synth.uniform_flags(2))
+    s = t.subgrids()
+    assert s.shape == (73, 5)
+    assert list(np.bincount(s[:, 0])) == [1, 8, 64]
+    lv = t.leaves()
+    assert lv.shape == (64, 4) and np.all(lv[:, 0] == 2)
+    # Morton order (x bit most significant within each triple)
+    assert [tuple(r[1:]) for r in lv[:5]] == [(0, 0, 0), (0, 0, 1), (0, 1, 0), (0, 1, 1), (1, 0, 0)]
+    assert tuple(lv[8, 1:]) == (0, 0, 2)
+
+
+def _check_tree(t, max_level, flags):
+    s = t.subgrids()
+    exist = {(int(r[0]), int(r[1]), int(r[2]), int(r[3])): int(r[4]) for r in s}
+    for (l, i, j, k), leaf in exist.items():
+        if l > 0:
+            assert exist.get((l - 1, i // 2, j // 2, k // 2)) == 0  # parent exists, refined
+        if not leaf:
+            assert l < max_level
+            n = 1 << l
+            for di in (-1, 0, 1):
+                for dj in (-1, 0, 1):
+                    for dk in (-1, 0, 1):
+                        a, b, c = i + di, j + dj, k + dk
+                        if 0 <= a < n and 0 <= b < n and 0 <= c < n:
+                            assert (l, a, b, c) in exist, "proper nesting violated"
+        off = synth.flags_offset(l)
+        n = 1 << l
+        if l < max_level and flags[off + (i * n + j) * n + k]:
+            assert leaf == 0, "flagged subgrid not refined"
+    # every refined subgrid is flagged or needed by a refined same-level neighbour's nesting
+    for (l, i, j, k), leaf in exist.items():
+        if leaf:
+            continue
+        n = 1 << l
+        if flags[synth.flags_offset(l) + (i * n + j) * n + k]:
+            continue
+        needed = False
+        for (l2, a, b, c), leaf2 in exist.items():
+            if l2 == l + 1 and not leaf2 and max(abs(a // 2 - i), abs(b // 2 - j), abs(c // 2 - k)) <= 1:
+                # a refined child-level subgrid whose 26-neighbourhood reaches into (i,j,k)
+                for da in (-1, 0, 1):
+                    for db in (-1, 0, 1):
+                        for dc in (-1, 0, 1):
+                            if ((a + da) // 2, (b + db) // 2, (c + dc) // 2) == (i, j, k):
+                                needed = True
+        assert needed, "refined subgrid neither flagged nor required by nesting"
+    # leaves tile the unit box exactly once
+    lv = t.leaves()
+    depth = int(lv[:, 0].max())
+    n = 1 << depth
+    cover = np.zeros((n, n, n), dtype=np.int32)
+    for l, i, j, k in lv:
+        f = 1 << (depth - l)
+        cover[i * f:(i + 1) * f, j * f:(j + 1) * f, k * f:(k + 1) * f] += 1
+    assert np.all(cover == 1)
+
+
+def test_tree_nesting_binary_and_random_flags():
+    w = synth.workload_binary(4)
+    _check_tree(O.Tree(w.max_level, w.flags), w.max_level, w.flags)
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        fl = (rng.uniform(size=synth.flags_size(4)) < 0.08).astype(np.uint8)
+        fl[0] = 1
+        _check_tree(O.Tree(4, fl), 4, fl)
+
+
+def test_stencil_sizes_and_reach():
+    # per-parity sizes from an independent brute-force enumeration; theta = 0.34 and 0.35 coincide
+    expect = {0.5: 231, 0.35: 651, 0.34: 651, 0.7: 133}
+    for th, n in expect.items():
+        for p in range(8):
+            st = O.stencil(th, p)
+            assert len(st) == n
+            assert np.abs(st).max() <= 5
+            assert len({tuple(r) for r in st}) == n
+
+
+def _tiny_amr_tree():
+    fl = np.zeros(synth.flags_size(3), dtype=np.uint8)
+    fl[0] = 1                                   # root
+    fl[synth.flags_offset(1) + 0] = 1           # level-1 (0,0,0)
+    fl[synth.flags_offset(2) + (1 * 4 + 1) * 4 + 0] = 1   # level-2 (1,1,0)
+    return O.Tree(3, fl), fl
+
+
+def test_every_leaf_pair_covered_exactly_once():
+    """With a single massive source j, phi_i must approximate -m_j/r_ij for every i != j (a pair
+    missed gives 0, a pair counted twice gives about twice the value) and vanish at j."""
+    t, fl = _tiny_amr_tree()
+    lv = t.leaves()
+    assert set(lv[:, 0]) == {1, 2, 3}
+    x, dx = synth.leaf_cell_centres(lv)
+    n = x.shape[0]
+    rng = np.random.default_rng(11)
+    picks = list(rng.choice(n, 10, replace=False))
+    for lev in (1, 2, 3):  # make sure sources at every level are exercised
+        picks.append(int(np.nonzero(np.repeat(lv[:, 0], 512) == lev)[0][137]))
+    for j in picks:
+        rho = np.zeros(n)
+        rho[j] = 1.0 / dx[j] ** 3
+        for theta in (0.5, 0.7):
+            phi, g, _ = O.solve(t, rho, theta)
+            r = np.linalg.norm(x - x[j], axis=1)
+            r[j] = np.inf
+            exact = -1.0 / r
+            assert phi[j] == 0.0
+            exact[j] = -1.0
+            rel = np.abs(phi - exact) / np.abs(exact)
+            rel[j] = 0
+            assert rel.max() < 0.2, (j, theta, rel.max())
+
+
+def test_all_near_reduces_to_direct_sum():
+    for depth in (0, 1):
+        w = synth.workload_uniform_polytrope(depth)
+        t = O.Tree(w.max_level, w.flags)
+        rho = synth.leaf_density(synth.binary_field(0.7, 0.1, 0.085, 0.35), t.leaves())
+        phi, g, cnt = O.solve(t, rho, 0.03)   # below dx/max|x_A-x_B| at depth 1
+        assert cnt["m2l"] == 0
+        x, m = O.leaf_masses(t, rho)
+        pd, gd = O.direct(x, m)
+        assert np.abs(phi - pd).max() <= 1e-13 * np.abs(pd).max()
+        assert np.abs(g - gd).max() <= 1e-13 * np.abs(gd).max()
+
+
+# ------------------------------------------------------------------------------------------
+# whole solve
+# ------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c1():
+    w = synth.workload_uniform_polytrope(2)
+    t = O.Tree(w.max_level, w.flags)
+    rho = synth.leaf_density(w.field, t.leaves())
+    x, m = O.leaf_masses(t, rho)
+    pd, gd = O.direct(x, m)
+    return t, rho, x, m, pd, gd
+
+
+def test_uniform_tree_counts(c1):
+    t, rho, *_ = c1
+    expect = {0.5: (7550136, 982136), 0.35: (19182600, 2733896), 0.7: (4599008, 559488)}
+    for th, (nm, npp) in expect.items():
+        _, _, cnt = O.solve(t, rho, th)
+        assert cnt["m2l"] == nm and cnt["p2p_same"] == npp and cnt["p2p_mixed"] == 0
+
+
+def test_error_vs_direct_falls_with_theta(c1):
+    t, rho, x, m, pd, gd = c1
+    gn = np.linalg.norm(gd, axis=1)
+    w = m / m.sum()
+    prev = None
+    for th in (0.7, 0.5, 0.35):
+        phi, g, _ = O.solve(t, rho, th)
+        ephi = np.abs(phi - pd).max() / np.abs(pd).max()
+        eg = np.sqrt((w * (np.linalg.norm(g - gd, axis=1) / gn) ** 2).sum())
+        if th == 0.5:
+            assert ephi < 5e-3 and eg < 5e-3
+        if prev is not None:
+            assert ephi < prev[0] and eg < prev[1]
+        prev = (ephi, eg)
+
+
+def _net(x, m, g):
+    f = m[:, None] * g
+    F = f.sum(0)
+    T = np.cross(x, f).sum(0)
+    norm = (np.linalg.norm(x, axis=1) * np.linalg.norm(f, axis=1)).sum()
+    return F, T, norm
+
+
+def test_conservation_with_correction_on_amr_binary():
+    # tilted, off-centre binary: no mirror symmetry that would cancel the torque by itself
+    w = synth.workload_binary(3, axis=(1.0, 0.6, 0.3), offset=(0.02, -0.03, 0.05))
+    t = O.Tree(w.max_level, w.flags)
+    rho = synth.leaf_density(w.field, t.leaves())
+    assert len(set(t.leaves()[:, 0])) >= 2
+    x, m = O.leaf_masses(t, rho)
+    phi, g, cnt = O.solve(t, rho, 0.5, amc=True)
+    assert cnt["p2p_mixed"] > 0
+    F, T, n = _net(x, m, g)
+    assert np.abs(F).max() <= 1e-13 * n
+    assert np.abs(T).max() <= 1e-13 * n
+    _, g0, _ = O.solve(t, rho, 0.5, amc=False)
+    F0, T0, n0 = _net(x, m, g0)
+    assert np.abs(F0).max() <= 1e-13 * n0
+    assert np.abs(T0).max() >= 1e-8 * n0
+    assert np.abs(T0).max() >= 1e6 * np.abs(T).max()
+
+
+def test_sampled_solve_equals_full_solve():
+    w = synth.workload_binary(3, axis=(1.0, 0.6, 0.3), offset=(0.02, -0.03, 0.05))
+    t = O.Tree(w.max_level, w.flags)
+    rho = synth.leaf_density(w.field, t.leaves())
+    phi, g, _ = O.solve(t, rho, 0.5)
+    idx = np.random.default_rng(2).choice(rho.size, 40, replace=False)
+    ps, gs = O.sample(t, rho, 0.5, idx)
+    assert np.array_equal(ps, phi[idx]) and np.array_equal(gs, g[idx])
+
+
+def test_uniform_sphere_residuals_band():
+    """Sec. 3.4: residual of phi against the analytic uniform-sphere potential on the equatorial
+    plane, 64^3 cells, theta = 0.5; the paper's table is the soft band."""
+    with open(os.path.join(HERE, "golden", "sphere_residuals.json")) as f:
+        paper = [c for c in json.load(f)["columns"] if c["n_cells"] == 64 and c["theta"] == 0.5][0]
+    w = synth.workload_uniform_sphere(3, 0.5)
+    t = O.Tree(w.max_level, w.flags)
+    rho = synth.leaf_density(w.field, t.leaves())
+    phi, _, _ = O.solve(t, rho, 0.5)
+    x, dx = synth.leaf_cell_centres(t.leaves())
+    m = rho * dx ** 3
+    M = m.sum()   # mass of the point-sampled sphere
+    R = 0.25
+    r = np.linalg.norm(x, axis=1)
+    phi_cells = phi - BETA_CUBE * rho * dx ** 2   # add each cell's own (uniform cube) potential
+    an = np.where(r < R, -M * (3 * R * R - r * r) / (2 * R ** 3), -M / r)
+    eq = np.abs(x[:, 2]) < dx
+    eps = np.abs((phi_cells - an) / an)[eq]
+    assert eps.mean() < 3 * paper["mean"] and eps.mean() > paper["mean"] / 3
+    assert eps.max() < paper["max"]
+
+
+def test_n1_polytrope_closed_form():
+    """n = 1 polytrope: phi = -(4 pi rho_c / k^2) sin(kr)/(kr) - M/R inside, -M/r outside,
+    k = pi/R, M = 4 rho_c R^3 / pi.  Residual falls with resolution."""
+    res = []
+    for depth in (1, 2):
+        fld = synth.n1_polytrope_field(0.25)
+        t = O.Tree(depth, synth.uniform_flags(depth))
+        rho = synth.leaf_density(fld, t.leaves())
+        phi, _, _ = O.solve(t, rho, 0.35)
+        x, dx = synth.leaf_cell_centres(t.leaves())
+        R, rc = 0.25, 1.0
+        k = math.pi / R
+        M = 4 * rc * R ** 3 / math.pi
+        r = np.linalg.norm(x, axis=1)
+        kr = k * r
+        inside = -(4 * math.pi * rc / k ** 2) * np.sin(kr) / kr - M / R
+        an = np.where(r < R, inside, -M / r)
+        phi_cells = phi - BETA_CUBE * rho * dx ** 2
+        star = r < R
+        res.append(np.abs((phi_cells - an) / an)[star].mean())
+    assert res[1] < res[0]
+    assert res[1] < 5e-3

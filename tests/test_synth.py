@@ -1,0 +1,71 @@
+"""Input generator checks (Lane-Emden profiles, binary scaling, splitmix64, flags)."""
+import math
+
+import numpy as np
+
+from paper_2101_08226_gb300 import synth
+
+
+def test_lane_emden_n1_matches_closed_form():
+    # n = 1: theta = sin(xi)/xi, xi_1 = pi
+    tab, xi1 = synth.lane_emden_table(1.0)
+    assert abs(xi1 - math.pi) < 1e-6
+    xi = np.linspace(0.01, 3.1, 200)
+    assert np.abs(synth.lane_emden_theta(1.0, xi) - np.sin(xi) / xi).max() < 1e-8
+
+
+def test_lane_emden_n15_surface():
+    # first zero of the n = 3/2 Lane-Emden function (Chandrasekhar's tables: 3.65375)
+    _, xi1 = synth.lane_emden_table(1.5)
+    assert abs(xi1 - 3.65375) < 1e-4
+
+
+def test_binary_mass_ratio_and_com():
+    fld = synth.binary_field(0.7, 0.1, 0.085, 0.35)
+    s1, s2 = fld.stars
+    # centre of mass at the origin, separation a
+    m_ratio_expected = 0.7
+    assert abs((s2.center[0] - s1.center[0]) - 0.35) < 1e-15
+    # integrate each profile radially: M = int 4 pi r^2 rho dr
+    def mass(s):
+        r = np.linspace(0, s.radius, 200001)
+        return np.trapezoid(4 * np.pi * r * r * s.rho_of_r(r), r)
+    M1, M2 = mass(s1), mass(s2)
+    assert abs(M2 / M1 - m_ratio_expected) < 1e-6
+    assert abs(M1 * s1.center[0] + M2 * s2.center[0]) < 1e-6 * M1
+
+
+def test_splitmix64_published_vector():
+    # splitmix64 with state 0: first output 0xE220A8397B1DCDAF (Steele, Lea, Flood 2014 reference)
+    assert synth.SplitMix64(0).next_u64() == 0xE220A8397B1DCDAF
+
+
+def test_refinement_flags_match_brute_force_small():
+    fld = synth.binary_field(0.7, 0.1, 0.085, 0.35)
+    flags = synth.refinement_flags(fld, 3, 1e-4)
+    thr = 1e-4 * fld.rho_peak
+    for lev in range(3):
+        n = 1 << lev
+        ii, jj, kk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+        ijk = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1)
+        c = synth.cell_centres(lev, ijk).reshape(len(ijk), 512, 3)
+        brute = (fld.rho(c).max(axis=1) > thr).astype(np.uint8)
+        off = synth.flags_offset(lev)
+        assert np.array_equal(flags[off:off + n ** 3], brute)
+
+
+def test_perturbed_density_bounds_and_seed():
+    rho0 = np.full(1000, 2.0)
+    a = synth.perturbed_density(rho0, 3, floor_value=1.0)
+    b = synth.perturbed_density(rho0, 3, floor_value=1.0)
+    assert np.array_equal(a, b)
+    assert np.all(np.abs(a / 2.0 - 1.0) <= 1e-3)
+    assert not np.array_equal(a, synth.perturbed_density(rho0, 4, floor_value=1.0))
+
+
+def test_batched_workloads_are_deterministic_and_valid():
+    w1 = synth.batched_workloads(4)
+    w2 = synth.batched_workloads(4)
+    for a, b in zip(w1, w2):
+        assert a.max_level == b.max_level and np.array_equal(a.flags, b.flags)
+        assert 2 <= a.max_level <= 5
