@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark of the octree FMM gravity solve (Sec. 2.2) on GB300.
+
+Workload: the AMR binary of two n = 3/2 polytropes (mass ratio 0.7, radii 0.1 and 0.085,
+separation 0.35, density floor 1e-10, subgrids refined where the density exceeds 1e-4 of the
+peak, 5 refinement levels: 1961 subgrids, 878,592 leaf cells), theta = 0.5, angular-momentum
+correction on.  One step = one whole solve (multipoles up, multipole interactions and near field,
+expansions down, net force and torque) on that step's density, perturbed by seeded 1e-3 noise.
+
+Metric: directed cell-cell multipole interactions per second (direct near-field pairs are
+reported separately), and ms per solve, for the FP64 path (`value`) and the mixed FP32/FP64 path
+(`mixed`), each with its error against the FP64 path on the same input.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own replica of the workload (independent trees, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+THETA = 0.5
+LEVELS = 5
+WORKLOAD = ("AMR binary: two n=3/2 polytropes, q=0.7, R=0.1/0.085, a=0.35, floor 1e-10, "
+            "refine where rho > 1e-4 rho_peak, 5 levels, theta=0.5, AMC on")
+METRIC = "FMM cell-cell interactions/s (directed M2L pairs) and gravity-solve ms per solve"
+
+# Algorithmic flops per directed interaction, counted from the kernels' formulas (an FMA counts
+# 2, a reciprocal square root 1): leaf<-leaf and direct pairs need only the monopole field; a
+# refined source adds its 2nd and 3rd moments; a refined target adds the 2nd and 3rd derivatives
+# of its expansion; the correction needs the 4th derivative contracted with 3rd moments.
+FLOPS = {"m2l_leaf_leaf": 20, "m2l_leaf_refined": 199, "m2l_refined_leaf": 186,
+         "m2l_refined_refined": 309, "p2p_same": 20, "p2p_mixed": 20}
+SMS = 152
+SM_MAX_GHZ = 2.07
+FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1e3    # 2 FP64 FMA / clock / SM
+FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MAX_GHZ / 1e3  # 128 FP32 FMA / clock / SM
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    def __init__(self, dev_uuid):
+        self.path = tempfile.mktemp(suffix=".csv")
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", dev_uuid, f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], None, set()
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_flops(counts):
+    return sum(FLOPS[k] * v for k, v in counts.items())
+
+
+def cpu_baseline(seconds_target=15.0):
+    """The oracle, as it stands, on a bounded sample of the same workload: phi and g at randomly
+    chosen leaf cells, each with its ancestors' expansions and its direct sums."""
+    import oracle as O
+    from paper_2101_08226_gb300 import synth
+    w = synth.workload_binary(LEVELS)
+    t = O.Tree(w.max_level, w.flags)
+    rho = synth.leaf_density(w.field, t.leaves())
+    rng = np.random.default_rng(20210120)
+    ns = 512
+    while True:
+        idx = rng.choice(rho.size, ns, replace=False)
+        t0 = time.perf_counter()
+        _, _, c = O.sample(t, rho, THETA, idx, with_counts=True)
+        dt = time.perf_counter() - t0
+        if dt >= seconds_target / 4 or ns >= rho.size // 4:
+            break
+        ns = min(rho.size // 4, int(ns * max(2.0, seconds_target / max(dt, 1e-3))))
+    return {"value": c["m2l"] / dt, "unit": "interactions/s", "cores": O.max_threads(),
+            "kind": "oracle",
+            "sample": f"{ns} random leaf cells of the same tree (their own and their ancestors' "
+                      f"{c['m2l']} multipole interactions and {c['p2p_same'] + c['p2p_mixed']} "
+                      f"direct pairs), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2101_08226_gb300 import synth
+    w = synth.workload_binary(LEVELS)
+    t = O.Tree(w.max_level, w.flags)
+    rho = synth.leaf_density(w.field, t.leaves())
+    rng = np.random.default_rng(7)
+    ns = 2048
+    rates, times = [], []
+    total_m2l = 0
+    for step in range(args.warmup + args.steps):
+        idx = rng.choice(rho.size, ns, replace=False)
+        t0 = time.perf_counter()
+        _, _, c = O.sample(t, rho, THETA, idx, with_counts=True)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            total_m2l += c["m2l"]
+    value = total_m2l / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "interactions/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "levels": LEVELS, "theta": THETA},
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": O.max_threads(),
+                             "kind": "oracle",
+                             "sample": f"each step: {ns} random leaf cells of the same tree"},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    from paper_2101_08226_gb300 import api, build, synth
+    build.build()
+    dev = torch.device("cuda", local_rank)
+
+    w = synth.workload_binary(LEVELS)
+    tree = api.Tree(w.max_level, w.flags)
+    n_sub, n_leaf_sub, depth = tree.info()
+    n = n_leaf_sub * 512
+    rho0 = synth.leaf_density(w.field, tree.leaves())
+    counts = tree.counts_by_type(THETA)
+    n_m2l = sum(v for k, v in counts.items() if k.startswith("m2l"))
+    flops = algorithmic_flops(counts)
+    m2l_flops = flops  # every counted interaction runs in the interaction kernel
+    floor = w.field.floor * w.field.rho_peak
+    n_steps = args.warmup + args.steps
+    rhos = [torch.from_numpy(synth.perturbed_density(rho0, rank * 1000 + k, floor_value=floor)).to(dev)
+            for k in range(n_steps)]
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    g = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    net = torch.empty(7, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+
+    def timed(precision, sampler=None):
+        tree.set_profiling(True)
+        for k in range(args.warmup):
+            tree.solve(rhos[k], THETA, precision, True, phi, g, net, stream, check_status=False)
+        torch.cuda.synchronize()
+        tree.sync_status(stream)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        step_ms, m2l_ms, phases = [], [], []
+        for k in range(args.warmup, n_steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tree.solve(rhos[k], THETA, precision, True, phi, g, net, stream, check_status=False)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            ph = tree.phase_times()
+            phases.append(ph)
+            m2l_ms.append(float(ph[1]))
+        torch.cuda.synchronize()
+        tree.sync_status(stream)
+        total = float(np.sum(step_ms))
+        if world > 1:
+            tt = torch.tensor([total], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            total = float(tt.item())
+        launches = tree.last_launches() * args.steps
+        return total, float(np.mean(m2l_ms)), np.mean(np.array(phases), axis=0), launches
+
+    sampler = ClockSampler(uuid) if (uuid and rank == 0) else None
+    t64, m2l64, ph64, l64 = timed("fp64")
+    phi64, g64, net64 = phi.clone(), g.clone(), net.clone()
+    t32, m2l32, ph32, l32 = timed("mixed")
+    clocks = sampler.stop() if sampler else None
+    # mixed-path error against the FP64 path on the same (last) input
+    gn = g64.norm(dim=1)
+    m = rhos[-1] * torch.from_numpy(np.repeat(1.0 / (8 * 2.0 ** tree.leaves()[:, 0]) ** 3, 512)).to(dev)
+    wgt = m / m.sum()
+    err = {
+        "g_inf_rel": float(((g - g64).abs().max() / g64.abs().max()).item()),
+        "g_rms_mass_weighted": float(torch.sqrt((wgt * ((g - g64).norm(dim=1) / gn) ** 2).sum()).item()),
+        "phi_max_rel": float(((phi - phi64).abs() / phi64.abs()).max().item()),
+        "torque_over_norm": float((net[3:6].abs().max() / net[6]).item()),
+        "torque_over_norm_fp64": float((net64[3:6].abs().max() / net64[6]).item()),
+        "force_over_norm_fp64": float((net64[:3].abs().max() / net64[6]).item()),
+    }
+
+    # end to end through the C ABI with pinned host buffers, copies inside the timed region
+    rho_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    rho_h.copy_(rhos[-1].cpu())
+    phi_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    g_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    net_h = torch.empty(7, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        tree.solve_host(rho_h.numpy(), THETA, "fp64", True, phi_h.numpy(), g_h.numpy(), net_h.numpy(), stream)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        tree.solve_host(rho_h.numpy(), THETA, "fp64", True, phi_h.numpy(), g_h.numpy(), net_h.numpy(), stream)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    cpu = cpu_baseline() if world == 1 else None
+    value64 = world * n_m2l * args.steps / (t64 * 1e-3)
+    value32 = world * n_m2l * args.steps / (t32 * 1e-3)
+    ach64 = m2l_flops / (m2l64 * 1e-3) / 1e12
+    ach32 = m2l_flops / (m2l32 * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value64, "unit": "interactions/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t64 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "levels": LEVELS, "theta": THETA, "subgrids": n_sub,
+                   "leaf_cells": n, "m2l_pairs": n_m2l, "p2p_pairs": counts["p2p_same"],
+                   "p2p_mixed_pairs": counts["p2p_mixed"], "pair_types": counts,
+                   "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": f"{world} independent replicas"},
+        "roofline": {"bound": "alu", "kernel": "k_m2l<double>", "achieved": ach64,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
+                     "traffic": None, "m2l_kernel_ms": m2l64,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"},
+        "phases_ms": {"upward": float(ph64[0]), "interactions": float(ph64[1]),
+                      "downward": float(ph64[2]), "reductions": float(ph64[3])},
+        "mixed": {"value": value32, "ms_per_step": t32 / args.steps, "dtype": "f32 pairs, f64 rest",
+                  "speedup_vs_fp64": t64 / t32, "err_vs_fp64": err,
+                  "roofline": {"bound": "alu", "kernel": "k_m2l<float>", "achieved": ach32,
+                               "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": ach32 / FP32_PEAK_TFLOPS, "traffic": None,
+                               "m2l_kernel_ms": m2l32,
+                               "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"},
+                  "phases_ms": {"upward": float(ph32[0]), "interactions": float(ph32[1]),
+                                "downward": float(ph32[2]), "reductions": float(ph32[3])},
+                  "gpu_launches": l32},
+        "e2e": {"value": world * n_m2l * args.steps / e2e_s, "unit": "interactions/s",
+                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n + 24 * n + 56,
+                "precision": "fp64"},
+        "gpu_launches": l64,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

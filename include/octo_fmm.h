@@ -1,0 +1,142 @@
+/*
+ * octo_fmm.h -- C ABI of the GB300 (sm_103a) octree FMM gravity solver.
+ *
+ * The solver computes the gravitational potential phi and acceleration g = -grad phi (G = 1) of a
+ * density field given on the leaf cells of an octree of 8x8x8-cell subgrids, with the Cartesian
+ * fast multipole method and the angular-momentum correction described in Marcello et al. 2021
+ * (arXiv 2101.08226), Sec. 2.2; the mesh and its proper nesting follow Sec. 2.4.
+ *
+ * Geometry.  The domain is the unit box [-1/2, 1/2]^3.  A level-l subgrid at integer position
+ * (i, j, k) in [0, 2^l)^3 covers [-1/2 + i/2^l, -1/2 + (i+1)/2^l] x ...; its 512 cells have width
+ * dx_l = 1 / (8 * 2^l) and are numbered (a*8 + b)*8 + c within the subgrid (c, the z index,
+ * fastest).  Every leaf cell is a point mass m = rho * dx^3 at its centre.
+ *
+ * Canonical leaf order.  Leaf subgrids are ordered by level, then by the Morton key of (i, j, k)
+ * (bits interleaved x, y, z from most to least significant within each triple); a leaf cell's
+ * index is (leaf-subgrid ordinal) * 512 + (a*8 + b)*8 + c.  Every per-cell array below (rho, phi,
+ * g) uses this order.
+ *
+ * Ownership.  The caller owns every density / potential / acceleration buffer and the CUDA stream;
+ * the library owns the tree, its device-resident tables and its workspace (allocated on the
+ * first solve, freed by fmm_destroy).  Pointers named *_dev are device pointers on the current
+ * CUDA device; pointers named *_host are host pointers (pinned memory gives faster copies).
+ *
+ * Errors.  Every int-returning entry point returns FMM_OK (0) or a negative FMM_ERR_* code and
+ * never aborts or throws; fmm_last_error() gives a message for the calling thread.  Solves are
+ * enqueued asynchronously on `stream`; problems found on the device (a non-finite or negative
+ * density) are recorded in the tree's status word and reported by fmm_sync_status().
+ *
+ * Threads.  A tree may be used by one host thread at a time.  Different trees are independent.
+ */
+#ifndef OCTO_FMM_H
+#define OCTO_FMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FMM_OK 0
+#define FMM_ERR_ARG (-1)       /* invalid argument (null pointer, size mismatch, bad level) */
+#define FMM_ERR_THETA (-3)     /* opening criterion outside [0.34, 1) */
+#define FMM_ERR_CUDA (-4)      /* a CUDA runtime call failed */
+#define FMM_ERR_NONFINITE (-6) /* a density was negative, NaN or infinite (found on the device) */
+#define FMM_ERR_NOMEM (-7)     /* host or device allocation failed */
+#define FMM_ERR_STATE (-8)     /* tree not usable (destroyed or built on another device) */
+
+#define FMM_FP64 0  /* every step in FP64 */
+#define FMM_MIXED 1 /* multipole interactions and direct sums in FP32; moments, shifts,
+                       correction sums and reductions in FP64 */
+
+#define FMM_MAX_LEVEL 9 /* deepest refinement level accepted (levels 0..9) */
+
+typedef struct fmm_tree fmm_tree;
+
+/* Build the octree (Sec. 2.4, refinement as in Sec. 2.7).
+ * refine_flags: host array of dense per-level flags for levels 0 .. max_level-1; level l occupies
+ *   8^l bytes starting at sum_{k<l} 8^k, indexed (i * 2^l + j) * 2^l + k.  A subgrid that exists
+ *   and is flagged is refined; flags of positions that do not exist are ignored.  Further
+ *   subgrids are refined until proper nesting holds: every refined subgrid has all 26
+ *   same-level neighbours inside the domain, so leaf levels differ by at most one across any
+ *   subgrid boundary.
+ * n_flags must equal sum_{l<max_level} 8^l; 0 <= max_level <= FMM_MAX_LEVEL.
+ * On success *out receives a new tree (destroy with fmm_destroy).  Host-only: needs no GPU. */
+int fmm_build_tree(int max_level, const uint8_t* refine_flags, int64_t n_flags, fmm_tree** out);
+
+/* Release a tree and its device workspace.  NULL is ignored. */
+void fmm_destroy(fmm_tree* tree);
+
+/* Sizes: total subgrids, leaf subgrids (leaf cells = 512 * n_leaf_subgrids), deepest level.
+ * Any output pointer may be NULL. */
+int fmm_tree_info(const fmm_tree* tree, int64_t* n_subgrids, int64_t* n_leaf_subgrids,
+                  int32_t* depth);
+
+/* Rows (level, i, j, k, is_leaf) of every subgrid, by level then Morton key: host array of
+ * 5 * n_subgrids int32. */
+int fmm_tree_subgrids(const fmm_tree* tree, int32_t* rows_host);
+
+/* Same-level interaction stencil (Sec. 2.2 opening criterion): the offsets d (in cells) for which
+ * cells A and A + d are well separated, dx/|x_A - x_B| < theta, while their parents are not.
+ * parity = (a & 1) << 2 | (b & 1) << 1 | (c & 1) of the target cell.  Writes up to `capacity`
+ * rows (dx, dy, dz) in lexicographic order into offsets_host and the full count into *count. */
+int fmm_stencil(double theta, int parity, int32_t* offsets_host, int32_t capacity,
+                int32_t* count);
+
+/* Directed interaction counts of one solve at this theta (host-only):
+ *   counts[0] multipole (cell-cell) interactions over all levels,
+ *   counts[1] direct leaf-leaf pairs at the same level,
+ *   counts[2] direct leaf-leaf pairs across one level jump. */
+int fmm_interaction_counts(const fmm_tree* tree, double theta, int64_t counts_host[3]);
+
+/* The same counts split by the kind of arithmetic they need (host-only), 6 entries:
+ *   [0] multipole interactions leaf cell <- leaf cell     [1] leaf cell <- refined cell
+ *   [2] refined cell <- leaf cell                          [3] refined cell <- refined cell
+ *   [4] same-level direct pairs                            [5] direct pairs across a level jump
+ * A refined cell has children (it carries 2nd and 3rd moments and needs the 2nd and 3rd
+ * derivatives of its expansion); a leaf cell is a point mass. */
+int fmm_interaction_counts_by_type(const fmm_tree* tree, double theta, int64_t counts_host[6]);
+
+/* One gravity solve (Sec. 2.2): multipoles up the tree, same-level multipole interactions with
+ * the angular-momentum correction (amc != 0), direct near-field sums, expansions down the tree.
+ * rho_dev: [n_leaf] leaf-cell densities (>= 0, finite).  phi_dev: [n_leaf] potential.
+ * g_dev: [n_leaf][3] acceleration.  net_dev (optional, may be NULL): 7 doubles
+ *   (F_x, F_y, F_z, T_x, T_y, T_z, S) with F = sum m g, T = sum x cross m g, S = sum |x| |m g|,
+ *   reduced in FP64 in a fixed order.
+ * theta in [0.34, 1).  precision FMM_FP64 or FMM_MIXED.  stream: a cudaStream_t (NULL = legacy
+ * default stream).  Asynchronous: returns once the work is enqueued. */
+int fmm_solve(fmm_tree* tree, const double* rho_dev, double theta, int precision, int amc,
+              double* phi_dev, double* g_dev, double* net_dev, void* stream);
+
+/* Waits for `stream`, then returns FMM_OK, or FMM_ERR_NONFINITE if a solve since the last call
+ * met an invalid density, or FMM_ERR_CUDA; clears the recorded status. */
+int fmm_sync_status(fmm_tree* tree, void* stream);
+
+/* End-to-end solve with host buffers: copies rho_host to the device, solves, copies phi, g and
+ * (if net_host is not NULL) the 7 net sums back, and waits for completion.  The device buffers
+ * are owned by the tree.  Returns the solve's status. */
+int fmm_solve_host(fmm_tree* tree, const double* rho_host, double theta, int precision, int amc,
+                   double* phi_host, double* g_host, double* net_host, void* stream);
+
+/* Net force, torque and normalisation (as net_dev above) of an arbitrary acceleration field g_dev
+ * for the masses given by rho_dev on this tree's leaf cells.  Uses the tree's workspace. */
+int fmm_net_force_torque(fmm_tree* tree, const double* rho_dev, const double* g_dev,
+                         double* net_dev, void* stream);
+
+/* Per-phase device times (ms) of the most recent solve on this tree, measured with CUDA events
+ * on the solve's stream when profiling is on: [0] upward pass, [1] multipole interactions and
+ * near field, [2] downward pass, [3] reductions.  fmm_set_profiling(tree, 1) turns it on. */
+int fmm_set_profiling(fmm_tree* tree, int on);
+int fmm_phase_times(fmm_tree* tree, float* ms_host, int n);
+
+/* Number of kernels the most recent solve on this tree launched (all of them this library's). */
+int fmm_last_launches(const fmm_tree* tree, int32_t* n);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* fmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCTO_FMM_H */

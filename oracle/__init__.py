@@ -40,7 +40,7 @@ def lib():
         L.oracle_stencil.restype = i32
         L.oracle_fmm_solve.argtypes = [vp, vp, dbl, i32, i32, vp, vp, vp]
         L.oracle_fmm_solve.restype = None
-        L.oracle_fmm_sample.argtypes = [vp, vp, dbl, i32, i32, i64, vp, vp, vp]
+        L.oracle_fmm_sample.argtypes = [vp, vp, dbl, i32, i32, i64, vp, vp, vp, vp]
         L.oracle_fmm_sample.restype = None
         L.oracle_inner_moments.argtypes = [vp, vp, i32, vp]
         L.oracle_inner_moments.restype = None
@@ -127,13 +127,17 @@ def solve(tree: Tree, rho: np.ndarray, theta: float, amc: bool = True,
 
 
 def sample(tree: Tree, rho: np.ndarray, theta: float, idx: np.ndarray, amc: bool = True,
-           nthreads: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+           nthreads: int = 0, with_counts: bool = False):
+    """phi, g at the listed leaf cells (and, with_counts, the interactions evaluated)."""
     rho = _f64(rho)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     phi = np.empty(idx.size)
     g = np.empty((idx.size, 3))
+    cnt = np.zeros(3, dtype=np.int64)
     lib().oracle_fmm_sample(tree._h, _p(rho), float(theta), int(bool(amc)), int(nthreads),
-                            int(idx.size), _p(idx), _p(phi), _p(g))
+                            int(idx.size), _p(idx), _p(phi), _p(g), _p(cnt))
+    if with_counts:
+        return phi, g, {"m2l": int(cnt[0]), "p2p_same": int(cnt[1]), "p2p_mixed": int(cnt[2])}
     return phi, g
 
 

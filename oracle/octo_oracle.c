@@ -308,7 +308,20 @@ static void visit_leaves(const otree *t, int lev, const int64_t g[3], leaf_visit
   }
 }
 
-typedef struct { const ctx_t *C; double m, mx[3]; const double *X; double M2[9], M3[27]; } mom_acc;
+/* Compensated (Neumaier 1974) running sum: the moment sums of a coarse cell run over up to
+ * 10^6 leaves, and a plain running sum would lose up to ~N eps of their magnitude. */
+typedef struct { double s, c; } csum;
+
+static void csum_add(csum *a, double v) {
+  double t = a->s + v;
+  if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+  else a->c += (v - t) + a->s;
+  a->s = t;
+}
+
+static double csum_val(const csum *a) { return a->s + a->c; }
+
+typedef struct { const ctx_t *C; csum m, mx[3]; const double *X; csum M2[9], M3[27]; } mom_acc;
 
 static void leaf_mass_of(const ctx_t *C, int lev, const int64_t g[3], double *m, double x[3]) {
   int64_t s = cell_subgrid(C->t, lev, g);
@@ -321,8 +334,8 @@ static void acc_first(void *u, int lev, const int64_t g[3]) {
   mom_acc *A = (mom_acc *)u;
   double m, x[3];
   leaf_mass_of(A->C, lev, g, &m, x);
-  A->m += m;
-  for (int a = 0; a < 3; ++a) A->mx[a] += m * x[a];
+  csum_add(&A->m, m);
+  for (int a = 0; a < 3; ++a) csum_add(&A->mx[a], m * x[a]);
 }
 
 static void acc_second(void *u, int lev, const int64_t g[3]) {
@@ -332,8 +345,8 @@ static void acc_second(void *u, int lev, const int64_t g[3]) {
   for (int a = 0; a < 3; ++a) r[a] = x[a] - A->X[a];
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
-      A->M2[3 * a + b] += m * r[a] * r[b];
-      for (int c = 0; c < 3; ++c) A->M3[9 * a + 3 * b + c] += m * r[a] * r[b] * r[c];
+      csum_add(&A->M2[3 * a + b], m * r[a] * r[b]);
+      for (int c = 0; c < 3; ++c) csum_add(&A->M3[9 * a + 3 * b + c], m * r[a] * r[b] * r[c]);
     }
 }
 
@@ -344,16 +357,17 @@ static void inner_cell_moments(const ctx_t *C, int lev, const int64_t g[3], doub
   A.C = C;
   visit_leaves(C->t, lev, g, acc_first, &A);
   memset(mom, 0, sizeof(double) * NMOM);
-  mom[0] = A.m;
-  if (A.m > 0) {
-    for (int a = 0; a < 3; ++a) mom[1 + a] = A.mx[a] / A.m;
+  double m = csum_val(&A.m);
+  mom[0] = m;
+  if (m > 0) {
+    for (int a = 0; a < 3; ++a) mom[1 + a] = csum_val(&A.mx[a]) / m;
   } else {
     cell_centre(lev, g, mom + 1);
   }
   A.X = mom + 1;
   visit_leaves(C->t, lev, g, acc_second, &A);
-  memcpy(mom + 4, A.M2, sizeof(A.M2));
-  memcpy(mom + 13, A.M3, sizeof(A.M3));
+  for (int k = 0; k < 9; ++k) mom[4 + k] = csum_val(&A.M2[k]);
+  for (int k = 0; k < 27; ++k) mom[13 + k] = csum_val(&A.M3[k]);
 }
 
 static void compute_inner_moments(ctx_t *C, int nthreads) {
@@ -642,7 +656,7 @@ static void leaf_solve(const ctx_t *C, int lev, const int64_t g[3], double theta
       memcpy(LA, src, sizeof(LA));
       memcpy(acA, src + NLOC, sizeof(acA));
     } else {
-      cell_expansion(C, m, gA, theta, amc, LA, acA, NULL);
+      cell_expansion(C, m, gA, theta, amc, LA, acA, &nm);
     }
     oracle_local_eval(LA, momA + 1, x, ev);
     ph += ev[0];
@@ -747,17 +761,25 @@ void oracle_fmm_solve(const otree *t, const double *rho, double theta, int amc, 
  * Multipoles of all refined cells are formed; expansions are formed only along the sampled
  * leaves' ancestor chains. */
 void oracle_fmm_sample(const otree *t, const double *rho, double theta, int amc, int nthreads,
-                       int64_t ns, const int64_t *idx, double *phi, double *g) {
+                       int64_t ns, const int64_t *idx, double *phi, double *g, int64_t *counts) {
   nthreads = resolve_threads(nthreads);
   ctx_t C = {t, rho, NULL};
   compute_inner_moments(&C, nthreads);
-#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+  int64_t n_m2l = 0, n_same = 0, n_mixed = 0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(+ : n_m2l, n_same, n_mixed)
   for (int64_t q = 0; q < ns; ++q) {
     int lev = 0;
     int64_t gc[3] = {0, 0, 0};
+    int64_t cc[3] = {0, 0, 0};
     leaf_cell_coords(t, idx[q], &lev, gc);
-    leaf_solve(&C, lev, gc, theta, amc, NULL, phi + q, g + 3 * q, NULL);
+    leaf_solve(&C, lev, gc, theta, amc, NULL, phi + q, g + 3 * q, cc);
+    n_m2l += cc[0];
+    n_same += cc[1];
+    n_mixed += cc[2];
   }
+  /* counts: multipole interactions evaluated (the sampled leaves' own and their ancestors'),
+   * direct pairs at the same level and across a level jump */
+  if (counts) { counts[0] = n_m2l; counts[1] = n_same; counts[2] = n_mixed; }
   free(C.inner_mom);
 }
 

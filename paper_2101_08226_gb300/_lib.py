@@ -1,0 +1,74 @@
+"""ctypes binding of libocto_fmm.so: the C ABI of include/octo_fmm.h, names unchanged.
+
+Argument marshalling only.  The library must have been built (paper_2101_08226_gb300.build);
+loading fails loudly otherwise -- there is no fallback implementation.
+"""
+import ctypes as C
+import os
+
+from . import build as _build
+
+FMM_OK = 0
+FMM_ERR_ARG = -1
+FMM_ERR_THETA = -3
+FMM_ERR_CUDA = -4
+FMM_ERR_NONFINITE = -6
+FMM_ERR_NOMEM = -7
+FMM_ERR_STATE = -8
+FMM_FP64 = 0
+FMM_MIXED = 1
+
+EXPORTS = [
+    "fmm_build_tree", "fmm_destroy", "fmm_tree_info", "fmm_tree_subgrids", "fmm_stencil",
+    "fmm_interaction_counts", "fmm_interaction_counts_by_type", "fmm_last_launches", "fmm_solve", "fmm_sync_status", "fmm_solve_host",
+    "fmm_net_force_torque", "fmm_set_profiling", "fmm_phase_times", "fmm_last_error",
+]
+
+_lib = None
+
+
+class FmmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"octo_fmm error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"CUDA library {path} is missing: run paper_2101_08226_gb300.build.build() "
+                "(there is no CPU fallback)")
+        L = C.CDLL(path)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        sig = {
+            "fmm_build_tree": (i32, [i32, vp, i64, C.POINTER(vp)]),
+            "fmm_destroy": (None, [vp]),
+            "fmm_tree_info": (i32, [vp, vp, vp, vp]),
+            "fmm_tree_subgrids": (i32, [vp, vp]),
+            "fmm_stencil": (i32, [dbl, i32, vp, i32, vp]),
+            "fmm_interaction_counts": (i32, [vp, dbl, vp]),
+            "fmm_interaction_counts_by_type": (i32, [vp, dbl, vp]),
+            "fmm_last_launches": (i32, [vp, vp]),
+            "fmm_solve": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
+            "fmm_sync_status": (i32, [vp, vp]),
+            "fmm_solve_host": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
+            "fmm_net_force_torque": (i32, [vp, vp, vp, vp, vp]),
+            "fmm_set_profiling": (i32, [vp, i32]),
+            "fmm_phase_times": (i32, [vp, vp, i32]),
+            "fmm_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(code: int) -> int:
+    if code != FMM_OK:
+        raise FmmError(code, lib().fmm_last_error().decode())
+    return code

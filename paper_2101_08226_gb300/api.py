@@ -1,0 +1,142 @@
+"""Thin Python API over the C ABI.  PyTorch provides device memory and streams only; every step
+of the solve runs in the library's CUDA kernels."""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import _lib
+from ._lib import check, lib
+
+PRECISIONS = {"fp64": _lib.FMM_FP64, "mixed": _lib.FMM_MIXED}
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def stencil(theta: float, parity: int) -> np.ndarray:
+    n = C.c_int32(0)
+    check(lib().fmm_stencil(float(theta), int(parity), None, 0, C.byref(n)))
+    out = np.empty((max(n.value, 1), 3), dtype=np.int32)
+    check(lib().fmm_stencil(float(theta), int(parity), _p(out), n.value, C.byref(n)))
+    return out[:n.value]
+
+
+class Tree:
+    """Octree of 8^3-cell subgrids owned by the CUDA library (fmm_build_tree / fmm_destroy)."""
+
+    def __init__(self, max_level: int, flags: np.ndarray):
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        h = C.c_void_p()
+        check(lib().fmm_build_tree(int(max_level), _p(flags), int(flags.size), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fmm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> Tuple[int, int, int]:
+        ns, nl, d = C.c_int64(), C.c_int64(), C.c_int32()
+        check(lib().fmm_tree_info(self._h, C.byref(ns), C.byref(nl), C.byref(d)))
+        return ns.value, nl.value, d.value
+
+    @property
+    def n_leaf_cells(self) -> int:
+        return self.info()[1] * 512
+
+    def subgrids(self) -> np.ndarray:
+        out = np.empty((self.info()[0], 5), dtype=np.int32)
+        check(lib().fmm_tree_subgrids(self._h, _p(out)))
+        return out
+
+    def leaves(self) -> np.ndarray:
+        s = self.subgrids()
+        return s[s[:, 4] == 1][:, :4].copy()
+
+    def counts(self, theta: float) -> dict:
+        out = np.zeros(3, dtype=np.int64)
+        check(lib().fmm_interaction_counts(self._h, float(theta), _p(out)))
+        return {"m2l": int(out[0]), "p2p_same": int(out[1]), "p2p_mixed": int(out[2])}
+
+    def counts_by_type(self, theta: float) -> dict:
+        out = np.zeros(6, dtype=np.int64)
+        check(lib().fmm_interaction_counts_by_type(self._h, float(theta), _p(out)))
+        keys = ("m2l_leaf_leaf", "m2l_leaf_refined", "m2l_refined_leaf", "m2l_refined_refined",
+                "p2p_same", "p2p_mixed")
+        return dict(zip(keys, (int(v) for v in out)))
+
+    def last_launches(self) -> int:
+        n = C.c_int32()
+        check(lib().fmm_last_launches(self._h, C.byref(n)))
+        return n.value
+
+    def solve(self, rho, theta: float, precision: str = "fp64", amc: bool = True, phi=None,
+              g=None, net=None, stream=None, check_status: bool = True):
+        """rho: CUDA float64 tensor [n_leaf].  Returns (phi, g, net) CUDA tensors."""
+        import torch
+        n = self.n_leaf_cells
+        assert rho.is_cuda and rho.dtype == torch.float64 and rho.is_contiguous() and rho.numel() == n
+        if phi is None:
+            phi = torch.empty(n, dtype=torch.float64, device=rho.device)
+        if g is None:
+            g = torch.empty((n, 3), dtype=torch.float64, device=rho.device)
+        if net is None:
+            net = torch.empty(7, dtype=torch.float64, device=rho.device)
+        sh = _stream_handle(stream)
+        check(lib().fmm_solve(self._h, rho.data_ptr(), float(theta), PRECISIONS[precision],
+                              int(bool(amc)), phi.data_ptr(), g.data_ptr(),
+                              net.data_ptr() if net is not False else None, sh))
+        if check_status:
+            check(lib().fmm_sync_status(self._h, sh))
+        return phi, g, net
+
+    def sync_status(self, stream=None):
+        check(lib().fmm_sync_status(self._h, _stream_handle(stream)))
+
+    def solve_host(self, rho: np.ndarray, theta: float, precision: str = "fp64", amc: bool = True,
+                   phi: Optional[np.ndarray] = None, g: Optional[np.ndarray] = None,
+                   net: Optional[np.ndarray] = None, stream=None):
+        """Host buffers in and out (the copies are part of the call)."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        n = self.n_leaf_cells
+        assert rho.size == n
+        phi = np.empty(n) if phi is None else phi
+        g = np.empty((n, 3)) if g is None else g
+        net = np.empty(7) if net is None else net
+        check(lib().fmm_solve_host(self._h, _p(rho), float(theta), PRECISIONS[precision],
+                                   int(bool(amc)), _p(phi), _p(g), _p(net),
+                                   _stream_handle(stream)))
+        return phi, g, net
+
+    def net_force_torque(self, rho, g, stream=None):
+        import torch
+        net = torch.empty(7, dtype=torch.float64, device=rho.device)
+        sh = _stream_handle(stream)
+        check(lib().fmm_net_force_torque(self._h, rho.data_ptr(), g.data_ptr(), net.data_ptr(), sh))
+        check(lib().fmm_sync_status(self._h, sh))
+        return net
+
+    def set_profiling(self, on: bool = True):
+        check(lib().fmm_set_profiling(self._h, int(bool(on))))
+
+    def phase_times(self) -> np.ndarray:
+        out = np.zeros(4, dtype=np.float32)
+        check(lib().fmm_phase_times(self._h, _p(out), 4))
+        return out

@@ -1,0 +1,1070 @@
+// GB300 (sm_103a) octree FMM gravity solve behind the C ABI of octo_fmm.h.
+//
+// One solve (Sec. 2.2 of Marcello et al. 2021) is a fixed sequence of kernels on the caller's
+// stream:
+//   p2m        leaf cells become point masses at their centres
+//   m2m        level by level from the finest: exact shift of the 8 children's moments
+//   m2l        every cell of every level at once: same-level multipole interactions over the
+//              opening-criterion stencil with the angular-momentum correction, plus, for leaf
+//              cells, the direct sums with non-separated leaves of the same level and of the
+//              adjacent level (proper nesting bounds level jumps to one)
+//   l2l        level by level from the root: exact Taylor shift of the parent's expansion, added
+//              to the cell's own; leaf cells write phi and g
+//   reduce     net force, net torque and their normalisation in FP64, fixed order
+// The FP64 path runs everything in double precision.  The mixed path keeps moments, shifts,
+// correction sums and reductions in FP64 and runs the pairwise interaction arithmetic in FP32 on
+// FP32 copies of the moments, with separations formed from exact cell offsets plus FP32
+// centre-of-mass displacements.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/octo_fmm.h"
+#include "fmm_kernels.cuh"
+#include "tree.hpp"
+
+using namespace octofmm;
+
+// ----------------------------------------------------------------------------------------------
+// errors
+// ----------------------------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      return fail(FMM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));    \
+  } while (0)
+
+// ----------------------------------------------------------------------------------------------
+// device-side tree and workspace
+// ----------------------------------------------------------------------------------------------
+struct DevArgs {
+  int64_t n_cell;          // n_sub * 512
+  int64_t n_leaf_cells;
+  int depth;
+  const int32_t* level;    // [n_sub]
+  const int32_t* ijk;      // [3 n_sub]
+  const uint8_t* leaf;     // [n_sub]
+  const int32_t* parent;   // [n_sub]
+  const int32_t* child;    // [8 n_sub]
+  const int32_t* nbr;      // [27 n_sub]
+  const int32_t* leaf_sub; // [n_leaf_sub]
+  const int32_t* leaf_ord; // [n_sub]
+  const int32_t* stencil;  // [8][kStencilCap] packed offsets
+  const int32_t* near;     // packed near offsets
+  int n_stencil;           // per parity (the same for every parity)
+  int n_near;
+  double* mom;             // [20][n_cell]
+  float* mom32;            // [20][n_cell] (mixed path)
+  double* loc;             // [20][n_cell] own, then total expansion
+  float* loc32;            // [20][n_cell] own expansion (mixed path)
+  double* ac;              // [3][n_cell] correction acceleration, own then total
+  double* root_part;       // [kRootChunks][23][512] root partial sums (FP64 path)
+  float* root_part32;      // [kRootChunks][20][512] (mixed path)
+  double* root_part_ac;    // [kRootChunks][3][512] (mixed path)
+  int* status;
+};
+
+constexpr int kStencilCap = 1024;
+constexpr int kRootChunks = 8;       // root sources split into 8 chunks of 64 cells
+constexpr int kM2LThreads = 64;      // one block = the 64 cells of one parity of one subgrid
+constexpr int kReduceThreads = 256;
+constexpr int kReduceBlocks = 512;
+
+__device__ __forceinline__ double cell_dx(int lev) { return 1.0 / double(kSub << lev); }
+
+// theta' = dx / |x_A - x_B| < theta for a same-level offset d (in cells); IEEE sqrt and
+// division, so the decision is the host's bit for bit.
+__device__ __forceinline__ bool well_separated_dev(int dx, int dy, int dz, double theta) {
+  int d2 = dx * dx + dy * dy + dz * dz;
+  if (d2 == 0) return false;
+  return 1.0 / sqrt(double(d2)) < theta;
+}
+
+// ----------------------------------------------------------------------------------------------
+// p2m: leaf cells are point masses rho dx^3 at their centres
+// ----------------------------------------------------------------------------------------------
+__global__ void k_p2m(DevArgs A, const double* __restrict__ rho) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= A.n_leaf_cells) return;
+  int32_t s = A.leaf_sub[i >> 9];
+  int lev = A.level[s];
+  int64_t cell = int64_t(s) * kCells + (i & 511);
+  double r = rho[i];
+  if (!(r >= 0.0) || !isfinite(r)) {
+    atomicOr(A.status, 1);
+    r = 0.0;
+  }
+  double h = cell_dx(lev);
+  // the other 19 moments of a leaf cell stay zero from the workspace initialisation
+  A.mom[cell] = r * h * h * h;
+}
+
+// ----------------------------------------------------------------------------------------------
+// m2m: moments of a refined cell from its 8 children (exact shift to the parent's centre of mass)
+// ----------------------------------------------------------------------------------------------
+__global__ void k_m2m(DevArgs A, const int32_t* __restrict__ subs, int n_subs) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= int64_t(n_subs) * kCells) return;
+  int32_t s = subs[t >> 9];
+  int loc = int(t & 511);
+  int a = loc >> 6, b = (loc >> 3) & 7, c = loc & 7;
+  int lev = A.level[s];
+  int32_t cs = A.child[8 * s + ((a >> 2) << 2 | (b >> 2) << 1 | (c >> 2))];
+  const int64_t N = A.n_cell;
+  double hc = cell_dx(lev + 1);
+  // children positions relative to the parent's geometric centre
+  double m[8], u[8][3];
+  int64_t ci[8];
+  double mt = 0, sx = 0, sy = 0, sz = 0;
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+    int cl = (((a & 3) * 2 + ox) * 8 + (b & 3) * 2 + oy) * 8 + (c & 3) * 2 + oz;
+    ci[o] = int64_t(cs) * kCells + cl;
+    m[o] = A.mom[ci[o]];
+    u[o][0] = (ox - 0.5) * hc + A.mom[N + ci[o]];
+    u[o][1] = (oy - 0.5) * hc + A.mom[2 * N + ci[o]];
+    u[o][2] = (oz - 0.5) * hc + A.mom[3 * N + ci[o]];
+    mt += m[o];
+    sx += m[o] * u[o][0];
+    sy += m[o] * u[o][1];
+    sz += m[o] * u[o][2];
+  }
+  double dx = 0, dy = 0, dz = 0;
+  if (mt > 0) {
+    dx = sx / mt;
+    dy = sy / mt;
+    dz = sz / mt;
+  }
+  double M2[6] = {0, 0, 0, 0, 0, 0}, M3[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    double rx = u[o][0] - dx, ry = u[o][1] - dy, rz = u[o][2] - dz;
+    double q[6], p[10];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q[k] = A.mom[(4 + k) * N + ci[o]];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) p[k] = A.mom[(10 + k) * N + ci[o]];
+    double mo = m[o];
+    M2[0] += q[0] + mo * rx * rx;
+    M2[1] += q[1] + mo * rx * ry;
+    M2[2] += q[2] + mo * rx * rz;
+    M2[3] += q[3] + mo * ry * ry;
+    M2[4] += q[4] + mo * ry * rz;
+    M2[5] += q[5] + mo * rz * rz;
+    // M3_abc += M3c_abc + r_a M2c_bc + r_b M2c_ac + r_c M2c_ab + m r_a r_b r_c
+    // q: xx0 xy1 xz2 yy3 yz4 zz5
+    M3[0] += p[0] + 3 * rx * q[0] + mo * rx * rx * rx;
+    M3[1] += p[1] + 2 * rx * q[1] + ry * q[0] + mo * rx * rx * ry;
+    M3[2] += p[2] + 2 * rx * q[2] + rz * q[0] + mo * rx * rx * rz;
+    M3[3] += p[3] + rx * q[3] + 2 * ry * q[1] + mo * rx * ry * ry;
+    M3[4] += p[4] + rx * q[4] + ry * q[2] + rz * q[1] + mo * rx * ry * rz;
+    M3[5] += p[5] + rx * q[5] + 2 * rz * q[2] + mo * rx * rz * rz;
+    M3[6] += p[6] + 3 * ry * q[3] + mo * ry * ry * ry;
+    M3[7] += p[7] + 2 * ry * q[4] + rz * q[3] + mo * ry * ry * rz;
+    M3[8] += p[8] + ry * q[5] + 2 * rz * q[4] + mo * ry * rz * rz;
+    M3[9] += p[9] + 3 * rz * q[5] + mo * rz * rz * rz;
+  }
+  int64_t cell = int64_t(s) * kCells + loc;
+  A.mom[cell] = mt;
+  A.mom[N + cell] = dx;
+  A.mom[2 * N + cell] = dy;
+  A.mom[3 * N + cell] = dz;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) A.mom[(4 + k) * N + cell] = M2[k];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) A.mom[(10 + k) * N + cell] = M3[k];
+}
+
+__global__ void k_to_fp32(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (; i < n; i += stride) dst[i] = float(src[i]);
+}
+
+// ----------------------------------------------------------------------------------------------
+// m2l: own expansion of every cell
+// ----------------------------------------------------------------------------------------------
+template <typename T>
+struct MomView;
+template <>
+struct MomView<double> {
+  static __device__ __forceinline__ const double* get(const DevArgs& A) { return A.mom; }
+};
+template <>
+struct MomView<float> {
+  static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.mom32; }
+};
+
+// Target state.
+template <typename T, bool AREF>
+struct Target {
+  T L[AREF ? 20 : 4];
+  double ax, ay, az;
+  T dAx, dAy, dAz;   // target centre-of-mass displacement
+  T mA_inv;          // 1 / m_A (0 when m_A = 0)
+  T M3A[AREF ? 10 : 1];
+  bool amc;
+};
+
+// Interaction of target A with one source cell B (same level) at separation R = X_A - X_B.
+template <typename T, bool AREF>
+__device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict__ M, int64_t N,
+                                         int64_t iB, bool bref, T x, T y, T z) {
+  T mB = M[iB];
+  Radial<T> g;
+  if (bref) {
+    T dBx = M[N + iB], dBy = M[2 * N + iB], dBz = M[3 * N + iB];
+    x -= dBx;
+    y -= dBy;
+    z -= dBz;
+    T M2[6], M3[10];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) M2[k] = M[(4 + k) * N + iB];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) M3[k] = M[(10 + k) * N + iB];
+    g.set(x, y, z, 4);
+    m2l_far<T>(x, y, z, g, mB, M2, M3, S.L);
+    if constexpr (AREF) m2l_high<T>(x, y, z, g, mB, S.L);
+    if (S.amc) {
+      T Q[10];
+      T w = mB * S.mA_inv;
+      if constexpr (AREF) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) Q[k] = w * S.M3A[k] - M3[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) Q[k] = -M3[k];
+      }
+      T cx, cy, cz;
+      amc_term<T>(x, y, z, g, Q, cx, cy, cz);
+      S.ax += double(cx);
+      S.ay += double(cy);
+      S.az += double(cz);
+    }
+  } else {
+    g.set(x, y, z, AREF ? 4 : 1);
+    m2l_mono<T>(x, y, z, g, mB, S.L);
+    if constexpr (AREF) {
+      m2l_high<T>(x, y, z, g, mB, S.L);
+      if (S.amc) {
+        T Q[10];
+        T w = mB * S.mA_inv;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) Q[k] = w * S.M3A[k];
+        T cx, cy, cz;
+        amc_term<T>(x, y, z, g, Q, cx, cy, cz);
+        S.ax += double(cx);
+        S.ay += double(cy);
+        S.az += double(cz);
+      }
+    }
+  }
+}
+
+// Point-mass source at separation R (exact positions).
+template <typename T, bool AREF>
+__device__ __forceinline__ void interact_point(Target<T, AREF>& S, T mB, T x, T y, T z) {
+  Radial<T> g;
+  g.set(x, y, z, 1);
+  m2l_mono<T>(x, y, z, g, mB, S.L);
+}
+
+template <typename T, bool AREF>
+__device__ __forceinline__ void load_target(Target<T, AREF>& S, const DevArgs& A,
+                                            const T* __restrict__ M, int64_t iA, bool amc) {
+#pragma unroll
+  for (int k = 0; k < (AREF ? 20 : 4); ++k) S.L[k] = T(0);
+  S.ax = S.ay = S.az = 0.0;
+  const int64_t N = A.n_cell;
+  S.amc = amc;
+  if constexpr (AREF) {
+    S.dAx = M[N + iA];
+    S.dAy = M[2 * N + iA];
+    S.dAz = M[3 * N + iA];
+    T mA = M[iA];
+    S.mA_inv = mA > T(0) ? T(1) / mA : T(0);
+    if (!(mA > T(0))) S.amc = false;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) S.M3A[k] = M[(10 + k) * N + iA];
+  } else {
+    S.dAx = S.dAy = S.dAz = T(0);
+    S.mA_inv = T(0);
+    if (!(M[iA] > T(0))) S.amc = false;
+  }
+}
+
+template <typename T, bool AREF>
+__device__ __forceinline__ void store_own(const DevArgs& A, const Target<T, AREF>& S, int64_t iA);
+
+template <>
+__device__ __forceinline__ void store_own<double, true>(const DevArgs& A,
+                                                        const Target<double, true>& S, int64_t iA) {
+  const int64_t N = A.n_cell;
+#pragma unroll
+  for (int k = 0; k < 20; ++k) A.loc[k * N + iA] = S.L[k];
+  A.ac[iA] = S.ax;
+  A.ac[N + iA] = S.ay;
+  A.ac[2 * N + iA] = S.az;
+}
+template <>
+__device__ __forceinline__ void store_own<double, false>(const DevArgs& A,
+                                                         const Target<double, false>& S, int64_t iA) {
+  const int64_t N = A.n_cell;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) A.loc[k * N + iA] = S.L[k];
+  A.ac[iA] = S.ax;
+  A.ac[N + iA] = S.ay;
+  A.ac[2 * N + iA] = S.az;
+}
+template <>
+__device__ __forceinline__ void store_own<float, true>(const DevArgs& A,
+                                                       const Target<float, true>& S, int64_t iA) {
+  const int64_t N = A.n_cell;
+#pragma unroll
+  for (int k = 0; k < 20; ++k) A.loc32[k * N + iA] = S.L[k];
+  A.ac[iA] = S.ax;
+  A.ac[N + iA] = S.ay;
+  A.ac[2 * N + iA] = S.az;
+}
+template <>
+__device__ __forceinline__ void store_own<float, false>(const DevArgs& A,
+                                                        const Target<float, false>& S, int64_t iA) {
+  const int64_t N = A.n_cell;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) A.loc32[k * N + iA] = S.L[k];
+  A.ac[iA] = S.ax;
+  A.ac[N + iA] = S.ay;
+  A.ac[2 * N + iA] = S.az;
+}
+
+// Target cell of a block: 64 threads = the 64 cells of one parity of one subgrid.
+__device__ __forceinline__ void block_cell(int parity, int t, int& a, int& b, int& c) {
+  int px = (parity >> 2) & 1, py = (parity >> 1) & 1, pz = parity & 1;
+  a = 2 * (t >> 4) + px;
+  b = 2 * ((t >> 2) & 3) + py;
+  c = 2 * (t & 3) + pz;
+}
+
+// Levels >= 1: target subgrid s, parity p.
+template <typename T, bool AREF>
+__device__ void m2l_level(const DevArgs& A, int32_t s, int parity, bool amc) {
+  __shared__ int32_t nb[27];
+  __shared__ uint8_t nb_ref[27];
+  __shared__ int32_t pnb[27];   // parent's neighbours (leaf targets: coarser direct partners)
+  __shared__ uint8_t pnb_leaf[27];
+  const int t = threadIdx.x;
+  if (t < 27) {
+    int32_t q = A.nbr[27 * s + t];
+    nb[t] = q;
+    nb_ref[t] = (q >= 0 && !A.leaf[q]) ? 1 : 0;
+    if (!AREF) {
+      int32_t P = A.parent[s];
+      int32_t pq = A.nbr[27 * P + t];
+      pnb[t] = pq;
+      pnb_leaf[t] = (pq >= 0 && A.leaf[pq]) ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  const int lev = A.level[s];
+  const T* __restrict__ M = MomView<T>::get(A);
+  const int64_t N = A.n_cell;
+  int a, b, c;
+  block_cell(parity, t, a, b, c);
+  const int64_t iA = int64_t(s) * kCells + (a * 8 + b) * 8 + c;
+  Target<T, AREF> S;
+  load_target<T, AREF>(S, A, M, iA, amc);
+  const T h = T(cell_dx(lev));
+  const int32_t* __restrict__ st = A.stencil + parity * kStencilCap;
+  // same-level multipole interactions
+  for (int q = 0; q < A.n_stencil; ++q) {
+    int32_t code = __ldg(st + q);
+    int dx, dy, dz;
+    unpack_offset(code, dx, dy, dz);
+    int px = a + dx, py = b + dy, pz = c + dz;
+    int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
+    int32_t sB = nb[slot];
+    if (sB < 0) continue;
+    int64_t iB = int64_t(sB) * kCells + ((px & 7) * 8 + (py & 7)) * 8 + (pz & 7);
+    interact<T, AREF>(S, M, N, iB, nb_ref[slot] != 0, S.dAx - T(dx) * h, S.dAy - T(dy) * h,
+                      S.dAz - T(dz) * h);
+  }
+  if (!AREF) {
+    // direct sums with non-separated cells of the same level: leaves directly, refined cells
+    // through their 8 (leaf) children one level finer
+    const T hc = h * T(0.5);
+    for (int q = 0; q < A.n_near; ++q) {
+      int32_t code = __ldg(A.near + q);
+      int dx, dy, dz;
+      unpack_offset(code, dx, dy, dz);
+      int px = a + dx, py = b + dy, pz = c + dz;
+      int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
+      int32_t sB = nb[slot];
+      if (sB < 0) continue;
+      int lx = px & 7, ly = py & 7, lz = pz & 7;
+      if (!nb_ref[slot]) {
+        int64_t iB = int64_t(sB) * kCells + (lx * 8 + ly) * 8 + lz;
+        interact_point<T, AREF>(S, M[iB], -T(dx) * h, -T(dy) * h, -T(dz) * h);
+      } else {
+        int32_t cs = A.child[8 * sB + ((lx >> 2) << 2 | (ly >> 2) << 1 | (lz >> 2))];
+        for (int o = 0; o < 8; ++o) {
+          int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+          int64_t iC = int64_t(cs) * kCells + (((lx & 3) * 2 + ox) * 8 + (ly & 3) * 2 + oy) * 8 +
+                       (lz & 3) * 2 + oz;
+          // x_A - x_C = (1/2 - o - 2 d) dx_(l+1)
+          interact_point<T, AREF>(S, M[iC], (T(0.5) - T(ox) - T(2 * dx)) * hc,
+                                  (T(0.5) - T(oy) - T(2 * dy)) * hc,
+                                  (T(0.5) - T(oz) - T(2 * dz)) * hc);
+        }
+      }
+    }
+    // direct sums with leaves one level coarser that are not separated from A's parent
+    int32_t P = A.parent[s];
+    int ga = A.ijk[3 * s] * 8 + a, gb = A.ijk[3 * s + 1] * 8 + b, gc = A.ijk[3 * s + 2] * 8 + c;
+    int ja = (ga >> 1) - A.ijk[3 * P] * 8, jb = (gb >> 1) - A.ijk[3 * P + 1] * 8,
+        jc = (gc >> 1) - A.ijk[3 * P + 2] * 8;
+    for (int q = 0; q < A.n_near; ++q) {
+      int32_t code = __ldg(A.near + q);
+      int dx, dy, dz;
+      unpack_offset(code, dx, dy, dz);
+      int px = ja + dx, py = jb + dy, pz = jc + dz;
+      int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
+      if (!pnb_leaf[slot]) continue;
+      int32_t sB = pnb[slot];
+      int64_t iB = int64_t(sB) * kCells + ((px & 7) * 8 + (py & 7)) * 8 + (pz & 7);
+      // x_A - x_i = ((g_A & 1) - 1/2 - 2 d) dx_l
+      interact_point<T, AREF>(S, M[iB], (T(ga & 1) - T(0.5) - T(2 * dx)) * h,
+                              (T(gb & 1) - T(0.5) - T(2 * dy)) * h,
+                              (T(gc & 1) - T(0.5) - T(2 * dz)) * h);
+    }
+  }
+  store_own<T, AREF>(A, S, iA);
+}
+
+// Root level: every well-separated pair inside the single root subgrid (no parent criterion);
+// when the root is a leaf, every other root cell interacts directly.  Sources are split into
+// kRootChunks chunks whose partial sums are added in a fixed order by the downward pass.
+template <typename T, bool AREF>
+__device__ void m2l_root(const DevArgs& A, int parity, int chunk, double theta, bool amc) {
+  const T* __restrict__ M = MomView<T>::get(A);
+  const int64_t N = A.n_cell;
+  int a, b, c;
+  block_cell(parity, threadIdx.x, a, b, c);
+  const int iloc = (a * 8 + b) * 8 + c;
+  Target<T, AREF> S;
+  load_target<T, AREF>(S, A, M, iloc, amc);
+  const T h = T(cell_dx(0));
+  const bool root_leaf = A.leaf[0] != 0;
+  for (int j = chunk * 64; j < chunk * 64 + 64; ++j) {
+    if (j == iloc) continue;
+    int dx = (j >> 6) - a, dy = ((j >> 3) & 7) - b, dz = (j & 7) - c;
+    bool ws = well_separated_dev(dx, dy, dz, theta);
+    if (!ws && !root_leaf) continue;
+    interact<T, AREF>(S, M, N, j, !root_leaf, S.dAx - T(dx) * h, S.dAy - T(dy) * h,
+                      S.dAz - T(dz) * h);
+  }
+  // partials: [chunk][component][cell]
+  if (sizeof(T) == 8) {
+    double* P = A.root_part + int64_t(chunk) * 23 * kCells;
+    for (int k = 0; k < (AREF ? 20 : 4); ++k) P[k * kCells + iloc] = double(S.L[k]);
+    for (int k = (AREF ? 20 : 4); k < 20; ++k) P[k * kCells + iloc] = 0.0;
+    P[20 * kCells + iloc] = S.ax;
+    P[21 * kCells + iloc] = S.ay;
+    P[22 * kCells + iloc] = S.az;
+  } else {
+    float* P = A.root_part32 + int64_t(chunk) * 20 * kCells;
+    for (int k = 0; k < (AREF ? 20 : 4); ++k) P[k * kCells + iloc] = float(S.L[k]);
+    for (int k = (AREF ? 20 : 4); k < 20; ++k) P[k * kCells + iloc] = 0.0f;
+    double* Q = A.root_part_ac + int64_t(chunk) * 3 * kCells;
+    Q[iloc] = S.ax;
+    Q[kCells + iloc] = S.ay;
+    Q[2 * kCells + iloc] = S.az;
+  }
+}
+
+// Block b < 8 * kRootChunks: root (parity b & 7, chunk b >> 3); then one block per (subgrid in
+// `work`, parity).
+template <typename T>
+__global__ void __launch_bounds__(kM2LThreads) k_m2l(DevArgs A, const int32_t* __restrict__ work,
+                                                     double theta, int amc) {
+  int b = blockIdx.x;
+  if (b < 8 * kRootChunks) {
+    if (A.leaf[0]) m2l_root<T, false>(A, b & 7, b >> 3, theta, amc != 0);
+    else m2l_root<T, true>(A, b & 7, b >> 3, theta, amc != 0);
+    return;
+  }
+  b -= 8 * kRootChunks;
+  int32_t s = work[b >> 3];
+  int parity = b & 7;
+  if (A.leaf[s]) m2l_level<T, false>(A, s, parity, amc != 0);
+  else m2l_level<T, true>(A, s, parity, amc != 0);
+}
+
+// ----------------------------------------------------------------------------------------------
+// l2l / l2p: total expansion = own + parent's total shifted to this cell's centre of mass
+// ----------------------------------------------------------------------------------------------
+// Shift of a cubic expansion by r (exact for a polynomial of degree 3):
+//   L0' = L0 + L1.r + 1/2 r.L2.r + 1/6 L3(r,r,r),  L1' = L1 + L2 r + 1/2 L3(r,r),
+//   L2' = L2 + L3 r,  L3' = L3.
+__device__ __forceinline__ void shift_add(const double* P, double rx, double ry, double rz,
+                                          double* L, bool full) {
+  double tx, ty, tz, qx, qy, qz;
+  sym3_vectors<double>(P + 10, rx, ry, rz, tx, ty, tz, qx, qy, qz);
+  // L2 r
+  double l2x = P[4] * rx + P[5] * ry + P[6] * rz;
+  double l2y = P[5] * rx + P[7] * ry + P[8] * rz;
+  double l2z = P[6] * rx + P[8] * ry + P[9] * rz;
+  L[0] += P[0] + P[1] * rx + P[2] * ry + P[3] * rz + 0.5 * (rx * l2x + ry * l2y + rz * l2z) +
+          (rx * qx + ry * qy + rz * qz) / 6.0;
+  L[1] += P[1] + l2x + 0.5 * qx;
+  L[2] += P[2] + l2y + 0.5 * qy;
+  L[3] += P[3] + l2z + 0.5 * qz;
+  if (full) {
+    // (L3 r)_ab, L3: xxx0 xxy1 xxz2 xyy3 xyz4 xzz5 yyy6 yyz7 yzz8 zzz9
+    const double* Q = P + 10;
+    L[4] += P[4] + Q[0] * rx + Q[1] * ry + Q[2] * rz;
+    L[5] += P[5] + Q[1] * rx + Q[3] * ry + Q[4] * rz;
+    L[6] += P[6] + Q[2] * rx + Q[4] * ry + Q[5] * rz;
+    L[7] += P[7] + Q[3] * rx + Q[6] * ry + Q[7] * rz;
+    L[8] += P[8] + Q[4] * rx + Q[7] * ry + Q[8] * rz;
+    L[9] += P[9] + Q[5] * rx + Q[8] * ry + Q[9] * rz;
+#pragma unroll
+    for (int k = 10; k < 20; ++k) L[k] += P[k];
+  }
+}
+
+template <bool MIXED>
+__global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs, double* __restrict__ phi,
+                      double* __restrict__ g) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n_subs * kCells) return;
+  const int32_t s = int32_t(s0 + (t >> 9));
+  const int loc = int(t & 511);
+  const int64_t N = A.n_cell;
+  const int64_t i = int64_t(s) * kCells + loc;
+  const bool isleaf = A.leaf[s] != 0;
+  const int nL = isleaf ? 4 : 20;
+  double L[20], ax, ay, az;
+  if (lev == 0) {
+    ax = ay = az = 0.0;
+    for (int k = 0; k < 20; ++k) L[k] = 0.0;
+    for (int ch = 0; ch < kRootChunks; ++ch) {
+      if (!MIXED) {
+        const double* P = A.root_part + int64_t(ch) * 23 * kCells;
+        for (int k = 0; k < nL; ++k) L[k] += P[k * kCells + loc];
+        ax += P[20 * kCells + loc];
+        ay += P[21 * kCells + loc];
+        az += P[22 * kCells + loc];
+      } else {
+        const float* P = A.root_part32 + int64_t(ch) * 20 * kCells;
+        for (int k = 0; k < nL; ++k) L[k] += double(P[k * kCells + loc]);
+        const double* Q = A.root_part_ac + int64_t(ch) * 3 * kCells;
+        ax += Q[loc];
+        ay += Q[kCells + loc];
+        az += Q[2 * kCells + loc];
+      }
+    }
+  } else {
+    for (int k = 0; k < nL; ++k) L[k] = MIXED ? double(A.loc32[k * N + i]) : A.loc[k * N + i];
+    for (int k = nL; k < 20; ++k) L[k] = 0.0;
+    ax = A.ac[i];
+    ay = A.ac[N + i];
+    az = A.ac[2 * N + i];
+    const int32_t Pn = A.parent[s];
+    int a = loc >> 6, b = (loc >> 3) & 7, c = loc & 7;
+    int ga = A.ijk[3 * s] * 8 + a, gb = A.ijk[3 * s + 1] * 8 + b, gc = A.ijk[3 * s + 2] * 8 + c;
+    int pl = (((ga >> 1) - A.ijk[3 * Pn] * 8) * 8 + ((gb >> 1) - A.ijk[3 * Pn + 1] * 8)) * 8 +
+             ((gc >> 1) - A.ijk[3 * Pn + 2] * 8);
+    const int64_t ip = int64_t(Pn) * kCells + pl;
+    double P[20];
+#pragma unroll
+    for (int k = 0; k < 20; ++k) P[k] = A.loc[k * N + ip];
+    const double h = cell_dx(lev);
+    // r = X_A - X_P = ((g & 1) - 1/2) dx_l + delta_A - delta_P
+    double rx = ((ga & 1) - 0.5) * h + A.mom[N + i] - A.mom[N + ip];
+    double ry = ((gb & 1) - 0.5) * h + A.mom[2 * N + i] - A.mom[2 * N + ip];
+    double rz = ((gc & 1) - 0.5) * h + A.mom[3 * N + i] - A.mom[3 * N + ip];
+    shift_add(P, rx, ry, rz, L, !isleaf);
+    ax += A.ac[ip];
+    ay += A.ac[N + ip];
+    az += A.ac[2 * N + ip];
+  }
+  if (isleaf) {
+    const int64_t o = int64_t(A.leaf_ord[s]) * kCells + loc;
+    phi[o] = L[0];
+    g[3 * o] = -L[1] + ax;
+    g[3 * o + 1] = -L[2] + ay;
+    g[3 * o + 2] = -L[3] + az;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 20; ++k) A.loc[k * N + i] = L[k];
+    A.ac[i] = ax;
+    A.ac[N + i] = ay;
+    A.ac[2 * N + i] = az;
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// net force and torque: F = sum m g, T = sum x cross m g, S = sum |x| |m g|; fixed order
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ void block_sum7(double* v, double (*sh)[kReduceThreads]) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) sh[k][t] = v[k];
+  __syncthreads();
+  for (int w = kReduceThreads / 2; w > 0; w >>= 1) {
+    if (t < w)
+#pragma unroll
+      for (int k = 0; k < 7; ++k) sh[k][t] += sh[k][t + w];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kReduceThreads)
+    k_net_partial(DevArgs A, const double* __restrict__ rho, const double* __restrict__ g,
+                  double* __restrict__ partials) {
+  __shared__ double sh[7][kReduceThreads];
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  const int64_t stride = int64_t(gridDim.x) * kReduceThreads;
+  for (int64_t i = int64_t(blockIdx.x) * kReduceThreads + threadIdx.x; i < A.n_leaf_cells;
+       i += stride) {
+    int32_t s = A.leaf_sub[i >> 9];
+    int lev = A.level[s];
+    int loc = int(i & 511);
+    double h = cell_dx(lev);
+    double x = -0.5 + (A.ijk[3 * s] * 8 + (loc >> 6) + 0.5) * h;
+    double y = -0.5 + (A.ijk[3 * s + 1] * 8 + ((loc >> 3) & 7) + 0.5) * h;
+    double z = -0.5 + (A.ijk[3 * s + 2] * 8 + (loc & 7) + 0.5) * h;
+    double m = rho[i] * h * h * h;
+    double fx = m * g[3 * i], fy = m * g[3 * i + 1], fz = m * g[3 * i + 2];
+    v[0] += fx;
+    v[1] += fy;
+    v[2] += fz;
+    v[3] += y * fz - z * fy;
+    v[4] += z * fx - x * fz;
+    v[5] += x * fy - y * fx;
+    v[6] += sqrt(x * x + y * y + z * z) * sqrt(fx * fx + fy * fy + fz * fz);
+  }
+  block_sum7(v, sh);
+  if (threadIdx.x < 7) partials[int64_t(blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kReduceThreads)
+    k_net_final(const double* __restrict__ partials, int n_blocks, double* __restrict__ out) {
+  __shared__ double sh[7][kReduceThreads];
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < n_blocks; b += kReduceThreads)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[k] += partials[int64_t(b) * 7 + k];
+  block_sum7(v, sh);
+  if (threadIdx.x < 7) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// ----------------------------------------------------------------------------------------------
+// host side
+// ----------------------------------------------------------------------------------------------
+struct StencilDev {
+  int32_t* d_stencil = nullptr;  // [8][kStencilCap]
+  int32_t* d_near = nullptr;
+  int n_stencil = 0, n_near = 0;
+};
+
+struct fmm_tree {
+  HostTree h;
+  int device = -1;
+  bool dev_ready = false, mixed_ready = false;
+  int32_t *d_level = nullptr, *d_ijk = nullptr, *d_parent = nullptr, *d_child = nullptr,
+          *d_nbr = nullptr, *d_leaf_sub = nullptr, *d_leaf_ord = nullptr, *d_work = nullptr,
+          *d_refined = nullptr;
+  uint8_t* d_leaf = nullptr;
+  std::vector<int64_t> refined_off;  // offsets into d_refined per level
+  int64_t n_work = 0;
+  double *d_mom = nullptr, *d_loc = nullptr, *d_ac = nullptr, *d_root_part = nullptr,
+         *d_root_part_ac = nullptr, *d_partials = nullptr;
+  float *d_mom32 = nullptr, *d_loc32 = nullptr, *d_root_part32 = nullptr;
+  int* d_status = nullptr;
+  double *d_rho = nullptr, *d_phi = nullptr, *d_g = nullptr, *d_net = nullptr;
+  std::map<double, StencilDev> stencils;
+  bool profiling = false;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool ev_recorded = false;
+  int32_t launches = 0;
+  std::vector<void*> allocs;
+};
+
+template <typename P>
+static cudaError_t dalloc(fmm_tree* t, P** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e == cudaSuccess) {
+    t->allocs.push_back(q);
+    *p = static_cast<P*>(q);
+  }
+  return e;
+}
+
+template <typename V>
+static cudaError_t upload(fmm_tree* t, typename V::value_type** p, const V& v) {
+  cudaError_t e = dalloc(t, p, sizeof(typename V::value_type) * v.size());
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpy(*p, v.data(), sizeof(typename V::value_type) * v.size(),
+                    cudaMemcpyHostToDevice);
+}
+
+static int ensure_device(fmm_tree* t) {
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (t->dev_ready) {
+    if (dev != t->device) return fail(FMM_ERR_STATE, "tree workspace lives on another device");
+    return FMM_OK;
+  }
+  t->device = dev;
+  const HostTree& h = t->h;
+  const int64_t nc = h.n_sub * kCells;
+  CUDA_TRY(upload(t, &t->d_level, h.level));
+  CUDA_TRY(upload(t, &t->d_ijk, h.ijk));
+  CUDA_TRY(upload(t, &t->d_leaf, h.leaf));
+  CUDA_TRY(upload(t, &t->d_parent, h.parent));
+  CUDA_TRY(upload(t, &t->d_child, h.child));
+  CUDA_TRY(upload(t, &t->d_nbr, h.nbr));
+  CUDA_TRY(upload(t, &t->d_leaf_sub, h.leaf_sub));
+  CUDA_TRY(upload(t, &t->d_leaf_ord, h.leaf_ord));
+  // multipole-interaction work: refined subgrids (coarse to fine), then leaf subgrids, levels >= 1
+  std::vector<int32_t> work, refined;
+  for (int l = 1; l <= h.depth; ++l) work.insert(work.end(), h.refined_at[l].begin(), h.refined_at[l].end());
+  for (int l = 1; l <= h.depth; ++l) work.insert(work.end(), h.leaves_at[l].begin(), h.leaves_at[l].end());
+  t->n_work = int64_t(work.size());
+  CUDA_TRY(upload(t, &t->d_work, work));
+  t->refined_off.assign(h.depth + 2, 0);
+  for (int l = 0; l <= h.depth; ++l) {
+    refined.insert(refined.end(), h.refined_at[l].begin(), h.refined_at[l].end());
+    t->refined_off[l + 1] = int64_t(refined.size());
+  }
+  CUDA_TRY(upload(t, &t->d_refined, refined));
+  CUDA_TRY(dalloc(t, &t->d_mom, sizeof(double) * kNMom * nc));
+  CUDA_TRY(cudaMemset(t->d_mom, 0, sizeof(double) * kNMom * nc));  // leaf cells keep zeros
+  CUDA_TRY(dalloc(t, &t->d_loc, sizeof(double) * 20 * nc));
+  CUDA_TRY(dalloc(t, &t->d_ac, sizeof(double) * 3 * nc));
+  CUDA_TRY(dalloc(t, &t->d_root_part, sizeof(double) * kRootChunks * 23 * kCells));
+  CUDA_TRY(dalloc(t, &t->d_partials, sizeof(double) * 7 * kReduceBlocks));
+  CUDA_TRY(dalloc(t, &t->d_status, sizeof(int)));
+  CUDA_TRY(cudaMemset(t->d_status, 0, sizeof(int)));
+  t->dev_ready = true;
+  return FMM_OK;
+}
+
+static int ensure_mixed(fmm_tree* t) {
+  if (t->mixed_ready) return FMM_OK;
+  const int64_t nc = t->h.n_sub * kCells;
+  CUDA_TRY(dalloc(t, &t->d_mom32, sizeof(float) * kNMom * nc));
+  CUDA_TRY(dalloc(t, &t->d_loc32, sizeof(float) * 20 * nc));
+  CUDA_TRY(dalloc(t, &t->d_root_part32, sizeof(float) * kRootChunks * 20 * kCells));
+  CUDA_TRY(dalloc(t, &t->d_root_part_ac, sizeof(double) * kRootChunks * 3 * kCells));
+  t->mixed_ready = true;
+  return FMM_OK;
+}
+
+static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
+  auto it = t->stencils.find(theta);
+  if (it == t->stencils.end()) {
+    Stencil st = make_stencil(theta);
+    std::vector<int32_t> packed(8 * kStencilCap, 0);
+    int n = int(st.offs[0].size());
+    for (int p = 0; p < 8; ++p) {
+      if (int(st.offs[p].size()) != n || n > kStencilCap)
+        return fail(FMM_ERR_THETA, "stencil sizes differ between parities");
+      std::copy(st.offs[p].begin(), st.offs[p].end(), packed.begin() + p * kStencilCap);
+    }
+    StencilDev sd;
+    CUDA_TRY(upload(t, &sd.d_stencil, packed));
+    CUDA_TRY(upload(t, &sd.d_near, st.near));
+    sd.n_stencil = n;
+    sd.n_near = int(st.near.size());
+    it = t->stencils.emplace(theta, sd).first;
+  }
+  *out = &it->second;
+  return FMM_OK;
+}
+
+static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
+  DevArgs A;
+  A.n_cell = t->h.n_sub * kCells;
+  A.n_leaf_cells = t->h.n_leaf_sub * kCells;
+  A.depth = t->h.depth;
+  A.level = t->d_level;
+  A.ijk = t->d_ijk;
+  A.leaf = t->d_leaf;
+  A.parent = t->d_parent;
+  A.child = t->d_child;
+  A.nbr = t->d_nbr;
+  A.leaf_sub = t->d_leaf_sub;
+  A.leaf_ord = t->d_leaf_ord;
+  A.stencil = sd ? sd->d_stencil : nullptr;
+  A.near = sd ? sd->d_near : nullptr;
+  A.n_stencil = sd ? sd->n_stencil : 0;
+  A.n_near = sd ? sd->n_near : 0;
+  A.mom = t->d_mom;
+  A.mom32 = t->d_mom32;
+  A.loc = t->d_loc;
+  A.loc32 = t->d_loc32;
+  A.ac = t->d_ac;
+  A.root_part = t->d_root_part;
+  A.root_part32 = t->d_root_part32;
+  A.root_part_ac = t->d_root_part_ac;
+  A.status = t->d_status;
+  return A;
+}
+
+static inline unsigned blocks_for(int64_t n, int threads) {
+  return unsigned((n + threads - 1) / threads);
+}
+
+static int record(fmm_tree* t, int k, cudaStream_t st) {
+  if (!t->profiling) return FMM_OK;
+  if (!t->ev[k]) CUDA_TRY(cudaEventCreate(&t->ev[k]));
+  CUDA_TRY(cudaEventRecord(t->ev[k], st));
+  return FMM_OK;
+}
+
+static int launch_net(fmm_tree* t, const DevArgs& A, const double* rho, const double* g,
+                      double* net, cudaStream_t st) {
+  k_net_partial<<<kReduceBlocks, kReduceThreads, 0, st>>>(A, rho, g, t->d_partials);
+  CUDA_TRY(cudaGetLastError());
+  k_net_final<<<1, kReduceThreads, 0, st>>>(t->d_partials, kReduceBlocks, net);
+  CUDA_TRY(cudaGetLastError());
+  return FMM_OK;
+}
+
+static int solve_impl(fmm_tree* t, const double* rho, double theta, int precision, int amc,
+                      double* phi, double* g, double* net, cudaStream_t st) {
+  if (!(theta >= kThetaMin && theta < 1.0))
+    return fail(FMM_ERR_THETA, "theta must lie in [0.34, 1)");
+  if (precision != FMM_FP64 && precision != FMM_MIXED) return fail(FMM_ERR_ARG, "bad precision");
+  if (!rho || !phi || !g) return fail(FMM_ERR_ARG, "null device pointer");
+  int rc = ensure_device(t);
+  if (rc) return rc;
+  const bool mixed = precision == FMM_MIXED;
+  if (mixed && (rc = ensure_mixed(t))) return rc;
+  StencilDev* sd = nullptr;
+  if ((rc = get_stencil(t, theta, &sd))) return rc;
+  const HostTree& h = t->h;
+  DevArgs A = make_args(t, sd);
+  if ((rc = record(t, 0, st))) return rc;
+  // upward pass
+  k_p2m<<<blocks_for(A.n_leaf_cells, 256), 256, 0, st>>>(A, rho);
+  CUDA_TRY(cudaGetLastError());
+  for (int l = h.depth - 1; l >= 0; --l) {
+    int64_t n = t->refined_off[l + 1] - t->refined_off[l];
+    if (n == 0) continue;
+    k_m2m<<<blocks_for(n * kCells, 128), 128, 0, st>>>(A, t->d_refined + t->refined_off[l], int(n));
+    CUDA_TRY(cudaGetLastError());
+  }
+  if (mixed) {
+    k_to_fp32<<<1216, 256, 0, st>>>(t->d_mom, t->d_mom32, int64_t(kNMom) * A.n_cell);
+    CUDA_TRY(cudaGetLastError());
+  }
+  if ((rc = record(t, 1, st))) return rc;
+  // interactions: root chunks + every (subgrid, parity) of levels >= 1
+  unsigned nb = unsigned(8 * kRootChunks + 8 * t->n_work);
+  if (mixed) k_m2l<float><<<nb, kM2LThreads, 0, st>>>(A, t->d_work, theta, amc);
+  else k_m2l<double><<<nb, kM2LThreads, 0, st>>>(A, t->d_work, theta, amc);
+  CUDA_TRY(cudaGetLastError());
+  if ((rc = record(t, 2, st))) return rc;
+  // downward pass
+  for (int l = 0; l <= h.depth; ++l) {
+    int64_t s0 = h.lev_off[l], n = h.lev_off[l + 1] - h.lev_off[l];
+    if (mixed) k_l2l<true><<<blocks_for(n * kCells, 128), 128, 0, st>>>(A, l, s0, n, phi, g);
+    else k_l2l<false><<<blocks_for(n * kCells, 128), 128, 0, st>>>(A, l, s0, n, phi, g);
+    CUDA_TRY(cudaGetLastError());
+  }
+  if ((rc = record(t, 3, st))) return rc;
+  if (net && (rc = launch_net(t, A, rho, g, net, st))) return rc;
+  if ((rc = record(t, 4, st))) return rc;
+  t->ev_recorded = t->profiling;
+  int32_t n_m2m = 0;
+  for (int l = 0; l < h.depth; ++l) n_m2m += (t->refined_off[l + 1] > t->refined_off[l]) ? 1 : 0;
+  t->launches = 1 + n_m2m + (mixed ? 1 : 0) + 1 + (h.depth + 1) + (net ? 2 : 0);
+  return FMM_OK;
+}
+
+// ----------------------------------------------------------------------------------------------
+// C ABI
+// ----------------------------------------------------------------------------------------------
+extern "C" {
+
+int fmm_build_tree(int max_level, const uint8_t* refine_flags, int64_t n_flags, fmm_tree** out) {
+  if (!out) return fail(FMM_ERR_ARG, "out is null");
+  *out = nullptr;
+  try {
+    std::unique_ptr<fmm_tree> t(new fmm_tree());
+    std::string err = build_host_tree(max_level, refine_flags, n_flags, t->h);
+    if (!err.empty()) return fail(FMM_ERR_ARG, err);
+    *out = t.release();
+    return FMM_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  } catch (...) {
+    return fail(FMM_ERR_ARG, "tree construction failed");
+  }
+}
+
+void fmm_destroy(fmm_tree* t) {
+  if (!t) return;
+  int cur = -1;
+  bool switched = false;
+  if (t->dev_ready && cudaGetDevice(&cur) == cudaSuccess && cur != t->device) {
+    switched = cudaSetDevice(t->device) == cudaSuccess;
+  }
+  for (void* p : t->allocs) cudaFree(p);
+  for (auto& e : t->ev)
+    if (e) cudaEventDestroy(e);
+  if (switched) cudaSetDevice(cur);
+  delete t;
+}
+
+int fmm_tree_info(const fmm_tree* t, int64_t* n_subgrids, int64_t* n_leaf_subgrids, int32_t* depth) {
+  if (!t) return fail(FMM_ERR_ARG, "tree is null");
+  if (n_subgrids) *n_subgrids = t->h.n_sub;
+  if (n_leaf_subgrids) *n_leaf_subgrids = t->h.n_leaf_sub;
+  if (depth) *depth = t->h.depth;
+  return FMM_OK;
+}
+
+int fmm_tree_subgrids(const fmm_tree* t, int32_t* rows) {
+  if (!t || !rows) return fail(FMM_ERR_ARG, "null argument");
+  for (int64_t s = 0; s < t->h.n_sub; ++s) {
+    rows[5 * s] = t->h.level[s];
+    rows[5 * s + 1] = t->h.ijk[3 * s];
+    rows[5 * s + 2] = t->h.ijk[3 * s + 1];
+    rows[5 * s + 3] = t->h.ijk[3 * s + 2];
+    rows[5 * s + 4] = t->h.leaf[s];
+  }
+  return FMM_OK;
+}
+
+int fmm_stencil(double theta, int parity, int32_t* offsets, int32_t capacity, int32_t* count) {
+  if (!(theta >= kThetaMin && theta < 1.0)) return fail(FMM_ERR_THETA, "theta must lie in [0.34, 1)");
+  if (parity < 0 || parity > 7 || !count || capacity < 0 || (capacity > 0 && !offsets))
+    return fail(FMM_ERR_ARG, "bad argument");
+  Stencil st = make_stencil(theta);
+  const auto& v = st.offs[parity];
+  *count = int32_t(v.size());
+  for (int32_t q = 0; q < int32_t(v.size()) && q < capacity; ++q) {
+    int dx, dy, dz;
+    unpack_offset(v[q], dx, dy, dz);
+    offsets[3 * q] = dx;
+    offsets[3 * q + 1] = dy;
+    offsets[3 * q + 2] = dz;
+  }
+  return FMM_OK;
+}
+
+int fmm_interaction_counts(const fmm_tree* t, double theta, int64_t counts[3]) {
+  if (!t || !counts) return fail(FMM_ERR_ARG, "null argument");
+  if (!(theta >= kThetaMin && theta < 1.0)) return fail(FMM_ERR_THETA, "theta must lie in [0.34, 1)");
+  interaction_counts(t->h, make_stencil(theta), counts);
+  return FMM_OK;
+}
+
+int fmm_interaction_counts_by_type(const fmm_tree* t, double theta, int64_t counts[6]) {
+  if (!t || !counts) return fail(FMM_ERR_ARG, "null argument");
+  if (!(theta >= kThetaMin && theta < 1.0)) return fail(FMM_ERR_THETA, "theta must lie in [0.34, 1)");
+  interaction_counts_by_type(t->h, make_stencil(theta), counts);
+  return FMM_OK;
+}
+
+int fmm_last_launches(const fmm_tree* t, int32_t* n) {
+  if (!t || !n) return fail(FMM_ERR_ARG, "null argument");
+  *n = t->launches;
+  return FMM_OK;
+}
+
+int fmm_solve(fmm_tree* t, const double* rho_dev, double theta, int precision, int amc,
+              double* phi_dev, double* g_dev, double* net_dev, void* stream) {
+  if (!t) return fail(FMM_ERR_ARG, "tree is null");
+  try {
+    return solve_impl(t, rho_dev, theta, precision, amc, phi_dev, g_dev, net_dev,
+                      static_cast<cudaStream_t>(stream));
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+int fmm_sync_status(fmm_tree* t, void* stream) {
+  if (!t) return fail(FMM_ERR_ARG, "tree is null");
+  if (!t->dev_ready) return FMM_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaStreamSynchronize(st));
+  int status = 0;
+  CUDA_TRY(cudaMemcpy(&status, t->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(t->d_status, 0, sizeof(int)));
+  if (status & 1) return fail(FMM_ERR_NONFINITE, "a density was negative, NaN or infinite");
+  return FMM_OK;
+}
+
+int fmm_solve_host(fmm_tree* t, const double* rho_host, double theta, int precision, int amc,
+                   double* phi_host, double* g_host, double* net_host, void* stream) {
+  if (!t || !rho_host || !phi_host || !g_host) return fail(FMM_ERR_ARG, "null argument");
+  int rc = ensure_device(t);
+  if (rc) return rc;
+  const int64_t n = t->h.n_leaf_sub * kCells;
+  if (!t->d_rho) {
+    CUDA_TRY(dalloc(t, &t->d_rho, sizeof(double) * n));
+    CUDA_TRY(dalloc(t, &t->d_phi, sizeof(double) * n));
+    CUDA_TRY(dalloc(t, &t->d_g, sizeof(double) * 3 * n));
+    CUDA_TRY(dalloc(t, &t->d_net, sizeof(double) * 7));
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaMemcpyAsync(t->d_rho, rho_host, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  rc = fmm_solve(t, t->d_rho, theta, precision, amc, t->d_phi, t->d_g, net_host ? t->d_net : nullptr,
+                 stream);
+  if (rc) return rc;
+  CUDA_TRY(cudaMemcpyAsync(phi_host, t->d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(g_host, t->d_g, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+  if (net_host)
+    CUDA_TRY(cudaMemcpyAsync(net_host, t->d_net, sizeof(double) * 7, cudaMemcpyDeviceToHost, st));
+  return fmm_sync_status(t, stream);
+}
+
+int fmm_net_force_torque(fmm_tree* t, const double* rho_dev, const double* g_dev, double* net_dev,
+                         void* stream) {
+  if (!t || !rho_dev || !g_dev || !net_dev) return fail(FMM_ERR_ARG, "null argument");
+  int rc = ensure_device(t);
+  if (rc) return rc;
+  DevArgs A = make_args(t, nullptr);
+  return launch_net(t, A, rho_dev, g_dev, net_dev, static_cast<cudaStream_t>(stream));
+}
+
+int fmm_set_profiling(fmm_tree* t, int on) {
+  if (!t) return fail(FMM_ERR_ARG, "tree is null");
+  t->profiling = on != 0;
+  t->ev_recorded = false;
+  return FMM_OK;
+}
+
+int fmm_phase_times(fmm_tree* t, float* ms, int n) {
+  if (!t || !ms || n < 0) return fail(FMM_ERR_ARG, "null argument");
+  if (!t->ev_recorded) return fail(FMM_ERR_STATE, "no profiled solve recorded");
+  CUDA_TRY(cudaEventSynchronize(t->ev[4]));
+  for (int k = 0; k < n && k < 4; ++k) CUDA_TRY(cudaEventElapsedTime(&ms[k], t->ev[k], t->ev[k + 1]));
+  return FMM_OK;
+}
+
+const char* fmm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

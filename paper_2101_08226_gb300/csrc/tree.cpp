@@ -1,0 +1,265 @@
+// Host-side tree construction for the CUDA solver.
+//
+// Subgrid sets are kept as hash sets of packed positions per level and refinement is propagated
+// with a work list: refining a subgrid makes its flagged children refine in turn, and every
+// refined subgrid at level l >= 1 demands that each of its 26 in-domain neighbours exists, i.e.
+// that the neighbour's parent is refined (proper nesting, Sec. 2.4).  The result is the least
+// refined tree that contains every flagged subgrid that exists and is properly nested.
+#include "tree.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <deque>
+#include <unordered_map>
+#include <unordered_set>
+
+namespace octofmm {
+
+namespace {
+
+inline uint64_t pos_key(int64_t i, int64_t j, int64_t k) {
+  return (uint64_t(i) << 42) | (uint64_t(j) << 21) | uint64_t(k);
+}
+inline void pos_unkey(uint64_t p, int64_t& i, int64_t& j, int64_t& k) {
+  i = int64_t(p >> 42);
+  j = int64_t((p >> 21) & ((1u << 21) - 1));
+  k = int64_t(p & ((1u << 21) - 1));
+}
+// Morton interleave: x bit above y bit above z bit in each triple.
+inline uint64_t morton(int lev, int64_t i, int64_t j, int64_t k) {
+  uint64_t m = 0;
+  for (int b = lev - 1; b >= 0; --b)
+    m = (m << 3) | (uint64_t((i >> b) & 1) << 2) | (uint64_t((j >> b) & 1) << 1) |
+        uint64_t((k >> b) & 1);
+  return m;
+}
+
+}  // namespace
+
+bool well_separated(int dx, int dy, int dz, double theta) {
+  int d2 = dx * dx + dy * dy + dz * dz;
+  if (d2 == 0) return false;
+  return 1.0 / std::sqrt(double(d2)) < theta;
+}
+
+std::string build_host_tree(int max_level, const uint8_t* flags, int64_t n_flags, HostTree& t) {
+  if (max_level < 0 || max_level > kMaxLevel) return "max_level out of range";
+  std::vector<int64_t> foff(max_level + 1, 0);
+  for (int l = 1; l <= max_level; ++l) foff[l] = foff[l - 1] + (int64_t(1) << (3 * (l - 1)));
+  if (n_flags != foff[max_level]) return "n_flags does not match max_level";
+  if (n_flags > 0 && !flags) return "refine_flags is null";
+
+  auto flagged = [&](int l, int64_t i, int64_t j, int64_t k) -> bool {
+    if (l >= max_level) return false;
+    int64_t n = int64_t(1) << l;
+    return flags[foff[l] + (i * n + j) * n + k] != 0;
+  };
+
+  std::vector<std::unordered_set<uint64_t>> refined(max_level + 1);
+  std::deque<std::pair<int, uint64_t>> work;
+  // Refine (l, p): its parent must be refined for it to exist; flagged children follow.
+  struct Refiner {
+    std::vector<std::unordered_set<uint64_t>>& refined;
+    std::deque<std::pair<int, uint64_t>>& work;
+    decltype(flagged)& is_flagged;
+    int max_level;
+    void operator()(int l, uint64_t p) {
+      if (l >= max_level || refined[l].count(p)) return;
+      int64_t i, j, k;
+      pos_unkey(p, i, j, k);
+      if (l > 0) (*this)(l - 1, pos_key(i / 2, j / 2, k / 2));
+      if (!refined[l].insert(p).second) return;
+      work.emplace_back(l, p);
+      for (int o = 0; o < 8; ++o) {
+        int64_t a = 2 * i + ((o >> 2) & 1), b = 2 * j + ((o >> 1) & 1), c = 2 * k + (o & 1);
+        if (is_flagged(l + 1, a, b, c)) (*this)(l + 1, pos_key(a, b, c));
+      }
+    }
+  } refine{refined, work, flagged, max_level};
+
+  if (flagged(0, 0, 0, 0)) refine(0, pos_key(0, 0, 0));
+  while (!work.empty()) {
+    auto [l, p] = work.front();
+    work.pop_front();
+    if (l == 0) continue;
+    int64_t i, j, k, n = int64_t(1) << l;
+    pos_unkey(p, i, j, k);
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dz = -1; dz <= 1; ++dz) {
+          int64_t a = i + dx, b = j + dy, c = k + dz;
+          if (a < 0 || b < 0 || c < 0 || a >= n || b >= n || c >= n) continue;
+          refine(l - 1, pos_key(a / 2, b / 2, c / 2));
+        }
+  }
+
+  // Existing subgrids per level: the root, and the children of refined subgrids.
+  struct Node { uint64_t key; int64_t i, j, k; };
+  std::vector<std::vector<Node>> levels;
+  levels.push_back({Node{0, 0, 0, 0}});
+  for (int l = 0; l < max_level && !refined[l].empty(); ++l) {
+    std::vector<Node> next;
+    next.reserve(refined[l].size() * 8);
+    for (uint64_t p : refined[l]) {
+      int64_t i, j, k;
+      pos_unkey(p, i, j, k);
+      for (int o = 0; o < 8; ++o) {
+        int64_t a = 2 * i + ((o >> 2) & 1), b = 2 * j + ((o >> 1) & 1), c = 2 * k + (o & 1);
+        next.push_back(Node{morton(l + 1, a, b, c), a, b, c});
+      }
+    }
+    levels.push_back(std::move(next));
+  }
+  t = HostTree();
+  t.depth = int(levels.size()) - 1;
+  t.lev_off.assign(t.depth + 2, 0);
+  for (int l = 0; l <= t.depth; ++l) {
+    std::sort(levels[l].begin(), levels[l].end(),
+              [](const Node& x, const Node& y) { return x.key < y.key; });
+    t.lev_off[l + 1] = t.lev_off[l] + int64_t(levels[l].size());
+  }
+  t.n_sub = t.lev_off[t.depth + 1];
+  t.level.resize(t.n_sub);
+  t.ijk.resize(3 * t.n_sub);
+  t.leaf.resize(t.n_sub);
+  t.parent.assign(t.n_sub, -1);
+  t.child.assign(8 * t.n_sub, -1);
+  t.nbr.assign(27 * t.n_sub, -1);
+  t.leaf_ord.assign(t.n_sub, -1);
+  t.refined_at.assign(t.depth + 1, {});
+  t.leaves_at.assign(t.depth + 1, {});
+  std::vector<std::unordered_map<uint64_t, int32_t>> index(t.depth + 1);
+  for (int l = 0; l <= t.depth; ++l) {
+    index[l].reserve(levels[l].size() * 2);
+    for (size_t q = 0; q < levels[l].size(); ++q) {
+      const Node& nd = levels[l][q];
+      int32_t s = int32_t(t.lev_off[l] + int64_t(q));
+      t.level[s] = l;
+      t.ijk[3 * s] = int32_t(nd.i);
+      t.ijk[3 * s + 1] = int32_t(nd.j);
+      t.ijk[3 * s + 2] = int32_t(nd.k);
+      bool is_ref = l < max_level && refined[l].count(pos_key(nd.i, nd.j, nd.k));
+      t.leaf[s] = is_ref ? 0 : 1;
+      index[l][pos_key(nd.i, nd.j, nd.k)] = s;
+    }
+  }
+  for (int l = 0; l <= t.depth; ++l) {
+    int64_t n = int64_t(1) << l;
+    for (int64_t s = t.lev_off[l]; s < t.lev_off[l + 1]; ++s) {
+      int64_t i = t.ijk[3 * s], j = t.ijk[3 * s + 1], k = t.ijk[3 * s + 2];
+      if (l > 0) {
+        auto it = index[l - 1].find(pos_key(i / 2, j / 2, k / 2));
+        if (it == index[l - 1].end()) return "internal: parent missing";
+        t.parent[s] = it->second;
+        int o = int((i & 1) << 2 | (j & 1) << 1 | (k & 1));
+        t.child[8 * it->second + o] = int32_t(s);
+      }
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            int64_t a = i + dx, b = j + dy, c = k + dz;
+            if (a < 0 || b < 0 || c < 0 || a >= n || b >= n || c >= n) continue;
+            auto it = index[l].find(pos_key(a, b, c));
+            if (it != index[l].end()) t.nbr[27 * s + (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1)] = it->second;
+          }
+      if (t.leaf[s]) {
+        t.leaf_ord[s] = int32_t(t.leaf_sub.size());
+        t.leaf_sub.push_back(int32_t(s));
+        t.leaves_at[l].push_back(int32_t(s));
+      } else {
+        t.refined_at[l].push_back(int32_t(s));
+        for (int o = 0; o < 8; ++o)
+          if (!index[l + 1].count(pos_key(2 * i + ((o >> 2) & 1), 2 * j + ((o >> 1) & 1),
+                                          2 * k + (o & 1))))
+            return "internal: child missing";
+        for (int slot = 0; slot < 27; ++slot)
+          if (slot != 13) {
+            int dx = slot / 9 - 1, dy = (slot / 3) % 3 - 1, dz = slot % 3 - 1;
+            int64_t a = i + dx, b = j + dy, c = k + dz;
+            if (a >= 0 && b >= 0 && c >= 0 && a < n && b < n && c < n && t.nbr[27 * s + slot] < 0)
+              return "internal: nesting violated";
+          }
+      }
+    }
+  }
+  t.n_leaf_sub = int64_t(t.leaf_sub.size());
+  return "";
+}
+
+Stencil make_stencil(double theta) {
+  Stencil st;
+  st.theta = theta;
+  for (int par = 0; par < 8; ++par) {
+    int a[3] = {(par >> 2) & 1, (par >> 1) & 1, par & 1};
+    for (int dx = -kMaxReach; dx <= kMaxReach; ++dx)
+      for (int dy = -kMaxReach; dy <= kMaxReach; ++dy)
+        for (int dz = -kMaxReach; dz <= kMaxReach; ++dz) {
+          if (!well_separated(dx, dy, dz, theta)) continue;
+          // parents' offset: floor((a + d) / 2) - floor(a / 2), with a in {0, 1}
+          int px = (a[0] + dx) >> 1, py = (a[1] + dy) >> 1, pz = (a[2] + dz) >> 1;
+          if (well_separated(px, py, pz, theta)) continue;
+          st.offs[par].push_back(pack_offset(dx, dy, dz));
+        }
+  }
+  for (int dx = -2; dx <= 2; ++dx)
+    for (int dy = -2; dy <= 2; ++dy)
+      for (int dz = -2; dz <= 2; ++dz)
+        if ((dx || dy || dz) && !well_separated(dx, dy, dz, theta))
+          st.near.push_back(pack_offset(dx, dy, dz));
+  return st;
+}
+
+void interaction_counts_by_type(const HostTree& t, const Stencil& st, int64_t out[6]) {
+  // Per neighbour slot: how many (target cell, offset) pairs of one subgrid land in that slot.
+  int64_t m2l_slot[27] = {0}, near_slot[27] = {0};
+  for (int c = 0; c < kCells; ++c) {
+    int a = c / 64, b = (c / 8) % 8, z = c % 8;
+    int par = (a & 1) << 2 | (b & 1) << 1 | (z & 1);
+    auto add = [&](const std::vector<int32_t>& list, int64_t* slots) {
+      for (int32_t code : list) {
+        int dx, dy, dz;
+        unpack_offset(code, dx, dy, dz);
+        int sx = ((a + dx) >> 3) + 1, sy = ((b + dy) >> 3) + 1, sz = ((z + dz) >> 3) + 1;
+        slots[sx * 9 + sy * 3 + sz]++;
+      }
+    };
+    add(st.offs[par], m2l_slot);
+    add(st.near, near_slot);
+  }
+  int64_t root_ws = 0, root_near = 0;
+  for (int c = 0; c < kCells; ++c)
+    for (int e = 0; e < kCells; ++e) {
+      if (c == e) continue;
+      if (well_separated(c / 64 - e / 64, (c / 8) % 8 - (e / 8) % 8, c % 8 - e % 8, st.theta))
+        root_ws++;
+      else
+        root_near++;
+    }
+  for (int k = 0; k < 6; ++k) out[k] = 0;
+  if (t.leaf[0]) {
+    out[0] += root_ws;
+    out[4] += root_near;
+  } else {
+    out[3] += root_ws;
+  }
+  for (int64_t s = 1; s < t.n_sub; ++s)
+    for (int slot = 0; slot < 27; ++slot) {
+      int32_t nb = t.nbr[27 * s + slot];
+      if (nb < 0) continue;
+      out[(t.leaf[s] ? 0 : 2) + (t.leaf[nb] ? 0 : 1)] += m2l_slot[slot];
+      if (t.leaf[s]) {
+        if (t.leaf[nb]) out[4] += near_slot[slot];
+        else out[5] += 16 * near_slot[slot];  // i <- 8 children and 8 children <- i
+      }
+    }
+}
+
+void interaction_counts(const HostTree& t, const Stencil& st, int64_t out[3]) {
+  int64_t c[6];
+  interaction_counts_by_type(t, st, c);
+  out[0] = c[0] + c[1] + c[2] + c[3];
+  out[1] = c[4];
+  out[2] = c[5];
+}
+
+}  // namespace octofmm

@@ -223,26 +223,28 @@ def leaf_density(fld: Field, leaves: np.ndarray) -> np.ndarray:
 
 
 def refinement_flags(fld: Field, max_level: int, refine_frac: float) -> np.ndarray:
-    """Dense flags: position p at level l (< max_level) is flagged iff the maximum of rho sampled at
-    its 8^3 cell centres exceeds refine_frac * rho_peak.  Positions whose box bound cannot exceed
-    the threshold are skipped without sampling."""
+    """Dense flags: position p at level l (< max_level) is flagged iff the density exceeds
+    refine_frac * rho_peak somewhere in the subgrid's volume.  Each star's profile is radial and
+    non-increasing, so its maximum over the box is its value at the box point closest to the
+    star's centre; the flag tests that maximum star by star (and the floor).  Point samples at
+    coarse cell centres would miss a star that lies between them, while in an evolved field the
+    coarse cells carry the mass of the finer ones."""
     out = np.zeros(flags_size(max_level), dtype=np.uint8)
     thr = refine_frac * fld.rho_peak
+    floor_hit = fld.floor * fld.rho_peak > thr
     for lev in range(max_level):
         n = 1 << lev
         ii, jj, kk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
         ijk = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1)
-        dx = 1.0 / (SUBGRID_N * n)
-        lo = -0.5 + ijk * (SUBGRID_N * dx) + 0.5 * dx
-        hi = lo + (SUBGRID_N - 1) * dx
-        cand = np.nonzero(fld.upper_bound_in_box(lo, hi) > thr)[0]
-        flags = np.zeros(ijk.shape[0], dtype=np.uint8)
-        for s in range(0, cand.size, 4096):
-            sel = cand[s:s + 4096]
-            c = cell_centres(lev, ijk[sel]).reshape(len(sel), 512, 3)
-            flags[sel] = (fld.rho(c).max(axis=1) > thr).astype(np.uint8)
+        lo = -0.5 + ijk / n
+        hi = lo + 1.0 / n
+        hit = np.full(ijk.shape[0], floor_hit)
+        for st in fld.stars:
+            c = np.asarray(st.center)
+            q = np.clip(c, lo, hi)
+            hit |= st.rho_of_r(np.linalg.norm(q - c, axis=1)) > thr
         off = flags_offset(lev)
-        out[off:off + ijk.shape[0]] = flags
+        out[off:off + ijk.shape[0]] = hit.astype(np.uint8)
     return out
 
 

@@ -40,18 +40,34 @@ def test_splitmix64_published_vector():
     assert synth.SplitMix64(0).next_u64() == 0xE220A8397B1DCDAF
 
 
-def test_refinement_flags_match_brute_force_small():
-    fld = synth.binary_field(0.7, 0.1, 0.085, 0.35)
-    flags = synth.refinement_flags(fld, 3, 1e-4)
+def test_refinement_flags_bracketed_by_sampling():
+    """A flagged subgrid holds a point above the threshold (its closest point to a star centre);
+    every subgrid with a fine sample above the threshold is flagged."""
+    fld = synth.binary_field(0.6, 0.1, 0.085, 0.3)
+    flags = synth.refinement_flags(fld, 4, 1e-4)
     thr = 1e-4 * fld.rho_peak
-    for lev in range(3):
+    for lev in range(4):
         n = 1 << lev
-        ii, jj, kk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
-        ijk = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1)
-        c = synth.cell_centres(lev, ijk).reshape(len(ijk), 512, 3)
-        brute = (fld.rho(c).max(axis=1) > thr).astype(np.uint8)
         off = synth.flags_offset(lev)
-        assert np.array_equal(flags[off:off + n ** 3], brute)
+        u = (np.arange(9) + 0.5) / 9
+        fx, fy, fz = np.meshgrid(u, u, u, indexing="ij")
+        fine = np.stack([fx.ravel(), fy.ravel(), fz.ravel()], axis=1)
+        for i in range(n):
+            for j in range(n):
+                for k in range(n):
+                    lo = -0.5 + np.array([i, j, k]) / n
+                    f = flags[off + (i * n + j) * n + k]
+                    pts = lo + fine / n
+                    sampled = fld.rho(pts).max() > thr
+                    if sampled:
+                        assert f == 1
+                    if f:
+                        ok = False
+                        for st in fld.stars:
+                            q = np.clip(np.asarray(st.center), lo, lo + 1.0 / n)
+                            ok |= bool(st.rho(q[None])[0] > thr)
+                        assert ok
+    assert flags[0] == 1  # the root holds both stars
 
 
 def test_perturbed_density_bounds_and_seed():
