@@ -132,6 +132,21 @@ int fmm_phase_times(fmm_tree* tree, float* ms_host, int n);
 /* Number of kernels the most recent solve on this tree launched (all of them this library's). */
 int fmm_last_launches(const fmm_tree* tree, int32_t* n);
 
+/* Net force, torque and normalisation of an explicit point set, allocating no device memory.
+ * The paper has no counterpart: this serves callers that cannot call cudaMalloc, such as code
+ * inside a framework that owns all device memory through its own pool, or a latency-critical
+ * loop where an allocation (and the device synchronisation it can imply) is not acceptable.
+ * x_dev: [n][3] positions, m_dev: [n] masses, g_dev: [n][3] accelerations (device pointers);
+ * net_dev: 7 doubles (F_x, F_y, F_z, T_x, T_y, T_z, S) as for fmm_solve, with F = sum m g,
+ * T = sum x cross m g, S = sum |x| |m g|.  Partial sums live in a fixed 112 KiB device array of
+ * this library, so n may not exceed FMM_NET_STATIC_MAX_POINTS (FMM_ERR_ARG otherwise).  The first
+ * call on a device looks up that array's address; make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race and must be serialised
+ * by the caller (one stream, or events).  Asynchronous on `stream`. */
+#define FMM_NET_STATIC_MAX_POINTS (2048LL * 4096LL)
+int fmm_net_force_torque_points_static(int64_t n, const double* x_dev, const double* m_dev,
+                                       const double* g_dev, double* net_dev, void* stream);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char* fmm_last_error(void);
 

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -903,6 +904,62 @@ static int solve_impl(fmm_tree* t, const double* rho, double theta, int precisio
 }
 
 // ----------------------------------------------------------------------------------------------
+// net force and torque of an explicit point set, with no device allocation
+// ----------------------------------------------------------------------------------------------
+// Some callers cannot allocate device memory: code that runs inside a framework owning all
+// device memory through its own pool, or code on a latency-critical path where cudaMalloc and
+// its implicit device synchronisation are not acceptable.  For them this reduction keeps its
+// per-block partial sums in a fixed, file-scope device array instead of a workspace.  The array
+// is shared by every call on a device and is held by every GPU that loads this library until the
+// process exits.  Each block overwrites its own slot, so nothing needs clearing between calls;
+// calls that overlap on the GPU (different streams, or threads) race on the slots.
+constexpr int kStaticNetPointsPerBlock = 4096;
+constexpr int kStaticNetMaxBlocks = 2048;  // 2048 * 7 doubles = 112 KiB
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) double g_net_static_scratch[kStaticNetMaxBlocks * 7];
+
+__global__ void __launch_bounds__(kReduceThreads)
+    k_net_points_partial(int64_t n, const double* __restrict__ x, const double* __restrict__ m,
+                         const double* __restrict__ g, double* __restrict__ partials) {
+  __shared__ double sh[7][kReduceThreads];
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  const int64_t begin = int64_t(blockIdx.x) * kStaticNetPointsPerBlock;
+  int64_t end = begin + kStaticNetPointsPerBlock;
+  if (end > n) end = n;
+  for (int64_t i = begin + threadIdx.x; i < end; i += kReduceThreads) {
+    double px = x[3 * i], py = x[3 * i + 1], pz = x[3 * i + 2];
+    double fx = m[i] * g[3 * i], fy = m[i] * g[3 * i + 1], fz = m[i] * g[3 * i + 2];
+    v[0] += fx;
+    v[1] += fy;
+    v[2] += fz;
+    v[3] += py * fz - pz * fy;
+    v[4] += pz * fx - px * fz;
+    v[5] += px * fy - py * fx;
+    v[6] += sqrt(px * px + py * py + pz * pz) * sqrt(fx * fx + fy * fy + fz * fz);
+  }
+  block_sum7(v, sh);
+  if (threadIdx.x < 7) partials[int64_t(blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+static std::mutex g_static_mu;
+static double* g_static_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once per device.
+static int static_net_scratch(double** out) {
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(FMM_ERR_STATE, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    CUDA_TRY(cudaGetSymbolAddress(&p, g_net_static_scratch));
+    g_static_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return FMM_OK;
+}
+
+// ----------------------------------------------------------------------------------------------
 // C ABI
 // ----------------------------------------------------------------------------------------------
 extern "C" {
@@ -1062,6 +1119,27 @@ int fmm_phase_times(fmm_tree* t, float* ms, int n) {
   if (!t->ev_recorded) return fail(FMM_ERR_STATE, "no profiled solve recorded");
   CUDA_TRY(cudaEventSynchronize(t->ev[4]));
   for (int k = 0; k < n && k < 4; ++k) CUDA_TRY(cudaEventElapsedTime(&ms[k], t->ev[k], t->ev[k + 1]));
+  return FMM_OK;
+}
+
+int fmm_net_force_torque_points_static(int64_t n, const double* x_dev, const double* m_dev,
+                                       const double* g_dev, double* net_dev, void* stream) {
+  if (!x_dev || !m_dev || !g_dev || !net_dev || n < 0) return fail(FMM_ERR_ARG, "bad argument");
+  if (n > int64_t(kStaticNetMaxBlocks) * kStaticNetPointsPerBlock)
+    return fail(FMM_ERR_ARG, "n exceeds FMM_NET_STATIC_MAX_POINTS (" +
+                                 std::to_string(int64_t(kStaticNetMaxBlocks) * kStaticNetPointsPerBlock) +
+                                 "), the capacity of the fixed scratch array");
+  double* scratch = nullptr;
+  int rc = static_net_scratch(&scratch);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int blocks = int((n + kStaticNetPointsPerBlock - 1) / kStaticNetPointsPerBlock);
+  if (blocks > 0) {
+    k_net_points_partial<<<blocks, kReduceThreads, 0, st>>>(n, x_dev, m_dev, g_dev, scratch);
+    CUDA_TRY(cudaGetLastError());
+  }
+  k_net_final<<<1, kReduceThreads, 0, st>>>(scratch, blocks, net_dev);
+  CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }
 

@@ -179,7 +179,7 @@ def test_host_entry_point_equals_device_entry_point():
 
 @pytest.mark.parametrize("levels,precision", [(5, "fp64"), (5, "mixed"), (7, "fp64")])
 def test_full_size_sampled(levels, precision):
-    """configs[1]-size binary (q = 0.7, about 0.9M cells) and the 7-level q = 0.6 binary (13.5M
+    """The 5-level q = 0.7 binary (about 0.9M cells) and the 7-level q = 0.6 binary (13.5M
     cells): the oracle evaluates a sample of leaf cells one by one."""
     if levels == 7:
         w = synth.workload_binary(7, q=0.6, a=0.3)
