@@ -36,11 +36,16 @@ WORKLOAD = ("AMR binary: two n=3/2 polytropes, q=0.7, R=0.1/0.085, a=0.35, floor
 METRIC = "FMM cell-cell interactions/s (directed M2L pairs) and gravity-solve ms per solve"
 
 # Algorithmic flops per directed interaction, counted from the kernels' formulas (an FMA counts
-# 2, a reciprocal square root 1): leaf<-leaf and direct pairs need only the monopole field; a
-# refined source adds its 2nd and 3rd moments; a refined target adds the 2nd and 3rd derivatives
-# of its expansion; the correction needs the 4th derivative contracted with 3rd moments.
-FLOPS = {"m2l_leaf_leaf": 20, "m2l_leaf_refined": 199, "m2l_refined_leaf": 186,
-         "m2l_refined_refined": 309, "p2p_same": 20, "p2p_mixed": 20}
+# 2, a reciprocal square root 1).  Same-level leaf pairs (multipole or direct) are two point masses
+# at cell centres: 4 FMAs against tabulated 1/|d| and d/|d|^3.  Direct pairs across a level jump
+# evaluate the point-mass field from the separation.  A refined source adds its 2nd and 3rd
+# moments; a refined target adds the 2nd and 3rd derivatives of its expansion; the correction
+# needs the 4th derivative contracted with 3rd moments.
+FLOPS = {"m2l_leaf_leaf": 8, "p2p_same": 8, "p2p_mixed": 20, "m2l_leaf_refined": 199,
+         "m2l_refined_leaf": 186, "m2l_refined_refined": 309}
+# which interaction kernel evaluates which pairs
+KERNEL_PAIRS = {"k_m2l_ref": ("m2l_refined_leaf", "m2l_refined_refined"),
+                "k_m2l_leaf": ("m2l_leaf_leaf", "m2l_leaf_refined", "p2p_same", "p2p_mixed")}
 SMS = 152
 SM_MAX_GHZ = 2.07
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1e3    # 2 FP64 FMA / clock / SM
@@ -181,8 +186,7 @@ def run_ours(args):
     rho0 = synth.leaf_density(w.field, tree.leaves())
     counts = tree.counts_by_type(THETA)
     n_m2l = sum(v for k, v in counts.items() if k.startswith("m2l"))
-    flops = algorithmic_flops(counts)
-    m2l_flops = flops  # every counted interaction runs in the interaction kernel
+    kernel_flops = {k: sum(FLOPS[c] * counts[c] for c in cs) for k, cs in KERNEL_PAIRS.items()}
     floor = w.field.floor * w.field.rho_peak
     n_steps = args.warmup + args.steps
     rhos = [torch.from_numpy(synth.perturbed_density(rho0, rank * 1000 + k, floor_value=floor)).to(dev)
@@ -207,7 +211,7 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        step_ms, m2l_ms, phases = [], [], []
+        step_ms, phases = [], []
         for k in range(args.warmup, n_steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -217,9 +221,7 @@ def run_ours(args):
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
-            ph = tree.phase_times()
-            phases.append(ph)
-            m2l_ms.append(float(ph[1]))
+            phases.append(tree.phase_times())
         torch.cuda.synchronize()
         tree.sync_status(stream)
         total = float(np.sum(step_ms))
@@ -228,12 +230,12 @@ def run_ours(args):
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             total = float(tt.item())
         launches = tree.last_launches() * args.steps
-        return total, float(np.mean(m2l_ms)), np.mean(np.array(phases), axis=0), launches
+        return total, np.mean(np.array(phases), axis=0), launches
 
     sampler = ClockSampler(uuid) if (uuid and rank == 0) else None
-    t64, m2l64, ph64, l64 = timed("fp64")
+    t64, ph64, l64 = timed("fp64")
     phi64, g64, net64 = phi.clone(), g.clone(), net.clone()
-    t32, m2l32, ph32, l32 = timed("mixed")
+    t32, ph32, l32 = timed("mixed")
     clocks = sampler.stop() if sampler else None
     # mixed-path error against the FP64 path on the same (last) input
     gn = g64.norm(dim=1)
@@ -275,8 +277,25 @@ def run_ours(args):
     cpu = cpu_baseline() if world == 1 else None
     value64 = world * n_m2l * args.steps / (t64 * 1e-3)
     value32 = world * n_m2l * args.steps / (t32 * 1e-3)
-    ach64 = m2l_flops / (m2l64 * 1e-3) / 1e12
-    ach32 = m2l_flops / (m2l32 * 1e-3) / 1e12
+
+    def roofline(ph, precision):
+        # the dominant interaction kernel of this precision, timed with CUDA events on the
+        # solve's stream inside the timed region
+        ms = {"k_m2l_ref": float(ph[4]), "k_m2l_leaf": float(ph[5])}
+        k = max(ms, key=ms.get)
+        ach = kernel_flops[k] / (ms[k] * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
+        unit = "FP64" if precision == "fp64" else "FP32"
+        return {"bound": "alu", "kernel": f"{k}<{'double' if precision == 'fp64' else 'float'}>",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel_ms": ms[k], "kernel_flops": kernel_flops[k],
+                "other_kernel_ms": {kk: v for kk, v in ms.items() if kk != k},
+                "peak_source": f"derived: 152 SMs x {2 if unit == 'FP64' else 128} {unit} FMA/clk "
+                               "x 2 flop x 2.07 GHz"}
+
+    def phases(ph):
+        return {"upward": float(ph[0]), "interactions": float(ph[1]), "downward": float(ph[2]),
+                "reductions": float(ph[3]), "k_m2l_ref": float(ph[4]), "k_m2l_leaf": float(ph[5])}
     line = {
         "metric": METRIC, "value": value64, "unit": "interactions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t64 / args.steps,
@@ -287,21 +306,12 @@ def run_ours(args):
                    "p2p_mixed_pairs": counts["p2p_mixed"], "pair_types": counts,
                    "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"{world} independent replicas"},
-        "roofline": {"bound": "alu", "kernel": "k_m2l<double>", "achieved": ach64,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
-                     "traffic": None, "m2l_kernel_ms": m2l64,
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"},
-        "phases_ms": {"upward": float(ph64[0]), "interactions": float(ph64[1]),
-                      "downward": float(ph64[2]), "reductions": float(ph64[3])},
+        "roofline": roofline(ph64, "fp64"),
+        "phases_ms": phases(ph64),
         "mixed": {"value": value32, "ms_per_step": t32 / args.steps, "dtype": "f32 pairs, f64 rest",
                   "speedup_vs_fp64": t64 / t32, "err_vs_fp64": err,
-                  "roofline": {"bound": "alu", "kernel": "k_m2l<float>", "achieved": ach32,
-                               "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                               "frac": ach32 / FP32_PEAK_TFLOPS, "traffic": None,
-                               "m2l_kernel_ms": m2l32,
-                               "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"},
-                  "phases_ms": {"upward": float(ph32[0]), "interactions": float(ph32[1]),
-                                "downward": float(ph32[2]), "reductions": float(ph32[3])},
+                  "roofline": roofline(ph32, "mixed"),
+                  "phases_ms": phases(ph32),
                   "gpu_launches": l32},
         "e2e": {"value": world * n_m2l * args.steps / e2e_s, "unit": "interactions/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n + 24 * n + 56,

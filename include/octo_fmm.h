@@ -125,7 +125,9 @@ int fmm_net_force_torque(fmm_tree* tree, const double* rho_dev, const double* g_
 
 /* Per-phase device times (ms) of the most recent solve on this tree, measured with CUDA events
  * on the solve's stream when profiling is on: [0] upward pass, [1] multipole interactions and
- * near field, [2] downward pass, [3] reductions.  fmm_set_profiling(tree, 1) turns it on. */
+ * near field, [2] downward pass, [3] reductions, [4] the interaction kernel of refined cells
+ * (with the root level), [5] the interaction kernel of leaf cells.  Writes min(n, 6) values.
+ * fmm_set_profiling(tree, 1) turns it on. */
 int fmm_set_profiling(fmm_tree* tree, int on);
 int fmm_phase_times(fmm_tree* tree, float* ms_host, int n);
 

@@ -137,6 +137,8 @@ class Tree:
         check(lib().fmm_set_profiling(self._h, int(bool(on))))
 
     def phase_times(self) -> np.ndarray:
-        out = np.zeros(4, dtype=np.float32)
-        check(lib().fmm_phase_times(self._h, _p(out), 4))
+        """ms of the last profiled solve: upward, interactions, downward, reductions, then the
+        two interaction kernels (refined targets with the root, leaf targets)."""
+        out = np.zeros(6, dtype=np.float32)
+        check(lib().fmm_phase_times(self._h, _p(out), 6))
         return out

@@ -19,6 +19,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -69,8 +70,15 @@ struct DevArgs {
   const int32_t* near;     // packed near offsets
   int n_stencil;           // per parity (the same for every parity)
   int n_near;
-  double* mom;             // [20][n_cell]
-  float* mom32;            // [20][n_cell] (mixed path)
+  const int32_t* ltab_off; // [8][kLeafCap] halo offsets of stencil + near entries
+  const int32_t* ltab_code;// [8][kLeafCap] packed offsets
+  const double* ltab_k64;  // [8][kLeafCap][4]: 1/|d|, d/|d|^3
+  const float* ltab_k32;   // same in FP32
+  const double* ltab_d64;  // [8][kLeafCap][4]: d (dx, dy, dz, 0) as floating-point numbers
+  const float* ltab_d32;
+  double* mom;             // [20][n_cell] raw moments (shifted by m2m)
+  double* mtl;             // [20][n_cell] same with detraced M2, M3 (read by the interactions)
+  float* mom32;            // [20][n_cell] FP32 copy of mtl (mixed path)
   double* loc;             // [20][n_cell] own, then total expansion
   float* loc32;            // [20][n_cell] own expansion (mixed path)
   double* ac;              // [3][n_cell] correction acceleration, own then total
@@ -81,6 +89,11 @@ struct DevArgs {
 };
 
 constexpr int kStencilCap = 1024;
+constexpr int kLeafCap = 1024;       // stencil + near entries per parity
+constexpr int kHalo = 18;            // subgrid plus 5 cells on each side
+constexpr int kHalo2 = kHalo * kHalo;
+constexpr int kHalo3 = kHalo2 * kHalo;
+constexpr int kLeafThreads = 256;    // one block = one leaf subgrid, two target cells per thread
 constexpr int kRootChunks = 8;       // root sources split into 8 chunks of 64 cells
 constexpr int kM2LThreads = 64;      // one block = the 64 cells of one parity of one subgrid
 constexpr int kReduceThreads = 256;
@@ -112,7 +125,9 @@ __global__ void k_p2m(DevArgs A, const double* __restrict__ rho) {
   }
   double h = cell_dx(lev);
   // the other 19 moments of a leaf cell stay zero from the workspace initialisation
-  A.mom[cell] = r * h * h * h;
+  const double m = r * h * h * h;
+  A.mom[cell] = m;
+  A.mtl[cell] = m;
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -148,9 +163,10 @@ __global__ void k_m2m(DevArgs A, const int32_t* __restrict__ subs, int n_subs) {
   }
   double dx = 0, dy = 0, dz = 0;
   if (mt > 0) {
-    dx = sx / mt;
-    dy = sy / mt;
-    dz = sz / mt;
+    const double inv = 1.0 / mt;
+    dx = sx * inv;
+    dy = sy * inv;
+    dz = sz * inv;
   }
   double M2[6] = {0, 0, 0, 0, 0, 0}, M3[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
@@ -190,6 +206,21 @@ __global__ void k_m2m(DevArgs A, const int32_t* __restrict__ subs, int n_subs) {
   for (int k = 0; k < 6; ++k) A.mom[(4 + k) * N + cell] = M2[k];
 #pragma unroll
   for (int k = 0; k < 10; ++k) A.mom[(10 + k) * N + cell] = M3[k];
+  // detraced copies for the interactions
+  const double tr3 = (M2[0] + M2[3] + M2[5]) * (1.0 / 3.0);
+  const double tx = (M3[0] + M3[3] + M3[5]) * 0.2, ty = (M3[1] + M3[6] + M3[8]) * 0.2,
+               tz = (M3[2] + M3[7] + M3[9]) * 0.2;
+  const double M2t[6] = {M2[0] - tr3, M2[1], M2[2], M2[3] - tr3, M2[4], M2[5] - tr3};
+  const double M3t[10] = {M3[0] - 3 * tx, M3[1] - ty,     M3[2] - tz, M3[3] - tx, M3[4],
+                          M3[5] - tx,     M3[6] - 3 * ty, M3[7] - tz, M3[8] - ty, M3[9] - 3 * tz};
+  A.mtl[cell] = mt;
+  A.mtl[N + cell] = dx;
+  A.mtl[2 * N + cell] = dy;
+  A.mtl[3 * N + cell] = dz;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) A.mtl[(4 + k) * N + cell] = M2t[k];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) A.mtl[(10 + k) * N + cell] = M3t[k];
 }
 
 __global__ void k_to_fp32(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
@@ -202,10 +233,21 @@ __global__ void k_to_fp32(const double* __restrict__ src, float* __restrict__ ds
 // m2l: own expansion of every cell
 // ----------------------------------------------------------------------------------------------
 template <typename T>
+struct LeafOffsets;
+template <>
+struct LeafOffsets<double> {
+  static __device__ __forceinline__ const double* get(const DevArgs& A) { return A.ltab_d64; }
+};
+template <>
+struct LeafOffsets<float> {
+  static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.ltab_d32; }
+};
+
+template <typename T>
 struct MomView;
 template <>
 struct MomView<double> {
-  static __device__ __forceinline__ const double* get(const DevArgs& A) { return A.mom; }
+  static __device__ __forceinline__ const double* get(const DevArgs& A) { return A.mtl; }
 };
 template <>
 struct MomView<float> {
@@ -216,7 +258,8 @@ struct MomView<float> {
 template <typename T, bool AREF>
 struct Target {
   T L[AREF ? 20 : 4];
-  double ax, ay, az;
+  double ax, ay, az;     // correction acceleration, FP64 sums
+  T px, py, pz;          // FP32-or-FP64 partial sums flushed into ax.. by flush()
   T dAx, dAy, dAz;   // target centre-of-mass displacement
   T mA_inv;          // 1 / m_A (0 when m_A = 0)
   T M3A[AREF ? 10 : 1];
@@ -254,9 +297,9 @@ __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict
       }
       T cx, cy, cz;
       amc_term<T>(x, y, z, g, Q, cx, cy, cz);
-      S.ax += double(cx);
-      S.ay += double(cy);
-      S.az += double(cz);
+      S.px += cx;
+      S.py += cy;
+      S.pz += cz;
     }
   } else {
     g.set(x, y, z, AREF ? 4 : 1);
@@ -270,12 +313,22 @@ __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict
         for (int k = 0; k < 10; ++k) Q[k] = w * S.M3A[k];
         T cx, cy, cz;
         amc_term<T>(x, y, z, g, Q, cx, cy, cz);
-        S.ax += double(cx);
-        S.ay += double(cy);
-        S.az += double(cz);
+        S.px += cx;
+        S.py += cy;
+        S.pz += cz;
       }
     }
   }
+}
+
+// Adds the partial correction sums to the FP64 accumulators (the mixed path sums at most 32
+// pair terms in FP32 before each flush).
+template <typename T, bool AREF>
+__device__ __forceinline__ void flush(Target<T, AREF>& S) {
+  S.ax += double(S.px);
+  S.ay += double(S.py);
+  S.az += double(S.pz);
+  S.px = S.py = S.pz = T(0);
 }
 
 // Point-mass source at separation R (exact positions).
@@ -292,6 +345,7 @@ __device__ __forceinline__ void load_target(Target<T, AREF>& S, const DevArgs& A
 #pragma unroll
   for (int k = 0; k < (AREF ? 20 : 4); ++k) S.L[k] = T(0);
   S.ax = S.ay = S.az = 0.0;
+  S.px = S.py = S.pz = T(0);
   const int64_t N = A.n_cell;
   S.amc = amc;
   if constexpr (AREF) {
@@ -317,8 +371,12 @@ template <>
 __device__ __forceinline__ void store_own<double, true>(const DevArgs& A,
                                                         const Target<double, true>& S, int64_t iA) {
   const int64_t N = A.n_cell;
+  double L[20];
 #pragma unroll
-  for (int k = 0; k < 20; ++k) A.loc[k * N + iA] = S.L[k];
+  for (int k = 0; k < 20; ++k) L[k] = S.L[k];
+  complete_traceless(L);
+#pragma unroll
+  for (int k = 0; k < 20; ++k) A.loc[k * N + iA] = L[k];
   A.ac[iA] = S.ax;
   A.ac[N + iA] = S.ay;
   A.ac[2 * N + iA] = S.az;
@@ -337,8 +395,12 @@ template <>
 __device__ __forceinline__ void store_own<float, true>(const DevArgs& A,
                                                        const Target<float, true>& S, int64_t iA) {
   const int64_t N = A.n_cell;
+  float L[20];
 #pragma unroll
-  for (int k = 0; k < 20; ++k) A.loc32[k * N + iA] = S.L[k];
+  for (int k = 0; k < 20; ++k) L[k] = S.L[k];
+  complete_traceless(L);
+#pragma unroll
+  for (int k = 0; k < 20; ++k) A.loc32[k * N + iA] = L[k];
   A.ac[iA] = S.ax;
   A.ac[N + iA] = S.ay;
   A.ac[2 * N + iA] = S.az;
@@ -391,7 +453,8 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, bool amc) {
   Target<T, AREF> S;
   load_target<T, AREF>(S, A, M, iA, amc);
   const T h = T(cell_dx(lev));
-  const int32_t* __restrict__ st = A.stencil + parity * kStencilCap;
+  const int32_t* __restrict__ st = A.ltab_code + parity * kLeafCap;
+  const T* __restrict__ td = LeafOffsets<T>::get(A) + int64_t(parity) * kLeafCap * 4;
   // same-level multipole interactions
   for (int q = 0; q < A.n_stencil; ++q) {
     int32_t code = __ldg(st + q);
@@ -402,9 +465,11 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, bool amc) {
     int32_t sB = nb[slot];
     if (sB < 0) continue;
     int64_t iB = int64_t(sB) * kCells + ((px & 7) * 8 + (py & 7)) * 8 + (pz & 7);
-    interact<T, AREF>(S, M, N, iB, nb_ref[slot] != 0, S.dAx - T(dx) * h, S.dAy - T(dy) * h,
-                      S.dAz - T(dz) * h);
+    interact<T, AREF>(S, M, N, iB, nb_ref[slot] != 0, S.dAx - __ldg(td + 4 * q) * h,
+                      S.dAy - __ldg(td + 4 * q + 1) * h, S.dAz - __ldg(td + 4 * q + 2) * h);
+    if ((q & 31) == 31) flush(S);
   }
+  flush(S);
   if (!AREF) {
     // direct sums with non-separated cells of the same level: leaves directly, refined cells
     // through their 8 (leaf) children one level finer
@@ -478,8 +543,11 @@ __device__ void m2l_root(const DevArgs& A, int parity, int chunk, double theta, 
     if (!ws && !root_leaf) continue;
     interact<T, AREF>(S, M, N, j, !root_leaf, S.dAx - T(dx) * h, S.dAy - T(dy) * h,
                       S.dAz - T(dz) * h);
+    if ((j & 31) == 31) flush(S);
   }
+  flush(S);
   // partials: [chunk][component][cell]
+  if constexpr (AREF) complete_traceless(S.L);
   if (sizeof(T) == 8) {
     double* P = A.root_part + int64_t(chunk) * 23 * kCells;
     for (int k = 0; k < (AREF ? 20 : 4); ++k) P[k * kCells + iloc] = double(S.L[k]);
@@ -498,22 +566,200 @@ __device__ void m2l_root(const DevArgs& A, int parity, int chunk, double theta, 
   }
 }
 
-// Block b < 8 * kRootChunks: root (parity b & 7, chunk b >> 3); then one block per (subgrid in
-// `work`, parity).
+// Leaf targets of a subgrid at a refinement boundary, one parity: multipole interactions with
+// cells of refined same-level neighbours, direct sums with the leaf children of refined near
+// cells, and direct sums with leaves one level coarser near the parent cell.  Runs after the
+// leaf kernel and adds onto its output.
 template <typename T>
-__global__ void __launch_bounds__(kM2LThreads) k_m2l(DevArgs A, const int32_t* __restrict__ work,
-                                                     double theta, int amc) {
-  int b = blockIdx.x;
-  if (b < 8 * kRootChunks) {
-    if (A.leaf[0]) m2l_root<T, false>(A, b & 7, b >> 3, theta, amc != 0);
-    else m2l_root<T, true>(A, b & 7, b >> 3, theta, amc != 0);
-    return;
+__device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, bool amc) {
+  __shared__ int32_t nb[27];
+  __shared__ uint8_t nb_ref[27];
+  __shared__ int32_t pnb[27];
+  __shared__ uint8_t pnb_leaf[27];
+  const int t = threadIdx.x;
+  if (t < 27) {
+    int32_t q = A.nbr[27 * s + t];
+    nb[t] = q;
+    nb_ref[t] = (q >= 0 && !A.leaf[q]) ? 1 : 0;
+    int32_t P = A.parent[s];
+    int32_t pq = A.nbr[27 * P + t];
+    pnb[t] = pq;
+    pnb_leaf[t] = (pq >= 0 && A.leaf[pq]) ? 1 : 0;
   }
-  b -= 8 * kRootChunks;
-  int32_t s = work[b >> 3];
-  int parity = b & 7;
-  if (A.leaf[s]) m2l_level<T, false>(A, s, parity, amc != 0);
-  else m2l_level<T, true>(A, s, parity, amc != 0);
+  __syncthreads();
+  const int lev = A.level[s];
+  const T* __restrict__ M = MomView<T>::get(A);
+  const int64_t N = A.n_cell;
+  int a, b, c;
+  block_cell(parity, t, a, b, c);
+  const int64_t iA = int64_t(s) * kCells + (a * 8 + b) * 8 + c;
+  Target<T, false> S;
+  load_target<T, false>(S, A, M, iA, amc);
+  const T h = T(cell_dx(lev)), hc = h * T(0.5);
+  const int32_t* __restrict__ st = A.ltab_code + parity * kLeafCap;
+  const T* __restrict__ td = LeafOffsets<T>::get(A) + int64_t(parity) * kLeafCap * 4;
+  for (int q = 0; q < A.n_stencil; ++q) {
+    int dx, dy, dz;
+    unpack_offset(__ldg(st + q), dx, dy, dz);
+    int px = a + dx, py = b + dy, pz = c + dz;
+    int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
+    if (!nb_ref[slot]) continue;
+    int64_t iB = int64_t(nb[slot]) * kCells + ((px & 7) * 8 + (py & 7)) * 8 + (pz & 7);
+    interact<T, false>(S, M, N, iB, true, -__ldg(td + 4 * q) * h, -__ldg(td + 4 * q + 1) * h,
+                       -__ldg(td + 4 * q + 2) * h);
+    if ((q & 31) == 31) flush(S);
+  }
+  flush(S);
+  for (int q = 0; q < A.n_near; ++q) {
+    int dx, dy, dz;
+    unpack_offset(__ldg(A.near + q), dx, dy, dz);
+    int px = a + dx, py = b + dy, pz = c + dz;
+    int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
+    if (!nb_ref[slot]) continue;
+    int lx = px & 7, ly = py & 7, lz = pz & 7;
+    int32_t cs = A.child[8 * nb[slot] + ((lx >> 2) << 2 | (ly >> 2) << 1 | (lz >> 2))];
+    for (int o = 0; o < 8; ++o) {
+      int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+      int64_t iC = int64_t(cs) * kCells + (((lx & 3) * 2 + ox) * 8 + (ly & 3) * 2 + oy) * 8 +
+                   (lz & 3) * 2 + oz;
+      // x_A - x_C = (1/2 - o - 2 d) dx_(l+1)
+      interact_point<T, false>(S, M[iC], (T(0.5) - T(ox) - T(2 * dx)) * hc,
+                               (T(0.5) - T(oy) - T(2 * dy)) * hc, (T(0.5) - T(oz) - T(2 * dz)) * hc);
+    }
+  }
+  const int32_t P = A.parent[s];
+  int ga = A.ijk[3 * s] * 8 + a, gb = A.ijk[3 * s + 1] * 8 + b, gc = A.ijk[3 * s + 2] * 8 + c;
+  int ja = (ga >> 1) - A.ijk[3 * P] * 8, jb = (gb >> 1) - A.ijk[3 * P + 1] * 8,
+      jc = (gc >> 1) - A.ijk[3 * P + 2] * 8;
+  for (int q = 0; q < A.n_near; ++q) {
+    int dx, dy, dz;
+    unpack_offset(__ldg(A.near + q), dx, dy, dz);
+    int px = ja + dx, py = jb + dy, pz = jc + dz;
+    int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
+    if (!pnb_leaf[slot]) continue;
+    int64_t iB = int64_t(pnb[slot]) * kCells + ((px & 7) * 8 + (py & 7)) * 8 + (pz & 7);
+    // x_A - x_i = ((g_A & 1) - 1/2 - 2 d) dx_l
+    interact_point<T, false>(S, M[iB], (T(ga & 1) - T(0.5) - T(2 * dx)) * h,
+                             (T(gb & 1) - T(0.5) - T(2 * dy)) * h, (T(gc & 1) - T(0.5) - T(2 * dz)) * h);
+  }
+  // add onto the leaf kernel's output
+  if (sizeof(T) == 8) {
+    for (int k = 0; k < 4; ++k) A.loc[k * N + iA] += double(S.L[k]);
+  } else {
+    for (int k = 0; k < 4; ++k) A.loc32[k * N + iA] += float(S.L[k]);
+  }
+  A.ac[iA] += S.ax;
+  A.ac[N + iA] += S.ay;
+  A.ac[2 * N + iA] += S.az;
+}
+
+// One block per entry of `blocks`, sorted by estimated cost (largest first): code
+// (kind << 30) | (parity << 27) | index, kind 0 = root source chunk `index`, 1 = refined subgrid
+// `index`, 2 = leaf subgrid `index` at a refinement boundary.
+template <typename T>
+__global__ void __launch_bounds__(kM2LThreads) k_m2l_ref(DevArgs A, const int32_t* __restrict__ blocks,
+                                                         double theta, int amc) {
+  const int32_t code = blocks[blockIdx.x];
+  const int kind = (code >> 30) & 3, parity = (code >> 27) & 7, idx = code & ((1 << 27) - 1);
+  if (kind == 0) {
+    if (A.leaf[0]) m2l_root<T, false>(A, parity, idx, theta, amc != 0);
+    else m2l_root<T, true>(A, parity, idx, theta, amc != 0);
+  } else if (kind == 1) {
+    m2l_level<T, true>(A, idx, parity, amc != 0);
+  } else {
+    m2l_boundary<T>(A, idx, parity, amc != 0);
+  }
+}
+
+template <typename T>
+struct LeafTab;
+template <>
+struct LeafTab<double> {
+  static __device__ __forceinline__ const double* get(const DevArgs& A) { return A.ltab_k64; }
+};
+template <>
+struct LeafTab<float> {
+  static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.ltab_k32; }
+};
+
+// Leaf subgrids at levels >= 1.  A leaf cell and a leaf partner at the same level are two point
+// masses at their geometric centres, R = -d dx exactly, so their interaction (multipole or direct,
+// the same monopole formula) is 1/|d| and d/|d|^3 from a per-offset table times the partner's
+// mass: L0 -= m / (|d| dx), L1 -= m d / (|d|^3 dx^2).  The masses of the subgrid and of the 5-cell
+// rim of its neighbours are staged in shared memory (0 for cells of refined or absent
+// neighbours, whose partners the boundary pass of k_m2l_ref adds afterwards).
+template <typename T>
+__global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int32_t* __restrict__ work) {
+  __shared__ T hm[kHalo3];
+  __shared__ int32_t nb[27];
+  const int32_t s = work[blockIdx.x];
+  const int t = threadIdx.x;
+  if (t < 27) {
+    int32_t q = A.nbr[27 * s + t];
+    nb[t] = (q >= 0 && A.leaf[q]) ? q : -1;
+  }
+  __syncthreads();
+  const T* __restrict__ M = MomView<T>::get(A);
+  const int64_t N = A.n_cell;
+  for (int i = t; i < kHalo3; i += kLeafThreads) {
+    int hx = i / kHalo2, r = i - hx * kHalo2, hy = r / kHalo, hz = r - hy * kHalo;
+    int x = hx - 5, y = hy - 5, z = hz - 5;
+    int32_t q = nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)];
+    hm[i] = q >= 0 ? M[int64_t(q) * kCells + ((x & 7) * 8 + (y & 7)) * 8 + (z & 7)] : T(0);
+  }
+  __syncthreads();
+  const T h = T(cell_dx(A.level[s]));
+  const int parity = t >> 5, lane = t & 31;
+  const int px = (parity >> 2) & 1, py = (parity >> 1) & 1, pz = parity & 1;
+  const int a0 = 2 * (lane >> 4) + px,  // second target: a0 + 4
+            b = 2 * ((lane >> 2) & 3) + py, c = 2 * (lane & 3) + pz;
+  const int base0 = (a0 + 5) * kHalo2 + (b + 5) * kHalo + (c + 5);
+  const int base1 = base0 + 4 * kHalo2;
+  const int32_t* __restrict__ toff = A.ltab_off + parity * kLeafCap;
+  const T* __restrict__ tk = LeafTab<T>::get(A) + int64_t(parity) * kLeafCap * 4;
+  const int n_tab = A.n_stencil + A.n_near;
+  T s0 = 0, sx = 0, sy = 0, sz = 0, u0 = 0, ux = 0, uy = 0, uz = 0;
+#pragma unroll 4
+  for (int q = 0; q < n_tab; ++q) {
+    const int off = __ldg(toff + q);
+    const T k0 = __ldg(tk + 4 * q), kx = __ldg(tk + 4 * q + 1), ky = __ldg(tk + 4 * q + 2),
+            kz = __ldg(tk + 4 * q + 3);
+    const T m0 = hm[base0 + off], m1 = hm[base1 + off];
+    s0 += m0 * k0;
+    sx += m0 * kx;
+    sy += m0 * ky;
+    sz += m0 * kz;
+    u0 += m1 * k0;
+    ux += m1 * kx;
+    uy += m1 * ky;
+    uz += m1 * kz;
+  }
+  const T ih = T(1) / h, ih2 = ih * ih;
+  const int64_t i0 = int64_t(s) * kCells + (a0 * 8 + b) * 8 + c;
+  const int64_t i1 = i0 + 4 * 64;
+  if (sizeof(T) == 8) {
+    double* L = reinterpret_cast<double*>(A.loc);
+    L[i0] = -double(s0 * ih);
+    L[N + i0] = -double(sx * ih2);
+    L[2 * N + i0] = -double(sy * ih2);
+    L[3 * N + i0] = -double(sz * ih2);
+    L[i1] = -double(u0 * ih);
+    L[N + i1] = -double(ux * ih2);
+    L[2 * N + i1] = -double(uy * ih2);
+    L[3 * N + i1] = -double(uz * ih2);
+  } else {
+    float* L = A.loc32;
+    L[i0] = -float(s0 * ih);
+    L[N + i0] = -float(sx * ih2);
+    L[2 * N + i0] = -float(sy * ih2);
+    L[3 * N + i0] = -float(sz * ih2);
+    L[i1] = -float(u0 * ih);
+    L[N + i1] = -float(ux * ih2);
+    L[2 * N + i1] = -float(uy * ih2);
+    L[3 * N + i1] = -float(uz * ih2);
+  }
+  A.ac[i0] = A.ac[N + i0] = A.ac[2 * N + i0] = 0.0;
+  A.ac[i1] = A.ac[N + i1] = A.ac[2 * N + i1] = 0.0;
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -524,14 +770,14 @@ __global__ void __launch_bounds__(kM2LThreads) k_m2l(DevArgs A, const int32_t* _
 //   L2' = L2 + L3 r,  L3' = L3.
 __device__ __forceinline__ void shift_add(const double* P, double rx, double ry, double rz,
                                           double* L, bool full) {
-  double tx, ty, tz, qx, qy, qz;
-  sym3_vectors<double>(P + 10, rx, ry, rz, tx, ty, tz, qx, qy, qz);
+  double qx, qy, qz;
+  sym3_rr<double>(P + 10, rx, ry, rz, qx, qy, qz);
   // L2 r
   double l2x = P[4] * rx + P[5] * ry + P[6] * rz;
   double l2y = P[5] * rx + P[7] * ry + P[8] * rz;
   double l2z = P[6] * rx + P[8] * ry + P[9] * rz;
   L[0] += P[0] + P[1] * rx + P[2] * ry + P[3] * rz + 0.5 * (rx * l2x + ry * l2y + rz * l2z) +
-          (rx * qx + ry * qy + rz * qz) / 6.0;
+          (rx * qx + ry * qy + rz * qz) * (1.0 / 6.0);
   L[1] += P[1] + l2x + 0.5 * qx;
   L[2] += P[2] + l2y + 0.5 * qy;
   L[3] += P[3] + l2z + 0.5 * qz;
@@ -682,6 +928,14 @@ __global__ void __launch_bounds__(kReduceThreads)
 struct StencilDev {
   int32_t* d_stencil = nullptr;  // [8][kStencilCap]
   int32_t* d_near = nullptr;
+  int32_t* d_ltab_off = nullptr;   // [8][kLeafCap]
+  int32_t* d_ltab_code = nullptr;  // [8][kLeafCap]
+  double* d_ltab_k64 = nullptr;    // [8][kLeafCap][4]
+  float* d_ltab_k32 = nullptr;
+  double* d_ltab_d64 = nullptr;    // [8][kLeafCap][4]
+  float* d_ltab_d32 = nullptr;
+  int32_t* d_blocks = nullptr;     // general-kernel block list for this tree and theta
+  int64_t n_blocks = 0;
   int n_stencil = 0, n_near = 0;
 };
 
@@ -691,21 +945,23 @@ struct fmm_tree {
   bool dev_ready = false, mixed_ready = false;
   int32_t *d_level = nullptr, *d_ijk = nullptr, *d_parent = nullptr, *d_child = nullptr,
           *d_nbr = nullptr, *d_leaf_sub = nullptr, *d_leaf_ord = nullptr, *d_work = nullptr,
-          *d_refined = nullptr;
+          *d_work_leaf = nullptr, *d_work_bnd = nullptr, *d_refined = nullptr;
+  int64_t n_work_leaf = 0, n_work_bnd = 0;
   uint8_t* d_leaf = nullptr;
   std::vector<int64_t> refined_off;  // offsets into d_refined per level
   int64_t n_work = 0;
-  double *d_mom = nullptr, *d_loc = nullptr, *d_ac = nullptr, *d_root_part = nullptr,
+  double *d_mom = nullptr, *d_mtl = nullptr, *d_loc = nullptr, *d_ac = nullptr, *d_root_part = nullptr,
          *d_root_part_ac = nullptr, *d_partials = nullptr;
   float *d_mom32 = nullptr, *d_loc32 = nullptr, *d_root_part32 = nullptr;
   int* d_status = nullptr;
   double *d_rho = nullptr, *d_phi = nullptr, *d_g = nullptr, *d_net = nullptr;
   std::map<double, StencilDev> stencils;
   bool profiling = false;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool ev_recorded = false;
   int32_t launches = 0;
   std::vector<void*> allocs;
+  std::vector<int32_t> work, work_bnd;  // refined and boundary leaf subgrids of levels >= 1
 };
 
 template <typename P>
@@ -745,12 +1001,31 @@ static int ensure_device(fmm_tree* t) {
   CUDA_TRY(upload(t, &t->d_nbr, h.nbr));
   CUDA_TRY(upload(t, &t->d_leaf_sub, h.leaf_sub));
   CUDA_TRY(upload(t, &t->d_leaf_ord, h.leaf_ord));
-  // multipole-interaction work: refined subgrids (coarse to fine), then leaf subgrids, levels >= 1
-  std::vector<int32_t> work, refined;
+  // interaction work at levels >= 1: refined subgrids (coarse to fine) and leaf subgrids
+  std::vector<int32_t> work, work_leaf, refined;
   for (int l = 1; l <= h.depth; ++l) work.insert(work.end(), h.refined_at[l].begin(), h.refined_at[l].end());
-  for (int l = 1; l <= h.depth; ++l) work.insert(work.end(), h.leaves_at[l].begin(), h.leaves_at[l].end());
+  for (int l = 1; l <= h.depth; ++l) work_leaf.insert(work_leaf.end(), h.leaves_at[l].begin(), h.leaves_at[l].end());
+  // leaf subgrids at a refinement boundary: a refined same-level neighbour, or a leaf neighbour
+  // of the parent (leaves one level coarser)
+  std::vector<int32_t> work_bnd;
+  for (int32_t s : work_leaf) {
+    bool bnd = false;
+    for (int k = 0; k < 27; ++k) {
+      int32_t q = h.nbr[27 * s + k];
+      if (q >= 0 && !h.leaf[q]) bnd = true;
+      int32_t pq = h.nbr[27 * h.parent[s] + k];
+      if (pq >= 0 && h.leaf[pq]) bnd = true;
+    }
+    if (bnd) work_bnd.push_back(s);
+  }
   t->n_work = int64_t(work.size());
+  t->n_work_leaf = int64_t(work_leaf.size());
+  t->n_work_bnd = int64_t(work_bnd.size());
+  t->work = work;
+  t->work_bnd = work_bnd;
   CUDA_TRY(upload(t, &t->d_work, work));
+  CUDA_TRY(upload(t, &t->d_work_leaf, work_leaf));
+  CUDA_TRY(upload(t, &t->d_work_bnd, work_bnd));
   t->refined_off.assign(h.depth + 2, 0);
   for (int l = 0; l <= h.depth; ++l) {
     refined.insert(refined.end(), h.refined_at[l].begin(), h.refined_at[l].end());
@@ -759,6 +1034,8 @@ static int ensure_device(fmm_tree* t) {
   CUDA_TRY(upload(t, &t->d_refined, refined));
   CUDA_TRY(dalloc(t, &t->d_mom, sizeof(double) * kNMom * nc));
   CUDA_TRY(cudaMemset(t->d_mom, 0, sizeof(double) * kNMom * nc));  // leaf cells keep zeros
+  CUDA_TRY(dalloc(t, &t->d_mtl, sizeof(double) * kNMom * nc));
+  CUDA_TRY(cudaMemset(t->d_mtl, 0, sizeof(double) * kNMom * nc));
   CUDA_TRY(dalloc(t, &t->d_loc, sizeof(double) * 20 * nc));
   CUDA_TRY(dalloc(t, &t->d_ac, sizeof(double) * 3 * nc));
   CUDA_TRY(dalloc(t, &t->d_root_part, sizeof(double) * kRootChunks * 23 * kCells));
@@ -780,6 +1057,75 @@ static int ensure_mixed(fmm_tree* t) {
   return FMM_OK;
 }
 
+static int32_t block_code(uint32_t kind, uint32_t parity, uint32_t index) {
+  return int32_t((kind << 30) | (parity << 27) | index);
+}
+
+// Block list of the general interaction kernel, sorted by an estimate of each block's work
+// (pairs times a per-kind cost in FP64 instructions), largest first, so that the long blocks
+// start early and the short ones fill the tail.
+static std::vector<int32_t> general_blocks(const HostTree& h, const Stencil& st,
+                                           const std::vector<int32_t>& work,
+                                           const std::vector<int32_t>& work_bnd) {
+  const double c_rr = 230, c_rl = 140, c_lr = 150, c_pt = 20, c_iter = 4;
+  // per target parity: how many (cell, offset) pairs land in each neighbour slot
+  double st_slot[8][27] = {}, nr_slot[8][27] = {}, co_slot[8][8][27] = {};
+  for (int c = 0; c < kCells; ++c) {
+    int a = c / 64, b = (c / 8) % 8, z = c % 8;
+    int par = (a & 1) << 2 | (b & 1) << 1 | (z & 1);
+    for (int32_t code : st.offs[par]) {
+      int dx, dy, dz;
+      unpack_offset(code, dx, dy, dz);
+      st_slot[par][((a + dx) >> 3) * 9 + ((b + dy) >> 3) * 3 + ((z + dz) >> 3) + 13]++;
+    }
+    for (int32_t code : st.near) {
+      int dx, dy, dz;
+      unpack_offset(code, dx, dy, dz);
+      nr_slot[par][((a + dx) >> 3) * 9 + ((b + dy) >> 3) * 3 + ((z + dz) >> 3) + 13]++;
+      for (int o = 0; o < 8; ++o) {  // octant of the subgrid within its parent
+        int ja = 4 * ((o >> 2) & 1) + (a >> 1) + dx, jb = 4 * ((o >> 1) & 1) + (b >> 1) + dy,
+            jc = 4 * (o & 1) + (z >> 1) + dz;
+        co_slot[o][par][(ja >> 3) * 9 + (jb >> 3) * 3 + (jc >> 3) + 13]++;
+      }
+    }
+  }
+  std::vector<std::pair<double, int32_t>> items;
+  const double root_cost = 64.0 * 64.0 * (h.leaf[0] ? c_pt : c_rr);
+  for (int ch = 0; ch < kRootChunks; ++ch)
+    for (int p = 0; p < 8; ++p) items.push_back({root_cost, block_code(0, p, ch)});
+  for (int32_t s : work)
+    for (int p = 0; p < 8; ++p) {
+      double cost = c_iter * 64 * double(st.offs[p].size());
+      for (int k = 0; k < 27; ++k) {
+        int32_t q = h.nbr[27 * s + k];
+        if (q >= 0) cost += st_slot[p][k] * (h.leaf[q] ? c_rl : c_rr);
+      }
+      items.push_back({cost, block_code(1, p, s)});
+    }
+  for (int32_t s : work_bnd) {
+    const int32_t P = h.parent[s];
+    const int o = int((h.ijk[3 * s] & 1) << 2 | (h.ijk[3 * s + 1] & 1) << 1 | (h.ijk[3 * s + 2] & 1));
+    for (int p = 0; p < 8; ++p) {
+      double cost = c_iter * 64 * double(st.offs[p].size() + 2 * st.near.size());
+      for (int k = 0; k < 27; ++k) {
+        int32_t q = h.nbr[27 * s + k];
+        if (q >= 0 && !h.leaf[q]) cost += st_slot[p][k] * c_lr + nr_slot[p][k] * 8 * c_pt;
+        int32_t pq = h.nbr[27 * P + k];
+        if (pq >= 0 && h.leaf[pq]) cost += co_slot[o][p][k] * c_pt;
+      }
+      items.push_back({cost, block_code(2, p, s)});
+    }
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const std::pair<double, int32_t>& x, const std::pair<double, int32_t>& y) {
+                     return x.first > y.first;
+                   });
+  std::vector<int32_t> out;
+  out.reserve(items.size());
+  for (auto& it : items) out.push_back(it.second);
+  return out;
+}
+
 static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
   auto it = t->stencils.find(theta);
   if (it == t->stencils.end()) {
@@ -794,6 +1140,41 @@ static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
     StencilDev sd;
     CUDA_TRY(upload(t, &sd.d_stencil, packed));
     CUDA_TRY(upload(t, &sd.d_near, st.near));
+    // per parity: stencil entries, then near entries, with their exact 1/|d| and d/|d|^3
+    if (n + int(st.near.size()) > kLeafCap) return fail(FMM_ERR_THETA, "stencil too large");
+    std::vector<int32_t> loff(8 * kLeafCap, 0), lcode(8 * kLeafCap, 0);
+    std::vector<double> lk(8 * kLeafCap * 4, 0.0), ld(8 * kLeafCap * 4, 0.0);
+    std::vector<float> lk32(8 * kLeafCap * 4, 0.0f), ld32(8 * kLeafCap * 4, 0.0f);
+    for (int p = 0; p < 8; ++p) {
+      std::vector<int32_t> all(st.offs[p]);
+      all.insert(all.end(), st.near.begin(), st.near.end());
+      for (size_t q = 0; q < all.size(); ++q) {
+        int dx, dy, dz;
+        unpack_offset(all[q], dx, dy, dz);
+        double d2 = double(dx * dx + dy * dy + dz * dz);
+        double k0 = 1.0 / std::sqrt(d2), k3 = k0 / d2;
+        size_t e = size_t(p) * kLeafCap + q;
+        loff[e] = dx * kHalo2 + dy * kHalo + dz;
+        lcode[e] = all[q];
+        double kk[4] = {k0, dx * k3, dy * k3, dz * k3};
+        double dd[4] = {double(dx), double(dy), double(dz), 0.0};
+        for (int c = 0; c < 4; ++c) {
+          lk[4 * e + c] = kk[c];
+          lk32[4 * e + c] = float(kk[c]);
+          ld[4 * e + c] = dd[c];
+          ld32[4 * e + c] = float(dd[c]);
+        }
+      }
+    }
+    CUDA_TRY(upload(t, &sd.d_ltab_off, loff));
+    CUDA_TRY(upload(t, &sd.d_ltab_code, lcode));
+    CUDA_TRY(upload(t, &sd.d_ltab_k64, lk));
+    CUDA_TRY(upload(t, &sd.d_ltab_k32, lk32));
+    CUDA_TRY(upload(t, &sd.d_ltab_d64, ld));
+    CUDA_TRY(upload(t, &sd.d_ltab_d32, ld32));
+    std::vector<int32_t> blocks = general_blocks(t->h, st, t->work, t->work_bnd);
+    sd.n_blocks = int64_t(blocks.size());
+    CUDA_TRY(upload(t, &sd.d_blocks, blocks));
     sd.n_stencil = n;
     sd.n_near = int(st.near.size());
     it = t->stencils.emplace(theta, sd).first;
@@ -819,7 +1200,14 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.near = sd ? sd->d_near : nullptr;
   A.n_stencil = sd ? sd->n_stencil : 0;
   A.n_near = sd ? sd->n_near : 0;
+  A.ltab_off = sd ? sd->d_ltab_off : nullptr;
+  A.ltab_code = sd ? sd->d_ltab_code : nullptr;
+  A.ltab_k64 = sd ? sd->d_ltab_k64 : nullptr;
+  A.ltab_k32 = sd ? sd->d_ltab_k32 : nullptr;
+  A.ltab_d64 = sd ? sd->d_ltab_d64 : nullptr;
+  A.ltab_d32 = sd ? sd->d_ltab_d32 : nullptr;
   A.mom = t->d_mom;
+  A.mtl = t->d_mtl;
   A.mom32 = t->d_mom32;
   A.loc = t->d_loc;
   A.loc32 = t->d_loc32;
@@ -876,14 +1264,21 @@ static int solve_impl(fmm_tree* t, const double* rho, double theta, int precisio
     CUDA_TRY(cudaGetLastError());
   }
   if (mixed) {
-    k_to_fp32<<<1216, 256, 0, st>>>(t->d_mom, t->d_mom32, int64_t(kNMom) * A.n_cell);
+    k_to_fp32<<<1216, 256, 0, st>>>(t->d_mtl, t->d_mom32, int64_t(kNMom) * A.n_cell);
     CUDA_TRY(cudaGetLastError());
   }
   if ((rc = record(t, 1, st))) return rc;
-  // interactions: root chunks + every (subgrid, parity) of levels >= 1
-  unsigned nb = unsigned(8 * kRootChunks + 8 * t->n_work);
-  if (mixed) k_m2l<float><<<nb, kM2LThreads, 0, st>>>(A, t->d_work, theta, amc);
-  else k_m2l<double><<<nb, kM2LThreads, 0, st>>>(A, t->d_work, theta, amc);
+  // interactions: leaf subgrids of levels >= 1 (same-level leaf partners), then the general
+  // kernel: root chunks, every (refined subgrid, parity) and every (boundary leaf subgrid, parity)
+  if (t->n_work_leaf > 0) {
+    if (mixed) k_m2l_leaf<float><<<unsigned(t->n_work_leaf), kLeafThreads, 0, st>>>(A, t->d_work_leaf);
+    else k_m2l_leaf<double><<<unsigned(t->n_work_leaf), kLeafThreads, 0, st>>>(A, t->d_work_leaf);
+    CUDA_TRY(cudaGetLastError());
+  }
+  if ((rc = record(t, 5, st))) return rc;
+  unsigned nb = unsigned(sd->n_blocks);
+  if (mixed) k_m2l_ref<float><<<nb, kM2LThreads, 0, st>>>(A, sd->d_blocks, theta, amc);
+  else k_m2l_ref<double><<<nb, kM2LThreads, 0, st>>>(A, sd->d_blocks, theta, amc);
   CUDA_TRY(cudaGetLastError());
   if ((rc = record(t, 2, st))) return rc;
   // downward pass
@@ -899,7 +1294,8 @@ static int solve_impl(fmm_tree* t, const double* rho, double theta, int precisio
   t->ev_recorded = t->profiling;
   int32_t n_m2m = 0;
   for (int l = 0; l < h.depth; ++l) n_m2m += (t->refined_off[l + 1] > t->refined_off[l]) ? 1 : 0;
-  t->launches = 1 + n_m2m + (mixed ? 1 : 0) + 1 + (h.depth + 1) + (net ? 2 : 0);
+  t->launches = 1 + n_m2m + (mixed ? 1 : 0) + 1 + (t->n_work_leaf > 0 ? 1 : 0) + (h.depth + 1) +
+                 (net ? 2 : 0);
   return FMM_OK;
 }
 
@@ -1119,6 +1515,9 @@ int fmm_phase_times(fmm_tree* t, float* ms, int n) {
   if (!t->ev_recorded) return fail(FMM_ERR_STATE, "no profiled solve recorded");
   CUDA_TRY(cudaEventSynchronize(t->ev[4]));
   for (int k = 0; k < n && k < 4; ++k) CUDA_TRY(cudaEventElapsedTime(&ms[k], t->ev[k], t->ev[k + 1]));
+  // [4] general interaction kernel (root, refined targets, boundary leaves), [5] leaf kernel
+  if (n > 4) CUDA_TRY(cudaEventElapsedTime(&ms[4], t->ev[5], t->ev[2]));
+  if (n > 5) CUDA_TRY(cudaEventElapsedTime(&ms[5], t->ev[1], t->ev[5]));
   return FMM_OK;
 }
 
