@@ -36,16 +36,18 @@ WORKLOAD = ("AMR binary: two n=3/2 polytropes, q=0.7, R=0.1/0.085, a=0.35, floor
 METRIC = "FMM cell-cell interactions/s (directed M2L pairs) and gravity-solve ms per solve"
 
 # Algorithmic flops per directed interaction, counted from the kernels' formulas (an FMA counts
-# 2, a reciprocal square root 1).  Same-level leaf pairs (multipole or direct) are two point masses
-# at cell centres: 4 FMAs against tabulated 1/|d| and d/|d|^3.  Direct pairs across a level jump
-# evaluate the point-mass field from the separation.  A refined source adds its 2nd and 3rd
-# moments; a refined target adds the 2nd and 3rd derivatives of its expansion; the correction
-# needs the 4th derivative contracted with 3rd moments.
-FLOPS = {"m2l_leaf_leaf": 8, "p2p_same": 8, "p2p_mixed": 20, "m2l_leaf_refined": 199,
-         "m2l_refined_leaf": 186, "m2l_refined_refined": 309}
+# 2, a multiply or add 1, a reciprocal square root 1).  Same-level leaf pairs (multipole or
+# direct) are two point masses at cell centres: 4 FMAs against tabulated 1/|d| and d/|d|^3.
+# Direct pairs across a level jump evaluate the point-mass field from the separation.  A refined
+# source adds its detraced 2nd and 3rd moments; a refined target adds the 12 independent
+# components of the 2nd and 3rd derivatives of its expansion; the correction contracts the 4th
+# derivative with detraced 3rd moments.
+FLOPS = {"m2l_leaf_leaf": 8, "p2p_same": 8, "p2p_mixed": 26, "m2l_leaf_refined": 173,
+         "m2l_refined_leaf": 148, "m2l_refined_refined": 243}
 # which interaction kernel evaluates which pairs
-KERNEL_PAIRS = {"k_m2l_ref": ("m2l_refined_leaf", "m2l_refined_refined"),
-                "k_m2l_leaf": ("m2l_leaf_leaf", "m2l_leaf_refined", "p2p_same", "p2p_mixed")}
+KERNEL_PAIRS = {"k_m2l_ref": ("m2l_refined_leaf", "m2l_refined_refined", "m2l_leaf_refined",
+                              "p2p_mixed"),
+                "k_m2l_leaf": ("m2l_leaf_leaf", "p2p_same")}
 SMS = 152
 SM_MAX_GHZ = 2.07
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1e3    # 2 FP64 FMA / clock / SM

@@ -102,7 +102,7 @@ int fmm_interaction_counts_by_type(const fmm_tree* tree, double theta, int64_t c
  * rho_dev: [n_leaf] leaf-cell densities (>= 0, finite).  phi_dev: [n_leaf] potential.
  * g_dev: [n_leaf][3] acceleration.  net_dev (optional, may be NULL): 7 doubles
  *   (F_x, F_y, F_z, T_x, T_y, T_z, S) with F = sum m g, T = sum x cross m g, S = sum |x| |m g|,
- *   reduced in FP64 in a fixed order.
+ *   reduced in FP64 in a fixed order (the terms of the normalisation S are formed in FP32).
  * theta in [0.34, 1).  precision FMM_FP64 or FMM_MIXED.  stream: a cudaStream_t (NULL = legacy
  * default stream).  Asynchronous: returns once the work is enqueued. */
 int fmm_solve(fmm_tree* tree, const double* rho_dev, double theta, int precision, int amc,
@@ -140,7 +140,7 @@ int fmm_last_launches(const fmm_tree* tree, int32_t* n);
  * loop where an allocation (and the device synchronisation it can imply) is not acceptable.
  * x_dev: [n][3] positions, m_dev: [n] masses, g_dev: [n][3] accelerations (device pointers);
  * net_dev: 7 doubles (F_x, F_y, F_z, T_x, T_y, T_z, S) as for fmm_solve, with F = sum m g,
- * T = sum x cross m g, S = sum |x| |m g|.  Partial sums live in a fixed 112 KiB device array of
+ * T = sum x cross m g, S = sum |x| |m g| (FP64 sums; the terms of S formed in FP32).  Partial sums live in a fixed 112 KiB device array of
  * this library, so n may not exceed FMM_NET_STATIC_MAX_POINTS (FMM_ERR_ARG otherwise).  The first
  * call on a device looks up that array's address; make that first call before any stream
  * capture.  All calls share the array: calls that overlap on the GPU race and must be serialised

@@ -70,6 +70,7 @@ struct DevArgs {
   const int32_t* near;     // packed near offsets
   int n_stencil;           // per parity (the same for every parity)
   int n_near;
+  int ws_d2;               // same-level cells are well separated iff |d|^2 > ws_d2
   const int32_t* ltab_off; // [8][kLeafCap] halo offsets of stencil + near entries
   const int32_t* ltab_code;// [8][kLeafCap] packed offsets
   const double* ltab_k64;  // [8][kLeafCap][4]: 1/|d|, d/|d|^3
@@ -101,18 +102,10 @@ constexpr int kReduceBlocks = 512;
 
 __device__ __forceinline__ double cell_dx(int lev) { return 1.0 / double(kSub << lev); }
 
-// theta' = dx / |x_A - x_B| < theta for a same-level offset d (in cells); IEEE sqrt and
-// division, so the decision is the host's bit for bit.
-__device__ __forceinline__ bool well_separated_dev(int dx, int dy, int dz, double theta) {
-  int d2 = dx * dx + dy * dy + dz * dz;
-  if (d2 == 0) return false;
-  return 1.0 / sqrt(double(d2)) < theta;
-}
-
 // ----------------------------------------------------------------------------------------------
 // p2m: leaf cells are point masses rho dx^3 at their centres
 // ----------------------------------------------------------------------------------------------
-__global__ void k_p2m(DevArgs A, const double* __restrict__ rho) {
+__global__ void k_p2m(DevArgs A, const double* __restrict__ rho, int mixed) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= A.n_leaf_cells) return;
   int32_t s = A.leaf_sub[i >> 9];
@@ -128,12 +121,14 @@ __global__ void k_p2m(DevArgs A, const double* __restrict__ rho) {
   const double m = r * h * h * h;
   A.mom[cell] = m;
   A.mtl[cell] = m;
+  if (mixed) A.mom32[cell] = float(m);
 }
 
 // ----------------------------------------------------------------------------------------------
 // m2m: moments of a refined cell from its 8 children (exact shift to the parent's centre of mass)
 // ----------------------------------------------------------------------------------------------
-__global__ void k_m2m(DevArgs A, const int32_t* __restrict__ subs, int n_subs) {
+// One thread per parent cell, for levels with enough cells to fill the GPU.
+__global__ void k_m2m_cell(DevArgs A, const int32_t* __restrict__ subs, int n_subs, int mixed) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= int64_t(n_subs) * kCells) return;
   int32_t s = subs[t >> 9];
@@ -221,13 +216,118 @@ __global__ void k_m2m(DevArgs A, const int32_t* __restrict__ subs, int n_subs) {
   for (int k = 0; k < 6; ++k) A.mtl[(4 + k) * N + cell] = M2t[k];
 #pragma unroll
   for (int k = 0; k < 10; ++k) A.mtl[(10 + k) * N + cell] = M3t[k];
+  if (mixed) {
+    A.mom32[cell] = float(mt);
+    A.mom32[N + cell] = float(dx);
+    A.mom32[2 * N + cell] = float(dy);
+    A.mom32[3 * N + cell] = float(dz);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) A.mom32[(4 + k) * N + cell] = float(M2t[k]);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) A.mom32[(10 + k) * N + cell] = float(M3t[k]);
+  }
 }
 
-__global__ void k_to_fp32(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  for (; i < n; i += stride) dst[i] = float(src[i]);
+// Sum over the 8 lanes of an aligned group, in a fixed order, result in the group's first lane.
+__device__ __forceinline__ double group8_sum(double v) {
+  v += __shfl_down_sync(0xffffffffu, v, 4);
+  v += __shfl_down_sync(0xffffffffu, v, 2);
+  v += __shfl_down_sync(0xffffffffu, v, 1);
+  return v;
 }
+
+// Eight threads per parent cell, one per child, for the coarse levels (FP64 is 1/64 of the FP32
+// rate on this part, so a level of a few subgrids would otherwise run on a few SMs; the shuffle
+// sums add redundant FP64 work, which only pays where cells are few).  The grid covers n_subs * 512 * 8 threads, a
+// multiple of the block size, so every warp is complete for the shuffles.
+constexpr int kM2MThreads = 256;
+constexpr int64_t kM2MCellMin = 16384;  // refined cells of a level from which one thread per cell wins
+__global__ void __launch_bounds__(kM2MThreads) k_m2m(DevArgs A, const int32_t* __restrict__ subs, int mixed) {
+  const int64_t t = int64_t(blockIdx.x) * kM2MThreads + threadIdx.x;
+  const int o = int(t & 7);
+  const int lead = int(threadIdx.x & 31) & ~7;
+  const int64_t pc = t >> 3;
+  const int32_t s = subs[pc >> 9];
+  const int loc = int(pc & 511);
+  const int a = loc >> 6, b = (loc >> 3) & 7, c = loc & 7;
+  const int lev = A.level[s];
+  const int32_t cs = A.child[8 * s + ((a >> 2) << 2 | (b >> 2) << 1 | (c >> 2))];
+  const int64_t N = A.n_cell;
+  const double hc = cell_dx(lev + 1);
+  const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+  const int64_t ci = int64_t(cs) * kCells + (((a & 3) * 2 + ox) * 8 + (b & 3) * 2 + oy) * 8 +
+                     (c & 3) * 2 + oz;
+  // this child's centre of mass relative to the parent's geometric centre
+  const double m = A.mom[ci];
+  const double ux = (ox - 0.5) * hc + A.mom[N + ci], uy = (oy - 0.5) * hc + A.mom[2 * N + ci],
+               uz = (oz - 0.5) * hc + A.mom[3 * N + ci];
+  double mt = group8_sum(m), sx = group8_sum(m * ux), sy = group8_sum(m * uy),
+         sz = group8_sum(m * uz);
+  mt = __shfl_sync(0xffffffffu, mt, lead);
+  sx = __shfl_sync(0xffffffffu, sx, lead);
+  sy = __shfl_sync(0xffffffffu, sy, lead);
+  sz = __shfl_sync(0xffffffffu, sz, lead);
+  double dx = 0, dy = 0, dz = 0;
+  if (mt > 0) {
+    const double inv = 1.0 / mt;
+    dx = sx * inv;
+    dy = sy * inv;
+    dz = sz * inv;
+  }
+  const double rx = ux - dx, ry = uy - dy, rz = uz - dz;
+  double q[6], p[10];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) q[k] = A.mom[(4 + k) * N + ci];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) p[k] = A.mom[(10 + k) * N + ci];
+  // this child's share: M2c + m r r, M3c + r_a M2c_bc + r_b M2c_ac + r_c M2c_ab + m r r r
+  // q: xx0 xy1 xz2 yy3 yz4 zz5
+  double M2[6], M3[10];
+  M2[0] = q[0] + m * rx * rx;
+  M2[1] = q[1] + m * rx * ry;
+  M2[2] = q[2] + m * rx * rz;
+  M2[3] = q[3] + m * ry * ry;
+  M2[4] = q[4] + m * ry * rz;
+  M2[5] = q[5] + m * rz * rz;
+  M3[0] = p[0] + 3 * rx * q[0] + m * rx * rx * rx;
+  M3[1] = p[1] + 2 * rx * q[1] + ry * q[0] + m * rx * rx * ry;
+  M3[2] = p[2] + 2 * rx * q[2] + rz * q[0] + m * rx * rx * rz;
+  M3[3] = p[3] + rx * q[3] + 2 * ry * q[1] + m * rx * ry * ry;
+  M3[4] = p[4] + rx * q[4] + ry * q[2] + rz * q[1] + m * rx * ry * rz;
+  M3[5] = p[5] + rx * q[5] + 2 * rz * q[2] + m * rx * rz * rz;
+  M3[6] = p[6] + 3 * ry * q[3] + m * ry * ry * ry;
+  M3[7] = p[7] + 2 * ry * q[4] + rz * q[3] + m * ry * ry * rz;
+  M3[8] = p[8] + ry * q[5] + 2 * rz * q[4] + m * ry * rz * rz;
+  M3[9] = p[9] + 3 * rz * q[5] + m * rz * rz * rz;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) M2[k] = group8_sum(M2[k]);
+#pragma unroll
+  for (int k = 0; k < 10; ++k) M3[k] = group8_sum(M3[k]);
+  if (o != 0) return;
+  const int64_t cell = int64_t(s) * kCells + loc;
+  A.mom[cell] = mt;
+  A.mom[N + cell] = dx;
+  A.mom[2 * N + cell] = dy;
+  A.mom[3 * N + cell] = dz;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) A.mom[(4 + k) * N + cell] = M2[k];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) A.mom[(10 + k) * N + cell] = M3[k];
+  // detraced copies for the interactions (and their FP32 copies for the mixed path)
+  const double tr3 = (M2[0] + M2[3] + M2[5]) * (1.0 / 3.0);
+  const double tx = (M3[0] + M3[3] + M3[5]) * 0.2, ty = (M3[1] + M3[6] + M3[8]) * 0.2,
+               tz = (M3[2] + M3[7] + M3[9]) * 0.2;
+  const double T[20] = {mt, dx, dy, dz, M2[0] - tr3, M2[1], M2[2], M2[3] - tr3, M2[4],
+                        M2[5] - tr3, M3[0] - 3 * tx, M3[1] - ty, M3[2] - tz, M3[3] - tx, M3[4],
+                        M3[5] - tx, M3[6] - 3 * ty, M3[7] - tz, M3[8] - ty, M3[9] - 3 * tz};
+#pragma unroll
+  for (int k = 0; k < 20; ++k) A.mtl[k * N + cell] = T[k];
+  if (mixed) {
+#pragma unroll
+    for (int k = 0; k < 20; ++k) A.mom32[k * N + cell] = float(T[k]);
+  }
+}
+
 
 // ----------------------------------------------------------------------------------------------
 // m2l: own expansion of every cell
@@ -321,7 +421,7 @@ __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict
   }
 }
 
-// Adds the partial correction sums to the FP64 accumulators (the mixed path sums at most 32
+// Adds the partial correction sums to the FP64 accumulators (the mixed path sums at most 64
 // pair terms in FP32 before each flush).
 template <typename T, bool AREF>
 __device__ __forceinline__ void flush(Target<T, AREF>& S) {
@@ -426,21 +526,21 @@ __device__ __forceinline__ void block_cell(int parity, int t, int& a, int& b, in
 
 // Levels >= 1: target subgrid s, parity p.
 template <typename T, bool AREF>
-__device__ void m2l_level(const DevArgs& A, int32_t s, int parity, bool amc) {
+__device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool amc) {
   __shared__ int32_t nb[27];
   __shared__ uint8_t nb_ref[27];
   __shared__ int32_t pnb[27];   // parent's neighbours (leaf targets: coarser direct partners)
   __shared__ uint8_t pnb_leaf[27];
-  const int t = threadIdx.x;
-  if (t < 27) {
-    int32_t q = A.nbr[27 * s + t];
-    nb[t] = q;
-    nb_ref[t] = (q >= 0 && !A.leaf[q]) ? 1 : 0;
+  const int tid = threadIdx.x;
+  if (tid < 27) {
+    int32_t q = A.nbr[27 * s + tid];
+    nb[tid] = q;
+    nb_ref[tid] = (q >= 0 && !A.leaf[q]) ? 1 : 0;
     if (!AREF) {
       int32_t P = A.parent[s];
-      int32_t pq = A.nbr[27 * P + t];
-      pnb[t] = pq;
-      pnb_leaf[t] = (pq >= 0 && A.leaf[pq]) ? 1 : 0;
+      int32_t pq = A.nbr[27 * P + tid];
+      pnb[tid] = pq;
+      pnb_leaf[tid] = (pq >= 0 && A.leaf[pq]) ? 1 : 0;
     }
   }
   __syncthreads();
@@ -467,7 +567,7 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, bool amc) {
     int64_t iB = int64_t(sB) * kCells + ((px & 7) * 8 + (py & 7)) * 8 + (pz & 7);
     interact<T, AREF>(S, M, N, iB, nb_ref[slot] != 0, S.dAx - __ldg(td + 4 * q) * h,
                       S.dAy - __ldg(td + 4 * q + 1) * h, S.dAz - __ldg(td + 4 * q + 2) * h);
-    if ((q & 31) == 31) flush(S);
+    if ((q & 63) == 63) flush(S);
   }
   flush(S);
   if (!AREF) {
@@ -526,24 +626,31 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, bool amc) {
 // when the root is a leaf, every other root cell interacts directly.  Sources are split into
 // kRootChunks chunks whose partial sums are added in a fixed order by the downward pass.
 template <typename T, bool AREF>
-__device__ void m2l_root(const DevArgs& A, int parity, int chunk, double theta, bool amc) {
+__device__ void m2l_root(const DevArgs& A, int parity, int t, int chunk, bool amc) {
   const T* __restrict__ M = MomView<T>::get(A);
   const int64_t N = A.n_cell;
   int a, b, c;
-  block_cell(parity, threadIdx.x, a, b, c);
+  block_cell(parity, t, a, b, c);
   const int iloc = (a * 8 + b) * 8 + c;
   Target<T, AREF> S;
   load_target<T, AREF>(S, A, M, iloc, amc);
   const T h = T(cell_dx(0));
   const bool root_leaf = A.leaf[0] != 0;
-  for (int j = chunk * 64; j < chunk * 64 + 64; ++j) {
-    if (j == iloc) continue;
-    int dx = (j >> 6) - a, dy = ((j >> 3) & 7) - b, dz = (j & 7) - c;
-    bool ws = well_separated_dev(dx, dy, dz, theta);
-    if (!ws && !root_leaf) continue;
-    interact<T, AREF>(S, M, N, j, !root_leaf, S.dAx - T(dx) * h, S.dAy - T(dy) * h,
-                      S.dAz - T(dz) * h);
-    if ((j & 31) == 31) flush(S);
+  // chunk = source x index; source offsets kept as floating-point counters (no conversions)
+  const int dx = chunk - a;
+  const T rx0 = S.dAx - T(dx) * h;
+  T ry = S.dAy + T(b) * h, rz0 = S.dAz + T(c) * h;  // X_A - x_B for a source at y = z = 0
+  for (int jy = 0; jy < 8; ++jy, ry -= h) {
+    T rz = rz0;
+    for (int jz = 0; jz < 8; ++jz, rz -= h) {
+      const int j = chunk * 64 + jy * 8 + jz;
+      if (j == iloc) continue;
+      const int dy = jy - b, dz = jz - c;
+      const bool ws = dx * dx + dy * dy + dz * dz > A.ws_d2;
+      if (!ws && !root_leaf) continue;
+      interact<T, AREF>(S, M, N, j, !root_leaf, rx0, ry, rz);
+    }
+    if (jy & 1) flush(S);
   }
   flush(S);
   // partials: [chunk][component][cell]
@@ -571,20 +678,20 @@ __device__ void m2l_root(const DevArgs& A, int parity, int chunk, double theta, 
 // cells, and direct sums with leaves one level coarser near the parent cell.  Runs after the
 // leaf kernel and adds onto its output.
 template <typename T>
-__device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, bool amc) {
+__device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, int t, bool amc) {
   __shared__ int32_t nb[27];
   __shared__ uint8_t nb_ref[27];
   __shared__ int32_t pnb[27];
   __shared__ uint8_t pnb_leaf[27];
-  const int t = threadIdx.x;
-  if (t < 27) {
-    int32_t q = A.nbr[27 * s + t];
-    nb[t] = q;
-    nb_ref[t] = (q >= 0 && !A.leaf[q]) ? 1 : 0;
+  const int tid = threadIdx.x;
+  if (tid < 27) {
+    int32_t q = A.nbr[27 * s + tid];
+    nb[tid] = q;
+    nb_ref[tid] = (q >= 0 && !A.leaf[q]) ? 1 : 0;
     int32_t P = A.parent[s];
-    int32_t pq = A.nbr[27 * P + t];
-    pnb[t] = pq;
-    pnb_leaf[t] = (pq >= 0 && A.leaf[pq]) ? 1 : 0;
+    int32_t pq = A.nbr[27 * P + tid];
+    pnb[tid] = pq;
+    pnb_leaf[tid] = (pq >= 0 && A.leaf[pq]) ? 1 : 0;
   }
   __syncthreads();
   const int lev = A.level[s];
@@ -607,40 +714,45 @@ __device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, bool amc) 
     int64_t iB = int64_t(nb[slot]) * kCells + ((px & 7) * 8 + (py & 7)) * 8 + (pz & 7);
     interact<T, false>(S, M, N, iB, true, -__ldg(td + 4 * q) * h, -__ldg(td + 4 * q + 1) * h,
                        -__ldg(td + 4 * q + 2) * h);
-    if ((q & 31) == 31) flush(S);
+    if ((q & 63) == 63) flush(S);
   }
   flush(S);
-  for (int q = 0; q < A.n_near; ++q) {
+  for (int q = A.n_stencil; q < A.n_stencil + A.n_near; ++q) {
     int dx, dy, dz;
-    unpack_offset(__ldg(A.near + q), dx, dy, dz);
+    unpack_offset(__ldg(st + q), dx, dy, dz);
     int px = a + dx, py = b + dy, pz = c + dz;
     int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
     if (!nb_ref[slot]) continue;
     int lx = px & 7, ly = py & 7, lz = pz & 7;
     int32_t cs = A.child[8 * nb[slot] + ((lx >> 2) << 2 | (ly >> 2) << 1 | (lz >> 2))];
+    // x_A - x_C = (1/2 - o - 2 d) dx_(l+1), o the child's octant
+    const T ex = (T(0.5) - T(2) * __ldg(td + 4 * q)) * hc, ey = (T(0.5) - T(2) * __ldg(td + 4 * q + 1)) * hc,
+            ez = (T(0.5) - T(2) * __ldg(td + 4 * q + 2)) * hc;
+    const int64_t c0 = int64_t(cs) * kCells + (((lx & 3) * 2) * 8 + (ly & 3) * 2) * 8 + (lz & 3) * 2;
+#pragma unroll
     for (int o = 0; o < 8; ++o) {
-      int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-      int64_t iC = int64_t(cs) * kCells + (((lx & 3) * 2 + ox) * 8 + (ly & 3) * 2 + oy) * 8 +
-                   (lz & 3) * 2 + oz;
-      // x_A - x_C = (1/2 - o - 2 d) dx_(l+1)
-      interact_point<T, false>(S, M[iC], (T(0.5) - T(ox) - T(2 * dx)) * hc,
-                               (T(0.5) - T(oy) - T(2 * dy)) * hc, (T(0.5) - T(oz) - T(2 * dz)) * hc);
+      const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+      interact_point<T, false>(S, M[c0 + (ox * 8 + oy) * 8 + oz], ex - (ox ? hc : T(0)),
+                               ey - (oy ? hc : T(0)), ez - (oz ? hc : T(0)));
     }
   }
   const int32_t P = A.parent[s];
   int ga = A.ijk[3 * s] * 8 + a, gb = A.ijk[3 * s + 1] * 8 + b, gc = A.ijk[3 * s + 2] * 8 + c;
   int ja = (ga >> 1) - A.ijk[3 * P] * 8, jb = (gb >> 1) - A.ijk[3 * P + 1] * 8,
       jc = (gc >> 1) - A.ijk[3 * P + 2] * 8;
-  for (int q = 0; q < A.n_near; ++q) {
+  // x_A - x_i = ((g_A & 1) - 1/2 - 2 d) dx_l
+  const T fa = (ga & 1) ? T(0.5) : T(-0.5), fb = (gb & 1) ? T(0.5) : T(-0.5),
+          fc = (gc & 1) ? T(0.5) : T(-0.5);
+  for (int q = A.n_stencil; q < A.n_stencil + A.n_near; ++q) {
     int dx, dy, dz;
-    unpack_offset(__ldg(A.near + q), dx, dy, dz);
+    unpack_offset(__ldg(st + q), dx, dy, dz);
     int px = ja + dx, py = jb + dy, pz = jc + dz;
     int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
     if (!pnb_leaf[slot]) continue;
     int64_t iB = int64_t(pnb[slot]) * kCells + ((px & 7) * 8 + (py & 7)) * 8 + (pz & 7);
-    // x_A - x_i = ((g_A & 1) - 1/2 - 2 d) dx_l
-    interact_point<T, false>(S, M[iB], (T(ga & 1) - T(0.5) - T(2 * dx)) * h,
-                             (T(gb & 1) - T(0.5) - T(2 * dy)) * h, (T(gc & 1) - T(0.5) - T(2 * dz)) * h);
+    interact_point<T, false>(S, M[iB], (fa - T(2) * __ldg(td + 4 * q)) * h,
+                             (fb - T(2) * __ldg(td + 4 * q + 1)) * h,
+                             (fc - T(2) * __ldg(td + 4 * q + 2)) * h);
   }
   // add onto the leaf kernel's output
   if (sizeof(T) == 8) {
@@ -655,20 +767,41 @@ __device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, bool amc) 
 
 // One block per entry of `blocks`, sorted by estimated cost (largest first): code
 // (kind << 30) | (parity << 27) | index, kind 0 = root source chunk `index`, 1 = refined subgrid
-// `index`, 2 = leaf subgrid `index` at a refinement boundary.
-template <typename T>
-__global__ void __launch_bounds__(kM2LThreads) k_m2l_ref(DevArgs A, const int32_t* __restrict__ blocks,
-                                                         double theta, int amc) {
+// `index`, 2 = leaf subgrid `index` at a refinement boundary.  With NT = 64 a block serves the 64
+// cells of one parity; with NT = 512 it serves all 8 parities of the subgrid (or all 512 root
+// cells), so that every source the subgrid's cells read is fetched into one SM's L1 once.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_m2l_ref(DevArgs A, const int32_t* __restrict__ blocks,
+                                                int amc) {
   const int32_t code = blocks[blockIdx.x];
-  const int kind = (code >> 30) & 3, parity = (code >> 27) & 7, idx = code & ((1 << 27) - 1);
+  const int kind = (code >> 30) & 3, idx = code & ((1 << 27) - 1);
+  const int parity = NT == 64 ? (code >> 27) & 7 : int(threadIdx.x >> 6);
+  const int t = int(threadIdx.x & 63);
   if (kind == 0) {
-    if (A.leaf[0]) m2l_root<T, false>(A, parity, idx, theta, amc != 0);
-    else m2l_root<T, true>(A, parity, idx, theta, amc != 0);
+    if (A.leaf[0]) m2l_root<T, false>(A, parity, t, idx, amc != 0);
+    else m2l_root<T, true>(A, parity, t, idx, amc != 0);
   } else if (kind == 1) {
-    m2l_level<T, true>(A, idx, parity, amc != 0);
+    m2l_level<T, true>(A, idx, parity, t, amc != 0);
   } else {
-    m2l_boundary<T>(A, idx, parity, amc != 0);
+    m2l_boundary<T>(A, idx, parity, t, amc != 0);
   }
+}
+
+// Four consecutive table values (16-byte aligned) in vector loads.
+__device__ __forceinline__ void load4(const float* p, float& a, float& b, float& c, float& d) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  a = v.x;
+  b = v.y;
+  c = v.z;
+  d = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double& a, double& b, double& c, double& d) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 w = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  a = v.x;
+  b = v.y;
+  c = w.x;
+  d = w.y;
 }
 
 template <typename T>
@@ -722,8 +855,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
 #pragma unroll 4
   for (int q = 0; q < n_tab; ++q) {
     const int off = __ldg(toff + q);
-    const T k0 = __ldg(tk + 4 * q), kx = __ldg(tk + 4 * q + 1), ky = __ldg(tk + 4 * q + 2),
-            kz = __ldg(tk + 4 * q + 3);
+    T k0, kx, ky, kz;
+    load4(tk + 4 * q, k0, kx, ky, kz);
     const T m0 = hm[base0 + off], m1 = hm[base1 + off];
     s0 += m0 * k0;
     sx += m0 * kx;
@@ -795,6 +928,23 @@ __device__ __forceinline__ void shift_add(const double* P, double rx, double ry,
   }
 }
 
+// Mixed path, leaf cells: the parent's total L0 and L1 enter in FP64; the shift terms
+// L1.r + 1/2 r.L2.r + 1/6 L3(r,r,r) and L2 r + 1/2 L3(r,r) (|r| < dx) are formed in FP32 from
+// the FP32 copy of the parent's total, then added in FP64.
+__device__ __forceinline__ void shift_terms32(const float* P, float rx, float ry, float rz,
+                                              float* d) {
+  float qx, qy, qz;
+  sym3_rr<float>(P + 10, rx, ry, rz, qx, qy, qz);
+  float l2x = P[4] * rx + P[5] * ry + P[6] * rz;
+  float l2y = P[5] * rx + P[7] * ry + P[8] * rz;
+  float l2z = P[6] * rx + P[8] * ry + P[9] * rz;
+  d[0] = P[1] * rx + P[2] * ry + P[3] * rz + 0.5f * (rx * l2x + ry * l2y + rz * l2z) +
+         (rx * qx + ry * qy + rz * qz) * (1.0f / 6.0f);
+  d[1] = l2x + 0.5f * qx;
+  d[2] = l2y + 0.5f * qy;
+  d[3] = l2z + 0.5f * qz;
+}
+
 template <bool MIXED>
 __global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs, double* __restrict__ phi,
                       double* __restrict__ g) {
@@ -826,6 +976,27 @@ __global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs, double* __
         az += Q[2 * kCells + loc];
       }
     }
+  } else if (MIXED && isleaf) {
+    const int32_t Pn = A.parent[s];
+    int a = loc >> 6, b = (loc >> 3) & 7, c = loc & 7;
+    int ga = A.ijk[3 * s] * 8 + a, gb = A.ijk[3 * s + 1] * 8 + b, gc = A.ijk[3 * s + 2] * 8 + c;
+    int pl = (((ga >> 1) - A.ijk[3 * Pn] * 8) * 8 + ((gb >> 1) - A.ijk[3 * Pn + 1] * 8)) * 8 +
+             ((gc >> 1) - A.ijk[3 * Pn + 2] * 8);
+    const int64_t ip = int64_t(Pn) * kCells + pl;
+    float P32[20], d[4];
+#pragma unroll
+    for (int k = 0; k < 20; ++k) P32[k] = A.loc32[k * N + ip];
+    const float h = float(cell_dx(lev));
+    // r = X_A - X_P = ((g & 1) - 1/2) dx_l - delta_P (a leaf's centre of mass is its centre)
+    const float rx = ((ga & 1) ? 0.5f : -0.5f) * h - A.mom32[N + ip];
+    const float ry = ((gb & 1) ? 0.5f : -0.5f) * h - A.mom32[2 * N + ip];
+    const float rz = ((gc & 1) ? 0.5f : -0.5f) * h - A.mom32[3 * N + ip];
+    shift_terms32(P32, rx, ry, rz, d);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) L[k] = (double(A.loc32[k * N + i]) + A.loc[k * N + ip]) + double(d[k]);
+    ax = A.ac[i] + A.ac[ip];
+    ay = A.ac[N + i] + A.ac[N + ip];
+    az = A.ac[2 * N + i] + A.ac[2 * N + ip];
   } else {
     for (int k = 0; k < nL; ++k) L[k] = MIXED ? double(A.loc32[k * N + i]) : A.loc[k * N + i];
     for (int k = nL; k < 20; ++k) L[k] = 0.0;
@@ -860,6 +1031,11 @@ __global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs, double* __
   } else {
 #pragma unroll
     for (int k = 0; k < 20; ++k) A.loc[k * N + i] = L[k];
+    if (MIXED) {
+      // FP32 copy of the total for the children's shift terms
+#pragma unroll
+      for (int k = 0; k < 20; ++k) A.loc32[k * N + i] = float(L[k]);
+    }
     A.ac[i] = ax;
     A.ac[N + i] = ay;
     A.ac[2 * N + i] = az;
@@ -905,7 +1081,10 @@ __global__ void __launch_bounds__(kReduceThreads)
     v[3] += y * fz - z * fy;
     v[4] += z * fx - x * fz;
     v[5] += x * fy - y * fx;
-    v[6] += sqrt(x * x + y * y + z * z) * sqrt(fx * fx + fy * fy + fz * fz);
+    // the normalisation S is a scale, formed in FP32 and summed in FP64
+    const float xf = float(x), yf = float(y), zf = float(z), gf = float(fx), hf = float(fy),
+                kf = float(fz);
+    v[6] += double(sqrtf(xf * xf + yf * yf + zf * zf) * sqrtf(gf * gf + hf * hf + kf * kf));
   }
   block_sum7(v, sh);
   if (threadIdx.x < 7) partials[int64_t(blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];
@@ -934,9 +1113,11 @@ struct StencilDev {
   float* d_ltab_k32 = nullptr;
   double* d_ltab_d64 = nullptr;    // [8][kLeafCap][4]
   float* d_ltab_d32 = nullptr;
-  int32_t* d_blocks = nullptr;     // general-kernel block list for this tree and theta
+  int32_t* d_blocks = nullptr;     // general-kernel blocks (one parity each) for this tree, theta
   int64_t n_blocks = 0;
+
   int n_stencil = 0, n_near = 0;
+  int ws_d2 = 0;
 };
 
 struct fmm_tree {
@@ -1050,6 +1231,7 @@ static int ensure_mixed(fmm_tree* t) {
   if (t->mixed_ready) return FMM_OK;
   const int64_t nc = t->h.n_sub * kCells;
   CUDA_TRY(dalloc(t, &t->d_mom32, sizeof(float) * kNMom * nc));
+  CUDA_TRY(cudaMemset(t->d_mom32, 0, sizeof(float) * kNMom * nc));  // leaf cells keep zeros
   CUDA_TRY(dalloc(t, &t->d_loc32, sizeof(float) * 20 * nc));
   CUDA_TRY(dalloc(t, &t->d_root_part32, sizeof(float) * kRootChunks * 20 * kCells));
   CUDA_TRY(dalloc(t, &t->d_root_part_ac, sizeof(double) * kRootChunks * 3 * kCells));
@@ -1066,7 +1248,7 @@ static int32_t block_code(uint32_t kind, uint32_t parity, uint32_t index) {
 // start early and the short ones fill the tail.
 static std::vector<int32_t> general_blocks(const HostTree& h, const Stencil& st,
                                            const std::vector<int32_t>& work,
-                                           const std::vector<int32_t>& work_bnd) {
+                                           const std::vector<int32_t>& work_bnd, bool whole) {
   const double c_rr = 230, c_rl = 140, c_lr = 150, c_pt = 20, c_iter = 4;
   // per target parity: how many (cell, offset) pairs land in each neighbour slot
   double st_slot[8][27] = {}, nr_slot[8][27] = {}, co_slot[8][8][27] = {};
@@ -1115,6 +1297,18 @@ static std::vector<int32_t> general_blocks(const HostTree& h, const Stencil& st,
       }
       items.push_back({cost, block_code(2, p, s)});
     }
+  }
+  if (whole) {
+    // merge the 8 parity items of each unit into one item (code with parity 0)
+    std::map<int32_t, double> unit;
+    std::vector<int32_t> order;
+    for (auto& it : items) {
+      int32_t key = it.second & ~int32_t(7 << 27);
+      if (!unit.count(key)) order.push_back(key);
+      unit[key] += it.first;
+    }
+    items.clear();
+    for (int32_t key : order) items.push_back({unit[key], key});
   }
   std::stable_sort(items.begin(), items.end(),
                    [](const std::pair<double, int32_t>& x, const std::pair<double, int32_t>& y) {
@@ -1172,11 +1366,20 @@ static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
     CUDA_TRY(upload(t, &sd.d_ltab_k32, lk32));
     CUDA_TRY(upload(t, &sd.d_ltab_d64, ld));
     CUDA_TRY(upload(t, &sd.d_ltab_d32, ld32));
-    std::vector<int32_t> blocks = general_blocks(t->h, st, t->work, t->work_bnd);
+    std::vector<int32_t> blocks = general_blocks(t->h, st, t->work, t->work_bnd, false);
     sd.n_blocks = int64_t(blocks.size());
     CUDA_TRY(upload(t, &sd.d_blocks, blocks));
+
     sd.n_stencil = n;
     sd.n_near = int(st.near.size());
+    // the opening test is monotone in |d|^2: find the largest |d|^2 that is not well separated
+    // (root cells are at most 7 apart per axis)
+    for (int d2 = 1; d2 <= 3 * 49; ++d2) {
+      bool ws = 1.0 / std::sqrt(double(d2)) < theta;
+      if (!ws) sd.ws_d2 = d2;
+    }
+    for (int d2 = sd.ws_d2 + 1; d2 <= 3 * 49; ++d2)
+      if (!(1.0 / std::sqrt(double(d2)) < theta)) return fail(FMM_ERR_THETA, "opening test not monotone");
     it = t->stencils.emplace(theta, sd).first;
   }
   *out = &it->second;
@@ -1200,6 +1403,7 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.near = sd ? sd->d_near : nullptr;
   A.n_stencil = sd ? sd->n_stencil : 0;
   A.n_near = sd ? sd->n_near : 0;
+  A.ws_d2 = sd ? sd->ws_d2 : 0;
   A.ltab_off = sd ? sd->d_ltab_off : nullptr;
   A.ltab_code = sd ? sd->d_ltab_code : nullptr;
   A.ltab_k64 = sd ? sd->d_ltab_k64 : nullptr;
@@ -1255,18 +1459,20 @@ static int solve_impl(fmm_tree* t, const double* rho, double theta, int precisio
   DevArgs A = make_args(t, sd);
   if ((rc = record(t, 0, st))) return rc;
   // upward pass
-  k_p2m<<<blocks_for(A.n_leaf_cells, 256), 256, 0, st>>>(A, rho);
+  k_p2m<<<blocks_for(A.n_leaf_cells, 256), 256, 0, st>>>(A, rho, mixed ? 1 : 0);
   CUDA_TRY(cudaGetLastError());
   for (int l = h.depth - 1; l >= 0; --l) {
     int64_t n = t->refined_off[l + 1] - t->refined_off[l];
     if (n == 0) continue;
-    k_m2m<<<blocks_for(n * kCells, 128), 128, 0, st>>>(A, t->d_refined + t->refined_off[l], int(n));
+    if (n * kCells >= kM2MCellMin)
+      k_m2m_cell<<<blocks_for(n * kCells, 128), 128, 0, st>>>(A, t->d_refined + t->refined_off[l],
+                                                              int(n), mixed ? 1 : 0);
+    else
+      k_m2m<<<unsigned(n * kCells * 8 / kM2MThreads), kM2MThreads, 0, st>>>(
+          A, t->d_refined + t->refined_off[l], mixed ? 1 : 0);
     CUDA_TRY(cudaGetLastError());
   }
-  if (mixed) {
-    k_to_fp32<<<1216, 256, 0, st>>>(t->d_mtl, t->d_mom32, int64_t(kNMom) * A.n_cell);
-    CUDA_TRY(cudaGetLastError());
-  }
+
   if ((rc = record(t, 1, st))) return rc;
   // interactions: leaf subgrids of levels >= 1 (same-level leaf partners), then the general
   // kernel: root chunks, every (refined subgrid, parity) and every (boundary leaf subgrid, parity)
@@ -1276,9 +1482,10 @@ static int solve_impl(fmm_tree* t, const double* rho, double theta, int precisio
     CUDA_TRY(cudaGetLastError());
   }
   if ((rc = record(t, 5, st))) return rc;
-  unsigned nb = unsigned(sd->n_blocks);
-  if (mixed) k_m2l_ref<float><<<nb, kM2LThreads, 0, st>>>(A, sd->d_blocks, theta, amc);
-  else k_m2l_ref<double><<<nb, kM2LThreads, 0, st>>>(A, sd->d_blocks, theta, amc);
+  if (mixed)
+    k_m2l_ref<float, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
+  else
+    k_m2l_ref<double, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
   CUDA_TRY(cudaGetLastError());
   if ((rc = record(t, 2, st))) return rc;
   // downward pass
@@ -1294,8 +1501,7 @@ static int solve_impl(fmm_tree* t, const double* rho, double theta, int precisio
   t->ev_recorded = t->profiling;
   int32_t n_m2m = 0;
   for (int l = 0; l < h.depth; ++l) n_m2m += (t->refined_off[l + 1] > t->refined_off[l]) ? 1 : 0;
-  t->launches = 1 + n_m2m + (mixed ? 1 : 0) + 1 + (t->n_work_leaf > 0 ? 1 : 0) + (h.depth + 1) +
-                 (net ? 2 : 0);
+  t->launches = 1 + n_m2m + 1 + (t->n_work_leaf > 0 ? 1 : 0) + (h.depth + 1) + (net ? 2 : 0);
   return FMM_OK;
 }
 
@@ -1331,7 +1537,10 @@ __global__ void __launch_bounds__(kReduceThreads)
     v[3] += py * fz - pz * fy;
     v[4] += pz * fx - px * fz;
     v[5] += px * fy - py * fx;
-    v[6] += sqrt(px * px + py * py + pz * pz) * sqrt(fx * fx + fy * fy + fz * fz);
+    // the normalisation S is a scale, formed in FP32 and summed in FP64 (as in k_net_partial)
+    const float xf = float(px), yf = float(py), zf = float(pz), gf = float(fx), hf = float(fy),
+                kf = float(fz);
+    v[6] += double(sqrtf(xf * xf + yf * yf + zf * zf) * sqrtf(gf * gf + hf * hf + kf * kf));
   }
   block_sum7(v, sh);
   if (threadIdx.x < 7) partials[int64_t(blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];

@@ -19,6 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
+NORM_TOL = 1e-6   # the normalisation S is formed from FP32 terms in both reductions
 
 
 def _tiny_amr():
@@ -58,7 +59,7 @@ def test_static_scratch_net_matches_workspace_net(which):
         assert rc == _lib.FMM_OK, _lib.lib().fmm_last_error()
         torch.cuda.synchronize()
         got = out.cpu().numpy()
-        assert abs(got[6] - ref[6]) <= FP64_TOL * ref[6]
+        assert abs(got[6] - ref[6]) <= NORM_TOL * ref[6]
         assert np.abs(got[:6] - ref[:6]).max() <= FP64_TOL * ref[6]
 
 
