@@ -64,8 +64,19 @@ typedef struct fmm_tree fmm_tree;
  * On success *out receives a new tree (destroy with fmm_destroy).  Host-only: needs no GPU. */
 int fmm_build_tree(int max_level, const uint8_t* refine_flags, int64_t n_flags, fmm_tree** out);
 
-/* Release a tree and its device workspace.  NULL is ignored. */
+/* Release a tree (or forest) and its device workspace.  NULL is ignored. */
 void fmm_destroy(fmm_tree* tree);
+
+/* A forest: the disjoint union of n independent trees (or forests), solved by one set of
+ * launches -- every level of every tree at once, however uneven their depths.  The parts are
+ * copied; they stay valid and independent.  In every per-cell array of a forest the trees' leaf
+ * cells follow each other in part order, each tree's in its own canonical order; net sums are
+ * per tree (7 doubles each, tree order).  Host-only: needs no GPU. */
+int fmm_build_forest(const fmm_tree* const* trees, int n, fmm_tree** out);
+
+/* Number of trees (1 for a tree built by fmm_build_tree) and, if leaf_subgrid_offsets is not
+ * NULL, n_trees + 1 offsets: tree k's leaf cells are [512 offsets[k], 512 offsets[k+1]). */
+int fmm_forest_info(const fmm_tree* tree, int32_t* n_trees, int64_t* leaf_subgrid_offsets);
 
 /* Sizes: total subgrids, leaf subgrids (leaf cells = 512 * n_leaf_subgrids), deepest level.
  * Any output pointer may be NULL. */
@@ -104,9 +115,18 @@ int fmm_interaction_counts_by_type(const fmm_tree* tree, double theta, int64_t c
  *   (F_x, F_y, F_z, T_x, T_y, T_z, S) with F = sum m g, T = sum x cross m g, S = sum |x| |m g|,
  *   reduced in FP64 in a fixed order (the terms of the normalisation S are formed in FP32).
  * theta in [0.34, 1).  precision FMM_FP64 or FMM_MIXED.  stream: a cudaStream_t (NULL = legacy
- * default stream).  Asynchronous: returns once the work is enqueued. */
+ * default stream).  Asynchronous: returns once the work is enqueued.  On a forest, net_dev holds
+ * 7 doubles per tree. */
 int fmm_solve(fmm_tree* tree, const double* rho_dev, double theta, int precision, int amc,
               double* phi_dev, double* g_dev, double* net_dev, void* stream);
+
+/* fmm_solve on a forest with one device buffer per tree: rho_dev[k], phi_dev[k], g_dev[k] are
+ * tree k's arrays (its own canonical order).  They are copied into and out of the forest's own
+ * concatenated buffers on `stream` around one fmm_solve; net_dev (optional) gets 7 doubles per
+ * tree.  Asynchronous. */
+int fmm_solve_batch(fmm_tree* forest, const double* const* rho_dev, double theta, int precision,
+                    int amc, double* const* phi_dev, double* const* g_dev, double* net_dev,
+                    void* stream);
 
 /* Waits for `stream`, then returns FMM_OK, or FMM_ERR_NONFINITE if a solve since the last call
  * met an invalid density, or FMM_ERR_CUDA; clears the recorded status. */

@@ -20,7 +20,7 @@ FMM_FP64 = 0
 FMM_MIXED = 1
 
 EXPORTS = [
-    "fmm_build_tree", "fmm_destroy", "fmm_tree_info", "fmm_tree_subgrids", "fmm_stencil",
+    "fmm_build_tree", "fmm_destroy", "fmm_build_forest", "fmm_forest_info", "fmm_solve_batch", "fmm_tree_info", "fmm_tree_subgrids", "fmm_stencil",
     "fmm_interaction_counts", "fmm_interaction_counts_by_type", "fmm_last_launches", "fmm_solve", "fmm_sync_status", "fmm_solve_host",
     "fmm_net_force_torque", "fmm_net_force_torque_points_static", "fmm_set_profiling", "fmm_phase_times", "fmm_last_error",
 ]
@@ -47,6 +47,9 @@ def lib():
         sig = {
             "fmm_build_tree": (i32, [i32, vp, i64, C.POINTER(vp)]),
             "fmm_destroy": (None, [vp]),
+            "fmm_build_forest": (i32, [vp, i32, C.POINTER(vp)]),
+            "fmm_forest_info": (i32, [vp, vp, vp]),
+            "fmm_solve_batch": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
             "fmm_tree_info": (i32, [vp, vp, vp, vp]),
             "fmm_tree_subgrids": (i32, [vp, vp]),
             "fmm_stencil": (i32, [dbl, i32, vp, i32, vp]),

@@ -52,6 +52,14 @@ class Tree:
         except Exception:
             pass
 
+    def forest_info(self) -> Tuple[int, np.ndarray]:
+        """(number of trees, leaf-subgrid offsets [n_trees + 1])."""
+        n = C.c_int32()
+        check(lib().fmm_forest_info(self._h, C.byref(n), None))
+        off = np.zeros(n.value + 1, dtype=np.int64)
+        check(lib().fmm_forest_info(self._h, C.byref(n), _p(off)))
+        return n.value, off
+
     def info(self) -> Tuple[int, int, int]:
         ns, nl, d = C.c_int64(), C.c_int64(), C.c_int32()
         check(lib().fmm_tree_info(self._h, C.byref(ns), C.byref(nl), C.byref(d)))
@@ -98,7 +106,7 @@ class Tree:
         if g is None:
             g = torch.empty((n, 3), dtype=torch.float64, device=rho.device)
         if net is None:
-            net = torch.empty(7, dtype=torch.float64, device=rho.device)
+            net = torch.empty(7 * self.forest_info()[0], dtype=torch.float64, device=rho.device)
         sh = _stream_handle(stream)
         check(lib().fmm_solve(self._h, rho.data_ptr(), float(theta), PRECISIONS[precision],
                               int(bool(amc)), phi.data_ptr(), g.data_ptr(),
@@ -119,7 +127,7 @@ class Tree:
         assert rho.size == n
         phi = np.empty(n) if phi is None else phi
         g = np.empty((n, 3)) if g is None else g
-        net = np.empty(7) if net is None else net
+        net = np.empty(7 * self.forest_info()[0]) if net is None else net
         check(lib().fmm_solve_host(self._h, _p(rho), float(theta), PRECISIONS[precision],
                                    int(bool(amc)), _p(phi), _p(g), _p(net),
                                    _stream_handle(stream)))
@@ -127,7 +135,7 @@ class Tree:
 
     def net_force_torque(self, rho, g, stream=None):
         import torch
-        net = torch.empty(7, dtype=torch.float64, device=rho.device)
+        net = torch.empty(7 * self.forest_info()[0], dtype=torch.float64, device=rho.device)
         sh = _stream_handle(stream)
         check(lib().fmm_net_force_torque(self._h, rho.data_ptr(), g.data_ptr(), net.data_ptr(), sh))
         check(lib().fmm_sync_status(self._h, sh))
@@ -142,3 +150,35 @@ class Tree:
         out = np.zeros(6, dtype=np.float32)
         check(lib().fmm_phase_times(self._h, _p(out), 6))
         return out
+
+
+class Forest(Tree):
+    """Independent trees solved together (fmm_build_forest): per-cell arrays are the trees'
+    arrays back to back, net sums 7 per tree."""
+
+    def __init__(self, trees):
+        arr = (C.c_void_p * len(trees))(*[t._h for t in trees])
+        h = C.c_void_p()
+        check(lib().fmm_build_forest(arr, len(trees), C.byref(h)))
+        self._h = h
+
+    def solve_batch(self, rhos, theta: float, precision: str = "fp64", amc: bool = True,
+                    phis=None, gs=None, net=None, stream=None, check_status: bool = True):
+        """One device buffer per tree (fmm_solve_batch)."""
+        import torch
+        n, off = self.forest_info()
+        sizes = (off[1:] - off[:-1]) * 512
+        dev = rhos[0].device
+        phis = phis or [torch.empty(int(m), dtype=torch.float64, device=dev) for m in sizes]
+        gs = gs or [torch.empty((int(m), 3), dtype=torch.float64, device=dev) for m in sizes]
+        if net is None:
+            net = torch.empty(7 * n, dtype=torch.float64, device=dev)
+        P = C.c_void_p * n
+        sh = _stream_handle(stream)
+        check(lib().fmm_solve_batch(self._h, P(*[r.data_ptr() for r in rhos]), float(theta),
+                                    PRECISIONS[precision], int(bool(amc)),
+                                    P(*[p.data_ptr() for p in phis]), P(*[x.data_ptr() for x in gs]),
+                                    net.data_ptr(), sh))
+        if check_status:
+            check(lib().fmm_sync_status(self._h, sh))
+        return phis, gs, net

@@ -58,6 +58,8 @@ struct DevArgs {
   int64_t n_cell;          // n_sub * 512
   int64_t n_leaf_cells;
   int depth;
+  int n_roots;             // trees in the forest; their roots are subgrids 0 .. n_roots-1
+  const int64_t* tree_leaf_off;  // [n_roots + 1] first leaf-subgrid ordinal of each tree
   const int32_t* level;    // [n_sub]
   const int32_t* ijk;      // [3 n_sub]
   const uint8_t* leaf;     // [n_sub]
@@ -83,9 +85,9 @@ struct DevArgs {
   double* loc;             // [20][n_cell] own, then total expansion
   float* loc32;            // [20][n_cell] own expansion (mixed path)
   double* ac;              // [3][n_cell] correction acceleration, own then total
-  double* root_part;       // [kRootChunks][23][512] root partial sums (FP64 path)
-  float* root_part32;      // [kRootChunks][20][512] (mixed path)
-  double* root_part_ac;    // [kRootChunks][3][512] (mixed path)
+  double* root_part;       // [n_roots][kRootChunks][23][512] root partial sums (FP64 path)
+  float* root_part32;      // [n_roots][kRootChunks][20][512] (mixed path)
+  double* root_part_ac;    // [n_roots][kRootChunks][3][512] (mixed path)
   int* status;
 };
 
@@ -626,16 +628,17 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool a
 // when the root is a leaf, every other root cell interacts directly.  Sources are split into
 // kRootChunks chunks whose partial sums are added in a fixed order by the downward pass.
 template <typename T, bool AREF>
-__device__ void m2l_root(const DevArgs& A, int parity, int t, int chunk, bool amc) {
+__device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chunk, bool amc) {
   const T* __restrict__ M = MomView<T>::get(A);
   const int64_t N = A.n_cell;
   int a, b, c;
   block_cell(parity, t, a, b, c);
   const int iloc = (a * 8 + b) * 8 + c;
+  const int64_t base = int64_t(root) * kCells;
   Target<T, AREF> S;
-  load_target<T, AREF>(S, A, M, iloc, amc);
+  load_target<T, AREF>(S, A, M, base + iloc, amc);
   const T h = T(cell_dx(0));
-  const bool root_leaf = A.leaf[0] != 0;
+  const bool root_leaf = A.leaf[root] != 0;
   // chunk = source x index; source offsets kept as floating-point counters (no conversions)
   const int dx = chunk - a;
   const T rx0 = S.dAx - T(dx) * h;
@@ -648,7 +651,7 @@ __device__ void m2l_root(const DevArgs& A, int parity, int t, int chunk, bool am
       const int dy = jy - b, dz = jz - c;
       const bool ws = dx * dx + dy * dy + dz * dz > A.ws_d2;
       if (!ws && !root_leaf) continue;
-      interact<T, AREF>(S, M, N, j, !root_leaf, rx0, ry, rz);
+      interact<T, AREF>(S, M, N, base + j, !root_leaf, rx0, ry, rz);
     }
     if (jy & 1) flush(S);
   }
@@ -656,17 +659,17 @@ __device__ void m2l_root(const DevArgs& A, int parity, int t, int chunk, bool am
   // partials: [chunk][component][cell]
   if constexpr (AREF) complete_traceless(S.L);
   if (sizeof(T) == 8) {
-    double* P = A.root_part + int64_t(chunk) * 23 * kCells;
+    double* P = A.root_part + (int64_t(root) * kRootChunks + chunk) * 23 * kCells;
     for (int k = 0; k < (AREF ? 20 : 4); ++k) P[k * kCells + iloc] = double(S.L[k]);
     for (int k = (AREF ? 20 : 4); k < 20; ++k) P[k * kCells + iloc] = 0.0;
     P[20 * kCells + iloc] = S.ax;
     P[21 * kCells + iloc] = S.ay;
     P[22 * kCells + iloc] = S.az;
   } else {
-    float* P = A.root_part32 + int64_t(chunk) * 20 * kCells;
+    float* P = A.root_part32 + (int64_t(root) * kRootChunks + chunk) * 20 * kCells;
     for (int k = 0; k < (AREF ? 20 : 4); ++k) P[k * kCells + iloc] = float(S.L[k]);
     for (int k = (AREF ? 20 : 4); k < 20; ++k) P[k * kCells + iloc] = 0.0f;
-    double* Q = A.root_part_ac + int64_t(chunk) * 3 * kCells;
+    double* Q = A.root_part_ac + (int64_t(root) * kRootChunks + chunk) * 3 * kCells;
     Q[iloc] = S.ax;
     Q[kCells + iloc] = S.ay;
     Q[2 * kCells + iloc] = S.az;
@@ -766,8 +769,8 @@ __device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, int t, boo
 }
 
 // One block per entry of `blocks`, sorted by estimated cost (largest first): code
-// (kind << 30) | (parity << 27) | index, kind 0 = root source chunk `index`, 1 = refined subgrid
-// `index`, 2 = leaf subgrid `index` at a refinement boundary.  With NT = 64 a block serves the 64
+// (kind << 30) | (parity << 27) | index, kind 0 = source chunk index & 7 of root index >> 3,
+// 1 = refined subgrid `index`, 2 = leaf subgrid `index` at a refinement boundary.  With NT = 64 a block serves the 64
 // cells of one parity; with NT = 512 it serves all 8 parities of the subgrid (or all 512 root
 // cells), so that every source the subgrid's cells read is fetched into one SM's L1 once.
 template <typename T, int NT>
@@ -778,8 +781,9 @@ __global__ void __launch_bounds__(NT) k_m2l_ref(DevArgs A, const int32_t* __rest
   const int parity = NT == 64 ? (code >> 27) & 7 : int(threadIdx.x >> 6);
   const int t = int(threadIdx.x & 63);
   if (kind == 0) {
-    if (A.leaf[0]) m2l_root<T, false>(A, parity, t, idx, amc != 0);
-    else m2l_root<T, true>(A, parity, t, idx, amc != 0);
+    const int root = idx >> 3, chunk = idx & 7;
+    if (A.leaf[root]) m2l_root<T, false>(A, root, parity, t, chunk, amc != 0);
+    else m2l_root<T, true>(A, root, parity, t, chunk, amc != 0);
   } else if (kind == 1) {
     m2l_level<T, true>(A, idx, parity, t, amc != 0);
   } else {
@@ -961,16 +965,17 @@ __global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs, double* __
     ax = ay = az = 0.0;
     for (int k = 0; k < 20; ++k) L[k] = 0.0;
     for (int ch = 0; ch < kRootChunks; ++ch) {
+      const int64_t pc = int64_t(s) * kRootChunks + ch;  // at level 0, s is the root's tree
       if (!MIXED) {
-        const double* P = A.root_part + int64_t(ch) * 23 * kCells;
+        const double* P = A.root_part + pc * 23 * kCells;
         for (int k = 0; k < nL; ++k) L[k] += P[k * kCells + loc];
         ax += P[20 * kCells + loc];
         ay += P[21 * kCells + loc];
         az += P[22 * kCells + loc];
       } else {
-        const float* P = A.root_part32 + int64_t(ch) * 20 * kCells;
+        const float* P = A.root_part32 + pc * 20 * kCells;
         for (int k = 0; k < nL; ++k) L[k] += double(P[k * kCells + loc]);
-        const double* Q = A.root_part_ac + int64_t(ch) * 3 * kCells;
+        const double* Q = A.root_part_ac + pc * 3 * kCells;
         ax += Q[loc];
         ay += Q[kCells + loc];
         az += Q[2 * kCells + loc];
@@ -1058,14 +1063,17 @@ __device__ __forceinline__ void block_sum7(double* v, double (*sh)[kReduceThread
   }
 }
 
+// blockIdx.y = tree; its leaf cells are reduced by gridDim.x blocks in a fixed order.
 __global__ void __launch_bounds__(kReduceThreads)
     k_net_partial(DevArgs A, const double* __restrict__ rho, const double* __restrict__ g,
                   double* __restrict__ partials) {
   __shared__ double sh[7][kReduceThreads];
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
   const int64_t stride = int64_t(gridDim.x) * kReduceThreads;
-  for (int64_t i = int64_t(blockIdx.x) * kReduceThreads + threadIdx.x; i < A.n_leaf_cells;
-       i += stride) {
+  const int64_t end = A.tree_leaf_off[blockIdx.y + 1] * kCells;
+  for (int64_t i = A.tree_leaf_off[blockIdx.y] * kCells + int64_t(blockIdx.x) * kReduceThreads +
+                   threadIdx.x;
+       i < end; i += stride) {
     int32_t s = A.leaf_sub[i >> 9];
     int lev = A.level[s];
     int loc = int(i & 511);
@@ -1087,18 +1095,21 @@ __global__ void __launch_bounds__(kReduceThreads)
     v[6] += double(sqrtf(xf * xf + yf * yf + zf * zf) * sqrtf(gf * gf + hf * hf + kf * kf));
   }
   block_sum7(v, sh);
-  if (threadIdx.x < 7) partials[int64_t(blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x < 7)
+    partials[(int64_t(blockIdx.y) * gridDim.x + blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// blockIdx.x = tree (or set of partials): sums n_blocks partials in a fixed order into out[7 x].
 __global__ void __launch_bounds__(kReduceThreads)
     k_net_final(const double* __restrict__ partials, int n_blocks, double* __restrict__ out) {
   __shared__ double sh[7][kReduceThreads];
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  const double* P = partials + int64_t(blockIdx.x) * n_blocks * 7;
   for (int b = threadIdx.x; b < n_blocks; b += kReduceThreads)
 #pragma unroll
-    for (int k = 0; k < 7; ++k) v[k] += partials[int64_t(b) * 7 + k];
+    for (int k = 0; k < 7; ++k) v[k] += P[int64_t(b) * 7 + k];
   block_sum7(v, sh);
-  if (threadIdx.x < 7) out[threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x < 7) out[int64_t(blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -1135,6 +1146,7 @@ struct fmm_tree {
          *d_root_part_ac = nullptr, *d_partials = nullptr;
   float *d_mom32 = nullptr, *d_loc32 = nullptr, *d_root_part32 = nullptr;
   int* d_status = nullptr;
+  int64_t* d_tree_leaf_off = nullptr;
   double *d_rho = nullptr, *d_phi = nullptr, *d_g = nullptr, *d_net = nullptr;
   std::map<double, StencilDev> stencils;
   bool profiling = false;
@@ -1144,6 +1156,12 @@ struct fmm_tree {
   std::vector<void*> allocs;
   std::vector<int32_t> work, work_bnd;  // refined and boundary leaf subgrids of levels >= 1
 };
+
+// blocks per tree of the net reduction: about 512 in all
+static inline int net_blocks(int64_t n_trees) {
+  int64_t b = kReduceBlocks / (n_trees > 0 ? n_trees : 1);
+  return int(b < 8 ? 8 : b);
+}
 
 template <typename P>
 static cudaError_t dalloc(fmm_tree* t, P** p, size_t bytes) {
@@ -1219,8 +1237,10 @@ static int ensure_device(fmm_tree* t) {
   CUDA_TRY(cudaMemset(t->d_mtl, 0, sizeof(double) * kNMom * nc));
   CUDA_TRY(dalloc(t, &t->d_loc, sizeof(double) * 20 * nc));
   CUDA_TRY(dalloc(t, &t->d_ac, sizeof(double) * 3 * nc));
-  CUDA_TRY(dalloc(t, &t->d_root_part, sizeof(double) * kRootChunks * 23 * kCells));
-  CUDA_TRY(dalloc(t, &t->d_partials, sizeof(double) * 7 * kReduceBlocks));
+  const int64_t nr = h.n_trees;
+  CUDA_TRY(dalloc(t, &t->d_root_part, sizeof(double) * nr * kRootChunks * 23 * kCells));
+  CUDA_TRY(dalloc(t, &t->d_partials, sizeof(double) * 7 * net_blocks(nr) * nr));
+  CUDA_TRY(upload(t, &t->d_tree_leaf_off, h.tree_leaf_off));
   CUDA_TRY(dalloc(t, &t->d_status, sizeof(int)));
   CUDA_TRY(cudaMemset(t->d_status, 0, sizeof(int)));
   t->dev_ready = true;
@@ -1233,8 +1253,9 @@ static int ensure_mixed(fmm_tree* t) {
   CUDA_TRY(dalloc(t, &t->d_mom32, sizeof(float) * kNMom * nc));
   CUDA_TRY(cudaMemset(t->d_mom32, 0, sizeof(float) * kNMom * nc));  // leaf cells keep zeros
   CUDA_TRY(dalloc(t, &t->d_loc32, sizeof(float) * 20 * nc));
-  CUDA_TRY(dalloc(t, &t->d_root_part32, sizeof(float) * kRootChunks * 20 * kCells));
-  CUDA_TRY(dalloc(t, &t->d_root_part_ac, sizeof(double) * kRootChunks * 3 * kCells));
+  const int64_t nr = t->h.n_trees;
+  CUDA_TRY(dalloc(t, &t->d_root_part32, sizeof(float) * nr * kRootChunks * 20 * kCells));
+  CUDA_TRY(dalloc(t, &t->d_root_part_ac, sizeof(double) * nr * kRootChunks * 3 * kCells));
   t->mixed_ready = true;
   return FMM_OK;
 }
@@ -1272,9 +1293,11 @@ static std::vector<int32_t> general_blocks(const HostTree& h, const Stencil& st,
     }
   }
   std::vector<std::pair<double, int32_t>> items;
-  const double root_cost = 64.0 * 64.0 * (h.leaf[0] ? c_pt : c_rr);
-  for (int ch = 0; ch < kRootChunks; ++ch)
-    for (int p = 0; p < 8; ++p) items.push_back({root_cost, block_code(0, p, ch)});
+  for (int r = 0; r < h.n_trees; ++r) {
+    const double root_cost = 64.0 * 64.0 * (h.leaf[r] ? c_pt : c_rr);
+    for (int ch = 0; ch < kRootChunks; ++ch)
+      for (int p = 0; p < 8; ++p) items.push_back({root_cost, block_code(0, p, uint32_t(r * 8 + ch))});
+  }
   for (int32_t s : work)
     for (int p = 0; p < 8; ++p) {
       double cost = c_iter * 64 * double(st.offs[p].size());
@@ -1391,6 +1414,8 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.n_cell = t->h.n_sub * kCells;
   A.n_leaf_cells = t->h.n_leaf_sub * kCells;
   A.depth = t->h.depth;
+  A.n_roots = t->h.n_trees;
+  A.tree_leaf_off = t->d_tree_leaf_off;
   A.level = t->d_level;
   A.ijk = t->d_ijk;
   A.leaf = t->d_leaf;
@@ -1436,9 +1461,11 @@ static int record(fmm_tree* t, int k, cudaStream_t st) {
 
 static int launch_net(fmm_tree* t, const DevArgs& A, const double* rho, const double* g,
                       double* net, cudaStream_t st) {
-  k_net_partial<<<kReduceBlocks, kReduceThreads, 0, st>>>(A, rho, g, t->d_partials);
+  const int nb = net_blocks(t->h.n_trees);
+  k_net_partial<<<dim3(unsigned(nb), unsigned(t->h.n_trees)), kReduceThreads, 0, st>>>(
+      A, rho, g, t->d_partials);
   CUDA_TRY(cudaGetLastError());
-  k_net_final<<<1, kReduceThreads, 0, st>>>(t->d_partials, kReduceBlocks, net);
+  k_net_final<<<unsigned(t->h.n_trees), kReduceThreads, 0, st>>>(t->d_partials, nb, net);
   CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }
@@ -1599,6 +1626,33 @@ void fmm_destroy(fmm_tree* t) {
   delete t;
 }
 
+int fmm_build_forest(const fmm_tree* const* trees, int n, fmm_tree** out) {
+  if (!out || !trees || n <= 0) return fail(FMM_ERR_ARG, "bad argument");
+  *out = nullptr;
+  try {
+    std::vector<const HostTree*> parts;
+    for (int k = 0; k < n; ++k) {
+      if (!trees[k]) return fail(FMM_ERR_ARG, "null tree");
+      parts.push_back(&trees[k]->h);
+    }
+    std::unique_ptr<fmm_tree> f(new fmm_tree());
+    std::string err = merge_trees(parts, f->h);
+    if (!err.empty()) return fail(FMM_ERR_ARG, err);
+    *out = f.release();
+    return FMM_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+int fmm_forest_info(const fmm_tree* t, int32_t* n_trees, int64_t* leaf_subgrid_offsets) {
+  if (!t) return fail(FMM_ERR_ARG, "tree is null");
+  if (n_trees) *n_trees = t->h.n_trees;
+  if (leaf_subgrid_offsets)
+    for (int k = 0; k <= t->h.n_trees; ++k) leaf_subgrid_offsets[k] = t->h.tree_leaf_off[k];
+  return FMM_OK;
+}
+
 int fmm_tree_info(const fmm_tree* t, int64_t* n_subgrids, int64_t* n_leaf_subgrids, int32_t* depth) {
   if (!t) return fail(FMM_ERR_ARG, "tree is null");
   if (n_subgrids) *n_subgrids = t->h.n_sub;
@@ -1667,6 +1721,36 @@ int fmm_solve(fmm_tree* t, const double* rho_dev, double theta, int precision, i
   }
 }
 
+int fmm_solve_batch(fmm_tree* f, const double* const* rho_dev, double theta, int precision,
+                    int amc, double* const* phi_dev, double* const* g_dev, double* net_dev,
+                    void* stream) {
+  if (!f || !rho_dev || !phi_dev || !g_dev) return fail(FMM_ERR_ARG, "null argument");
+  int rc = ensure_device(f);
+  if (rc) return rc;
+  const int n = f->h.n_trees;
+  const int64_t total = f->h.n_leaf_sub * kCells;
+  if (!f->d_rho) {
+    CUDA_TRY(dalloc(f, &f->d_rho, sizeof(double) * total));
+    CUDA_TRY(dalloc(f, &f->d_phi, sizeof(double) * total));
+    CUDA_TRY(dalloc(f, &f->d_g, sizeof(double) * 3 * total));
+    CUDA_TRY(dalloc(f, &f->d_net, sizeof(double) * 7 * n));
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int k = 0; k < n; ++k) {
+    if (!rho_dev[k] || !phi_dev[k] || !g_dev[k]) return fail(FMM_ERR_ARG, "null per-tree pointer");
+    const int64_t o = f->h.tree_leaf_off[k] * kCells, m = (f->h.tree_leaf_off[k + 1] - f->h.tree_leaf_off[k]) * kCells;
+    CUDA_TRY(cudaMemcpyAsync(f->d_rho + o, rho_dev[k], sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+  }
+  rc = fmm_solve(f, f->d_rho, theta, precision, amc, f->d_phi, f->d_g, net_dev, stream);
+  if (rc) return rc;
+  for (int k = 0; k < n; ++k) {
+    const int64_t o = f->h.tree_leaf_off[k] * kCells, m = (f->h.tree_leaf_off[k + 1] - f->h.tree_leaf_off[k]) * kCells;
+    CUDA_TRY(cudaMemcpyAsync(phi_dev[k], f->d_phi + o, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(g_dev[k], f->d_g + 3 * o, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice, st));
+  }
+  return FMM_OK;
+}
+
 int fmm_sync_status(fmm_tree* t, void* stream) {
   if (!t) return fail(FMM_ERR_ARG, "tree is null");
   if (!t->dev_ready) return FMM_OK;
@@ -1689,7 +1773,7 @@ int fmm_solve_host(fmm_tree* t, const double* rho_host, double theta, int precis
     CUDA_TRY(dalloc(t, &t->d_rho, sizeof(double) * n));
     CUDA_TRY(dalloc(t, &t->d_phi, sizeof(double) * n));
     CUDA_TRY(dalloc(t, &t->d_g, sizeof(double) * 3 * n));
-    CUDA_TRY(dalloc(t, &t->d_net, sizeof(double) * 7));
+    CUDA_TRY(dalloc(t, &t->d_net, sizeof(double) * 7 * t->h.n_trees));
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CUDA_TRY(cudaMemcpyAsync(t->d_rho, rho_host, sizeof(double) * n, cudaMemcpyHostToDevice, st));
@@ -1699,7 +1783,8 @@ int fmm_solve_host(fmm_tree* t, const double* rho_host, double theta, int precis
   CUDA_TRY(cudaMemcpyAsync(phi_host, t->d_phi, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaMemcpyAsync(g_host, t->d_g, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
   if (net_host)
-    CUDA_TRY(cudaMemcpyAsync(net_host, t->d_net, sizeof(double) * 7, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(net_host, t->d_net, sizeof(double) * 7 * t->h.n_trees,
+                             cudaMemcpyDeviceToHost, st));
   return fmm_sync_status(t, stream);
 }
 

@@ -183,6 +183,77 @@ std::string build_host_tree(int max_level, const uint8_t* flags, int64_t n_flags
     }
   }
   t.n_leaf_sub = int64_t(t.leaf_sub.size());
+  t.n_trees = 1;
+  t.tree_leaf_off = {0, t.n_leaf_sub};
+  return "";
+}
+
+std::string merge_trees(const std::vector<const HostTree*>& parts, HostTree& out) {
+  if (parts.empty()) return "no trees";
+  HostTree f;
+  f.depth = 0;
+  f.n_trees = 0;
+  for (const HostTree* p : parts) {
+    f.depth = std::max(f.depth, p->depth);
+    f.n_trees += p->n_trees;
+  }
+  // new index of every part's subgrids: level-major, part order within a level
+  std::vector<std::vector<int32_t>> remap(parts.size());
+  f.lev_off.assign(f.depth + 2, 0);
+  int64_t next = 0;
+  for (int l = 0; l <= f.depth; ++l) {
+    f.lev_off[l] = next;
+    for (size_t q = 0; q < parts.size(); ++q) {
+      const HostTree* p = parts[q];
+      if (remap[q].empty()) remap[q].assign(p->n_sub, -1);
+      if (l > p->depth) continue;
+      for (int64_t s = p->lev_off[l]; s < p->lev_off[l + 1]; ++s) remap[q][s] = int32_t(next++);
+    }
+  }
+  f.lev_off[f.depth + 1] = next;
+  f.n_sub = next;
+  if (f.n_sub >= (int64_t(1) << 27)) return "forest too large";
+  f.level.assign(f.n_sub, 0);
+  f.ijk.assign(3 * f.n_sub, 0);
+  f.leaf.assign(f.n_sub, 0);
+  f.parent.assign(f.n_sub, -1);
+  f.child.assign(8 * f.n_sub, -1);
+  f.nbr.assign(27 * f.n_sub, -1);
+  f.leaf_ord.assign(f.n_sub, -1);
+  f.refined_at.assign(f.depth + 1, {});
+  f.leaves_at.assign(f.depth + 1, {});
+  auto map = [](const std::vector<int32_t>& m, int32_t s) { return s < 0 ? -1 : m[s]; };
+  for (size_t q = 0; q < parts.size(); ++q) {
+    const HostTree* p = parts[q];
+    for (int64_t s = 0; s < p->n_sub; ++s) {
+      int32_t n = remap[q][s];
+      f.level[n] = p->level[s];
+      for (int k = 0; k < 3; ++k) f.ijk[3 * n + k] = p->ijk[3 * s + k];
+      f.leaf[n] = p->leaf[s];
+      f.parent[n] = map(remap[q], p->parent[s]);
+      for (int k = 0; k < 8; ++k) f.child[8 * n + k] = map(remap[q], p->child[8 * s + k]);
+      for (int k = 0; k < 27; ++k) f.nbr[27 * n + k] = map(remap[q], p->nbr[27 * s + k]);
+    }
+  }
+  // leaves tree-major, each part's leaves in its own order
+  f.tree_leaf_off.assign(1, 0);
+  for (size_t q = 0; q < parts.size(); ++q) {
+    const HostTree* p = parts[q];
+    for (int k = 0; k < p->n_trees; ++k) {
+      for (int64_t o = p->tree_leaf_off[k]; o < p->tree_leaf_off[k + 1]; ++o) {
+        int32_t n = remap[q][p->leaf_sub[o]];
+        f.leaf_ord[n] = int32_t(f.leaf_sub.size());
+        f.leaf_sub.push_back(n);
+      }
+      f.tree_leaf_off.push_back(int64_t(f.leaf_sub.size()));
+    }
+  }
+  f.n_leaf_sub = int64_t(f.leaf_sub.size());
+  for (int64_t s = 0; s < f.n_sub; ++s) {
+    if (f.leaf[s]) f.leaves_at[f.level[s]].push_back(int32_t(s));
+    else f.refined_at[f.level[s]].push_back(int32_t(s));
+  }
+  out = std::move(f);
   return "";
 }
 
@@ -236,13 +307,15 @@ void interaction_counts_by_type(const HostTree& t, const Stencil& st, int64_t ou
         root_near++;
     }
   for (int k = 0; k < 6; ++k) out[k] = 0;
-  if (t.leaf[0]) {
-    out[0] += root_ws;
-    out[4] += root_near;
-  } else {
-    out[3] += root_ws;
+  for (int64_t s = 0; s < t.lev_off[1]; ++s) {  // the roots: every well-separated pair
+    if (t.leaf[s]) {
+      out[0] += root_ws;
+      out[4] += root_near;
+    } else {
+      out[3] += root_ws;
+    }
   }
-  for (int64_t s = 1; s < t.n_sub; ++s)
+  for (int64_t s = t.lev_off[1]; s < t.n_sub; ++s)
     for (int slot = 0; slot < 27; ++slot) {
       int32_t nb = t.nbr[27 * s + slot];
       if (nb < 0) continue;

@@ -19,8 +19,13 @@ constexpr int kMaxLevel = 9;   // deepest level accepted
 constexpr int kMaxReach = 5;   // stencil reach in cells for theta >= 0.34
 constexpr double kThetaMin = 0.34;
 
+// A tree, or a forest of independent trees: subgrids are numbered level-major across the trees
+// (tree order within a level), so the roots of the n_trees trees are subgrids 0 .. n_trees-1; leaf
+// subgrids are ordered tree-major, each tree's in its own canonical (level, Morton) order.
 struct HostTree {
   int depth = 0;                       // deepest level that has subgrids
+  int n_trees = 1;
+  std::vector<int64_t> tree_leaf_off;  // [n_trees + 1]: first leaf-subgrid ordinal of each tree
   int64_t n_sub = 0, n_leaf_sub = 0;
   std::vector<int64_t> lev_off;        // [depth + 2]: first global subgrid index of each level
   std::vector<int32_t> level;          // [n_sub]
@@ -37,6 +42,8 @@ struct HostTree {
 
 // Returns an empty string on success, otherwise an error message.
 std::string build_host_tree(int max_level, const uint8_t* flags, int64_t n_flags, HostTree& t);
+// Disjoint union of trees (each may itself be a forest).
+std::string merge_trees(const std::vector<const HostTree*>& parts, HostTree& out);
 
 struct Stencil {
   double theta = 0;

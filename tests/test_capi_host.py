@@ -117,3 +117,26 @@ def test_argument_errors():
     assert _lib.lib().fmm_solve(t._h, C.c_void_p(16), 0.2, 0, 1, C.c_void_p(16), C.c_void_p(16),
                                 None, None) == _lib.FMM_ERR_THETA
     assert b"theta" in _lib.lib().fmm_last_error()
+
+
+def test_forest_is_the_disjoint_union():
+    trees = [api.Tree(2, synth.uniform_flags(2)), api.Tree(0, np.zeros(0, np.uint8))]
+    w = synth.workload_binary(3, axis=(1.0, 0.6, 0.3), offset=(0.02, -0.03, 0.05))
+    trees.append(api.Tree(w.max_level, w.flags))
+    f = api.Forest(trees)
+    n, off = f.forest_info()
+    assert n == 3
+    sizes = [t.info() for t in trees]
+    assert list(np.diff(off)) == [s[1] for s in sizes]
+    ns, nl, depth = f.info()
+    assert ns == sum(s[0] for s in sizes) and nl == sum(s[1] for s in sizes)
+    assert depth == max(s[2] for s in sizes)
+    for th in (0.5, 0.35):
+        tot = {}
+        for t in trees:
+            for k, v in t.counts_by_type(th).items():
+                tot[k] = tot.get(k, 0) + v
+        assert f.counts_by_type(th) == tot
+    # a forest of forests flattens
+    f2 = api.Forest([f, trees[0]])
+    assert f2.forest_info()[0] == 4
