@@ -42,8 +42,8 @@ METRIC = "FMM cell-cell interactions/s (directed M2L pairs) and gravity-solve ms
 # source adds its detraced 2nd and 3rd moments; a refined target adds the 12 independent
 # components of the 2nd and 3rd derivatives of its expansion; the correction contracts the 4th
 # derivative with detraced 3rd moments.
-FLOPS = {"m2l_leaf_leaf": 8, "p2p_same": 8, "p2p_mixed": 26, "m2l_leaf_refined": 173,
-         "m2l_refined_leaf": 148, "m2l_refined_refined": 243}
+FLOPS = {"m2l_leaf_leaf": 8, "p2p_same": 8, "p2p_mixed": 26, "m2l_leaf_refined": 126,
+         "m2l_refined_leaf": 142, "m2l_refined_refined": 231}
 # which interaction kernel evaluates which pairs
 KERNEL_PAIRS = {"k_m2l_ref": ("m2l_refined_leaf", "m2l_refined_refined", "m2l_leaf_refined",
                               "p2p_mixed"),

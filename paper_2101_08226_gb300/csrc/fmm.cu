@@ -104,6 +104,21 @@ constexpr int kReduceBlocks = 512;
 
 __device__ __forceinline__ double cell_dx(int lev) { return 1.0 / double(kSub << lev); }
 
+// Internal order of the 512 cells of a subgrid (the solver's own arrays; user arrays keep
+// (a*8 + b)*8 + c): parity-major, cell (a, b, c) = (2 ia + pa, 2 ib + pb, 2 ic + pc) at
+// ((pa<<2 | pb<<1 | pc) << 6) | ia << 4 | ib << 2 | ic.  The 64 cells of one parity are then
+// contiguous, and the cells a warp of one parity reads at one stencil offset form contiguous runs.
+__device__ __forceinline__ int cidx(int a, int b, int c) {
+  return ((((a & 1) << 2) | ((b & 1) << 1) | (c & 1)) << 6) | ((a >> 1) << 4) | ((b >> 1) << 2) |
+         (c >> 1);
+}
+__device__ __forceinline__ void cdecode(int i, int& a, int& b, int& c) {
+  const int p = i >> 6;
+  a = (((i >> 4) & 3) << 1) | ((p >> 2) & 1);
+  b = (((i >> 2) & 3) << 1) | ((p >> 1) & 1);
+  c = ((i & 3) << 1) | (p & 1);
+}
+
 // ----------------------------------------------------------------------------------------------
 // p2m: leaf cells are point masses rho dx^3 at their centres
 // ----------------------------------------------------------------------------------------------
@@ -112,7 +127,8 @@ __global__ void k_p2m(DevArgs A, const double* __restrict__ rho, int mixed) {
   if (i >= A.n_leaf_cells) return;
   int32_t s = A.leaf_sub[i >> 9];
   int lev = A.level[s];
-  int64_t cell = int64_t(s) * kCells + (i & 511);
+  const int u = int(i & 511);
+  int64_t cell = int64_t(s) * kCells + cidx(u >> 6, (u >> 3) & 7, u & 7);
   double r = rho[i];
   if (!(r >= 0.0) || !isfinite(r)) {
     atomicOr(A.status, 1);
@@ -135,7 +151,8 @@ __global__ void k_m2m_cell(DevArgs A, const int32_t* __restrict__ subs, int n_su
   if (t >= int64_t(n_subs) * kCells) return;
   int32_t s = subs[t >> 9];
   int loc = int(t & 511);
-  int a = loc >> 6, b = (loc >> 3) & 7, c = loc & 7;
+  int a, b, c;
+  cdecode(loc, a, b, c);
   int lev = A.level[s];
   int32_t cs = A.child[8 * s + ((a >> 2) << 2 | (b >> 2) << 1 | (c >> 2))];
   const int64_t N = A.n_cell;
@@ -147,7 +164,7 @@ __global__ void k_m2m_cell(DevArgs A, const int32_t* __restrict__ subs, int n_su
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
     int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-    int cl = (((a & 3) * 2 + ox) * 8 + (b & 3) * 2 + oy) * 8 + (c & 3) * 2 + oz;
+    int cl = cidx((a & 3) * 2 + ox, (b & 3) * 2 + oy, (c & 3) * 2 + oz);
     ci[o] = int64_t(cs) * kCells + cl;
     m[o] = A.mom[ci[o]];
     u[o][0] = (ox - 0.5) * hc + A.mom[N + ci[o]];
@@ -251,14 +268,14 @@ __global__ void __launch_bounds__(kM2MThreads) k_m2m(DevArgs A, const int32_t* _
   const int64_t pc = t >> 3;
   const int32_t s = subs[pc >> 9];
   const int loc = int(pc & 511);
-  const int a = loc >> 6, b = (loc >> 3) & 7, c = loc & 7;
+  int a, b, c;
+  cdecode(loc, a, b, c);
   const int lev = A.level[s];
   const int32_t cs = A.child[8 * s + ((a >> 2) << 2 | (b >> 2) << 1 | (c >> 2))];
   const int64_t N = A.n_cell;
   const double hc = cell_dx(lev + 1);
   const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-  const int64_t ci = int64_t(cs) * kCells + (((a & 3) * 2 + ox) * 8 + (b & 3) * 2 + oy) * 8 +
-                     (c & 3) * 2 + oz;
+  const int64_t ci = int64_t(cs) * kCells + cidx((a & 3) * 2 + ox, (b & 3) * 2 + oy, (c & 3) * 2 + oz);
   // this child's centre of mass relative to the parent's geometric centre
   const double m = A.mom[ci];
   const double ux = (ox - 0.5) * hc + A.mom[N + ci], uy = (oy - 0.5) * hc + A.mom[2 * N + ci],
@@ -385,20 +402,28 @@ __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict
 #pragma unroll
     for (int k = 0; k < 10; ++k) M3[k] = M[(10 + k) * N + iB];
     g.set(x, y, z, 4);
-    m2l_far<T>(x, y, z, g, mB, M2, M3, S.L);
+    T qx, qy, qz, rrr;
+    m2l_far<T>(x, y, z, g, mB, M2, M3, S.L, qx, qy, qz, rrr);
     if constexpr (AREF) m2l_high<T>(x, y, z, g, mB, S.L);
     if (S.amc) {
-      T Q[10];
-      T w = mB * S.mA_inv;
+      // Q(R,R) = w M3'_A(R,R) - M3'_B(R,R), w = m_B / m_A
       if constexpr (AREF) {
-#pragma unroll
-        for (int k = 0; k < 10; ++k) Q[k] = w * S.M3A[k] - M3[k];
+        const T w = mB * S.mA_inv;
+        T px, py, pz;
+        sym3_rr(S.M3A, x, y, z, px, py, pz);
+        const T prrr = x * px + y * py + z * pz;
+        qx = w * px - qx;
+        qy = w * py - qy;
+        qz = w * pz - qz;
+        rrr = w * prrr - rrr;
       } else {
-#pragma unroll
-        for (int k = 0; k < 10; ++k) Q[k] = -M3[k];
+        qx = -qx;
+        qy = -qy;
+        qz = -qz;
+        rrr = -rrr;
       }
       T cx, cy, cz;
-      amc_term<T>(x, y, z, g, Q, cx, cy, cz);
+      amc_from<T>(x, y, z, g, qx, qy, qz, rrr, cx, cy, cz);
       S.px += cx;
       S.py += cy;
       S.pz += cz;
@@ -409,12 +434,12 @@ __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict
     if constexpr (AREF) {
       m2l_high<T>(x, y, z, g, mB, S.L);
       if (S.amc) {
-        T Q[10];
-        T w = mB * S.mA_inv;
-#pragma unroll
-        for (int k = 0; k < 10; ++k) Q[k] = w * S.M3A[k];
+        const T w = mB * S.mA_inv;
+        T px, py, pz;
+        sym3_rr(S.M3A, x, y, z, px, py, pz);
+        const T prrr = x * px + y * py + z * pz;
         T cx, cy, cz;
-        amc_term<T>(x, y, z, g, Q, cx, cy, cz);
+        amc_from<T>(x, y, z, g, w * px, w * py, w * pz, w * prrr, cx, cy, cz);
         S.px += cx;
         S.py += cy;
         S.pz += cz;
@@ -551,7 +576,7 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool a
   const int64_t N = A.n_cell;
   int a, b, c;
   block_cell(parity, t, a, b, c);
-  const int64_t iA = int64_t(s) * kCells + (a * 8 + b) * 8 + c;
+  const int64_t iA = int64_t(s) * kCells + cidx(a, b, c);
   Target<T, AREF> S;
   load_target<T, AREF>(S, A, M, iA, amc);
   const T h = T(cell_dx(lev));
@@ -566,7 +591,7 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool a
     int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
     int32_t sB = nb[slot];
     if (sB < 0) continue;
-    int64_t iB = int64_t(sB) * kCells + ((px & 7) * 8 + (py & 7)) * 8 + (pz & 7);
+    int64_t iB = int64_t(sB) * kCells + cidx(px & 7, py & 7, pz & 7);
     interact<T, AREF>(S, M, N, iB, nb_ref[slot] != 0, S.dAx - __ldg(td + 4 * q) * h,
                       S.dAy - __ldg(td + 4 * q + 1) * h, S.dAz - __ldg(td + 4 * q + 2) * h);
     if ((q & 63) == 63) flush(S);
@@ -586,14 +611,13 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool a
       if (sB < 0) continue;
       int lx = px & 7, ly = py & 7, lz = pz & 7;
       if (!nb_ref[slot]) {
-        int64_t iB = int64_t(sB) * kCells + (lx * 8 + ly) * 8 + lz;
+        int64_t iB = int64_t(sB) * kCells + cidx(lx, ly, lz);
         interact_point<T, AREF>(S, M[iB], -T(dx) * h, -T(dy) * h, -T(dz) * h);
       } else {
         int32_t cs = A.child[8 * sB + ((lx >> 2) << 2 | (ly >> 2) << 1 | (lz >> 2))];
         for (int o = 0; o < 8; ++o) {
           int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-          int64_t iC = int64_t(cs) * kCells + (((lx & 3) * 2 + ox) * 8 + (ly & 3) * 2 + oy) * 8 +
-                       (lz & 3) * 2 + oz;
+          int64_t iC = int64_t(cs) * kCells + cidx((lx & 3) * 2 + ox, (ly & 3) * 2 + oy, (lz & 3) * 2 + oz);
           // x_A - x_C = (1/2 - o - 2 d) dx_(l+1)
           interact_point<T, AREF>(S, M[iC], (T(0.5) - T(ox) - T(2 * dx)) * hc,
                                   (T(0.5) - T(oy) - T(2 * dy)) * hc,
@@ -614,7 +638,7 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool a
       int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
       if (!pnb_leaf[slot]) continue;
       int32_t sB = pnb[slot];
-      int64_t iB = int64_t(sB) * kCells + ((px & 7) * 8 + (py & 7)) * 8 + (pz & 7);
+      int64_t iB = int64_t(sB) * kCells + cidx(px & 7, py & 7, pz & 7);
       // x_A - x_i = ((g_A & 1) - 1/2 - 2 d) dx_l
       interact_point<T, AREF>(S, M[iB], (T(ga & 1) - T(0.5) - T(2 * dx)) * h,
                               (T(gb & 1) - T(0.5) - T(2 * dy)) * h,
@@ -633,7 +657,7 @@ __device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chun
   const int64_t N = A.n_cell;
   int a, b, c;
   block_cell(parity, t, a, b, c);
-  const int iloc = (a * 8 + b) * 8 + c;
+  const int iloc = cidx(a, b, c);
   const int64_t base = int64_t(root) * kCells;
   Target<T, AREF> S;
   load_target<T, AREF>(S, A, M, base + iloc, amc);
@@ -646,7 +670,7 @@ __device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chun
   for (int jy = 0; jy < 8; ++jy, ry -= h) {
     T rz = rz0;
     for (int jz = 0; jz < 8; ++jz, rz -= h) {
-      const int j = chunk * 64 + jy * 8 + jz;
+      const int j = cidx(chunk, jy, jz);
       if (j == iloc) continue;
       const int dy = jy - b, dz = jz - c;
       const bool ws = dx * dx + dy * dy + dz * dz > A.ws_d2;
@@ -702,7 +726,7 @@ __device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, int t, boo
   const int64_t N = A.n_cell;
   int a, b, c;
   block_cell(parity, t, a, b, c);
-  const int64_t iA = int64_t(s) * kCells + (a * 8 + b) * 8 + c;
+  const int64_t iA = int64_t(s) * kCells + cidx(a, b, c);
   Target<T, false> S;
   load_target<T, false>(S, A, M, iA, amc);
   const T h = T(cell_dx(lev)), hc = h * T(0.5);
@@ -714,7 +738,7 @@ __device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, int t, boo
     int px = a + dx, py = b + dy, pz = c + dz;
     int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
     if (!nb_ref[slot]) continue;
-    int64_t iB = int64_t(nb[slot]) * kCells + ((px & 7) * 8 + (py & 7)) * 8 + (pz & 7);
+    int64_t iB = int64_t(nb[slot]) * kCells + cidx(px & 7, py & 7, pz & 7);
     interact<T, false>(S, M, N, iB, true, -__ldg(td + 4 * q) * h, -__ldg(td + 4 * q + 1) * h,
                        -__ldg(td + 4 * q + 2) * h);
     if ((q & 63) == 63) flush(S);
@@ -731,11 +755,12 @@ __device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, int t, boo
     // x_A - x_C = (1/2 - o - 2 d) dx_(l+1), o the child's octant
     const T ex = (T(0.5) - T(2) * __ldg(td + 4 * q)) * hc, ey = (T(0.5) - T(2) * __ldg(td + 4 * q + 1)) * hc,
             ez = (T(0.5) - T(2) * __ldg(td + 4 * q + 2)) * hc;
-    const int64_t c0 = int64_t(cs) * kCells + (((lx & 3) * 2) * 8 + (ly & 3) * 2) * 8 + (lz & 3) * 2;
+    const int64_t c0 = int64_t(cs) * kCells;
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
       const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-      interact_point<T, false>(S, M[c0 + (ox * 8 + oy) * 8 + oz], ex - (ox ? hc : T(0)),
+      const int cl = cidx((lx & 3) * 2 + ox, (ly & 3) * 2 + oy, (lz & 3) * 2 + oz);
+      interact_point<T, false>(S, M[c0 + cl], ex - (ox ? hc : T(0)),
                                ey - (oy ? hc : T(0)), ez - (oz ? hc : T(0)));
     }
   }
@@ -752,7 +777,7 @@ __device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, int t, boo
     int px = ja + dx, py = jb + dy, pz = jc + dz;
     int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
     if (!pnb_leaf[slot]) continue;
-    int64_t iB = int64_t(pnb[slot]) * kCells + ((px & 7) * 8 + (py & 7)) * 8 + (pz & 7);
+    int64_t iB = int64_t(pnb[slot]) * kCells + cidx(px & 7, py & 7, pz & 7);
     interact_point<T, false>(S, M[iB], (fa - T(2) * __ldg(td + 4 * q)) * h,
                              (fb - T(2) * __ldg(td + 4 * q + 1)) * h,
                              (fc - T(2) * __ldg(td + 4 * q + 2)) * h);
@@ -842,7 +867,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
     int hx = i / kHalo2, r = i - hx * kHalo2, hy = r / kHalo, hz = r - hy * kHalo;
     int x = hx - 5, y = hy - 5, z = hz - 5;
     int32_t q = nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)];
-    hm[i] = q >= 0 ? M[int64_t(q) * kCells + ((x & 7) * 8 + (y & 7)) * 8 + (z & 7)] : T(0);
+    hm[i] = q >= 0 ? M[int64_t(q) * kCells + cidx(x & 7, y & 7, z & 7)] : T(0);
   }
   __syncthreads();
   const T h = T(cell_dx(A.level[s]));
@@ -872,8 +897,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
     uz += m1 * kz;
   }
   const T ih = T(1) / h, ih2 = ih * ih;
-  const int64_t i0 = int64_t(s) * kCells + (a0 * 8 + b) * 8 + c;
-  const int64_t i1 = i0 + 4 * 64;
+  const int64_t i0 = int64_t(s) * kCells + cidx(a0, b, c);
+  const int64_t i1 = int64_t(s) * kCells + cidx(a0 + 4, b, c);
   if (sizeof(T) == 8) {
     double* L = reinterpret_cast<double*>(A.loc);
     L[i0] = -double(s0 * ih);
@@ -983,10 +1008,11 @@ __global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs, double* __
     }
   } else if (MIXED && isleaf) {
     const int32_t Pn = A.parent[s];
-    int a = loc >> 6, b = (loc >> 3) & 7, c = loc & 7;
+    int a, b, c;
+    cdecode(loc, a, b, c);
     int ga = A.ijk[3 * s] * 8 + a, gb = A.ijk[3 * s + 1] * 8 + b, gc = A.ijk[3 * s + 2] * 8 + c;
-    int pl = (((ga >> 1) - A.ijk[3 * Pn] * 8) * 8 + ((gb >> 1) - A.ijk[3 * Pn + 1] * 8)) * 8 +
-             ((gc >> 1) - A.ijk[3 * Pn + 2] * 8);
+    int pl = cidx((ga >> 1) - A.ijk[3 * Pn] * 8, (gb >> 1) - A.ijk[3 * Pn + 1] * 8,
+                  (gc >> 1) - A.ijk[3 * Pn + 2] * 8);
     const int64_t ip = int64_t(Pn) * kCells + pl;
     float P32[20], d[4];
 #pragma unroll
@@ -1009,10 +1035,11 @@ __global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs, double* __
     ay = A.ac[N + i];
     az = A.ac[2 * N + i];
     const int32_t Pn = A.parent[s];
-    int a = loc >> 6, b = (loc >> 3) & 7, c = loc & 7;
+    int a, b, c;
+    cdecode(loc, a, b, c);
     int ga = A.ijk[3 * s] * 8 + a, gb = A.ijk[3 * s + 1] * 8 + b, gc = A.ijk[3 * s + 2] * 8 + c;
-    int pl = (((ga >> 1) - A.ijk[3 * Pn] * 8) * 8 + ((gb >> 1) - A.ijk[3 * Pn + 1] * 8)) * 8 +
-             ((gc >> 1) - A.ijk[3 * Pn + 2] * 8);
+    int pl = cidx((ga >> 1) - A.ijk[3 * Pn] * 8, (gb >> 1) - A.ijk[3 * Pn + 1] * 8,
+                  (gc >> 1) - A.ijk[3 * Pn + 2] * 8);
     const int64_t ip = int64_t(Pn) * kCells + pl;
     double P[20];
 #pragma unroll
@@ -1028,7 +1055,9 @@ __global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs, double* __
     az += A.ac[2 * N + ip];
   }
   if (isleaf) {
-    const int64_t o = int64_t(A.leaf_ord[s]) * kCells + loc;
+    int a, b, c;
+    cdecode(loc, a, b, c);
+    const int64_t o = int64_t(A.leaf_ord[s]) * kCells + (a * 8 + b) * 8 + c;  // user order
     phi[o] = L[0];
     g[3 * o] = -L[1] + ax;
     g[3 * o + 1] = -L[2] + ay;

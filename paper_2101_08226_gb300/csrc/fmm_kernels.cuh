@@ -73,17 +73,17 @@ struct Radial {
 //   L0 -= m D0 + 1/2 D2:M2 - 1/6 D3:M3,   L1 -= m D1 + 1/2 D3:M2,   L2 -= m D2,   L3 -= m D3.
 // With detraced moments: D2:M2' = g2 R.M2'.R, D3:M3' = g3 M3'(R,R,R),
 // (D3:M2')_a = g3 R_a R.M2'.R + 2 g2 (M2' R)_a.
+// Also returns q = M3'(R,R) and rrr = R.q, which the correction reuses.
 template <typename T>
 __device__ __forceinline__ void m2l_far(T x, T y, T z, const Radial<T>& g, T m, const T* M2,
-                                        const T* M3, T* L) {
+                                        const T* M3, T* L, T& qx, T& qy, T& qz, T& rrr) {
   // M2: xx xy xz yy yz zz
   T m2rx = M2[0] * x + M2[1] * y + M2[2] * z;
   T m2ry = M2[1] * x + M2[3] * y + M2[4] * z;
   T m2rz = M2[2] * x + M2[4] * y + M2[5] * z;
   T rm2r = x * m2rx + y * m2ry + z * m2rz;
-  T qx, qy, qz;
   sym3_rr(M3, x, y, z, qx, qy, qz);
-  T rrr = x * qx + y * qy + z * qz;
+  rrr = x * qx + y * qy + z * qz;
   const T sixth = T(1) / T(6);
   L[0] -= m * g.g0 + T(0.5) * g.g2 * rm2r - sixth * g.g3 * rrr;
   T c1 = m * g.g1 + T(0.5) * g.g3 * rm2r;
@@ -138,13 +138,12 @@ __device__ __forceinline__ void complete_traceless(T* L) {
 
 // Angular-momentum correction acceleration of A (Sec. 2.2):
 //   a_A += 1/6 D4 : Q,  Q = (m_B / m_A) M3'_A - M3'_B,
-//   (D4:Q)_a = g4 R_a Q(R,R,R) + 3 g3 Q(R,R)_a  (Q traceless).
+//   (D4:Q)_a = g4 R_a Q(R,R,R) + 3 g3 Q(R,R)_a  (Q traceless),
+// given the contracted vector Q(R,R) and Q(R,R,R) (linear in Q, so the parts of M3'_A and M3'_B
+// are contracted separately and M3'_B(R,R) is shared with the expansion).
 template <typename T>
-__device__ __forceinline__ void amc_term(T x, T y, T z, const Radial<T>& g, const T* Q, T& ax,
-                                         T& ay, T& az) {
-  T qx, qy, qz;
-  sym3_rr(Q, x, y, z, qx, qy, qz);
-  T qrrr = x * qx + y * qy + z * qz;
+__device__ __forceinline__ void amc_from(T x, T y, T z, const Radial<T>& g, T qx, T qy, T qz,
+                                         T qrrr, T& ax, T& ay, T& az) {
   const T sixth = T(1) / T(6);
   T c4 = sixth * g.g4 * qrrr, c3 = T(0.5) * g.g3;
   ax = c4 * x + c3 * qx;
