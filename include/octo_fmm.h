@@ -116,14 +116,21 @@ int fmm_interaction_counts_by_type(const fmm_tree* tree, double theta, int64_t c
  *   reduced in FP64 in a fixed order (the terms of the normalisation S are formed in FP32).
  * theta in [0.34, 1).  precision FMM_FP64 or FMM_MIXED.  stream: a cudaStream_t (NULL = legacy
  * default stream).  Asynchronous: returns once the work is enqueued.  On a forest, net_dev holds
- * 7 doubles per tree. */
+ * 7 doubles per tree.
+ * Execution: the work runs on a stream the tree owns, after all work enqueued on `stream` before
+ * the call and before all work enqueued on `stream` after it, so that the calls of one tree never
+ * overlap whatever streams they name.  By default the launches of each configuration (theta,
+ * precision, amc, net_dev NULL or not, profiling) are captured once into a CUDA graph, which
+ * every later call of that configuration replays after one small kernel that writes this call's
+ * pointers into a device table (fmm_set_graphs turns this off).  The first call of a
+ * configuration therefore costs extra host time. */
 int fmm_solve(fmm_tree* tree, const double* rho_dev, double theta, int precision, int amc,
               double* phi_dev, double* g_dev, double* net_dev, void* stream);
 
 /* fmm_solve on a forest with one device buffer per tree: rho_dev[k], phi_dev[k], g_dev[k] are
- * tree k's arrays (its own canonical order).  They are copied into and out of the forest's own
- * concatenated buffers on `stream` around one fmm_solve; net_dev (optional) gets 7 doubles per
- * tree.  Asynchronous. */
+ * tree k's arrays (its own canonical order), read and written in place by the kernels (the
+ * pointer arrays themselves are host arrays, read before the call returns); net_dev (optional)
+ * gets 7 doubles per tree.  Asynchronous, ordered on `stream` as fmm_solve. */
 int fmm_solve_batch(fmm_tree* forest, const double* const* rho_dev, double theta, int precision,
                     int amc, double* const* phi_dev, double* const* g_dev, double* net_dev,
                     void* stream);
@@ -142,6 +149,10 @@ int fmm_solve_host(fmm_tree* tree, const double* rho_host, double theta, int pre
  * for the masses given by rho_dev on this tree's leaf cells.  Uses the tree's workspace. */
 int fmm_net_force_torque(fmm_tree* tree, const double* rho_dev, const double* g_dev,
                          double* net_dev, void* stream);
+
+/* on != 0 (the default): replay one captured CUDA graph per solve configuration; on == 0:
+ * enqueue the kernels one by one on every call.  The results are the same bit for bit. */
+int fmm_set_graphs(fmm_tree* tree, int on);
 
 /* Per-phase device times (ms) of the most recent solve on this tree, measured with CUDA events
  * on the solve's stream when profiling is on: [0] upward pass, [1] multipole interactions and

@@ -144,6 +144,11 @@ class Tree:
     def set_profiling(self, on: bool = True):
         check(lib().fmm_set_profiling(self._h, int(bool(on))))
 
+    def set_graphs(self, on: bool = True):
+        """Replay one captured CUDA graph per solve configuration (the default), or launch the
+        kernels one by one."""
+        check(lib().fmm_set_graphs(self._h, int(bool(on))))
+
     def phase_times(self) -> np.ndarray:
         """ms of the last profiled solve: upward, interactions, downward, reductions, then the
         two interaction kernels (refined targets with the root, leaf targets)."""

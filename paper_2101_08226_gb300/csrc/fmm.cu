@@ -54,6 +54,16 @@ static int fail(int code, const std::string& msg) {
 // ----------------------------------------------------------------------------------------------
 // device-side tree and workspace
 // ----------------------------------------------------------------------------------------------
+// The caller's arrays of one tree: rho and phi hold its leaf cells in leaf order (512 per leaf
+// subgrid, x-major inside a subgrid), g three numbers per cell.  The solve reads these pointers
+// from a small device table written at the start of every call, so that a captured graph does not
+// depend on the buffers a call passes.
+struct TreeIo {
+  const double* rho;
+  double* phi;
+  double* g;
+};
+
 struct DevArgs {
   int64_t n_cell;          // n_sub * 512
   int64_t n_leaf_cells;
@@ -89,6 +99,9 @@ struct DevArgs {
   float* root_part32;      // [n_roots][kRootChunks][20][512] (mixed path)
   double* root_part_ac;    // [n_roots][kRootChunks][3][512] (mixed path)
   int* status;
+  const int32_t* leaf_tree;  // [n_leaf_sub] tree of each leaf subgrid
+  const TreeIo* io;          // [n_roots] the caller's arrays of each tree
+  double* const* io_net;     // the caller's net array (7 numbers per tree), or null
 };
 
 constexpr int kStencilCap = 1024;
@@ -122,14 +135,15 @@ __device__ __forceinline__ void cdecode(int i, int& a, int& b, int& c) {
 // ----------------------------------------------------------------------------------------------
 // p2m: leaf cells are point masses rho dx^3 at their centres
 // ----------------------------------------------------------------------------------------------
-__global__ void k_p2m(DevArgs A, const double* __restrict__ rho, int mixed) {
+__global__ void k_p2m(DevArgs A, int mixed) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= A.n_leaf_cells) return;
   int32_t s = A.leaf_sub[i >> 9];
   int lev = A.level[s];
   const int u = int(i & 511);
   int64_t cell = int64_t(s) * kCells + cidx(u >> 6, (u >> 3) & 7, u & 7);
-  double r = rho[i];
+  const int k = A.leaf_tree[i >> 9];
+  double r = A.io[k].rho[i - A.tree_leaf_off[k] * kCells];
   if (!(r >= 0.0) || !isfinite(r)) {
     atomicOr(A.status, 1);
     r = 0.0;
@@ -975,8 +989,7 @@ __device__ __forceinline__ void shift_terms32(const float* P, float rx, float ry
 }
 
 template <bool MIXED>
-__global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs, double* __restrict__ phi,
-                      double* __restrict__ g) {
+__global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs) {
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n_subs * kCells) return;
   const int32_t s = int32_t(s0 + (t >> 9));
@@ -1057,7 +1070,11 @@ __global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs, double* __
   if (isleaf) {
     int a, b, c;
     cdecode(loc, a, b, c);
-    const int64_t o = int64_t(A.leaf_ord[s]) * kCells + (a * 8 + b) * 8 + c;  // user order
+    const int32_t ls = A.leaf_ord[s];
+    const int k = A.leaf_tree[ls];
+    const int64_t o = (int64_t(ls) - A.tree_leaf_off[k]) * kCells + (a * 8 + b) * 8 + c;
+    double* __restrict__ phi = A.io[k].phi;
+    double* __restrict__ g = A.io[k].g;
     phi[o] = L[0];
     g[3 * o] = -L[1] + ax;
     g[3 * o + 1] = -L[2] + ay;
@@ -1094,15 +1111,16 @@ __device__ __forceinline__ void block_sum7(double* v, double (*sh)[kReduceThread
 
 // blockIdx.y = tree; its leaf cells are reduced by gridDim.x blocks in a fixed order.
 __global__ void __launch_bounds__(kReduceThreads)
-    k_net_partial(DevArgs A, const double* __restrict__ rho, const double* __restrict__ g,
-                  double* __restrict__ partials) {
+    k_net_partial(DevArgs A, double* __restrict__ partials) {
   __shared__ double sh[7][kReduceThreads];
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
   const int64_t stride = int64_t(gridDim.x) * kReduceThreads;
+  const int64_t base = A.tree_leaf_off[blockIdx.y] * kCells;
   const int64_t end = A.tree_leaf_off[blockIdx.y + 1] * kCells;
-  for (int64_t i = A.tree_leaf_off[blockIdx.y] * kCells + int64_t(blockIdx.x) * kReduceThreads +
-                   threadIdx.x;
-       i < end; i += stride) {
+  const double* __restrict__ rho = A.io[blockIdx.y].rho;
+  const double* __restrict__ g = A.io[blockIdx.y].g;
+  for (int64_t i = base + int64_t(blockIdx.x) * kReduceThreads + threadIdx.x; i < end;
+       i += stride) {
     int32_t s = A.leaf_sub[i >> 9];
     int lev = A.level[s];
     int loc = int(i & 511);
@@ -1110,8 +1128,9 @@ __global__ void __launch_bounds__(kReduceThreads)
     double x = -0.5 + (A.ijk[3 * s] * 8 + (loc >> 6) + 0.5) * h;
     double y = -0.5 + (A.ijk[3 * s + 1] * 8 + ((loc >> 3) & 7) + 0.5) * h;
     double z = -0.5 + (A.ijk[3 * s + 2] * 8 + (loc & 7) + 0.5) * h;
-    double m = rho[i] * h * h * h;
-    double fx = m * g[3 * i], fy = m * g[3 * i + 1], fz = m * g[3 * i + 2];
+    const int64_t o = i - base;
+    double m = rho[o] * h * h * h;
+    double fx = m * g[3 * o], fy = m * g[3 * o + 1], fz = m * g[3 * o + 2];
     v[0] += fx;
     v[1] += fy;
     v[2] += fz;
@@ -1128,9 +1147,12 @@ __global__ void __launch_bounds__(kReduceThreads)
     partials[(int64_t(blockIdx.y) * gridDim.x + blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// blockIdx.x = tree (or set of partials): sums n_blocks partials in a fixed order into out[7 x].
+// blockIdx.x = tree (or set of partials): sums n_blocks partials in a fixed order into out[7 x];
+// out is read from *out_slot when that is given.
 __global__ void __launch_bounds__(kReduceThreads)
-    k_net_final(const double* __restrict__ partials, int n_blocks, double* __restrict__ out) {
+    k_net_final(const double* __restrict__ partials, int n_blocks, double* out,
+                double* const* out_slot) {
+  if (out_slot) out = *out_slot;
   __shared__ double sh[7][kReduceThreads];
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
   const double* P = partials + int64_t(blockIdx.x) * n_blocks * 7;
@@ -1139,6 +1161,23 @@ __global__ void __launch_bounds__(kReduceThreads)
     for (int k = 0; k < 7; ++k) v[k] += P[int64_t(b) * 7 + k];
   block_sum7(v, sh);
   if (threadIdx.x < 7) out[int64_t(blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// ----------------------------------------------------------------------------------------------
+// the caller's pointers of one call, passed by value as kernel parameters
+// ----------------------------------------------------------------------------------------------
+constexpr int kIoChunk = 128;  // trees per launch: the parameter block stays under 4 KB
+struct IoChunk {
+  double* net;
+  int32_t first, count;
+  TreeIo e[kIoChunk];
+};
+static_assert(sizeof(IoChunk) <= 4000, "kernel parameter block too large");
+
+__global__ void k_set_io(IoChunk c, TreeIo* __restrict__ table, double** net_slot) {
+  const int j = threadIdx.x;
+  if (j < c.count) table[c.first + j] = c.e[j];
+  if (j == 0) *net_slot = c.net;
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -1184,6 +1223,21 @@ struct fmm_tree {
   int32_t launches = 0;
   std::vector<void*> allocs;
   std::vector<int32_t> work, work_bnd;  // refined and boundary leaf subgrids of levels >= 1
+  int32_t* d_leaf_tree = nullptr;
+  TreeIo* d_io = nullptr;         // [n_trees] the caller's arrays of the current call
+  double** d_io_net = nullptr;    // the caller's net array of the current call
+  // Every call of a tree runs on the tree's own stream, ordered after the caller's stream by
+  // ev_in and before its later work by ev_out, so that calls of one tree never overlap.
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  bool use_graphs = true;
+  bool capturing = false;
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int32_t launches = 0;
+  };
+  // one instantiated graph per (theta, precision, correction, net output, profiling)
+  std::map<std::tuple<double, int, int, int, int>, Graph> graphs;
 };
 
 // blocks per tree of the net reduction: about 512 in all
@@ -1272,6 +1326,16 @@ static int ensure_device(fmm_tree* t) {
   CUDA_TRY(upload(t, &t->d_tree_leaf_off, h.tree_leaf_off));
   CUDA_TRY(dalloc(t, &t->d_status, sizeof(int)));
   CUDA_TRY(cudaMemset(t->d_status, 0, sizeof(int)));
+  std::vector<int32_t> leaf_tree(size_t(h.n_leaf_sub));
+  for (int k = 0; k < h.n_trees; ++k)
+    for (int64_t l = h.tree_leaf_off[k]; l < h.tree_leaf_off[k + 1]; ++l) leaf_tree[size_t(l)] = k;
+  CUDA_TRY(upload(t, &t->d_leaf_tree, leaf_tree));
+  CUDA_TRY(dalloc(t, &t->d_io, sizeof(TreeIo) * size_t(nr)));
+  CUDA_TRY(dalloc(t, &t->d_io_net, sizeof(double*)));
+  CUDA_TRY(cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&t->ev_in, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&t->ev_out, cudaEventDisableTiming));
+  for (auto& e : t->ev) CUDA_TRY(cudaEventCreate(&e));
   t->dev_ready = true;
   return FMM_OK;
 }
@@ -1474,6 +1538,9 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.root_part32 = t->d_root_part32;
   A.root_part_ac = t->d_root_part_ac;
   A.status = t->d_status;
+  A.leaf_tree = t->d_leaf_tree;
+  A.io = t->d_io;
+  A.io_net = t->d_io_net;
   return A;
 }
 
@@ -1483,40 +1550,52 @@ static inline unsigned blocks_for(int64_t n, int threads) {
 
 static int record(fmm_tree* t, int k, cudaStream_t st) {
   if (!t->profiling) return FMM_OK;
-  if (!t->ev[k]) CUDA_TRY(cudaEventCreate(&t->ev[k]));
-  CUDA_TRY(cudaEventRecord(t->ev[k], st));
+  // inside a capture the record becomes an event node of the graph
+  CUDA_TRY(cudaEventRecordWithFlags(t->ev[k], st, t->capturing ? cudaEventRecordExternal : 0));
   return FMM_OK;
 }
 
-static int launch_net(fmm_tree* t, const DevArgs& A, const double* rho, const double* g,
-                      double* net, cudaStream_t st) {
+// Writes the caller's pointers of this call into the device table (one launch per kIoChunk trees).
+static int set_io(fmm_tree* t, const std::vector<TreeIo>& io, double* net, cudaStream_t st,
+                  int32_t* launches) {
+  const int n = int(io.size());  // the trees of t: at least one
+  const int chunks = (n + kIoChunk - 1) / kIoChunk;
+  for (int q = 0; q < chunks; ++q) {
+    IoChunk c;
+    c.net = net;
+    c.first = q * kIoChunk;
+    c.count = std::min(kIoChunk, n - c.first);
+    for (int j = 0; j < c.count; ++j) c.e[j] = io[size_t(c.first + j)];
+    k_set_io<<<1, kIoChunk, 0, st>>>(c, t->d_io, t->d_io_net);
+    CUDA_TRY(cudaGetLastError());
+  }
+  *launches = chunks;
+  return FMM_OK;
+}
+
+static int launch_net(fmm_tree* t, const DevArgs& A, cudaStream_t st) {
   const int nb = net_blocks(t->h.n_trees);
   k_net_partial<<<dim3(unsigned(nb), unsigned(t->h.n_trees)), kReduceThreads, 0, st>>>(
-      A, rho, g, t->d_partials);
+      A, t->d_partials);
   CUDA_TRY(cudaGetLastError());
-  k_net_final<<<unsigned(t->h.n_trees), kReduceThreads, 0, st>>>(t->d_partials, nb, net);
+  k_net_final<<<unsigned(t->h.n_trees), kReduceThreads, 0, st>>>(t->d_partials, nb, nullptr,
+                                                                  A.io_net);
   CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }
 
-static int solve_impl(fmm_tree* t, const double* rho, double theta, int precision, int amc,
-                      double* phi, double* g, double* net, cudaStream_t st) {
-  if (!(theta >= kThetaMin && theta < 1.0))
-    return fail(FMM_ERR_THETA, "theta must lie in [0.34, 1)");
-  if (precision != FMM_FP64 && precision != FMM_MIXED) return fail(FMM_ERR_ARG, "bad precision");
-  if (!rho || !phi || !g) return fail(FMM_ERR_ARG, "null device pointer");
-  int rc = ensure_device(t);
-  if (rc) return rc;
-  const bool mixed = precision == FMM_MIXED;
-  if (mixed && (rc = ensure_mixed(t))) return rc;
-  StencilDev* sd = nullptr;
-  if ((rc = get_stencil(t, theta, &sd))) return rc;
+// All launches of one solve, in order, on stream st (which may be capturing).
+static int enqueue_solve(fmm_tree* t, const StencilDev* sd, bool mixed, int amc, bool net,
+                         cudaStream_t st, int32_t* launches) {
   const HostTree& h = t->h;
   DevArgs A = make_args(t, sd);
+  int rc;
+  int32_t nl = 0;
   if ((rc = record(t, 0, st))) return rc;
   // upward pass
-  k_p2m<<<blocks_for(A.n_leaf_cells, 256), 256, 0, st>>>(A, rho, mixed ? 1 : 0);
+  k_p2m<<<blocks_for(A.n_leaf_cells, 256), 256, 0, st>>>(A, mixed ? 1 : 0);
   CUDA_TRY(cudaGetLastError());
+  ++nl;
   for (int l = h.depth - 1; l >= 0; --l) {
     int64_t n = t->refined_off[l + 1] - t->refined_off[l];
     if (n == 0) continue;
@@ -1527,6 +1606,7 @@ static int solve_impl(fmm_tree* t, const double* rho, double theta, int precisio
       k_m2m<<<unsigned(n * kCells * 8 / kM2MThreads), kM2MThreads, 0, st>>>(
           A, t->d_refined + t->refined_off[l], mixed ? 1 : 0);
     CUDA_TRY(cudaGetLastError());
+    ++nl;
   }
 
   if ((rc = record(t, 1, st))) return rc;
@@ -1536,6 +1616,7 @@ static int solve_impl(fmm_tree* t, const double* rho, double theta, int precisio
     if (mixed) k_m2l_leaf<float><<<unsigned(t->n_work_leaf), kLeafThreads, 0, st>>>(A, t->d_work_leaf);
     else k_m2l_leaf<double><<<unsigned(t->n_work_leaf), kLeafThreads, 0, st>>>(A, t->d_work_leaf);
     CUDA_TRY(cudaGetLastError());
+    ++nl;
   }
   if ((rc = record(t, 5, st))) return rc;
   if (mixed)
@@ -1543,22 +1624,102 @@ static int solve_impl(fmm_tree* t, const double* rho, double theta, int precisio
   else
     k_m2l_ref<double, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
   CUDA_TRY(cudaGetLastError());
+  ++nl;
   if ((rc = record(t, 2, st))) return rc;
   // downward pass
   for (int l = 0; l <= h.depth; ++l) {
     int64_t s0 = h.lev_off[l], n = h.lev_off[l + 1] - h.lev_off[l];
-    if (mixed) k_l2l<true><<<blocks_for(n * kCells, 128), 128, 0, st>>>(A, l, s0, n, phi, g);
-    else k_l2l<false><<<blocks_for(n * kCells, 128), 128, 0, st>>>(A, l, s0, n, phi, g);
+    if (mixed) k_l2l<true><<<blocks_for(n * kCells, 128), 128, 0, st>>>(A, l, s0, n);
+    else k_l2l<false><<<blocks_for(n * kCells, 128), 128, 0, st>>>(A, l, s0, n);
     CUDA_TRY(cudaGetLastError());
+    ++nl;
   }
   if ((rc = record(t, 3, st))) return rc;
-  if (net && (rc = launch_net(t, A, rho, g, net, st))) return rc;
+  if (net) {
+    if ((rc = launch_net(t, A, st))) return rc;
+    nl += 2;
+  }
   if ((rc = record(t, 4, st))) return rc;
-  t->ev_recorded = t->profiling;
-  int32_t n_m2m = 0;
-  for (int l = 0; l < h.depth; ++l) n_m2m += (t->refined_off[l + 1] > t->refined_off[l]) ? 1 : 0;
-  t->launches = 1 + n_m2m + 1 + (t->n_work_leaf > 0 ? 1 : 0) + (h.depth + 1) + (net ? 2 : 0);
+  *launches = nl;
   return FMM_OK;
+}
+
+// Captures the launches of one solve configuration into a graph and instantiates it.
+static int capture_graph(fmm_tree* t, const StencilDev* sd, bool mixed, int amc, bool net,
+                         fmm_tree::Graph* out) {
+  CUDA_TRY(cudaStreamBeginCapture(t->stream, cudaStreamCaptureModeThreadLocal));
+  t->capturing = true;
+  int32_t nl = 0;
+  int rc = enqueue_solve(t, sd, mixed, amc, net, t->stream, &nl);
+  t->capturing = false;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(t->stream, &g);
+  if (rc || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc ? rc : fail(FMM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(FMM_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+  out->exec = x;
+  out->launches = nl;
+  return FMM_OK;
+}
+
+// One solve of every tree of t: io[k] holds the caller's arrays of tree k.
+static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, int precision,
+                      int amc, double* net, cudaStream_t caller) {
+  if (!(theta >= kThetaMin && theta < 1.0))
+    return fail(FMM_ERR_THETA, "theta must lie in [0.34, 1)");
+  if (precision != FMM_FP64 && precision != FMM_MIXED) return fail(FMM_ERR_ARG, "bad precision");
+  for (const TreeIo& e : io)
+    if (!e.rho || !e.phi || !e.g) return fail(FMM_ERR_ARG, "null device pointer");
+  int rc = ensure_device(t);
+  if (rc) return rc;
+  const bool mixed = precision == FMM_MIXED;
+  if (mixed && (rc = ensure_mixed(t))) return rc;
+  StencilDev* sd = nullptr;
+  if ((rc = get_stencil(t, theta, &sd))) return rc;
+  amc = amc ? 1 : 0;
+  fmm_tree::Graph* gr = nullptr;
+  if (t->use_graphs) {
+    auto key = std::make_tuple(theta, precision, amc, net ? 1 : 0, t->profiling ? 1 : 0);
+    auto it = t->graphs.find(key);
+    if (it == t->graphs.end()) {
+      fmm_tree::Graph fresh;
+      if ((rc = capture_graph(t, sd, mixed, amc, net != nullptr, &fresh))) return rc;
+      it = t->graphs.emplace(key, fresh).first;
+    }
+    gr = &it->second;
+  }
+  CUDA_TRY(cudaEventRecord(t->ev_in, caller));
+  CUDA_TRY(cudaStreamWaitEvent(t->stream, t->ev_in, 0));
+  int32_t n_io = 0, n_solve = 0;
+  if ((rc = set_io(t, io, net, t->stream, &n_io))) return rc;
+  if (gr) {
+    CUDA_TRY(cudaGraphLaunch(gr->exec, t->stream));
+    n_solve = gr->launches;
+  } else if ((rc = enqueue_solve(t, sd, mixed, amc, net != nullptr, t->stream, &n_solve))) {
+    return rc;
+  }
+  CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
+  CUDA_TRY(cudaStreamWaitEvent(caller, t->ev_out, 0));
+  t->ev_recorded = t->profiling;
+  t->launches = n_io + n_solve;
+  return FMM_OK;
+}
+
+// io table of a forest whose trees' arrays are consecutive parts of one array each
+static std::vector<TreeIo> contiguous_io(const fmm_tree* t, const double* rho, double* phi,
+                                         double* g) {
+  std::vector<TreeIo> io(size_t(t->h.n_trees));
+  for (int k = 0; k < t->h.n_trees; ++k) {
+    const int64_t o = t->h.tree_leaf_off[k] * kCells;
+    io[size_t(k)] = TreeIo{rho ? rho + o : nullptr, phi ? phi + o : nullptr, g ? g + 3 * o : nullptr};
+  }
+  return io;
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -1648,9 +1809,16 @@ void fmm_destroy(fmm_tree* t) {
   if (t->dev_ready && cudaGetDevice(&cur) == cudaSuccess && cur != t->device) {
     switched = cudaSetDevice(t->device) == cudaSuccess;
   }
+  for (auto& kv : t->graphs) cudaGraphExecDestroy(kv.second.exec);
+  if (t->stream) {
+    cudaStreamSynchronize(t->stream);
+    cudaStreamDestroy(t->stream);
+  }
   for (void* p : t->allocs) cudaFree(p);
   for (auto& e : t->ev)
     if (e) cudaEventDestroy(e);
+  if (t->ev_in) cudaEventDestroy(t->ev_in);
+  if (t->ev_out) cudaEventDestroy(t->ev_out);
   if (switched) cudaSetDevice(cur);
   delete t;
 }
@@ -1742,9 +1910,10 @@ int fmm_last_launches(const fmm_tree* t, int32_t* n) {
 int fmm_solve(fmm_tree* t, const double* rho_dev, double theta, int precision, int amc,
               double* phi_dev, double* g_dev, double* net_dev, void* stream) {
   if (!t) return fail(FMM_ERR_ARG, "tree is null");
+  if (!rho_dev || !phi_dev || !g_dev) return fail(FMM_ERR_ARG, "null device pointer");
   try {
-    return solve_impl(t, rho_dev, theta, precision, amc, phi_dev, g_dev, net_dev,
-                      static_cast<cudaStream_t>(stream));
+    return solve_impl(t, contiguous_io(t, rho_dev, phi_dev, g_dev), theta, precision, amc,
+                      net_dev, static_cast<cudaStream_t>(stream));
   } catch (...) {
     return fail(FMM_ERR_NOMEM, "host allocation failed");
   }
@@ -1754,30 +1923,16 @@ int fmm_solve_batch(fmm_tree* f, const double* const* rho_dev, double theta, int
                     int amc, double* const* phi_dev, double* const* g_dev, double* net_dev,
                     void* stream) {
   if (!f || !rho_dev || !phi_dev || !g_dev) return fail(FMM_ERR_ARG, "null argument");
-  int rc = ensure_device(f);
-  if (rc) return rc;
-  const int n = f->h.n_trees;
-  const int64_t total = f->h.n_leaf_sub * kCells;
-  if (!f->d_rho) {
-    CUDA_TRY(dalloc(f, &f->d_rho, sizeof(double) * total));
-    CUDA_TRY(dalloc(f, &f->d_phi, sizeof(double) * total));
-    CUDA_TRY(dalloc(f, &f->d_g, sizeof(double) * 3 * total));
-    CUDA_TRY(dalloc(f, &f->d_net, sizeof(double) * 7 * n));
+  try {
+    std::vector<TreeIo> io(size_t(f->h.n_trees));
+    for (int k = 0; k < f->h.n_trees; ++k) {
+      if (!rho_dev[k] || !phi_dev[k] || !g_dev[k]) return fail(FMM_ERR_ARG, "null per-tree pointer");
+      io[size_t(k)] = TreeIo{rho_dev[k], phi_dev[k], g_dev[k]};
+    }
+    return solve_impl(f, io, theta, precision, amc, net_dev, static_cast<cudaStream_t>(stream));
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
   }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  for (int k = 0; k < n; ++k) {
-    if (!rho_dev[k] || !phi_dev[k] || !g_dev[k]) return fail(FMM_ERR_ARG, "null per-tree pointer");
-    const int64_t o = f->h.tree_leaf_off[k] * kCells, m = (f->h.tree_leaf_off[k + 1] - f->h.tree_leaf_off[k]) * kCells;
-    CUDA_TRY(cudaMemcpyAsync(f->d_rho + o, rho_dev[k], sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
-  }
-  rc = fmm_solve(f, f->d_rho, theta, precision, amc, f->d_phi, f->d_g, net_dev, stream);
-  if (rc) return rc;
-  for (int k = 0; k < n; ++k) {
-    const int64_t o = f->h.tree_leaf_off[k] * kCells, m = (f->h.tree_leaf_off[k + 1] - f->h.tree_leaf_off[k]) * kCells;
-    CUDA_TRY(cudaMemcpyAsync(phi_dev[k], f->d_phi + o, sizeof(double) * m, cudaMemcpyDeviceToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(g_dev[k], f->d_g + 3 * o, sizeof(double) * 3 * m, cudaMemcpyDeviceToDevice, st));
-  }
-  return FMM_OK;
 }
 
 int fmm_sync_status(fmm_tree* t, void* stream) {
@@ -1822,8 +1977,28 @@ int fmm_net_force_torque(fmm_tree* t, const double* rho_dev, const double* g_dev
   if (!t || !rho_dev || !g_dev || !net_dev) return fail(FMM_ERR_ARG, "null argument");
   int rc = ensure_device(t);
   if (rc) return rc;
-  DevArgs A = make_args(t, nullptr);
-  return launch_net(t, A, rho_dev, g_dev, net_dev, static_cast<cudaStream_t>(stream));
+  try {
+    // the reduction reads rho and g through the tree's pointer table, on the tree's stream
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
+    // (the reduction only reads g)
+    std::vector<TreeIo> io = contiguous_io(t, rho_dev, nullptr, const_cast<double*>(g_dev));
+    CUDA_TRY(cudaEventRecord(t->ev_in, caller));
+    CUDA_TRY(cudaStreamWaitEvent(t->stream, t->ev_in, 0));
+    int32_t n_io = 0;
+    if ((rc = set_io(t, io, net_dev, t->stream, &n_io))) return rc;
+    if ((rc = launch_net(t, make_args(t, nullptr), t->stream))) return rc;
+    CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
+    CUDA_TRY(cudaStreamWaitEvent(caller, t->ev_out, 0));
+    return FMM_OK;
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+int fmm_set_graphs(fmm_tree* t, int on) {
+  if (!t) return fail(FMM_ERR_ARG, "tree is null");
+  t->use_graphs = on != 0;
+  return FMM_OK;
 }
 
 int fmm_set_profiling(fmm_tree* t, int on) {
@@ -1860,7 +2035,7 @@ int fmm_net_force_torque_points_static(int64_t n, const double* x_dev, const dou
     k_net_points_partial<<<blocks, kReduceThreads, 0, st>>>(n, x_dev, m_dev, g_dev, scratch);
     CUDA_TRY(cudaGetLastError());
   }
-  k_net_final<<<1, kReduceThreads, 0, st>>>(scratch, blocks, net_dev);
+  k_net_final<<<1, kReduceThreads, 0, st>>>(scratch, blocks, net_dev, nullptr);
   CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }
