@@ -115,7 +115,18 @@ constexpr int kM2LThreads = 64;      // one block = the 64 cells of one parity o
 constexpr int kReduceThreads = 256;
 constexpr int kReduceBlocks = 512;
 
-__device__ __forceinline__ double cell_dx(int lev) { return 1.0 / double(kSub << lev); }
+// Cell width 1 / (8 2^lev), a power of two, assembled from its exponent bits (exact; no divide or
+// conversion, which run on the FP64 pipe).
+__device__ __forceinline__ double cell_dx(int lev) {
+  return __longlong_as_double(int64_t(1023 - 3 - lev) << 52);
+}
+__device__ __forceinline__ float cell_dx32(int lev) { return __int_as_float((127 - 3 - lev) << 23); }
+template <typename T>
+__device__ __forceinline__ T cell_h(int lev);
+template <>
+__device__ __forceinline__ double cell_h<double>(int lev) { return cell_dx(lev); }
+template <>
+__device__ __forceinline__ float cell_h<float>(int lev) { return cell_dx32(lev); }
 
 // Internal order of the 512 cells of a subgrid (the solver's own arrays; user arrays keep
 // (a*8 + b)*8 + c): parity-major, cell (a, b, c) = (2 ia + pa, 2 ib + pb, 2 ic + pc) at
@@ -399,13 +410,14 @@ struct Target {
   bool amc;
 };
 
-// Interaction of target A with one source cell B (same level) at separation R = X_A - X_B.
-template <typename T, bool AREF>
+// Interaction of target A with one source cell B (same level) at separation R = X_A - X_B; BREF:
+// B is refined (full moments), else a point mass.
+template <typename T, bool AREF, bool BREF>
 __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict__ M, int64_t N,
-                                         int64_t iB, bool bref, T x, T y, T z) {
+                                         int64_t iB, T x, T y, T z) {
   T mB = M[iB];
   Radial<T> g;
-  if (bref) {
+  if constexpr (BREF) {
     T dBx = M[N + iB], dBy = M[2 * N + iB], dBz = M[3 * N + iB];
     x -= dBx;
     y -= dBy;
@@ -565,25 +577,18 @@ __device__ __forceinline__ void block_cell(int parity, int t, int& a, int& b, in
   c = 2 * (t & 3) + pz;
 }
 
-// Levels >= 1: target subgrid s, parity p.
-template <typename T, bool AREF>
+// Refined target subgrid s of a level >= 1, parity p: multipole interactions with every stencil
+// partner.  Under proper nesting a refined subgrid has all 26 same-level neighbours, and a leaf
+// partner is a point mass whose centre-of-mass offset and higher moments are stored as zeros, so
+// every pair takes the full multipole formula and a warp never splits on the partner's kind.
+// The correction partial sums are flushed after each chunk of kFlush stencil entries, outside the
+// pair loop: FP64 work under a predicate inside the loop would occupy the FP64 pipe on every pass.
+constexpr int kFlush = 64;
+
+template <typename T>
 __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool amc) {
   __shared__ int32_t nb[27];
-  __shared__ uint8_t nb_ref[27];
-  __shared__ int32_t pnb[27];   // parent's neighbours (leaf targets: coarser direct partners)
-  __shared__ uint8_t pnb_leaf[27];
-  const int tid = threadIdx.x;
-  if (tid < 27) {
-    int32_t q = A.nbr[27 * s + tid];
-    nb[tid] = q;
-    nb_ref[tid] = (q >= 0 && !A.leaf[q]) ? 1 : 0;
-    if (!AREF) {
-      int32_t P = A.parent[s];
-      int32_t pq = A.nbr[27 * P + tid];
-      pnb[tid] = pq;
-      pnb_leaf[tid] = (pq >= 0 && A.leaf[pq]) ? 1 : 0;
-    }
-  }
+  if (threadIdx.x < 27) nb[threadIdx.x] = A.nbr[27 * s + threadIdx.x];
   __syncthreads();
   const int lev = A.level[s];
   const T* __restrict__ M = MomView<T>::get(A);
@@ -591,75 +596,27 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool a
   int a, b, c;
   block_cell(parity, t, a, b, c);
   const int64_t iA = int64_t(s) * kCells + cidx(a, b, c);
-  Target<T, AREF> S;
-  load_target<T, AREF>(S, A, M, iA, amc);
-  const T h = T(cell_dx(lev));
+  Target<T, true> S;
+  load_target<T, true>(S, A, M, iA, amc);
+  const T h = cell_h<T>(lev);
   const int32_t* __restrict__ st = A.ltab_code + parity * kLeafCap;
   const T* __restrict__ td = LeafOffsets<T>::get(A) + int64_t(parity) * kLeafCap * 4;
-  // same-level multipole interactions
-  for (int q = 0; q < A.n_stencil; ++q) {
-    int32_t code = __ldg(st + q);
-    int dx, dy, dz;
-    unpack_offset(code, dx, dy, dz);
-    int px = a + dx, py = b + dy, pz = c + dz;
-    int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
-    int32_t sB = nb[slot];
-    if (sB < 0) continue;
-    int64_t iB = int64_t(sB) * kCells + cidx(px & 7, py & 7, pz & 7);
-    interact<T, AREF>(S, M, N, iB, nb_ref[slot] != 0, S.dAx - __ldg(td + 4 * q) * h,
-                      S.dAy - __ldg(td + 4 * q + 1) * h, S.dAz - __ldg(td + 4 * q + 2) * h);
-    if ((q & 63) == 63) flush(S);
-  }
-  flush(S);
-  if (!AREF) {
-    // direct sums with non-separated cells of the same level: leaves directly, refined cells
-    // through their 8 (leaf) children one level finer
-    const T hc = h * T(0.5);
-    for (int q = 0; q < A.n_near; ++q) {
-      int32_t code = __ldg(A.near + q);
+  for (int q0 = 0; q0 < A.n_stencil; q0 += kFlush) {
+    const int q1 = min(q0 + kFlush, A.n_stencil);
+    for (int q = q0; q < q1; ++q) {
       int dx, dy, dz;
-      unpack_offset(code, dx, dy, dz);
+      unpack_offset(__ldg(st + q), dx, dy, dz);
       int px = a + dx, py = b + dy, pz = c + dz;
       int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
       int32_t sB = nb[slot];
-      if (sB < 0) continue;
-      int lx = px & 7, ly = py & 7, lz = pz & 7;
-      if (!nb_ref[slot]) {
-        int64_t iB = int64_t(sB) * kCells + cidx(lx, ly, lz);
-        interact_point<T, AREF>(S, M[iB], -T(dx) * h, -T(dy) * h, -T(dz) * h);
-      } else {
-        int32_t cs = A.child[8 * sB + ((lx >> 2) << 2 | (ly >> 2) << 1 | (lz >> 2))];
-        for (int o = 0; o < 8; ++o) {
-          int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-          int64_t iC = int64_t(cs) * kCells + cidx((lx & 3) * 2 + ox, (ly & 3) * 2 + oy, (lz & 3) * 2 + oz);
-          // x_A - x_C = (1/2 - o - 2 d) dx_(l+1)
-          interact_point<T, AREF>(S, M[iC], (T(0.5) - T(ox) - T(2 * dx)) * hc,
-                                  (T(0.5) - T(oy) - T(2 * dy)) * hc,
-                                  (T(0.5) - T(oz) - T(2 * dz)) * hc);
-        }
-      }
-    }
-    // direct sums with leaves one level coarser that are not separated from A's parent
-    int32_t P = A.parent[s];
-    int ga = A.ijk[3 * s] * 8 + a, gb = A.ijk[3 * s + 1] * 8 + b, gc = A.ijk[3 * s + 2] * 8 + c;
-    int ja = (ga >> 1) - A.ijk[3 * P] * 8, jb = (gb >> 1) - A.ijk[3 * P + 1] * 8,
-        jc = (gc >> 1) - A.ijk[3 * P + 2] * 8;
-    for (int q = 0; q < A.n_near; ++q) {
-      int32_t code = __ldg(A.near + q);
-      int dx, dy, dz;
-      unpack_offset(code, dx, dy, dz);
-      int px = ja + dx, py = jb + dy, pz = jc + dz;
-      int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
-      if (!pnb_leaf[slot]) continue;
-      int32_t sB = pnb[slot];
+      if (sB < 0) continue;  // only without proper nesting
       int64_t iB = int64_t(sB) * kCells + cidx(px & 7, py & 7, pz & 7);
-      // x_A - x_i = ((g_A & 1) - 1/2 - 2 d) dx_l
-      interact_point<T, AREF>(S, M[iB], (T(ga & 1) - T(0.5) - T(2 * dx)) * h,
-                              (T(gb & 1) - T(0.5) - T(2 * dy)) * h,
-                              (T(gc & 1) - T(0.5) - T(2 * dz)) * h);
+      interact<T, true, true>(S, M, N, iB, S.dAx - __ldg(td + 4 * q) * h,
+                              S.dAy - __ldg(td + 4 * q + 1) * h, S.dAz - __ldg(td + 4 * q + 2) * h);
     }
+    flush(S);
   }
-  store_own<T, AREF>(A, S, iA);
+  store_own<T, true>(A, S, iA);
 }
 
 // Root level: every well-separated pair inside the single root subgrid (no parent criterion);
@@ -675,7 +632,7 @@ __device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chun
   const int64_t base = int64_t(root) * kCells;
   Target<T, AREF> S;
   load_target<T, AREF>(S, A, M, base + iloc, amc);
-  const T h = T(cell_dx(0));
+  const T h = cell_h<T>(0);
   const bool root_leaf = A.leaf[root] != 0;
   // chunk = source x index; source offsets kept as floating-point counters (no conversions)
   const int dx = chunk - a;
@@ -689,7 +646,7 @@ __device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chun
       const int dy = jy - b, dz = jz - c;
       const bool ws = dx * dx + dy * dy + dz * dz > A.ws_d2;
       if (!ws && !root_leaf) continue;
-      interact<T, AREF>(S, M, N, base + j, !root_leaf, rx0, ry, rz);
+      interact<T, AREF, AREF>(S, M, N, base + j, rx0, ry, rz);  // AREF: the root is refined
     }
     if (jy & 1) flush(S);
   }
@@ -743,21 +700,23 @@ __device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, int t, boo
   const int64_t iA = int64_t(s) * kCells + cidx(a, b, c);
   Target<T, false> S;
   load_target<T, false>(S, A, M, iA, amc);
-  const T h = T(cell_dx(lev)), hc = h * T(0.5);
+  const T h = cell_h<T>(lev), hc = h * T(0.5);
   const int32_t* __restrict__ st = A.ltab_code + parity * kLeafCap;
   const T* __restrict__ td = LeafOffsets<T>::get(A) + int64_t(parity) * kLeafCap * 4;
-  for (int q = 0; q < A.n_stencil; ++q) {
-    int dx, dy, dz;
-    unpack_offset(__ldg(st + q), dx, dy, dz);
-    int px = a + dx, py = b + dy, pz = c + dz;
-    int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
-    if (!nb_ref[slot]) continue;
-    int64_t iB = int64_t(nb[slot]) * kCells + cidx(px & 7, py & 7, pz & 7);
-    interact<T, false>(S, M, N, iB, true, -__ldg(td + 4 * q) * h, -__ldg(td + 4 * q + 1) * h,
-                       -__ldg(td + 4 * q + 2) * h);
-    if ((q & 63) == 63) flush(S);
+  for (int q0 = 0; q0 < A.n_stencil; q0 += kFlush) {
+    const int q1 = min(q0 + kFlush, A.n_stencil);
+    for (int q = q0; q < q1; ++q) {
+      int dx, dy, dz;
+      unpack_offset(__ldg(st + q), dx, dy, dz);
+      int px = a + dx, py = b + dy, pz = c + dz;
+      int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
+      if (!nb_ref[slot]) continue;
+      int64_t iB = int64_t(nb[slot]) * kCells + cidx(px & 7, py & 7, pz & 7);
+      interact<T, false, true>(S, M, N, iB, -__ldg(td + 4 * q) * h, -__ldg(td + 4 * q + 1) * h,
+                               -__ldg(td + 4 * q + 2) * h);
+    }
+    flush(S);
   }
-  flush(S);
   for (int q = A.n_stencil; q < A.n_stencil + A.n_near; ++q) {
     int dx, dy, dz;
     unpack_offset(__ldg(st + q), dx, dy, dz);
@@ -824,7 +783,7 @@ __global__ void __launch_bounds__(NT) k_m2l_ref(DevArgs A, const int32_t* __rest
     if (A.leaf[root]) m2l_root<T, false>(A, root, parity, t, chunk, amc != 0);
     else m2l_root<T, true>(A, root, parity, t, chunk, amc != 0);
   } else if (kind == 1) {
-    m2l_level<T, true>(A, idx, parity, t, amc != 0);
+    m2l_level<T>(A, idx, parity, t, amc != 0);
   } else {
     m2l_boundary<T>(A, idx, parity, t, amc != 0);
   }
@@ -884,7 +843,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
     hm[i] = q >= 0 ? M[int64_t(q) * kCells + cidx(x & 7, y & 7, z & 7)] : T(0);
   }
   __syncthreads();
-  const T h = T(cell_dx(A.level[s]));
+  const T h = cell_h<T>(A.level[s]);
   const int parity = t >> 5, lane = t & 31;
   const int px = (parity >> 2) & 1, py = (parity >> 1) & 1, pz = parity & 1;
   const int a0 = 2 * (lane >> 4) + px,  // second target: a0 + 4
@@ -1030,7 +989,7 @@ __global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs) {
     float P32[20], d[4];
 #pragma unroll
     for (int k = 0; k < 20; ++k) P32[k] = A.loc32[k * N + ip];
-    const float h = float(cell_dx(lev));
+    const float h = cell_dx32(lev);
     // r = X_A - X_P = ((g & 1) - 1/2) dx_l - delta_P (a leaf's centre of mass is its centre)
     const float rx = ((ga & 1) ? 0.5f : -0.5f) * h - A.mom32[N + ip];
     const float ry = ((gb & 1) ? 0.5f : -0.5f) * h - A.mom32[2 * N + ip];
