@@ -99,6 +99,15 @@ struct DevArgs {
   float* root_part32;      // [n_roots][kRootChunks][20][512] (mixed path)
   double* root_part_ac;    // [n_roots][kRootChunks][3][512] (mixed path)
   int* status;
+  // boundary pair lists (per theta): leaf target cells at a refinement boundary, sorted by work
+  int64_t n_bt;
+  const int32_t* bt_cell;  // [n_bt] internal cell index of each target
+  const int32_t* bm_off;   // [n_bt + 1] its multipole partners: bm_src / bm_q [bm_off[k], ..)
+  const int32_t* bm_src;   // partner cell (in a refined same-level neighbour)
+  const int32_t* bm_q;     // stencil entry of the partner (offset d in the target's parity table)
+  const int32_t* bp_off;   // [n_bt + 1] its point-mass partners: bp_src / bp_code
+  const int32_t* bp_src;
+  const int32_t* bp_code;  // x_A - x_B in units of dx / 4, three 10-bit fields biased by 512
   const int32_t* leaf_tree;  // [n_leaf_sub] tree of each leaf subgrid
   const TreeIo* io;          // [n_roots] the caller's arrays of each tree
   double* const* io_net;     // the caller's net array (7 numbers per tree), or null
@@ -671,95 +680,50 @@ __device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chun
   }
 }
 
-// Leaf targets of a subgrid at a refinement boundary, one parity: multipole interactions with
-// cells of refined same-level neighbours, direct sums with the leaf children of refined near
-// cells, and direct sums with leaves one level coarser near the parent cell.  Runs after the
-// leaf kernel and adds onto its output.
+// Leaf targets at a refinement boundary, 64 per block, from the pair lists built on the host:
+// multipole interactions with the cells of refined same-level neighbours, then direct sums with
+// point masses (the leaf children of refined near cells, and leaves one level coarser near the
+// parent cell).  The targets are sorted by work, so the lanes of a warp run lists of similar
+// length and no lane scans entries that do not apply to it.  Adds onto the leaf kernel's output.
+constexpr int kCodeMax = 64;  // |point-pair offset| in units of dx / 4
+
 template <typename T>
-__device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, int t, bool amc) {
-  __shared__ int32_t nb[27];
-  __shared__ uint8_t nb_ref[27];
-  __shared__ int32_t pnb[27];
-  __shared__ uint8_t pnb_leaf[27];
-  const int tid = threadIdx.x;
-  if (tid < 27) {
-    int32_t q = A.nbr[27 * s + tid];
-    nb[tid] = q;
-    nb_ref[tid] = (q >= 0 && !A.leaf[q]) ? 1 : 0;
-    int32_t P = A.parent[s];
-    int32_t pq = A.nbr[27 * P + tid];
-    pnb[tid] = pq;
-    pnb_leaf[tid] = (pq >= 0 && A.leaf[pq]) ? 1 : 0;
-  }
+__device__ void m2l_boundary(const DevArgs& A, int chunk, int t, bool amc) {
+  __shared__ T quarter[2 * kCodeMax + 1];  // quarter[i] = (i - kCodeMax) / 4, exact
+  for (int i = threadIdx.x; i <= 2 * kCodeMax; i += blockDim.x) quarter[i] = T(i - kCodeMax) * T(0.25);
   __syncthreads();
-  const int lev = A.level[s];
+  const int64_t k = int64_t(chunk) * 64 + t;
+  if (k >= A.n_bt) return;
+  const int64_t iA = A.bt_cell[k];
+  const int parity = int(iA & 511) >> 6;
   const T* __restrict__ M = MomView<T>::get(A);
   const int64_t N = A.n_cell;
-  int a, b, c;
-  block_cell(parity, t, a, b, c);
-  const int64_t iA = int64_t(s) * kCells + cidx(a, b, c);
   Target<T, false> S;
   load_target<T, false>(S, A, M, iA, amc);
-  const T h = cell_h<T>(lev), hc = h * T(0.5);
-  const int32_t* __restrict__ st = A.ltab_code + parity * kLeafCap;
+  const T h = cell_h<T>(A.level[iA >> 9]);
   const T* __restrict__ td = LeafOffsets<T>::get(A) + int64_t(parity) * kLeafCap * 4;
-  for (int q0 = 0; q0 < A.n_stencil; q0 += kFlush) {
-    const int q1 = min(q0 + kFlush, A.n_stencil);
-    for (int q = q0; q < q1; ++q) {
-      int dx, dy, dz;
-      unpack_offset(__ldg(st + q), dx, dy, dz);
-      int px = a + dx, py = b + dy, pz = c + dz;
-      int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
-      if (!nb_ref[slot]) continue;
-      int64_t iB = int64_t(nb[slot]) * kCells + cidx(px & 7, py & 7, pz & 7);
-      interact<T, false, true>(S, M, N, iB, -__ldg(td + 4 * q) * h, -__ldg(td + 4 * q + 1) * h,
-                               -__ldg(td + 4 * q + 2) * h);
+  const int32_t m1 = A.bm_off[k + 1];
+  for (int32_t j0 = A.bm_off[k]; j0 < m1; j0 += kFlush) {
+    const int32_t j1 = min(j0 + kFlush, m1);
+    for (int32_t j = j0; j < j1; ++j) {
+      const int q = __ldg(A.bm_q + j);
+      interact<T, false, true>(S, M, N, __ldg(A.bm_src + j), -__ldg(td + 4 * q) * h,
+                               -__ldg(td + 4 * q + 1) * h, -__ldg(td + 4 * q + 2) * h);
     }
     flush(S);
   }
-  for (int q = A.n_stencil; q < A.n_stencil + A.n_near; ++q) {
-    int dx, dy, dz;
-    unpack_offset(__ldg(st + q), dx, dy, dz);
-    int px = a + dx, py = b + dy, pz = c + dz;
-    int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
-    if (!nb_ref[slot]) continue;
-    int lx = px & 7, ly = py & 7, lz = pz & 7;
-    int32_t cs = A.child[8 * nb[slot] + ((lx >> 2) << 2 | (ly >> 2) << 1 | (lz >> 2))];
-    // x_A - x_C = (1/2 - o - 2 d) dx_(l+1), o the child's octant
-    const T ex = (T(0.5) - T(2) * __ldg(td + 4 * q)) * hc, ey = (T(0.5) - T(2) * __ldg(td + 4 * q + 1)) * hc,
-            ez = (T(0.5) - T(2) * __ldg(td + 4 * q + 2)) * hc;
-    const int64_t c0 = int64_t(cs) * kCells;
-#pragma unroll
-    for (int o = 0; o < 8; ++o) {
-      const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-      const int cl = cidx((lx & 3) * 2 + ox, (ly & 3) * 2 + oy, (lz & 3) * 2 + oz);
-      interact_point<T, false>(S, M[c0 + cl], ex - (ox ? hc : T(0)),
-                               ey - (oy ? hc : T(0)), ez - (oz ? hc : T(0)));
-    }
+  const int32_t p1 = A.bp_off[k + 1];
+  for (int32_t j = A.bp_off[k]; j < p1; ++j) {
+    const int32_t code = __ldg(A.bp_code + j);
+    const T x = quarter[((code >> 20) & 1023) - 512 + kCodeMax] * h;
+    const T y = quarter[((code >> 10) & 1023) - 512 + kCodeMax] * h;
+    const T z = quarter[(code & 1023) - 512 + kCodeMax] * h;
+    interact_point<T, false>(S, M[__ldg(A.bp_src + j)], x, y, z);
   }
-  const int32_t P = A.parent[s];
-  int ga = A.ijk[3 * s] * 8 + a, gb = A.ijk[3 * s + 1] * 8 + b, gc = A.ijk[3 * s + 2] * 8 + c;
-  int ja = (ga >> 1) - A.ijk[3 * P] * 8, jb = (gb >> 1) - A.ijk[3 * P + 1] * 8,
-      jc = (gc >> 1) - A.ijk[3 * P + 2] * 8;
-  // x_A - x_i = ((g_A & 1) - 1/2 - 2 d) dx_l
-  const T fa = (ga & 1) ? T(0.5) : T(-0.5), fb = (gb & 1) ? T(0.5) : T(-0.5),
-          fc = (gc & 1) ? T(0.5) : T(-0.5);
-  for (int q = A.n_stencil; q < A.n_stencil + A.n_near; ++q) {
-    int dx, dy, dz;
-    unpack_offset(__ldg(st + q), dx, dy, dz);
-    int px = ja + dx, py = jb + dy, pz = jc + dz;
-    int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
-    if (!pnb_leaf[slot]) continue;
-    int64_t iB = int64_t(pnb[slot]) * kCells + cidx(px & 7, py & 7, pz & 7);
-    interact_point<T, false>(S, M[iB], (fa - T(2) * __ldg(td + 4 * q)) * h,
-                             (fb - T(2) * __ldg(td + 4 * q + 1)) * h,
-                             (fc - T(2) * __ldg(td + 4 * q + 2)) * h);
-  }
-  // add onto the leaf kernel's output
   if (sizeof(T) == 8) {
-    for (int k = 0; k < 4; ++k) A.loc[k * N + iA] += double(S.L[k]);
+    for (int c = 0; c < 4; ++c) A.loc[c * N + iA] += double(S.L[c]);
   } else {
-    for (int k = 0; k < 4; ++k) A.loc32[k * N + iA] += float(S.L[k]);
+    for (int c = 0; c < 4; ++c) A.loc32[c * N + iA] += float(S.L[c]);
   }
   A.ac[iA] += S.ax;
   A.ac[N + iA] += S.ay;
@@ -768,7 +732,7 @@ __device__ void m2l_boundary(const DevArgs& A, int32_t s, int parity, int t, boo
 
 // One block per entry of `blocks`, sorted by estimated cost (largest first): code
 // (kind << 30) | (parity << 27) | index, kind 0 = source chunk index & 7 of root index >> 3,
-// 1 = refined subgrid `index`, 2 = leaf subgrid `index` at a refinement boundary.  With NT = 64 a block serves the 64
+// 1 = refined subgrid `index`, 2 = chunk `index` of 64 boundary leaf targets (parity unused).  With NT = 64 a block serves the 64
 // cells of one parity; with NT = 512 it serves all 8 parities of the subgrid (or all 512 root
 // cells), so that every source the subgrid's cells read is fetched into one SM's L1 once.
 template <typename T, int NT>
@@ -785,7 +749,7 @@ __global__ void __launch_bounds__(NT) k_m2l_ref(DevArgs A, const int32_t* __rest
   } else if (kind == 1) {
     m2l_level<T>(A, idx, parity, t, amc != 0);
   } else {
-    m2l_boundary<T>(A, idx, parity, t, amc != 0);
+    m2l_boundary<T>(A, idx, t, amc != 0);
   }
 }
 
@@ -1153,6 +1117,10 @@ struct StencilDev {
   float* d_ltab_d32 = nullptr;
   int32_t* d_blocks = nullptr;     // general-kernel blocks (one parity each) for this tree, theta
   int64_t n_blocks = 0;
+  // boundary pair lists (see DevArgs)
+  int64_t n_bt = 0;
+  int32_t *d_bt_cell = nullptr, *d_bm_off = nullptr, *d_bm_src = nullptr, *d_bm_q = nullptr,
+          *d_bp_off = nullptr, *d_bp_src = nullptr, *d_bp_code = nullptr;
 
   int n_stencil = 0, n_near = 0;
   int ws_d2 = 0;
@@ -1164,7 +1132,7 @@ struct fmm_tree {
   bool dev_ready = false, mixed_ready = false;
   int32_t *d_level = nullptr, *d_ijk = nullptr, *d_parent = nullptr, *d_child = nullptr,
           *d_nbr = nullptr, *d_leaf_sub = nullptr, *d_leaf_ord = nullptr, *d_work = nullptr,
-          *d_work_leaf = nullptr, *d_work_bnd = nullptr, *d_refined = nullptr;
+          *d_work_leaf = nullptr, *d_refined = nullptr;
   int64_t n_work_leaf = 0, n_work_bnd = 0;
   uint8_t* d_leaf = nullptr;
   std::vector<int64_t> refined_off;  // offsets into d_refined per level
@@ -1266,7 +1234,6 @@ static int ensure_device(fmm_tree* t) {
   t->work_bnd = work_bnd;
   CUDA_TRY(upload(t, &t->d_work, work));
   CUDA_TRY(upload(t, &t->d_work_leaf, work_leaf));
-  CUDA_TRY(upload(t, &t->d_work_bnd, work_bnd));
   t->refined_off.assign(h.depth + 2, 0);
   for (int l = 0; l <= h.depth; ++l) {
     refined.insert(refined.end(), h.refined_at[l].begin(), h.refined_at[l].end());
@@ -1316,15 +1283,134 @@ static int32_t block_code(uint32_t kind, uint32_t parity, uint32_t index) {
   return int32_t((kind << 30) | (parity << 27) | index);
 }
 
+// Host copy of the internal cell order (parity-major inside a subgrid).
+static inline int host_cidx(int a, int b, int c) {
+  return (((a & 1) << 2 | (b & 1) << 1 | (c & 1)) << 6) | (a >> 1) << 4 | (b >> 1) << 2 | (c >> 1);
+}
+static inline int slot_of(int p) { return p < 0 ? 0 : (p < 8 ? 1 : 2); }
+
+// Pair lists of the leaf targets at refinement boundaries (Sec. 2.2 same-level interactions,
+// with the mixed-level pairs read as direct sums): for every cell of every boundary leaf subgrid,
+//   - multipole partners: stencil entries that land in a refined same-level neighbour;
+//   - point-mass partners: the 8 leaf children of each near entry in a refined same-level
+//     neighbour, and the near entries of the parent cell that land in a leaf one level coarser.
+// Targets without partners are dropped; the rest are sorted by estimated work, largest first.
+struct BoundaryLists {
+  std::vector<int32_t> cell, m_off, m_src, m_q, p_off, p_src, p_code;
+  std::vector<double> cost;  // per target, in the order of `cell`
+};
+
+static std::string boundary_lists(const HostTree& h, const Stencil& st,
+                                  const std::vector<int32_t>& work_bnd, BoundaryLists& out) {
+  const double c_m = 150, c_p = 20;
+  struct Tgt {
+    int32_t cell;
+    std::vector<int32_t> ms, mq, ps, pc;
+  };
+  std::vector<Tgt> tg;
+  auto code3 = [](int x, int y, int z) {
+    return int32_t((uint32_t(x + 512) << 20) | (uint32_t(y + 512) << 10) | uint32_t(z + 512));
+  };
+  for (int32_t s : work_bnd) {
+    int32_t nb[27], pnb[27];
+    bool nb_ref[27], pnb_leaf[27];
+    const int32_t P = h.parent[s];
+    for (int k = 0; k < 27; ++k) {
+      nb[k] = h.nbr[27 * s + k];
+      nb_ref[k] = nb[k] >= 0 && !h.leaf[nb[k]];
+      pnb[k] = h.nbr[27 * P + k];
+      pnb_leaf[k] = pnb[k] >= 0 && h.leaf[pnb[k]];
+    }
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b)
+        for (int c = 0; c < 8; ++c) {
+          const int par = (a & 1) << 2 | (b & 1) << 1 | (c & 1);
+          Tgt e;
+          e.cell = int32_t(int64_t(s) * kCells + host_cidx(a, b, c));
+          const auto& offs = st.offs[par];
+          for (size_t q = 0; q < offs.size(); ++q) {
+            int dx, dy, dz;
+            unpack_offset(offs[q], dx, dy, dz);
+            const int px = a + dx, py = b + dy, pz = c + dz;
+            const int sl = slot_of(px) * 9 + slot_of(py) * 3 + slot_of(pz);
+            if (!nb_ref[sl]) continue;
+            e.ms.push_back(int32_t(int64_t(nb[sl]) * kCells + host_cidx(px & 7, py & 7, pz & 7)));
+            e.mq.push_back(int32_t(q));
+          }
+          for (int32_t code : st.near) {
+            int dx, dy, dz;
+            unpack_offset(code, dx, dy, dz);
+            const int px = a + dx, py = b + dy, pz = c + dz;
+            const int sl = slot_of(px) * 9 + slot_of(py) * 3 + slot_of(pz);
+            if (!nb_ref[sl]) continue;
+            const int lx = px & 7, ly = py & 7, lz = pz & 7;
+            const int32_t cs = h.child[8 * nb[sl] + ((lx >> 2) << 2 | (ly >> 2) << 1 | (lz >> 2))];
+            for (int o = 0; o < 8; ++o) {
+              const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+              e.ps.push_back(int32_t(int64_t(cs) * kCells +
+                                     host_cidx((lx & 3) * 2 + ox, (ly & 3) * 2 + oy, (lz & 3) * 2 + oz)));
+              // x_A - x_C = (1/2 - o - 2 d) dx_(l+1) = (1 - 2 o - 4 d) dx_l / 4
+              e.pc.push_back(code3(1 - 2 * ox - 4 * dx, 1 - 2 * oy - 4 * dy, 1 - 2 * oz - 4 * dz));
+            }
+          }
+          const int ga = h.ijk[3 * s] * 8 + a, gb = h.ijk[3 * s + 1] * 8 + b, gc = h.ijk[3 * s + 2] * 8 + c;
+          const int ja = (ga >> 1) - h.ijk[3 * P] * 8, jb = (gb >> 1) - h.ijk[3 * P + 1] * 8,
+                    jc = (gc >> 1) - h.ijk[3 * P + 2] * 8;
+          for (int32_t code : st.near) {
+            int dx, dy, dz;
+            unpack_offset(code, dx, dy, dz);
+            const int px = ja + dx, py = jb + dy, pz = jc + dz;
+            const int sl = slot_of(px) * 9 + slot_of(py) * 3 + slot_of(pz);
+            if (!pnb_leaf[sl]) continue;
+            e.ps.push_back(int32_t(int64_t(pnb[sl]) * kCells + host_cidx(px & 7, py & 7, pz & 7)));
+            // x_A - x_i = ((g_A & 1) - 1/2 - 2 d) dx_l = (4 (g_A & 1) - 2 - 8 d) dx_l / 4
+            e.pc.push_back(code3(4 * (ga & 1) - 2 - 8 * dx, 4 * (gb & 1) - 2 - 8 * dy,
+                                 4 * (gc & 1) - 2 - 8 * dz));
+          }
+          if (!e.ms.empty() || !e.ps.empty()) tg.push_back(std::move(e));
+        }
+  }
+  for (const Tgt& e : tg)
+    for (int32_t code : e.pc)
+      for (int f = 0; f < 3; ++f) {
+        const int v = int((uint32_t(code) >> (20 - 10 * f)) & 1023u) - 512;
+        if (v < -kCodeMax || v > kCodeMax) return "point-pair offset outside the table";
+      }
+  std::vector<double> cost(tg.size());
+  std::vector<size_t> order(tg.size());
+  for (size_t k = 0; k < tg.size(); ++k) {
+    cost[k] = c_m * double(tg[k].ms.size()) + c_p * double(tg[k].ps.size());
+    order[k] = k;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+  out = BoundaryLists();
+  out.m_off.push_back(0);
+  out.p_off.push_back(0);
+  for (size_t k : order) {
+    const Tgt& e = tg[k];
+    out.cell.push_back(e.cell);
+    out.cost.push_back(cost[k]);
+    out.m_src.insert(out.m_src.end(), e.ms.begin(), e.ms.end());
+    out.m_q.insert(out.m_q.end(), e.mq.begin(), e.mq.end());
+    out.p_src.insert(out.p_src.end(), e.ps.begin(), e.ps.end());
+    out.p_code.insert(out.p_code.end(), e.pc.begin(), e.pc.end());
+    if (out.m_src.size() > size_t(INT32_MAX) || out.p_src.size() > size_t(INT32_MAX))
+      return "boundary pair lists exceed 2^31 entries";
+    out.m_off.push_back(int32_t(out.m_src.size()));
+    out.p_off.push_back(int32_t(out.p_src.size()));
+  }
+  return "";
+}
+
 // Block list of the general interaction kernel, sorted by an estimate of each block's work
 // (pairs times a per-kind cost in FP64 instructions), largest first, so that the long blocks
 // start early and the short ones fill the tail.
 static std::vector<int32_t> general_blocks(const HostTree& h, const Stencil& st,
                                            const std::vector<int32_t>& work,
-                                           const std::vector<int32_t>& work_bnd, bool whole) {
-  const double c_rr = 230, c_rl = 140, c_lr = 150, c_pt = 20, c_iter = 4;
+                                           const BoundaryLists& bnd, bool whole) {
+  const double c_rr = 230, c_pt = 20, c_iter = 4;
   // per target parity: how many (cell, offset) pairs land in each neighbour slot
-  double st_slot[8][27] = {}, nr_slot[8][27] = {}, co_slot[8][8][27] = {};
+  double st_slot[8][27] = {};
   for (int c = 0; c < kCells; ++c) {
     int a = c / 64, b = (c / 8) % 8, z = c % 8;
     int par = (a & 1) << 2 | (b & 1) << 1 | (z & 1);
@@ -1332,16 +1418,6 @@ static std::vector<int32_t> general_blocks(const HostTree& h, const Stencil& st,
       int dx, dy, dz;
       unpack_offset(code, dx, dy, dz);
       st_slot[par][((a + dx) >> 3) * 9 + ((b + dy) >> 3) * 3 + ((z + dz) >> 3) + 13]++;
-    }
-    for (int32_t code : st.near) {
-      int dx, dy, dz;
-      unpack_offset(code, dx, dy, dz);
-      nr_slot[par][((a + dx) >> 3) * 9 + ((b + dy) >> 3) * 3 + ((z + dz) >> 3) + 13]++;
-      for (int o = 0; o < 8; ++o) {  // octant of the subgrid within its parent
-        int ja = 4 * ((o >> 2) & 1) + (a >> 1) + dx, jb = 4 * ((o >> 1) & 1) + (b >> 1) + dy,
-            jc = 4 * (o & 1) + (z >> 1) + dz;
-        co_slot[o][par][(ja >> 3) * 9 + (jb >> 3) * 3 + (jc >> 3) + 13]++;
-      }
     }
   }
   std::vector<std::pair<double, int32_t>> items;
@@ -1355,23 +1431,14 @@ static std::vector<int32_t> general_blocks(const HostTree& h, const Stencil& st,
       double cost = c_iter * 64 * double(st.offs[p].size());
       for (int k = 0; k < 27; ++k) {
         int32_t q = h.nbr[27 * s + k];
-        if (q >= 0) cost += st_slot[p][k] * (h.leaf[q] ? c_rl : c_rr);
+        if (q >= 0) cost += st_slot[p][k] * c_rr;  // leaf partners take the full formula too
       }
       items.push_back({cost, block_code(1, p, s)});
     }
-  for (int32_t s : work_bnd) {
-    const int32_t P = h.parent[s];
-    const int o = int((h.ijk[3 * s] & 1) << 2 | (h.ijk[3 * s + 1] & 1) << 1 | (h.ijk[3 * s + 2] & 1));
-    for (int p = 0; p < 8; ++p) {
-      double cost = c_iter * 64 * double(st.offs[p].size() + 2 * st.near.size());
-      for (int k = 0; k < 27; ++k) {
-        int32_t q = h.nbr[27 * s + k];
-        if (q >= 0 && !h.leaf[q]) cost += st_slot[p][k] * c_lr + nr_slot[p][k] * 8 * c_pt;
-        int32_t pq = h.nbr[27 * P + k];
-        if (pq >= 0 && h.leaf[pq]) cost += co_slot[o][p][k] * c_pt;
-      }
-      items.push_back({cost, block_code(2, p, s)});
-    }
+  for (size_t c = 0; c * 64 < bnd.cell.size(); ++c) {
+    double cost = 0;
+    for (size_t k = c * 64; k < std::min(bnd.cell.size(), c * 64 + 64); ++k) cost += bnd.cost[k];
+    items.push_back({cost, block_code(2, 0, uint32_t(c))});
   }
   if (whole) {
     // merge the 8 parity items of each unit into one item (code with parity 0)
@@ -1441,7 +1508,18 @@ static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
     CUDA_TRY(upload(t, &sd.d_ltab_k32, lk32));
     CUDA_TRY(upload(t, &sd.d_ltab_d64, ld));
     CUDA_TRY(upload(t, &sd.d_ltab_d32, ld32));
-    std::vector<int32_t> blocks = general_blocks(t->h, st, t->work, t->work_bnd, false);
+    BoundaryLists bl;
+    std::string err = boundary_lists(t->h, st, t->work_bnd, bl);
+    if (!err.empty()) return fail(FMM_ERR_ARG, err);
+    sd.n_bt = int64_t(bl.cell.size());
+    CUDA_TRY(upload(t, &sd.d_bt_cell, bl.cell));
+    CUDA_TRY(upload(t, &sd.d_bm_off, bl.m_off));
+    CUDA_TRY(upload(t, &sd.d_bm_src, bl.m_src));
+    CUDA_TRY(upload(t, &sd.d_bm_q, bl.m_q));
+    CUDA_TRY(upload(t, &sd.d_bp_off, bl.p_off));
+    CUDA_TRY(upload(t, &sd.d_bp_src, bl.p_src));
+    CUDA_TRY(upload(t, &sd.d_bp_code, bl.p_code));
+    std::vector<int32_t> blocks = general_blocks(t->h, st, t->work, bl, false);
     sd.n_blocks = int64_t(blocks.size());
     CUDA_TRY(upload(t, &sd.d_blocks, blocks));
 
@@ -1497,6 +1575,14 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.root_part32 = t->d_root_part32;
   A.root_part_ac = t->d_root_part_ac;
   A.status = t->d_status;
+  A.n_bt = sd ? sd->n_bt : 0;
+  A.bt_cell = sd ? sd->d_bt_cell : nullptr;
+  A.bm_off = sd ? sd->d_bm_off : nullptr;
+  A.bm_src = sd ? sd->d_bm_src : nullptr;
+  A.bm_q = sd ? sd->d_bm_q : nullptr;
+  A.bp_off = sd ? sd->d_bp_off : nullptr;
+  A.bp_src = sd ? sd->d_bp_src : nullptr;
+  A.bp_code = sd ? sd->d_bp_code : nullptr;
   A.leaf_tree = t->d_leaf_tree;
   A.io = t->d_io;
   A.io_net = t->d_io_net;
