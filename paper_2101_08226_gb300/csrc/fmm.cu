@@ -130,6 +130,18 @@ __device__ __forceinline__ double cell_dx(int lev) {
   return __longlong_as_double(int64_t(1023 - 3 - lev) << 52);
 }
 __device__ __forceinline__ float cell_dx32(int lev) { return __int_as_float((127 - 3 - lev) << 23); }
+__device__ __forceinline__ double cell_vol(int lev) {
+  return __longlong_as_double(int64_t(1023 - 3 * (3 + lev)) << 52);
+}
+// The double n 2^-k of a nonzero integer |n| < 2^31, assembled from integer operations (an
+// int-to-double conversion runs on the FP64 pipe): sign, exponent of the leading bit, mantissa.
+__device__ __forceinline__ double dyadic(int n, int k) {
+  const uint32_t a = uint32_t(n < 0 ? -n : n);
+  const int e = 31 - __clz(int(a));
+  const uint64_t mant = (uint64_t(a) << (52 - e)) & ((1ull << 52) - 1);
+  const uint64_t bits = (uint64_t(n < 0) << 63) | (uint64_t(1023 + e - k) << 52) | mant;
+  return __longlong_as_double(int64_t(bits));
+}
 template <typename T>
 __device__ __forceinline__ T cell_h(int lev);
 template <>
@@ -164,13 +176,15 @@ __global__ void k_p2m(DevArgs A, int mixed) {
   int64_t cell = int64_t(s) * kCells + cidx(u >> 6, (u >> 3) & 7, u & 7);
   const int k = A.leaf_tree[i >> 9];
   double r = A.io[k].rho[i - A.tree_leaf_off[k] * kCells];
-  if (!(r >= 0.0) || !isfinite(r)) {
+  // finite and >= 0, tested on the bit pattern (a double compare runs on the FP64 pipe): +0 up to
+  // the largest finite value lie below the exponent mask, and -0 is the sign bit alone
+  const uint64_t bits = uint64_t(__double_as_longlong(r));
+  if (!(bits < 0x7ff0000000000000ull || bits == 0x8000000000000000ull)) {
     atomicOr(A.status, 1);
     r = 0.0;
   }
-  double h = cell_dx(lev);
   // the other 19 moments of a leaf cell stay zero from the workspace initialisation
-  const double m = r * h * h * h;
+  const double m = r * cell_vol(lev);
   A.mom[cell] = m;
   A.mtl[cell] = m;
   if (mixed) A.mom32[cell] = float(m);
@@ -179,73 +193,12 @@ __global__ void k_p2m(DevArgs A, int mixed) {
 // ----------------------------------------------------------------------------------------------
 // m2m: moments of a refined cell from its 8 children (exact shift to the parent's centre of mass)
 // ----------------------------------------------------------------------------------------------
-// One thread per parent cell, for levels with enough cells to fill the GPU.
-__global__ void k_m2m_cell(DevArgs A, const int32_t* __restrict__ subs, int n_subs, int mixed) {
-  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= int64_t(n_subs) * kCells) return;
-  int32_t s = subs[t >> 9];
-  int loc = int(t & 511);
-  int a, b, c;
-  cdecode(loc, a, b, c);
-  int lev = A.level[s];
-  int32_t cs = A.child[8 * s + ((a >> 2) << 2 | (b >> 2) << 1 | (c >> 2))];
+// Writes the moments of one refined cell: raw (m, delta, M2, M3), detraced, and the FP32 copy of
+// the detraced set (mixed path).
+__device__ __forceinline__ void store_moments(const DevArgs& A, int64_t cell, double mt, double dx,
+                                              double dy, double dz, const double* M2,
+                                              const double* M3, int mixed) {
   const int64_t N = A.n_cell;
-  double hc = cell_dx(lev + 1);
-  // children positions relative to the parent's geometric centre
-  double m[8], u[8][3];
-  int64_t ci[8];
-  double mt = 0, sx = 0, sy = 0, sz = 0;
-#pragma unroll
-  for (int o = 0; o < 8; ++o) {
-    int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-    int cl = cidx((a & 3) * 2 + ox, (b & 3) * 2 + oy, (c & 3) * 2 + oz);
-    ci[o] = int64_t(cs) * kCells + cl;
-    m[o] = A.mom[ci[o]];
-    u[o][0] = (ox - 0.5) * hc + A.mom[N + ci[o]];
-    u[o][1] = (oy - 0.5) * hc + A.mom[2 * N + ci[o]];
-    u[o][2] = (oz - 0.5) * hc + A.mom[3 * N + ci[o]];
-    mt += m[o];
-    sx += m[o] * u[o][0];
-    sy += m[o] * u[o][1];
-    sz += m[o] * u[o][2];
-  }
-  double dx = 0, dy = 0, dz = 0;
-  if (mt > 0) {
-    const double inv = 1.0 / mt;
-    dx = sx * inv;
-    dy = sy * inv;
-    dz = sz * inv;
-  }
-  double M2[6] = {0, 0, 0, 0, 0, 0}, M3[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-#pragma unroll
-  for (int o = 0; o < 8; ++o) {
-    double rx = u[o][0] - dx, ry = u[o][1] - dy, rz = u[o][2] - dz;
-    double q[6], p[10];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) q[k] = A.mom[(4 + k) * N + ci[o]];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) p[k] = A.mom[(10 + k) * N + ci[o]];
-    double mo = m[o];
-    M2[0] += q[0] + mo * rx * rx;
-    M2[1] += q[1] + mo * rx * ry;
-    M2[2] += q[2] + mo * rx * rz;
-    M2[3] += q[3] + mo * ry * ry;
-    M2[4] += q[4] + mo * ry * rz;
-    M2[5] += q[5] + mo * rz * rz;
-    // M3_abc += M3c_abc + r_a M2c_bc + r_b M2c_ac + r_c M2c_ab + m r_a r_b r_c
-    // q: xx0 xy1 xz2 yy3 yz4 zz5
-    M3[0] += p[0] + 3 * rx * q[0] + mo * rx * rx * rx;
-    M3[1] += p[1] + 2 * rx * q[1] + ry * q[0] + mo * rx * rx * ry;
-    M3[2] += p[2] + 2 * rx * q[2] + rz * q[0] + mo * rx * rx * rz;
-    M3[3] += p[3] + rx * q[3] + 2 * ry * q[1] + mo * rx * ry * ry;
-    M3[4] += p[4] + rx * q[4] + ry * q[2] + rz * q[1] + mo * rx * ry * rz;
-    M3[5] += p[5] + rx * q[5] + 2 * rz * q[2] + mo * rx * rz * rz;
-    M3[6] += p[6] + 3 * ry * q[3] + mo * ry * ry * ry;
-    M3[7] += p[7] + 2 * ry * q[4] + rz * q[3] + mo * ry * ry * rz;
-    M3[8] += p[8] + ry * q[5] + 2 * rz * q[4] + mo * ry * rz * rz;
-    M3[9] += p[9] + 3 * rz * q[5] + mo * rz * rz * rz;
-  }
-  int64_t cell = int64_t(s) * kCells + loc;
   A.mom[cell] = mt;
   A.mom[N + cell] = dx;
   A.mom[2 * N + cell] = dy;
@@ -254,119 +207,6 @@ __global__ void k_m2m_cell(DevArgs A, const int32_t* __restrict__ subs, int n_su
   for (int k = 0; k < 6; ++k) A.mom[(4 + k) * N + cell] = M2[k];
 #pragma unroll
   for (int k = 0; k < 10; ++k) A.mom[(10 + k) * N + cell] = M3[k];
-  // detraced copies for the interactions
-  const double tr3 = (M2[0] + M2[3] + M2[5]) * (1.0 / 3.0);
-  const double tx = (M3[0] + M3[3] + M3[5]) * 0.2, ty = (M3[1] + M3[6] + M3[8]) * 0.2,
-               tz = (M3[2] + M3[7] + M3[9]) * 0.2;
-  const double M2t[6] = {M2[0] - tr3, M2[1], M2[2], M2[3] - tr3, M2[4], M2[5] - tr3};
-  const double M3t[10] = {M3[0] - 3 * tx, M3[1] - ty,     M3[2] - tz, M3[3] - tx, M3[4],
-                          M3[5] - tx,     M3[6] - 3 * ty, M3[7] - tz, M3[8] - ty, M3[9] - 3 * tz};
-  A.mtl[cell] = mt;
-  A.mtl[N + cell] = dx;
-  A.mtl[2 * N + cell] = dy;
-  A.mtl[3 * N + cell] = dz;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) A.mtl[(4 + k) * N + cell] = M2t[k];
-#pragma unroll
-  for (int k = 0; k < 10; ++k) A.mtl[(10 + k) * N + cell] = M3t[k];
-  if (mixed) {
-    A.mom32[cell] = float(mt);
-    A.mom32[N + cell] = float(dx);
-    A.mom32[2 * N + cell] = float(dy);
-    A.mom32[3 * N + cell] = float(dz);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) A.mom32[(4 + k) * N + cell] = float(M2t[k]);
-#pragma unroll
-    for (int k = 0; k < 10; ++k) A.mom32[(10 + k) * N + cell] = float(M3t[k]);
-  }
-}
-
-// Sum over the 8 lanes of an aligned group, in a fixed order, result in the group's first lane.
-__device__ __forceinline__ double group8_sum(double v) {
-  v += __shfl_down_sync(0xffffffffu, v, 4);
-  v += __shfl_down_sync(0xffffffffu, v, 2);
-  v += __shfl_down_sync(0xffffffffu, v, 1);
-  return v;
-}
-
-// Eight threads per parent cell, one per child, for the coarse levels (FP64 is 1/64 of the FP32
-// rate on this part, so a level of a few subgrids would otherwise run on a few SMs; the shuffle
-// sums add redundant FP64 work, which only pays where cells are few).  The grid covers n_subs * 512 * 8 threads, a
-// multiple of the block size, so every warp is complete for the shuffles.
-constexpr int kM2MThreads = 256;
-constexpr int64_t kM2MCellMin = 16384;  // refined cells of a level from which one thread per cell wins
-__global__ void __launch_bounds__(kM2MThreads) k_m2m(DevArgs A, const int32_t* __restrict__ subs, int mixed) {
-  const int64_t t = int64_t(blockIdx.x) * kM2MThreads + threadIdx.x;
-  const int o = int(t & 7);
-  const int lead = int(threadIdx.x & 31) & ~7;
-  const int64_t pc = t >> 3;
-  const int32_t s = subs[pc >> 9];
-  const int loc = int(pc & 511);
-  int a, b, c;
-  cdecode(loc, a, b, c);
-  const int lev = A.level[s];
-  const int32_t cs = A.child[8 * s + ((a >> 2) << 2 | (b >> 2) << 1 | (c >> 2))];
-  const int64_t N = A.n_cell;
-  const double hc = cell_dx(lev + 1);
-  const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-  const int64_t ci = int64_t(cs) * kCells + cidx((a & 3) * 2 + ox, (b & 3) * 2 + oy, (c & 3) * 2 + oz);
-  // this child's centre of mass relative to the parent's geometric centre
-  const double m = A.mom[ci];
-  const double ux = (ox - 0.5) * hc + A.mom[N + ci], uy = (oy - 0.5) * hc + A.mom[2 * N + ci],
-               uz = (oz - 0.5) * hc + A.mom[3 * N + ci];
-  double mt = group8_sum(m), sx = group8_sum(m * ux), sy = group8_sum(m * uy),
-         sz = group8_sum(m * uz);
-  mt = __shfl_sync(0xffffffffu, mt, lead);
-  sx = __shfl_sync(0xffffffffu, sx, lead);
-  sy = __shfl_sync(0xffffffffu, sy, lead);
-  sz = __shfl_sync(0xffffffffu, sz, lead);
-  double dx = 0, dy = 0, dz = 0;
-  if (mt > 0) {
-    const double inv = 1.0 / mt;
-    dx = sx * inv;
-    dy = sy * inv;
-    dz = sz * inv;
-  }
-  const double rx = ux - dx, ry = uy - dy, rz = uz - dz;
-  double q[6], p[10];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) q[k] = A.mom[(4 + k) * N + ci];
-#pragma unroll
-  for (int k = 0; k < 10; ++k) p[k] = A.mom[(10 + k) * N + ci];
-  // this child's share: M2c + m r r, M3c + r_a M2c_bc + r_b M2c_ac + r_c M2c_ab + m r r r
-  // q: xx0 xy1 xz2 yy3 yz4 zz5
-  double M2[6], M3[10];
-  M2[0] = q[0] + m * rx * rx;
-  M2[1] = q[1] + m * rx * ry;
-  M2[2] = q[2] + m * rx * rz;
-  M2[3] = q[3] + m * ry * ry;
-  M2[4] = q[4] + m * ry * rz;
-  M2[5] = q[5] + m * rz * rz;
-  M3[0] = p[0] + 3 * rx * q[0] + m * rx * rx * rx;
-  M3[1] = p[1] + 2 * rx * q[1] + ry * q[0] + m * rx * rx * ry;
-  M3[2] = p[2] + 2 * rx * q[2] + rz * q[0] + m * rx * rx * rz;
-  M3[3] = p[3] + rx * q[3] + 2 * ry * q[1] + m * rx * ry * ry;
-  M3[4] = p[4] + rx * q[4] + ry * q[2] + rz * q[1] + m * rx * ry * rz;
-  M3[5] = p[5] + rx * q[5] + 2 * rz * q[2] + m * rx * rz * rz;
-  M3[6] = p[6] + 3 * ry * q[3] + m * ry * ry * ry;
-  M3[7] = p[7] + 2 * ry * q[4] + rz * q[3] + m * ry * ry * rz;
-  M3[8] = p[8] + ry * q[5] + 2 * rz * q[4] + m * ry * rz * rz;
-  M3[9] = p[9] + 3 * rz * q[5] + m * rz * rz * rz;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) M2[k] = group8_sum(M2[k]);
-#pragma unroll
-  for (int k = 0; k < 10; ++k) M3[k] = group8_sum(M3[k]);
-  if (o != 0) return;
-  const int64_t cell = int64_t(s) * kCells + loc;
-  A.mom[cell] = mt;
-  A.mom[N + cell] = dx;
-  A.mom[2 * N + cell] = dy;
-  A.mom[3 * N + cell] = dz;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) A.mom[(4 + k) * N + cell] = M2[k];
-#pragma unroll
-  for (int k = 0; k < 10; ++k) A.mom[(10 + k) * N + cell] = M3[k];
-  // detraced copies for the interactions (and their FP32 copies for the mixed path)
   const double tr3 = (M2[0] + M2[3] + M2[5]) * (1.0 / 3.0);
   const double tx = (M3[0] + M3[3] + M3[5]) * 0.2, ty = (M3[1] + M3[6] + M3[8]) * 0.2,
                tz = (M3[2] + M3[7] + M3[9]) * 0.2;
@@ -381,6 +221,180 @@ __global__ void __launch_bounds__(kM2MThreads) k_m2m(DevArgs A, const int32_t* _
   }
 }
 
+// Parent cells go by child octant: thread u of octant o of subgrid s takes parent cell
+// (4 o_a + u_a, 4 o_b + u_b, 4 o_c + u_c), whose 8 children are cells (2 u + e) of child subgrid
+// child[s][o], internal index (e << 6) | u: a warp reads one child subgrid, coalesced.  The host
+// lists each level's octants twice, by the kind of their child subgrid; each kind has its own
+// kernel, and a cell's arithmetic depends only on its children, not on what else is solved.
+__device__ __forceinline__ void octant_cell(int o, int u, int& a, int& b, int& c) {
+  a = 4 * (o >> 2) + (u >> 4);
+  b = 4 * ((o >> 1) & 1) + ((u >> 2) & 3);
+  c = 4 * (o & 1) + (u & 3);
+}
+
+// Octants whose children are leaves, one thread per parent cell.  The children are point masses
+// m_e at offsets s_e w (s_e = +-1 per axis, w = dx_(l+1) / 2) from the parent cell's centre, so
+// their moments about that centre are sign sums: the 8-point Walsh-Hadamard transform of the
+// masses gives M = sum m, D_a = sum s_a m, Q_ab = sum s_a s_b m, W = sum s_x s_y s_z m, with
+// sum m u_a u_b = w^2 (M or Q_ab) and sum m u_a u_b u_c = w^3 (D_a if a = b = c, D_c if a = b != c,
+// W for x y z).  Shifted to the centre of mass delta = w D / M (parallel axes, sum m (u - delta)
+// = 0), with G_ab = M (a = b) or Q_ab:
+//   M2_ab = w^2 G_ab - w D_a delta_b,
+//   M3_abc = w^3 H_abc - w^2 (delta_a G_bc + delta_b G_ac + delta_c G_ab) + 2 w D_a delta_b delta_c.
+__global__ void __launch_bounds__(64) k_m2m_walsh(DevArgs A, const int32_t* __restrict__ octs, int mixed) {
+  const int32_t code = octs[blockIdx.x];
+  const int32_t s = code >> 3;
+  const int o = code & 7, u = int(threadIdx.x);
+  int a, b, c;
+  octant_cell(o, u, a, b, c);
+  const int64_t c0 = int64_t(A.child[8 * s + o]) * kCells + u;  // child e at c0 + (e << 6)
+  double v[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) v[e] = A.mom[c0 + (e << 6)];
+  // in-place transform over the bits of e (z, y, x): afterwards v[k] = sum_e prod_(bit in k) s_bit m_e
+#pragma unroll
+  for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (!(e & bit)) {
+        const double lo = v[e], hi = v[e | bit];
+        v[e] = hi + lo;
+        v[e | bit] = hi - lo;
+      }
+  // v[0] = M, v[4] = D_x, v[2] = D_y, v[1] = D_z, v[6] = Q_xy, v[5] = Q_xz, v[3] = Q_yz, v[7] = W
+  const double mt = v[0];
+  const double w = 0.5 * cell_dx(A.level[s] + 1), w2 = w * w, w3 = w2 * w;
+  const double Dx = v[4], Dy = v[2], Dz = v[1], Qxy = v[6], Qxz = v[5], Qyz = v[3], W = v[7];
+  double dx = 0, dy = 0, dz = 0;
+  if (mt > 0) {
+    const double f = w / mt;
+    dx = f * Dx;
+    dy = f * Dy;
+    dz = f * Dz;
+  }
+  const double ex = w * Dx, ey = w * Dy, ez = w * Dz;  // = M delta
+  double M2[6], M3[10];
+  M2[0] = w2 * mt - ex * dx;
+  M2[1] = w2 * Qxy - ex * dy;
+  M2[2] = w2 * Qxz - ex * dz;
+  M2[3] = w2 * mt - ey * dy;
+  M2[4] = w2 * Qyz - ey * dz;
+  M2[5] = w2 * mt - ez * dz;
+  // M3: xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz
+  const double gx = w2 * dx, gy = w2 * dy, gz = w2 * dz;  // w^2 delta
+  M3[0] = w3 * Dx - 3 * gx * mt + 2 * ex * dx * dx;
+  M3[1] = w3 * Dy - (2 * gx * Qxy + gy * mt) + 2 * ex * dx * dy;
+  M3[2] = w3 * Dz - (2 * gx * Qxz + gz * mt) + 2 * ex * dx * dz;
+  M3[3] = w3 * Dx - (gx * mt + 2 * gy * Qxy) + 2 * ex * dy * dy;
+  M3[4] = w3 * W - (gx * Qyz + gy * Qxz + gz * Qxy) + 2 * ex * dy * dz;
+  M3[5] = w3 * Dx - (gx * mt + 2 * gz * Qxz) + 2 * ex * dz * dz;
+  M3[6] = w3 * Dy - 3 * gy * mt + 2 * ey * dy * dy;
+  M3[7] = w3 * Dz - (2 * gy * Qyz + gz * mt) + 2 * ey * dy * dz;
+  M3[8] = w3 * Dy - (gy * mt + 2 * gz * Qyz) + 2 * ey * dz * dz;
+  M3[9] = w3 * Dz - 3 * gz * mt + 2 * ez * dz * dz;
+  store_moments(A, int64_t(s) * kCells + cidx(a, b, c), mt, dx, dy, dz, M2, M3, mixed);
+}
+
+// Octants whose children are refined: eight lanes per parent cell, one per child, 64 threads per
+// block.  Each lane shifts its child's moments exactly from the child's centre of mass to the
+// parent's.  The centre of mass is a butterfly sum (every lane gets the same totals: IEEE
+// addition is commutative); the 16 shifted moments are reduced by recursive halving (each stage
+// keeps half the values and adds the partner's copy of them), then gathered into the group's
+// first lane.  The grid covers 512 threads per octant, so every warp is complete for the shuffles.
+constexpr int kM2MThreads = 64;
+__global__ void __launch_bounds__(kM2MThreads) k_m2m_lanes(DevArgs A, const int32_t* __restrict__ octs, int mixed) {
+  const int32_t code = octs[blockIdx.x >> 3];
+  const int32_t s = code >> 3;
+  const int o = code & 7;
+  const int e = int(threadIdx.x & 7);
+  const int lead = int(threadIdx.x & 31) & ~7;
+  const int u = int(blockIdx.x & 7) * 8 + int(threadIdx.x >> 3);
+  int a, b, c;
+  octant_cell(o, u, a, b, c);
+  const int64_t N = A.n_cell;
+  const double hc = cell_dx(A.level[s] + 1);
+  const int64_t ci = int64_t(A.child[8 * s + o]) * kCells + u + (e << 6);
+  // this child's centre of mass relative to the parent cell's geometric centre
+  const double m = A.mom[ci];
+  const double ux = (((e >> 2) & 1) ? 0.5 : -0.5) * hc + A.mom[N + ci],
+               uy = (((e >> 1) & 1) ? 0.5 : -0.5) * hc + A.mom[2 * N + ci],
+               uz = ((e & 1) ? 0.5 : -0.5) * hc + A.mom[3 * N + ci];
+  double mt = m, sx = m * ux, sy = m * uy, sz = m * uz;
+#pragma unroll
+  for (int w = 4; w >= 1; w >>= 1) {
+    mt += __shfl_xor_sync(0xffffffffu, mt, w);
+    sx += __shfl_xor_sync(0xffffffffu, sx, w);
+    sy += __shfl_xor_sync(0xffffffffu, sy, w);
+    sz += __shfl_xor_sync(0xffffffffu, sz, w);
+  }
+  double dx = 0, dy = 0, dz = 0;
+  if (mt > 0) {
+    const double inv = 1.0 / mt;
+    dx = sx * inv;
+    dy = sy * inv;
+    dz = sz * inv;
+  }
+  const double rx = ux - dx, ry = uy - dy, rz = uz - dz;
+  double q[6], p[10];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) q[k] = A.mom[(4 + k) * N + ci];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) p[k] = A.mom[(10 + k) * N + ci];
+  // this child's share: M2c + m r r, M3c + r_a M2c_bc + r_b M2c_ac + r_c M2c_ab + m r r r
+  // q: xx0 xy1 xz2 yy3 yz4 zz5; X = M2 (6) then M3 (10)
+  double X[16];
+  X[0] = q[0] + m * rx * rx;
+  X[1] = q[1] + m * rx * ry;
+  X[2] = q[2] + m * rx * rz;
+  X[3] = q[3] + m * ry * ry;
+  X[4] = q[4] + m * ry * rz;
+  X[5] = q[5] + m * rz * rz;
+  X[6] = p[0] + 3 * rx * q[0] + m * rx * rx * rx;
+  X[7] = p[1] + 2 * rx * q[1] + ry * q[0] + m * rx * rx * ry;
+  X[8] = p[2] + 2 * rx * q[2] + rz * q[0] + m * rx * rx * rz;
+  X[9] = p[3] + rx * q[3] + 2 * ry * q[1] + m * rx * ry * ry;
+  X[10] = p[4] + rx * q[4] + ry * q[2] + rz * q[1] + m * rx * ry * rz;
+  X[11] = p[5] + rx * q[5] + 2 * rz * q[2] + m * rx * rz * rz;
+  X[12] = p[6] + 3 * ry * q[3] + m * ry * ry * ry;
+  X[13] = p[7] + 2 * ry * q[4] + rz * q[3] + m * ry * ry * rz;
+  X[14] = p[8] + ry * q[5] + 2 * rz * q[4] + m * ry * rz * rz;
+  X[15] = p[9] + 3 * rz * q[5] + m * rz * rz * rz;
+  // recursive halving: after the stage of lane bit w the lane keeps the half selected by that bit
+  double Y[8], Z[4], F[2];
+  {
+    const bool hi = (e & 4) != 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double keep = hi ? X[k + 8] : X[k], give = hi ? X[k] : X[k + 8];
+      Y[k] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+    }
+  }
+  {
+    const bool hi = (e & 2) != 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double keep = hi ? Y[k + 4] : Y[k], give = hi ? Y[k] : Y[k + 4];
+      Z[k] = keep + __shfl_xor_sync(0xffffffffu, give, 2);
+    }
+  }
+  {
+    const bool hi = (e & 1) != 0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const double keep = hi ? Z[k + 2] : Z[k], give = hi ? Z[k] : Z[k + 2];
+      F[k] = keep + __shfl_xor_sync(0xffffffffu, give, 1);
+    }
+  }
+  // lane e holds entries 8 (e >> 2 & 1) + 4 (e >> 1 & 1) + 2 (e & 1) + {0, 1}
+  double R[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int owner = ((j >> 3) & 1) << 2 | ((j >> 2) & 1) << 1 | ((j >> 1) & 1);
+    R[j] = __shfl_sync(0xffffffffu, F[j & 1], lead + owner);
+  }
+  if (e != 0) return;
+  store_moments(A, int64_t(s) * kCells + cidx(a, b, c), mt, dx, dy, dz, R, R + 6, mixed);
+}
 
 // ----------------------------------------------------------------------------------------------
 // m2l: own expansion of every cell
@@ -1036,7 +1050,8 @@ __device__ __forceinline__ void block_sum7(double* v, double (*sh)[kReduceThread
 __global__ void __launch_bounds__(kReduceThreads)
     k_net_partial(DevArgs A, double* __restrict__ partials) {
   __shared__ double sh[7][kReduceThreads];
-  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  float sn = 0.0f;  // this thread's share of the normalisation S, formed and summed in FP32
   const int64_t stride = int64_t(gridDim.x) * kReduceThreads;
   const int64_t base = A.tree_leaf_off[blockIdx.y] * kCells;
   const int64_t end = A.tree_leaf_off[blockIdx.y + 1] * kCells;
@@ -1044,28 +1059,30 @@ __global__ void __launch_bounds__(kReduceThreads)
   const double* __restrict__ g = A.io[blockIdx.y].g;
   for (int64_t i = base + int64_t(blockIdx.x) * kReduceThreads + threadIdx.x; i < end;
        i += stride) {
-    int32_t s = A.leaf_sub[i >> 9];
-    int lev = A.level[s];
-    int loc = int(i & 511);
-    double h = cell_dx(lev);
-    double x = -0.5 + (A.ijk[3 * s] * 8 + (loc >> 6) + 0.5) * h;
-    double y = -0.5 + (A.ijk[3 * s + 1] * 8 + ((loc >> 3) & 7) + 0.5) * h;
-    double z = -0.5 + (A.ijk[3 * s + 2] * 8 + (loc & 7) + 0.5) * h;
+    const int32_t s = A.leaf_sub[i >> 9];
+    const int lev = A.level[s];
+    const int loc = int(i & 511);
+    // cell centre x = -1/2 + (g + 1/2) dx = (2 g + 1 - 2^(lev + 3)) 2^-(lev + 4), an odd multiple
+    const int full = 1 << (lev + 3);
+    const int nx = 2 * (A.ijk[3 * s] * 8 + (loc >> 6)) + 1 - full;
+    const int ny = 2 * (A.ijk[3 * s + 1] * 8 + ((loc >> 3) & 7)) + 1 - full;
+    const int nz = 2 * (A.ijk[3 * s + 2] * 8 + (loc & 7)) + 1 - full;
+    const double x = dyadic(nx, lev + 4), y = dyadic(ny, lev + 4), z = dyadic(nz, lev + 4);
     const int64_t o = i - base;
-    double m = rho[o] * h * h * h;
-    double fx = m * g[3 * o], fy = m * g[3 * o + 1], fz = m * g[3 * o + 2];
+    const double m = rho[o] * cell_vol(lev);
+    const double fx = m * g[3 * o], fy = m * g[3 * o + 1], fz = m * g[3 * o + 2];
     v[0] += fx;
     v[1] += fy;
     v[2] += fz;
-    v[3] += y * fz - z * fy;
-    v[4] += z * fx - x * fz;
-    v[5] += x * fy - y * fx;
-    // the normalisation S is a scale, formed in FP32 and summed in FP64
-    const float xf = float(x), yf = float(y), zf = float(z), gf = float(fx), hf = float(fy),
-                kf = float(fz);
-    v[6] += double(sqrtf(xf * xf + yf * yf + zf * zf) * sqrtf(gf * gf + hf * hf + kf * kf));
+    v[3] = fma(y, fz, fma(-z, fy, v[3]));
+    v[4] = fma(z, fx, fma(-x, fz, v[4]));
+    v[5] = fma(x, fy, fma(-y, fx, v[5]));
+    const float sc = __int_as_float((127 - lev - 4) << 23);
+    const float xf = float(nx) * sc, yf = float(ny) * sc, zf = float(nz) * sc;
+    sn += sqrtf(xf * xf + yf * yf + zf * zf) * sqrtf(float(fx * fx + fy * fy + fz * fz));
   }
-  block_sum7(v, sh);
+  double w[7] = {v[0], v[1], v[2], v[3], v[4], v[5], double(sn)};
+  block_sum7(w, sh);
   if (threadIdx.x < 7)
     partials[(int64_t(blockIdx.y) * gridDim.x + blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];
 }
@@ -1129,13 +1146,16 @@ struct StencilDev {
 struct fmm_tree {
   HostTree h;
   int device = -1;
+  int n_sms = 1;
   bool dev_ready = false, mixed_ready = false;
   int32_t *d_level = nullptr, *d_ijk = nullptr, *d_parent = nullptr, *d_child = nullptr,
           *d_nbr = nullptr, *d_leaf_sub = nullptr, *d_leaf_ord = nullptr, *d_work = nullptr,
-          *d_work_leaf = nullptr, *d_refined = nullptr;
+          *d_work_leaf = nullptr;
   int64_t n_work_leaf = 0, n_work_bnd = 0;
   uint8_t* d_leaf = nullptr;
-  std::vector<int64_t> refined_off;  // offsets into d_refined per level
+  // upward pass: (refined subgrid << 3 | octant) of each level, by the kind of the child subgrid
+  int32_t *d_oct_leaf = nullptr, *d_oct_ref = nullptr;
+  std::vector<int64_t> oct_leaf_off, oct_ref_off;
   int64_t n_work = 0;
   double *d_mom = nullptr, *d_mtl = nullptr, *d_loc = nullptr, *d_ac = nullptr, *d_root_part = nullptr,
          *d_root_part_ac = nullptr, *d_partials = nullptr;
@@ -1200,6 +1220,7 @@ static int ensure_device(fmm_tree* t) {
     return FMM_OK;
   }
   t->device = dev;
+  CUDA_TRY(cudaDeviceGetAttribute(&t->n_sms, cudaDevAttrMultiProcessorCount, dev));
   const HostTree& h = t->h;
   const int64_t nc = h.n_sub * kCells;
   CUDA_TRY(upload(t, &t->d_level, h.level));
@@ -1211,7 +1232,7 @@ static int ensure_device(fmm_tree* t) {
   CUDA_TRY(upload(t, &t->d_leaf_sub, h.leaf_sub));
   CUDA_TRY(upload(t, &t->d_leaf_ord, h.leaf_ord));
   // interaction work at levels >= 1: refined subgrids (coarse to fine) and leaf subgrids
-  std::vector<int32_t> work, work_leaf, refined;
+  std::vector<int32_t> work, work_leaf;
   for (int l = 1; l <= h.depth; ++l) work.insert(work.end(), h.refined_at[l].begin(), h.refined_at[l].end());
   for (int l = 1; l <= h.depth; ++l) work_leaf.insert(work_leaf.end(), h.leaves_at[l].begin(), h.leaves_at[l].end());
   // leaf subgrids at a refinement boundary: a refined same-level neighbour, or a leaf neighbour
@@ -1234,12 +1255,18 @@ static int ensure_device(fmm_tree* t) {
   t->work_bnd = work_bnd;
   CUDA_TRY(upload(t, &t->d_work, work));
   CUDA_TRY(upload(t, &t->d_work_leaf, work_leaf));
-  t->refined_off.assign(h.depth + 2, 0);
+  std::vector<int32_t> oct_leaf, oct_ref;
+  t->oct_leaf_off.assign(h.depth + 2, 0);
+  t->oct_ref_off.assign(h.depth + 2, 0);
   for (int l = 0; l <= h.depth; ++l) {
-    refined.insert(refined.end(), h.refined_at[l].begin(), h.refined_at[l].end());
-    t->refined_off[l + 1] = int64_t(refined.size());
+    for (int32_t s : h.refined_at[l])
+      for (int o = 0; o < 8; ++o) (h.leaf[h.child[8 * s + o]] ? oct_leaf : oct_ref).push_back(s * 8 + o);
+    t->oct_leaf_off[l + 1] = int64_t(oct_leaf.size());
+    t->oct_ref_off[l + 1] = int64_t(oct_ref.size());
   }
-  CUDA_TRY(upload(t, &t->d_refined, refined));
+  if (int64_t(h.n_sub) * 8 > INT32_MAX) return fail(FMM_ERR_ARG, "too many subgrids");
+  CUDA_TRY(upload(t, &t->d_oct_leaf, oct_leaf));
+  CUDA_TRY(upload(t, &t->d_oct_ref, oct_ref));
   CUDA_TRY(dalloc(t, &t->d_mom, sizeof(double) * kNMom * nc));
   CUDA_TRY(cudaMemset(t->d_mom, 0, sizeof(double) * kNMom * nc));  // leaf cells keep zeros
   CUDA_TRY(dalloc(t, &t->d_mtl, sizeof(double) * kNMom * nc));
@@ -1303,14 +1330,13 @@ struct BoundaryLists {
 static std::string boundary_lists(const HostTree& h, const Stencil& st,
                                   const std::vector<int32_t>& work_bnd, BoundaryLists& out) {
   const double c_m = 150, c_p = 20;
-  struct Tgt {
-    int32_t cell;
-    std::vector<int32_t> ms, mq, ps, pc;
-  };
-  std::vector<Tgt> tg;
   auto code3 = [](int x, int y, int z) {
     return int32_t((uint32_t(x + 512) << 20) | (uint32_t(y + 512) << 10) | uint32_t(z + 512));
   };
+  // first pass: every target's lists in subgrid order, flat
+  std::vector<int32_t> cell;
+  std::vector<int64_t> moff{0}, poff{0};
+  std::vector<int32_t> ms, mq, ps, pc;
   for (int32_t s : work_bnd) {
     int32_t nb[27], pnb[27];
     bool nb_ref[27], pnb_leaf[27];
@@ -1325,8 +1351,7 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
       for (int b = 0; b < 8; ++b)
         for (int c = 0; c < 8; ++c) {
           const int par = (a & 1) << 2 | (b & 1) << 1 | (c & 1);
-          Tgt e;
-          e.cell = int32_t(int64_t(s) * kCells + host_cidx(a, b, c));
+          const size_t m0 = ms.size(), p0 = ps.size();
           const auto& offs = st.offs[par];
           for (size_t q = 0; q < offs.size(); ++q) {
             int dx, dy, dz;
@@ -1334,8 +1359,8 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
             const int px = a + dx, py = b + dy, pz = c + dz;
             const int sl = slot_of(px) * 9 + slot_of(py) * 3 + slot_of(pz);
             if (!nb_ref[sl]) continue;
-            e.ms.push_back(int32_t(int64_t(nb[sl]) * kCells + host_cidx(px & 7, py & 7, pz & 7)));
-            e.mq.push_back(int32_t(q));
+            ms.push_back(int32_t(int64_t(nb[sl]) * kCells + host_cidx(px & 7, py & 7, pz & 7)));
+            mq.push_back(int32_t(q));
           }
           for (int32_t code : st.near) {
             int dx, dy, dz;
@@ -1347,10 +1372,10 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
             const int32_t cs = h.child[8 * nb[sl] + ((lx >> 2) << 2 | (ly >> 2) << 1 | (lz >> 2))];
             for (int o = 0; o < 8; ++o) {
               const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-              e.ps.push_back(int32_t(int64_t(cs) * kCells +
-                                     host_cidx((lx & 3) * 2 + ox, (ly & 3) * 2 + oy, (lz & 3) * 2 + oz)));
+              ps.push_back(int32_t(int64_t(cs) * kCells +
+                                   host_cidx((lx & 3) * 2 + ox, (ly & 3) * 2 + oy, (lz & 3) * 2 + oz)));
               // x_A - x_C = (1/2 - o - 2 d) dx_(l+1) = (1 - 2 o - 4 d) dx_l / 4
-              e.pc.push_back(code3(1 - 2 * ox - 4 * dx, 1 - 2 * oy - 4 * dy, 1 - 2 * oz - 4 * dz));
+              pc.push_back(code3(1 - 2 * ox - 4 * dx, 1 - 2 * oy - 4 * dy, 1 - 2 * oz - 4 * dz));
             }
           }
           const int ga = h.ijk[3 * s] * 8 + a, gb = h.ijk[3 * s + 1] * 8 + b, gc = h.ijk[3 * s + 2] * 8 + c;
@@ -1362,49 +1387,60 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
             const int px = ja + dx, py = jb + dy, pz = jc + dz;
             const int sl = slot_of(px) * 9 + slot_of(py) * 3 + slot_of(pz);
             if (!pnb_leaf[sl]) continue;
-            e.ps.push_back(int32_t(int64_t(pnb[sl]) * kCells + host_cidx(px & 7, py & 7, pz & 7)));
+            ps.push_back(int32_t(int64_t(pnb[sl]) * kCells + host_cidx(px & 7, py & 7, pz & 7)));
             // x_A - x_i = ((g_A & 1) - 1/2 - 2 d) dx_l = (4 (g_A & 1) - 2 - 8 d) dx_l / 4
-            e.pc.push_back(code3(4 * (ga & 1) - 2 - 8 * dx, 4 * (gb & 1) - 2 - 8 * dy,
-                                 4 * (gc & 1) - 2 - 8 * dz));
+            pc.push_back(code3(4 * (ga & 1) - 2 - 8 * dx, 4 * (gb & 1) - 2 - 8 * dy,
+                               4 * (gc & 1) - 2 - 8 * dz));
           }
-          if (!e.ms.empty() || !e.ps.empty()) tg.push_back(std::move(e));
+          if (ms.size() == m0 && ps.size() == p0) continue;  // no partners
+          cell.push_back(int32_t(int64_t(s) * kCells + host_cidx(a, b, c)));
+          moff.push_back(int64_t(ms.size()));
+          poff.push_back(int64_t(ps.size()));
         }
   }
-  for (const Tgt& e : tg)
-    for (int32_t code : e.pc)
-      for (int f = 0; f < 3; ++f) {
-        const int v = int((uint32_t(code) >> (20 - 10 * f)) & 1023u) - 512;
-        if (v < -kCodeMax || v > kCodeMax) return "point-pair offset outside the table";
-      }
-  std::vector<double> cost(tg.size());
-  std::vector<size_t> order(tg.size());
-  for (size_t k = 0; k < tg.size(); ++k) {
-    cost[k] = c_m * double(tg[k].ms.size()) + c_p * double(tg[k].ps.size());
+  for (int32_t code : pc)
+    for (int f = 0; f < 3; ++f) {
+      const int v = int((uint32_t(code) >> (20 - 10 * f)) & 1023u) - 512;
+      if (v < -kCodeMax || v > kCodeMax) return "point-pair offset outside the table";
+    }
+  if (ms.size() > size_t(INT32_MAX) || ps.size() > size_t(INT32_MAX))
+    return "boundary pair lists exceed 2^31 entries";
+  // second pass: targets by estimated work, largest first
+  const size_t n = cell.size();
+  std::vector<double> cost(n);
+  std::vector<size_t> order(n);
+  for (size_t k = 0; k < n; ++k) {
+    cost[k] = c_m * double(moff[k + 1] - moff[k]) + c_p * double(poff[k + 1] - poff[k]);
     order[k] = k;
   }
   std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
   out = BoundaryLists();
-  out.m_off.push_back(0);
-  out.p_off.push_back(0);
-  for (size_t k : order) {
-    const Tgt& e = tg[k];
-    out.cell.push_back(e.cell);
-    out.cost.push_back(cost[k]);
-    out.m_src.insert(out.m_src.end(), e.ms.begin(), e.ms.end());
-    out.m_q.insert(out.m_q.end(), e.mq.begin(), e.mq.end());
-    out.p_src.insert(out.p_src.end(), e.ps.begin(), e.ps.end());
-    out.p_code.insert(out.p_code.end(), e.pc.begin(), e.pc.end());
-    if (out.m_src.size() > size_t(INT32_MAX) || out.p_src.size() > size_t(INT32_MAX))
-      return "boundary pair lists exceed 2^31 entries";
-    out.m_off.push_back(int32_t(out.m_src.size()));
-    out.p_off.push_back(int32_t(out.p_src.size()));
+  out.cell.resize(n);
+  out.cost.resize(n);
+  out.m_off.resize(n + 1);
+  out.p_off.resize(n + 1);
+  out.m_src.resize(ms.size());
+  out.m_q.resize(mq.size());
+  out.p_src.resize(ps.size());
+  out.p_code.resize(pc.size());
+  int64_t mo = 0, po = 0;
+  out.m_off[0] = out.p_off[0] = 0;
+  for (size_t r = 0; r < n; ++r) {
+    const size_t k = order[r];
+    out.cell[r] = cell[k];
+    out.cost[r] = cost[k];
+    std::copy(ms.begin() + moff[k], ms.begin() + moff[k + 1], out.m_src.begin() + mo);
+    std::copy(mq.begin() + moff[k], mq.begin() + moff[k + 1], out.m_q.begin() + mo);
+    std::copy(ps.begin() + poff[k], ps.begin() + poff[k + 1], out.p_src.begin() + po);
+    std::copy(pc.begin() + poff[k], pc.begin() + poff[k + 1], out.p_code.begin() + po);
+    mo += moff[k + 1] - moff[k];
+    po += poff[k + 1] - poff[k];
+    out.m_off[r + 1] = int32_t(mo);
+    out.p_off[r + 1] = int32_t(po);
   }
   return "";
 }
 
-// Block list of the general interaction kernel, sorted by an estimate of each block's work
-// (pairs times a per-kind cost in FP64 instructions), largest first, so that the long blocks
-// start early and the short ones fill the tail.
 static std::vector<int32_t> general_blocks(const HostTree& h, const Stencil& st,
                                            const std::vector<int32_t>& work,
                                            const BoundaryLists& bnd, bool whole) {
@@ -1642,16 +1678,19 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, bool mixed, int amc,
   CUDA_TRY(cudaGetLastError());
   ++nl;
   for (int l = h.depth - 1; l >= 0; --l) {
-    int64_t n = t->refined_off[l + 1] - t->refined_off[l];
-    if (n == 0) continue;
-    if (n * kCells >= kM2MCellMin)
-      k_m2m_cell<<<blocks_for(n * kCells, 128), 128, 0, st>>>(A, t->d_refined + t->refined_off[l],
-                                                              int(n), mixed ? 1 : 0);
-    else
-      k_m2m<<<unsigned(n * kCells * 8 / kM2MThreads), kM2MThreads, 0, st>>>(
-          A, t->d_refined + t->refined_off[l], mixed ? 1 : 0);
-    CUDA_TRY(cudaGetLastError());
-    ++nl;
+    const int64_t nl_oct = t->oct_leaf_off[l + 1] - t->oct_leaf_off[l];
+    const int64_t nr_oct = t->oct_ref_off[l + 1] - t->oct_ref_off[l];
+    if (nl_oct > 0) {
+      k_m2m_walsh<<<unsigned(nl_oct), 64, 0, st>>>(A, t->d_oct_leaf + t->oct_leaf_off[l], mixed ? 1 : 0);
+      CUDA_TRY(cudaGetLastError());
+      ++nl;
+    }
+    if (nr_oct > 0) {
+      k_m2m_lanes<<<unsigned(nr_oct * 8), kM2MThreads, 0, st>>>(A, t->d_oct_ref + t->oct_ref_off[l],
+                                                                 mixed ? 1 : 0);
+      CUDA_TRY(cudaGetLastError());
+      ++nl;
+    }
   }
 
   if ((rc = record(t, 1, st))) return rc;

@@ -54,9 +54,11 @@ def test_forest_slices_equal_individual_solves(precision):
         sl = slice(off[k] * 512, off[k + 1] * 512)
         assert np.array_equal(phi[sl], p1.cpu().numpy())
         assert np.array_equal(g[sl], g1.cpu().numpy())
-        # the reduction's block layout depends on the number of trees: equal to round-off
+        # the reduction's block layout depends on the number of trees: F and T equal to FP64
+        # round-off, the normalisation S (summed in FP32 per thread) to FP32 round-off
         n1 = n1.cpu().numpy()
-        assert np.abs(net[k] - n1).max() <= 1e-14 * n1[6]
+        assert np.abs(net[k][:6] - n1[:6]).max() <= 1e-14 * n1[6]
+        assert abs(net[k][6] - n1[6]) <= 1e-6 * n1[6]
     rs = [torch.from_numpy(x).cuda() for x in rhos]
     phis, gs, net2 = f.solve_batch(rs, 0.5, precision)
     for k in range(n):
