@@ -26,6 +26,8 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/octo_fmm.h"
@@ -875,158 +877,235 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
   A.ac[i1] = A.ac[N + i1] = A.ac[2 * N + i1] = 0.0;
 }
 
-// ----------------------------------------------------------------------------------------------
-// l2l / l2p: total expansion = own + parent's total shifted to this cell's centre of mass
-// ----------------------------------------------------------------------------------------------
-// Shift of a cubic expansion by r (exact for a polynomial of degree 3):
-//   L0' = L0 + L1.r + 1/2 r.L2.r + 1/6 L3(r,r,r),  L1' = L1 + L2 r + 1/2 L3(r,r),
-//   L2' = L2 + L3 r,  L3' = L3.
-__device__ __forceinline__ void shift_add(const double* P, double rx, double ry, double rz,
-                                          double* L, bool full) {
-  double qx, qy, qz;
-  sym3_rr<double>(P + 10, rx, ry, rz, qx, qy, qz);
+// Exact Taylor shift of a 3rd-order expansion P about X to the point X + r, added onto L:
+//   L0 += P0 + P1.r + 1/2 r.P2.r + 1/6 P3(r,r,r),  L1 += P1 + P2 r + 1/2 P3(r,r),
+//   L2 += P2 + P3 r,  L3 += P3.
+template <typename T>
+__device__ __forceinline__ void shift_add(const T* P, T rx, T ry, T rz, T* L) {
+  T qx, qy, qz;
+  sym3_rr<T>(P + 10, rx, ry, rz, qx, qy, qz);
   // L2 r
-  double l2x = P[4] * rx + P[5] * ry + P[6] * rz;
-  double l2y = P[5] * rx + P[7] * ry + P[8] * rz;
-  double l2z = P[6] * rx + P[8] * ry + P[9] * rz;
-  L[0] += P[0] + P[1] * rx + P[2] * ry + P[3] * rz + 0.5 * (rx * l2x + ry * l2y + rz * l2z) +
-          (rx * qx + ry * qy + rz * qz) * (1.0 / 6.0);
-  L[1] += P[1] + l2x + 0.5 * qx;
-  L[2] += P[2] + l2y + 0.5 * qy;
-  L[3] += P[3] + l2z + 0.5 * qz;
-  if (full) {
-    // (L3 r)_ab, L3: xxx0 xxy1 xxz2 xyy3 xyz4 xzz5 yyy6 yyz7 yzz8 zzz9
-    const double* Q = P + 10;
-    L[4] += P[4] + Q[0] * rx + Q[1] * ry + Q[2] * rz;
-    L[5] += P[5] + Q[1] * rx + Q[3] * ry + Q[4] * rz;
-    L[6] += P[6] + Q[2] * rx + Q[4] * ry + Q[5] * rz;
-    L[7] += P[7] + Q[3] * rx + Q[6] * ry + Q[7] * rz;
-    L[8] += P[8] + Q[4] * rx + Q[7] * ry + Q[8] * rz;
-    L[9] += P[9] + Q[5] * rx + Q[8] * ry + Q[9] * rz;
+  T l2x = P[4] * rx + P[5] * ry + P[6] * rz;
+  T l2y = P[5] * rx + P[7] * ry + P[8] * rz;
+  T l2z = P[6] * rx + P[8] * ry + P[9] * rz;
+  L[0] += P[0] + P[1] * rx + P[2] * ry + P[3] * rz + T(0.5) * (rx * l2x + ry * l2y + rz * l2z) +
+          (rx * qx + ry * qy + rz * qz) * (T(1) / T(6));
+  L[1] += P[1] + l2x + T(0.5) * qx;
+  L[2] += P[2] + l2y + T(0.5) * qy;
+  L[3] += P[3] + l2z + T(0.5) * qz;
+  // (L3 r)_ab, L3: xxx0 xxy1 xxz2 xyy3 xyz4 xzz5 yyy6 yyz7 yzz8 zzz9
+  const T* Q = P + 10;
+  L[4] += P[4] + Q[0] * rx + Q[1] * ry + Q[2] * rz;
+  L[5] += P[5] + Q[1] * rx + Q[3] * ry + Q[4] * rz;
+  L[6] += P[6] + Q[2] * rx + Q[4] * ry + Q[5] * rz;
+  L[7] += P[7] + Q[3] * rx + Q[6] * ry + Q[7] * rz;
+  L[8] += P[8] + Q[4] * rx + Q[7] * ry + Q[8] * rz;
+  L[9] += P[9] + Q[5] * rx + Q[8] * ry + Q[9] * rz;
 #pragma unroll
-    for (int k = 10; k < 20; ++k) L[k] += P[k];
-  }
+  for (int k = 10; k < 20; ++k) L[k] += P[k];
 }
 
-// Mixed path, leaf cells: the parent's total L0 and L1 enter in FP64; the shift terms
-// L1.r + 1/2 r.L2.r + 1/6 L3(r,r,r) and L2 r + 1/2 L3(r,r) (|r| < dx) are formed in FP32 from
-// the FP32 copy of the parent's total, then added in FP64.
-__device__ __forceinline__ void shift_terms32(const float* P, float rx, float ry, float rz,
-                                              float* d) {
-  float qx, qy, qz;
-  sym3_rr<float>(P + 10, rx, ry, rz, qx, qy, qz);
-  float l2x = P[4] * rx + P[5] * ry + P[6] * rz;
-  float l2y = P[5] * rx + P[7] * ry + P[8] * rz;
-  float l2z = P[6] * rx + P[8] * ry + P[9] * rz;
-  d[0] = P[1] * rx + P[2] * ry + P[3] * rz + 0.5f * (rx * l2x + ry * l2y + rz * l2z) +
-         (rx * qx + ry * qy + rz * qz) * (1.0f / 6.0f);
-  d[1] = l2x + 0.5f * qx;
-  d[2] = l2y + 0.5f * qy;
-  d[3] = l2z + 0.5f * qz;
-}
-
+// Downward pass.  Expansions: FP64 in the FP64 path; in the mixed path every expansion is FP32
+// (own, shifted and total), while the correction accelerations stay FP64 sums.
 template <bool MIXED>
-__global__ void k_l2l(DevArgs A, int lev, int64_t s0, int64_t n_subs) {
-  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= n_subs * kCells) return;
-  const int32_t s = int32_t(s0 + (t >> 9));
+struct Down {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  static __device__ __forceinline__ T ld(const DevArgs& A, int k, int64_t i) {
+    if constexpr (MIXED) return A.loc32[k * A.n_cell + i];
+    else return A.loc[k * A.n_cell + i];
+  }
+  static __device__ __forceinline__ void st(const DevArgs& A, int k, int64_t i, T v) {
+    if constexpr (MIXED) A.loc32[k * A.n_cell + i] = v;
+    else A.loc[k * A.n_cell + i] = v;
+  }
+  static __device__ __forceinline__ T com(const DevArgs& A, int k, int64_t i) {
+    if constexpr (MIXED) return A.mom32[k * A.n_cell + i];
+    else return A.mom[k * A.n_cell + i];
+  }
+};
+
+// Writes phi and g of leaf cell (subgrid s, cell (a, b, c)) in the caller's arrays.
+__device__ __forceinline__ void store_leaf(const DevArgs& A, int32_t s, int a, int b, int c,
+                                           double phi_v, double gx, double gy, double gz) {
+  const int32_t ls = A.leaf_ord[s];
+  const int k = A.leaf_tree[ls];
+  const int64_t o = (int64_t(ls) - A.tree_leaf_off[k]) * kCells + (a * 8 + b) * 8 + c;
+  double* __restrict__ phi = A.io[k].phi;
+  double* __restrict__ g = A.io[k].g;
+  phi[o] = phi_v;
+  g[3 * o] = gx;
+  g[3 * o + 1] = gy;
+  g[3 * o + 2] = gz;
+}
+
+// Level 0: each root cell's expansion is the fixed-order sum of its kRootChunks partial sums.
+// A refined root keeps it as its total; a leaf root is evaluated (phi = L0, g = -L1 + a_c).
+template <bool MIXED>
+__global__ void k_root_total(DevArgs A) {
+  using T = typename Down<MIXED>::T;
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= int64_t(A.n_roots) * kCells) return;
+  const int32_t s = int32_t(t >> 9);  // roots are subgrids 0 .. n_roots - 1
   const int loc = int(t & 511);
-  const int64_t N = A.n_cell;
   const int64_t i = int64_t(s) * kCells + loc;
   const bool isleaf = A.leaf[s] != 0;
   const int nL = isleaf ? 4 : 20;
-  double L[20], ax, ay, az;
-  if (lev == 0) {
-    ax = ay = az = 0.0;
-    for (int k = 0; k < 20; ++k) L[k] = 0.0;
-    for (int ch = 0; ch < kRootChunks; ++ch) {
-      const int64_t pc = int64_t(s) * kRootChunks + ch;  // at level 0, s is the root's tree
-      if (!MIXED) {
-        const double* P = A.root_part + pc * 23 * kCells;
-        for (int k = 0; k < nL; ++k) L[k] += P[k * kCells + loc];
-        ax += P[20 * kCells + loc];
-        ay += P[21 * kCells + loc];
-        az += P[22 * kCells + loc];
-      } else {
-        const float* P = A.root_part32 + pc * 20 * kCells;
-        for (int k = 0; k < nL; ++k) L[k] += double(P[k * kCells + loc]);
-        const double* Q = A.root_part_ac + pc * 3 * kCells;
-        ax += Q[loc];
-        ay += Q[kCells + loc];
-        az += Q[2 * kCells + loc];
-      }
+  double L[20], ax = 0.0, ay = 0.0, az = 0.0;
+  for (int k = 0; k < 20; ++k) L[k] = 0.0;
+  for (int ch = 0; ch < kRootChunks; ++ch) {
+    const int64_t pc = int64_t(s) * kRootChunks + ch;
+    if (!MIXED) {
+      const double* P = A.root_part + pc * 23 * kCells;
+      for (int k = 0; k < nL; ++k) L[k] += P[k * kCells + loc];
+      ax += P[20 * kCells + loc];
+      ay += P[21 * kCells + loc];
+      az += P[22 * kCells + loc];
+    } else {
+      const float* P = A.root_part32 + pc * 20 * kCells;
+      for (int k = 0; k < nL; ++k) L[k] += double(P[k * kCells + loc]);
+      const double* Q = A.root_part_ac + pc * 3 * kCells;
+      ax += Q[loc];
+      ay += Q[kCells + loc];
+      az += Q[2 * kCells + loc];
     }
-  } else if (MIXED && isleaf) {
-    const int32_t Pn = A.parent[s];
-    int a, b, c;
-    cdecode(loc, a, b, c);
-    int ga = A.ijk[3 * s] * 8 + a, gb = A.ijk[3 * s + 1] * 8 + b, gc = A.ijk[3 * s + 2] * 8 + c;
-    int pl = cidx((ga >> 1) - A.ijk[3 * Pn] * 8, (gb >> 1) - A.ijk[3 * Pn + 1] * 8,
-                  (gc >> 1) - A.ijk[3 * Pn + 2] * 8);
-    const int64_t ip = int64_t(Pn) * kCells + pl;
-    float P32[20], d[4];
-#pragma unroll
-    for (int k = 0; k < 20; ++k) P32[k] = A.loc32[k * N + ip];
-    const float h = cell_dx32(lev);
-    // r = X_A - X_P = ((g & 1) - 1/2) dx_l - delta_P (a leaf's centre of mass is its centre)
-    const float rx = ((ga & 1) ? 0.5f : -0.5f) * h - A.mom32[N + ip];
-    const float ry = ((gb & 1) ? 0.5f : -0.5f) * h - A.mom32[2 * N + ip];
-    const float rz = ((gc & 1) ? 0.5f : -0.5f) * h - A.mom32[3 * N + ip];
-    shift_terms32(P32, rx, ry, rz, d);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) L[k] = (double(A.loc32[k * N + i]) + A.loc[k * N + ip]) + double(d[k]);
-    ax = A.ac[i] + A.ac[ip];
-    ay = A.ac[N + i] + A.ac[N + ip];
-    az = A.ac[2 * N + i] + A.ac[2 * N + ip];
-  } else {
-    for (int k = 0; k < nL; ++k) L[k] = MIXED ? double(A.loc32[k * N + i]) : A.loc[k * N + i];
-    for (int k = nL; k < 20; ++k) L[k] = 0.0;
-    ax = A.ac[i];
-    ay = A.ac[N + i];
-    az = A.ac[2 * N + i];
-    const int32_t Pn = A.parent[s];
-    int a, b, c;
-    cdecode(loc, a, b, c);
-    int ga = A.ijk[3 * s] * 8 + a, gb = A.ijk[3 * s + 1] * 8 + b, gc = A.ijk[3 * s + 2] * 8 + c;
-    int pl = cidx((ga >> 1) - A.ijk[3 * Pn] * 8, (gb >> 1) - A.ijk[3 * Pn + 1] * 8,
-                  (gc >> 1) - A.ijk[3 * Pn + 2] * 8);
-    const int64_t ip = int64_t(Pn) * kCells + pl;
-    double P[20];
-#pragma unroll
-    for (int k = 0; k < 20; ++k) P[k] = A.loc[k * N + ip];
-    const double h = cell_dx(lev);
-    // r = X_A - X_P = ((g & 1) - 1/2) dx_l + delta_A - delta_P
-    double rx = ((ga & 1) - 0.5) * h + A.mom[N + i] - A.mom[N + ip];
-    double ry = ((gb & 1) - 0.5) * h + A.mom[2 * N + i] - A.mom[2 * N + ip];
-    double rz = ((gc & 1) - 0.5) * h + A.mom[3 * N + i] - A.mom[3 * N + ip];
-    shift_add(P, rx, ry, rz, L, !isleaf);
-    ax += A.ac[ip];
-    ay += A.ac[N + ip];
-    az += A.ac[2 * N + ip];
   }
   if (isleaf) {
     int a, b, c;
     cdecode(loc, a, b, c);
-    const int32_t ls = A.leaf_ord[s];
-    const int k = A.leaf_tree[ls];
-    const int64_t o = (int64_t(ls) - A.tree_leaf_off[k]) * kCells + (a * 8 + b) * 8 + c;
-    double* __restrict__ phi = A.io[k].phi;
-    double* __restrict__ g = A.io[k].g;
-    phi[o] = L[0];
-    g[3 * o] = -L[1] + ax;
-    g[3 * o + 1] = -L[2] + ay;
-    g[3 * o + 2] = -L[3] + az;
-  } else {
+    store_leaf(A, s, a, b, c, L[0], -L[1] + ax, -L[2] + ay, -L[3] + az);
+    return;
+  }
 #pragma unroll
-    for (int k = 0; k < 20; ++k) A.loc[k * N + i] = L[k];
-    if (MIXED) {
-      // FP32 copy of the total for the children's shift terms
+  for (int k = 0; k < 20; ++k) Down<MIXED>::st(A, k, i, T(L[k]));
+  const int64_t N = A.n_cell;
+  A.ac[i] = ax;
+  A.ac[N + i] = ay;
+  A.ac[2 * N + i] = az;
+}
+
+// Levels >= 1, one launch per level, 64 threads per block.  Blocks [0, n_ref_blocks): 8 per
+// refined subgrid of the level, one thread per cell: total = own + the parent's total shifted
+// from the parent's centre of mass to the cell's (r = X_A - X_P).  The other blocks: one per
+// (refined parent subgrid, octant) whose child subgrid is a leaf of this level, one thread per
+// parent cell and its 8 leaf children.  The parent's total is shifted once to the parent cell's
+// geometric centre; there the children sit at s w (s = +-1 per axis, w = dx_l / 2), and the
+// expansion's value and gradient at the 8 children are sums of the 8 Walsh functions
+// prod_(a in k) s_a.  With L2, L3 traceless up to rounding (t_a = L3_abb, kept for exactness):
+//   phi(s w) = [L0 + w^2/2 tr L2] + w sum_a s_a [L1_a + w^2 (t_a / 2 - L3_aaa / 3)]
+//              + w^2 sum_(a<b) s_a s_b L2_ab + w^3 s_x s_y s_z L3_xyz,
+//   dphi/dr_a (s w) = [L1_a + w^2 t_a / 2] + w sum_b s_b L2_ab + w^2 sum_(b<c) s_b s_c L3_abc,
+// each evaluated at all 8 children by an inverse 8-point Walsh-Hadamard transform.
+template <bool MIXED>
+__global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* __restrict__ ref,
+                                             int n_ref_blocks, const int32_t* __restrict__ octs) {
+  using T = typename Down<MIXED>::T;
+  const int64_t N = A.n_cell;
+  if (int(blockIdx.x) < n_ref_blocks) {
+    const int32_t s = ref[blockIdx.x >> 3];
+    const int loc = int(blockIdx.x & 7) * 64 + int(threadIdx.x);
+    const int64_t i = int64_t(s) * kCells + loc;
+    const int32_t Pn = A.parent[s];
+    int a, b, c;
+    cdecode(loc, a, b, c);
+    const int ga = A.ijk[3 * s] * 8 + a, gb = A.ijk[3 * s + 1] * 8 + b, gc = A.ijk[3 * s + 2] * 8 + c;
+    const int64_t ip = int64_t(Pn) * kCells + cidx((ga >> 1) - A.ijk[3 * Pn] * 8,
+                                                   (gb >> 1) - A.ijk[3 * Pn + 1] * 8,
+                                                   (gc >> 1) - A.ijk[3 * Pn + 2] * 8);
+    T P[20], L[20];
 #pragma unroll
-      for (int k = 0; k < 20; ++k) A.loc32[k * N + i] = float(L[k]);
+    for (int k = 0; k < 20; ++k) {
+      P[k] = Down<MIXED>::ld(A, k, ip);
+      L[k] = Down<MIXED>::ld(A, k, i);
     }
-    A.ac[i] = ax;
-    A.ac[N + i] = ay;
-    A.ac[2 * N + i] = az;
+    const T h = cell_h<T>(lev), hh = T(0.5) * h;
+    // r = X_A - X_P = ((g & 1) - 1/2) dx_l + delta_A - delta_P
+    const T rx = ((ga & 1) ? hh : -hh) + Down<MIXED>::com(A, 1, i) - Down<MIXED>::com(A, 1, ip);
+    const T ry = ((gb & 1) ? hh : -hh) + Down<MIXED>::com(A, 2, i) - Down<MIXED>::com(A, 2, ip);
+    const T rz = ((gc & 1) ? hh : -hh) + Down<MIXED>::com(A, 3, i) - Down<MIXED>::com(A, 3, ip);
+    shift_add<T>(P, rx, ry, rz, L);
+#pragma unroll
+    for (int k = 0; k < 20; ++k) Down<MIXED>::st(A, k, i, L[k]);
+    A.ac[i] += A.ac[ip];
+    A.ac[N + i] += A.ac[N + ip];
+    A.ac[2 * N + i] += A.ac[2 * N + ip];
+    return;
+  }
+  const int32_t code = octs[blockIdx.x - n_ref_blocks];
+  const int32_t Pn = code >> 3;
+  const int o = code & 7, u = int(threadIdx.x);
+  int pa, pb, pc;
+  octant_cell(o, u, pa, pb, pc);
+  const int64_t ip = int64_t(Pn) * kCells + cidx(pa, pb, pc);
+  const int32_t s = A.child[8 * Pn + o];
+  T L[20], P[20];
+#pragma unroll
+  for (int k = 0; k < 20; ++k) {
+    P[k] = Down<MIXED>::ld(A, k, ip);
+    L[k] = T(0);
+  }
+  // to the parent cell's geometric centre: r = -delta_P
+  shift_add<T>(P, -Down<MIXED>::com(A, 1, ip), -Down<MIXED>::com(A, 2, ip),
+               -Down<MIXED>::com(A, 3, ip), L);
+  const T w = T(0.5) * cell_h<T>(lev), w2 = w * w, w3 = w2 * w;
+  const T tr2 = L[4] + L[7] + L[9];
+  const T tx = L[10] + L[13] + L[15], ty = L[11] + L[16] + L[18], tz = L[12] + L[17] + L[19];
+  // Walsh coefficients, index (x << 2) | (y << 1) | z
+  T f[8], gxv[8], gyv[8], gzv[8];
+  f[0] = L[0] + T(0.5) * w2 * tr2;
+  f[4] = w * (L[1] + w2 * (T(0.5) * tx - L[10] * (T(1) / T(3))));
+  f[2] = w * (L[2] + w2 * (T(0.5) * ty - L[16] * (T(1) / T(3))));
+  f[1] = w * (L[3] + w2 * (T(0.5) * tz - L[19] * (T(1) / T(3))));
+  f[6] = w2 * L[5];
+  f[5] = w2 * L[6];
+  f[3] = w2 * L[8];
+  f[7] = w3 * L[14];
+  gxv[0] = L[1] + T(0.5) * w2 * tx;
+  gxv[4] = w * L[4];
+  gxv[2] = w * L[5];
+  gxv[1] = w * L[6];
+  gxv[6] = w2 * L[11];
+  gxv[5] = w2 * L[12];
+  gxv[3] = w2 * L[14];
+  gxv[7] = T(0);
+  gyv[0] = L[2] + T(0.5) * w2 * ty;
+  gyv[4] = w * L[5];
+  gyv[2] = w * L[7];
+  gyv[1] = w * L[8];
+  gyv[6] = w2 * L[13];
+  gyv[5] = w2 * L[14];
+  gyv[3] = w2 * L[17];
+  gyv[7] = T(0);
+  gzv[0] = L[3] + T(0.5) * w2 * tz;
+  gzv[4] = w * L[6];
+  gzv[2] = w * L[8];
+  gzv[1] = w * L[9];
+  gzv[6] = w2 * L[14];
+  gzv[5] = w2 * L[15];
+  gzv[3] = w2 * L[18];
+  gzv[7] = T(0);
+  // inverse transforms: value at child e (bit set = upper half, s = +1)
+#pragma unroll
+  for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      if (!(e & bit)) {
+        T lo, hi;
+        lo = f[e], hi = f[e | bit], f[e] = lo - hi, f[e | bit] = lo + hi;
+        lo = gxv[e], hi = gxv[e | bit], gxv[e] = lo - hi, gxv[e | bit] = lo + hi;
+        lo = gyv[e], hi = gyv[e | bit], gyv[e] = lo - hi, gyv[e | bit] = lo + hi;
+        lo = gzv[e], hi = gzv[e | bit], gzv[e] = lo - hi, gzv[e | bit] = lo + hi;
+      }
+  const double apx = A.ac[ip], apy = A.ac[N + ip], apz = A.ac[2 * N + ip];
+  const int64_t c0 = int64_t(s) * kCells + u;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int64_t i = c0 + (e << 6);
+    const T phi = Down<MIXED>::ld(A, 0, i) + f[e];
+    const T l1x = Down<MIXED>::ld(A, 1, i) + gxv[e], l1y = Down<MIXED>::ld(A, 2, i) + gyv[e],
+            l1z = Down<MIXED>::ld(A, 3, i) + gzv[e];
+    const double ax = A.ac[i] + apx, ay = A.ac[N + i] + apy, az = A.ac[2 * N + i] + apz;
+    store_leaf(A, s, 2 * (pa & 3) + ((e >> 2) & 1), 2 * (pb & 3) + ((e >> 1) & 1), 2 * (pc & 3) + (e & 1),
+               double(phi), -double(l1x) + ax, -double(l1y) + ay, -double(l1z) + az);
   }
 }
 
@@ -1156,6 +1235,9 @@ struct fmm_tree {
   // upward pass: (refined subgrid << 3 | octant) of each level, by the kind of the child subgrid
   int32_t *d_oct_leaf = nullptr, *d_oct_ref = nullptr;
   std::vector<int64_t> oct_leaf_off, oct_ref_off;
+  // downward pass: refined subgrids of each level
+  int32_t* d_ref_sub = nullptr;
+  std::vector<int64_t> ref_off;
   int64_t n_work = 0;
   double *d_mom = nullptr, *d_mtl = nullptr, *d_loc = nullptr, *d_ac = nullptr, *d_root_part = nullptr,
          *d_root_part_ac = nullptr, *d_partials = nullptr;
@@ -1255,6 +1337,13 @@ static int ensure_device(fmm_tree* t) {
   t->work_bnd = work_bnd;
   CUDA_TRY(upload(t, &t->d_work, work));
   CUDA_TRY(upload(t, &t->d_work_leaf, work_leaf));
+  std::vector<int32_t> ref_sub;
+  t->ref_off.assign(h.depth + 2, 0);
+  for (int l = 0; l <= h.depth; ++l) {
+    ref_sub.insert(ref_sub.end(), h.refined_at[l].begin(), h.refined_at[l].end());
+    t->ref_off[l + 1] = int64_t(ref_sub.size());
+  }
+  CUDA_TRY(upload(t, &t->d_ref_sub, ref_sub));
   std::vector<int32_t> oct_leaf, oct_ref;
   t->oct_leaf_off.assign(h.depth + 2, 0);
   t->oct_ref_off.assign(h.depth + 2, 0);
@@ -1710,11 +1799,19 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, bool mixed, int amc,
   CUDA_TRY(cudaGetLastError());
   ++nl;
   if ((rc = record(t, 2, st))) return rc;
-  // downward pass
-  for (int l = 0; l <= h.depth; ++l) {
-    int64_t s0 = h.lev_off[l], n = h.lev_off[l + 1] - h.lev_off[l];
-    if (mixed) k_l2l<true><<<blocks_for(n * kCells, 128), 128, 0, st>>>(A, l, s0, n);
-    else k_l2l<false><<<blocks_for(n * kCells, 128), 128, 0, st>>>(A, l, s0, n);
+  // downward pass: the roots, then per level the refined cells' totals and the leaf cells
+  if (mixed) k_root_total<true><<<blocks_for(int64_t(h.n_trees) * kCells, 128), 128, 0, st>>>(A);
+  else k_root_total<false><<<blocks_for(int64_t(h.n_trees) * kCells, 128), 128, 0, st>>>(A);
+  CUDA_TRY(cudaGetLastError());
+  ++nl;
+  for (int l = 1; l <= h.depth; ++l) {
+    const int64_t nr = t->ref_off[l + 1] - t->ref_off[l];
+    const int64_t no = t->oct_leaf_off[l] - t->oct_leaf_off[l - 1];
+    if (nr * 8 + no == 0) continue;
+    const int32_t* ref = t->d_ref_sub + t->ref_off[l];
+    const int32_t* octs = t->d_oct_leaf + t->oct_leaf_off[l - 1];
+    if (mixed) k_down<true><<<unsigned(nr * 8 + no), 64, 0, st>>>(A, l, ref, int(nr * 8), octs);
+    else k_down<false><<<unsigned(nr * 8 + no), 64, 0, st>>>(A, l, ref, int(nr * 8), octs);
     CUDA_TRY(cudaGetLastError());
     ++nl;
   }
