@@ -118,8 +118,15 @@ struct DevArgs {
 constexpr int kStencilCap = 1024;
 constexpr int kLeafCap = 1024;       // stencil + near entries per parity
 constexpr int kHalo = 18;            // subgrid plus 5 cells on each side
-constexpr int kHalo2 = kHalo * kHalo;
-constexpr int kHalo3 = kHalo2 * kHalo;
+// The halo is stored split by cell parity: cell (x, y, z) of the 18^3 halo at
+// ((x & 1) << 2 | (y & 1) << 1 | (z & 1)) * kHaloPar + (x >> 1) * kHaloSX + (y >> 1) * kHaloSY + (z >> 1),
+// each parity class a 9 x 9 x 9 lattice padded to strides 120 / 10 / 1.  A warp's lanes read one
+// parity class at lattice offsets 120 i + 10 j + k (i, j < 4, k < 2 or k >= 2), which fall on 32
+// distinct 4-byte banks, and on 16 distinct 8-byte banks per half warp.
+constexpr int kHaloSY = 10;
+constexpr int kHaloSX = 120;
+constexpr int kHaloPar = 9 * kHaloSX;
+constexpr int kHaloWords = 8 * kHaloPar;
 constexpr int kLeafThreads = 256;    // one block = one leaf subgrid, two target cells per thread
 constexpr int kRootChunks = 8;       // root sources split into 8 chunks of 64 cells
 constexpr int kM2LThreads = 64;      // one block = the 64 cells of one parity of one subgrid
@@ -805,7 +812,8 @@ struct LeafTab<float> {
 // neighbours, whose partners the boundary pass of k_m2l_ref adds afterwards).
 template <typename T>
 __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int32_t* __restrict__ work) {
-  __shared__ T hm[kHalo3];
+  extern __shared__ __align__(16) unsigned char leaf_smem[];
+  T* hm = reinterpret_cast<T*>(leaf_smem);  // kHaloWords
   __shared__ int32_t nb[27];
   const int32_t s = work[blockIdx.x];
   const int t = threadIdx.x;
@@ -816,20 +824,22 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
   __syncthreads();
   const T* __restrict__ M = MomView<T>::get(A);
   const int64_t N = A.n_cell;
-  for (int i = t; i < kHalo3; i += kLeafThreads) {
-    int hx = i / kHalo2, r = i - hx * kHalo2, hy = r / kHalo, hz = r - hy * kHalo;
-    int x = hx - 5, y = hy - 5, z = hz - 5;
-    int32_t q = nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)];
-    hm[i] = q >= 0 ? M[int64_t(q) * kCells + cidx(x & 7, y & 7, z & 7)] : T(0);
+  for (int i = t; i < kHalo * kHalo * kHalo; i += kLeafThreads) {
+    const int hx = i / (kHalo * kHalo), r = i - hx * (kHalo * kHalo), hy = r / kHalo, hz = r - hy * kHalo;
+    const int x = hx - 5, y = hy - 5, z = hz - 5;
+    const int32_t q = nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)];
+    hm[((hx & 1) << 2 | (hy & 1) << 1 | (hz & 1)) * kHaloPar + (hx >> 1) * kHaloSX + (hy >> 1) * kHaloSY +
+       (hz >> 1)] = q >= 0 ? M[int64_t(q) * kCells + cidx(x & 7, y & 7, z & 7)] : T(0);
   }
   __syncthreads();
   const T h = cell_h<T>(A.level[s]);
+  // warp = parity class; lane = lattice cell (i, j, k), k < 2; second target k + 2
   const int parity = t >> 5, lane = t & 31;
   const int px = (parity >> 2) & 1, py = (parity >> 1) & 1, pz = parity & 1;
-  const int a0 = 2 * (lane >> 4) + px,  // second target: a0 + 4
-            b = 2 * ((lane >> 2) & 3) + py, c = 2 * (lane & 3) + pz;
-  const int base0 = (a0 + 5) * kHalo2 + (b + 5) * kHalo + (c + 5);
-  const int base1 = base0 + 4 * kHalo2;
+  const int li = lane >> 3, lj = (lane >> 1) & 3, lk = lane & 1;
+  const int a = 2 * li + px, b = 2 * lj + py, c0 = 2 * lk + pz;  // second target: c0 + 4
+  const int base0 = li * kHaloSX + lj * kHaloSY + lk;
+  const int base1 = base0 + 2;
   const int32_t* __restrict__ toff = A.ltab_off + parity * kLeafCap;
   const T* __restrict__ tk = LeafTab<T>::get(A) + int64_t(parity) * kLeafCap * 4;
   const int n_tab = A.n_stencil + A.n_near;
@@ -850,8 +860,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
     uz += m1 * kz;
   }
   const T ih = T(1) / h, ih2 = ih * ih;
-  const int64_t i0 = int64_t(s) * kCells + cidx(a0, b, c);
-  const int64_t i1 = int64_t(s) * kCells + cidx(a0 + 4, b, c);
+  const int64_t i0 = int64_t(s) * kCells + cidx(a, b, c0);
+  const int64_t i1 = int64_t(s) * kCells + cidx(a, b, c0 + 4);
   if (sizeof(T) == 8) {
     double* L = reinterpret_cast<double*>(A.loc);
     L[i0] = -double(s0 * ih);
@@ -1303,6 +1313,10 @@ static int ensure_device(fmm_tree* t) {
   }
   t->device = dev;
   CUDA_TRY(cudaDeviceGetAttribute(&t->n_sms, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(kHaloWords * sizeof(double))));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(kHaloWords * sizeof(float))));
   const HostTree& h = t->h;
   const int64_t nc = h.n_sub * kCells;
   CUDA_TRY(upload(t, &t->d_level, h.level));
@@ -1615,7 +1629,12 @@ static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
         double d2 = double(dx * dx + dy * dy + dz * dz);
         double k0 = 1.0 / std::sqrt(d2), k3 = k0 / d2;
         size_t e = size_t(p) * kLeafCap + q;
-        loff[e] = dx * kHalo2 + dy * kHalo + dz;
+        // source halo cell (a + d + 5) of a target of parity p: its parity class and lattice
+        // offset from the target's lattice cell
+        const int px = (p >> 2) & 1, py = (p >> 1) & 1, pz = p & 1;
+        const int hx = px + dx + 5, hy = py + dy + 5, hz = pz + dz + 5;
+        loff[e] = ((hx & 1) << 2 | (hy & 1) << 1 | (hz & 1)) * kHaloPar + (hx >> 1) * kHaloSX +
+                  (hy >> 1) * kHaloSY + (hz >> 1);
         lcode[e] = all[q];
         double kk[4] = {k0, dx * k3, dy * k3, dz * k3};
         double dd[4] = {double(dx), double(dy), double(dz), 0.0};
@@ -1786,8 +1805,12 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, bool mixed, int amc,
   // interactions: leaf subgrids of levels >= 1 (same-level leaf partners), then the general
   // kernel: root chunks, every (refined subgrid, parity) and every (boundary leaf subgrid, parity)
   if (t->n_work_leaf > 0) {
-    if (mixed) k_m2l_leaf<float><<<unsigned(t->n_work_leaf), kLeafThreads, 0, st>>>(A, t->d_work_leaf);
-    else k_m2l_leaf<double><<<unsigned(t->n_work_leaf), kLeafThreads, 0, st>>>(A, t->d_work_leaf);
+    if (mixed)
+      k_m2l_leaf<float><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), st>>>(
+          A, t->d_work_leaf);
+    else
+      k_m2l_leaf<double><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(double), st>>>(
+          A, t->d_work_leaf);
     CUDA_TRY(cudaGetLastError());
     ++nl;
   }
