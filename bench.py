@@ -54,6 +54,32 @@ FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1e3    # 2 FP64 FMA / clock / SM
 FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MAX_GHZ / 1e3  # 128 FP32 FMA / clock / SM
 
 
+def measured_traffic():
+    """Per-launch DRAM bytes of the interaction kernels from the committed ncu summary, if the
+    kernel sources are the ones it was captured from (else nothing: the counters are stale)."""
+    import hashlib
+    here = os.path.dirname(os.path.abspath(__file__))
+    csrc = os.path.join(here, "paper_2101_08226_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("fmm.cu", "fmm_kernels.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    out, sha = {}, None
+    try:
+        with open(os.path.join(here, "profiles", "dram_traffic.txt")) as fh:
+            for line in fh:
+                parts = line.split()
+                if not parts or parts[0].startswith("#"):
+                    continue
+                if parts[0] == "sha256":
+                    sha = parts[1]
+                else:
+                    out[parts[0]] = int(parts[1]) + int(parts[2])
+    except OSError:
+        return {}
+    return out if sha == h.hexdigest() else {}
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
@@ -208,6 +234,23 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_solve_only(args):
+    """Profiling driver: the benchmark tree, `--warmup` untimed solves then `--steps` more in the
+    given precision (graph-replayed, as in the timed run), nothing else -- a small, fixed launch
+    sequence to run under ncu."""
+    import torch
+    from paper_2101_08226_gb300 import api, build, synth
+    build.build()
+    w = synth.workload_binary(LEVELS)
+    tree = api.Tree(w.max_level, w.flags)
+    rho = torch.from_numpy(synth.leaf_density(w.field, tree.leaves())).cuda()
+    for _ in range(args.warmup + args.steps):
+        phi, g, net = tree.solve(rho, THETA, args.solve_only, True)
+    torch.cuda.synchronize()
+    print(json.dumps({"solve_only": args.solve_only, "solves": args.warmup + args.steps,
+                      "launches_per_solve": tree.last_launches(), "net": net.cpu().tolist()}))
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -323,6 +366,8 @@ def run_ours(args):
     value64 = world * n_m2l * args.steps / (t64 * 1e-3)
     value32 = world * n_m2l * args.steps / (t32 * 1e-3)
 
+    traffic = measured_traffic()
+
     def roofline(ph, precision):
         # the dominant interaction kernel of this precision, timed with CUDA events on the
         # solve's stream inside the timed region
@@ -331,9 +376,11 @@ def run_ours(args):
         ach = kernel_flops[k] / (ms[k] * 1e-3) / 1e12
         peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
         unit = "FP64" if precision == "fp64" else "FP32"
-        return {"bound": "alu", "kernel": f"{k}<{'double' if precision == 'fp64' else 'float'}>",
+        kname = f"{k}<{'double' if precision == 'fp64' else 'float'}>"
+        return {"bound": "alu", "kernel": kname,
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel_ms": ms[k], "kernel_flops": kernel_flops[k],
+                "traffic": traffic.get(kname), "traffic_unit": "bytes per launch (ncu)",
+                "kernel_ms": ms[k], "kernel_flops": kernel_flops[k],
                 "other_kernel_ms": {kk: v for kk, v in ms.items() if kk != k},
                 "peak_source": f"derived: 152 SMs x {2 if unit == 'FP64' else 128} {unit} FMA/clk "
                                "x 2 flop x 2.07 GHz"}
@@ -380,8 +427,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--solve-only", choices=["fp64", "mixed"], default=None,
+                    help="profiling driver: run warmup + steps solves of the benchmark tree, no timing")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.solve_only:
+        run_solve_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
