@@ -136,6 +136,46 @@ def algorithmic_flops(counts):
     return sum(FLOPS[k] * v for k, v in counts.items())
 
 
+def measure_paper_binary(tree_api, synth, torch, dev, stream, steps, flush):
+    """The merger binary in the paper's proportions (9 levels, theta = 0.34, 2.07M leaf cells):
+    the same metric on the paper's deepest tree and smallest opening angle."""
+    w = synth.workload_paper_binary()
+    t = tree_api.Tree(w.max_level, w.flags)
+    n_sub, n_leaf_sub, _ = t.info()
+    rho0 = synth.leaf_density(w.field, t.leaves())
+    floor = w.field.floor * w.field.rho_peak
+    rhos = [torch.from_numpy(synth.perturbed_density(rho0, 500 + k, floor_value=floor)).to(dev)
+            for k in range(steps + 2)]
+    counts = t.counts_by_type(w.theta)
+    n_m2l = sum(v for k, v in counts.items() if k.startswith("m2l"))
+    out = {"workload": "merger binary in the paper's proportions: q=0.5, accretor 50 finest cells "
+                       "across, donor filling its Roche lobe, a=0.024 of the box, 9 levels, "
+                       "refine_frac 1e-4, theta=0.34",
+           "subgrids": n_sub, "leaf_cells": n_leaf_sub * 512, "m2l_pairs": n_m2l,
+           "pair_types": counts, "l2": "flushed before every timed solve"}
+    for precision in ("fp64", "mixed"):
+        for k in range(2):
+            t.solve(rhos[k], w.theta, precision, True, stream=stream, check_status=False)
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t.solve(rhos[2 + k], w.theta, precision, True, stream=stream, check_status=False)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t.sync_status(stream)
+        tm = float(np.mean(ms))
+        out[precision] = {"value": n_m2l / (tm * 1e-3), "ms_per_solve": tm,
+                          "gpu_launches": t.last_launches()}
+    out["unit"] = "interactions/s"
+    t.close()
+    return out
+
+
 def measure_batched(tree_api, synth, torch, dev, stream, steps):
     """The 64 seeded trees of uneven depth (levels 2..5, single stars or binaries) as one forest:
     every level of every tree in one set of launches.  Same metric as the headline."""
@@ -357,6 +397,7 @@ def run_ours(args):
         e2e_s = float(tt.item())
 
     batched = measure_batched(api, synth, torch, dev, stream, min(args.steps, 3))
+    paper = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), flush)
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -412,6 +453,7 @@ def run_ours(args):
                 "precision": "fp64"},
         "gpu_launches": l64,
         "batched": batched,
+        "paper_binary": paper,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }

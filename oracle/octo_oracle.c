@@ -51,7 +51,7 @@
 #endif
 
 #define NSUB 8
-#define O_MAXLEV 9 /* levels 0..8 */
+#define O_MAXLEV 10 /* levels 0..9 (the paper's merger models use 9 refinement levels) */
 #define NMOM 40    /* m, X[3], M2[9], M3[27] */
 #define NLOC 40    /* L0, L1[3], L2[9], L3[27] */
 

@@ -321,6 +321,29 @@ def workload_binary(levels: int = 4, q: float = 0.7, r1: float = 0.1, r2: float 
                                  "axis": tuple(axis), "offset": tuple(offset)})
 
 
+def roche_lobe_radius(q: float, a: float) -> float:
+    """Eggleton's volume-equivalent Roche-lobe radius of a star of mass ratio q = M_star / M_other
+    at separation a (an approximation accurate to 1 % for all q)."""
+    q23 = q ** (2.0 / 3.0)
+    return a * 0.49 * q23 / (0.6 * q23 + math.log(1.0 + q ** (1.0 / 3.0)))
+
+
+def workload_paper_binary(levels: int = 9, theta: float = 0.34, refine_frac: float = 1e-4) -> Workload:
+    """The merger models' binary in the paper's proportions (Sec. 4): a domain 40 code lengths wide
+    mapped to the unit box, 9 refinement levels (finest spacing 1/4096 of the box), accretor 50
+    finest cells across, donor of half the accretor's mass filling its Roche lobe (spherical
+    stand-in of the lobe's volume-equivalent radius), separation 0.96 code lengths (6e-2 solar
+    radii), theta = 0.34 as for the paper's interacting binaries.  Refinement: every subgrid whose
+    volume reaches a density above refine_frac * rho_peak is refined, to the deepest level."""
+    a = 0.96 / 40.0
+    q = 0.5
+    r1 = 25.0 / 4096.0
+    r2 = roche_lobe_radius(q, a)
+    fld = binary_field(q, r1, r2, a)
+    return Workload(f"paper_binary_L{levels}", levels, refinement_flags(fld, levels, refine_frac),
+                    fld, theta, {"q": q, "r1": r1, "r2": r2, "a": a, "refine_frac": refine_frac})
+
+
 def workload_uniform_sphere(depth: int, theta: float = 0.5) -> Workload:
     return Workload(f"uniform_sphere_d{depth}", depth, uniform_flags(depth),
                     uniform_sphere_field(), theta, {"depth": depth})

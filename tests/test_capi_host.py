@@ -69,6 +69,15 @@ def test_large_binary_tree_equals_oracle_tree():
     assert sa.shape[0] > 10000
 
 
+def test_nine_level_paper_binary_tree_equals_oracle_tree():
+    """The deepest tree the paper uses (9 refinement levels), built both ways."""
+    w = synth.workload_paper_binary()
+    a = api.Tree(w.max_level, w.flags)
+    b = O.Tree(w.max_level, w.flags)
+    assert np.array_equal(a.subgrids(), b.subgrids())
+    assert a.subgrids()[:, 0].max() == 9
+
+
 @pytest.mark.parametrize("theta", [0.34, 0.35, 0.4, 0.5, 0.6, 0.7, 0.9, 0.999])
 def test_stencil_equals_oracle(theta):
     for p in range(8):

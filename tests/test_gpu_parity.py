@@ -203,3 +203,27 @@ def test_full_size_sampled(levels, precision):
     else:
         assert np.abs(phi[idx] - ps).max() / np.abs(ps).max() <= MIXED_PHI_TOL
         assert np.abs(g[idx] - gs).max() / np.abs(g).max() <= MIXED_G_TOL
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_paper_binary_sampled(precision):
+    """The merger binary in the paper's proportions: 9 levels, theta = 0.34, 2.07M leaf cells;
+    the oracle evaluates sampled leaf cells one by one."""
+    w = synth.workload_paper_binary()
+    a, b = both_trees(w.max_level, w.flags)
+    rho = synth.leaf_density(w.field, b.leaves())
+    phi, g, net = gpu_solve(a, rho, w.theta, precision)
+    lev = np.repeat(b.leaves()[:, 0], 512)
+    idx = np.random.default_rng(9).choice(rho.size, 48, replace=False)
+    extra = [int(np.nonzero(lev == l)[0][len(np.nonzero(lev == l)[0]) // 2]) for l in np.unique(lev)]
+    idx = np.unique(np.concatenate([idx, extra]))
+    ps, gs = O.sample(b, rho, w.theta, idx)
+    if precision == "fp64":
+        d_phi = np.abs(phi[idx] - ps) / np.abs(ps)
+        d_g = np.linalg.norm(g[idx] - gs, axis=1) / np.maximum(np.linalg.norm(gs, axis=1),
+                                                                 1e-6 * np.abs(g).max())
+        assert d_phi.max() <= FP64_TOL and d_g.max() <= FP64_TOL
+        assert np.abs(net[:6]).max() <= CONS_TOL * net[6]
+    else:
+        assert np.abs(phi[idx] - ps).max() / np.abs(ps).max() <= MIXED_PHI_TOL
+        assert np.abs(g[idx] - gs).max() / np.abs(g).max() <= MIXED_G_TOL

@@ -85,3 +85,19 @@ def test_batched_workloads_are_deterministic_and_valid():
     for a, b in zip(w1, w2):
         assert a.max_level == b.max_level and np.array_equal(a.flags, b.flags)
         assert 2 <= a.max_level <= 5
+
+
+def test_roche_lobe_and_paper_binary():
+    # Eggleton's formula at q = 1: 0.49 / (0.6 + ln 2)
+    assert abs(synth.roche_lobe_radius(1.0, 1.0) - 0.49 / (0.6 + np.log(2.0))) < 1e-15
+    w = synth.workload_paper_binary()
+    s1, s2 = w.field.stars
+    assert w.max_level == 9 and w.theta == 0.34
+    assert abs((s2.center[0] - s1.center[0]) - 0.024) < 1e-15
+    # the donor fills its lobe, holds half the accretor's mass, and the centre of mass is at 0
+    assert abs(s2.radius - synth.roche_lobe_radius(0.5, 0.024)) < 1e-15
+    m1, m2 = s1.rho_c * s1.radius ** 3, s2.rho_c * s2.radius ** 3
+    assert abs(m2 / m1 - 0.5) < 1e-12
+    assert abs(m1 * s1.center[0] + m2 * s2.center[0]) < 1e-15 * m1
+    # the accretor spans 50 finest cells
+    assert abs(2 * s1.radius * 4096 - 50) < 1e-9
