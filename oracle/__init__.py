@@ -54,6 +54,10 @@ def lib():
         L.oracle_m2l.restype = None
         L.oracle_local_eval.argtypes = [vp, vp, vp, vp]
         L.oracle_local_eval.restype = None
+        L.oracle_fmm_sample_dt.argtypes = [vp, vp, vp, dbl, i32, i64, vp, vp]
+        L.oracle_fmm_sample_dt.restype = None
+        L.oracle_m2l_source.argtypes = [vp, vp, vp, vp]
+        L.oracle_m2l_source.restype = None
         L.oracle_max_threads.argtypes = []
         L.oracle_max_threads.restype = i32
         _lib = L
@@ -139,6 +143,34 @@ def sample(tree: Tree, rho: np.ndarray, theta: float, idx: np.ndarray, amc: bool
     if with_counts:
         return phi, g, {"m2l": int(cnt[0]), "p2p_same": int(cnt[1]), "p2p_mixed": int(cnt[2])}
     return phi, g
+
+
+def solve_dt(tree: Tree, rho: np.ndarray, src: np.ndarray, theta: float, idx=None,
+             nthreads: int = 0) -> np.ndarray:
+    """dphi/dt (Sec. 2.1): the rho solve's operator applied to the source density src (d rho/dt),
+    at every leaf cell or at the listed ones."""
+    rho = _f64(rho)
+    src = _f64(src)
+    n = tree.n_leaf_cells
+    assert rho.shape == (n,) and src.shape == (n,)
+    if idx is None:
+        out = np.empty(n)
+        lib().oracle_fmm_sample_dt(tree._h, _p(rho), _p(src), float(theta), int(nthreads), n, None,
+                                   _p(out))
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        out = np.empty(idx.size)
+        lib().oracle_fmm_sample_dt(tree._h, _p(rho), _p(src), float(theta), int(nthreads),
+                                   int(idx.size), _p(idx), _p(out))
+    return out
+
+
+def m2l_source(XA, XB, smB) -> np.ndarray:
+    """Expansion (40 numbers) at centre XA due to source moments smB (S0, S1[3], S2[9], S3[27])
+    about XB."""
+    L = np.zeros(40)
+    lib().oracle_m2l_source(_p(_f64(XA)), _p(_f64(XB)), _p(_f64(smB)), _p(L))
+    return L
 
 
 def inner_moments(tree: Tree, rho: np.ndarray, nthreads: int = 0) -> np.ndarray:

@@ -40,6 +40,17 @@
  *   5. Leaf pairs whose cells are not well separated at the level of the coarser of the two
  *      leaves interact directly (point-mass sum).  Every leaf pair is then covered exactly once.
  *
+ * The time derivative of the potential (Sec. 2.1: the FMM with the numerically computed
+ * d(rho)/dt as the source, so that the two parts of the energy source term cancel when summed
+ * over the grid): the same operator -- same lists, the same expansion centres X_A (rho's
+ * centres of mass), the same truncation -- applied to a source s_i = (d rho/dt)_i dx^3.  About
+ * those centres s has a dipole, so a cell carries S0 = sum s, S1 = sum s r, S2 = sum s r r,
+ * S3 = sum s r r r (r = x_i - X_A), and expanding -s/|R + t - u| to total order 3 gives
+ *        L_k = -sum_(n <= 3 - k) (-1)^n / n! D^(k+n) : S_n,
+ * which is step 3 with the dipole terms added (S1 = 0 for rho itself).  Only the potential is
+ * evaluated; there is no correction term.  With these centres the operator is symmetric, so
+ * sum_i s_i phi_i = sum_i m_i (dphi/dt)_i up to rounding -- the cancellation the paper relies on.
+ *
  * Readings where the paper is silent are listed in the design notes; this file implements them.
  */
 #include <math.h>
@@ -813,3 +824,217 @@ void oracle_direct(int64_t n, const double *x, const double *m, int nthreads, do
 }
 
 int oracle_max_threads(void) { return resolve_threads(0); }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Time derivative of the potential (Sec. 2.1)                                                */
+/* ------------------------------------------------------------------------------------------ */
+#define NSRC 40 /* S0, S1[3], S2[9], S3[27] about the cell's rho centre of mass */
+
+typedef struct {
+  ctx_t C;             /* the rho field: lists, centres of mass */
+  const double *src;   /* source density (d rho / dt), canonical leaf order */
+  double *inner_src;   /* [n_inner_sub * 512][NSRC] */
+} dt_ctx;
+
+static void leaf_source_of(const dt_ctx *D, int lev, const int64_t g[3], double *s, double x[3]) {
+  int64_t sg = cell_subgrid(D->C.t, lev, g);
+  double dx = cell_dx(lev);
+  *s = D->src[D->C.t->leaf_slot[lev][sg] * 512 + local_index(g)] * dx * dx * dx;
+  cell_centre(lev, g, x);
+}
+
+typedef struct { const dt_ctx *D; const double *X; csum S0, S1[3], S2[9], S3[27]; } src_acc;
+
+static void src_acc_leaf(void *u, int lev, const int64_t g[3]) {
+  src_acc *A = (src_acc *)u;
+  double sv, x[3], r[3];
+  leaf_source_of(A->D, lev, g, &sv, x);
+  for (int a = 0; a < 3; ++a) r[a] = x[a] - A->X[a];
+  csum_add(&A->S0, sv);
+  for (int a = 0; a < 3; ++a) {
+    csum_add(&A->S1[a], sv * r[a]);
+    for (int b = 0; b < 3; ++b) {
+      csum_add(&A->S2[3 * a + b], sv * r[a] * r[b]);
+      for (int c = 0; c < 3; ++c) csum_add(&A->S3[9 * a + 3 * b + c], sv * r[a] * r[b] * r[c]);
+    }
+  }
+}
+
+/* Source moments of a cell about its rho centre of mass X (written to X as well). */
+static void cell_source_moments(const dt_ctx *D, int lev, const int64_t g[3], double sm[NSRC],
+                                double X[3]) {
+  double mom[NMOM];
+  cell_moments(&D->C, lev, g, mom);
+  memcpy(X, mom + 1, sizeof(double) * 3);
+  int64_t sg = cell_subgrid(D->C.t, lev, g);
+  if (D->C.t->leaf[lev][sg]) {
+    double x[3];
+    memset(sm, 0, sizeof(double) * NSRC);
+    leaf_source_of(D, lev, g, &sm[0], x);
+    return;
+  }
+  memcpy(sm, D->inner_src + (D->C.t->inner_slot[lev][sg] * 512 + local_index(g)) * NSRC,
+         sizeof(double) * NSRC);
+}
+
+static void compute_inner_sources(dt_ctx *D, int nthreads) {
+  const otree *t = D->C.t;
+  D->inner_src = (double *)calloc((size_t)(t->n_inner_sub ? t->n_inner_sub : 1) * 512 * NSRC,
+                                  sizeof(double));
+  for (int l = 0; l <= t->depth; ++l) {
+    int64_t cnt = t->count[l];
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+    for (int64_t sg = 0; sg < cnt; ++sg) {
+      if (t->leaf[l][sg]) continue;
+      for (int64_t c = 0; c < 512; ++c) {
+        int64_t g[3] = {(int64_t)t->ijk[l][3 * sg] * NSUB + c / 64,
+                        (int64_t)t->ijk[l][3 * sg + 1] * NSUB + (c / 8) % 8,
+                        (int64_t)t->ijk[l][3 * sg + 2] * NSUB + c % 8};
+        double mom[NMOM];
+        cell_moments(&D->C, l, g, mom);
+        src_acc A;
+        memset(&A, 0, sizeof(A));
+        A.D = D;
+        A.X = mom + 1;
+        visit_leaves(t, l, g, src_acc_leaf, &A);
+        double *out = D->inner_src + (t->inner_slot[l][sg] * 512 + c) * NSRC;
+        out[0] = csum_val(&A.S0);
+        for (int k = 0; k < 3; ++k) out[1 + k] = csum_val(&A.S1[k]);
+        for (int k = 0; k < 9; ++k) out[4 + k] = csum_val(&A.S2[k]);
+        for (int k = 0; k < 27; ++k) out[13 + k] = csum_val(&A.S3[k]);
+      }
+    }
+  }
+}
+
+/* Adds the expansion at centre XA due to the source moments smB about XB:
+ *   L_k -= sum_(n <= 3 - k) (-1)^n / n! D^(k+n) : S_n. */
+void oracle_m2l_source(const double *XA, const double *XB, const double *smB, double *L) {
+  double Dt[121];
+  double R[3] = {XA[0] - XB[0], XA[1] - XB[1], XA[2] - XB[2]};
+  oracle_dtensors(R, Dt);
+  const double *D0 = Dt, *D1 = Dt + 1, *D2 = Dt + 4, *D3 = Dt + 13;
+  const double S0 = smB[0], *S1 = smB + 1, *S2 = smB + 4, *S3 = smB + 13;
+  double l0 = S0 * D0[0];
+  for (int a = 0; a < 3; ++a) {
+    l0 -= D1[a] * S1[a];
+    for (int b = 0; b < 3; ++b) {
+      l0 += 0.5 * D2[3 * a + b] * S2[3 * a + b];
+      for (int c = 0; c < 3; ++c) l0 -= D3[9 * a + 3 * b + c] * S3[9 * a + 3 * b + c] / 6.0;
+    }
+  }
+  L[0] -= l0;
+  for (int a = 0; a < 3; ++a) {
+    double l1 = S0 * D1[a];
+    for (int b = 0; b < 3; ++b) {
+      l1 -= D2[3 * a + b] * S1[b];
+      for (int c = 0; c < 3; ++c) l1 += 0.5 * D3[9 * a + 3 * b + c] * S2[3 * b + c];
+    }
+    L[1 + a] -= l1;
+    for (int b = 0; b < 3; ++b) {
+      double l2 = S0 * D2[3 * a + b];
+      for (int c = 0; c < 3; ++c) l2 -= D3[9 * a + 3 * b + c] * S1[c];
+      L[4 + 3 * a + b] -= l2;
+      for (int c = 0; c < 3; ++c) L[13 + 9 * a + 3 * b + c] -= S0 * D3[9 * a + 3 * b + c];
+    }
+  }
+}
+
+typedef struct {
+  const dt_ctx *D;
+  double XA[3];
+  double L[NLOC];
+} src_m2l_acc;
+
+static void src_m2l_cb(void *u, int lev, const int64_t gB[3]) {
+  src_m2l_acc *A = (src_m2l_acc *)u;
+  double sm[NSRC], XB[3];
+  cell_source_moments(A->D, lev, gB, sm, XB);
+  oracle_m2l_source(A->XA, XB, sm, A->L);
+}
+
+/* The source expansion of cell (lev, g) about its rho centre of mass. */
+static void cell_source_expansion(const dt_ctx *D, int lev, const int64_t g[3], double theta,
+                                  double L[NLOC], double XA[3]) {
+  src_m2l_acc A;
+  memset(&A, 0, sizeof(A));
+  A.D = D;
+  double mom[NMOM];
+  cell_moments(&D->C, lev, g, mom);
+  memcpy(A.XA, mom + 1, sizeof(A.XA));
+  for_each_m2l_partner(D->C.t, lev, g, theta, src_m2l_cb, &A);
+  memcpy(L, A.L, sizeof(A.L));
+  memcpy(XA, A.XA, sizeof(A.XA));
+}
+
+typedef struct { const dt_ctx *D; double x[3]; double phi; } src_p2p_acc;
+
+static void src_p2p_leaf_cb(void *u, int lev, const int64_t gB[3]) {
+  src_p2p_acc *P = (src_p2p_acc *)u;
+  double sv, y[3];
+  leaf_source_of(P->D, lev, gB, &sv, y);
+  double d[3] = {P->x[0] - y[0], P->x[1] - y[1], P->x[2] - y[2]};
+  P->phi += -sv / sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+}
+
+static void src_p2p_same_level_cb(void *u, int lev, const int64_t gB[3]) {
+  src_p2p_acc *P = (src_p2p_acc *)u;
+  visit_leaves(P->D->C.t, lev, gB, src_p2p_leaf_cb, P);
+}
+
+static void src_p2p_coarser_cb(void *u, int lev, const int64_t gB[3]) {
+  src_p2p_acc *P = (src_p2p_acc *)u;
+  int64_t sg = cell_subgrid(P->D->C.t, lev, gB);
+  if (P->D->C.t->leaf[lev][sg]) src_p2p_leaf_cb(u, lev, gB);
+}
+
+/* dphi/dt of one leaf cell: its own and every ancestor's source expansion evaluated at the
+ * leaf's centre, plus the direct sums over the same partners as the rho solve. */
+static double leaf_solve_dt(const dt_ctx *D, int lev, const int64_t g[3], double theta) {
+  const otree *t = D->C.t;
+  double x[3], ev[4], L[NLOC], X[3];
+  cell_centre(lev, g, x);
+  double ph = 0;
+  for (int m = 0; m <= lev; ++m) {
+    int sh = lev - m;
+    int64_t gA[3] = {g[0] >> sh, g[1] >> sh, g[2] >> sh};
+    cell_source_expansion(D, m, gA, theta, L, X);
+    oracle_local_eval(L, X, x, ev);
+    ph += ev[0];
+  }
+  src_p2p_acc P;
+  memset(&P, 0, sizeof(P));
+  P.D = D;
+  memcpy(P.x, x, sizeof(x));
+  for (int m = 0; m < lev; ++m) {
+    int sh = lev - m;
+    int64_t gA[3] = {g[0] >> sh, g[1] >> sh, g[2] >> sh};
+    for_each_near_cell(t, m, gA, theta, src_p2p_coarser_cb, &P);
+  }
+  for_each_near_cell(t, lev, g, theta, src_p2p_same_level_cb, &P);
+  return ph + P.phi;
+}
+
+/* dphi/dt at the leaf cells listed in idx (all leaf cells when idx is NULL and ns is their
+ * number): rho fixes the tree's expansion centres, src is the source density. */
+void oracle_fmm_sample_dt(const otree *t, const double *rho, const double *src, double theta,
+                          int nthreads, int64_t ns, const int64_t *idx, double *phidot) {
+  nthreads = resolve_threads(nthreads);
+  dt_ctx D;
+  memset(&D, 0, sizeof(D));
+  D.C.t = t;
+  D.C.rho = rho;
+  D.src = src;
+  compute_inner_moments(&D.C, nthreads);
+  compute_inner_sources(&D, nthreads);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+  for (int64_t q = 0; q < ns; ++q) {
+    int lev = 0;
+    int64_t gc[3] = {0, 0, 0};
+    leaf_cell_coords(t, idx ? idx[q] : q, &lev, gc);
+    phidot[q] = leaf_solve_dt(&D, lev, gc, theta);
+  }
+  free(D.inner_src);
+  free(D.C.inner_mom);
+}
+

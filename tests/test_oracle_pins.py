@@ -410,3 +410,94 @@ def test_n1_polytrope_closed_form():
         res.append(np.abs((phi_cells - an) / an)[star].mean())
     assert res[1] < res[0]
     assert res[1] < 5e-3
+
+
+# ------------------------------------------------------------------------------------------
+# time derivative of the potential (Sec. 2.1)
+# ------------------------------------------------------------------------------------------
+def _source_moments(x, s, X):
+    """S0, S1, S2, S3 of signed point sources about X (input preparation for the cluster test)."""
+    r = x - X
+    return np.concatenate([[s.sum()], np.einsum("i,ia->a", s, r),
+                           np.einsum("i,ia,ib->ab", s, r, r).ravel(),
+                           np.einsum("i,ia,ib,ic->abc", s, r, r, r).ravel()])
+
+
+def test_source_expansion_error_order_with_dipole():
+    """Signed sources about a centre that is not their centroid (so S1 != 0): the expansion's
+    error against the exact sum falls as h^4; a missing or mis-signed dipole term would leave
+    an error of order h or h^2."""
+    rng = np.random.default_rng(3)
+    xb0 = rng.uniform(-1, 1, (30, 3))
+    s = rng.uniform(-1.0, 1.5, 30)
+    ya0 = rng.uniform(-1, 1, (6, 3))
+    XA = np.array([10.0, 3.0, -4.0])
+    errs = []
+    for h in (0.4, 0.2, 0.1):
+        xb = h * xb0
+        sm = _source_moments(xb, s, np.zeros(3))
+        assert np.abs(sm[1:4]).max() > 0.1 * h * np.abs(s).sum() / 30
+        L = O.m2l_source(XA, np.zeros(3), sm)
+        e = 0.0
+        for y in XA + h * ya0:
+            phi, _ = O.local_eval(L, XA, y)
+            e = max(e, abs(phi + (s / np.linalg.norm(y - xb, axis=1)).sum()))
+        errs.append(e)
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 12 < e0 / e1 < 20
+
+
+def _amr_cases():
+    fl = np.zeros(synth.flags_size(3), dtype=np.uint8)
+    fl[0] = 1
+    fl[synth.flags_offset(1)] = 1
+    fl[synth.flags_offset(2) + (1 * 4 + 1) * 4] = 1
+    yield 3, fl, synth.binary_field(0.7, 0.1, 0.085, 0.35)
+    w = synth.workload_binary(3, axis=(1.0, 0.6, 0.3), offset=(0.02, -0.03, 0.05))
+    yield w.max_level, w.flags, w.field
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_dt_of_rho_is_phi(case):
+    """With d rho/dt = rho the source moments about rho's centres of mass have no dipole, and
+    the time-derivative solve is the potential of the rho solve."""
+    max_level, flags, fld = list(_amr_cases())[case]
+    t = O.Tree(max_level, flags)
+    rho = synth.leaf_density(fld, t.leaves())
+    phi, _, _ = O.solve(t, rho, 0.5)
+    pd = O.solve_dt(t, rho, rho, 0.5)
+    assert np.abs(pd - phi).max() <= 1e-13 * np.abs(phi).max()
+
+
+@pytest.mark.parametrize("case", [0, 1])
+@pytest.mark.parametrize("theta", [0.5, 0.34])
+def test_dt_energy_terms_cancel(case, theta):
+    """Sec. 2.1: with the rho centres the operator is symmetric, so sum_i s_i phi_i equals
+    sum_i m_i (dphi/dt)_i -- the two parts of the energy source term cancel over the grid."""
+    max_level, flags, fld = list(_amr_cases())[case]
+    t = O.Tree(max_level, flags)
+    rho = synth.leaf_density(fld, t.leaves())
+    src = rho * np.random.default_rng(11).uniform(-1, 1, rho.size)
+    phi, _, _ = O.solve(t, rho, theta)
+    pd = O.solve_dt(t, rho, src, theta)
+    _, m = O.leaf_masses(t, rho)
+    _, s = O.leaf_masses(t, src)
+    lhs, rhs = (s * phi).sum(), (m * pd).sum()
+    scale = (np.abs(s) * np.abs(phi)).sum()
+    assert abs(lhs - rhs) <= 1e-14 * scale
+
+
+def test_dt_all_near_is_direct_sum_and_linear():
+    w = synth.workload_uniform_polytrope(1)
+    t = O.Tree(w.max_level, w.flags)
+    rho = synth.leaf_density(synth.binary_field(0.7, 0.1, 0.085, 0.35), t.leaves())
+    rng = np.random.default_rng(5)
+    s1 = rng.uniform(-1, 1, rho.size)
+    s2 = rng.uniform(-1, 1, rho.size)
+    x, m1 = O.leaf_masses(t, s1)
+    pd, _ = O.direct(x, m1)
+    got = O.solve_dt(t, rho, s1, 0.03)
+    assert np.abs(got - pd).max() <= 1e-13 * np.abs(pd).max()
+    a1, a2 = O.solve_dt(t, rho, s1, 0.5), O.solve_dt(t, rho, s2, 0.5)
+    a12 = O.solve_dt(t, rho, 2.0 * s1 - 3.0 * s2, 0.5)
+    assert np.abs(a12 - (2.0 * a1 - 3.0 * a2)).max() <= 1e-13 * np.abs(a12).max()
