@@ -127,6 +127,18 @@ int fmm_interaction_counts_by_type(const fmm_tree* tree, double theta, int64_t c
 int fmm_solve(fmm_tree* tree, const double* rho_dev, double theta, int precision, int amc,
               double* phi_dev, double* g_dev, double* net_dev, void* stream);
 
+/* fmm_solve plus the time derivative of the potential (Sec. 2.1: the FMM with the computed
+ * d(rho)/dt as the source, so that the two parts of the energy equation's gravity term cancel
+ * over the grid).  rhodot_dev: [n_leaf] d(rho)/dt (any sign, finite).  phidot_dev: [n_leaf]
+ * d(phi)/dt out: the same operator as the rho solve -- same lists, the same expansion centres
+ * (rho's centres of mass), the same truncation -- applied to s = rhodot dx^3, whose moments about
+ * those centres include a dipole.  With these centres the operator is symmetric:
+ * sum_i s_i phi_i = sum_i m_i phidot_i to rounding.  Other arguments, ordering and errors as
+ * fmm_solve (FMM_ERR_NONFINITE also for a NaN or infinite rhodot); one graph per configuration. */
+int fmm_solve_dt(fmm_tree* tree, const double* rho_dev, const double* rhodot_dev, double theta,
+                 int precision, int amc, double* phi_dev, double* g_dev, double* phidot_dev,
+                 double* net_dev, void* stream);
+
 /* fmm_solve on a forest with one device buffer per tree: rho_dev[k], phi_dev[k], g_dev[k] are
  * tree k's arrays (its own canonical order), read and written in place by the kernels (the
  * pointer arrays themselves are host arrays, read before the call returns); net_dev (optional)

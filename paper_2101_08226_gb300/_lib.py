@@ -21,7 +21,7 @@ FMM_MIXED = 1
 
 EXPORTS = [
     "fmm_build_tree", "fmm_destroy", "fmm_build_forest", "fmm_forest_info", "fmm_solve_batch", "fmm_tree_info", "fmm_tree_subgrids", "fmm_stencil",
-    "fmm_interaction_counts", "fmm_interaction_counts_by_type", "fmm_last_launches", "fmm_solve", "fmm_sync_status", "fmm_solve_host",
+    "fmm_interaction_counts", "fmm_interaction_counts_by_type", "fmm_last_launches", "fmm_solve", "fmm_solve_dt", "fmm_sync_status", "fmm_solve_host",
     "fmm_net_force_torque", "fmm_net_force_torque_points_static", "fmm_set_profiling", "fmm_set_graphs", "fmm_phase_times", "fmm_last_error",
 ]
 
@@ -50,6 +50,7 @@ def lib():
             "fmm_build_forest": (i32, [vp, i32, C.POINTER(vp)]),
             "fmm_forest_info": (i32, [vp, vp, vp]),
             "fmm_solve_batch": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
+            "fmm_solve_dt": (i32, [vp, vp, vp, dbl, i32, i32, vp, vp, vp, vp, vp]),
             "fmm_tree_info": (i32, [vp, vp, vp, vp]),
             "fmm_tree_subgrids": (i32, [vp, vp]),
             "fmm_stencil": (i32, [dbl, i32, vp, i32, vp]),

@@ -115,6 +115,26 @@ class Tree:
             check(lib().fmm_sync_status(self._h, sh))
         return phi, g, net
 
+    def solve_dt(self, rho, rhodot, theta: float, precision: str = "fp64", amc: bool = True,
+                 phi=None, g=None, phidot=None, net=None, stream=None, check_status: bool = True):
+        """fmm_solve_dt: (phi, g, phidot, net) for CUDA float64 tensors rho and rhodot [n_leaf]."""
+        import torch
+        n = self.n_leaf_cells
+        for x in (rho, rhodot):
+            assert x.is_cuda and x.dtype == torch.float64 and x.is_contiguous() and x.numel() == n
+        phi = torch.empty(n, dtype=torch.float64, device=rho.device) if phi is None else phi
+        g = torch.empty((n, 3), dtype=torch.float64, device=rho.device) if g is None else g
+        phidot = torch.empty(n, dtype=torch.float64, device=rho.device) if phidot is None else phidot
+        if net is None:
+            net = torch.empty(7 * self.forest_info()[0], dtype=torch.float64, device=rho.device)
+        sh = _stream_handle(stream)
+        check(lib().fmm_solve_dt(self._h, rho.data_ptr(), rhodot.data_ptr(), float(theta),
+                                 PRECISIONS[precision], int(bool(amc)), phi.data_ptr(), g.data_ptr(),
+                                 phidot.data_ptr(), net.data_ptr() if net is not False else None, sh))
+        if check_status:
+            check(lib().fmm_sync_status(self._h, sh))
+        return phi, g, phidot, net
+
     def sync_status(self, stream=None):
         check(lib().fmm_sync_status(self._h, _stream_handle(stream)))
 

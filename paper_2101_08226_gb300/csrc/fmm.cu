@@ -64,6 +64,8 @@ struct TreeIo {
   const double* rho;
   double* phi;
   double* g;
+  const double* src;  // d rho / dt (time-derivative solve), or null
+  double* phidot;     // d phi / dt out, or null
 };
 
 struct DevArgs {
@@ -97,6 +99,13 @@ struct DevArgs {
   double* loc;             // [20][n_cell] own, then total expansion
   float* loc32;            // [20][n_cell] own expansion (mixed path)
   double* ac;              // [3][n_cell] correction acceleration, own then total
+  // time-derivative solve (Sec. 2.1): source moments about rho's centres of mass
+  // (S0, S1 dipole, S2, S3), raw and with detraced S2, S3, and source expansions
+  double* smom;            // [20][n_cell]
+  double* smtl;            // [20][n_cell]
+  float* smom32;           // [20][n_cell] FP32 copy of smtl (mixed path)
+  double* sloc;            // [20][n_cell]
+  float* sloc32;           // [20][n_cell]
   double* root_part;       // [n_roots][kRootChunks][23][512] root partial sums (FP64 path)
   float* root_part32;      // [n_roots][kRootChunks][20][512] (mixed path)
   double* root_part_ac;    // [n_roots][kRootChunks][3][512] (mixed path)
@@ -428,6 +437,18 @@ struct MomView<double> {
 template <>
 struct MomView<float> {
   static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.mom32; }
+};
+
+// Source moments of the time-derivative solve, as read by the interactions.
+template <typename T>
+struct SrcView;
+template <>
+struct SrcView<double> {
+  static __device__ __forceinline__ const double* get(const DevArgs& A) { return A.smtl; }
+};
+template <>
+struct SrcView<float> {
+  static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.smom32; }
 };
 
 // Target state.
@@ -810,7 +831,8 @@ struct LeafTab<float> {
 // mass: L0 -= m / (|d| dx), L1 -= m d / (|d|^3 dx^2).  The masses of the subgrid and of the 5-cell
 // rim of its neighbours are staged in shared memory (0 for cells of refined or absent
 // neighbours, whose partners the boundary pass of k_m2l_ref adds afterwards).
-template <typename T>
+// SRC: the time-derivative solve -- the halo holds the source values and only L0 is formed.
+template <typename T, bool SRC>
 __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int32_t* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char leaf_smem[];
   T* hm = reinterpret_cast<T*>(leaf_smem);  // kHaloWords
@@ -822,7 +844,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
     nb[t] = (q >= 0 && A.leaf[q]) ? q : -1;
   }
   __syncthreads();
-  const T* __restrict__ M = MomView<T>::get(A);
+  const T* __restrict__ M = SRC ? SrcView<T>::get(A) : MomView<T>::get(A);
   const int64_t N = A.n_cell;
   for (int i = t; i < kHalo * kHalo * kHalo; i += kLeafThreads) {
     const int hx = i / (kHalo * kHalo), r = i - hx * (kHalo * kHalo), hy = r / kHalo, hz = r - hy * kHalo;
@@ -851,17 +873,29 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
     load4(tk + 4 * q, k0, kx, ky, kz);
     const T m0 = hm[base0 + off], m1 = hm[base1 + off];
     s0 += m0 * k0;
-    sx += m0 * kx;
-    sy += m0 * ky;
-    sz += m0 * kz;
     u0 += m1 * k0;
-    ux += m1 * kx;
-    uy += m1 * ky;
-    uz += m1 * kz;
+    if (!SRC) {
+      sx += m0 * kx;
+      sy += m0 * ky;
+      sz += m0 * kz;
+      ux += m1 * kx;
+      uy += m1 * ky;
+      uz += m1 * kz;
+    }
   }
   const T ih = T(1) / h, ih2 = ih * ih;
   const int64_t i0 = int64_t(s) * kCells + cidx(a, b, c0);
   const int64_t i1 = int64_t(s) * kCells + cidx(a, b, c0 + 4);
+  if (SRC) {
+    if (sizeof(T) == 8) {
+      A.sloc[i0] = -double(s0 * ih);
+      A.sloc[i1] = -double(u0 * ih);
+    } else {
+      A.sloc32[i0] = -float(s0 * ih);
+      A.sloc32[i1] = -float(u0 * ih);
+    }
+    return;
+  }
   if (sizeof(T) == 8) {
     double* L = reinterpret_cast<double*>(A.loc);
     L[i0] = -double(s0 * ih);
@@ -917,16 +951,17 @@ __device__ __forceinline__ void shift_add(const T* P, T rx, T ry, T rz, T* L) {
 
 // Downward pass.  Expansions: FP64 in the FP64 path; in the mixed path every expansion is FP32
 // (own, shifted and total), while the correction accelerations stay FP64 sums.
-template <bool MIXED>
+// SRC: the time-derivative solve's source expansions (same centres, no correction term).
+template <bool MIXED, bool SRC = false>
 struct Down {
   using T = typename std::conditional<MIXED, float, double>::type;
   static __device__ __forceinline__ T ld(const DevArgs& A, int k, int64_t i) {
-    if constexpr (MIXED) return A.loc32[k * A.n_cell + i];
-    else return A.loc[k * A.n_cell + i];
+    if constexpr (MIXED) return (SRC ? A.sloc32 : A.loc32)[k * A.n_cell + i];
+    else return (SRC ? A.sloc : A.loc)[k * A.n_cell + i];
   }
   static __device__ __forceinline__ void st(const DevArgs& A, int k, int64_t i, T v) {
-    if constexpr (MIXED) A.loc32[k * A.n_cell + i] = v;
-    else A.loc[k * A.n_cell + i] = v;
+    if constexpr (MIXED) (SRC ? A.sloc32 : A.loc32)[k * A.n_cell + i] = v;
+    else (SRC ? A.sloc : A.loc)[k * A.n_cell + i] = v;
   }
   static __device__ __forceinline__ T com(const DevArgs& A, int k, int64_t i) {
     if constexpr (MIXED) return A.mom32[k * A.n_cell + i];
@@ -948,9 +983,16 @@ __device__ __forceinline__ void store_leaf(const DevArgs& A, int32_t s, int a, i
   g[3 * o + 2] = gz;
 }
 
+// dphi/dt of leaf cell (subgrid s, cell (a, b, c)) in the caller's array.
+__device__ __forceinline__ void store_leaf_dt(const DevArgs& A, int32_t s, int a, int b, int c, double v) {
+  const int32_t ls = A.leaf_ord[s];
+  const int k = A.leaf_tree[ls];
+  A.io[k].phidot[(int64_t(ls) - A.tree_leaf_off[k]) * kCells + (a * 8 + b) * 8 + c] = v;
+}
+
 // Level 0: each root cell's expansion is the fixed-order sum of its kRootChunks partial sums.
 // A refined root keeps it as its total; a leaf root is evaluated (phi = L0, g = -L1 + a_c).
-template <bool MIXED>
+template <bool MIXED, bool SRC>
 __global__ void k_root_total(DevArgs A) {
   using T = typename Down<MIXED>::T;
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -967,26 +1009,32 @@ __global__ void k_root_total(DevArgs A) {
     if (!MIXED) {
       const double* P = A.root_part + pc * 23 * kCells;
       for (int k = 0; k < nL; ++k) L[k] += P[k * kCells + loc];
-      ax += P[20 * kCells + loc];
-      ay += P[21 * kCells + loc];
-      az += P[22 * kCells + loc];
+      if (!SRC) {
+        ax += P[20 * kCells + loc];
+        ay += P[21 * kCells + loc];
+        az += P[22 * kCells + loc];
+      }
     } else {
       const float* P = A.root_part32 + pc * 20 * kCells;
       for (int k = 0; k < nL; ++k) L[k] += double(P[k * kCells + loc]);
-      const double* Q = A.root_part_ac + pc * 3 * kCells;
-      ax += Q[loc];
-      ay += Q[kCells + loc];
-      az += Q[2 * kCells + loc];
+      if (!SRC) {
+        const double* Q = A.root_part_ac + pc * 3 * kCells;
+        ax += Q[loc];
+        ay += Q[kCells + loc];
+        az += Q[2 * kCells + loc];
+      }
     }
   }
   if (isleaf) {
     int a, b, c;
     cdecode(loc, a, b, c);
-    store_leaf(A, s, a, b, c, L[0], -L[1] + ax, -L[2] + ay, -L[3] + az);
+    if (SRC) store_leaf_dt(A, s, a, b, c, L[0]);
+    else store_leaf(A, s, a, b, c, L[0], -L[1] + ax, -L[2] + ay, -L[3] + az);
     return;
   }
 #pragma unroll
-  for (int k = 0; k < 20; ++k) Down<MIXED>::st(A, k, i, T(L[k]));
+  for (int k = 0; k < 20; ++k) Down<MIXED, SRC>::st(A, k, i, T(L[k]));
+  if (SRC) return;
   const int64_t N = A.n_cell;
   A.ac[i] = ax;
   A.ac[N + i] = ay;
@@ -1005,10 +1053,11 @@ __global__ void k_root_total(DevArgs A) {
 //              + w^2 sum_(a<b) s_a s_b L2_ab + w^3 s_x s_y s_z L3_xyz,
 //   dphi/dr_a (s w) = [L1_a + w^2 t_a / 2] + w sum_b s_b L2_ab + w^2 sum_(b<c) s_b s_c L3_abc,
 // each evaluated at all 8 children by an inverse 8-point Walsh-Hadamard transform.
-template <bool MIXED>
+template <bool MIXED, bool SRC>
 __global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* __restrict__ ref,
                                              int n_ref_blocks, const int32_t* __restrict__ octs) {
   using T = typename Down<MIXED>::T;
+  using D = Down<MIXED, SRC>;
   const int64_t N = A.n_cell;
   if (int(blockIdx.x) < n_ref_blocks) {
     const int32_t s = ref[blockIdx.x >> 3];
@@ -1024,8 +1073,8 @@ __global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* 
     T P[20], L[20];
 #pragma unroll
     for (int k = 0; k < 20; ++k) {
-      P[k] = Down<MIXED>::ld(A, k, ip);
-      L[k] = Down<MIXED>::ld(A, k, i);
+      P[k] = D::ld(A, k, ip);
+      L[k] = D::ld(A, k, i);
     }
     const T h = cell_h<T>(lev), hh = T(0.5) * h;
     // r = X_A - X_P = ((g & 1) - 1/2) dx_l + delta_A - delta_P
@@ -1034,7 +1083,8 @@ __global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* 
     const T rz = ((gc & 1) ? hh : -hh) + Down<MIXED>::com(A, 3, i) - Down<MIXED>::com(A, 3, ip);
     shift_add<T>(P, rx, ry, rz, L);
 #pragma unroll
-    for (int k = 0; k < 20; ++k) Down<MIXED>::st(A, k, i, L[k]);
+    for (int k = 0; k < 20; ++k) D::st(A, k, i, L[k]);
+    if (SRC) return;
     A.ac[i] += A.ac[ip];
     A.ac[N + i] += A.ac[N + ip];
     A.ac[2 * N + i] += A.ac[2 * N + ip];
@@ -1050,7 +1100,7 @@ __global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* 
   T L[20], P[20];
 #pragma unroll
   for (int k = 0; k < 20; ++k) {
-    P[k] = Down<MIXED>::ld(A, k, ip);
+    P[k] = D::ld(A, k, ip);
     L[k] = T(0);
   }
   // to the parent cell's geometric centre: r = -delta_P
@@ -1069,6 +1119,23 @@ __global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* 
   f[5] = w2 * L[6];
   f[3] = w2 * L[8];
   f[7] = w3 * L[14];
+  if (SRC) {
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (!(e & bit)) {
+          const T lo = f[e], hi = f[e | bit];
+          f[e] = lo - hi;
+          f[e | bit] = lo + hi;
+        }
+    const int64_t c0 = int64_t(s) * kCells + u;
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+      store_leaf_dt(A, s, 2 * (pa & 3) + ((e >> 2) & 1), 2 * (pb & 3) + ((e >> 1) & 1),
+                    2 * (pc & 3) + (e & 1), double(D::ld(A, 0, c0 + (e << 6)) + f[e]));
+    return;
+  }
   gxv[0] = L[1] + T(0.5) * w2 * tx;
   gxv[4] = w * L[4];
   gxv[2] = w * L[5];
@@ -1110,12 +1177,371 @@ __global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* 
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int64_t i = c0 + (e << 6);
-    const T phi = Down<MIXED>::ld(A, 0, i) + f[e];
-    const T l1x = Down<MIXED>::ld(A, 1, i) + gxv[e], l1y = Down<MIXED>::ld(A, 2, i) + gyv[e],
-            l1z = Down<MIXED>::ld(A, 3, i) + gzv[e];
+    const T phi = D::ld(A, 0, i) + f[e];
+    const T l1x = D::ld(A, 1, i) + gxv[e], l1y = D::ld(A, 2, i) + gyv[e],
+            l1z = D::ld(A, 3, i) + gzv[e];
     const double ax = A.ac[i] + apx, ay = A.ac[N + i] + apy, az = A.ac[2 * N + i] + apz;
     store_leaf(A, s, 2 * (pa & 3) + ((e >> 2) & 1), 2 * (pb & 3) + ((e >> 1) & 1), 2 * (pc & 3) + (e & 1),
                double(phi), -double(l1x) + ax, -double(l1y) + ay, -double(l1z) + az);
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// time derivative of the potential (Sec. 2.1): the same operator applied to s = (d rho/dt) dx^3
+// ----------------------------------------------------------------------------------------------
+// The expansion centres stay rho's centres of mass, so about them a source cell has a dipole:
+// S0 = sum s, S1 = sum s r, S2 = sum s r r, S3 = sum s r r r (r = x - X), stored in the order of
+// the moments (S1 where rho's cells keep delta).  Expanding -s / |R + t - u| to total order 3:
+//   L_k = -sum_(n <= 3 - k) (-1)^n / n! D^(k+n) : S_n.
+// Only the potential is needed at the leaves; there is no correction term.
+
+// index of (a, b) in the 6 stored components of a symmetric 2-tensor (xx xy xz yy yz zz)
+__host__ __device__ constexpr int sym2_index(int a, int b) {
+  return a > b ? sym2_index(b, a) : (a == 0 ? b : (a == 1 ? 2 + b : 5));
+}
+// the (a <= b <= c) triples of the 10 stored components of a symmetric 3-tensor
+__device__ constexpr int kSym3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
+                                         {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+
+// Exact shift of raw source moments c about X_c to the point X_c - r (r = X_c - X_new), added
+// onto S:  S0 += c0,  S1 += c1 + c0 r,  S2 += c2 + r c1 + c1 r + c0 r r,
+//          S3 += c3 + 3 sym(r c2) + 3 sym(r r c1) + c0 r r r.
+__device__ __forceinline__ void src_shift_add(const double* c, const double* r, double* S) {
+  S[0] += c[0];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) S[1 + a] += c[1 + a] + c[0] * r[a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a; b < 3; ++b)
+      S[4 + sym2_index(a, b)] += c[4 + sym2_index(a, b)] + r[a] * c[1 + b] + r[b] * c[1 + a] +
+                                 c[0] * r[a] * r[b];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    const int a = kSym3[k][0], b = kSym3[k][1], cc = kSym3[k][2];
+    S[10 + k] += c[10 + k] + r[a] * c[4 + sym2_index(b, cc)] + r[b] * c[4 + sym2_index(a, cc)] +
+                 r[cc] * c[4 + sym2_index(a, b)] + r[a] * r[b] * c[1 + cc] + r[a] * r[cc] * c[1 + b] +
+                 r[b] * r[cc] * c[1 + a] + c[0] * r[a] * r[b] * r[cc];
+  }
+}
+
+// Raw source moments of one refined cell, their detraced copy, and its FP32 copy (mixed path).
+__device__ __forceinline__ void store_src_moments(const DevArgs& A, int64_t cell, const double* S,
+                                                  int mixed) {
+  const int64_t N = A.n_cell;
+#pragma unroll
+  for (int k = 0; k < 20; ++k) A.smom[k * N + cell] = S[k];
+  const double tr3 = (S[4] + S[7] + S[9]) * (1.0 / 3.0);
+  const double tx = (S[10] + S[13] + S[15]) * 0.2, ty = (S[11] + S[16] + S[18]) * 0.2,
+               tz = (S[12] + S[17] + S[19]) * 0.2;
+  const double T[20] = {S[0], S[1], S[2], S[3], S[4] - tr3, S[5], S[6], S[7] - tr3, S[8],
+                        S[9] - tr3, S[10] - 3 * tx, S[11] - ty, S[12] - tz, S[13] - tx, S[14],
+                        S[15] - tx, S[16] - 3 * ty, S[17] - tz, S[18] - ty, S[19] - 3 * tz};
+#pragma unroll
+  for (int k = 0; k < 20; ++k) A.smtl[k * N + cell] = T[k];
+  if (mixed) {
+#pragma unroll
+    for (int k = 0; k < 20; ++k) A.smom32[k * N + cell] = float(T[k]);
+  }
+}
+
+// Leaf cells: s = (d rho/dt) dx^3 at the centre (a leaf's centre of mass), no higher moments.
+__global__ void k_p2m_src(DevArgs A, int mixed) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= A.n_leaf_cells) return;
+  const int32_t s = A.leaf_sub[i >> 9];
+  const int u = int(i & 511);
+  const int64_t cell = int64_t(s) * kCells + cidx(u >> 6, (u >> 3) & 7, u & 7);
+  const int k = A.leaf_tree[i >> 9];
+  double v = A.io[k].src[i - A.tree_leaf_off[k] * kCells];
+  // finite (any sign), on the bit pattern
+  if ((uint64_t(__double_as_longlong(v)) & 0x7ff0000000000000ull) == 0x7ff0000000000000ull) {
+    atomicOr(A.status, 2);
+    v = 0.0;
+  }
+  const double m = v * cell_vol(A.level[s]);
+  A.smom[cell] = m;
+  A.smtl[cell] = m;
+  if (mixed) A.smom32[cell] = float(m);
+}
+
+// Source moments of the refined cells of one level, one thread per parent cell, 64 per block
+// (one octant, as for rho).  Blocks [0, n_walsh) take octants with leaf children: the children
+// are point sources at s_e w about the parent cell's centre, whose raw moments there are the
+// sign sums of the Walsh-Hadamard transform (P1 = w D, P2 = w^2 G, P3 = w^3 H as for rho), then
+// shifted to the parent's centre of mass.  The other blocks take octants with refined children:
+// each child's moments are shifted exactly from the child's centre of mass.
+__global__ void __launch_bounds__(64) k_m2m_src(DevArgs A, const int32_t* __restrict__ oct_leaf,
+                                                int n_walsh, const int32_t* __restrict__ oct_ref,
+                                                int mixed) {
+  const bool walsh = int(blockIdx.x) < n_walsh;
+  const int32_t code = walsh ? oct_leaf[blockIdx.x] : oct_ref[blockIdx.x - n_walsh];
+  const int32_t s = code >> 3;
+  const int o = code & 7, u = int(threadIdx.x);
+  int a, b, c;
+  octant_cell(o, u, a, b, c);
+  const int64_t N = A.n_cell;
+  const int64_t cell = int64_t(s) * kCells + cidx(a, b, c);
+  const int64_t c0 = int64_t(A.child[8 * s + o]) * kCells + u;  // child e at c0 + (e << 6)
+  const double hc = cell_dx(A.level[s] + 1);
+  const double d[3] = {A.mom[N + cell], A.mom[2 * N + cell], A.mom[3 * N + cell]};  // parent delta
+  double S[20];
+#pragma unroll
+  for (int k = 0; k < 20; ++k) S[k] = 0.0;
+  if (walsh) {
+    double v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = A.smom[c0 + (e << 6)];
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (!(e & bit)) {
+          const double lo = v[e], hi = v[e | bit];
+          v[e] = hi + lo;
+          v[e | bit] = hi - lo;
+        }
+    const double w = 0.5 * hc, w2 = w * w, w3 = w2 * w;
+    const double S0 = v[0];
+    const double P1[3] = {w * v[4], w * v[2], w * v[1]};
+    // P2 (xx xy xz yy yz zz) and P3 (xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz) about the centre
+    const double P2[6] = {w2 * S0, w2 * v[6], w2 * v[5], w2 * S0, w2 * v[3], w2 * S0};
+    const double D[3] = {v[4], v[2], v[1]};
+    const double P3[10] = {w3 * D[0], w3 * D[1], w3 * D[2], w3 * D[0], w3 * v[7],
+                           w3 * D[0], w3 * D[1], w3 * D[2], w3 * D[1], w3 * D[2]};
+    // the same points about the parent's centre of mass: r = u - delta
+    S[0] = S0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) S[1 + k] = P1[k] - S0 * d[k];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int q = p; q < 3; ++q)
+        S[4 + sym2_index(p, q)] = P2[sym2_index(p, q)] - d[p] * P1[q] - d[q] * P1[p] + S0 * d[p] * d[q];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+      const int p = kSym3[k][0], q = kSym3[k][1], r = kSym3[k][2];
+      S[10 + k] = P3[k] - (d[p] * P2[sym2_index(q, r)] + d[q] * P2[sym2_index(p, r)] +
+                           d[r] * P2[sym2_index(p, q)]) +
+                  (d[p] * d[q] * P1[r] + d[p] * d[r] * P1[q] + d[q] * d[r] * P1[p]) -
+                  S0 * d[p] * d[q] * d[r];
+    }
+  } else {
+#pragma unroll 1
+    for (int e = 0; e < 8; ++e) {
+      const int64_t ci = c0 + (e << 6);
+      double ch[20];
+#pragma unroll
+      for (int k = 0; k < 20; ++k) ch[k] = A.smom[k * N + ci];
+      // r = X_child - X_parent
+      const double r[3] = {(((e >> 2) & 1) ? 0.5 : -0.5) * hc + A.mom[N + ci] - d[0],
+                           (((e >> 1) & 1) ? 0.5 : -0.5) * hc + A.mom[2 * N + ci] - d[1],
+                           ((e & 1) ? 0.5 : -0.5) * hc + A.mom[3 * N + ci] - d[2]};
+      src_shift_add(ch, r, S);
+    }
+  }
+  store_src_moments(A, cell, S, mixed);
+}
+
+// Expansion of a target due to a source cell at separation R = X_A - X_B (truncation k + n <= 3),
+// with detraced S2', S3' (every D^(n) is traceless) and rs1 = R.S1, rs2r = R.S2'.R, q = S3'(R,R):
+//   L0 -= S0 g0 - g1 rs1 + 1/2 g2 rs2r - 1/6 g3 R.q
+//   L1 -= (S0 g1 - g2 rs1 + 1/2 g3 rs2r) R - g1 S1 + g2 S2' R
+//   L2 -= (S0 g2 - g3 rs1) R R + (S0 g1 - g2 rs1) I - g2 (R S1 + S1 R)
+//   L3 -= S0 (g3 R R R + g2 sym(R I)).
+// AREF: all 20 components (targets with children; L2, L3 as 12 independent components); else
+// L0 only.  BREF: the source has children (full moments); else a point source.
+template <typename T, bool AREF, bool BREF>
+__device__ __forceinline__ void interact_src(T* L, const T* __restrict__ Sm, const T* __restrict__ G,
+                                             int64_t N, int64_t iB, T x, T y, T z) {
+  const T s0 = Sm[iB];
+  Radial<T> g;
+  if constexpr (BREF) {
+    x -= G[N + iB];
+    y -= G[2 * N + iB];
+    z -= G[3 * N + iB];
+    g.set(x, y, z, 3);
+    const T s1x = Sm[N + iB], s1y = Sm[2 * N + iB], s1z = Sm[3 * N + iB];
+    T S2[6], S3[10];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) S2[k] = Sm[(4 + k) * N + iB];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) S3[k] = Sm[(10 + k) * N + iB];
+    const T q2x = S2[0] * x + S2[1] * y + S2[2] * z;
+    const T q2y = S2[1] * x + S2[3] * y + S2[4] * z;
+    const T q2z = S2[2] * x + S2[4] * y + S2[5] * z;
+    const T rs2r = x * q2x + y * q2y + z * q2z;
+    const T rs1 = x * s1x + y * s1y + z * s1z;
+    T qx, qy, qz;
+    sym3_rr(S3, x, y, z, qx, qy, qz);
+    const T rrr = x * qx + y * qy + z * qz;
+    L[0] -= s0 * g.g0 - g.g1 * rs1 + T(0.5) * g.g2 * rs2r - (T(1) / T(6)) * g.g3 * rrr;
+    if constexpr (AREF) {
+      const T c1 = s0 * g.g1 - g.g2 * rs1 + T(0.5) * g.g3 * rs2r;
+      L[1] -= c1 * x - g.g1 * s1x + g.g2 * q2x;
+      L[2] -= c1 * y - g.g1 * s1y + g.g2 * q2y;
+      L[3] -= c1 * z - g.g1 * s1z + g.g2 * q2z;
+      const T c2 = s0 * g.g2 - g.g3 * rs1, c0 = s0 * g.g1 - g.g2 * rs1, e = g.g2;
+      L[4] -= c2 * x * x + c0 - T(2) * e * x * s1x;
+      L[5] -= c2 * x * y - e * (x * s1y + s1x * y);
+      L[6] -= c2 * x * z - e * (x * s1z + s1x * z);
+      L[7] -= c2 * y * y + c0 - T(2) * e * y * s1y;
+      L[8] -= c2 * y * z - e * (y * s1z + s1y * z);
+      // L3 from S0 alone: the L3 part of m2l_high
+      const T a2 = s0 * g.g2, a3 = s0 * g.g3;
+      const T a2x = a2 * x, a2y = a2 * y, a2z = a2 * z, a3xx = a3 * x * x, a3yy = a3 * y * y;
+      L[10] -= a3xx * x + T(3) * a2x;
+      L[11] -= a3xx * y + a2y;
+      L[12] -= a3xx * z + a2z;
+      L[13] -= a3yy * x + a2x;
+      L[14] -= a3 * x * y * z;
+      L[16] -= a3yy * y + T(3) * a2y;
+      L[17] -= a3yy * z + a2z;
+    }
+  } else {
+    g.set(x, y, z, AREF ? 3 : 0);
+    L[0] -= s0 * g.g0;
+    if constexpr (AREF) {
+      const T c = s0 * g.g1;
+      L[1] -= c * x;
+      L[2] -= c * y;
+      L[3] -= c * z;
+      m2l_high<T>(x, y, z, g, s0, L);
+    }
+  }
+}
+
+
+__device__ __forceinline__ void store_src_expansion(const DevArgs& A, int64_t i, const double* L, int n) {
+  for (int k = 0; k < n; ++k) A.sloc[k * A.n_cell + i] = L[k];
+}
+__device__ __forceinline__ void store_src_expansion(const DevArgs& A, int64_t i, const float* L, int n) {
+  for (int k = 0; k < n; ++k) A.sloc32[k * A.n_cell + i] = L[k];
+}
+
+// Refined targets of a level >= 1, one parity per block (as m2l_level): every stencil partner
+// through the full source formula (a leaf partner's dipole and higher moments are zeros).
+template <typename T>
+__device__ void m2l_level_src(const DevArgs& A, int32_t s, int parity, int t) {
+  __shared__ int32_t nb[27];
+  if (threadIdx.x < 27) nb[threadIdx.x] = A.nbr[27 * s + threadIdx.x];
+  __syncthreads();
+  const T* __restrict__ G = MomView<T>::get(A);
+  const T* __restrict__ Sm = SrcView<T>::get(A);
+  const int64_t N = A.n_cell;
+  int a, b, c;
+  block_cell(parity, t, a, b, c);
+  const int64_t iA = int64_t(s) * kCells + cidx(a, b, c);
+  const T dAx = G[N + iA], dAy = G[2 * N + iA], dAz = G[3 * N + iA];
+  T L[20];
+#pragma unroll
+  for (int k = 0; k < 20; ++k) L[k] = T(0);
+  const T h = cell_h<T>(A.level[s]);
+  const int32_t* __restrict__ st = A.ltab_code + parity * kLeafCap;
+  const T* __restrict__ td = LeafOffsets<T>::get(A) + int64_t(parity) * kLeafCap * 4;
+  for (int q = 0; q < A.n_stencil; ++q) {
+    int dx, dy, dz;
+    unpack_offset(__ldg(st + q), dx, dy, dz);
+    const int px = a + dx, py = b + dy, pz = c + dz;
+    const int slot = ((px >> 3) + 1) * 9 + ((py >> 3) + 1) * 3 + ((pz >> 3) + 1);
+    const int32_t sB = nb[slot];
+    if (sB < 0) continue;  // only without proper nesting
+    interact_src<T, true, true>(L, Sm, G, N, int64_t(sB) * kCells + cidx(px & 7, py & 7, pz & 7),
+                                dAx - __ldg(td + 4 * q) * h, dAy - __ldg(td + 4 * q + 1) * h,
+                                dAz - __ldg(td + 4 * q + 2) * h);
+  }
+  complete_traceless(L);
+  store_src_expansion(A, iA, L, 20);
+}
+
+// Root level: every well-separated root pair (all pairs, directly, when the root is a leaf),
+// sources in kRootChunks chunks whose partial sums the downward pass adds in a fixed order.
+template <typename T, bool AREF>
+__device__ void m2l_root_src(const DevArgs& A, int root, int parity, int t, int chunk) {
+  const T* __restrict__ G = MomView<T>::get(A);
+  const T* __restrict__ Sm = SrcView<T>::get(A);
+  const int64_t N = A.n_cell;
+  int a, b, c;
+  block_cell(parity, t, a, b, c);
+  const int iloc = cidx(a, b, c);
+  const int64_t base = int64_t(root) * kCells;
+  const T dAx = G[N + base + iloc], dAy = G[2 * N + base + iloc], dAz = G[3 * N + base + iloc];
+  T L[20];
+#pragma unroll
+  for (int k = 0; k < 20; ++k) L[k] = T(0);
+  const T h = cell_h<T>(0);
+  const int dx = chunk - a;
+  const T rx0 = dAx - T(dx) * h;
+  T ry = dAy + T(b) * h;
+  const T rz0 = dAz + T(c) * h;
+  for (int jy = 0; jy < 8; ++jy, ry -= h) {
+    T rz = rz0;
+    for (int jz = 0; jz < 8; ++jz, rz -= h) {
+      const int j = cidx(chunk, jy, jz);
+      if (j == iloc) continue;
+      const int dy = jy - b, dz = jz - c;
+      if (AREF && !(dx * dx + dy * dy + dz * dz > A.ws_d2)) continue;
+      interact_src<T, AREF, AREF>(L, Sm, G, N, base + j, rx0, ry, rz);
+    }
+  }
+  if constexpr (AREF) complete_traceless(L);
+  // partials: [chunk][component][cell]
+  if (sizeof(T) == 8) {
+    double* P = A.root_part + (int64_t(root) * kRootChunks + chunk) * 23 * kCells;
+    for (int k = 0; k < 20; ++k) P[k * kCells + iloc] = (AREF || k == 0) ? double(L[k]) : 0.0;
+  } else {
+    float* P = A.root_part32 + (int64_t(root) * kRootChunks + chunk) * 20 * kCells;
+    for (int k = 0; k < 20; ++k) P[k * kCells + iloc] = (AREF || k == 0) ? float(L[k]) : 0.0f;
+  }
+}
+
+// Leaf targets at refinement boundaries from the pair lists: multipole partners (refined) and
+// point partners; adds L0 onto the source leaf kernel's output.
+template <typename T>
+__device__ void m2l_boundary_src(const DevArgs& A, int chunk, int t) {
+  __shared__ T quarter[2 * kCodeMax + 1];
+  for (int i = threadIdx.x; i <= 2 * kCodeMax; i += blockDim.x) quarter[i] = T(i - kCodeMax) * T(0.25);
+  __syncthreads();
+  const int64_t k = int64_t(chunk) * 64 + t;
+  if (k >= A.n_bt) return;
+  const int64_t iA = A.bt_cell[k];
+  const int parity = int(iA & 511) >> 6;
+  const T* __restrict__ G = MomView<T>::get(A);
+  const T* __restrict__ Sm = SrcView<T>::get(A);
+  const int64_t N = A.n_cell;
+  const T h = cell_h<T>(A.level[iA >> 9]);
+  const T* __restrict__ td = LeafOffsets<T>::get(A) + int64_t(parity) * kLeafCap * 4;
+  T L[1] = {T(0)};
+  for (int32_t j = A.bm_off[k]; j < A.bm_off[k + 1]; ++j) {
+    const int q = __ldg(A.bm_q + j);
+    interact_src<T, false, true>(L, Sm, G, N, __ldg(A.bm_src + j), -__ldg(td + 4 * q) * h,
+                                 -__ldg(td + 4 * q + 1) * h, -__ldg(td + 4 * q + 2) * h);
+  }
+  for (int32_t j = A.bp_off[k]; j < A.bp_off[k + 1]; ++j) {
+    const int32_t code = __ldg(A.bp_code + j);
+    interact_src<T, false, false>(L, Sm, G, N, __ldg(A.bp_src + j),
+                                  quarter[((code >> 20) & 1023) - 512 + kCodeMax] * h,
+                                  quarter[((code >> 10) & 1023) - 512 + kCodeMax] * h,
+                                  quarter[(code & 1023) - 512 + kCodeMax] * h);
+  }
+  if (sizeof(T) == 8) A.sloc[iA] += double(L[0]);
+  else A.sloc32[iA] += float(L[0]);
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_m2l_ref_src(DevArgs A, const int32_t* __restrict__ blocks) {
+  const int32_t code = blocks[blockIdx.x];
+  const int kind = (code >> 30) & 3, idx = code & ((1 << 27) - 1);
+  const int parity = (code >> 27) & 7;
+  const int t = int(threadIdx.x & 63);
+  if (kind == 0) {
+    const int root = idx >> 3, chunk = idx & 7;
+    if (A.leaf[root]) m2l_root_src<T, false>(A, root, parity, t, chunk);
+    else m2l_root_src<T, true>(A, root, parity, t, chunk);
+  } else if (kind == 1) {
+    m2l_level_src<T>(A, idx, parity, t);
+  } else {
+    m2l_boundary_src<T>(A, idx, t);
   }
 }
 
@@ -1195,7 +1621,7 @@ __global__ void __launch_bounds__(kReduceThreads)
 // ----------------------------------------------------------------------------------------------
 // the caller's pointers of one call, passed by value as kernel parameters
 // ----------------------------------------------------------------------------------------------
-constexpr int kIoChunk = 128;  // trees per launch: the parameter block stays under 4 KB
+constexpr int kIoChunk = 96;  // trees per launch: the parameter block stays under 4 KB
 struct IoChunk {
   double* net;
   int32_t first, count;
@@ -1255,6 +1681,10 @@ struct fmm_tree {
   int* d_status = nullptr;
   int64_t* d_tree_leaf_off = nullptr;
   double *d_rho = nullptr, *d_phi = nullptr, *d_g = nullptr, *d_net = nullptr;
+  // time-derivative solve workspace (allocated on first use)
+  bool src_ready = false, src32_ready = false;
+  double *d_smom = nullptr, *d_smtl = nullptr, *d_sloc = nullptr;
+  float *d_smom32 = nullptr, *d_sloc32 = nullptr;
   std::map<double, StencilDev> stencils;
   bool profiling = false;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -1275,8 +1705,8 @@ struct fmm_tree {
     cudaGraphExec_t exec = nullptr;
     int32_t launches = 0;
   };
-  // one instantiated graph per (theta, precision, correction, net output, profiling)
-  std::map<std::tuple<double, int, int, int, int>, Graph> graphs;
+  // one instantiated graph per (theta, precision, correction, net output, profiling, dphi/dt)
+  std::map<std::tuple<double, int, int, int, int, int>, Graph> graphs;
 };
 
 // blocks per tree of the net reduction: about 512 in all
@@ -1313,9 +1743,13 @@ static int ensure_device(fmm_tree* t) {
   }
   t->device = dev;
   CUDA_TRY(cudaDeviceGetAttribute(&t->n_sms, cudaDevAttrMultiProcessorCount, dev));
-  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(kHaloWords * sizeof(double))));
-  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(kHaloWords * sizeof(float))));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(kHaloWords * sizeof(double))));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(kHaloWords * sizeof(float))));
   const HostTree& h = t->h;
   const int64_t nc = h.n_sub * kCells;
@@ -1406,6 +1840,25 @@ static int ensure_mixed(fmm_tree* t) {
   CUDA_TRY(dalloc(t, &t->d_root_part32, sizeof(float) * nr * kRootChunks * 20 * kCells));
   CUDA_TRY(dalloc(t, &t->d_root_part_ac, sizeof(double) * nr * kRootChunks * 3 * kCells));
   t->mixed_ready = true;
+  return FMM_OK;
+}
+
+static int ensure_src(fmm_tree* t, bool mixed) {
+  const int64_t nc = t->h.n_sub * kCells;
+  if (!t->src_ready) {
+    CUDA_TRY(dalloc(t, &t->d_smom, sizeof(double) * kNMom * nc));
+    CUDA_TRY(cudaMemset(t->d_smom, 0, sizeof(double) * kNMom * nc));  // leaf cells keep zeros
+    CUDA_TRY(dalloc(t, &t->d_smtl, sizeof(double) * kNMom * nc));
+    CUDA_TRY(cudaMemset(t->d_smtl, 0, sizeof(double) * kNMom * nc));
+    CUDA_TRY(dalloc(t, &t->d_sloc, sizeof(double) * 20 * nc));
+    t->src_ready = true;
+  }
+  if (mixed && !t->src32_ready) {
+    CUDA_TRY(dalloc(t, &t->d_smom32, sizeof(float) * kNMom * nc));
+    CUDA_TRY(cudaMemset(t->d_smom32, 0, sizeof(float) * kNMom * nc));
+    CUDA_TRY(dalloc(t, &t->d_sloc32, sizeof(float) * 20 * nc));
+    t->src32_ready = true;
+  }
   return FMM_OK;
 }
 
@@ -1719,6 +2172,11 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.root_part32 = t->d_root_part32;
   A.root_part_ac = t->d_root_part_ac;
   A.status = t->d_status;
+  A.smom = t->d_smom;
+  A.smtl = t->d_smtl;
+  A.smom32 = t->d_smom32;
+  A.sloc = t->d_sloc;
+  A.sloc32 = t->d_sloc32;
   A.n_bt = sd ? sd->n_bt : 0;
   A.bt_cell = sd ? sd->d_bt_cell : nullptr;
   A.bm_off = sd ? sd->d_bm_off : nullptr;
@@ -1774,8 +2232,10 @@ static int launch_net(fmm_tree* t, const DevArgs& A, cudaStream_t st) {
 }
 
 // All launches of one solve, in order, on stream st (which may be capturing).
+static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream_t st, int32_t* nl);
+
 static int enqueue_solve(fmm_tree* t, const StencilDev* sd, bool mixed, int amc, bool net,
-                         cudaStream_t st, int32_t* launches) {
+                         bool src, cudaStream_t st, int32_t* launches) {
   const HostTree& h = t->h;
   DevArgs A = make_args(t, sd);
   int rc;
@@ -1806,10 +2266,10 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, bool mixed, int amc,
   // kernel: root chunks, every (refined subgrid, parity) and every (boundary leaf subgrid, parity)
   if (t->n_work_leaf > 0) {
     if (mixed)
-      k_m2l_leaf<float><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), st>>>(
+      k_m2l_leaf<float, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), st>>>(
           A, t->d_work_leaf);
     else
-      k_m2l_leaf<double><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(double), st>>>(
+      k_m2l_leaf<double, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(double), st>>>(
           A, t->d_work_leaf);
     CUDA_TRY(cudaGetLastError());
     ++nl;
@@ -1823,8 +2283,8 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, bool mixed, int amc,
   ++nl;
   if ((rc = record(t, 2, st))) return rc;
   // downward pass: the roots, then per level the refined cells' totals and the leaf cells
-  if (mixed) k_root_total<true><<<blocks_for(int64_t(h.n_trees) * kCells, 128), 128, 0, st>>>(A);
-  else k_root_total<false><<<blocks_for(int64_t(h.n_trees) * kCells, 128), 128, 0, st>>>(A);
+  if (mixed) k_root_total<true, false><<<blocks_for(int64_t(h.n_trees) * kCells, 128), 128, 0, st>>>(A);
+  else k_root_total<false, false><<<blocks_for(int64_t(h.n_trees) * kCells, 128), 128, 0, st>>>(A);
   CUDA_TRY(cudaGetLastError());
   ++nl;
   for (int l = 1; l <= h.depth; ++l) {
@@ -1833,8 +2293,8 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, bool mixed, int amc,
     if (nr * 8 + no == 0) continue;
     const int32_t* ref = t->d_ref_sub + t->ref_off[l];
     const int32_t* octs = t->d_oct_leaf + t->oct_leaf_off[l - 1];
-    if (mixed) k_down<true><<<unsigned(nr * 8 + no), 64, 0, st>>>(A, l, ref, int(nr * 8), octs);
-    else k_down<false><<<unsigned(nr * 8 + no), 64, 0, st>>>(A, l, ref, int(nr * 8), octs);
+    if (mixed) k_down<true, false><<<unsigned(nr * 8 + no), 64, 0, st>>>(A, l, ref, int(nr * 8), octs);
+    else k_down<false, false><<<unsigned(nr * 8 + no), 64, 0, st>>>(A, l, ref, int(nr * 8), octs);
     CUDA_TRY(cudaGetLastError());
     ++nl;
   }
@@ -1844,17 +2304,68 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, bool mixed, int amc,
     nl += 2;
   }
   if ((rc = record(t, 4, st))) return rc;
+  // time-derivative solve: rho's centres of mass and lists, the source's moments (it reuses the
+  // root partial sums, which the rho downward pass has consumed)
+  if (src && (rc = enqueue_src(t, sd, mixed, st, &nl))) return rc;
   *launches = nl;
+  return FMM_OK;
+}
+
+static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream_t st, int32_t* nl) {
+  const HostTree& h = t->h;
+  DevArgs A = make_args(t, sd);
+  const int mx = mixed ? 1 : 0;
+  k_p2m_src<<<blocks_for(A.n_leaf_cells, 256), 256, 0, st>>>(A, mx);
+  CUDA_TRY(cudaGetLastError());
+  ++*nl;
+  for (int l = h.depth - 1; l >= 0; --l) {
+    const int64_t nw = t->oct_leaf_off[l + 1] - t->oct_leaf_off[l];
+    const int64_t nr = t->oct_ref_off[l + 1] - t->oct_ref_off[l];
+    if (nw + nr == 0) continue;
+    k_m2m_src<<<unsigned(nw + nr), 64, 0, st>>>(A, t->d_oct_leaf + t->oct_leaf_off[l], int(nw),
+                                                 t->d_oct_ref + t->oct_ref_off[l], mx);
+    CUDA_TRY(cudaGetLastError());
+    ++*nl;
+  }
+  if (t->n_work_leaf > 0) {
+    if (mixed)
+      k_m2l_leaf<float, true><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), st>>>(
+          A, t->d_work_leaf);
+    else
+      k_m2l_leaf<double, true><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(double), st>>>(
+          A, t->d_work_leaf);
+    CUDA_TRY(cudaGetLastError());
+    ++*nl;
+  }
+  if (mixed) k_m2l_ref_src<float, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks);
+  else k_m2l_ref_src<double, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks);
+  CUDA_TRY(cudaGetLastError());
+  ++*nl;
+  if (mixed) k_root_total<true, true><<<blocks_for(int64_t(h.n_trees) * kCells, 128), 128, 0, st>>>(A);
+  else k_root_total<false, true><<<blocks_for(int64_t(h.n_trees) * kCells, 128), 128, 0, st>>>(A);
+  CUDA_TRY(cudaGetLastError());
+  ++*nl;
+  for (int l = 1; l <= h.depth; ++l) {
+    const int64_t nr = t->ref_off[l + 1] - t->ref_off[l];
+    const int64_t no = t->oct_leaf_off[l] - t->oct_leaf_off[l - 1];
+    if (nr * 8 + no == 0) continue;
+    const int32_t* ref = t->d_ref_sub + t->ref_off[l];
+    const int32_t* octs = t->d_oct_leaf + t->oct_leaf_off[l - 1];
+    if (mixed) k_down<true, true><<<unsigned(nr * 8 + no), 64, 0, st>>>(A, l, ref, int(nr * 8), octs);
+    else k_down<false, true><<<unsigned(nr * 8 + no), 64, 0, st>>>(A, l, ref, int(nr * 8), octs);
+    CUDA_TRY(cudaGetLastError());
+    ++*nl;
+  }
   return FMM_OK;
 }
 
 // Captures the launches of one solve configuration into a graph and instantiates it.
 static int capture_graph(fmm_tree* t, const StencilDev* sd, bool mixed, int amc, bool net,
-                         fmm_tree::Graph* out) {
+                         bool src, fmm_tree::Graph* out) {
   CUDA_TRY(cudaStreamBeginCapture(t->stream, cudaStreamCaptureModeThreadLocal));
   t->capturing = true;
   int32_t nl = 0;
-  int rc = enqueue_solve(t, sd, mixed, amc, net, t->stream, &nl);
+  int rc = enqueue_solve(t, sd, mixed, amc, net, src, t->stream, &nl);
   t->capturing = false;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(t->stream, &g);
@@ -1878,22 +2389,25 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   if (!(theta >= kThetaMin && theta < 1.0))
     return fail(FMM_ERR_THETA, "theta must lie in [0.34, 1)");
   if (precision != FMM_FP64 && precision != FMM_MIXED) return fail(FMM_ERR_ARG, "bad precision");
+  const bool src = !io.empty() && io[0].src != nullptr;
   for (const TreeIo& e : io)
-    if (!e.rho || !e.phi || !e.g) return fail(FMM_ERR_ARG, "null device pointer");
+    if (!e.rho || !e.phi || !e.g || (src && (!e.src || !e.phidot)))
+      return fail(FMM_ERR_ARG, "null device pointer");
   int rc = ensure_device(t);
   if (rc) return rc;
   const bool mixed = precision == FMM_MIXED;
   if (mixed && (rc = ensure_mixed(t))) return rc;
+  if (src && (rc = ensure_src(t, mixed))) return rc;
   StencilDev* sd = nullptr;
   if ((rc = get_stencil(t, theta, &sd))) return rc;
   amc = amc ? 1 : 0;
   fmm_tree::Graph* gr = nullptr;
   if (t->use_graphs) {
-    auto key = std::make_tuple(theta, precision, amc, net ? 1 : 0, t->profiling ? 1 : 0);
+    auto key = std::make_tuple(theta, precision, amc, net ? 1 : 0, t->profiling ? 1 : 0, src ? 1 : 0);
     auto it = t->graphs.find(key);
     if (it == t->graphs.end()) {
       fmm_tree::Graph fresh;
-      if ((rc = capture_graph(t, sd, mixed, amc, net != nullptr, &fresh))) return rc;
+      if ((rc = capture_graph(t, sd, mixed, amc, net != nullptr, src, &fresh))) return rc;
       it = t->graphs.emplace(key, fresh).first;
     }
     gr = &it->second;
@@ -1905,7 +2419,7 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   if (gr) {
     CUDA_TRY(cudaGraphLaunch(gr->exec, t->stream));
     n_solve = gr->launches;
-  } else if ((rc = enqueue_solve(t, sd, mixed, amc, net != nullptr, t->stream, &n_solve))) {
+  } else if ((rc = enqueue_solve(t, sd, mixed, amc, net != nullptr, src, t->stream, &n_solve))) {
     return rc;
   }
   CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
@@ -2123,6 +2637,25 @@ int fmm_solve(fmm_tree* t, const double* rho_dev, double theta, int precision, i
   }
 }
 
+int fmm_solve_dt(fmm_tree* t, const double* rho_dev, const double* rhodot_dev, double theta,
+                 int precision, int amc, double* phi_dev, double* g_dev, double* phidot_dev,
+                 double* net_dev, void* stream) {
+  if (!t) return fail(FMM_ERR_ARG, "tree is null");
+  if (!rho_dev || !phi_dev || !g_dev || !rhodot_dev || !phidot_dev)
+    return fail(FMM_ERR_ARG, "null device pointer");
+  try {
+    std::vector<TreeIo> io = contiguous_io(t, rho_dev, phi_dev, g_dev);
+    for (int k = 0; k < t->h.n_trees; ++k) {
+      const int64_t o = t->h.tree_leaf_off[k] * kCells;
+      io[size_t(k)].src = rhodot_dev + o;
+      io[size_t(k)].phidot = phidot_dev + o;
+    }
+    return solve_impl(t, io, theta, precision, amc, net_dev, static_cast<cudaStream_t>(stream));
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+}
+
 int fmm_solve_batch(fmm_tree* f, const double* const* rho_dev, double theta, int precision,
                     int amc, double* const* phi_dev, double* const* g_dev, double* net_dev,
                     void* stream) {
@@ -2148,6 +2681,7 @@ int fmm_sync_status(fmm_tree* t, void* stream) {
   CUDA_TRY(cudaMemcpy(&status, t->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemset(t->d_status, 0, sizeof(int)));
   if (status & 1) return fail(FMM_ERR_NONFINITE, "a density was negative, NaN or infinite");
+  if (status & 2) return fail(FMM_ERR_NONFINITE, "a density time derivative was NaN or infinite");
   return FMM_OK;
 }
 
