@@ -396,6 +396,34 @@ def run_ours(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
 
+    # the time-derivative solve on the same tree: rho and d rho/dt in one call (Sec. 2.1)
+    rhodot = torch.from_numpy(rho0 * np.random.default_rng(31).uniform(-1.0, 1.0, rho0.size)).to(dev)
+    phidot = torch.empty(n, dtype=torch.float64, device=dev)
+    dt_out = {"workload": WORKLOAD + "; d rho/dt = rho u, u ~ U[-1, 1]",
+              "what": "fmm_solve_dt: the rho solve plus dphi/dt (same operator, source with a dipole)"}
+    tree.set_profiling(False)
+    for precision in ("fp64", "mixed"):
+        for k in range(2):
+            tree.solve_dt(rhos[k], rhodot, THETA, precision, True, phi, g, phidot, net, stream,
+                          check_status=False)
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(min(args.steps, 5)):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tree.solve_dt(rhos[k], rhodot, THETA, precision, True, phi, g, phidot, net, stream,
+                          check_status=False)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        tree.sync_status(stream)
+        tm = float(np.mean(ms))
+        base = t64 / args.steps if precision == "fp64" else t32 / args.steps
+        dt_out[precision] = {"ms_per_solve": tm, "ms_rho_solve_alone": base,
+                             "added_ms_for_dphi_dt": tm - base,
+                             "gpu_launches": tree.last_launches()}
     batched = measure_batched(api, synth, torch, dev, stream, min(args.steps, 3))
     paper = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), flush)
     if rank != 0:
@@ -454,6 +482,7 @@ def run_ours(args):
         "gpu_launches": l64,
         "batched": batched,
         "paper_binary": paper,
+        "dphi_dt": dt_out,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
