@@ -424,6 +424,27 @@ def run_ours(args):
         dt_out[precision] = {"ms_per_solve": tm, "ms_rho_solve_alone": base,
                              "added_ms_for_dphi_dt": tm - base,
                              "gpu_launches": tree.last_launches()}
+    # binary diagnostics (Sec. 4): one fused membership + per-star reduction pass over phi's g
+    s1, s2 = w.field.stars
+    sep = float(np.linalg.norm(np.subtract(s2.center, s1.center)))
+    diag_ms = []
+    for k in range(2 + min(args.steps, 5)):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sums = tree.binary_diagnostics(rhos[-1], g, (1.7 / sep ** 3) ** 0.5, s1.center, s2.center,
+                                       0.08 * sep, 0.07 * sep, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 2:
+            diag_ms.append(e0.elapsed_time(e1))
+    tdiag = float(np.mean(diag_ms))
+    diag = {"what": "star membership by the effective acceleration and per-star M, sum m x, F, T "
+                    "(fmm_binary_diagnostics, one pass, sums copied to the host)",
+            "ms_per_pass": tdiag, "leaf_cells": n,
+            "input_bytes": 32 * n, "input_gb_per_s": 32 * n / (tdiag * 1e-3) / 1e9,
+            "stars": [{"M": float(r[0]), "cells": int(r[10])} for r in sums]}
     batched = measure_batched(api, synth, torch, dev, stream, min(args.steps, 3))
     paper = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), flush)
     if rank != 0:
@@ -483,6 +504,7 @@ def run_ours(args):
         "batched": batched,
         "paper_binary": paper,
         "dphi_dt": dt_out,
+        "binary_diagnostics": diag,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }

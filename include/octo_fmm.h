@@ -162,6 +162,21 @@ int fmm_solve_host(fmm_tree* tree, const double* rho_host, double theta, int pre
 int fmm_net_force_torque(fmm_tree* tree, const double* rho_dev, const double* g_dev,
                          double* net_dev, void* stream);
 
+/* Binary diagnostics (Sec. 4, the merger analysis), one pass over the leaf cells of a single
+ * tree (a forest is rejected).  In the frame rotating about the z axis at omega, with
+ * g_eff = g + omega^2 (x, y, 0) and q_s = g_eff . (x - x_s) / |x - x_s| (0 at x_s), a cell
+ * belongs to star 1 (the accretor) if min(q_1, 0) < min(q_2, 0), to star 2 (the donor) if
+ * min(q_1, 0) > min(q_2, 0), else to neither; a cell closer to x_s than rc_s (the paper uses a
+ * quarter of the star's Roche-lobe radius) belongs to star s regardless (star 1 wins).  The
+ * decision uses single correctly rounded FP64 operations in a fixed order.
+ * rho_dev [n_leaf], g_dev [n_leaf][3] (e.g. fmm_solve's output); x1, x2: host double[3];
+ * out_dev: 22 doubles, per star (1 then 2): M, sum m x (3), F = sum m g (3),
+ * T = sum (x - x_s) x m g (3), cell count; m = rho dx^3, sums in FP64 in a fixed order.
+ * member_dev (optional): int8 [n_leaf], 0 / 1 / 2.  Asynchronous, ordered on `stream`. */
+int fmm_binary_diagnostics(fmm_tree* tree, const double* rho_dev, const double* g_dev,
+                           double omega, const double* x1, const double* x2, double rc1,
+                           double rc2, double* out_dev, int8_t* member_dev, void* stream);
+
 /* on != 0 (the default): replay one captured CUDA graph per solve configuration; on == 0:
  * enqueue the kernels one by one on every call.  The results are the same bit for bit. */
 int fmm_set_graphs(fmm_tree* tree, int on);

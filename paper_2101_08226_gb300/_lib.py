@@ -22,7 +22,7 @@ FMM_MIXED = 1
 EXPORTS = [
     "fmm_build_tree", "fmm_destroy", "fmm_build_forest", "fmm_forest_info", "fmm_solve_batch", "fmm_tree_info", "fmm_tree_subgrids", "fmm_stencil",
     "fmm_interaction_counts", "fmm_interaction_counts_by_type", "fmm_last_launches", "fmm_solve", "fmm_solve_dt", "fmm_sync_status", "fmm_solve_host",
-    "fmm_net_force_torque", "fmm_net_force_torque_points_static", "fmm_set_profiling", "fmm_set_graphs", "fmm_phase_times", "fmm_last_error",
+    "fmm_net_force_torque", "fmm_net_force_torque_points_static", "fmm_set_profiling", "fmm_set_graphs", "fmm_binary_diagnostics", "fmm_phase_times", "fmm_last_error",
 ]
 
 _lib = None
@@ -64,6 +64,7 @@ def lib():
             "fmm_net_force_torque_points_static": (i32, [i64, vp, vp, vp, vp, vp]),
             "fmm_set_profiling": (i32, [vp, i32]),
             "fmm_set_graphs": (i32, [vp, i32]),
+            "fmm_binary_diagnostics": (i32, [vp, vp, vp, dbl, vp, vp, dbl, dbl, vp, vp, vp]),
             "fmm_phase_times": (i32, [vp, vp, i32]),
             "fmm_last_error": (C.c_char_p, []),
         }

@@ -1619,6 +1619,99 @@ __global__ void __launch_bounds__(kReduceThreads)
 }
 
 // ----------------------------------------------------------------------------------------------
+// binary diagnostics (Sec. 4): star membership by the effective acceleration, per-star sums
+// ----------------------------------------------------------------------------------------------
+// g_eff = g + Omega^2 (x, y, 0);  q_s = g_eff . (x - x_s) / |x - x_s| (0 at x_s itself).  A cell
+// belongs to the accretor (1) if min(q_1, 0) < min(q_2, 0), to the donor (2) if greater, else to
+// neither; within rc_s of x_s it belongs to star s whatever q says (the accretor tested last, so
+// it wins).  The decision is taken with single correctly rounded FP64 operations in a fixed order
+// (no fused multiply-add), so it is reproducible operation for operation.  Per star, with
+// m = rho dx^3: M, sum m x, F = sum m g, T = sum (x - x_s) x m g, and the number of cells.
+struct BinaryParams {
+  double w2;          // Omega^2
+  double c[2][3];     // x_1, x_2
+  double rc2[2];      // squared critical radii
+};
+constexpr int kDiagVals = 22;   // 2 stars x (M, m x[3], F[3], T[3], count)
+constexpr int kDiagThreads = 128;
+
+__device__ __forceinline__ double q_of(double gex, double gey, double gez, double dx, double dy,
+                                       double dz, double& d2) {
+  d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  const double dot = __dadd_rn(__dadd_rn(__dmul_rn(gex, dx), __dmul_rn(gey, dy)), __dmul_rn(gez, dz));
+  return d2 > 0.0 ? __ddiv_rn(dot, __dsqrt_rn(d2)) : 0.0;
+}
+
+__global__ void __launch_bounds__(kDiagThreads)
+    k_binary_partial(DevArgs A, BinaryParams P, double* __restrict__ partials, int8_t* member) {
+  __shared__ double sh[kDiagVals][kDiagThreads];
+  double v[kDiagVals];
+#pragma unroll
+  for (int k = 0; k < kDiagVals; ++k) v[k] = 0.0;
+  const int64_t stride = int64_t(gridDim.x) * kDiagThreads;
+  const double* __restrict__ rho = A.io[0].rho;
+  const double* __restrict__ g = A.io[0].g;
+  for (int64_t i = int64_t(blockIdx.x) * kDiagThreads + threadIdx.x; i < A.n_leaf_cells; i += stride) {
+    const int32_t s = A.leaf_sub[i >> 9];
+    const int lev = A.level[s];
+    const int loc = int(i & 511);
+    const int full = 1 << (lev + 3);
+    const double x = dyadic(2 * (A.ijk[3 * s] * 8 + (loc >> 6)) + 1 - full, lev + 4);
+    const double y = dyadic(2 * (A.ijk[3 * s + 1] * 8 + ((loc >> 3) & 7)) + 1 - full, lev + 4);
+    const double z = dyadic(2 * (A.ijk[3 * s + 2] * 8 + (loc & 7)) + 1 - full, lev + 4);
+    const double gx = g[3 * i], gy = g[3 * i + 1], gz = g[3 * i + 2];
+    const double gex = __dadd_rn(gx, __dmul_rn(P.w2, x)), gey = __dadd_rn(gy, __dmul_rn(P.w2, y));
+    double d2a, d2b;
+    const double q1 = q_of(gex, gey, gz, __dsub_rn(x, P.c[0][0]), __dsub_rn(y, P.c[0][1]),
+                           __dsub_rn(z, P.c[0][2]), d2a);
+    const double q2 = q_of(gex, gey, gz, __dsub_rn(x, P.c[1][0]), __dsub_rn(y, P.c[1][1]),
+                           __dsub_rn(z, P.c[1][2]), d2b);
+    const double m1 = fmin(q1, 0.0), m2 = fmin(q2, 0.0);
+    int who = m1 < m2 ? 1 : (m1 > m2 ? 2 : 0);
+    if (d2b < P.rc2[1]) who = 2;
+    if (d2a < P.rc2[0]) who = 1;
+    if (member) member[i] = int8_t(who);
+    if (who == 0) continue;
+    const int b = who == 1 ? 0 : 11;
+    const double m = rho[i] * cell_vol(lev);
+    const double fx = m * gx, fy = m * gy, fz = m * gz;
+    const double rx = x - P.c[who - 1][0], ry = y - P.c[who - 1][1], rz = z - P.c[who - 1][2];
+    v[b] += m;
+    v[b + 1] += m * x;
+    v[b + 2] += m * y;
+    v[b + 3] += m * z;
+    v[b + 4] += fx;
+    v[b + 5] += fy;
+    v[b + 6] += fz;
+    v[b + 7] += ry * fz - rz * fy;
+    v[b + 8] += rz * fx - rx * fz;
+    v[b + 9] += rx * fy - ry * fx;
+    v[b + 10] += 1.0;
+  }
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < kDiagVals; ++k) sh[k][t] = v[k];
+  __syncthreads();
+  for (int w = kDiagThreads / 2; w > 0; w >>= 1) {
+    if (t < w)
+#pragma unroll
+      for (int k = 0; k < kDiagVals; ++k) sh[k][t] += sh[k][t + w];
+    __syncthreads();
+  }
+  if (t < kDiagVals) partials[int64_t(blockIdx.x) * kDiagVals + t] = sh[t][0];
+}
+
+// One block: the partials of all blocks in a fixed order.
+__global__ void __launch_bounds__(kDiagThreads)
+    k_binary_final(const double* __restrict__ partials, int n_blocks, double* __restrict__ out) {
+  const int t = threadIdx.x;
+  if (t >= kDiagVals) return;
+  double v = 0.0;
+  for (int b = 0; b < n_blocks; ++b) v += partials[int64_t(b) * kDiagVals + t];
+  out[t] = v;
+}
+
+// ----------------------------------------------------------------------------------------------
 // the caller's pointers of one call, passed by value as kernel parameters
 // ----------------------------------------------------------------------------------------------
 constexpr int kIoChunk = 96;  // trees per launch: the parameter block stays under 4 KB
@@ -1683,6 +1776,7 @@ struct fmm_tree {
   double *d_rho = nullptr, *d_phi = nullptr, *d_g = nullptr, *d_net = nullptr;
   // time-derivative solve workspace (allocated on first use)
   bool src_ready = false, src32_ready = false;
+  double* d_diag_partials = nullptr;  // binary diagnostics: [blocks][kDiagVals]
   double *d_smom = nullptr, *d_smtl = nullptr, *d_sloc = nullptr;
   float *d_smom32 = nullptr, *d_sloc32 = nullptr;
   std::map<double, StencilDev> stencils;
@@ -2725,6 +2819,44 @@ int fmm_net_force_torque(fmm_tree* t, const double* rho_dev, const double* g_dev
     int32_t n_io = 0;
     if ((rc = set_io(t, io, net_dev, t->stream, &n_io))) return rc;
     if ((rc = launch_net(t, make_args(t, nullptr), t->stream))) return rc;
+    CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
+    CUDA_TRY(cudaStreamWaitEvent(caller, t->ev_out, 0));
+    return FMM_OK;
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+int fmm_binary_diagnostics(fmm_tree* t, const double* rho_dev, const double* g_dev, double omega,
+                           const double* x1, const double* x2, double rc1, double rc2,
+                           double* out_dev, int8_t* member_dev, void* stream) {
+  if (!t || !rho_dev || !g_dev || !x1 || !x2 || !out_dev) return fail(FMM_ERR_ARG, "null argument");
+  if (t->h.n_trees != 1) return fail(FMM_ERR_ARG, "diagnostics take a single tree");
+  if (!(rc1 >= 0.0) || !(rc2 >= 0.0)) return fail(FMM_ERR_ARG, "critical radii must be >= 0");
+  int rc = ensure_device(t);
+  if (rc) return rc;
+  try {
+    const int nb = 2 * t->n_sms;
+    if (!t->d_diag_partials) CUDA_TRY(dalloc(t, &t->d_diag_partials, sizeof(double) * nb * kDiagVals));
+    BinaryParams P;
+    P.w2 = omega * omega;
+    for (int a = 0; a < 3; ++a) {
+      P.c[0][a] = x1[a];
+      P.c[1][a] = x2[a];
+    }
+    P.rc2[0] = rc1 * rc1;
+    P.rc2[1] = rc2 * rc2;
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
+    std::vector<TreeIo> io = contiguous_io(t, rho_dev, nullptr, const_cast<double*>(g_dev));
+    CUDA_TRY(cudaEventRecord(t->ev_in, caller));
+    CUDA_TRY(cudaStreamWaitEvent(t->stream, t->ev_in, 0));
+    int32_t n_io = 0;
+    if ((rc = set_io(t, io, nullptr, t->stream, &n_io))) return rc;
+    DevArgs A = make_args(t, nullptr);
+    k_binary_partial<<<nb, kDiagThreads, 0, t->stream>>>(A, P, t->d_diag_partials, member_dev);
+    CUDA_TRY(cudaGetLastError());
+    k_binary_final<<<1, kDiagThreads, 0, t->stream>>>(t->d_diag_partials, nb, out_dev);
+    CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
     CUDA_TRY(cudaStreamWaitEvent(caller, t->ev_out, 0));
     return FMM_OK;

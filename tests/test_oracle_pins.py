@@ -501,3 +501,74 @@ def test_dt_all_near_is_direct_sum_and_linear():
     a1, a2 = O.solve_dt(t, rho, s1, 0.5), O.solve_dt(t, rho, s2, 0.5)
     a12 = O.solve_dt(t, rho, 2.0 * s1 - 3.0 * s2, 0.5)
     assert np.abs(a12 - (2.0 * a1 - 3.0 * a2)).max() <= 1e-13 * np.abs(a12).max()
+
+
+# ------------------------------------------------------------------------------------------
+# binary diagnostics (Sec. 4)
+# ------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def binary_direct():
+    """The 3-level q = 0.7 binary (75,776 leaf cells) with g from the exact direct sum."""
+    w = synth.workload_binary(3)
+    t = O.Tree(w.max_level, w.flags)
+    rho = synth.leaf_density(w.field, t.leaves())
+    x, m = O.leaf_masses(t, rho)
+    _, g = O.direct(x, m)
+    s1, s2 = w.field.stars
+    return w, x, m, g, np.array(s1.center), np.array(s2.center)
+
+
+def _star_mass(star, h=1e-4):
+    # M = 4 pi rho_c (R / xi_1)^3 int_0^xi_1 theta^n xi^2 dxi (trapezoid on the Lane-Emden table)
+    table, xi1 = synth.lane_emden_table(1.5, h)
+    xi = np.arange(len(table)) * h
+    f = np.clip(table, 0.0, None) ** 1.5 * xi ** 2
+    integral = h * (f.sum() - 0.5 * (f[0] + f[-1]))
+    return 4.0 * math.pi * star.rho_c * (star.radius / xi1) ** 3 * integral
+
+
+def test_binary_diagnostics_physics(binary_direct):
+    from oracle import diagnostics as D
+    w, x, m, g, c1, c2 = binary_direct
+    s1, s2 = w.field.stars
+    M1, M2 = _star_mass(s1), _star_mass(s2)
+    a = float(np.linalg.norm(c2 - c1))
+    omega = math.sqrt((M1 + M2) / a ** 3)          # Kepler
+    mem, sums, _, _ = D.iterate(x, m, g, omega, c1, c2, n_iter=5)
+    # each star is one region holding its own centre and close to its own mass
+    near1 = np.argmin(np.linalg.norm(x - c1, axis=1))
+    near2 = np.argmin(np.linalg.norm(x - c2, axis=1))
+    assert mem[near1] == 1 and mem[near2] == 2
+    assert abs(sums[0, 0] / M1 - 1) < 0.02 and abs(sums[1, 0] / M2 - 1) < 0.02
+    # shell theorem: the stars attract like point masses, along the axis
+    F = M1 * M2 / a ** 2
+    assert abs(sums[0, 4] / F - 1) < 0.03 and abs(sums[1, 4] / F + 1) < 0.03
+    # the force on everything sums to zero (exact direct sum)
+    Fall = (m[:, None] * g).sum(0)
+    assert np.abs(Fall).max() <= 1e-13 * (m[:, None] * np.abs(g)).sum()
+    # mirror symmetry y -> -y, z -> -z of the whole configuration: no spin torque about z
+    scale = (np.linalg.norm(x, axis=1) * m * np.linalg.norm(g, axis=1)).sum()
+    assert abs(sums[0, 9]) <= 1e-13 * scale and abs(sums[1, 9]) <= 1e-13 * scale
+
+
+def test_binary_membership_rules(binary_direct):
+    from oracle import diagnostics as D
+    w, x, m, g, c1, c2 = binary_direct
+    # a critical radius beyond everything puts every cell into that star
+    mem = D.membership(x, g, 0.0, c1, c2, 10.0, 0.0)
+    assert (mem == 1).all()
+    mem = D.membership(x, g, 0.0, c1, c2, 0.0, 10.0)
+    assert (mem == 2).all()
+    # the rule itself, cell by cell, written with scalar Python arithmetic
+    mem = D.membership(x, g, 0.3, c1, c2, 0.0, 0.0)
+    rng = np.random.default_rng(2)
+    for i in rng.choice(len(x), 200, replace=False):
+        ge = [g[i][0] + 0.09 * x[i][0], g[i][1] + 0.09 * x[i][1], g[i][2]]
+        qs = []
+        for c in (c1, c2):
+            d = [x[i][k] - c[k] for k in range(3)]
+            qs.append(sum(ge[k] * d[k] for k in range(3)) / math.sqrt(sum(v * v for v in d)))
+        m1, m2 = min(qs[0], 0.0), min(qs[1], 0.0)
+        expect = 1 if m1 < m2 else (2 if m1 > m2 else 0)
+        if abs(m1 - m2) > 1e-12 * (abs(m1) + abs(m2)):   # away from exact ties
+            assert mem[i] == expect
