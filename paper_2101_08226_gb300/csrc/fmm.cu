@@ -527,6 +527,80 @@ __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict
   }
 }
 
+// The dominant pair kind -- a refined target and a refined (or leaf, with zero offset and higher
+// moments) partner -- written as explicit multiply-add chains, which the compiler cannot form from
+// "L -= a b + c d" on its own: the same expansion and correction as interact<T, true, true>.
+// M3'(R,R) uses the tracelessness of the stored M3' (T_xzz = -T_xxx - T_xyy, ...) on the shared
+// monomials xx - zz, yy - zz, 2xy, 2xz, 2yz; the correction's Q(R,R,R) is contracted directly.
+template <typename T>
+__device__ __forceinline__ void interact_rr(Target<T, true>& S, const T* __restrict__ M, int64_t N,
+                                            int64_t iB, T x, T y, T z) {
+  const T mB = M[iB];
+  x -= M[N + iB];
+  y -= M[2 * N + iB];
+  z -= M[3 * N + iB];
+  T M2[6], M3[9];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) M2[k] = M[(4 + k) * N + iB];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) M3[k] = M[(10 + k) * N + iB];  // zzz is not needed
+  Radial<T> g;
+  g.set(x, y, z, 4);
+  const T xx = x * x, yy = y * y, zz = z * z;
+  const T dx2 = xx - zz, dy2 = yy - zz;
+  const T x2 = x + x, y2 = y + y;
+  const T xy2 = x2 * y, xz2 = x2 * z, yz2 = y2 * z;
+  // q = M3'_B(R,R) (M3: xxx0 xxy1 xxz2 xyy3 xyz4 xzz5 yyy6 yyz7 yzz8)
+  const T qx = fma(M3[0], dx2, fma(M3[3], dy2, fma(M3[1], xy2, fma(M3[2], xz2, M3[4] * yz2))));
+  const T qy = fma(M3[1], dx2, fma(M3[6], dy2, fma(M3[3], xy2, fma(M3[4], xz2, M3[7] * yz2))));
+  const T qz = fma(M3[2], dx2, fma(M3[7], dy2, fma(M3[4], xy2, fma(M3[5], xz2, M3[8] * yz2))));
+  const T rrr = fma(x, qx, fma(y, qy, z * qz));
+  // M2' R and R.M2'.R (M2: xx0 xy1 xz2 yy3 yz4 zz5)
+  const T m2rx = fma(M2[0], x, fma(M2[1], y, M2[2] * z));
+  const T m2ry = fma(M2[1], x, fma(M2[3], y, M2[4] * z));
+  const T m2rz = fma(M2[2], x, fma(M2[4], y, M2[5] * z));
+  const T rm2r = fma(x, m2rx, fma(y, m2ry, z * m2rz));
+  T* L = S.L;
+  // L0 -= m g0 + 1/2 g2 R.M2.R - 1/6 g3 M3(R,R,R)
+  const T h2 = T(0.5) * g.g2, h3 = g.g3 * (T(1) / T(6)), k3 = T(0.5) * g.g3;
+  L[0] = fma(h3, rrr, fma(-h2, rm2r, fma(-mB, g.g0, L[0])));
+  // L1 -= (m g1 + 1/2 g3 R.M2.R) R + g2 M2 R
+  const T a1 = mB * g.g1;
+  const T c1 = fma(k3, rm2r, a1);
+  L[1] = fma(-g.g2, m2rx, fma(-c1, x, L[1]));
+  L[2] = fma(-g.g2, m2ry, fma(-c1, y, L[2]));
+  L[3] = fma(-g.g2, m2rz, fma(-c1, z, L[3]));
+  // L2 -= m (g2 R R + g1 I), L3 -= m (g3 R R R + g2 sym(R I)): the 12 independent components
+  const T a2 = mB * g.g2, a3 = mB * g.g3;
+  const T a2x = a2 * x, a2y = a2 * y, a2z = a2 * z;
+  L[4] = fma(-a2x, x, L[4] - a1);
+  L[5] = fma(-a2x, y, L[5]);
+  L[6] = fma(-a2x, z, L[6]);
+  L[7] = fma(-a2y, y, L[7] - a1);
+  L[8] = fma(-a2y, z, L[8]);
+  const T a3x = a3 * x, a3y = a3 * y;
+  const T a3xx = a3x * x, a3yy = a3y * y;
+  L[10] = fma(-a3xx, x, L[10] - T(3) * a2x);
+  L[11] = fma(-a3xx, y, L[11] - a2y);
+  L[12] = fma(-a3xx, z, L[12] - a2z);
+  L[13] = fma(-a3yy, x, L[13] - a2x);
+  L[14] = fma(-(a3x * y), z, L[14]);
+  L[16] = fma(-a3yy, y, L[16] - T(3) * a2y);
+  L[17] = fma(-a3yy, z, L[17] - a2z);
+  if (S.amc) {
+    // Q = (m_B / m_A) M3'_A - M3'_B;  a += 1/6 g4 R Q(R,R,R) + 1/2 g3 Q(R,R)
+    const T w = mB * S.mA_inv;
+    const T* A3 = S.M3A;
+    const T Qx = fma(w, fma(A3[0], dx2, fma(A3[3], dy2, fma(A3[1], xy2, fma(A3[2], xz2, A3[4] * yz2)))), -qx);
+    const T Qy = fma(w, fma(A3[1], dx2, fma(A3[6], dy2, fma(A3[3], xy2, fma(A3[4], xz2, A3[7] * yz2)))), -qy);
+    const T Qz = fma(w, fma(A3[2], dx2, fma(A3[7], dy2, fma(A3[4], xy2, fma(A3[5], xz2, A3[8] * yz2)))), -qz);
+    const T c4 = (g.g4 * (T(1) / T(6))) * fma(x, Qx, fma(y, Qy, z * Qz));
+    S.px = fma(k3, Qx, fma(c4, x, S.px));
+    S.py = fma(k3, Qy, fma(c4, y, S.py));
+    S.pz = fma(k3, Qz, fma(c4, z, S.pz));
+  }
+}
+
 // Adds the partial correction sums to the FP64 accumulators (the mixed path sums at most 64
 // pair terms in FP32 before each flush).
 template <typename T, bool AREF>
@@ -664,8 +738,8 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool a
       int32_t sB = nb[slot];
       if (sB < 0) continue;  // only without proper nesting
       int64_t iB = int64_t(sB) * kCells + cidx(px & 7, py & 7, pz & 7);
-      interact<T, true, true>(S, M, N, iB, S.dAx - __ldg(td + 4 * q) * h,
-                              S.dAy - __ldg(td + 4 * q + 1) * h, S.dAz - __ldg(td + 4 * q + 2) * h);
+      interact_rr<T>(S, M, N, iB, S.dAx - __ldg(td + 4 * q) * h, S.dAy - __ldg(td + 4 * q + 1) * h,
+                     S.dAz - __ldg(td + 4 * q + 2) * h);
     }
     flush(S);
   }
