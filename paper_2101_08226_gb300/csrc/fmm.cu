@@ -455,6 +455,7 @@ struct SrcView<float> {
 template <typename T, bool AREF>
 struct Target {
   T L[AREF ? 20 : 4];
+  T sa1, sa2x, sa2y, sa2z;  // refined targets: running sums of m g1 and m g2 R (interact_rr)
   double ax, ay, az;     // correction acceleration, FP64 sums
   T px, py, pz;          // FP32-or-FP64 partial sums flushed into ax.. by flush()
   T dAx, dAy, dAz;   // target centre-of-mass displacement
@@ -573,20 +574,26 @@ __device__ __forceinline__ void interact_rr(Target<T, true>& S, const T* __restr
   // L2 -= m (g2 R R + g1 I), L3 -= m (g3 R R R + g2 sym(R I)): the 12 independent components
   const T a2 = mB * g.g2, a3 = mB * g.g3;
   const T a2x = a2 * x, a2y = a2 * y, a2z = a2 * z;
-  L[4] = fma(-a2x, x, L[4] - a1);
+  // the m g1 I and m g2 sym(R I) parts are the same few sums for every component that has them:
+  // kept as running sums and applied once by finish_rr
+  S.sa1 += a1;
+  S.sa2x += a2x;
+  S.sa2y += a2y;
+  S.sa2z += a2z;
+  L[4] = fma(-a2x, x, L[4]);
   L[5] = fma(-a2x, y, L[5]);
   L[6] = fma(-a2x, z, L[6]);
-  L[7] = fma(-a2y, y, L[7] - a1);
+  L[7] = fma(-a2y, y, L[7]);
   L[8] = fma(-a2y, z, L[8]);
   const T a3x = a3 * x, a3y = a3 * y;
   const T a3xx = a3x * x, a3yy = a3y * y;
-  L[10] = fma(-a3xx, x, L[10] - T(3) * a2x);
-  L[11] = fma(-a3xx, y, L[11] - a2y);
-  L[12] = fma(-a3xx, z, L[12] - a2z);
-  L[13] = fma(-a3yy, x, L[13] - a2x);
+  L[10] = fma(-a3xx, x, L[10]);
+  L[11] = fma(-a3xx, y, L[11]);
+  L[12] = fma(-a3xx, z, L[12]);
+  L[13] = fma(-a3yy, x, L[13]);
   L[14] = fma(-(a3x * y), z, L[14]);
-  L[16] = fma(-a3yy, y, L[16] - T(3) * a2y);
-  L[17] = fma(-a3yy, z, L[17] - a2z);
+  L[16] = fma(-a3yy, y, L[16]);
+  L[17] = fma(-a3yy, z, L[17]);
   if (S.amc) {
     // Q = (m_B / m_A) M3'_A - M3'_B;  a += 1/6 g4 R Q(R,R,R) + 1/2 g3 Q(R,R)
     const T w = mB * S.mA_inv;
@@ -599,6 +606,66 @@ __device__ __forceinline__ void interact_rr(Target<T, true>& S, const T* __restr
     S.py = fma(k3, Qy, fma(c4, y, S.py));
     S.pz = fma(k3, Qz, fma(c4, z, S.pz));
   }
+}
+
+// A leaf target (a point mass at its centre: only L0, L1; no M3 of its own, so the correction
+// takes Q = -M3'_B) and a refined partner, in the same multiply-add form as interact_rr.
+template <typename T>
+__device__ __forceinline__ void interact_lr(Target<T, false>& S, const T* __restrict__ M, int64_t N,
+                                            int64_t iB, T x, T y, T z) {
+  const T mB = M[iB];
+  x -= M[N + iB];
+  y -= M[2 * N + iB];
+  z -= M[3 * N + iB];
+  T M2[6], M3[9];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) M2[k] = M[(4 + k) * N + iB];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) M3[k] = M[(10 + k) * N + iB];
+  Radial<T> g;
+  g.set(x, y, z, 4);
+  const T xx = x * x, yy = y * y, zz = z * z;
+  const T dx2 = xx - zz, dy2 = yy - zz;
+  const T x2 = x + x, y2 = y + y;
+  const T xy2 = x2 * y, xz2 = x2 * z, yz2 = y2 * z;
+  const T qx = fma(M3[0], dx2, fma(M3[3], dy2, fma(M3[1], xy2, fma(M3[2], xz2, M3[4] * yz2))));
+  const T qy = fma(M3[1], dx2, fma(M3[6], dy2, fma(M3[3], xy2, fma(M3[4], xz2, M3[7] * yz2))));
+  const T qz = fma(M3[2], dx2, fma(M3[7], dy2, fma(M3[4], xy2, fma(M3[5], xz2, M3[8] * yz2))));
+  const T rrr = fma(x, qx, fma(y, qy, z * qz));
+  const T m2rx = fma(M2[0], x, fma(M2[1], y, M2[2] * z));
+  const T m2ry = fma(M2[1], x, fma(M2[3], y, M2[4] * z));
+  const T m2rz = fma(M2[2], x, fma(M2[4], y, M2[5] * z));
+  const T rm2r = fma(x, m2rx, fma(y, m2ry, z * m2rz));
+  T* L = S.L;
+  const T h2 = T(0.5) * g.g2, h3 = g.g3 * (T(1) / T(6)), k3 = T(0.5) * g.g3;
+  L[0] = fma(h3, rrr, fma(-h2, rm2r, fma(-mB, g.g0, L[0])));
+  const T c1 = fma(k3, rm2r, mB * g.g1);
+  L[1] = fma(-g.g2, m2rx, fma(-c1, x, L[1]));
+  L[2] = fma(-g.g2, m2ry, fma(-c1, y, L[2]));
+  L[3] = fma(-g.g2, m2rz, fma(-c1, z, L[3]));
+  if (S.amc) {
+    // Q = -M3'_B: a += 1/6 g4 R Q(R,R,R) + 1/2 g3 Q(R,R)
+    const T c4 = (g.g4 * (T(1) / T(6))) * rrr;
+    S.px = fma(-k3, qx, fma(-c4, x, S.px));
+    S.py = fma(-k3, qy, fma(-c4, y, S.py));
+    S.pz = fma(-k3, qz, fma(-c4, z, S.pz));
+  }
+}
+
+// The running sums of interact_rr into the L2, L3 components: L2 -= sum m g1 I,
+// L3 -= sum m g2 sym(R I) (xxx: 3 x, xxy: y, xxz: z, xyy: x, yyy: 3 y, yyz: z).
+template <typename T>
+__device__ __forceinline__ void finish_rr(Target<T, true>& S) {
+  T* L = S.L;
+  L[4] -= S.sa1;
+  L[7] -= S.sa1;
+  L[10] -= T(3) * S.sa2x;
+  L[11] -= S.sa2y;
+  L[12] -= S.sa2z;
+  L[13] -= S.sa2x;
+  L[16] -= T(3) * S.sa2y;
+  L[17] -= S.sa2z;
+  S.sa1 = S.sa2x = S.sa2y = S.sa2z = T(0);
 }
 
 // Adds the partial correction sums to the FP64 accumulators (the mixed path sums at most 64
@@ -626,6 +693,7 @@ __device__ __forceinline__ void load_target(Target<T, AREF>& S, const DevArgs& A
   for (int k = 0; k < (AREF ? 20 : 4); ++k) S.L[k] = T(0);
   S.ax = S.ay = S.az = 0.0;
   S.px = S.py = S.pz = T(0);
+  S.sa1 = S.sa2x = S.sa2y = S.sa2z = T(0);
   const int64_t N = A.n_cell;
   S.amc = amc;
   if constexpr (AREF) {
@@ -743,6 +811,7 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool a
     }
     flush(S);
   }
+  finish_rr(S);
   store_own<T, true>(A, S, iA);
 }
 
@@ -825,8 +894,8 @@ __device__ void m2l_boundary(const DevArgs& A, int chunk, int t, bool amc) {
     const int32_t j1 = min(j0 + kFlush, m1);
     for (int32_t j = j0; j < j1; ++j) {
       const int q = __ldg(A.bm_q + j);
-      interact<T, false, true>(S, M, N, __ldg(A.bm_src + j), -__ldg(td + 4 * q) * h,
-                               -__ldg(td + 4 * q + 1) * h, -__ldg(td + 4 * q + 2) * h);
+      interact_lr<T>(S, M, N, __ldg(A.bm_src + j), -__ldg(td + 4 * q) * h,
+                     -__ldg(td + 4 * q + 1) * h, -__ldg(td + 4 * q + 2) * h);
     }
     flush(S);
   }
