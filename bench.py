@@ -80,6 +80,27 @@ def measured_traffic():
     return out if sha == h.hexdigest() else {}
 
 
+def reduce_max(x: float, dist, world: int, device) -> float:
+    """The maximum of x over all ranks (the job is as slow as its slowest replica)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(rank: int, step: int) -> int:
+    """Seed of the density perturbation of one step of one rank's replica."""
+    return rank * 1000 + step
+
+
+def whole_job_rate(world: int, units_per_step: float, steps: int, max_total_ms: float) -> float:
+    """Units processed by all ranks (independent replicas, equal work) per second of the slowest
+    rank's timed region."""
+    return world * units_per_step * steps / (max_total_ms * 1e-3)
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
@@ -312,7 +333,7 @@ def run_ours(args):
     kernel_flops = {k: sum(FLOPS[c] * counts[c] for c in cs) for k, cs in KERNEL_PAIRS.items()}
     floor = w.field.floor * w.field.rho_peak
     n_steps = args.warmup + args.steps
-    rhos = [torch.from_numpy(synth.perturbed_density(rho0, rank * 1000 + k, floor_value=floor)).to(dev)
+    rhos = [torch.from_numpy(synth.perturbed_density(rho0, replica_seed(rank, k), floor_value=floor)).to(dev)
             for k in range(n_steps)]
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     g = torch.empty((n, 3), dtype=torch.float64, device=dev)
@@ -347,11 +368,7 @@ def run_ours(args):
             phases.append(tree.phase_times())
         torch.cuda.synchronize()
         tree.sync_status(stream)
-        total = float(np.sum(step_ms))
-        if world > 1:
-            tt = torch.tensor([total], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            total = float(tt.item())
+        total = reduce_max(float(np.sum(step_ms)), dist, world, dev)
         launches = tree.last_launches() * args.steps
         return total, np.mean(np.array(phases), axis=0), launches
 
@@ -390,11 +407,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         tree.solve_host(rho_h.numpy(), THETA, "fp64", True, phi_h.numpy(), g_h.numpy(), net_h.numpy(), stream)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = reduce_max(time.perf_counter() - t0, dist, world, dev)
 
     # the time-derivative solve on the same tree: rho and d rho/dt in one call (Sec. 2.1)
     rhodot = torch.from_numpy(rho0 * np.random.default_rng(31).uniform(-1.0, 1.0, rho0.size)).to(dev)
@@ -453,8 +466,8 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     cpu = cpu_baseline() if world == 1 else None
-    value64 = world * n_m2l * args.steps / (t64 * 1e-3)
-    value32 = world * n_m2l * args.steps / (t32 * 1e-3)
+    value64 = whole_job_rate(world, n_m2l, args.steps, t64)
+    value32 = whole_job_rate(world, n_m2l, args.steps, t32)
 
     traffic = measured_traffic()
 
