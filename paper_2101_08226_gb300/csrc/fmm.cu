@@ -95,7 +95,9 @@ struct DevArgs {
   const float* ltab_d32;
   double* mom;             // [20][n_cell] raw moments (shifted by m2m)
   double* mtl;             // [20][n_cell] same with detraced M2, M3 (read by the interactions)
-  float* mom32;            // [20][n_cell] FP32 copy of mtl (mixed path)
+  float* mom32;            // [n_cell][20] FP32 copy of mtl (mixed path), cell-major: a partner's
+                           // 20 moments are 80 contiguous bytes, five 16-byte loads
+  float* m32;              // [n_cell] FP32 masses (the leaf kernel's halo)
   double* loc;             // [20][n_cell] own, then total expansion
   float* loc32;            // [20][n_cell] own expansion (mixed path)
   double* ac;              // [3][n_cell] correction acceleration, own then total
@@ -205,7 +207,10 @@ __global__ void k_p2m(DevArgs A, int mixed) {
   const double m = r * cell_vol(lev);
   A.mom[cell] = m;
   A.mtl[cell] = m;
-  if (mixed) A.mom32[cell] = float(m);
+  if (mixed) {
+    A.mom32[cell * 20] = float(m);
+    A.m32[cell] = float(m);
+  }
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -235,7 +240,10 @@ __device__ __forceinline__ void store_moments(const DevArgs& A, int64_t cell, do
   for (int k = 0; k < 20; ++k) A.mtl[k * N + cell] = T[k];
   if (mixed) {
 #pragma unroll
-    for (int k = 0; k < 20; ++k) A.mom32[k * N + cell] = float(T[k]);
+    for (int q = 0; q < 5; ++q)
+      reinterpret_cast<float4*>(A.mom32 + cell * 20)[q] =
+          make_float4(float(T[4 * q]), float(T[4 * q + 1]), float(T[4 * q + 2]), float(T[4 * q + 3]));
+    A.m32[cell] = float(mt);
   }
 }
 
@@ -439,6 +447,39 @@ struct MomView<float> {
   static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.mom32; }
 };
 
+// Component k of cell i in a moment array: component-major in FP64, cell-major in FP32.
+template <typename T>
+struct MomAt;
+template <>
+struct MomAt<double> {
+  static __device__ __forceinline__ int64_t at(int64_t N, int64_t i, int k) { return k * N + i; }
+};
+template <>
+struct MomAt<float> {
+  static __device__ __forceinline__ int64_t at(int64_t, int64_t i, int k) { return i * 20 + k; }
+};
+template <typename T>
+__device__ __forceinline__ T mom_get(const T* __restrict__ M, int64_t N, int64_t i, int k) {
+  return M[MomAt<T>::at(N, i, k)];
+}
+// All 20 moments of cell i.
+__device__ __forceinline__ void mom_load20(const double* __restrict__ M, int64_t N, int64_t i,
+                                           double* out) {
+#pragma unroll
+  for (int k = 0; k < 20; ++k) out[k] = M[k * N + i];
+}
+__device__ __forceinline__ void mom_load20(const float* __restrict__ M, int64_t, int64_t i, float* out) {
+  const float4* p = reinterpret_cast<const float4*>(M + i * 20);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const float4 v = __ldg(p + q);
+    out[4 * q] = v.x;
+    out[4 * q + 1] = v.y;
+    out[4 * q + 2] = v.z;
+    out[4 * q + 3] = v.w;
+  }
+}
+
 // Source moments of the time-derivative solve, as read by the interactions.
 template <typename T>
 struct SrcView;
@@ -469,18 +510,17 @@ struct Target {
 template <typename T, bool AREF, bool BREF>
 __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict__ M, int64_t N,
                                          int64_t iB, T x, T y, T z) {
-  T mB = M[iB];
+  T mB;
   Radial<T> g;
   if constexpr (BREF) {
-    T dBx = M[N + iB], dBy = M[2 * N + iB], dBz = M[3 * N + iB];
-    x -= dBx;
-    y -= dBy;
-    z -= dBz;
-    T M2[6], M3[10];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) M2[k] = M[(4 + k) * N + iB];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) M3[k] = M[(10 + k) * N + iB];
+    T Mv[20];
+    mom_load20(M, N, iB, Mv);
+    mB = Mv[0];
+    x -= Mv[1];
+    y -= Mv[2];
+    z -= Mv[3];
+    const T* M2 = Mv + 4;
+    const T* M3 = Mv + 10;
     g.set(x, y, z, 4);
     T qx, qy, qz, rrr;
     m2l_far<T>(x, y, z, g, mB, M2, M3, S.L, qx, qy, qz, rrr);
@@ -509,6 +549,7 @@ __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict
       S.pz += cz;
     }
   } else {
+    mB = mom_get(M, N, iB, 0);
     g.set(x, y, z, AREF ? 4 : 1);
     m2l_mono<T>(x, y, z, g, mB, S.L);
     if constexpr (AREF) {
@@ -536,15 +577,14 @@ __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict
 template <typename T>
 __device__ __forceinline__ void interact_rr(Target<T, true>& S, const T* __restrict__ M, int64_t N,
                                             int64_t iB, T x, T y, T z) {
-  const T mB = M[iB];
-  x -= M[N + iB];
-  y -= M[2 * N + iB];
-  z -= M[3 * N + iB];
-  T M2[6], M3[9];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) M2[k] = M[(4 + k) * N + iB];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) M3[k] = M[(10 + k) * N + iB];  // zzz is not needed
+  T Mv[20];
+  mom_load20(M, N, iB, Mv);
+  const T mB = Mv[0];
+  x -= Mv[1];
+  y -= Mv[2];
+  z -= Mv[3];
+  const T* M2 = Mv + 4;
+  const T* M3 = Mv + 10;  // zzz is not needed
   Radial<T> g;
   g.set(x, y, z, 4);
   const T xx = x * x, yy = y * y, zz = z * z;
@@ -613,15 +653,14 @@ __device__ __forceinline__ void interact_rr(Target<T, true>& S, const T* __restr
 template <typename T>
 __device__ __forceinline__ void interact_lr(Target<T, false>& S, const T* __restrict__ M, int64_t N,
                                             int64_t iB, T x, T y, T z) {
-  const T mB = M[iB];
-  x -= M[N + iB];
-  y -= M[2 * N + iB];
-  z -= M[3 * N + iB];
-  T M2[6], M3[9];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) M2[k] = M[(4 + k) * N + iB];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) M3[k] = M[(10 + k) * N + iB];
+  T Mv[20];
+  mom_load20(M, N, iB, Mv);
+  const T mB = Mv[0];
+  x -= Mv[1];
+  y -= Mv[2];
+  z -= Mv[3];
+  const T* M2 = Mv + 4;
+  const T* M3 = Mv + 10;
   Radial<T> g;
   g.set(x, y, z, 4);
   const T xx = x * x, yy = y * y, zz = z * z;
@@ -697,18 +736,20 @@ __device__ __forceinline__ void load_target(Target<T, AREF>& S, const DevArgs& A
   const int64_t N = A.n_cell;
   S.amc = amc;
   if constexpr (AREF) {
-    S.dAx = M[N + iA];
-    S.dAy = M[2 * N + iA];
-    S.dAz = M[3 * N + iA];
-    T mA = M[iA];
+    T Mv[20];
+    mom_load20(M, N, iA, Mv);
+    S.dAx = Mv[1];
+    S.dAy = Mv[2];
+    S.dAz = Mv[3];
+    const T mA = Mv[0];
     S.mA_inv = mA > T(0) ? T(1) / mA : T(0);
     if (!(mA > T(0))) S.amc = false;
 #pragma unroll
-    for (int k = 0; k < 10; ++k) S.M3A[k] = M[(10 + k) * N + iA];
+    for (int k = 0; k < 10; ++k) S.M3A[k] = Mv[10 + k];
   } else {
     S.dAx = S.dAy = S.dAz = T(0);
     S.mA_inv = T(0);
-    if (!(M[iA] > T(0))) S.amc = false;
+    if (!(mom_get(M, N, iA, 0) > T(0))) S.amc = false;
   }
 }
 
@@ -905,7 +946,7 @@ __device__ void m2l_boundary(const DevArgs& A, int chunk, int t, bool amc) {
     const T x = quarter[((code >> 20) & 1023) - 512 + kCodeMax] * h;
     const T y = quarter[((code >> 10) & 1023) - 512 + kCodeMax] * h;
     const T z = quarter[(code & 1023) - 512 + kCodeMax] * h;
-    interact_point<T, false>(S, M[__ldg(A.bp_src + j)], x, y, z);
+    interact_point<T, false>(S, mom_get(M, N, __ldg(A.bp_src + j), 0), x, y, z);
   }
   if (sizeof(T) == 8) {
     for (int c = 0; c < 4; ++c) A.loc[c * N + iA] += double(S.L[c]);
@@ -958,6 +999,17 @@ __device__ __forceinline__ void load4(const double* p, double& a, double& b, dou
 }
 
 template <typename T>
+struct LeafMass;
+template <>
+struct LeafMass<double> {
+  static __device__ __forceinline__ const double* get(const DevArgs& A) { return A.mtl; }
+};
+template <>
+struct LeafMass<float> {
+  static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.m32; }
+};
+
+template <typename T>
 struct LeafTab;
 template <>
 struct LeafTab<double> {
@@ -987,7 +1039,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
     nb[t] = (q >= 0 && A.leaf[q]) ? q : -1;
   }
   __syncthreads();
-  const T* __restrict__ M = SRC ? SrcView<T>::get(A) : MomView<T>::get(A);
+  // masses: component 0 of the (component-major) FP64 or source arrays, or the FP32 mass array
+  const T* __restrict__ M = SRC ? SrcView<T>::get(A) : LeafMass<T>::get(A);
   const int64_t N = A.n_cell;
   for (int i = t; i < kHalo * kHalo * kHalo; i += kLeafThreads) {
     const int hx = i / (kHalo * kHalo), r = i - hx * (kHalo * kHalo), hy = r / kHalo, hz = r - hy * kHalo;
@@ -1107,7 +1160,7 @@ struct Down {
     else (SRC ? A.sloc : A.loc)[k * A.n_cell + i] = v;
   }
   static __device__ __forceinline__ T com(const DevArgs& A, int k, int64_t i) {
-    if constexpr (MIXED) return A.mom32[k * A.n_cell + i];
+    if constexpr (MIXED) return A.mom32[i * 20 + k];
     else return A.mom[k * A.n_cell + i];
   }
 };
@@ -1500,9 +1553,9 @@ __device__ __forceinline__ void interact_src(T* L, const T* __restrict__ Sm, con
   const T s0 = Sm[iB];
   Radial<T> g;
   if constexpr (BREF) {
-    x -= G[N + iB];
-    y -= G[2 * N + iB];
-    z -= G[3 * N + iB];
+    x -= mom_get(G, N, iB, 1);
+    y -= mom_get(G, N, iB, 2);
+    z -= mom_get(G, N, iB, 3);
     g.set(x, y, z, 3);
     const T s1x = Sm[N + iB], s1y = Sm[2 * N + iB], s1z = Sm[3 * N + iB];
     T S2[6], S3[10];
@@ -1575,7 +1628,7 @@ __device__ void m2l_level_src(const DevArgs& A, int32_t s, int parity, int t) {
   int a, b, c;
   block_cell(parity, t, a, b, c);
   const int64_t iA = int64_t(s) * kCells + cidx(a, b, c);
-  const T dAx = G[N + iA], dAy = G[2 * N + iA], dAz = G[3 * N + iA];
+  const T dAx = mom_get(G, N, iA, 1), dAy = mom_get(G, N, iA, 2), dAz = mom_get(G, N, iA, 3);
   T L[20];
 #pragma unroll
   for (int k = 0; k < 20; ++k) L[k] = T(0);
@@ -1608,7 +1661,8 @@ __device__ void m2l_root_src(const DevArgs& A, int root, int parity, int t, int 
   block_cell(parity, t, a, b, c);
   const int iloc = cidx(a, b, c);
   const int64_t base = int64_t(root) * kCells;
-  const T dAx = G[N + base + iloc], dAy = G[2 * N + base + iloc], dAz = G[3 * N + base + iloc];
+  const T dAx = mom_get(G, N, base + iloc, 1), dAy = mom_get(G, N, base + iloc, 2),
+          dAz = mom_get(G, N, base + iloc, 3);
   T L[20];
 #pragma unroll
   for (int k = 0; k < 20; ++k) L[k] = T(0);
@@ -1913,7 +1967,7 @@ struct fmm_tree {
   int64_t n_work = 0;
   double *d_mom = nullptr, *d_mtl = nullptr, *d_loc = nullptr, *d_ac = nullptr, *d_root_part = nullptr,
          *d_root_part_ac = nullptr, *d_partials = nullptr;
-  float *d_mom32 = nullptr, *d_loc32 = nullptr, *d_root_part32 = nullptr;
+  float *d_mom32 = nullptr, *d_m32 = nullptr, *d_loc32 = nullptr, *d_root_part32 = nullptr;
   int* d_status = nullptr;
   int64_t* d_tree_leaf_off = nullptr;
   double *d_rho = nullptr, *d_phi = nullptr, *d_g = nullptr, *d_net = nullptr;
@@ -2072,6 +2126,7 @@ static int ensure_mixed(fmm_tree* t) {
   const int64_t nc = t->h.n_sub * kCells;
   CUDA_TRY(dalloc(t, &t->d_mom32, sizeof(float) * kNMom * nc));
   CUDA_TRY(cudaMemset(t->d_mom32, 0, sizeof(float) * kNMom * nc));  // leaf cells keep zeros
+  CUDA_TRY(dalloc(t, &t->d_m32, sizeof(float) * nc));
   CUDA_TRY(dalloc(t, &t->d_loc32, sizeof(float) * 20 * nc));
   const int64_t nr = t->h.n_trees;
   CUDA_TRY(dalloc(t, &t->d_root_part32, sizeof(float) * nr * kRootChunks * 20 * kCells));
@@ -2402,6 +2457,7 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.mom = t->d_mom;
   A.mtl = t->d_mtl;
   A.mom32 = t->d_mom32;
+  A.m32 = t->d_m32;
   A.loc = t->d_loc;
   A.loc32 = t->d_loc32;
   A.ac = t->d_ac;
