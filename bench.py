@@ -376,6 +376,12 @@ def run_ours(args):
     t64, ph64, l64 = timed("fp64")
     phi64, g64, net64 = phi.clone(), g.clone(), net.clone()
     t32, ph32, l32 = timed("mixed")
+    # FP64 results with the pair arithmetic in double-float on the FP32 pipes
+    tdf, phdf, ldf = timed("df64")
+    df_err = {"phi_max_rel_vs_fp64": float(((phi - phi64).abs() / phi64.abs()).max().item()),
+              "g_max_rel_vs_fp64": float(((g - g64).norm(dim=1) / g64.norm(dim=1)).max().item()),
+              "force_over_norm": float((net[:3].abs().max() / net[6]).item()),
+              "torque_over_norm": float((net[3:6].abs().max() / net[6]).item())}
     # the same mixed solve with its kernels launched one by one instead of one graph replay
     tree.set_graphs(False)
     t32d, _, _ = timed("mixed")
@@ -504,6 +510,10 @@ def run_ours(args):
                    "parallelism": f"{world} independent replicas"},
         "roofline": roofline(ph64, "fp64"),
         "phases_ms": phases(ph64),
+        "df64": {"value": whole_job_rate(world, n_m2l, args.steps, tdf), "ms_per_step": tdf / args.steps,
+                 "dtype": "double-float (2 x f32) pair arithmetic, f64 rest",
+                 "speedup_vs_fp64": t64 / tdf, "err_vs_fp64_path": df_err,
+                 "phases_ms": phases(phdf), "gpu_launches": ldf},
         "mixed": {"value": value32, "ms_per_step": t32 / args.steps, "dtype": "f32 pairs, f64 rest",
                   "speedup_vs_fp64": t64 / t32, "err_vs_fp64": err,
                   "roofline": roofline(ph32, "mixed"),

@@ -46,8 +46,13 @@ extern "C" {
 #define FMM_ERR_STATE (-8)     /* tree not usable (destroyed or built on another device) */
 
 #define FMM_FP64 0  /* every step in FP64 */
-#define FMM_MIXED 1 /* multipole interactions and direct sums in FP32; moments, shifts,
-                       correction sums and reductions in FP64 */
+#define FMM_MIXED 1 /* multipole interactions and direct sums in FP32, expansions in FP32;
+                       moments, correction sums and reductions in FP64 */
+#define FMM_DF64 2  /* FP64 except the pair arithmetic of the interactions and direct sums, which
+                       runs in double-float (pairs of floats, about 48 bits, on the FP32 pipes):
+                       results within the FP64 path's 1e-12 parity bar, at FP32-pipe speed.  The
+                       float exponent range applies inside the pair arithmetic (|values| between
+                       about 1e-38 and 3e38).  Not for fmm_solve_dt. */
 
 #define FMM_MAX_LEVEL 9 /* deepest refinement level accepted (levels 0..9) */
 
@@ -114,7 +119,7 @@ int fmm_interaction_counts_by_type(const fmm_tree* tree, double theta, int64_t c
  * g_dev: [n_leaf][3] acceleration.  net_dev (optional, may be NULL): 7 doubles
  *   (F_x, F_y, F_z, T_x, T_y, T_z, S) with F = sum m g, T = sum x cross m g, S = sum |x| |m g|,
  *   reduced in FP64 in a fixed order (the terms of the normalisation S are formed in FP32).
- * theta in [0.34, 1).  precision FMM_FP64 or FMM_MIXED.  stream: a cudaStream_t (NULL = legacy
+ * theta in [0.34, 1).  precision FMM_FP64, FMM_MIXED or FMM_DF64.  stream: a cudaStream_t (NULL = legacy
  * default stream).  Asynchronous: returns once the work is enqueued.  On a forest, net_dev holds
  * 7 doubles per tree.
  * Execution: the work runs on a stream the tree owns, after all work enqueued on `stream` before

@@ -18,6 +18,7 @@ FMM_ERR_STATE = -8
 FMM_NET_STATIC_MAX_POINTS = 2048 * 4096
 FMM_FP64 = 0
 FMM_MIXED = 1
+FMM_DF64 = 2
 
 EXPORTS = [
     "fmm_build_tree", "fmm_destroy", "fmm_build_forest", "fmm_forest_info", "fmm_solve_batch", "fmm_tree_info", "fmm_tree_subgrids", "fmm_stencil",

@@ -11,7 +11,7 @@ import numpy as np
 from . import _lib
 from ._lib import check, lib
 
-PRECISIONS = {"fp64": _lib.FMM_FP64, "mixed": _lib.FMM_MIXED}
+PRECISIONS = {"fp64": _lib.FMM_FP64, "mixed": _lib.FMM_MIXED, "df64": _lib.FMM_DF64}
 
 
 def _p(a: np.ndarray):

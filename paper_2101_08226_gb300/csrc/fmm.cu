@@ -93,11 +93,15 @@ struct DevArgs {
   const float* ltab_k32;   // same in FP32
   const double* ltab_d64;  // [8][kLeafCap][4]: d (dx, dy, dz, 0) as floating-point numbers
   const float* ltab_d32;
+  const dfloat* ltab_kff;  // the 1/|d|, d/|d|^3 table as double-float pairs
+  const dfloat* ltab_dff;  // offsets d as double-float
   double* mom;             // [20][n_cell] raw moments (shifted by m2m)
   double* mtl;             // [20][n_cell] same with detraced M2, M3 (read by the interactions)
   float* mom32;            // [n_cell][20] FP32 copy of mtl (mixed path), cell-major: a partner's
                            // 20 moments are 80 contiguous bytes, five 16-byte loads
   float* m32;              // [n_cell] FP32 masses (the leaf kernel's halo)
+  dfloat* momff;           // [n_cell][20] double-float copy of mtl (df64 path), cell-major
+  dfloat* massff;          // [n_cell] double-float masses
   double* loc;             // [20][n_cell] own, then total expansion
   float* loc32;            // [20][n_cell] own expansion (mixed path)
   double* ac;              // [3][n_cell] correction acceleration, own then total
@@ -168,6 +172,8 @@ template <>
 __device__ __forceinline__ double cell_h<double>(int lev) { return cell_dx(lev); }
 template <>
 __device__ __forceinline__ float cell_h<float>(int lev) { return cell_dx32(lev); }
+template <>
+__device__ __forceinline__ dfloat cell_h<dfloat>(int lev) { return dfloat(cell_dx32(lev), 0.0f); }
 
 // Internal order of the 512 cells of a subgrid (the solver's own arrays; user arrays keep
 // (a*8 + b)*8 + c): parity-major, cell (a, b, c) = (2 ia + pa, 2 ib + pb, 2 ic + pc) at
@@ -207,9 +213,12 @@ __global__ void k_p2m(DevArgs A, int mixed) {
   const double m = r * cell_vol(lev);
   A.mom[cell] = m;
   A.mtl[cell] = m;
-  if (mixed) {
+  if (mixed == 1) {
     A.mom32[cell * 20] = float(m);
     A.m32[cell] = float(m);
+  } else if (mixed == 2) {
+    A.momff[cell * 20] = dfloat(m);
+    A.massff[cell] = dfloat(m);
   }
 }
 
@@ -238,12 +247,19 @@ __device__ __forceinline__ void store_moments(const DevArgs& A, int64_t cell, do
                         M3[5] - tx, M3[6] - 3 * ty, M3[7] - tz, M3[8] - ty, M3[9] - 3 * tz};
 #pragma unroll
   for (int k = 0; k < 20; ++k) A.mtl[k * N + cell] = T[k];
-  if (mixed) {
+  if (mixed == 1) {
 #pragma unroll
     for (int q = 0; q < 5; ++q)
       reinterpret_cast<float4*>(A.mom32 + cell * 20)[q] =
           make_float4(float(T[4 * q]), float(T[4 * q + 1]), float(T[4 * q + 2]), float(T[4 * q + 3]));
     A.m32[cell] = float(mt);
+  } else if (mixed == 2) {
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      const dfloat u = dfloat(T[2 * q]), v = dfloat(T[2 * q + 1]);
+      reinterpret_cast<float4*>(A.momff + cell * 20)[q] = make_float4(u.hi, u.lo, v.hi, v.lo);
+    }
+    A.massff[cell] = dfloat(mt);
   }
 }
 
@@ -435,6 +451,10 @@ template <>
 struct LeafOffsets<float> {
   static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.ltab_d32; }
 };
+template <>
+struct LeafOffsets<dfloat> {
+  static __device__ __forceinline__ const dfloat* get(const DevArgs& A) { return A.ltab_dff; }
+};
 
 template <typename T>
 struct MomView;
@@ -446,6 +466,18 @@ template <>
 struct MomView<float> {
   static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.mom32; }
 };
+template <>
+struct MomView<dfloat> {
+  static __device__ __forceinline__ const dfloat* get(const DevArgs& A) { return A.momff; }
+};
+
+// Read-only loads of table values of any of the arithmetic types.
+__device__ __forceinline__ double ldg_t(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldg_t(const float* p) { return __ldg(p); }
+__device__ __forceinline__ dfloat ldg_t(const dfloat* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return dfloat(v.x, v.y);
+}
 
 // Component k of cell i in a moment array: component-major in FP64, cell-major in FP32.
 template <typename T>
@@ -456,6 +488,10 @@ struct MomAt<double> {
 };
 template <>
 struct MomAt<float> {
+  static __device__ __forceinline__ int64_t at(int64_t, int64_t i, int k) { return i * 20 + k; }
+};
+template <>
+struct MomAt<dfloat> {
   static __device__ __forceinline__ int64_t at(int64_t, int64_t i, int k) { return i * 20 + k; }
 };
 template <typename T>
@@ -477,6 +513,16 @@ __device__ __forceinline__ void mom_load20(const float* __restrict__ M, int64_t,
     out[4 * q + 1] = v.y;
     out[4 * q + 2] = v.z;
     out[4 * q + 3] = v.w;
+  }
+}
+
+__device__ __forceinline__ void mom_load20(const dfloat* __restrict__ M, int64_t, int64_t i, dfloat* out) {
+  const float4* p = reinterpret_cast<const float4*>(M + i * 20);
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    const float4 v = __ldg(p + q);
+    out[2 * q] = dfloat(v.x, v.y);
+    out[2 * q + 1] = dfloat(v.z, v.w);
   }
 }
 
@@ -603,7 +649,7 @@ __device__ __forceinline__ void interact_rr(Target<T, true>& S, const T* __restr
   const T rm2r = fma(x, m2rx, fma(y, m2ry, z * m2rz));
   T* L = S.L;
   // L0 -= m g0 + 1/2 g2 R.M2.R - 1/6 g3 M3(R,R,R)
-  const T h2 = T(0.5) * g.g2, h3 = g.g3 * (T(1) / T(6)), k3 = T(0.5) * g.g3;
+  const T h2 = T(0.5) * g.g2, h3 = g.g3 * T(1.0 / 6.0), k3 = T(0.5) * g.g3;
   L[0] = fma(h3, rrr, fma(-h2, rm2r, fma(-mB, g.g0, L[0])));
   // L1 -= (m g1 + 1/2 g3 R.M2.R) R + g2 M2 R
   const T a1 = mB * g.g1;
@@ -641,7 +687,7 @@ __device__ __forceinline__ void interact_rr(Target<T, true>& S, const T* __restr
     const T Qx = fma(w, fma(A3[0], dx2, fma(A3[3], dy2, fma(A3[1], xy2, fma(A3[2], xz2, A3[4] * yz2)))), -qx);
     const T Qy = fma(w, fma(A3[1], dx2, fma(A3[6], dy2, fma(A3[3], xy2, fma(A3[4], xz2, A3[7] * yz2)))), -qy);
     const T Qz = fma(w, fma(A3[2], dx2, fma(A3[7], dy2, fma(A3[4], xy2, fma(A3[5], xz2, A3[8] * yz2)))), -qz);
-    const T c4 = (g.g4 * (T(1) / T(6))) * fma(x, Qx, fma(y, Qy, z * Qz));
+    const T c4 = (g.g4 * T(1.0 / 6.0)) * fma(x, Qx, fma(y, Qy, z * Qz));
     S.px = fma(k3, Qx, fma(c4, x, S.px));
     S.py = fma(k3, Qy, fma(c4, y, S.py));
     S.pz = fma(k3, Qz, fma(c4, z, S.pz));
@@ -676,7 +722,7 @@ __device__ __forceinline__ void interact_lr(Target<T, false>& S, const T* __rest
   const T m2rz = fma(M2[2], x, fma(M2[4], y, M2[5] * z));
   const T rm2r = fma(x, m2rx, fma(y, m2ry, z * m2rz));
   T* L = S.L;
-  const T h2 = T(0.5) * g.g2, h3 = g.g3 * (T(1) / T(6)), k3 = T(0.5) * g.g3;
+  const T h2 = T(0.5) * g.g2, h3 = g.g3 * T(1.0 / 6.0), k3 = T(0.5) * g.g3;
   L[0] = fma(h3, rrr, fma(-h2, rm2r, fma(-mB, g.g0, L[0])));
   const T c1 = fma(k3, rm2r, mB * g.g1);
   L[1] = fma(-g.g2, m2rx, fma(-c1, x, L[1]));
@@ -684,7 +730,7 @@ __device__ __forceinline__ void interact_lr(Target<T, false>& S, const T* __rest
   L[3] = fma(-g.g2, m2rz, fma(-c1, z, L[3]));
   if (S.amc) {
     // Q = -M3'_B: a += 1/6 g4 R Q(R,R,R) + 1/2 g3 Q(R,R)
-    const T c4 = (g.g4 * (T(1) / T(6))) * rrr;
+    const T c4 = (g.g4 * T(1.0 / 6.0)) * rrr;
     S.px = fma(-k3, qx, fma(-c4, x, S.px));
     S.py = fma(-k3, qy, fma(-c4, y, S.py));
     S.pz = fma(-k3, qz, fma(-c4, z, S.pz));
@@ -781,6 +827,30 @@ __device__ __forceinline__ void store_own<double, false>(const DevArgs& A,
   A.ac[2 * N + iA] = S.az;
 }
 template <>
+__device__ __forceinline__ void store_own<dfloat, true>(const DevArgs& A,
+                                                        const Target<dfloat, true>& S, int64_t iA) {
+  const int64_t N = A.n_cell;
+  dfloat L[20];
+#pragma unroll
+  for (int k = 0; k < 20; ++k) L[k] = S.L[k];
+  complete_traceless(L);
+#pragma unroll
+  for (int k = 0; k < 20; ++k) A.loc[k * N + iA] = double(L[k]);
+  A.ac[iA] = S.ax;
+  A.ac[N + iA] = S.ay;
+  A.ac[2 * N + iA] = S.az;
+}
+template <>
+__device__ __forceinline__ void store_own<dfloat, false>(const DevArgs& A,
+                                                         const Target<dfloat, false>& S, int64_t iA) {
+  const int64_t N = A.n_cell;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) A.loc[k * N + iA] = double(S.L[k]);
+  A.ac[iA] = S.ax;
+  A.ac[N + iA] = S.ay;
+  A.ac[2 * N + iA] = S.az;
+}
+template <>
 __device__ __forceinline__ void store_own<float, true>(const DevArgs& A,
                                                        const Target<float, true>& S, int64_t iA) {
   const int64_t N = A.n_cell;
@@ -847,8 +917,8 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool a
       int32_t sB = nb[slot];
       if (sB < 0) continue;  // only without proper nesting
       int64_t iB = int64_t(sB) * kCells + cidx(px & 7, py & 7, pz & 7);
-      interact_rr<T>(S, M, N, iB, S.dAx - __ldg(td + 4 * q) * h, S.dAy - __ldg(td + 4 * q + 1) * h,
-                     S.dAz - __ldg(td + 4 * q + 2) * h);
+      interact_rr<T>(S, M, N, iB, S.dAx - ldg_t(td + 4 * q) * h, S.dAy - ldg_t(td + 4 * q + 1) * h,
+                     S.dAz - ldg_t(td + 4 * q + 2) * h);
     }
     flush(S);
   }
@@ -935,8 +1005,8 @@ __device__ void m2l_boundary(const DevArgs& A, int chunk, int t, bool amc) {
     const int32_t j1 = min(j0 + kFlush, m1);
     for (int32_t j = j0; j < j1; ++j) {
       const int q = __ldg(A.bm_q + j);
-      interact_lr<T>(S, M, N, __ldg(A.bm_src + j), -__ldg(td + 4 * q) * h,
-                     -__ldg(td + 4 * q + 1) * h, -__ldg(td + 4 * q + 2) * h);
+      interact_lr<T>(S, M, N, __ldg(A.bm_src + j), -ldg_t(td + 4 * q) * h,
+                     -ldg_t(td + 4 * q + 1) * h, -ldg_t(td + 4 * q + 2) * h);
     }
     flush(S);
   }
@@ -989,6 +1059,14 @@ __device__ __forceinline__ void load4(const float* p, float& a, float& b, float&
   c = v.z;
   d = v.w;
 }
+__device__ __forceinline__ void load4(const dfloat* p, dfloat& a, dfloat& b, dfloat& c, dfloat& d) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 w = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  a = dfloat(v.x, v.y);
+  b = dfloat(v.z, v.w);
+  c = dfloat(w.x, w.y);
+  d = dfloat(w.z, w.w);
+}
 __device__ __forceinline__ void load4(const double* p, double& a, double& b, double& c, double& d) {
   const double2 v = __ldg(reinterpret_cast<const double2*>(p));
   const double2 w = __ldg(reinterpret_cast<const double2*>(p) + 1);
@@ -1008,6 +1086,10 @@ template <>
 struct LeafMass<float> {
   static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.m32; }
 };
+template <>
+struct LeafMass<dfloat> {
+  static __device__ __forceinline__ const dfloat* get(const DevArgs& A) { return A.massff; }
+};
 
 template <typename T>
 struct LeafTab;
@@ -1018,6 +1100,10 @@ struct LeafTab<double> {
 template <>
 struct LeafTab<float> {
   static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.ltab_k32; }
+};
+template <>
+struct LeafTab<dfloat> {
+  static __device__ __forceinline__ const dfloat* get(const DevArgs& A) { return A.ltab_kff; }
 };
 
 // Leaf subgrids at levels >= 1.  A leaf cell and a leaf partner at the same level are two point
@@ -1040,7 +1126,9 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
   }
   __syncthreads();
   // masses: component 0 of the (component-major) FP64 or source arrays, or the FP32 mass array
-  const T* __restrict__ M = SRC ? SrcView<T>::get(A) : LeafMass<T>::get(A);
+  const T* __restrict__ M;
+  if constexpr (SRC) M = SrcView<T>::get(A);
+  else M = LeafMass<T>::get(A);
   const int64_t N = A.n_cell;
   for (int i = t; i < kHalo * kHalo * kHalo; i += kLeafThreads) {
     const int hx = i / (kHalo * kHalo), r = i - hx * (kHalo * kHalo), hy = r / kHalo, hz = r - hy * kHalo;
@@ -1068,15 +1156,15 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
     T k0, kx, ky, kz;
     load4(tk + 4 * q, k0, kx, ky, kz);
     const T m0 = hm[base0 + off], m1 = hm[base1 + off];
-    s0 += m0 * k0;
-    u0 += m1 * k0;
+    s0 = fma(m0, k0, s0);
+    u0 = fma(m1, k0, u0);
     if (!SRC) {
-      sx += m0 * kx;
-      sy += m0 * ky;
-      sz += m0 * kz;
-      ux += m1 * kx;
-      uy += m1 * ky;
-      uz += m1 * kz;
+      sx = fma(m0, kx, sx);
+      sy = fma(m0, ky, sy);
+      sz = fma(m0, kz, sz);
+      ux = fma(m1, kx, ux);
+      uy = fma(m1, ky, uy);
+      uz = fma(m1, kz, uz);
     }
   }
   const T ih = T(1) / h, ih2 = ih * ih;
@@ -1129,7 +1217,7 @@ __device__ __forceinline__ void shift_add(const T* P, T rx, T ry, T rz, T* L) {
   T l2y = P[5] * rx + P[7] * ry + P[8] * rz;
   T l2z = P[6] * rx + P[8] * ry + P[9] * rz;
   L[0] += P[0] + P[1] * rx + P[2] * ry + P[3] * rz + T(0.5) * (rx * l2x + ry * l2y + rz * l2z) +
-          (rx * qx + ry * qy + rz * qz) * (T(1) / T(6));
+          (rx * qx + ry * qy + rz * qz) * T(1.0 / 6.0);
   L[1] += P[1] + l2x + T(0.5) * qx;
   L[2] += P[2] + l2y + T(0.5) * qy;
   L[3] += P[3] + l2z + T(0.5) * qz;
@@ -1571,7 +1659,7 @@ __device__ __forceinline__ void interact_src(T* L, const T* __restrict__ Sm, con
     T qx, qy, qz;
     sym3_rr(S3, x, y, z, qx, qy, qz);
     const T rrr = x * qx + y * qy + z * qz;
-    L[0] -= s0 * g.g0 - g.g1 * rs1 + T(0.5) * g.g2 * rs2r - (T(1) / T(6)) * g.g3 * rrr;
+    L[0] -= s0 * g.g0 - g.g1 * rs1 + T(0.5) * g.g2 * rs2r - T(1.0 / 6.0) * g.g3 * rrr;
     if constexpr (AREF) {
       const T c1 = s0 * g.g1 - g.g2 * rs1 + T(0.5) * g.g3 * rs2r;
       L[1] -= c1 * x - g.g1 * s1x + g.g2 * q2x;
@@ -1643,8 +1731,8 @@ __device__ void m2l_level_src(const DevArgs& A, int32_t s, int parity, int t) {
     const int32_t sB = nb[slot];
     if (sB < 0) continue;  // only without proper nesting
     interact_src<T, true, true>(L, Sm, G, N, int64_t(sB) * kCells + cidx(px & 7, py & 7, pz & 7),
-                                dAx - __ldg(td + 4 * q) * h, dAy - __ldg(td + 4 * q + 1) * h,
-                                dAz - __ldg(td + 4 * q + 2) * h);
+                                dAx - ldg_t(td + 4 * q) * h, dAy - ldg_t(td + 4 * q + 1) * h,
+                                dAz - ldg_t(td + 4 * q + 2) * h);
   }
   complete_traceless(L);
   store_src_expansion(A, iA, L, 20);
@@ -1711,8 +1799,8 @@ __device__ void m2l_boundary_src(const DevArgs& A, int chunk, int t) {
   T L[1] = {T(0)};
   for (int32_t j = A.bm_off[k]; j < A.bm_off[k + 1]; ++j) {
     const int q = __ldg(A.bm_q + j);
-    interact_src<T, false, true>(L, Sm, G, N, __ldg(A.bm_src + j), -__ldg(td + 4 * q) * h,
-                                 -__ldg(td + 4 * q + 1) * h, -__ldg(td + 4 * q + 2) * h);
+    interact_src<T, false, true>(L, Sm, G, N, __ldg(A.bm_src + j), -ldg_t(td + 4 * q) * h,
+                                 -ldg_t(td + 4 * q + 1) * h, -ldg_t(td + 4 * q + 2) * h);
   }
   for (int32_t j = A.bp_off[k]; j < A.bp_off[k + 1]; ++j) {
     const int32_t code = __ldg(A.bp_code + j);
@@ -1937,6 +2025,8 @@ struct StencilDev {
   float* d_ltab_k32 = nullptr;
   double* d_ltab_d64 = nullptr;    // [8][kLeafCap][4]
   float* d_ltab_d32 = nullptr;
+  dfloat* d_ltab_kff = nullptr;    // [8][kLeafCap][4] double-float copies
+  dfloat* d_ltab_dff = nullptr;
   int32_t* d_blocks = nullptr;     // general-kernel blocks (one parity each) for this tree, theta
   int64_t n_blocks = 0;
   // boundary pair lists (see DevArgs)
@@ -1974,6 +2064,8 @@ struct fmm_tree {
   // time-derivative solve workspace (allocated on first use)
   bool src_ready = false, src32_ready = false;
   double* d_diag_partials = nullptr;  // binary diagnostics: [blocks][kDiagVals]
+  bool df_ready = false;
+  dfloat *d_momff = nullptr, *d_massff = nullptr;
   double *d_smom = nullptr, *d_smtl = nullptr, *d_sloc = nullptr;
   float *d_smom32 = nullptr, *d_sloc32 = nullptr;
   std::map<double, StencilDev> stencils;
@@ -2038,6 +2130,8 @@ static int ensure_device(fmm_tree* t) {
                                 int(kHaloWords * sizeof(double))));
   CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(kHaloWords * sizeof(float))));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<dfloat, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(kHaloWords * sizeof(dfloat))));
   CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(kHaloWords * sizeof(double))));
   CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2132,6 +2226,16 @@ static int ensure_mixed(fmm_tree* t) {
   CUDA_TRY(dalloc(t, &t->d_root_part32, sizeof(float) * nr * kRootChunks * 20 * kCells));
   CUDA_TRY(dalloc(t, &t->d_root_part_ac, sizeof(double) * nr * kRootChunks * 3 * kCells));
   t->mixed_ready = true;
+  return FMM_OK;
+}
+
+static int ensure_df(fmm_tree* t) {
+  if (t->df_ready) return FMM_OK;
+  const int64_t nc = t->h.n_sub * kCells;
+  CUDA_TRY(dalloc(t, &t->d_momff, sizeof(dfloat) * kNMom * nc));
+  CUDA_TRY(cudaMemset(t->d_momff, 0, sizeof(dfloat) * kNMom * nc));  // leaf cells keep zeros
+  CUDA_TRY(dalloc(t, &t->d_massff, sizeof(dfloat) * nc));
+  t->df_ready = true;
   return FMM_OK;
 }
 
@@ -2365,6 +2469,7 @@ static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
     std::vector<int32_t> loff(8 * kLeafCap, 0), lcode(8 * kLeafCap, 0);
     std::vector<double> lk(8 * kLeafCap * 4, 0.0), ld(8 * kLeafCap * 4, 0.0);
     std::vector<float> lk32(8 * kLeafCap * 4, 0.0f), ld32(8 * kLeafCap * 4, 0.0f);
+    std::vector<dfloat> lkff(8 * kLeafCap * 4, dfloat(0)), ldff(8 * kLeafCap * 4, dfloat(0));
     for (int p = 0; p < 8; ++p) {
       std::vector<int32_t> all(st.offs[p]);
       all.insert(all.end(), st.near.begin(), st.near.end());
@@ -2386,6 +2491,8 @@ static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
         for (int c = 0; c < 4; ++c) {
           lk[4 * e + c] = kk[c];
           lk32[4 * e + c] = float(kk[c]);
+          lkff[4 * e + c] = dfloat(kk[c]);
+          ldff[4 * e + c] = dfloat(dd[c]);
           ld[4 * e + c] = dd[c];
           ld32[4 * e + c] = float(dd[c]);
         }
@@ -2397,6 +2504,8 @@ static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
     CUDA_TRY(upload(t, &sd.d_ltab_k32, lk32));
     CUDA_TRY(upload(t, &sd.d_ltab_d64, ld));
     CUDA_TRY(upload(t, &sd.d_ltab_d32, ld32));
+    CUDA_TRY(upload(t, &sd.d_ltab_kff, lkff));
+    CUDA_TRY(upload(t, &sd.d_ltab_dff, ldff));
     BoundaryLists bl;
     std::string err = boundary_lists(t->h, st, t->work_bnd, bl);
     if (!err.empty()) return fail(FMM_ERR_ARG, err);
@@ -2454,10 +2563,14 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.ltab_k32 = sd ? sd->d_ltab_k32 : nullptr;
   A.ltab_d64 = sd ? sd->d_ltab_d64 : nullptr;
   A.ltab_d32 = sd ? sd->d_ltab_d32 : nullptr;
+  A.ltab_kff = sd ? sd->d_ltab_kff : nullptr;
+  A.ltab_dff = sd ? sd->d_ltab_dff : nullptr;
   A.mom = t->d_mom;
   A.mtl = t->d_mtl;
   A.mom32 = t->d_mom32;
   A.m32 = t->d_m32;
+  A.momff = t->d_momff;
+  A.massff = t->d_massff;
   A.loc = t->d_loc;
   A.loc32 = t->d_loc32;
   A.ac = t->d_ac;
@@ -2527,28 +2640,29 @@ static int launch_net(fmm_tree* t, const DevArgs& A, cudaStream_t st) {
 // All launches of one solve, in order, on stream st (which may be capturing).
 static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream_t st, int32_t* nl);
 
-static int enqueue_solve(fmm_tree* t, const StencilDev* sd, bool mixed, int amc, bool net,
+static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, bool net,
                          bool src, cudaStream_t st, int32_t* launches) {
   const HostTree& h = t->h;
   DevArgs A = make_args(t, sd);
+  const bool mixed = mode == FMM_MIXED, df = mode == FMM_DF64;
   int rc;
   int32_t nl = 0;
   if ((rc = record(t, 0, st))) return rc;
   // upward pass
-  k_p2m<<<blocks_for(A.n_leaf_cells, 256), 256, 0, st>>>(A, mixed ? 1 : 0);
+  k_p2m<<<blocks_for(A.n_leaf_cells, 256), 256, 0, st>>>(A, mode);
   CUDA_TRY(cudaGetLastError());
   ++nl;
   for (int l = h.depth - 1; l >= 0; --l) {
     const int64_t nl_oct = t->oct_leaf_off[l + 1] - t->oct_leaf_off[l];
     const int64_t nr_oct = t->oct_ref_off[l + 1] - t->oct_ref_off[l];
     if (nl_oct > 0) {
-      k_m2m_walsh<<<unsigned(nl_oct), 64, 0, st>>>(A, t->d_oct_leaf + t->oct_leaf_off[l], mixed ? 1 : 0);
+      k_m2m_walsh<<<unsigned(nl_oct), 64, 0, st>>>(A, t->d_oct_leaf + t->oct_leaf_off[l], mode);
       CUDA_TRY(cudaGetLastError());
       ++nl;
     }
     if (nr_oct > 0) {
       k_m2m_lanes<<<unsigned(nr_oct * 8), kM2MThreads, 0, st>>>(A, t->d_oct_ref + t->oct_ref_off[l],
-                                                                 mixed ? 1 : 0);
+                                                                 mode);
       CUDA_TRY(cudaGetLastError());
       ++nl;
     }
@@ -2561,6 +2675,9 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, bool mixed, int amc,
     if (mixed)
       k_m2l_leaf<float, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), st>>>(
           A, t->d_work_leaf);
+    else if (df)
+      k_m2l_leaf<dfloat, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(dfloat), st>>>(
+          A, t->d_work_leaf);
     else
       k_m2l_leaf<double, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(double), st>>>(
           A, t->d_work_leaf);
@@ -2570,6 +2687,8 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, bool mixed, int amc,
   if ((rc = record(t, 5, st))) return rc;
   if (mixed)
     k_m2l_ref<float, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
+  else if (df)
+    k_m2l_ref<dfloat, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
   else
     k_m2l_ref<double, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
   CUDA_TRY(cudaGetLastError());
@@ -2653,12 +2772,12 @@ static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream
 }
 
 // Captures the launches of one solve configuration into a graph and instantiates it.
-static int capture_graph(fmm_tree* t, const StencilDev* sd, bool mixed, int amc, bool net,
+static int capture_graph(fmm_tree* t, const StencilDev* sd, int mode, int amc, bool net,
                          bool src, fmm_tree::Graph* out) {
   CUDA_TRY(cudaStreamBeginCapture(t->stream, cudaStreamCaptureModeThreadLocal));
   t->capturing = true;
   int32_t nl = 0;
-  int rc = enqueue_solve(t, sd, mixed, amc, net, src, t->stream, &nl);
+  int rc = enqueue_solve(t, sd, mode, amc, net, src, t->stream, &nl);
   t->capturing = false;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(t->stream, &g);
@@ -2681,8 +2800,11 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
                       int amc, double* net, cudaStream_t caller) {
   if (!(theta >= kThetaMin && theta < 1.0))
     return fail(FMM_ERR_THETA, "theta must lie in [0.34, 1)");
-  if (precision != FMM_FP64 && precision != FMM_MIXED) return fail(FMM_ERR_ARG, "bad precision");
+  if (precision != FMM_FP64 && precision != FMM_MIXED && precision != FMM_DF64)
+    return fail(FMM_ERR_ARG, "bad precision");
   const bool src = !io.empty() && io[0].src != nullptr;
+  if (src && precision == FMM_DF64)
+    return fail(FMM_ERR_ARG, "the time-derivative solve takes FMM_FP64 or FMM_MIXED");
   for (const TreeIo& e : io)
     if (!e.rho || !e.phi || !e.g || (src && (!e.src || !e.phidot)))
       return fail(FMM_ERR_ARG, "null device pointer");
@@ -2690,6 +2812,7 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   if (rc) return rc;
   const bool mixed = precision == FMM_MIXED;
   if (mixed && (rc = ensure_mixed(t))) return rc;
+  if (precision == FMM_DF64 && (rc = ensure_df(t))) return rc;
   if (src && (rc = ensure_src(t, mixed))) return rc;
   StencilDev* sd = nullptr;
   if ((rc = get_stencil(t, theta, &sd))) return rc;
@@ -2700,7 +2823,7 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
     auto it = t->graphs.find(key);
     if (it == t->graphs.end()) {
       fmm_tree::Graph fresh;
-      if ((rc = capture_graph(t, sd, mixed, amc, net != nullptr, src, &fresh))) return rc;
+      if ((rc = capture_graph(t, sd, precision, amc, net != nullptr, src, &fresh))) return rc;
       it = t->graphs.emplace(key, fresh).first;
     }
     gr = &it->second;
@@ -2712,7 +2835,7 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   if (gr) {
     CUDA_TRY(cudaGraphLaunch(gr->exec, t->stream));
     n_solve = gr->launches;
-  } else if ((rc = enqueue_solve(t, sd, mixed, amc, net != nullptr, src, t->stream, &n_solve))) {
+  } else if ((rc = enqueue_solve(t, sd, precision, amc, net != nullptr, src, t->stream, &n_solve))) {
     return rc;
   }
   CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));

@@ -16,6 +16,8 @@
 #pragma once
 #include <cstdint>
 
+#include "dfloat.cuh"
+
 namespace octofmm {
 
 constexpr int kNMom = 20;
@@ -53,6 +55,8 @@ template <>
 __device__ __forceinline__ double rsqrt_t<double>(double v) { return rsqrt(v); }
 template <>
 __device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
+template <>
+__device__ __forceinline__ dfloat rsqrt_t<dfloat>(dfloat v) { return df_rsqrt(v); }
 
 template <typename T>
 struct Radial {
@@ -84,7 +88,7 @@ __device__ __forceinline__ void m2l_far(T x, T y, T z, const Radial<T>& g, T m, 
   T rm2r = x * m2rx + y * m2ry + z * m2rz;
   sym3_rr(M3, x, y, z, qx, qy, qz);
   rrr = x * qx + y * qy + z * qz;
-  const T sixth = T(1) / T(6);
+  const T sixth = T(1.0 / 6.0);
   L[0] -= m * g.g0 + T(0.5) * g.g2 * rm2r - sixth * g.g3 * rrr;
   T c1 = m * g.g1 + T(0.5) * g.g3 * rm2r;
   L[1] -= c1 * x + g.g2 * m2rx;
@@ -144,7 +148,7 @@ __device__ __forceinline__ void complete_traceless(T* L) {
 template <typename T>
 __device__ __forceinline__ void amc_from(T x, T y, T z, const Radial<T>& g, T qx, T qy, T qz,
                                          T qrrr, T& ax, T& ay, T& az) {
-  const T sixth = T(1) / T(6);
+  const T sixth = T(1.0 / 6.0);
   T c4 = sixth * g.g4 * qrrr, c3 = T(0.5) * g.g3;
   ax = c4 * x + c3 * qx;
   ay = c4 * y + c3 * qy;

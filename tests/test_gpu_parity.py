@@ -227,3 +227,60 @@ def test_paper_binary_sampled(precision):
     else:
         assert np.abs(phi[idx] - ps).max() / np.abs(ps).max() <= MIXED_PHI_TOL
         assert np.abs(g[idx] - gs).max() / np.abs(g).max() <= MIXED_G_TOL
+
+
+# ---- df64: FP64 results with the pair arithmetic in double-float on the FP32 pipes; the FP64
+# path's per-cell bar at the paper's opening angles.  At theta = 0.7 the centre-of-mass series
+# diverges on these trees (terms far larger than a cell's potential cancel), which amplifies the
+# ~2^-44 operation error of double-float: there the bar is 1e-12 of the largest value.
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("theta", [0.5, 0.34, 0.7])
+def test_df64_matches_oracle_every_cell(case, theta):
+    max_level, flags, fld = CASES[case]()
+    a, b = both_trees(max_level, flags)
+    rho = synth.leaf_density(fld, b.leaves())
+    phi_o, g_o, _ = O.solve(b, rho, theta)
+    phi, g, net = gpu_solve(a, rho, theta, "df64")
+    if theta < 0.6:
+        assert rel_err(phi, phi_o) <= FP64_TOL
+        assert rel_err(g, g_o) <= FP64_TOL
+    else:
+        assert np.abs(phi - phi_o).max() <= FP64_TOL * np.abs(phi_o).max()
+        assert np.abs(g - g_o).max() <= FP64_TOL * np.abs(g_o).max()
+
+
+def test_df64_conservation_and_correction_off():
+    max_level, flags, fld = CASES["tilted_binary_L3"]()
+    a, b = both_trees(max_level, flags)
+    rho = synth.leaf_density(fld, b.leaves())
+    phi, g, net = gpu_solve(a, rho, 0.5, "df64")
+    assert np.abs(net[:3]).max() <= CONS_TOL * net[6]
+    assert np.abs(net[3:6]).max() <= CONS_TOL * net[6]
+    phi_o, g_o, _ = O.solve(b, rho, 0.5, amc=False)
+    phi, g, _ = gpu_solve(a, rho, 0.5, "df64", amc=False)
+    assert rel_err(phi, phi_o) <= FP64_TOL and rel_err(g, g_o) <= FP64_TOL
+
+
+@pytest.mark.parametrize("which", ["binary_L5", "paper_binary_L9"])
+def test_df64_full_size_sampled(which):
+    w = synth.workload_binary(5) if which == "binary_L5" else synth.workload_paper_binary()
+    a, b = both_trees(w.max_level, w.flags)
+    rho = synth.leaf_density(w.field, b.leaves())
+    phi, g, net = gpu_solve(a, rho, w.theta, "df64")
+    idx = np.random.default_rng(5).choice(rho.size, 48, replace=False)
+    lev = np.repeat(b.leaves()[:, 0], 512)
+    extra = [int(np.nonzero(lev == l)[0][len(np.nonzero(lev == l)[0]) // 2]) for l in np.unique(lev)]
+    idx = np.unique(np.concatenate([idx, extra]))
+    ps, gs = O.sample(b, rho, w.theta, idx)
+    d_phi = np.abs(phi[idx] - ps) / np.abs(ps)
+    d_g = np.linalg.norm(g[idx] - gs, axis=1) / np.maximum(np.linalg.norm(gs, axis=1),
+                                                             1e-6 * np.abs(g).max())
+    assert d_phi.max() <= FP64_TOL and d_g.max() <= FP64_TOL
+    assert np.abs(net[:6]).max() <= CONS_TOL * net[6]
+
+
+def test_df64_rejected_for_time_derivative():
+    a = api.Tree(1, synth.uniform_flags(1))
+    r = torch.ones(a.n_leaf_cells, dtype=torch.float64, device="cuda")
+    with pytest.raises(_lib.FmmError):
+        a.solve_dt(r, r, 0.5, "df64")
