@@ -217,8 +217,8 @@ __global__ void k_p2m(DevArgs A, int mixed) {
     A.mom32[cell * 20] = float(m);
     A.m32[cell] = float(m);
   } else if (mixed == 2) {
-    A.momff[cell * 20] = dfloat(m);
-    A.massff[cell] = dfloat(m);
+    A.momff[cell * 20] = df_from_double(m);
+    A.massff[cell] = df_from_double(m);
   }
 }
 
@@ -256,10 +256,10 @@ __device__ __forceinline__ void store_moments(const DevArgs& A, int64_t cell, do
   } else if (mixed == 2) {
 #pragma unroll
     for (int q = 0; q < 10; ++q) {
-      const dfloat u = dfloat(T[2 * q]), v = dfloat(T[2 * q + 1]);
+      const dfloat u = df_from_double(T[2 * q]), v = df_from_double(T[2 * q + 1]);
       reinterpret_cast<float4*>(A.momff + cell * 20)[q] = make_float4(u.hi, u.lo, v.hi, v.lo);
     }
-    A.massff[cell] = dfloat(mt);
+    A.massff[cell] = df_from_double(mt);
   }
 }
 
