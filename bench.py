@@ -61,7 +61,7 @@ def measured_traffic():
     here = os.path.dirname(os.path.abspath(__file__))
     csrc = os.path.join(here, "paper_2101_08226_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("fmm.cu", "fmm_kernels.cuh"):
+    for f in ("fmm.cu", "fmm_kernels.cuh", "dfloat.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     out, sha = {}, None
@@ -543,7 +543,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--solve-only", choices=["fp64", "mixed"], default=None,
+    ap.add_argument("--solve-only", choices=["fp64", "mixed", "df64"], default=None,
                     help="profiling driver: run warmup + steps solves of the benchmark tree, no timing")
     args = ap.parse_args()
     if args.solve_only:
