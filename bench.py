@@ -47,7 +47,20 @@ FLOPS = {"m2l_leaf_leaf": 8, "p2p_same": 8, "p2p_mixed": 26, "m2l_leaf_refined":
 # which interaction kernel evaluates which pairs
 KERNEL_PAIRS = {"k_m2l_ref": ("m2l_refined_leaf", "m2l_refined_refined", "m2l_leaf_refined",
                               "p2p_mixed"),
-                "k_m2l_leaf": ("m2l_leaf_leaf", "p2p_same")}
+                "k_m2l_leaf": ("m2l_leaf_leaf", "p2p_same"),
+                # mixed path: refined targets of levels >= 1 (the root level stays with the root
+                # and boundary blocks, so its pairs are taken off this kernel's count)
+                "k_m2l_stage": ("m2l_refined_leaf", "m2l_refined_refined")}
+def root_pairs(theta):
+    """Directed well-separated pairs among the 512 cells of a refined root: the root level's
+    share of the refined-pair count."""
+    d = np.arange(-7, 8)
+    d2 = (d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2)
+    mult = (8 - np.abs(d))[:, None, None] * (8 - np.abs(d))[None, :, None] * (8 - np.abs(d))[None, None, :]
+    ws = (1.0 / np.sqrt(np.maximum(d2, 1)) < theta) & (d2 > 0)
+    return int((mult * ws).sum())
+
+
 SMS = 152
 SM_MAX_GHZ = 2.07
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1e3    # 2 FP64 FMA / clock / SM
@@ -331,6 +344,8 @@ def run_ours(args):
     counts = tree.counts_by_type(THETA)
     n_m2l = sum(v for k, v in counts.items() if k.startswith("m2l"))
     kernel_flops = {k: sum(FLOPS[c] * counts[c] for c in cs) for k, cs in KERNEL_PAIRS.items()}
+    if depth > 0:
+        kernel_flops["k_m2l_stage"] -= FLOPS["m2l_refined_refined"] * root_pairs(THETA)
     floor = w.field.floor * w.field.rho_peak
     n_steps = args.warmup + args.steps
     rhos = [torch.from_numpy(synth.perturbed_density(rho0, replica_seed(rank, k), floor_value=floor)).to(dev)
@@ -479,13 +494,19 @@ def run_ours(args):
 
     def roofline(ph, precision):
         # the dominant interaction kernel of this precision, timed with CUDA events on the
-        # solve's stream inside the timed region
-        ms = {"k_m2l_ref": float(ph[4]), "k_m2l_leaf": float(ph[5])}
-        k = max(ms, key=ms.get)
+        # stream it runs on, inside the timed region.  FP64: the general kernel (refined and
+        # boundary targets, root) or the leaf kernel; mixed: the refined targets' kernel, which
+        # runs on the tree's second stream beside the leaf and boundary kernels
+        if precision == "mixed":
+            ms = {"k_m2l_stage": float(ph[6]), "k_m2l_leaf": float(ph[5])}
+            k = "k_m2l_stage"
+        else:
+            ms = {"k_m2l_ref": float(ph[4]), "k_m2l_leaf": float(ph[5])}
+            k = max(ms, key=ms.get)
         ach = kernel_flops[k] / (ms[k] * 1e-3) / 1e12
         peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
         unit = "FP64" if precision == "fp64" else "FP32"
-        kname = f"{k}<{'double' if precision == 'fp64' else 'float'}>"
+        kname = k if k == "k_m2l_stage" else f"{k}<{'double' if precision == 'fp64' else 'float'}>"
         return {"bound": "alu", "kernel": kname,
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": traffic.get(kname), "traffic_unit": "bytes per launch (ncu)",
@@ -494,9 +515,17 @@ def run_ours(args):
                 "peak_source": f"derived: 152 SMs x {2 if unit == 'FP64' else 128} {unit} FMA/clk "
                                "x 2 flop x 2.07 GHz"}
 
-    def phases(ph):
-        return {"upward": float(ph[0]), "interactions": float(ph[1]), "downward": float(ph[2]),
-                "reductions": float(ph[3]), "k_m2l_ref": float(ph[4]), "k_m2l_leaf": float(ph[5])}
+    def phases(ph, precision="fp64"):
+        out = {"upward": float(ph[0]), "interactions": float(ph[1]), "downward": float(ph[2]),
+               "reductions": float(ph[3])}
+        if precision == "mixed":
+            # leaf kernel, then root and boundary kernel, on the tree's stream; refined targets
+            # on the second stream at the same time
+            out.update({"k_m2l_leaf": float(ph[5]), "k_m2l_split_and_join": float(ph[4]),
+                        "k_m2l_stage": float(ph[6])})
+        else:
+            out.update({"k_m2l_ref": float(ph[4]), "k_m2l_leaf": float(ph[5])})
+        return out
     line = {
         "metric": METRIC, "value": value64, "unit": "interactions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t64 / args.steps,
@@ -517,7 +546,7 @@ def run_ours(args):
         "mixed": {"value": value32, "ms_per_step": t32 / args.steps, "dtype": "f32 pairs, f64 rest",
                   "speedup_vs_fp64": t64 / t32, "err_vs_fp64": err,
                   "roofline": roofline(ph32, "mixed"),
-                  "phases_ms": phases(ph32),
+                  "phases_ms": phases(ph32, "mixed"),
                   "ms_per_step_direct_launches": t32d / args.steps,
                   "gpu_launches": l32},
         "e2e": {"value": world * n_m2l * args.steps / e2e_s, "unit": "interactions/s",

@@ -24,7 +24,8 @@
  * Errors.  Every int-returning entry point returns FMM_OK (0) or a negative FMM_ERR_* code and
  * never aborts or throws; fmm_last_error() gives a message for the calling thread.  Solves are
  * enqueued asynchronously on `stream`; problems found on the device (a non-finite or negative
- * density) are recorded in the tree's status word and reported by fmm_sync_status().
+ * density, a timed-out wait) are recorded in the tree's status word and reported by
+ * fmm_sync_status().
  *
  * Threads.  A tree may be used by one host thread at a time.  Different trees are independent.
  */
@@ -44,6 +45,8 @@ extern "C" {
 #define FMM_ERR_NONFINITE (-6) /* a density was negative, NaN or infinite (found on the device) */
 #define FMM_ERR_NOMEM (-7)     /* host or device allocation failed */
 #define FMM_ERR_STATE (-8)     /* tree not usable (destroyed or built on another device) */
+#define FMM_ERR_TIMEOUT (-9)   /* a kernel's bounded wait for its shared-memory copies gave up
+                                  (found on the device; that block's results are missing) */
 
 #define FMM_FP64 0  /* every step in FP64 */
 #define FMM_MIXED 1 /* multipole interactions and direct sums in FP32, expansions in FP32;
@@ -153,7 +156,8 @@ int fmm_solve_batch(fmm_tree* forest, const double* const* rho_dev, double theta
                     void* stream);
 
 /* Waits for `stream`, then returns FMM_OK, or FMM_ERR_NONFINITE if a solve since the last call
- * met an invalid density, or FMM_ERR_CUDA; clears the recorded status. */
+ * met an invalid density, FMM_ERR_TIMEOUT if one of its bounded waits gave up, or FMM_ERR_CUDA;
+ * clears the recorded status. */
 int fmm_sync_status(fmm_tree* tree, void* stream);
 
 /* End-to-end solve with host buffers: copies rho_host to the device, solves, copies phi, g and
@@ -182,14 +186,24 @@ int fmm_binary_diagnostics(fmm_tree* tree, const double* rho_dev, const double* 
                            double omega, const double* x1, const double* x2, double rc1,
                            double rc2, double* out_dev, int8_t* member_dev, void* stream);
 
+/* Mixed-precision refined targets stage their partners' moments in shared memory with bulk
+ * asynchronous copies; each wait for a parity class's copies gives up after `cycles` SM clock
+ * cycles (0, the default: 2^31, about a second), records FMM_ERR_TIMEOUT in the status word and
+ * leaves that subgrid's expansions unset.  A small limit exercises this path; the solve's
+ * results are then invalid.  FMM_ERR_ARG for a negative limit. */
+int fmm_set_wait_limit(fmm_tree* tree, long long cycles);
+
 /* on != 0 (the default): replay one captured CUDA graph per solve configuration; on == 0:
  * enqueue the kernels one by one on every call.  The results are the same bit for bit. */
 int fmm_set_graphs(fmm_tree* tree, int on);
 
 /* Per-phase device times (ms) of the most recent solve on this tree, measured with CUDA events
- * on the solve's stream when profiling is on: [0] upward pass, [1] multipole interactions and
- * near field, [2] downward pass, [3] reductions, [4] the interaction kernel of refined cells
- * (with the root level), [5] the interaction kernel of leaf cells.  Writes min(n, 6) values.
+ * when profiling is on: [0] upward pass, [1] multipole interactions and near field, [2]
+ * downward pass, [3] reductions, [4] from the end of the leaf-cell interaction kernel to the
+ * end of the interaction phase (FP64 and df64: the kernel of refined cells, the root level and
+ * boundary leaves; mixed: the root and boundary kernel, then the wait for the refined cells'
+ * kernel), [5] the interaction kernel of leaf cells, [6] mixed only (else 0): the refined
+ * cells' kernel, which runs on a second stream beside [5] and [4].  Writes min(n, 7) values.
  * fmm_set_profiling(tree, 1) turns it on. */
 int fmm_set_profiling(fmm_tree* tree, int on);
 int fmm_phase_times(fmm_tree* tree, float* ms_host, int n);

@@ -216,11 +216,18 @@ class Tree:
         kernels one by one."""
         check(lib().fmm_set_graphs(self._h, int(bool(on))))
 
+    def set_wait_limit(self, cycles: int = 0):
+        """Limit, in SM clock cycles, of the staging kernel's wait for each parity class's
+        copies (0: the default, about a second); a wait that runs out is reported by the next
+        status check as FMM_ERR_TIMEOUT."""
+        check(lib().fmm_set_wait_limit(self._h, int(cycles)))
+
     def phase_times(self) -> np.ndarray:
         """ms of the last profiled solve: upward, interactions, downward, reductions, then the
-        two interaction kernels (refined targets with the root, leaf targets)."""
-        out = np.zeros(6, dtype=np.float32)
-        check(lib().fmm_phase_times(self._h, _p(out), 6))
+        end of the leaf kernel to the end of the interactions, the leaf kernel, and (mixed) the
+        refined targets' kernel on the second stream (fmm_phase_times)."""
+        out = np.zeros(7, dtype=np.float32)
+        check(lib().fmm_phase_times(self._h, _p(out), 7))
         return out
 
 

@@ -116,6 +116,11 @@ struct DevArgs {
   float* root_part32;      // [n_roots][kRootChunks][20][512] (mixed path)
   double* root_part_ac;    // [n_roots][kRootChunks][3][512] (mixed path)
   int* status;
+  // refined targets with staged partners (mixed path): per target parity, the stencil entries
+  // grouped by the parity class of their partner cell
+  const float4* stage_tab;    // [8][kLeafCap] {dx, dy, dz, lattice offset (int bits)}
+  const int32_t* stage_seg;   // [8][9] class c of parity p: entries [seg[9p + c], seg[9p + c + 1])
+  long long wait_cycles;      // limit of its first wait for each class's copies (SM clock cycles)
   // boundary pair lists (per theta): leaf target cells at a refinement boundary, sorted by work
   int64_t n_bt;
   const int32_t* bt_cell;  // [n_bt] internal cell index of each target
@@ -621,10 +626,7 @@ __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict
 // M3'(R,R) uses the tracelessness of the stored M3' (T_xzz = -T_xxx - T_xyy, ...) on the shared
 // monomials xx - zz, yy - zz, 2xy, 2xz, 2yz; the correction's Q(R,R,R) is contracted directly.
 template <typename T>
-__device__ __forceinline__ void interact_rr(Target<T, true>& S, const T* __restrict__ M, int64_t N,
-                                            int64_t iB, T x, T y, T z) {
-  T Mv[20];
-  mom_load20(M, N, iB, Mv);
+__device__ __forceinline__ void interact_rr_v(Target<T, true>& S, const T* Mv, T x, T y, T z) {
   const T mB = Mv[0];
   x -= Mv[1];
   y -= Mv[2];
@@ -692,6 +694,14 @@ __device__ __forceinline__ void interact_rr(Target<T, true>& S, const T* __restr
     S.py = fma(k3, Qy, fma(c4, y, S.py));
     S.pz = fma(k3, Qz, fma(c4, z, S.pz));
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void interact_rr(Target<T, true>& S, const T* __restrict__ M, int64_t N,
+                                            int64_t iB, T x, T y, T z) {
+  T Mv[20];
+  mom_load20(M, N, iB, Mv);
+  interact_rr_v<T>(S, Mv, x, y, z);
 }
 
 // A leaf target (a point mass at its centre: only L0, L1; no M3 of its own, so the correction
@@ -929,8 +939,26 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool a
 // Root level: every well-separated pair inside the single root subgrid (no parent criterion);
 // when the root is a leaf, every other root cell interacts directly.  Sources are split into
 // kRootChunks chunks whose partial sums are added in a fixed order by the downward pass.
-template <typename T, bool AREF>
-__device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chunk, bool amc) {
+// Sums a target's partial state over the LANES consecutive lanes that share it (LANES = 1, 2, 4
+// or 8); every lane of the warp calls it.  The correction partials must have been flushed.
+template <int LANES, typename T, bool AREF>
+__device__ __forceinline__ void lane_reduce(Target<T, AREF>& S) {
+#pragma unroll
+  for (int m = 1; m < LANES; m <<= 1) {
+#pragma unroll
+    for (int k = 0; k < (AREF ? 20 : 4); ++k) S.L[k] += __shfl_xor_sync(0xffffffffu, S.L[k], m);
+    S.ax += __shfl_xor_sync(0xffffffffu, S.ax, m);
+    S.ay += __shfl_xor_sync(0xffffffffu, S.ay, m);
+    S.az += __shfl_xor_sync(0xffffffffu, S.az, m);
+  }
+}
+
+// LANES lanes per target: lane r takes the source rows jy in [r 8 / LANES, (r + 1) 8 / LANES),
+// and lane 0 stores the sum.
+template <typename T, bool AREF, int LANES = 1>
+__device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chunk, bool amc,
+                         int r = 0) {
+  static_assert(LANES == 1 || LANES == 2 || LANES == 4 || LANES == 8, "LANES divides 8");
   const T* __restrict__ M = MomView<T>::get(A);
   const int64_t N = A.n_cell;
   int a, b, c;
@@ -944,8 +972,11 @@ __device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chun
   // chunk = source x index; source offsets kept as floating-point counters (no conversions)
   const int dx = chunk - a;
   const T rx0 = S.dAx - T(dx) * h;
-  T ry = S.dAy + T(b) * h, rz0 = S.dAz + T(c) * h;  // X_A - x_B for a source at y = z = 0
-  for (int jy = 0; jy < 8; ++jy, ry -= h) {
+  constexpr int kRows = 8 / LANES;
+  const int jy0 = r * kRows;
+  // X_A - x_B for a source at y = jy0, z = 0
+  T ry = S.dAy + T(b - jy0) * h, rz0 = S.dAz + T(c) * h;
+  for (int jy = jy0; jy < jy0 + kRows; ++jy, ry -= h) {
     T rz = rz0;
     for (int jz = 0; jz < 8; ++jz, rz -= h) {
       const int j = cidx(chunk, jy, jz);
@@ -958,6 +989,10 @@ __device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chun
     if (jy & 1) flush(S);
   }
   flush(S);
+  if constexpr (LANES > 1) {
+    lane_reduce<LANES>(S);
+    if (r != 0) return;
+  }
   // partials: [chunk][component][cell]
   if constexpr (AREF) complete_traceless(S.L);
   if (sizeof(T) == 8) {
@@ -985,14 +1020,17 @@ __device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chun
 // length and no lane scans entries that do not apply to it.  Adds onto the leaf kernel's output.
 constexpr int kCodeMax = 64;  // |point-pair offset| in units of dx / 4
 
-template <typename T>
-__device__ void m2l_boundary(const DevArgs& A, int chunk, int t, bool amc) {
+// LANES lanes per target: lane r takes the list entries r, r + LANES, ..., and lane 0 stores
+// the sum (every lane of the block calls this, also past the last target).
+template <typename T, int LANES = 1>
+__device__ void m2l_boundary(const DevArgs& A, int chunk, int t, bool amc, int r = 0) {
   __shared__ T quarter[2 * kCodeMax + 1];  // quarter[i] = (i - kCodeMax) / 4, exact
   for (int i = threadIdx.x; i <= 2 * kCodeMax; i += blockDim.x) quarter[i] = T(i - kCodeMax) * T(0.25);
   __syncthreads();
   const int64_t k = int64_t(chunk) * 64 + t;
-  if (k >= A.n_bt) return;
-  const int64_t iA = A.bt_cell[k];
+  const bool valid = k < A.n_bt;
+  if (LANES == 1 && !valid) return;
+  const int64_t iA = valid ? A.bt_cell[k] : 0;
   const int parity = int(iA & 511) >> 6;
   const T* __restrict__ M = MomView<T>::get(A);
   const int64_t N = A.n_cell;
@@ -1000,23 +1038,27 @@ __device__ void m2l_boundary(const DevArgs& A, int chunk, int t, bool amc) {
   load_target<T, false>(S, A, M, iA, amc);
   const T h = cell_h<T>(A.level[iA >> 9]);
   const T* __restrict__ td = LeafOffsets<T>::get(A) + int64_t(parity) * kLeafCap * 4;
-  const int32_t m1 = A.bm_off[k + 1];
-  for (int32_t j0 = A.bm_off[k]; j0 < m1; j0 += kFlush) {
-    const int32_t j1 = min(j0 + kFlush, m1);
-    for (int32_t j = j0; j < j1; ++j) {
+  const int32_t m1 = valid ? A.bm_off[k + 1] : 0;
+  for (int32_t j0 = (valid ? A.bm_off[k] : 0) + r; j0 < m1; j0 += LANES * kFlush) {
+    const int32_t j1 = min(j0 + LANES * kFlush, m1);
+    for (int32_t j = j0; j < j1; j += LANES) {
       const int q = __ldg(A.bm_q + j);
       interact_lr<T>(S, M, N, __ldg(A.bm_src + j), -ldg_t(td + 4 * q) * h,
                      -ldg_t(td + 4 * q + 1) * h, -ldg_t(td + 4 * q + 2) * h);
     }
     flush(S);
   }
-  const int32_t p1 = A.bp_off[k + 1];
-  for (int32_t j = A.bp_off[k]; j < p1; ++j) {
+  const int32_t p1 = valid ? A.bp_off[k + 1] : 0;
+  for (int32_t j = (valid ? A.bp_off[k] : 0) + r; j < p1; j += LANES) {
     const int32_t code = __ldg(A.bp_code + j);
     const T x = quarter[((code >> 20) & 1023) - 512 + kCodeMax] * h;
     const T y = quarter[((code >> 10) & 1023) - 512 + kCodeMax] * h;
     const T z = quarter[(code & 1023) - 512 + kCodeMax] * h;
     interact_point<T, false>(S, mom_get(M, N, __ldg(A.bp_src + j), 0), x, y, z);
+  }
+  if constexpr (LANES > 1) {
+    lane_reduce<LANES>(S);  // the correction partials were flushed after the multipole pairs
+    if (r != 0 || !valid) return;
   }
   if (sizeof(T) == 8) {
     for (int c = 0; c < 4; ++c) A.loc[c * N + iA] += double(S.L[c]);
@@ -1049,6 +1091,199 @@ __global__ void __launch_bounds__(NT) k_m2l_ref(DevArgs A, const int32_t* __rest
   } else {
     m2l_boundary<T>(A, idx, t, amc != 0);
   }
+}
+
+// The root and boundary blocks of k_m2l_ref (kinds 0 and 2) with 4 lanes per target: these
+// threads run long serial lists of partners read from L2, so the list is split four ways and
+// the partial sums added with warp shuffles.  Used by the mixed path, where refined subgrids
+// go to k_m2l_stage.
+constexpr int kSplitLanes = 4;
+template <typename T>
+__global__ void __launch_bounds__(64 * kSplitLanes) k_m2l_split(DevArgs A, const int32_t* __restrict__ blocks,
+                                                                 int amc) {
+  const int32_t code = blocks[blockIdx.x];
+  const int kind = (code >> 30) & 3, idx = code & ((1 << 27) - 1);
+  const int parity = (code >> 27) & 7;
+  const int t = int(threadIdx.x) / kSplitLanes, r = int(threadIdx.x) % kSplitLanes;
+  if (kind == 0) {
+    const int root = idx >> 3, chunk = idx & 7;
+    if (A.leaf[root]) m2l_root<T, false, kSplitLanes>(A, root, parity, t, chunk, amc != 0, r);
+    else m2l_root<T, true, kSplitLanes>(A, root, parity, t, chunk, amc != 0, r);
+  } else if (kind == 2) {
+    m2l_boundary<T, kSplitLanes>(A, idx, t, amc != 0, r);
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
+// Refined targets with their partners' moments staged in shared memory (mixed path)
+// ----------------------------------------------------------------------------------------------
+// A refined subgrid's 512 targets read the FP32 moments of the 18^3 cells of the subgrid and its
+// 5-cell rim, each about 20 times.  The block stages them one parity class at a time (a 9^3
+// lattice of 80-byte cells, 57 KB) with bulk asynchronous copies (TMA, cp.async.bulk) completing
+// on an mbarrier, double-buffered so that class c + 1 arrives while class c is evaluated, and
+// every target then walks the stencil entries whose partner lies in class c.
+//
+// Halo cell (x, y, z) in [-5, 12]^3, h = x + 5: class ((hx & 1) << 2 | (hy & 1) << 1 | (hz & 1)),
+// lattice cell (hx >> 1, hy >> 1, hz >> 1) at lattice strides (kStageSX, kStageSY, 1) cells.
+// A warp holds the 32 targets (ia, ib, ic) = (2 half + (lane >> 2 & 1), lane >> 3, lane & 3) of
+// one parity, so the 8 lanes of each quarter warp (ic = 0..3, ia even and odd) read 16-byte
+// words at 5 (ic + kStageSX ia) mod 8 = {0, 5, 2, 7} + {0, 4}: 8 distinct bank groups.
+constexpr int kStageThreads = 512;
+constexpr int kStageSY = 9;
+constexpr int kStageSX = 84;  // = 4 (mod 8), see above; 84 >= 9 * 9
+constexpr int kStageCells = 8 * kStageSX + 8 * kStageSY + 9;
+constexpr int kStageBufBytes = kStageCells * 80;
+constexpr int kStageSmem = 2 * kStageBufBytes;
+constexpr int kStageRuns = 243;  // per class: 9 x 9 lattice columns, each 3 runs along z
+constexpr long long kStageWaitCycles = 1ll << 31;  // about a second: then report and give up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return uint32_t(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// (the arrive operations return the barrier state, which the callers do not need)
+__device__ __forceinline__ uint64_t mbar_arrive(uint64_t* bar) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(bar)) : "memory");
+  return state;
+}
+__device__ __forceinline__ uint64_t mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  uint64_t state;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+               : "=l"(state)
+               : "r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  return state;
+}
+// Non-blocking test of the phase of the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Waits for the phase of the given parity to complete, for at most `limit` SM clock cycles;
+// false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_test_wait(bar, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+// Global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16), completing
+// `bytes` transactions on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(uint64_t(__cvta_generic_to_global(src))), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Thread j < kStageRuns copies run j of class c into buf: lattice column (lx, ly) = (j / 27,
+// j / 3 % 9), z run j % 3 (halo z < 0, 0 <= z < 8, z >= 8), from the neighbour subgrid that
+// holds it; an absent neighbour (only without proper nesting) gives zeros.
+__device__ __forceinline__ void stage_issue(const DevArgs& A, const int32_t* nb, int c, float* buf,
+                                            uint64_t* bar, int j) {
+  if (j >= kStageRuns) return;
+  const int rx = (c >> 2) & 1, ry = (c >> 1) & 1, rz = c & 1;
+  const int lx = j / 27, ly = (j / 3) % 9, run = j % 3;
+  const int x = 2 * lx + rx - 5, y = 2 * ly + ry - 5;
+  // lattice z range of the run: z = 2 lz + rz - 5 in [-5, 0), [0, 8), [8, 13)
+  const int z1 = rz ? 2 : 3, z2 = rz ? 6 : 7;
+  const int lz0 = run == 0 ? 0 : (run == 1 ? z1 : z2);
+  const int lz1 = run == 0 ? z1 : (run == 1 ? z2 : 9);
+  const int z = 2 * lz0 + rz - 5;
+  const int32_t sB = nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)];
+  float* dst = buf + (lx * kStageSX + ly * kStageSY + lz0) * 20;
+  const uint32_t bytes = uint32_t(lz1 - lz0) * 80u;
+  if (sB >= 0) {
+    // the run's cells are consecutive in the neighbour's parity-major order (cidx)
+    const int64_t row = int64_t(sB) * kCells + cidx(x & 7, y & 7, z & 7);
+    mbar_arrive_tx(bar, bytes);
+    bulk_g2s(dst, A.mom32 + row * 20, bytes, bar);
+  } else {
+    for (int k = 0; k < int(bytes / 4); ++k) dst[k] = 0.0f;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive(bar);
+  }
+}
+
+// One block per refined subgrid of a level >= 1 (the list `subs`): the same pairs and
+// correction as m2l_level<float>, with the partners read from shared memory.
+__global__ void __launch_bounds__(kStageThreads, 1) k_m2l_stage(DevArgs A, const int32_t* __restrict__ subs,
+                                                                 int amc) {
+  extern __shared__ __align__(128) unsigned char stage_smem[];
+  float* buf0 = reinterpret_cast<float*>(stage_smem);
+  float* buf1 = reinterpret_cast<float*>(stage_smem + kStageBufBytes);
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int32_t nb[27];
+  const int32_t s = subs[blockIdx.x];
+  const int t = threadIdx.x;
+  if (t < 27) nb[t] = A.nbr[27 * s + t];
+  if (t == 0) {
+    mbar_init(&bar[0], kStageRuns);
+    mbar_init(&bar[1], kStageRuns);
+    mbar_fence_init();
+  }
+  const int w = t >> 5, lane = t & 31;
+  const int parity = w >> 1;
+  const int ia = ((w & 1) << 1) | ((lane >> 2) & 1), ib = lane >> 3, ic = lane & 3;
+  const int a = 2 * ia + ((parity >> 2) & 1), b = 2 * ib + ((parity >> 1) & 1), c = 2 * ic + (parity & 1);
+  const int64_t iA = int64_t(s) * kCells + cidx(a, b, c);
+  Target<float, true> S;
+  load_target<float, true>(S, A, A.mom32, iA, amc != 0);
+  const float h = cell_h<float>(A.level[s]);
+  const int base = (ia * kStageSX + ib * kStageSY + ic) * 20;
+  const float4* __restrict__ tab = A.stage_tab + parity * kLeafCap;
+  const int32_t* __restrict__ seg = A.stage_seg + parity * 9;
+  __syncthreads();
+  stage_issue(A, nb, 0, buf0, &bar[0], t);
+  for (int cl = 0; cl < 8; ++cl) {
+    const bool ok = mbar_wait_bounded(&bar[cl & 1], uint32_t((cl >> 1) & 1), A.wait_cycles);
+    // block-uniform decision; also makes the zero fills of class cl visible and frees the other
+    // buffer (every thread has finished class cl - 1)
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) atomicOr(A.status, 4);
+      // the copies in flight are class cl's (class cl + 1 is issued after this wait): give them
+      // time to land before the block's shared memory is released
+      mbar_wait_bounded(&bar[cl & 1], uint32_t((cl >> 1) & 1), kStageWaitCycles);
+      return;
+    }
+    if (cl < 7) stage_issue(A, nb, cl + 1, (cl & 1) ? buf0 : buf1, &bar[(cl + 1) & 1], t);
+    const float* __restrict__ B = ((cl & 1) ? buf1 : buf0) + base;
+    const int q1 = __ldg(seg + cl + 1);
+    for (int q0 = __ldg(seg + cl); q0 < q1; q0 += kFlush) {
+      const int qe = min(q0 + kFlush, q1);
+      for (int q = q0; q < qe; ++q) {
+        const float4 e = __ldg(tab + q);
+        const float4* m = reinterpret_cast<const float4*>(B + __float_as_int(e.w) * 20);
+        float Mv[20];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          const float4 v = m[k];
+          Mv[4 * k] = v.x;
+          Mv[4 * k + 1] = v.y;
+          Mv[4 * k + 2] = v.z;
+          Mv[4 * k + 3] = v.w;
+        }
+        interact_rr_v<float>(S, Mv, fmaf(-e.x, h, S.dAx), fmaf(-e.y, h, S.dAy), fmaf(-e.z, h, S.dAz));
+      }
+      flush(S);
+    }
+  }
+  finish_rr(S);
+  store_own<float, true>(A, S, iA);
 }
 
 // Four consecutive table values (16-byte aligned) in vector loads.
@@ -1275,54 +1510,48 @@ __device__ __forceinline__ void store_leaf_dt(const DevArgs& A, int32_t s, int a
 }
 
 // Level 0: each root cell's expansion is the fixed-order sum of its kRootChunks partial sums.
-// A refined root keeps it as its total; a leaf root is evaluated (phi = L0, g = -L1 + a_c).
+// A refined root keeps it as its total, one thread per (root, component, cell) -- 20 expansion
+// and 3 correction components; a leaf root is evaluated by the component-0 thread of each cell
+// (phi = L0, g = -L1 + a_c).
+constexpr int kRootComps = 23;
 template <bool MIXED, bool SRC>
 __global__ void k_root_total(DevArgs A) {
   using T = typename Down<MIXED>::T;
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= int64_t(A.n_roots) * kCells) return;
-  const int32_t s = int32_t(t >> 9);  // roots are subgrids 0 .. n_roots - 1
+  if (t >= int64_t(A.n_roots) * kRootComps * kCells) return;
   const int loc = int(t & 511);
+  const int comp = int((t >> 9) % kRootComps);
+  const int32_t s = int32_t((t >> 9) / kRootComps);  // roots are subgrids 0 .. n_roots - 1
   const int64_t i = int64_t(s) * kCells + loc;
-  const bool isleaf = A.leaf[s] != 0;
-  const int nL = isleaf ? 4 : 20;
-  double L[20], ax = 0.0, ay = 0.0, az = 0.0;
-  for (int k = 0; k < 20; ++k) L[k] = 0.0;
-  for (int ch = 0; ch < kRootChunks; ++ch) {
+  // partial sum of component k (0..22) of chunk ch
+  auto part = [&](int ch, int k) -> double {
     const int64_t pc = int64_t(s) * kRootChunks + ch;
-    if (!MIXED) {
-      const double* P = A.root_part + pc * 23 * kCells;
-      for (int k = 0; k < nL; ++k) L[k] += P[k * kCells + loc];
+    if (!MIXED) return A.root_part[(pc * 23 + k) * kCells + loc];
+    if (k < 20) return double(A.root_part32[(pc * 20 + k) * kCells + loc]);
+    return A.root_part_ac[(pc * 3 + (k - 20)) * kCells + loc];
+  };
+  if (A.leaf[s]) {
+    if (comp != 0) return;
+    double L[4] = {0.0, 0.0, 0.0, 0.0}, ax = 0.0, ay = 0.0, az = 0.0;
+    for (int ch = 0; ch < kRootChunks; ++ch) {
+      for (int k = 0; k < 4; ++k) L[k] += part(ch, k);
       if (!SRC) {
-        ax += P[20 * kCells + loc];
-        ay += P[21 * kCells + loc];
-        az += P[22 * kCells + loc];
-      }
-    } else {
-      const float* P = A.root_part32 + pc * 20 * kCells;
-      for (int k = 0; k < nL; ++k) L[k] += double(P[k * kCells + loc]);
-      if (!SRC) {
-        const double* Q = A.root_part_ac + pc * 3 * kCells;
-        ax += Q[loc];
-        ay += Q[kCells + loc];
-        az += Q[2 * kCells + loc];
+        ax += part(ch, 20);
+        ay += part(ch, 21);
+        az += part(ch, 22);
       }
     }
-  }
-  if (isleaf) {
     int a, b, c;
     cdecode(loc, a, b, c);
     if (SRC) store_leaf_dt(A, s, a, b, c, L[0]);
     else store_leaf(A, s, a, b, c, L[0], -L[1] + ax, -L[2] + ay, -L[3] + az);
     return;
   }
-#pragma unroll
-  for (int k = 0; k < 20; ++k) Down<MIXED, SRC>::st(A, k, i, T(L[k]));
-  if (SRC) return;
-  const int64_t N = A.n_cell;
-  A.ac[i] = ax;
-  A.ac[N + i] = ay;
-  A.ac[2 * N + i] = az;
+  if (SRC && comp >= 20) return;
+  double v = 0.0;
+  for (int ch = 0; ch < kRootChunks; ++ch) v += part(ch, comp);
+  if (comp < 20) Down<MIXED, SRC>::st(A, comp, i, T(v));
+  else A.ac[(comp - 20) * A.n_cell + i] = v;
 }
 
 // Levels >= 1, one launch per level, 64 threads per block.  Blocks [0, n_ref_blocks): 8 per
@@ -2029,6 +2258,10 @@ struct StencilDev {
   dfloat* d_ltab_dff = nullptr;
   int32_t* d_blocks = nullptr;     // general-kernel blocks (one parity each) for this tree, theta
   int64_t n_blocks = 0;
+  int32_t* d_blocks_nr = nullptr;  // the same without the refined subgrids (mixed path: k_m2l_stage)
+  int64_t n_blocks_nr = 0;
+  float* d_stage_tab = nullptr;    // [8][kLeafCap][4] (DevArgs::stage_tab)
+  int32_t* d_stage_seg = nullptr;  // [8][9]
   // boundary pair lists (see DevArgs)
   int64_t n_bt = 0;
   int32_t *d_bt_cell = nullptr, *d_bm_off = nullptr, *d_bm_src = nullptr, *d_bm_q = nullptr,
@@ -2070,8 +2303,12 @@ struct fmm_tree {
   float *d_smom32 = nullptr, *d_sloc32 = nullptr;
   std::map<double, StencilDev> stencils;
   bool profiling = false;
-  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // mixed path: k_m2l_stage runs on stream2, forked from and joined back to the tree's stream
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool ev_recorded = false;
+  bool ev_stage = false;  // the recorded solve ran k_m2l_stage between ev[6] and ev[7]
   int32_t launches = 0;
   std::vector<void*> allocs;
   std::vector<int32_t> work, work_bnd;  // refined and boundary leaf subgrids of levels >= 1
@@ -2083,13 +2320,14 @@ struct fmm_tree {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   bool use_graphs = true;
+  long long wait_cycles = 0;  // first-wait limit of the staging kernel (0: kStageWaitCycles)
   bool capturing = false;
   struct Graph {
     cudaGraphExec_t exec = nullptr;
     int32_t launches = 0;
   };
   // one instantiated graph per (theta, precision, correction, net output, profiling, dphi/dt)
-  std::map<std::tuple<double, int, int, int, int, int>, Graph> graphs;
+  std::map<std::tuple<double, int, int, int, int, int, long long>, Graph> graphs;
 };
 
 // blocks per tree of the net reduction: about 512 in all
@@ -2208,6 +2446,9 @@ static int ensure_device(fmm_tree* t) {
   CUDA_TRY(dalloc(t, &t->d_io, sizeof(TreeIo) * size_t(nr)));
   CUDA_TRY(dalloc(t, &t->d_io_net, sizeof(double*)));
   CUDA_TRY(cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking));
+  CUDA_TRY(cudaStreamCreateWithFlags(&t->stream2, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&t->ev_in, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&t->ev_out, cudaEventDisableTiming));
   for (auto& e : t->ev) CUDA_TRY(cudaEventCreate(&e));
@@ -2225,6 +2466,7 @@ static int ensure_mixed(fmm_tree* t) {
   const int64_t nr = t->h.n_trees;
   CUDA_TRY(dalloc(t, &t->d_root_part32, sizeof(float) * nr * kRootChunks * 20 * kCells));
   CUDA_TRY(dalloc(t, &t->d_root_part_ac, sizeof(double) * nr * kRootChunks * 3 * kCells));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageSmem));
   t->mixed_ready = true;
   return FMM_OK;
 }
@@ -2520,6 +2762,38 @@ static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
     std::vector<int32_t> blocks = general_blocks(t->h, st, t->work, bl, false);
     sd.n_blocks = int64_t(blocks.size());
     CUDA_TRY(upload(t, &sd.d_blocks, blocks));
+    std::vector<int32_t> blocks_nr = general_blocks(t->h, st, {}, bl, false);
+    sd.n_blocks_nr = int64_t(blocks_nr.size());
+    CUDA_TRY(upload(t, &sd.d_blocks_nr, blocks_nr));
+    // staged refined targets: per parity, the stencil entries grouped by partner class, with
+    // the partner's lattice offset from a target at lattice cell (0, 0, 0) of that parity
+    std::vector<float> stab(8 * kLeafCap * 4, 0.0f);
+    std::vector<int32_t> sseg(8 * 9, 0);
+    for (int p = 0; p < 8; ++p) {
+      const int px = (p >> 2) & 1, py = (p >> 1) & 1, pz = p & 1;
+      int e = 0;
+      for (int cl = 0; cl < 8; ++cl) {
+        sseg[9 * p + cl] = e;
+        for (int32_t code : st.offs[p]) {
+          int dx, dy, dz;
+          unpack_offset(code, dx, dy, dz);
+          const int hx = px + dx + 5, hy = py + dy + 5, hz = pz + dz + 5;
+          if (hx < 0 || hy < 0 || hz < 0 || hx > 11 || hy > 11 || hz > 11)
+            return fail(FMM_ERR_THETA, "stencil reaches beyond the 5-cell rim");
+          if (((hx & 1) << 2 | (hy & 1) << 1 | (hz & 1)) != cl) continue;
+          const int32_t off = (hx >> 1) * kStageSX + (hy >> 1) * kStageSY + (hz >> 1);
+          float* f = &stab[(size_t(p) * kLeafCap + e) * 4];
+          f[0] = float(dx);
+          f[1] = float(dy);
+          f[2] = float(dz);
+          std::memcpy(&f[3], &off, sizeof(off));
+          ++e;
+        }
+      }
+      sseg[9 * p + 8] = e;
+    }
+    CUDA_TRY(upload(t, &sd.d_stage_tab, stab));
+    CUDA_TRY(upload(t, &sd.d_stage_seg, sseg));
 
     sd.n_stencil = n;
     sd.n_near = int(st.near.size());
@@ -2578,6 +2852,9 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.root_part32 = t->d_root_part32;
   A.root_part_ac = t->d_root_part_ac;
   A.status = t->d_status;
+  A.stage_tab = sd ? reinterpret_cast<const float4*>(sd->d_stage_tab) : nullptr;
+  A.stage_seg = sd ? sd->d_stage_seg : nullptr;
+  A.wait_cycles = t->wait_cycles > 0 ? t->wait_cycles : kStageWaitCycles;
   A.smom = t->d_smom;
   A.smtl = t->d_smtl;
   A.smom32 = t->d_smom32;
@@ -2670,7 +2947,20 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
 
   if ((rc = record(t, 1, st))) return rc;
   // interactions: leaf subgrids of levels >= 1 (same-level leaf partners), then the general
-  // kernel: root chunks, every (refined subgrid, parity) and every (boundary leaf subgrid, parity)
+  // kernel: root chunks, every (refined subgrid, parity) and every (boundary leaf subgrid, parity).
+  // Mixed path: the refined subgrids go to k_m2l_stage on a second stream, beside the leaf and
+  // general kernels (one block per SM, it leaves room for theirs).
+  const bool fork = mixed && !t->work.empty();
+  if (fork) {
+    CUDA_TRY(cudaEventRecord(t->ev_fork, st));
+    CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_fork, 0));
+    if ((rc = record(t, 6, t->stream2))) return rc;
+    k_m2l_stage<<<unsigned(t->work.size()), kStageThreads, kStageSmem, t->stream2>>>(A, t->d_work, amc);
+    CUDA_TRY(cudaGetLastError());
+    ++nl;
+    if ((rc = record(t, 7, t->stream2))) return rc;
+    CUDA_TRY(cudaEventRecord(t->ev_join, t->stream2));
+  }
   if (t->n_work_leaf > 0) {
     if (mixed)
       k_m2l_leaf<float, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), st>>>(
@@ -2685,18 +2975,26 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
     ++nl;
   }
   if ((rc = record(t, 5, st))) return rc;
-  if (mixed)
-    k_m2l_ref<float, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
-  else if (df)
-    k_m2l_ref<dfloat, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
-  else
-    k_m2l_ref<double, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
-  CUDA_TRY(cudaGetLastError());
-  ++nl;
+  if (mixed) {
+    // root and boundary blocks here, refined subgrids with staged partners below
+    if (sd->n_blocks_nr > 0) {
+      k_m2l_split<float><<<unsigned(sd->n_blocks_nr), 64 * kSplitLanes, 0, st>>>(A, sd->d_blocks_nr, amc);
+      CUDA_TRY(cudaGetLastError());
+      ++nl;
+    }
+    if (fork) CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
+  } else {
+    if (df)
+      k_m2l_ref<dfloat, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
+    else
+      k_m2l_ref<double, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
+    CUDA_TRY(cudaGetLastError());
+    ++nl;
+  }
   if ((rc = record(t, 2, st))) return rc;
   // downward pass: the roots, then per level the refined cells' totals and the leaf cells
-  if (mixed) k_root_total<true, false><<<blocks_for(int64_t(h.n_trees) * kCells, 128), 128, 0, st>>>(A);
-  else k_root_total<false, false><<<blocks_for(int64_t(h.n_trees) * kCells, 128), 128, 0, st>>>(A);
+  if (mixed) k_root_total<true, false><<<blocks_for(int64_t(h.n_trees) * kRootComps * kCells, 128), 128, 0, st>>>(A);
+  else k_root_total<false, false><<<blocks_for(int64_t(h.n_trees) * kRootComps * kCells, 128), 128, 0, st>>>(A);
   CUDA_TRY(cudaGetLastError());
   ++nl;
   for (int l = 1; l <= h.depth; ++l) {
@@ -2753,8 +3051,8 @@ static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream
   else k_m2l_ref_src<double, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks);
   CUDA_TRY(cudaGetLastError());
   ++*nl;
-  if (mixed) k_root_total<true, true><<<blocks_for(int64_t(h.n_trees) * kCells, 128), 128, 0, st>>>(A);
-  else k_root_total<false, true><<<blocks_for(int64_t(h.n_trees) * kCells, 128), 128, 0, st>>>(A);
+  if (mixed) k_root_total<true, true><<<blocks_for(int64_t(h.n_trees) * kRootComps * kCells, 128), 128, 0, st>>>(A);
+  else k_root_total<false, true><<<blocks_for(int64_t(h.n_trees) * kRootComps * kCells, 128), 128, 0, st>>>(A);
   CUDA_TRY(cudaGetLastError());
   ++*nl;
   for (int l = 1; l <= h.depth; ++l) {
@@ -2819,7 +3117,8 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   amc = amc ? 1 : 0;
   fmm_tree::Graph* gr = nullptr;
   if (t->use_graphs) {
-    auto key = std::make_tuple(theta, precision, amc, net ? 1 : 0, t->profiling ? 1 : 0, src ? 1 : 0);
+    auto key = std::make_tuple(theta, precision, amc, net ? 1 : 0, t->profiling ? 1 : 0, src ? 1 : 0,
+                               t->wait_cycles);
     auto it = t->graphs.find(key);
     if (it == t->graphs.end()) {
       fmm_tree::Graph fresh;
@@ -2841,6 +3140,7 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
   CUDA_TRY(cudaStreamWaitEvent(caller, t->ev_out, 0));
   t->ev_recorded = t->profiling;
+  t->ev_stage = t->profiling && mixed && !t->work.empty();
   t->launches = n_io + n_solve;
   return FMM_OK;
 }
@@ -2948,6 +3248,12 @@ void fmm_destroy(fmm_tree* t) {
     cudaStreamSynchronize(t->stream);
     cudaStreamDestroy(t->stream);
   }
+  if (t->stream2) {
+    cudaStreamSynchronize(t->stream2);
+    cudaStreamDestroy(t->stream2);
+  }
+  if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+  if (t->ev_join) cudaEventDestroy(t->ev_join);
   for (void* p : t->allocs) cudaFree(p);
   for (auto& e : t->ev)
     if (e) cudaEventDestroy(e);
@@ -3098,6 +3404,7 @@ int fmm_sync_status(fmm_tree* t, void* stream) {
   CUDA_TRY(cudaMemset(t->d_status, 0, sizeof(int)));
   if (status & 1) return fail(FMM_ERR_NONFINITE, "a density was negative, NaN or infinite");
   if (status & 2) return fail(FMM_ERR_NONFINITE, "a density time derivative was NaN or infinite");
+  if (status & 4) return fail(FMM_ERR_TIMEOUT, "a shared-memory staging wait timed out");
   return FMM_OK;
 }
 
@@ -3187,6 +3494,12 @@ int fmm_binary_diagnostics(fmm_tree* t, const double* rho_dev, const double* g_d
   }
 }
 
+int fmm_set_wait_limit(fmm_tree* t, long long cycles) {
+  if (!t || cycles < 0) return fail(FMM_ERR_ARG, "tree is null or limit negative");
+  t->wait_cycles = cycles;
+  return FMM_OK;
+}
+
 int fmm_set_graphs(fmm_tree* t, int on) {
   if (!t) return fail(FMM_ERR_ARG, "tree is null");
   t->use_graphs = on != 0;
@@ -3208,6 +3521,11 @@ int fmm_phase_times(fmm_tree* t, float* ms, int n) {
   // [4] general interaction kernel (root, refined targets, boundary leaves), [5] leaf kernel
   if (n > 4) CUDA_TRY(cudaEventElapsedTime(&ms[4], t->ev[5], t->ev[2]));
   if (n > 5) CUDA_TRY(cudaEventElapsedTime(&ms[5], t->ev[1], t->ev[5]));
+  // [6] the staged refined-target kernel of a mixed solve (0 for the other precisions)
+  if (n > 6) {
+    ms[6] = 0.0f;
+    if (t->ev_stage) CUDA_TRY(cudaEventElapsedTime(&ms[6], t->ev[6], t->ev[7]));
+  }
   return FMM_OK;
 }
 

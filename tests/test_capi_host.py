@@ -126,6 +126,9 @@ def test_argument_errors():
     assert _lib.lib().fmm_solve(t._h, C.c_void_p(16), 0.2, 0, 1, C.c_void_p(16), C.c_void_p(16),
                                 None, None) == _lib.FMM_ERR_THETA
     assert b"theta" in _lib.lib().fmm_last_error()
+    assert _lib.lib().fmm_set_wait_limit(None, 0) == _lib.FMM_ERR_ARG
+    assert _lib.lib().fmm_set_wait_limit(t._h, -1) == _lib.FMM_ERR_ARG
+    assert _lib.lib().fmm_set_wait_limit(t._h, 0) == _lib.FMM_OK
 
 
 def test_forest_is_the_disjoint_union():
