@@ -123,6 +123,7 @@ struct DevArgs {
   long long wait_cycles;      // limit of its first wait for each class's copies (SM clock cycles)
   // boundary pair lists (per theta): leaf target cells at a refinement boundary, sorted by work
   int64_t n_bt;
+  int64_t n_bt_long;       // k_m2l_split: the targets [0, n_bt_long) with four lanes each
   const int32_t* bt_cell;  // [n_bt] internal cell index of each target
   const int32_t* bm_off;   // [n_bt + 1] its multipole partners: bm_src / bm_q [bm_off[k], ..)
   const int32_t* bm_src;   // partner cell (in a refined same-level neighbour)
@@ -150,6 +151,7 @@ constexpr int kHaloWords = 8 * kHaloPar;
 constexpr int kLeafThreads = 256;    // one block = one leaf subgrid, two target cells per thread
 constexpr int kRootChunks = 8;       // root sources split into 8 chunks of 64 cells
 constexpr int kM2LThreads = 64;      // one block = the 64 cells of one parity of one subgrid
+constexpr int kSplitLanes = 4;       // lanes per target in k_m2l_split's long-list blocks
 constexpr int kReduceThreads = 256;
 constexpr int kReduceBlocks = 512;
 
@@ -1022,13 +1024,15 @@ constexpr int kCodeMax = 64;  // |point-pair offset| in units of dx / 4
 
 // LANES lanes per target: lane r takes the list entries r, r + LANES, ..., and lane 0 stores
 // the sum (every lane of the block calls this, also past the last target).
+// The block's targets are first + 64 chunk + t, those below end.
 template <typename T, int LANES = 1>
-__device__ void m2l_boundary(const DevArgs& A, int chunk, int t, bool amc, int r = 0) {
+__device__ void m2l_boundary(const DevArgs& A, int64_t first, int64_t end, int chunk, int t, bool amc,
+                             int r = 0) {
   __shared__ T quarter[2 * kCodeMax + 1];  // quarter[i] = (i - kCodeMax) / 4, exact
   for (int i = threadIdx.x; i <= 2 * kCodeMax; i += blockDim.x) quarter[i] = T(i - kCodeMax) * T(0.25);
   __syncthreads();
-  const int64_t k = int64_t(chunk) * 64 + t;
-  const bool valid = k < A.n_bt;
+  const int64_t k = first + int64_t(chunk) * 64 + t;
+  const bool valid = k < end;
   if (LANES == 1 && !valid) return;
   const int64_t iA = valid ? A.bt_cell[k] : 0;
   const int parity = int(iA & 511) >> 6;
@@ -1089,15 +1093,15 @@ __global__ void __launch_bounds__(NT) k_m2l_ref(DevArgs A, const int32_t* __rest
   } else if (kind == 1) {
     m2l_level<T>(A, idx, parity, t, amc != 0);
   } else {
-    m2l_boundary<T>(A, idx, t, amc != 0);
+    m2l_boundary<T>(A, 0, A.n_bt, idx, t, amc != 0);
   }
 }
 
-// The root and boundary blocks of k_m2l_ref (kinds 0 and 2) with 4 lanes per target: these
-// threads run long serial lists of partners read from L2, so the list is split four ways and
-// the partial sums added with warp shuffles.  Used by the mixed path, where refined subgrids
-// go to k_m2l_stage.
-constexpr int kSplitLanes = 4;
+// The root and boundary work of k_m2l_ref for the mixed path (refined subgrids go to
+// k_m2l_stage), 256 threads per block.  Kinds 0 (root chunk) and 2 (64 boundary targets of
+// [0, n_bt_long)): 4 lanes per target -- these threads would run long serial lists of partners
+// read from L2, so each list is split four ways and the partial sums are added with warp
+// shuffles.  Kind 3: the targets n_bt_long + 64 (idx .. idx + 3) + t, one lane each.
 template <typename T>
 __global__ void __launch_bounds__(64 * kSplitLanes) k_m2l_split(DevArgs A, const int32_t* __restrict__ blocks,
                                                                  int amc) {
@@ -1110,7 +1114,10 @@ __global__ void __launch_bounds__(64 * kSplitLanes) k_m2l_split(DevArgs A, const
     if (A.leaf[root]) m2l_root<T, false, kSplitLanes>(A, root, parity, t, chunk, amc != 0, r);
     else m2l_root<T, true, kSplitLanes>(A, root, parity, t, chunk, amc != 0, r);
   } else if (kind == 2) {
-    m2l_boundary<T, kSplitLanes>(A, idx, t, amc != 0, r);
+    m2l_boundary<T, kSplitLanes>(A, 0, A.n_bt_long, idx, t, amc != 0, r);
+  } else {
+    m2l_boundary<T, 1>(A, A.n_bt_long, A.n_bt, idx + int(threadIdx.x) / 64, int(threadIdx.x) % 64,
+                       amc != 0);
   }
 }
 
@@ -2258,8 +2265,9 @@ struct StencilDev {
   dfloat* d_ltab_dff = nullptr;
   int32_t* d_blocks = nullptr;     // general-kernel blocks (one parity each) for this tree, theta
   int64_t n_blocks = 0;
-  int32_t* d_blocks_nr = nullptr;  // the same without the refined subgrids (mixed path: k_m2l_stage)
-  int64_t n_blocks_nr = 0;
+  int32_t* d_blocks_split = nullptr;  // mixed path: k_m2l_split's blocks (root, boundary)
+  int64_t n_blocks_split = 0;
+  int64_t n_bt_long = 0;              // boundary targets [0, n_bt_long) take four lanes
   float* d_stage_tab = nullptr;    // [8][kLeafCap][4] (DevArgs::stage_tab)
   int32_t* d_stage_seg = nullptr;  // [8][9]
   // boundary pair lists (see DevArgs)
@@ -2692,6 +2700,36 @@ static std::vector<int32_t> general_blocks(const HostTree& h, const Stencil& st,
   return out;
 }
 
+// Blocks of k_m2l_split (mixed path).  The root chunks, and the boundary targets whose lists
+// are long (estimated cost above kSplitCost), get four lanes per target (kinds 0 and 2); the
+// other boundary targets go 256 to a block with one lane each (kind 3), where splitting would
+// only add per-target overhead.  The choice depends on the target's own lists alone, so a tree
+// gives the same results alone and inside a forest.  Largest per-lane work first.
+constexpr double kSplitCost = 6000;  // about 40 multipole partners
+static std::vector<int32_t> split_blocks(const HostTree& h, const BoundaryLists& bnd, int64_t* n_long) {
+  const double c_rr = 230, root_lane = 64.0 * c_rr / kSplitLanes;
+  std::vector<std::pair<double, int32_t>> items;
+  for (int r = 0; r < h.n_trees; ++r)
+    for (int ch = 0; ch < kRootChunks; ++ch)
+      for (int p = 0; p < 8; ++p) items.push_back({root_lane, block_code(0, p, uint32_t(r * 8 + ch))});
+  const int64_t n = int64_t(bnd.cell.size());
+  int64_t nl = 0;
+  while (nl < n && bnd.cost[size_t(nl)] > kSplitCost) ++nl;  // targets are sorted by cost
+  *n_long = nl;
+  for (int64_t c = 0; c * 64 < nl; ++c)
+    items.push_back({bnd.cost[size_t(c * 64)] / kSplitLanes, block_code(2, 0, uint32_t(c))});
+  for (int64_t c = 0; nl + c * 64 < n; c += 4)
+    items.push_back({bnd.cost[size_t(nl + c * 64)], block_code(3, 0, uint32_t(c))});
+  std::stable_sort(items.begin(), items.end(),
+                   [](const std::pair<double, int32_t>& x, const std::pair<double, int32_t>& y) {
+                     return x.first > y.first;
+                   });
+  std::vector<int32_t> out;
+  out.reserve(items.size());
+  for (auto& it : items) out.push_back(it.second);
+  return out;
+}
+
 static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
   auto it = t->stencils.find(theta);
   if (it == t->stencils.end()) {
@@ -2762,9 +2800,9 @@ static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
     std::vector<int32_t> blocks = general_blocks(t->h, st, t->work, bl, false);
     sd.n_blocks = int64_t(blocks.size());
     CUDA_TRY(upload(t, &sd.d_blocks, blocks));
-    std::vector<int32_t> blocks_nr = general_blocks(t->h, st, {}, bl, false);
-    sd.n_blocks_nr = int64_t(blocks_nr.size());
-    CUDA_TRY(upload(t, &sd.d_blocks_nr, blocks_nr));
+    std::vector<int32_t> blocks_split = split_blocks(t->h, bl, &sd.n_bt_long);
+    sd.n_blocks_split = int64_t(blocks_split.size());
+    CUDA_TRY(upload(t, &sd.d_blocks_split, blocks_split));
     // staged refined targets: per parity, the stencil entries grouped by partner class, with
     // the partner's lattice offset from a target at lattice cell (0, 0, 0) of that parity
     std::vector<float> stab(8 * kLeafCap * 4, 0.0f);
@@ -2854,6 +2892,7 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.status = t->d_status;
   A.stage_tab = sd ? reinterpret_cast<const float4*>(sd->d_stage_tab) : nullptr;
   A.stage_seg = sd ? sd->d_stage_seg : nullptr;
+  A.n_bt_long = sd ? sd->n_bt_long : 0;
   A.wait_cycles = t->wait_cycles > 0 ? t->wait_cycles : kStageWaitCycles;
   A.smom = t->d_smom;
   A.smtl = t->d_smtl;
@@ -2977,8 +3016,8 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   if ((rc = record(t, 5, st))) return rc;
   if (mixed) {
     // root and boundary blocks here, refined subgrids with staged partners below
-    if (sd->n_blocks_nr > 0) {
-      k_m2l_split<float><<<unsigned(sd->n_blocks_nr), 64 * kSplitLanes, 0, st>>>(A, sd->d_blocks_nr, amc);
+    if (sd->n_blocks_split > 0) {
+      k_m2l_split<float><<<unsigned(sd->n_blocks_split), 64 * kSplitLanes, 0, st>>>(A, sd->d_blocks_split, amc);
       CUDA_TRY(cudaGetLastError());
       ++nl;
     }
