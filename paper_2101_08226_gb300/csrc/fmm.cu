@@ -1270,10 +1270,13 @@ __global__ void __launch_bounds__(kStageThreads, 1) k_m2l_stage(DevArgs A, const
     if (cl < 7) stage_issue(A, nb, cl + 1, (cl & 1) ? buf0 : buf1, &bar[(cl + 1) & 1], t);
     const float* __restrict__ B = ((cl & 1) ? buf1 : buf0) + base;
     const int q1 = __ldg(seg + cl + 1);
-    for (int q0 = __ldg(seg + cl); q0 < q1; q0 += kFlush) {
+    const int qb = __ldg(seg + cl);
+    float4 e_next = __ldg(tab + min(qb, kLeafCap - 1));  // loaded while the previous is evaluated
+    for (int q0 = qb; q0 < q1; q0 += kFlush) {
       const int qe = min(q0 + kFlush, q1);
       for (int q = q0; q < qe; ++q) {
-        const float4 e = __ldg(tab + q);
+        const float4 e = e_next;
+        e_next = __ldg(tab + min(q + 1, q1 - 1));
         const float4* m = reinterpret_cast<const float4*>(B + __float_as_int(e.w) * 20);
         float Mv[20];
 #pragma unroll
@@ -1445,6 +1448,115 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
   }
   A.ac[i0] = A.ac[N + i0] = A.ac[2 * N + i0] = 0.0;
   A.ac[i1] = A.ac[N + i1] = A.ac[2 * N + i1] = 0.0;
+}
+
+// FP32 form of k_m2l_leaf: the same pairs, with the shared-memory and table traffic per
+// multiply-add cut (the FP32 kernel is bound by L1 / shared-memory wavefronts, not by its
+// arithmetic).  A block holds two leaf subgrids (two halos); warp w = parity class w of both,
+// lanes 0-15 the first subgrid's and 16-31 the second's lattice cells (i, j) = (lane >> 2 & 3,
+// lane & 3), each lane the four targets k = 0..3 along z.  Every lane of a warp reads the same
+// table entry; the offsets come four to a 16-byte load (the tables are zero-padded, so the loop
+// runs to a multiple of four).  The second halo starts one word past the first, so the two half
+// warps fall on the even and the odd banks: lattice offsets 120 i + 10 j are the 16 even banks.
+constexpr int kLeaf4Threads = 256;
+constexpr int kLeaf4Smem = (2 * kHaloWords + 1) * 4;
+template <bool SRC>
+__global__ void __launch_bounds__(kLeaf4Threads) k_m2l_leaf4(DevArgs A, const int32_t* __restrict__ work,
+                                                            int64_t n_work) {
+  extern __shared__ __align__(16) float leaf4_smem[];
+  __shared__ int32_t nb[2][27];
+  __shared__ int32_t sub[2];
+  const int t = threadIdx.x;
+  if (t < 2) {
+    const int64_t w = 2 * int64_t(blockIdx.x) + t;
+    sub[t] = w < n_work ? work[w] : -1;
+  }
+  __syncthreads();
+  if (t < 54) {
+    const int h = t / 27, k = t % 27;
+    int32_t q = sub[h] >= 0 ? A.nbr[27 * sub[h] + k] : -1;
+    nb[h][k] = (q >= 0 && A.leaf[q]) ? q : -1;
+  }
+  __syncthreads();
+  const float* __restrict__ M = SRC ? A.smom32 : A.m32;
+  constexpr int kH3 = kHalo * kHalo * kHalo;
+  constexpr int kFill = 8;  // halo loads in flight per thread
+  for (int i0 = t; i0 < 2 * kH3; i0 += kFill * kLeaf4Threads) {
+    float v[kFill];
+    int dst[kFill];
+#pragma unroll
+    for (int u = 0; u < kFill; ++u) {
+      const int i = i0 + u * kLeaf4Threads;
+      const int h = i >= kH3, j = i - h * kH3;
+      const int hx = j / (kHalo * kHalo), r = j - hx * (kHalo * kHalo), hy = r / kHalo, hz = r - hy * kHalo;
+      const int x = hx - 5, y = hy - 5, z = hz - 5;
+      const int32_t q = i < 2 * kH3 ? nb[h][((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)] : -1;
+      dst[u] = i < 2 * kH3 ? h * (kHaloWords + 1) + ((hx & 1) << 2 | (hy & 1) << 1 | (hz & 1)) * kHaloPar +
+                                 (hx >> 1) * kHaloSX + (hy >> 1) * kHaloSY + (hz >> 1)
+                           : -1;
+      v[u] = q >= 0 ? __ldg(M + int64_t(q) * kCells + cidx(x & 7, y & 7, z & 7)) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kFill; ++u)
+      if (dst[u] >= 0) leaf4_smem[dst[u]] = v[u];
+  }
+  __syncthreads();
+  const int parity = t >> 5, lane = t & 31, half = lane >> 4;
+  const int32_t s = sub[half];
+  const int px = (parity >> 2) & 1, py = (parity >> 1) & 1, pz = parity & 1;
+  const int li = (lane >> 2) & 3, lj = lane & 3;
+  const float* __restrict__ hm = leaf4_smem + half * (kHaloWords + 1) + li * kHaloSX + lj * kHaloSY;
+  const int4* __restrict__ toff = reinterpret_cast<const int4*>(A.ltab_off + parity * kLeafCap);
+  const float4* __restrict__ tk = reinterpret_cast<const float4*>(A.ltab_k32 + int64_t(parity) * kLeafCap * 4);
+  const int n4 = (A.n_stencil + A.n_near + 3) >> 2;
+  float s0[4] = {0, 0, 0, 0}, sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0}, sz[4] = {0, 0, 0, 0};
+  // the next group's table entries are loaded while this group's are used
+  int4 o = __ldg(toff);
+  float4 kv[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) kv[u] = __ldg(tk + u);
+  for (int q4 = 0; q4 < n4; ++q4) {
+    const int qn = min(q4 + 1, n4 - 1);
+    const int4 on = __ldg(toff + qn);
+    float4 kn[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) kn[u] = __ldg(tk + 4 * qn + u);
+    const int off[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float m = hm[off[u] + k];
+        s0[k] = fmaf(m, kv[u].x, s0[k]);
+        if (!SRC) {
+          sx[k] = fmaf(m, kv[u].y, sx[k]);
+          sy[k] = fmaf(m, kv[u].z, sy[k]);
+          sz[k] = fmaf(m, kv[u].w, sz[k]);
+        }
+      }
+    }
+    o = on;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) kv[u] = kn[u];
+  }
+  if (s < 0) return;
+  const float h = cell_dx32(A.level[s]);
+  const float ih = 1.0f / h, ih2 = ih * ih;
+  const int64_t N = A.n_cell;
+  const int a = 2 * li + px, b = 2 * lj + py;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t i = int64_t(s) * kCells + cidx(a, b, 2 * k + pz);
+    if (SRC) {
+      A.sloc32[i] = -s0[k] * ih;
+      continue;
+    }
+    A.loc32[i] = -s0[k] * ih;
+    A.loc32[N + i] = -sx[k] * ih2;
+    A.loc32[2 * N + i] = -sy[k] * ih2;
+    A.loc32[3 * N + i] = -sz[k] * ih2;
+    A.ac[i] = A.ac[N + i] = A.ac[2 * N + i] = 0.0;
+  }
 }
 
 // Exact Taylor shift of a 3rd-order expansion P about X to the point X + r, added onto L:
@@ -2382,6 +2494,8 @@ static int ensure_device(fmm_tree* t) {
                                 int(kHaloWords * sizeof(double))));
   CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(kHaloWords * sizeof(float))));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLeaf4Smem));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLeaf4Smem));
   const HostTree& h = t->h;
   const int64_t nc = h.n_sub * kCells;
   CUDA_TRY(upload(t, &t->d_level, h.level));
@@ -3002,8 +3116,8 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   }
   if (t->n_work_leaf > 0) {
     if (mixed)
-      k_m2l_leaf<float, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), st>>>(
-          A, t->d_work_leaf);
+      k_m2l_leaf4<false><<<unsigned((t->n_work_leaf + 1) / 2), kLeaf4Threads, kLeaf4Smem, st>>>(
+          A, t->d_work_leaf, t->n_work_leaf);
     else if (df)
       k_m2l_leaf<dfloat, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(dfloat), st>>>(
           A, t->d_work_leaf);
@@ -3078,8 +3192,8 @@ static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream
   }
   if (t->n_work_leaf > 0) {
     if (mixed)
-      k_m2l_leaf<float, true><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), st>>>(
-          A, t->d_work_leaf);
+      k_m2l_leaf4<true><<<unsigned((t->n_work_leaf + 1) / 2), kLeaf4Threads, kLeaf4Smem, st>>>(
+          A, t->d_work_leaf, t->n_work_leaf);
     else
       k_m2l_leaf<double, true><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(double), st>>>(
           A, t->d_work_leaf);
