@@ -153,7 +153,7 @@ constexpr int kRootChunks = 8;       // root sources split into 8 chunks of 64 c
 constexpr int kM2LThreads = 64;      // one block = the 64 cells of one parity of one subgrid
 constexpr int kSplitLanes = 4;       // lanes per target in k_m2l_split's long-list blocks
 constexpr int kReduceThreads = 256;
-constexpr int kReduceBlocks = 512;
+constexpr int kReduceBlocks = 1216;  // 8 per SM
 
 // Cell width 1 / (8 2^lev), a power of two, assembled from its exponent bits (exact; no divide or
 // conversion, which run on the FP64 pipe).
@@ -290,8 +290,9 @@ __device__ __forceinline__ void octant_cell(int o, int u, int& a, int& b, int& c
 // = 0), with G_ab = M (a = b) or Q_ab:
 //   M2_ab = w^2 G_ab - w D_a delta_b,
 //   M3_abc = w^3 H_abc - w^2 (delta_a G_bc + delta_b G_ac + delta_c G_ab) + 2 w D_a delta_b delta_c.
-__global__ void __launch_bounds__(64) k_m2m_walsh(DevArgs A, const int32_t* __restrict__ octs, int mixed) {
-  const int32_t code = octs[blockIdx.x];
+__device__ __forceinline__ void m2m_walsh(const DevArgs& A, const int32_t* __restrict__ octs, int blk,
+                                          int mixed) {
+  const int32_t code = octs[blk];
   const int32_t s = code >> 3;
   const int o = code & 7, u = int(threadIdx.x);
   int a, b, c;
@@ -351,13 +352,14 @@ __global__ void __launch_bounds__(64) k_m2m_walsh(DevArgs A, const int32_t* __re
 // keeps half the values and adds the partner's copy of them), then gathered into the group's
 // first lane.  The grid covers 512 threads per octant, so every warp is complete for the shuffles.
 constexpr int kM2MThreads = 64;
-__global__ void __launch_bounds__(kM2MThreads) k_m2m_lanes(DevArgs A, const int32_t* __restrict__ octs, int mixed) {
-  const int32_t code = octs[blockIdx.x >> 3];
+__device__ __forceinline__ void m2m_lanes(const DevArgs& A, const int32_t* __restrict__ octs, int blk,
+                                          int mixed) {
+  const int32_t code = octs[blk >> 3];
   const int32_t s = code >> 3;
   const int o = code & 7;
   const int e = int(threadIdx.x & 7);
   const int lead = int(threadIdx.x & 31) & ~7;
-  const int u = int(blockIdx.x & 7) * 8 + int(threadIdx.x >> 3);
+  const int u = (blk & 7) * 8 + int(threadIdx.x >> 3);
   int a, b, c;
   octant_cell(o, u, a, b, c);
   const int64_t N = A.n_cell;
@@ -443,6 +445,16 @@ __global__ void __launch_bounds__(kM2MThreads) k_m2m_lanes(DevArgs A, const int3
   }
   if (e != 0) return;
   store_moments(A, int64_t(s) * kCells + cidx(a, b, c), mt, dx, dy, dz, R, R + 6, mixed);
+}
+
+// One level of the upward pass in one launch: blocks [0, n_walsh) take the octants whose
+// children are leaves (m2m_walsh), the others eight blocks per octant whose children are refined
+// (m2m_lanes).  The two kinds write different parent cells.
+__global__ void __launch_bounds__(kM2MThreads) k_m2m(DevArgs A, const int32_t* __restrict__ walsh_octs,
+                                                    int n_walsh, const int32_t* __restrict__ lanes_octs,
+                                                    int mixed) {
+  if (int(blockIdx.x) < n_walsh) m2m_walsh(A, walsh_octs, int(blockIdx.x), mixed);
+  else m2m_lanes(A, lanes_octs, int(blockIdx.x) - n_walsh, mixed);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -1375,12 +1387,24 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
   if constexpr (SRC) M = SrcView<T>::get(A);
   else M = LeafMass<T>::get(A);
   const int64_t N = A.n_cell;
-  for (int i = t; i < kHalo * kHalo * kHalo; i += kLeafThreads) {
-    const int hx = i / (kHalo * kHalo), r = i - hx * (kHalo * kHalo), hy = r / kHalo, hz = r - hy * kHalo;
-    const int x = hx - 5, y = hy - 5, z = hz - 5;
-    const int32_t q = nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)];
-    hm[((hx & 1) << 2 | (hy & 1) << 1 | (hz & 1)) * kHaloPar + (hx >> 1) * kHaloSX + (hy >> 1) * kHaloSY +
-       (hz >> 1)] = q >= 0 ? M[int64_t(q) * kCells + cidx(x & 7, y & 7, z & 7)] : T(0);
+  constexpr int kH3 = kHalo * kHalo * kHalo, kFill = 8;  // halo loads in flight per thread
+  for (int i0 = t; i0 < kH3; i0 += kFill * kLeafThreads) {
+    T v[kFill];
+    int dst[kFill];
+#pragma unroll
+    for (int u = 0; u < kFill; ++u) {
+      const int i = i0 + u * kLeafThreads;
+      const int hx = i / (kHalo * kHalo), r = i - hx * (kHalo * kHalo), hy = r / kHalo, hz = r - hy * kHalo;
+      const int x = hx - 5, y = hy - 5, z = hz - 5;
+      const int32_t q = i < kH3 ? nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)] : -1;
+      dst[u] = i < kH3 ? ((hx & 1) << 2 | (hy & 1) << 1 | (hz & 1)) * kHaloPar + (hx >> 1) * kHaloSX +
+                             (hy >> 1) * kHaloSY + (hz >> 1)
+                       : -1;
+      v[u] = q >= 0 ? M[int64_t(q) * kCells + cidx(x & 7, y & 7, z & 7)] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kFill; ++u)
+      if (dst[u] >= 0) hm[dst[u]] = v[u];
   }
   __syncthreads();
   const T h = cell_h<T>(A.level[s]);
@@ -1673,10 +1697,10 @@ __global__ void k_root_total(DevArgs A) {
   else A.ac[(comp - 20) * A.n_cell + i] = v;
 }
 
-// Levels >= 1, one launch per level, 64 threads per block.  Blocks [0, n_ref_blocks): 8 per
-// refined subgrid of the level, one thread per cell: total = own + the parent's total shifted
-// from the parent's centre of mass to the cell's (r = X_A - X_P).  The other blocks: one per
-// (refined parent subgrid, octant) whose child subgrid is a leaf of this level, one thread per
+// Levels >= 1, 64 threads per block.  Blocks [0, n_ref_blocks): 8 per refined subgrid of level
+// lev, one thread per cell: total = own + the parent's total shifted from the parent's centre of
+// mass to the cell's (r = X_A - X_P).  The other blocks: one per (refined parent subgrid,
+// octant) whose child subgrid is a leaf (of any level: lev is then the child's), one thread per
 // parent cell and its 8 leaf children.  The parent's total is shifted once to the parent cell's
 // geometric centre; there the children sit at s w (s = +-1 per axis, w = dx_l / 2), and the
 // expansion's value and gradient at the 8 children are sums of the 8 Walsh functions
@@ -1729,6 +1753,7 @@ __global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* 
   octant_cell(o, u, pa, pb, pc);
   const int64_t ip = int64_t(Pn) * kCells + cidx(pa, pb, pc);
   const int32_t s = A.child[8 * Pn + o];
+  lev = A.level[s];  // the leaf octants of every level share one launch
   T L[20], P[20];
 #pragma unroll
   for (int k = 0; k < 20; ++k) {
@@ -2194,9 +2219,13 @@ __device__ __forceinline__ void block_sum7(double* v, double (*sh)[kReduceThread
   }
 }
 
-// blockIdx.y = tree; its leaf cells are reduced by gridDim.x blocks in a fixed order.
+// blockIdx.y = tree; its leaf cells are reduced by gridDim.x blocks in a fixed order, and the
+// last of them to finish (a counter per tree, reset by that block) adds the gridDim.x partial
+// sums in block order into the tree's 7 numbers.  The FP64 work per cell is m, m g, F and the
+// torque (13 operations); the normalisation S, a scale, is formed in FP32 from values converted
+// with integer operations.
 __global__ void __launch_bounds__(kReduceThreads)
-    k_net_partial(DevArgs A, double* __restrict__ partials) {
+    k_net_partial(DevArgs A, double* __restrict__ partials, unsigned* __restrict__ counters) {
   __shared__ double sh[7][kReduceThreads];
   double v[6] = {0, 0, 0, 0, 0, 0};
   float sn = 0.0f;  // this thread's share of the normalisation S, formed and summed in FP32
@@ -2205,6 +2234,7 @@ __global__ void __launch_bounds__(kReduceThreads)
   const int64_t end = A.tree_leaf_off[blockIdx.y + 1] * kCells;
   const double* __restrict__ rho = A.io[blockIdx.y].rho;
   const double* __restrict__ g = A.io[blockIdx.y].g;
+#pragma unroll 4
   for (int64_t i = base + int64_t(blockIdx.x) * kReduceThreads + threadIdx.x; i < end;
        i += stride) {
     const int32_t s = A.leaf_sub[i >> 9];
@@ -2227,12 +2257,27 @@ __global__ void __launch_bounds__(kReduceThreads)
     v[5] = fma(x, fy, fma(-y, fx, v[5]));
     const float sc = __int_as_float((127 - lev - 4) << 23);
     const float xf = float(nx) * sc, yf = float(ny) * sc, zf = float(nz) * sc;
-    sn += sqrtf(xf * xf + yf * yf + zf * zf) * sqrtf(float(fx * fx + fy * fy + fz * fz));
+    const float ffx = df_d2f_trunc(fx), ffy = df_d2f_trunc(fy), ffz = df_d2f_trunc(fz);
+    sn += sqrtf(xf * xf + yf * yf + zf * zf) * sqrtf(ffx * ffx + ffy * ffy + ffz * ffz);
   }
-  double w[7] = {v[0], v[1], v[2], v[3], v[4], v[5], double(sn)};
+  double w[7] = {v[0], v[1], v[2], v[3], v[4], v[5], df_f2d(sn)};
   block_sum7(w, sh);
-  if (threadIdx.x < 7)
-    partials[(int64_t(blockIdx.y) * gridDim.x + blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];
+  double* P = partials + int64_t(blockIdx.y) * gridDim.x * 7;
+  if (threadIdx.x < 7) P[int64_t(blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];
+  __shared__ bool last;
+  __threadfence();  // this block's partial sums are visible before it is counted
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&counters[blockIdx.y], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double u[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < int(gridDim.x); b += kReduceThreads)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) u[k] += P[int64_t(b) * 7 + k];
+  block_sum7(u, sh);
+  if (threadIdx.x < 7) (*A.io_net)[int64_t(blockIdx.y) * 7 + threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x == 0) counters[blockIdx.y] = 0u;  // ready for the next solve
 }
 
 // blockIdx.x = tree (or set of partials): sums n_blocks partials in a fixed order into out[7 x];
@@ -2410,6 +2455,7 @@ struct fmm_tree {
   int64_t n_work = 0;
   double *d_mom = nullptr, *d_mtl = nullptr, *d_loc = nullptr, *d_ac = nullptr, *d_root_part = nullptr,
          *d_root_part_ac = nullptr, *d_partials = nullptr;
+  unsigned* d_net_count = nullptr;  // k_net_partial's finished-block counters, one per tree
   float *d_mom32 = nullptr, *d_m32 = nullptr, *d_loc32 = nullptr, *d_root_part32 = nullptr;
   int* d_status = nullptr;
   int64_t* d_tree_leaf_off = nullptr;
@@ -2558,6 +2604,8 @@ static int ensure_device(fmm_tree* t) {
   const int64_t nr = h.n_trees;
   CUDA_TRY(dalloc(t, &t->d_root_part, sizeof(double) * nr * kRootChunks * 23 * kCells));
   CUDA_TRY(dalloc(t, &t->d_partials, sizeof(double) * 7 * net_blocks(nr) * nr));
+  CUDA_TRY(dalloc(t, &t->d_net_count, sizeof(unsigned) * size_t(nr)));
+  CUDA_TRY(cudaMemset(t->d_net_count, 0, sizeof(unsigned) * size_t(nr)));
   CUDA_TRY(upload(t, &t->d_tree_leaf_off, h.tree_leaf_off));
   CUDA_TRY(dalloc(t, &t->d_status, sizeof(int)));
   CUDA_TRY(cudaMemset(t->d_status, 0, sizeof(int)));
@@ -3059,11 +3107,33 @@ static int set_io(fmm_tree* t, const std::vector<TreeIo>& io, double* net, cudaS
 static int launch_net(fmm_tree* t, const DevArgs& A, cudaStream_t st) {
   const int nb = net_blocks(t->h.n_trees);
   k_net_partial<<<dim3(unsigned(nb), unsigned(t->h.n_trees)), kReduceThreads, 0, st>>>(
-      A, t->d_partials);
+      A, t->d_partials, t->d_net_count);
   CUDA_TRY(cudaGetLastError());
-  k_net_final<<<unsigned(t->h.n_trees), kReduceThreads, 0, st>>>(t->d_partials, nb, nullptr,
-                                                                  A.io_net);
-  CUDA_TRY(cudaGetLastError());
+  return FMM_OK;
+}
+
+// Downward pass below the root: one launch per level with refined subgrids (their cells'
+// totals need the parent level's), then one launch evaluating every leaf octant of every level
+// from its parent cell's total.
+template <bool SRC>
+static int launch_down(fmm_tree* t, const DevArgs& A, bool mixed, cudaStream_t st, int32_t* nl) {
+  const HostTree& h = t->h;
+  for (int l = 1; l <= h.depth; ++l) {
+    const int64_t nr = t->ref_off[l + 1] - t->ref_off[l];
+    if (nr == 0) continue;
+    const int32_t* ref = t->d_ref_sub + t->ref_off[l];
+    if (mixed) k_down<true, SRC><<<unsigned(nr * 8), 64, 0, st>>>(A, l, ref, int(nr * 8), nullptr);
+    else k_down<false, SRC><<<unsigned(nr * 8), 64, 0, st>>>(A, l, ref, int(nr * 8), nullptr);
+    CUDA_TRY(cudaGetLastError());
+    ++*nl;
+  }
+  const int64_t no = t->oct_leaf_off[h.depth + 1];  // every leaf octant, parents of all levels
+  if (no > 0) {
+    if (mixed) k_down<true, SRC><<<unsigned(no), 64, 0, st>>>(A, 0, nullptr, 0, t->d_oct_leaf);
+    else k_down<false, SRC><<<unsigned(no), 64, 0, st>>>(A, 0, nullptr, 0, t->d_oct_leaf);
+    CUDA_TRY(cudaGetLastError());
+    ++*nl;
+  }
   return FMM_OK;
 }
 
@@ -3085,14 +3155,9 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   for (int l = h.depth - 1; l >= 0; --l) {
     const int64_t nl_oct = t->oct_leaf_off[l + 1] - t->oct_leaf_off[l];
     const int64_t nr_oct = t->oct_ref_off[l + 1] - t->oct_ref_off[l];
-    if (nl_oct > 0) {
-      k_m2m_walsh<<<unsigned(nl_oct), 64, 0, st>>>(A, t->d_oct_leaf + t->oct_leaf_off[l], mode);
-      CUDA_TRY(cudaGetLastError());
-      ++nl;
-    }
-    if (nr_oct > 0) {
-      k_m2m_lanes<<<unsigned(nr_oct * 8), kM2MThreads, 0, st>>>(A, t->d_oct_ref + t->oct_ref_off[l],
-                                                                 mode);
+    if (nl_oct + nr_oct > 0) {
+      k_m2m<<<unsigned(nl_oct + nr_oct * 8), kM2MThreads, 0, st>>>(
+          A, t->d_oct_leaf + t->oct_leaf_off[l], int(nl_oct), t->d_oct_ref + t->oct_ref_off[l], mode);
       CUDA_TRY(cudaGetLastError());
       ++nl;
     }
@@ -3150,21 +3215,11 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   else k_root_total<false, false><<<blocks_for(int64_t(h.n_trees) * kRootComps * kCells, 128), 128, 0, st>>>(A);
   CUDA_TRY(cudaGetLastError());
   ++nl;
-  for (int l = 1; l <= h.depth; ++l) {
-    const int64_t nr = t->ref_off[l + 1] - t->ref_off[l];
-    const int64_t no = t->oct_leaf_off[l] - t->oct_leaf_off[l - 1];
-    if (nr * 8 + no == 0) continue;
-    const int32_t* ref = t->d_ref_sub + t->ref_off[l];
-    const int32_t* octs = t->d_oct_leaf + t->oct_leaf_off[l - 1];
-    if (mixed) k_down<true, false><<<unsigned(nr * 8 + no), 64, 0, st>>>(A, l, ref, int(nr * 8), octs);
-    else k_down<false, false><<<unsigned(nr * 8 + no), 64, 0, st>>>(A, l, ref, int(nr * 8), octs);
-    CUDA_TRY(cudaGetLastError());
-    ++nl;
-  }
+  if ((rc = launch_down<false>(t, A, mixed, st, &nl))) return rc;
   if ((rc = record(t, 3, st))) return rc;
   if (net) {
     if ((rc = launch_net(t, A, st))) return rc;
-    nl += 2;
+    nl += 1;
   }
   if ((rc = record(t, 4, st))) return rc;
   // time-derivative solve: rho's centres of mass and lists, the source's moments (it reuses the
@@ -3208,17 +3263,8 @@ static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream
   else k_root_total<false, true><<<blocks_for(int64_t(h.n_trees) * kRootComps * kCells, 128), 128, 0, st>>>(A);
   CUDA_TRY(cudaGetLastError());
   ++*nl;
-  for (int l = 1; l <= h.depth; ++l) {
-    const int64_t nr = t->ref_off[l + 1] - t->ref_off[l];
-    const int64_t no = t->oct_leaf_off[l] - t->oct_leaf_off[l - 1];
-    if (nr * 8 + no == 0) continue;
-    const int32_t* ref = t->d_ref_sub + t->ref_off[l];
-    const int32_t* octs = t->d_oct_leaf + t->oct_leaf_off[l - 1];
-    if (mixed) k_down<true, true><<<unsigned(nr * 8 + no), 64, 0, st>>>(A, l, ref, int(nr * 8), octs);
-    else k_down<false, true><<<unsigned(nr * 8 + no), 64, 0, st>>>(A, l, ref, int(nr * 8), octs);
-    CUDA_TRY(cudaGetLastError());
-    ++*nl;
-  }
+  int rc = launch_down<true>(t, A, mixed, st, nl);
+  if (rc) return rc;
   return FMM_OK;
 }
 
