@@ -447,9 +447,8 @@ __device__ __forceinline__ void m2m_lanes(const DevArgs& A, const int32_t* __res
   store_moments(A, int64_t(s) * kCells + cidx(a, b, c), mt, dx, dy, dz, R, R + 6, mixed);
 }
 
-// One level of the upward pass in one launch: blocks [0, n_walsh) take the octants whose
-// children are leaves (m2m_walsh), the others eight blocks per octant whose children are refined
-// (m2m_lanes).  The two kinds write different parent cells.
+// Upward pass: blocks [0, n_walsh) take octants whose children are leaves (m2m_walsh), the
+// others eight blocks per octant whose children are refined (m2m_lanes).
 __global__ void __launch_bounds__(kM2MThreads) k_m2m(DevArgs A, const int32_t* __restrict__ walsh_octs,
                                                     int n_walsh, const int32_t* __restrict__ lanes_octs,
                                                     int mixed) {
@@ -3152,12 +3151,19 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   k_p2m<<<blocks_for(A.n_leaf_cells, 256), 256, 0, st>>>(A, mode);
   CUDA_TRY(cudaGetLastError());
   ++nl;
+  // octants whose children are leaves need only the leaf masses: every level's in one launch;
+  // then the octants with refined children, finest level first
+  const int64_t n_walsh = t->oct_leaf_off[h.depth + 1];
+  if (n_walsh > 0) {
+    k_m2m<<<unsigned(n_walsh), kM2MThreads, 0, st>>>(A, t->d_oct_leaf, int(n_walsh), nullptr, mode);
+    CUDA_TRY(cudaGetLastError());
+    ++nl;
+  }
   for (int l = h.depth - 1; l >= 0; --l) {
-    const int64_t nl_oct = t->oct_leaf_off[l + 1] - t->oct_leaf_off[l];
     const int64_t nr_oct = t->oct_ref_off[l + 1] - t->oct_ref_off[l];
-    if (nl_oct + nr_oct > 0) {
-      k_m2m<<<unsigned(nl_oct + nr_oct * 8), kM2MThreads, 0, st>>>(
-          A, t->d_oct_leaf + t->oct_leaf_off[l], int(nl_oct), t->d_oct_ref + t->oct_ref_off[l], mode);
+    if (nr_oct > 0) {
+      k_m2m<<<unsigned(nr_oct * 8), kM2MThreads, 0, st>>>(A, nullptr, 0, t->d_oct_ref + t->oct_ref_off[l],
+                                                          mode);
       CUDA_TRY(cudaGetLastError());
       ++nl;
     }

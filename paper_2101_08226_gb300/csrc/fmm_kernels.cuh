@@ -53,8 +53,15 @@ template <typename T>
 __device__ __forceinline__ T rsqrt_t(T v);
 template <>
 __device__ __forceinline__ double rsqrt_t<double>(double v) { return rsqrt(v); }
+// FP32: the hardware approximation (PTX rsqrt.approx.ftz.f32, relative error below 2^-22.9)
+// as one instruction; arguments are squared separations of at least a cell width, never
+// subnormal.
 template <>
-__device__ __forceinline__ float rsqrt_t<float>(float v) { return rsqrtf(v); }
+__device__ __forceinline__ float rsqrt_t<float>(float v) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
 template <>
 __device__ __forceinline__ dfloat rsqrt_t<dfloat>(dfloat v) { return df_rsqrt(v); }
 
