@@ -387,6 +387,8 @@ def run_ours(args):
         launches = tree.last_launches() * args.steps
         return total, np.mean(np.array(phases), axis=0), launches
 
+    # the library's autotuner picks the mixed path's launch variant for this tree (untimed)
+    tuned_variant, tuned_ms, _, _ = tree.autotune(rhos[0], THETA, "mixed", reps=3, stream=stream)
     sampler = ClockSampler(uuid) if (uuid and rank == 0) else None
     t64, ph64, l64 = timed("fp64")
     phi64, g64, net64 = phi.clone(), g.clone(), net.clone()
@@ -497,7 +499,7 @@ def run_ours(args):
         # stream it runs on, inside the timed region.  FP64: the general kernel (refined and
         # boundary targets, root) or the leaf kernel; mixed: the refined targets' kernel, which
         # runs on the tree's second stream beside the leaf and boundary kernels
-        if precision == "mixed":
+        if precision == "mixed" and float(ph[6]) > 0:
             ms = {"k_m2l_stage": float(ph[6]), "k_m2l_leaf": float(ph[5])}
             k = "k_m2l_stage"
         else:
@@ -507,6 +509,8 @@ def run_ours(args):
         peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
         unit = "FP64" if precision == "fp64" else "FP32"
         kname = k if k == "k_m2l_stage" else f"{k}<{'double' if precision == 'fp64' else 'float'}>"
+        if precision == "mixed" and k == "k_m2l_ref":
+            kname = "k_m2l_ref<float> or k_m2l_split<float> + k_m2l_stage (one stream)"
         return {"bound": "alu", "kernel": kname,
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": traffic.get(kname), "traffic_unit": "bytes per launch (ncu)",
@@ -548,6 +552,11 @@ def run_ours(args):
                   "roofline": roofline(ph32, "mixed"),
                   "phases_ms": phases(ph32, "mixed"),
                   "ms_per_step_direct_launches": t32d / args.steps,
+                  "autotune": {"variant": int(tuned_variant),
+                               "median_ms_per_variant": [round(float(x), 4) for x in tuned_ms],
+                               "variants": "r + 3 l; r: refined targets 0 staged on a second stream, "
+                                           "1 staged on one stream, 2 per-parity blocks from L2; "
+                                           "l: leaf kernel 0 four targets per lane, 1 two per thread"},
                   "gpu_launches": l32},
         "e2e": {"value": world * n_m2l * args.steps / e2e_s, "unit": "interactions/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n + 24 * n + 56,

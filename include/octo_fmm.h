@@ -186,6 +186,30 @@ int fmm_binary_diagnostics(fmm_tree* tree, const double* rho_dev, const double* 
                            double omega, const double* x1, const double* x2, double rc1,
                            double rc2, double* out_dev, int8_t* member_dev, void* stream);
 
+/* Launch variants of the mixed path (FMM_MIXED), per tree and theta: variant = r + 3 l with
+ *   r = 0: refined targets by the shared-memory staging kernel on a second stream, beside the
+ *          leaf and boundary kernels (the default);
+ *   r = 1: the same kernel after them, on one stream;
+ *   r = 2: refined targets by per-parity blocks that read their partners from L2;
+ *   l = 0: leaf pairs by the four-targets-per-lane FP32 kernel (the default);
+ *   l = 1: leaf pairs by the two-targets-per-thread kernel.
+ * r = 0 and 1 give the same results bit for bit, and so do l = 0 and 1; r = 2 sums the refined
+ * targets' pairs in another order (results differ at FP32 rounding, within the mixed path's
+ * tolerance).  FMM_ERR_ARG for a variant outside [0, FMM_MIXED_VARIANTS), FMM_ERR_THETA for a
+ * theta outside [0.34, 1).  The FP64 and df64 paths have one launch configuration. */
+#define FMM_MIXED_VARIANTS 6
+int fmm_set_variant(fmm_tree* tree, double theta, int variant);
+
+/* Autotuner: times every launch variant of `precision` (FMM_MIXED: FMM_MIXED_VARIANTS; FP64,
+ * df64: one) on the caller's density, `reps` timed solves each after one warm-up solve (CUDA
+ * events on `stream`, the median kept), keeps the fastest for this tree and theta, writes its
+ * number to *variant_out and the medians (ms) to ms_host[variant] when ms_host is not null, and
+ * leaves that variant's phi and g in the output buffers.  Blocks the calling thread until done.
+ * rho_dev, phi_dev, g_dev as for fmm_solve.  FMM_ERR_ARG for a null pointer or reps < 1. */
+int fmm_autotune(fmm_tree* tree, const double* rho_dev, double theta, int precision, int amc,
+                 double* phi_dev, double* g_dev, int reps, float* ms_host, int32_t* variant_out,
+                 void* stream);
+
 /* Mixed-precision refined targets stage their partners' moments in shared memory with bulk
  * asynchronous copies; each wait for a parity class's copies gives up after `cycles` SM clock
  * cycles (0, the default: 2^31, about a second), records FMM_ERR_TIMEOUT in the status word and

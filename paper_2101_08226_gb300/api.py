@@ -216,6 +216,27 @@ class Tree:
         kernels one by one."""
         check(lib().fmm_set_graphs(self._h, int(bool(on))))
 
+    def set_variant(self, theta: float, variant: int):
+        """Launch variant of the mixed path for this tree and theta (fmm_set_variant)."""
+        check(lib().fmm_set_variant(self._h, float(theta), int(variant)))
+
+    def autotune(self, rho, theta: float, precision: str = "mixed", amc: bool = True, reps: int = 5,
+                 stream=None):
+        """fmm_autotune on the CUDA float64 density rho: returns (chosen variant, median ms per
+        variant, phi, g of the chosen variant)."""
+        import torch
+        n = self.n_leaf_cells
+        assert rho.is_cuda and rho.dtype == torch.float64 and rho.is_contiguous() and rho.numel() == n
+        phi = torch.empty(n, dtype=torch.float64, device=rho.device)
+        g = torch.empty((n, 3), dtype=torch.float64, device=rho.device)
+        ms = np.zeros(_lib.FMM_MIXED_VARIANTS, dtype=np.float32)
+        v = C.c_int32()
+        check(lib().fmm_autotune(self._h, rho.data_ptr(), float(theta), PRECISIONS[precision],
+                                 int(bool(amc)), phi.data_ptr(), g.data_ptr(), int(reps), _p(ms),
+                                 C.byref(v), _stream_handle(stream)))
+        n_var = _lib.FMM_MIXED_VARIANTS if precision == "mixed" else 1
+        return v.value, ms[:n_var], phi, g
+
     def set_wait_limit(self, cycles: int = 0):
         """Limit, in SM clock cycles, of the staging kernel's wait for each parity class's
         copies (0: the default, about a second); a wait that runs out is reported by the next

@@ -152,6 +152,7 @@ constexpr int kLeafThreads = 256;    // one block = one leaf subgrid, two target
 constexpr int kRootChunks = 8;       // root sources split into 8 chunks of 64 cells
 constexpr int kM2LThreads = 64;      // one block = the 64 cells of one parity of one subgrid
 constexpr int kSplitLanes = 4;       // lanes per target in k_m2l_split's long-list blocks
+constexpr int kMixedVariants = 6;    // mixed path launch variants: refined (3) x leaf kernel (2)
 constexpr int kReduceThreads = 256;
 constexpr int kReduceBlocks = 1216;  // 8 per SM
 
@@ -2421,6 +2422,7 @@ struct StencilDev {
   dfloat* d_ltab_dff = nullptr;
   int32_t* d_blocks = nullptr;     // general-kernel blocks (one parity each) for this tree, theta
   int64_t n_blocks = 0;
+  int mixed_variant = 0;              // mixed path launch variant (fmm_set_variant, fmm_autotune)
   int32_t* d_blocks_split = nullptr;  // mixed path: k_m2l_split's blocks (root, boundary)
   int64_t n_blocks_split = 0;
   int64_t n_bt_long = 0;              // boundary targets [0, n_bt_long) take four lanes
@@ -2492,7 +2494,7 @@ struct fmm_tree {
     int32_t launches = 0;
   };
   // one instantiated graph per (theta, precision, correction, net output, profiling, dphi/dt)
-  std::map<std::tuple<double, int, int, int, int, int, long long>, Graph> graphs;
+  std::map<std::tuple<double, int, int, int, int, int, long long, int>, Graph> graphs;
 };
 
 // blocks per tree of the net reduction: about 512 in all
@@ -3172,9 +3174,14 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   if ((rc = record(t, 1, st))) return rc;
   // interactions: leaf subgrids of levels >= 1 (same-level leaf partners), then the general
   // kernel: root chunks, every (refined subgrid, parity) and every (boundary leaf subgrid, parity).
-  // Mixed path: the refined subgrids go to k_m2l_stage on a second stream, beside the leaf and
-  // general kernels (one block per SM, it leaves room for theirs).
-  const bool fork = mixed && !t->work.empty();
+  // Mixed path, by the launch variant of this tree and theta (kMixedVariants): the refined
+  // subgrids go to k_m2l_stage on a second stream beside the leaf and general kernels (one block
+  // per SM leaves room for theirs), or after them on the same stream, or to k_m2l_ref's
+  // per-parity blocks reading their partners from L2; the leaf pairs to k_m2l_leaf4 or
+  // k_m2l_leaf<float>.
+  const int v_ref = sd->mixed_variant % 3, v_leaf = sd->mixed_variant / 3;
+  const bool staged = mixed && !t->work.empty() && v_ref != 2;
+  const bool fork = staged && v_ref == 0;
   if (fork) {
     CUDA_TRY(cudaEventRecord(t->ev_fork, st));
     CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_fork, 0));
@@ -3186,9 +3193,12 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
     CUDA_TRY(cudaEventRecord(t->ev_join, t->stream2));
   }
   if (t->n_work_leaf > 0) {
-    if (mixed)
+    if (mixed && v_leaf == 0)
       k_m2l_leaf4<false><<<unsigned((t->n_work_leaf + 1) / 2), kLeaf4Threads, kLeaf4Smem, st>>>(
           A, t->d_work_leaf, t->n_work_leaf);
+    else if (mixed)
+      k_m2l_leaf<float, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), st>>>(
+          A, t->d_work_leaf);
     else if (df)
       k_m2l_leaf<dfloat, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(dfloat), st>>>(
           A, t->d_work_leaf);
@@ -3199,10 +3209,19 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
     ++nl;
   }
   if ((rc = record(t, 5, st))) return rc;
-  if (mixed) {
-    // root and boundary blocks here, refined subgrids with staged partners below
+  if (mixed && v_ref == 2) {
+    k_m2l_ref<float, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
+    CUDA_TRY(cudaGetLastError());
+    ++nl;
+  } else if (mixed) {
+    // root and boundary blocks here; refined subgrids on the second stream, or after these
     if (sd->n_blocks_split > 0) {
       k_m2l_split<float><<<unsigned(sd->n_blocks_split), 64 * kSplitLanes, 0, st>>>(A, sd->d_blocks_split, amc);
+      CUDA_TRY(cudaGetLastError());
+      ++nl;
+    }
+    if (staged && !fork) {
+      k_m2l_stage<<<unsigned(t->work.size()), kStageThreads, kStageSmem, st>>>(A, t->d_work, amc);
       CUDA_TRY(cudaGetLastError());
       ++nl;
     }
@@ -3323,7 +3342,7 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   fmm_tree::Graph* gr = nullptr;
   if (t->use_graphs) {
     auto key = std::make_tuple(theta, precision, amc, net ? 1 : 0, t->profiling ? 1 : 0, src ? 1 : 0,
-                               t->wait_cycles);
+                               t->wait_cycles, precision == FMM_MIXED ? sd->mixed_variant : 0);
     auto it = t->graphs.find(key);
     if (it == t->graphs.end()) {
       fmm_tree::Graph fresh;
@@ -3345,7 +3364,7 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
   CUDA_TRY(cudaStreamWaitEvent(caller, t->ev_out, 0));
   t->ev_recorded = t->profiling;
-  t->ev_stage = t->profiling && mixed && !t->work.empty();
+  t->ev_stage = t->profiling && mixed && !t->work.empty() && sd->mixed_variant % 3 == 0;
   t->launches = n_io + n_solve;
   return FMM_OK;
 }
@@ -3694,6 +3713,76 @@ int fmm_binary_diagnostics(fmm_tree* t, const double* rho_dev, const double* g_d
     CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
     CUDA_TRY(cudaStreamWaitEvent(caller, t->ev_out, 0));
     return FMM_OK;
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+int fmm_set_variant(fmm_tree* t, double theta, int variant) {
+  if (!t) return fail(FMM_ERR_ARG, "tree is null");
+  if (variant < 0 || variant >= kMixedVariants) return fail(FMM_ERR_ARG, "variant out of range");
+  if (!(theta >= kThetaMin && theta < 1.0)) return fail(FMM_ERR_THETA, "theta must lie in [0.34, 1)");
+  int rc = ensure_device(t);
+  if (rc) return rc;
+  StencilDev* sd = nullptr;
+  try {
+    if ((rc = get_stencil(t, theta, &sd))) return rc;
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+  sd->mixed_variant = variant;
+  return FMM_OK;
+}
+
+int fmm_autotune(fmm_tree* t, const double* rho_dev, double theta, int precision, int amc,
+                 double* phi_dev, double* g_dev, int reps, float* ms_host, int32_t* variant_out,
+                 void* stream) {
+  if (!t || !rho_dev || !phi_dev || !g_dev || !variant_out || reps < 1)
+    return fail(FMM_ERR_ARG, "null argument or reps < 1");
+  if (precision != FMM_FP64 && precision != FMM_MIXED && precision != FMM_DF64)
+    return fail(FMM_ERR_ARG, "bad precision");
+  try {
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
+    const std::vector<TreeIo> io = contiguous_io(t, rho_dev, phi_dev, g_dev);
+    const int n_var = precision == FMM_MIXED ? kMixedVariants : 1;
+    int rc = solve_impl(t, io, theta, precision, amc, nullptr, caller);  // builds the lists
+    if (rc) return rc;
+    StencilDev* sd = nullptr;
+    if ((rc = get_stencil(t, theta, &sd))) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    int best = 0;
+    float best_ms = 0.0f;
+    for (int v = 0; v < n_var && rc == FMM_OK; ++v) {
+      sd->mixed_variant = v;
+      rc = solve_impl(t, io, theta, precision, amc, nullptr, caller);  // warm-up (captures its graph)
+      std::vector<float> ms;
+      for (int r = 0; r < reps && rc == FMM_OK; ++r) {
+        float x = 0.0f;
+        if (cudaEventRecord(e0, caller) != cudaSuccess) rc = fail(FMM_ERR_CUDA, "event record");
+        if (!rc) rc = solve_impl(t, io, theta, precision, amc, nullptr, caller);
+        if (!rc && (cudaEventRecord(e1, caller) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&x, e0, e1) != cudaSuccess))
+          rc = fail(FMM_ERR_CUDA, "event timing");
+        ms.push_back(x);
+      }
+      if (rc) break;
+      std::sort(ms.begin(), ms.end());
+      const float med = ms[ms.size() / 2];
+      if (ms_host) ms_host[v] = med;
+      if (v == 0 || med < best_ms) {
+        best = v;
+        best_ms = med;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    sd->mixed_variant = precision == FMM_MIXED ? best : sd->mixed_variant;
+    *variant_out = best;
+    // leave the outputs of the chosen variant in phi and g
+    return solve_impl(t, io, theta, precision, amc, nullptr, caller);
   } catch (...) {
     return fail(FMM_ERR_NOMEM, "host allocation failed");
   }

@@ -129,6 +129,15 @@ def test_argument_errors():
     assert _lib.lib().fmm_set_wait_limit(None, 0) == _lib.FMM_ERR_ARG
     assert _lib.lib().fmm_set_wait_limit(t._h, -1) == _lib.FMM_ERR_ARG
     assert _lib.lib().fmm_set_wait_limit(t._h, 0) == _lib.FMM_OK
+    assert _lib.lib().fmm_set_variant(None, 0.5, 0) == _lib.FMM_ERR_ARG
+    assert _lib.lib().fmm_set_variant(t._h, 0.5, -1) == _lib.FMM_ERR_ARG
+    assert _lib.lib().fmm_set_variant(t._h, 0.5, _lib.FMM_MIXED_VARIANTS) == _lib.FMM_ERR_ARG
+    assert _lib.lib().fmm_set_variant(t._h, 0.2, 0) == _lib.FMM_ERR_THETA
+    v = C.c_int32()
+    assert _lib.lib().fmm_autotune(t._h, None, 0.5, 1, 1, None, None, 3, None, C.byref(v),
+                                   None) == _lib.FMM_ERR_ARG
+    assert _lib.lib().fmm_autotune(t._h, C.c_void_p(16), 0.5, 1, 1, C.c_void_p(16), C.c_void_p(16),
+                                   0, None, C.byref(v), None) == _lib.FMM_ERR_ARG
 
 
 def test_forest_is_the_disjoint_union():

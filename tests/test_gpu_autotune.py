@@ -1,0 +1,71 @@
+"""Mixed-path launch variants and the autotuner that picks among them (fmm_set_variant,
+fmm_autotune): every variant against the FP64 oracle within the mixed tolerance; the variants
+that only move kernels between streams or swap the leaf kernel's thread layout give the same
+results bit for bit; the autotuner's choice is a valid variant whose results it leaves in the
+outputs, and later solves use it; the FP64 path has one configuration."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2101_08226_gb300 import _lib, api, build, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+def _case():
+    w = synth.workload_binary(3, axis=(1.0, 0.6, 0.3), offset=(0.02, -0.03, 0.05))
+    a, b = api.Tree(w.max_level, w.flags), O.Tree(w.max_level, w.flags)
+    rho = synth.leaf_density(w.field, b.leaves())
+    return a, b, rho
+
+
+def _inf(x, ref):
+    return float(np.abs(np.asarray(x) - ref).max() / np.abs(ref).max())
+
+
+def test_every_mixed_variant_matches_oracle():
+    a, b, rho = _case()
+    phi_o, g_o, _ = O.solve(b, rho, 0.5)
+    r = torch.from_numpy(rho).cuda()
+    out = {}
+    for v in range(_lib.FMM_MIXED_VARIANTS):
+        a.set_variant(0.5, v)
+        phi, g, _ = a.solve(r, 0.5, "mixed")
+        out[v] = (phi.cpu().numpy(), g.cpu().numpy())
+        assert _inf(out[v][0], phi_o) <= MIXED_TOL and _inf(out[v][1], g_o) <= MIXED_TOL, v
+    # same arithmetic in the same order: streams (r = 0, 1) and leaf layouts (l = 0, 1)
+    for v, w in ((0, 1), (0, 3), (0, 4), (2, 5)):
+        assert np.array_equal(out[v][0], out[w][0]) and np.array_equal(out[v][1], out[w][1]), (v, w)
+
+
+def test_autotune_picks_a_variant_and_keeps_it():
+    a, _, rho = _case()
+    r = torch.from_numpy(rho).cuda()
+    v, ms, phi, g = a.autotune(r, 0.5, "mixed", reps=3)
+    assert 0 <= v < _lib.FMM_MIXED_VARIANTS
+    assert ms.shape == (_lib.FMM_MIXED_VARIANTS,) and (ms > 0).all()
+    assert ms[v] == ms.min()
+    phi2, g2, _ = a.solve(r, 0.5, "mixed")  # uses the chosen variant
+    a.set_variant(0.5, v)
+    phi3, g3, _ = a.solve(r, 0.5, "mixed")
+    for x, y in ((phi, phi2), (phi2, phi3), (g, g2), (g2, g3)):
+        assert torch.equal(x, y)
+
+
+def test_autotune_fp64_has_one_configuration():
+    a, _, rho = _case()
+    r = torch.from_numpy(rho).cuda()
+    ref_phi, ref_g, _ = a.solve(r, 0.5, "fp64")
+    v, ms, phi, g = a.autotune(r, 0.5, "fp64", reps=2)
+    assert v == 0 and ms.shape == (1,) and ms[0] > 0
+    assert torch.equal(phi, ref_phi) and torch.equal(g, ref_g)
