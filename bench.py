@@ -315,11 +315,16 @@ def run_solve_only(args):
     import torch
     from paper_2101_08226_gb300 import api, build, synth
     build.build()
-    w = synth.workload_binary(LEVELS)
+    if args.solve_workload == "paper9":
+        w = synth.workload_paper_binary()
+        theta = w.theta
+    else:
+        w = synth.workload_binary(LEVELS)
+        theta = THETA
     tree = api.Tree(w.max_level, w.flags)
     rho = torch.from_numpy(synth.leaf_density(w.field, tree.leaves())).cuda()
     for _ in range(args.warmup + args.steps):
-        phi, g, net = tree.solve(rho, THETA, args.solve_only, True)
+        phi, g, net = tree.solve(rho, theta, args.solve_only, True)
     torch.cuda.synchronize()
     print(json.dumps({"solve_only": args.solve_only, "solves": args.warmup + args.steps,
                       "launches_per_solve": tree.last_launches(), "net": net.cpu().tolist()}))
@@ -581,6 +586,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--solve-workload", choices=["binary5", "paper9"], default="binary5",
+                    help="with --solve-only: the 5-level binary (default) or the 9-level merger "
+                         "binary in the paper's proportions")
     ap.add_argument("--solve-only", choices=["fp64", "mixed", "df64"], default=None,
                     help="profiling driver: run warmup + steps solves of the benchmark tree, no timing")
     args = ap.parse_args()

@@ -1027,6 +1027,22 @@ __device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chun
   }
 }
 
+// Masses of cells as point sources, in each precision's array.
+template <typename T>
+struct LeafMass;
+template <>
+struct LeafMass<double> {
+  static __device__ __forceinline__ const double* get(const DevArgs& A) { return A.mtl; }
+};
+template <>
+struct LeafMass<float> {
+  static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.m32; }
+};
+template <>
+struct LeafMass<dfloat> {
+  static __device__ __forceinline__ const dfloat* get(const DevArgs& A) { return A.massff; }
+};
+
 // Leaf targets at a refinement boundary, 64 per block, from the pair lists built on the host:
 // multipole interactions with the cells of refined same-level neighbours, then direct sums with
 // point masses (the leaf children of refined near cells, and leaves one level coarser near the
@@ -1054,23 +1070,47 @@ __device__ void m2l_boundary(const DevArgs& A, int64_t first, int64_t end, int c
   load_target<T, false>(S, A, M, iA, amc);
   const T h = cell_h<T>(A.level[iA >> 9]);
   const T* __restrict__ td = LeafOffsets<T>::get(A) + int64_t(parity) * kLeafCap * 4;
-  const int32_t m1 = valid ? A.bm_off[k + 1] : 0;
-  for (int32_t j0 = (valid ? A.bm_off[k] : 0) + r; j0 < m1; j0 += LANES * kFlush) {
+  // each list entry's indices are loaded one entry ahead, so that a pair waits for its partner's
+  // moments only, not for the index that locates them first; point partners' masses come from
+  // the contiguous mass array (the same values as component 0 of the moments)
+  const T* __restrict__ Mass = LeafMass<T>::get(A);
+  const int32_t m0 = (valid ? A.bm_off[k] : 0) + r, m1 = valid ? A.bm_off[k + 1] : 0;
+  int q_next = 0;
+  int32_t src_next = 0;
+  if (m0 < m1) {
+    q_next = __ldg(A.bm_q + m0);
+    src_next = __ldg(A.bm_src + m0);
+  }
+  for (int32_t j0 = m0; j0 < m1; j0 += LANES * kFlush) {
     const int32_t j1 = min(j0 + LANES * kFlush, m1);
     for (int32_t j = j0; j < j1; j += LANES) {
-      const int q = __ldg(A.bm_q + j);
-      interact_lr<T>(S, M, N, __ldg(A.bm_src + j), -ldg_t(td + 4 * q) * h,
-                     -ldg_t(td + 4 * q + 1) * h, -ldg_t(td + 4 * q + 2) * h);
+      const int q = q_next;
+      const int32_t src = src_next;
+      if (j + LANES < m1) {
+        q_next = __ldg(A.bm_q + j + LANES);
+        src_next = __ldg(A.bm_src + j + LANES);
+      }
+      interact_lr<T>(S, M, N, src, -ldg_t(td + 4 * q) * h, -ldg_t(td + 4 * q + 1) * h,
+                     -ldg_t(td + 4 * q + 2) * h);
     }
     flush(S);
   }
-  const int32_t p1 = valid ? A.bp_off[k + 1] : 0;
-  for (int32_t j = (valid ? A.bp_off[k] : 0) + r; j < p1; j += LANES) {
-    const int32_t code = __ldg(A.bp_code + j);
+  const int32_t p0 = (valid ? A.bp_off[k] : 0) + r, p1 = valid ? A.bp_off[k + 1] : 0;
+  int32_t code_next = 0, psrc_next = 0;
+  if (p0 < p1) {
+    code_next = __ldg(A.bp_code + p0);
+    psrc_next = __ldg(A.bp_src + p0);
+  }
+  for (int32_t j = p0; j < p1; j += LANES) {
+    const int32_t code = code_next, src = psrc_next;
+    if (j + LANES < p1) {
+      code_next = __ldg(A.bp_code + j + LANES);
+      psrc_next = __ldg(A.bp_src + j + LANES);
+    }
     const T x = quarter[((code >> 20) & 1023) - 512 + kCodeMax] * h;
     const T y = quarter[((code >> 10) & 1023) - 512 + kCodeMax] * h;
     const T z = quarter[(code & 1023) - 512 + kCodeMax] * h;
-    interact_point<T, false>(S, mom_get(M, N, __ldg(A.bp_src + j), 0), x, y, z);
+    interact_point<T, false>(S, Mass[src], x, y, z);
   }
   if constexpr (LANES > 1) {
     lane_reduce<LANES>(S);  // the correction partials were flushed after the multipole pairs
@@ -1332,21 +1372,6 @@ __device__ __forceinline__ void load4(const double* p, double& a, double& b, dou
   c = w.x;
   d = w.y;
 }
-
-template <typename T>
-struct LeafMass;
-template <>
-struct LeafMass<double> {
-  static __device__ __forceinline__ const double* get(const DevArgs& A) { return A.mtl; }
-};
-template <>
-struct LeafMass<float> {
-  static __device__ __forceinline__ const float* get(const DevArgs& A) { return A.m32; }
-};
-template <>
-struct LeafMass<dfloat> {
-  static __device__ __forceinline__ const dfloat* get(const DevArgs& A) { return A.massff; }
-};
 
 template <typename T>
 struct LeafTab;
