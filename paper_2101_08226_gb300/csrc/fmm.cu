@@ -110,6 +110,8 @@ struct DevArgs {
   double* smom;            // [20][n_cell]
   double* smtl;            // [20][n_cell]
   float* smom32;           // [20][n_cell] FP32 copy of smtl (mixed path)
+  float* src32;            // [n_cell][28] the same, cell-major, then rho's centre-of-mass offset
+                           // (3) and 5 zeros: the staged kernel's records (mixed path)
   double* sloc;            // [20][n_cell]
   float* sloc32;           // [20][n_cell]
   double* root_part;       // [n_roots][kRootChunks][23][512] root partial sums (FP64 path)
@@ -1191,8 +1193,7 @@ constexpr int kStageThreads = 512;
 constexpr int kStageSY = 9;
 constexpr int kStageSX = 84;  // = 4 (mod 8), see above; 84 >= 9 * 9
 constexpr int kStageCells = 8 * kStageSX + 8 * kStageSY + 9;
-constexpr int kStageBufBytes = kStageCells * 80;
-constexpr int kStageSmem = 2 * kStageBufBytes;
+constexpr int kStageSmem = 2 * kStageCells * 80;  // two buffers of 20-float cells
 constexpr int kStageRuns = 243;  // per class: 9 x 9 lattice columns, each 3 runs along z
 constexpr long long kStageWaitCycles = 1ll << 31;  // about a second: then report and give up
 
@@ -1251,8 +1252,9 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 // Thread j < kStageRuns copies run j of class c into buf: lattice column (lx, ly) = (j / 27,
 // j / 3 % 9), z run j % 3 (halo z < 0, 0 <= z < 8, z >= 8), from the neighbour subgrid that
-// holds it; an absent neighbour (only without proper nesting) gives zeros.
-__device__ __forceinline__ void stage_issue(const DevArgs& A, const int32_t* nb, int c, float* buf,
+// holds it; an absent neighbour (only without proper nesting) gives zeros.  W floats per cell.
+template <int W>
+__device__ __forceinline__ void stage_issue(const float* __restrict__ arr, const int32_t* nb, int c, float* buf,
                                             uint64_t* bar, int j) {
   if (j >= kStageRuns) return;
   const int rx = (c >> 2) & 1, ry = (c >> 1) & 1, rz = c & 1;
@@ -1264,13 +1266,13 @@ __device__ __forceinline__ void stage_issue(const DevArgs& A, const int32_t* nb,
   const int lz1 = run == 0 ? z1 : (run == 1 ? z2 : 9);
   const int z = 2 * lz0 + rz - 5;
   const int32_t sB = nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)];
-  float* dst = buf + (lx * kStageSX + ly * kStageSY + lz0) * 20;
-  const uint32_t bytes = uint32_t(lz1 - lz0) * 80u;
+  float* dst = buf + (lx * kStageSX + ly * kStageSY + lz0) * W;
+  const uint32_t bytes = uint32_t(lz1 - lz0) * uint32_t(W * 4);
   if (sB >= 0) {
     // the run's cells are consecutive in the neighbour's parity-major order (cidx)
     const int64_t row = int64_t(sB) * kCells + cidx(x & 7, y & 7, z & 7);
     mbar_arrive_tx(bar, bytes);
-    bulk_g2s(dst, A.mom32 + row * 20, bytes, bar);
+    bulk_g2s(dst, arr + row * W, bytes, bar);
   } else {
     for (int k = 0; k < int(bytes / 4); ++k) dst[k] = 0.0f;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1278,15 +1280,35 @@ __device__ __forceinline__ void stage_issue(const DevArgs& A, const int32_t* nb,
   }
 }
 
+template <typename T, bool AREF>
+__device__ __forceinline__ void src_far(T* L, T s0, T s1x, T s1y, T s1z, const T* S2, const T* S3,
+                                        T x, T y, T z);
+__device__ __forceinline__ void store_src_expansion(const DevArgs& A, int64_t i, const float* L, int n);
+
+// Record width per cell of the staged arrays: the FP32 moments (20 floats) or, for the
+// time-derivative solve, the source moments S0, S1, S2', S3' followed by rho's centre-of-mass
+// offset (28 floats, padded so that 7 w mod 8 over a quarter warp's cells stays distinct:
+// 7 (ic + 84 ia) mod 8 = {0, 7, 6, 5} + {0, 4}).
+template <bool SRC>
+struct StageW {
+  static constexpr int W = SRC ? 28 : 20;
+  static constexpr int kBufBytes = kStageCells * W * 4;
+};
+constexpr int kStageSmemSrc = 2 * StageW<true>::kBufBytes;
+
 // One block per refined subgrid of a level >= 1 (the list `subs`): the same pairs and
-// correction as m2l_level<float>, with the partners read from shared memory.
+// correction as m2l_level<float>, with the partners read from shared memory.  SRC: the
+// time-derivative solve's source expansions of the same targets (as m2l_level_src<float>).
+template <bool SRC>
 __global__ void __launch_bounds__(kStageThreads, 1) k_m2l_stage(DevArgs A, const int32_t* __restrict__ subs,
                                                                  int amc) {
+  constexpr int W = StageW<SRC>::W;
   extern __shared__ __align__(128) unsigned char stage_smem[];
   float* buf0 = reinterpret_cast<float*>(stage_smem);
-  float* buf1 = reinterpret_cast<float*>(stage_smem + kStageBufBytes);
+  float* buf1 = reinterpret_cast<float*>(stage_smem + StageW<SRC>::kBufBytes);
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int32_t nb[27];
+  const float* __restrict__ arr = SRC ? A.src32 : A.mom32;
   const int32_t s = subs[blockIdx.x];
   const int t = threadIdx.x;
   if (t < 27) nb[t] = A.nbr[27 * s + t];
@@ -1301,13 +1323,22 @@ __global__ void __launch_bounds__(kStageThreads, 1) k_m2l_stage(DevArgs A, const
   const int a = 2 * ia + ((parity >> 2) & 1), b = 2 * ib + ((parity >> 1) & 1), c = 2 * ic + (parity & 1);
   const int64_t iA = int64_t(s) * kCells + cidx(a, b, c);
   Target<float, true> S;
-  load_target<float, true>(S, A, A.mom32, iA, amc != 0);
+  float Ls[SRC ? 20 : 1];
+  if constexpr (SRC) {
+#pragma unroll
+    for (int k = 0; k < 20; ++k) Ls[k] = 0.0f;
+    S.dAx = A.mom32[iA * 20 + 1];
+    S.dAy = A.mom32[iA * 20 + 2];
+    S.dAz = A.mom32[iA * 20 + 3];
+  } else {
+    load_target<float, true>(S, A, A.mom32, iA, amc != 0);
+  }
   const float h = cell_h<float>(A.level[s]);
-  const int base = (ia * kStageSX + ib * kStageSY + ic) * 20;
+  const int base = (ia * kStageSX + ib * kStageSY + ic) * W;
   const float4* __restrict__ tab = A.stage_tab + parity * kLeafCap;
   const int32_t* __restrict__ seg = A.stage_seg + parity * 9;
   __syncthreads();
-  stage_issue(A, nb, 0, buf0, &bar[0], t);
+  stage_issue<W>(arr, nb, 0, buf0, &bar[0], t);
   for (int cl = 0; cl < 8; ++cl) {
     const bool ok = mbar_wait_bounded(&bar[cl & 1], uint32_t((cl >> 1) & 1), A.wait_cycles);
     // block-uniform decision; also makes the zero fills of class cl visible and frees the other
@@ -1319,7 +1350,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) k_m2l_stage(DevArgs A, const
       mbar_wait_bounded(&bar[cl & 1], uint32_t((cl >> 1) & 1), kStageWaitCycles);
       return;
     }
-    if (cl < 7) stage_issue(A, nb, cl + 1, (cl & 1) ? buf0 : buf1, &bar[(cl + 1) & 1], t);
+    if (cl < 7) stage_issue<W>(arr, nb, cl + 1, (cl & 1) ? buf0 : buf1, &bar[(cl + 1) & 1], t);
     const float* __restrict__ B = ((cl & 1) ? buf1 : buf0) + base;
     const int q1 = __ldg(seg + cl + 1);
     const int qb = __ldg(seg + cl);
@@ -1329,23 +1360,33 @@ __global__ void __launch_bounds__(kStageThreads, 1) k_m2l_stage(DevArgs A, const
       for (int q = q0; q < qe; ++q) {
         const float4 e = e_next;
         e_next = __ldg(tab + min(q + 1, q1 - 1));
-        const float4* m = reinterpret_cast<const float4*>(B + __float_as_int(e.w) * 20);
-        float Mv[20];
+        const float4* m = reinterpret_cast<const float4*>(B + __float_as_int(e.w) * W);
+        float Mv[W];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < W / 4; ++k) {
           const float4 v = m[k];
           Mv[4 * k] = v.x;
           Mv[4 * k + 1] = v.y;
           Mv[4 * k + 2] = v.z;
           Mv[4 * k + 3] = v.w;
         }
-        interact_rr_v<float>(S, Mv, fmaf(-e.x, h, S.dAx), fmaf(-e.y, h, S.dAy), fmaf(-e.z, h, S.dAz));
+        const float x = fmaf(-e.x, h, S.dAx), y = fmaf(-e.y, h, S.dAy), z = fmaf(-e.z, h, S.dAz);
+        if constexpr (SRC)
+          src_far<float, true>(Ls, Mv[0], Mv[1], Mv[2], Mv[3], Mv + 4, Mv + 10, x - Mv[20], y - Mv[21],
+                               z - Mv[22]);
+        else
+          interact_rr_v<float>(S, Mv, x, y, z);
       }
-      flush(S);
+      if constexpr (!SRC) flush(S);
     }
   }
-  finish_rr(S);
-  store_own<float, true>(A, S, iA);
+  if constexpr (SRC) {
+    complete_traceless(Ls);
+    store_src_expansion(A, iA, Ls, 20);
+  } else {
+    finish_rr(S);
+    store_own<float, true>(A, S, iA);
+  }
 }
 
 // Four consecutive table values (16-byte aligned) in vector loads.
@@ -1924,6 +1965,11 @@ __device__ __forceinline__ void store_src_moments(const DevArgs& A, int64_t cell
   if (mixed) {
 #pragma unroll
     for (int k = 0; k < 20; ++k) A.smom32[k * N + cell] = float(T[k]);
+    float4* r = reinterpret_cast<float4*>(A.src32 + cell * 28);
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+      r[q] = make_float4(float(T[4 * q]), float(T[4 * q + 1]), float(T[4 * q + 2]), float(T[4 * q + 3]));
+    r[5] = make_float4(float(A.mom[N + cell]), float(A.mom[2 * N + cell]), float(A.mom[3 * N + cell]), 0.0f);
   }
 }
 
@@ -1944,7 +1990,10 @@ __global__ void k_p2m_src(DevArgs A, int mixed) {
   const double m = v * cell_vol(A.level[s]);
   A.smom[cell] = m;
   A.smtl[cell] = m;
-  if (mixed) A.smom32[cell] = float(m);
+  if (mixed) {
+    A.smom32[cell] = float(m);
+    A.src32[cell * 28] = float(m);  // a leaf's centre of mass is its centre: offset zero
+  }
 }
 
 // Source moments of the refined cells of one level, one thread per parent cell, 64 per block
@@ -2033,54 +2082,62 @@ __global__ void __launch_bounds__(64) k_m2m_src(DevArgs A, const int32_t* __rest
 //   L3 -= S0 (g3 R R R + g2 sym(R I)).
 // AREF: all 20 components (targets with children; L2, L3 as 12 independent components); else
 // L0 only.  BREF: the source has children (full moments); else a point source.
+// A source cell with children (S0, dipole S1, detraced S2, S3) at separation R = (x, y, z) from
+// the target's expansion centre.
+template <typename T, bool AREF>
+__device__ __forceinline__ void src_far(T* L, T s0, T s1x, T s1y, T s1z, const T* S2, const T* S3,
+                                        T x, T y, T z) {
+  Radial<T> g;
+  g.set(x, y, z, 3);
+  const T q2x = S2[0] * x + S2[1] * y + S2[2] * z;
+  const T q2y = S2[1] * x + S2[3] * y + S2[4] * z;
+  const T q2z = S2[2] * x + S2[4] * y + S2[5] * z;
+  const T rs2r = x * q2x + y * q2y + z * q2z;
+  const T rs1 = x * s1x + y * s1y + z * s1z;
+  T qx, qy, qz;
+  sym3_rr(S3, x, y, z, qx, qy, qz);
+  const T rrr = x * qx + y * qy + z * qz;
+  L[0] -= s0 * g.g0 - g.g1 * rs1 + T(0.5) * g.g2 * rs2r - T(1.0 / 6.0) * g.g3 * rrr;
+  if constexpr (AREF) {
+    const T c1 = s0 * g.g1 - g.g2 * rs1 + T(0.5) * g.g3 * rs2r;
+    L[1] -= c1 * x - g.g1 * s1x + g.g2 * q2x;
+    L[2] -= c1 * y - g.g1 * s1y + g.g2 * q2y;
+    L[3] -= c1 * z - g.g1 * s1z + g.g2 * q2z;
+    const T c2 = s0 * g.g2 - g.g3 * rs1, c0 = s0 * g.g1 - g.g2 * rs1, e = g.g2;
+    L[4] -= c2 * x * x + c0 - T(2) * e * x * s1x;
+    L[5] -= c2 * x * y - e * (x * s1y + s1x * y);
+    L[6] -= c2 * x * z - e * (x * s1z + s1x * z);
+    L[7] -= c2 * y * y + c0 - T(2) * e * y * s1y;
+    L[8] -= c2 * y * z - e * (y * s1z + s1y * z);
+    // L3 from S0 alone: the L3 part of m2l_high
+    const T a2 = s0 * g.g2, a3 = s0 * g.g3;
+    const T a2x = a2 * x, a2y = a2 * y, a2z = a2 * z, a3xx = a3 * x * x, a3yy = a3 * y * y;
+    L[10] -= a3xx * x + T(3) * a2x;
+    L[11] -= a3xx * y + a2y;
+    L[12] -= a3xx * z + a2z;
+    L[13] -= a3yy * x + a2x;
+    L[14] -= a3 * x * y * z;
+    L[16] -= a3yy * y + T(3) * a2y;
+    L[17] -= a3yy * z + a2z;
+  }
+}
+
 template <typename T, bool AREF, bool BREF>
 __device__ __forceinline__ void interact_src(T* L, const T* __restrict__ Sm, const T* __restrict__ G,
                                              int64_t N, int64_t iB, T x, T y, T z) {
   const T s0 = Sm[iB];
-  Radial<T> g;
   if constexpr (BREF) {
     x -= mom_get(G, N, iB, 1);
     y -= mom_get(G, N, iB, 2);
     z -= mom_get(G, N, iB, 3);
-    g.set(x, y, z, 3);
-    const T s1x = Sm[N + iB], s1y = Sm[2 * N + iB], s1z = Sm[3 * N + iB];
     T S2[6], S3[10];
 #pragma unroll
     for (int k = 0; k < 6; ++k) S2[k] = Sm[(4 + k) * N + iB];
 #pragma unroll
     for (int k = 0; k < 10; ++k) S3[k] = Sm[(10 + k) * N + iB];
-    const T q2x = S2[0] * x + S2[1] * y + S2[2] * z;
-    const T q2y = S2[1] * x + S2[3] * y + S2[4] * z;
-    const T q2z = S2[2] * x + S2[4] * y + S2[5] * z;
-    const T rs2r = x * q2x + y * q2y + z * q2z;
-    const T rs1 = x * s1x + y * s1y + z * s1z;
-    T qx, qy, qz;
-    sym3_rr(S3, x, y, z, qx, qy, qz);
-    const T rrr = x * qx + y * qy + z * qz;
-    L[0] -= s0 * g.g0 - g.g1 * rs1 + T(0.5) * g.g2 * rs2r - T(1.0 / 6.0) * g.g3 * rrr;
-    if constexpr (AREF) {
-      const T c1 = s0 * g.g1 - g.g2 * rs1 + T(0.5) * g.g3 * rs2r;
-      L[1] -= c1 * x - g.g1 * s1x + g.g2 * q2x;
-      L[2] -= c1 * y - g.g1 * s1y + g.g2 * q2y;
-      L[3] -= c1 * z - g.g1 * s1z + g.g2 * q2z;
-      const T c2 = s0 * g.g2 - g.g3 * rs1, c0 = s0 * g.g1 - g.g2 * rs1, e = g.g2;
-      L[4] -= c2 * x * x + c0 - T(2) * e * x * s1x;
-      L[5] -= c2 * x * y - e * (x * s1y + s1x * y);
-      L[6] -= c2 * x * z - e * (x * s1z + s1x * z);
-      L[7] -= c2 * y * y + c0 - T(2) * e * y * s1y;
-      L[8] -= c2 * y * z - e * (y * s1z + s1y * z);
-      // L3 from S0 alone: the L3 part of m2l_high
-      const T a2 = s0 * g.g2, a3 = s0 * g.g3;
-      const T a2x = a2 * x, a2y = a2 * y, a2z = a2 * z, a3xx = a3 * x * x, a3yy = a3 * y * y;
-      L[10] -= a3xx * x + T(3) * a2x;
-      L[11] -= a3xx * y + a2y;
-      L[12] -= a3xx * z + a2z;
-      L[13] -= a3yy * x + a2x;
-      L[14] -= a3 * x * y * z;
-      L[16] -= a3yy * y + T(3) * a2y;
-      L[17] -= a3yy * z + a2z;
-    }
+    src_far<T, AREF>(L, s0, Sm[N + iB], Sm[2 * N + iB], Sm[3 * N + iB], S2, S3, x, y, z);
   } else {
+    Radial<T> g;
     g.set(x, y, z, AREF ? 3 : 0);
     L[0] -= s0 * g.g0;
     if constexpr (AREF) {
@@ -2138,8 +2195,9 @@ __device__ void m2l_level_src(const DevArgs& A, int32_t s, int parity, int t) {
 
 // Root level: every well-separated root pair (all pairs, directly, when the root is a leaf),
 // sources in kRootChunks chunks whose partial sums the downward pass adds in a fixed order.
-template <typename T, bool AREF>
-__device__ void m2l_root_src(const DevArgs& A, int root, int parity, int t, int chunk) {
+// LANES lanes per target (as m2l_root): lane r takes rows jy in [r 8 / LANES, (r + 1) 8 / LANES).
+template <typename T, bool AREF, int LANES = 1>
+__device__ void m2l_root_src(const DevArgs& A, int root, int parity, int t, int chunk, int r = 0) {
   const T* __restrict__ G = MomView<T>::get(A);
   const T* __restrict__ Sm = SrcView<T>::get(A);
   const int64_t N = A.n_cell;
@@ -2155,9 +2213,11 @@ __device__ void m2l_root_src(const DevArgs& A, int root, int parity, int t, int 
   const T h = cell_h<T>(0);
   const int dx = chunk - a;
   const T rx0 = dAx - T(dx) * h;
-  T ry = dAy + T(b) * h;
+  constexpr int kRows = 8 / LANES;
+  const int jy0 = r * kRows;
+  T ry = dAy + T(b - jy0) * h;
   const T rz0 = dAz + T(c) * h;
-  for (int jy = 0; jy < 8; ++jy, ry -= h) {
+  for (int jy = jy0; jy < jy0 + kRows; ++jy, ry -= h) {
     T rz = rz0;
     for (int jz = 0; jz < 8; ++jz, rz -= h) {
       const int j = cidx(chunk, jy, jz);
@@ -2166,6 +2226,13 @@ __device__ void m2l_root_src(const DevArgs& A, int root, int parity, int t, int 
       if (AREF && !(dx * dx + dy * dy + dz * dz > A.ws_d2)) continue;
       interact_src<T, AREF, AREF>(L, Sm, G, N, base + j, rx0, ry, rz);
     }
+  }
+  if constexpr (LANES > 1) {
+#pragma unroll
+    for (int m = 1; m < LANES; m <<= 1)
+#pragma unroll
+      for (int k = 0; k < (AREF ? 20 : 1); ++k) L[k] += __shfl_xor_sync(0xffffffffu, L[k], m);
+    if (r != 0) return;
   }
   if constexpr (AREF) complete_traceless(L);
   // partials: [chunk][component][cell]
@@ -2180,14 +2247,17 @@ __device__ void m2l_root_src(const DevArgs& A, int root, int parity, int t, int 
 
 // Leaf targets at refinement boundaries from the pair lists: multipole partners (refined) and
 // point partners; adds L0 onto the source leaf kernel's output.
-template <typename T>
-__device__ void m2l_boundary_src(const DevArgs& A, int chunk, int t) {
+// The block's targets are first + 64 chunk + t, those below end; LANES lanes per target (as
+// m2l_boundary), every lane of the block calls this.
+template <typename T, int LANES = 1>
+__device__ void m2l_boundary_src(const DevArgs& A, int64_t first, int64_t end, int chunk, int t, int r = 0) {
   __shared__ T quarter[2 * kCodeMax + 1];
   for (int i = threadIdx.x; i <= 2 * kCodeMax; i += blockDim.x) quarter[i] = T(i - kCodeMax) * T(0.25);
   __syncthreads();
-  const int64_t k = int64_t(chunk) * 64 + t;
-  if (k >= A.n_bt) return;
-  const int64_t iA = A.bt_cell[k];
+  const int64_t k = first + int64_t(chunk) * 64 + t;
+  const bool valid = k < end;
+  if (LANES == 1 && !valid) return;
+  const int64_t iA = valid ? A.bt_cell[k] : 0;
   const int parity = int(iA & 511) >> 6;
   const T* __restrict__ G = MomView<T>::get(A);
   const T* __restrict__ Sm = SrcView<T>::get(A);
@@ -2195,17 +2265,24 @@ __device__ void m2l_boundary_src(const DevArgs& A, int chunk, int t) {
   const T h = cell_h<T>(A.level[iA >> 9]);
   const T* __restrict__ td = LeafOffsets<T>::get(A) + int64_t(parity) * kLeafCap * 4;
   T L[1] = {T(0)};
-  for (int32_t j = A.bm_off[k]; j < A.bm_off[k + 1]; ++j) {
+  const int32_t m1 = valid ? A.bm_off[k + 1] : 0;
+  for (int32_t j = (valid ? A.bm_off[k] : 0) + r; j < m1; j += LANES) {
     const int q = __ldg(A.bm_q + j);
     interact_src<T, false, true>(L, Sm, G, N, __ldg(A.bm_src + j), -ldg_t(td + 4 * q) * h,
                                  -ldg_t(td + 4 * q + 1) * h, -ldg_t(td + 4 * q + 2) * h);
   }
-  for (int32_t j = A.bp_off[k]; j < A.bp_off[k + 1]; ++j) {
+  const int32_t p1 = valid ? A.bp_off[k + 1] : 0;
+  for (int32_t j = (valid ? A.bp_off[k] : 0) + r; j < p1; j += LANES) {
     const int32_t code = __ldg(A.bp_code + j);
     interact_src<T, false, false>(L, Sm, G, N, __ldg(A.bp_src + j),
                                   quarter[((code >> 20) & 1023) - 512 + kCodeMax] * h,
                                   quarter[((code >> 10) & 1023) - 512 + kCodeMax] * h,
                                   quarter[(code & 1023) - 512 + kCodeMax] * h);
+  }
+  if constexpr (LANES > 1) {
+#pragma unroll
+    for (int m = 1; m < LANES; m <<= 1) L[0] += __shfl_xor_sync(0xffffffffu, L[0], m);
+    if (r != 0 || !valid) return;
   }
   if (sizeof(T) == 8) A.sloc[iA] += double(L[0]);
   else A.sloc32[iA] += float(L[0]);
@@ -2224,7 +2301,26 @@ __global__ void __launch_bounds__(NT) k_m2l_ref_src(DevArgs A, const int32_t* __
   } else if (kind == 1) {
     m2l_level_src<T>(A, idx, parity, t);
   } else {
-    m2l_boundary_src<T>(A, idx, t);
+    m2l_boundary_src<T>(A, 0, A.n_bt, idx, t);
+  }
+}
+
+// The time-derivative solve's root and boundary work for the mixed path (its refined subgrids
+// go to k_m2l_stage<true>), with k_m2l_split's block list and lanes.
+template <typename T>
+__global__ void __launch_bounds__(64 * kSplitLanes) k_m2l_split_src(DevArgs A, const int32_t* __restrict__ blocks) {
+  const int32_t code = blocks[blockIdx.x];
+  const int kind = (code >> 30) & 3, idx = code & ((1 << 27) - 1);
+  const int parity = (code >> 27) & 7;
+  const int t = int(threadIdx.x) / kSplitLanes, r = int(threadIdx.x) % kSplitLanes;
+  if (kind == 0) {
+    const int root = idx >> 3, chunk = idx & 7;
+    if (A.leaf[root]) m2l_root_src<T, false, kSplitLanes>(A, root, parity, t, chunk, r);
+    else m2l_root_src<T, true, kSplitLanes>(A, root, parity, t, chunk, r);
+  } else if (kind == 2) {
+    m2l_boundary_src<T, kSplitLanes>(A, 0, A.n_bt_long, idx, t, r);
+  } else {
+    m2l_boundary_src<T, 1>(A, A.n_bt_long, A.n_bt, idx + int(threadIdx.x) / 64, int(threadIdx.x) % 64);
   }
 }
 
@@ -2492,7 +2588,7 @@ struct fmm_tree {
   bool df_ready = false;
   dfloat *d_momff = nullptr, *d_massff = nullptr;
   double *d_smom = nullptr, *d_smtl = nullptr, *d_sloc = nullptr;
-  float *d_smom32 = nullptr, *d_sloc32 = nullptr;
+  float *d_smom32 = nullptr, *d_sloc32 = nullptr, *d_src32 = nullptr;
   std::map<double, StencilDev> stencils;
   bool profiling = false;
   cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -2662,7 +2758,8 @@ static int ensure_mixed(fmm_tree* t) {
   const int64_t nr = t->h.n_trees;
   CUDA_TRY(dalloc(t, &t->d_root_part32, sizeof(float) * nr * kRootChunks * 20 * kCells));
   CUDA_TRY(dalloc(t, &t->d_root_part_ac, sizeof(double) * nr * kRootChunks * 3 * kCells));
-  CUDA_TRY(cudaFuncSetAttribute(k_m2l_stage, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageSmem));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_stage<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageSmem));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_stage<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageSmemSrc));
   t->mixed_ready = true;
   return FMM_OK;
 }
@@ -2691,6 +2788,8 @@ static int ensure_src(fmm_tree* t, bool mixed) {
     CUDA_TRY(dalloc(t, &t->d_smom32, sizeof(float) * kNMom * nc));
     CUDA_TRY(cudaMemset(t->d_smom32, 0, sizeof(float) * kNMom * nc));
     CUDA_TRY(dalloc(t, &t->d_sloc32, sizeof(float) * 20 * nc));
+    CUDA_TRY(dalloc(t, &t->d_src32, sizeof(float) * 28 * nc));
+    CUDA_TRY(cudaMemset(t->d_src32, 0, sizeof(float) * 28 * nc));  // leaf cells keep zeros
     t->src32_ready = true;
   }
   return FMM_OK;
@@ -3085,6 +3184,7 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.smom = t->d_smom;
   A.smtl = t->d_smtl;
   A.smom32 = t->d_smom32;
+  A.src32 = t->d_src32;
   A.sloc = t->d_sloc;
   A.sloc32 = t->d_sloc32;
   A.n_bt = sd ? sd->n_bt : 0;
@@ -3211,7 +3311,7 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
     CUDA_TRY(cudaEventRecord(t->ev_fork, st));
     CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_fork, 0));
     if ((rc = record(t, 6, t->stream2))) return rc;
-    k_m2l_stage<<<unsigned(t->work.size()), kStageThreads, kStageSmem, t->stream2>>>(A, t->d_work, amc);
+    k_m2l_stage<false><<<unsigned(t->work.size()), kStageThreads, kStageSmem, t->stream2>>>(A, t->d_work, amc);
     CUDA_TRY(cudaGetLastError());
     ++nl;
     if ((rc = record(t, 7, t->stream2))) return rc;
@@ -3246,7 +3346,7 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
       ++nl;
     }
     if (staged && !fork) {
-      k_m2l_stage<<<unsigned(t->work.size()), kStageThreads, kStageSmem, st>>>(A, t->d_work, amc);
+      k_m2l_stage<false><<<unsigned(t->work.size()), kStageThreads, kStageSmem, st>>>(A, t->d_work, amc);
       CUDA_TRY(cudaGetLastError());
       ++nl;
     }
@@ -3295,6 +3395,17 @@ static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream
     CUDA_TRY(cudaGetLastError());
     ++*nl;
   }
+  // mixed path: the refined subgrids by the staging kernel on the second stream, the leaf and
+  // the root and boundary kernels on this one (as in the rho solve)
+  const bool fork = mixed && !t->work.empty();
+  if (fork) {
+    CUDA_TRY(cudaEventRecord(t->ev_fork, st));
+    CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_fork, 0));
+    k_m2l_stage<true><<<unsigned(t->work.size()), kStageThreads, kStageSmemSrc, t->stream2>>>(A, t->d_work, 0);
+    CUDA_TRY(cudaGetLastError());
+    ++*nl;
+    CUDA_TRY(cudaEventRecord(t->ev_join, t->stream2));
+  }
   if (t->n_work_leaf > 0) {
     if (mixed)
       k_m2l_leaf4<true><<<unsigned((t->n_work_leaf + 1) / 2), kLeaf4Threads, kLeaf4Smem, st>>>(
@@ -3305,10 +3416,11 @@ static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream
     CUDA_TRY(cudaGetLastError());
     ++*nl;
   }
-  if (mixed) k_m2l_ref_src<float, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks);
+  if (mixed) k_m2l_split_src<float><<<unsigned(sd->n_blocks_split), 64 * kSplitLanes, 0, st>>>(A, sd->d_blocks_split);
   else k_m2l_ref_src<double, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks);
   CUDA_TRY(cudaGetLastError());
   ++*nl;
+  if (fork) CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
   if (mixed) k_root_total<true, true><<<blocks_for(int64_t(h.n_trees) * kRootComps * kCells, 128), 128, 0, st>>>(A);
   else k_root_total<false, true><<<blocks_for(int64_t(h.n_trees) * kRootComps * kCells, 128), 128, 0, st>>>(A);
   CUDA_TRY(cudaGetLastError());
