@@ -527,10 +527,13 @@ def run_ours(args):
     def phases(ph, precision="fp64"):
         out = {"upward": float(ph[0]), "interactions": float(ph[1]), "downward": float(ph[2]),
                "reductions": float(ph[3])}
+        # the leaf kernel runs on the tree's second stream from the end of the first upward step
+        # (it overlaps "upward"); "after_leaf_kernel" runs from its end to the end of the
+        # interactions
         if precision == "mixed":
-            # leaf kernel, then root and boundary kernel, on the tree's stream; refined targets
-            # on the second stream at the same time
-            out.update({"k_m2l_leaf": float(ph[5]), "k_m2l_split_and_join": float(ph[4]),
+            # refined targets (k_m2l_stage) on the tree's stream after the upward pass, the root
+            # and boundary kernel on the second stream after the leaf kernel
+            out.update({"k_m2l_leaf": float(ph[5]), "after_leaf_kernel": float(ph[4]),
                         "k_m2l_stage": float(ph[6])})
         else:
             out.update({"k_m2l_ref": float(ph[4]), "k_m2l_leaf": float(ph[5])})

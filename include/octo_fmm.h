@@ -222,13 +222,13 @@ int fmm_set_wait_limit(fmm_tree* tree, long long cycles);
 int fmm_set_graphs(fmm_tree* tree, int on);
 
 /* Per-phase device times (ms) of the most recent solve on this tree, measured with CUDA events
- * when profiling is on: [0] upward pass, [1] multipole interactions and near field, [2]
- * downward pass, [3] reductions, [4] from the end of the leaf-cell interaction kernel to the
- * end of the interaction phase (FP64 and df64: the kernel of refined cells, the root level and
- * boundary leaves; mixed: the root and boundary kernel, then the wait for the refined cells'
- * kernel), [5] the interaction kernel of leaf cells, [6] mixed only (else 0): the refined
- * cells' kernel, which runs on a second stream beside [5] and [4].  Writes min(n, 7) values.
- * fmm_set_profiling(tree, 1) turns it on. */
+ * when profiling is on: [0] upward pass, [1] interactions after the upward pass, [2] downward
+ * pass, [3] reductions, [4] from the end of the leaf-cell interaction kernel to the end of the
+ * interactions (FP64 and df64: the kernel of refined cells, the root level and boundary leaves;
+ * mixed: the root and boundary kernel, and the wait for the refined cells' kernel), [5] the
+ * leaf-cell interaction kernel, which runs on a second stream from the end of the first upward
+ * step (so it overlaps [0]), [6] mixed only (else 0): the refined cells' kernel.  Writes
+ * min(n, 7) values.  fmm_set_profiling(tree, 1) turns it on. */
 int fmm_set_profiling(fmm_tree* tree, int on);
 int fmm_phase_times(fmm_tree* tree, float* ms_host, int n);
 

@@ -2591,10 +2591,12 @@ struct fmm_tree {
   float *d_smom32 = nullptr, *d_sloc32 = nullptr, *d_src32 = nullptr;
   std::map<double, StencilDev> stencils;
   bool profiling = false;
-  cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  // mixed path: k_m2l_stage runs on stream2, forked from and joined back to the tree's stream
+  cudaEvent_t ev[10] = {nullptr, nullptr, nullptr, nullptr, nullptr,
+                        nullptr, nullptr, nullptr, nullptr, nullptr};
+  // a second stream, forked from and joined back to the tree's stream inside a solve: the leaf
+  // kernel beside the upward pass, and the mixed path's root and boundary kernel
   cudaStream_t stream2 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_m2m = nullptr;
   bool ev_recorded = false;
   bool ev_stage = false;  // the recorded solve ran k_m2l_stage between ev[6] and ev[7]
   int32_t launches = 0;
@@ -2741,6 +2743,7 @@ static int ensure_device(fmm_tree* t) {
   CUDA_TRY(cudaStreamCreateWithFlags(&t->stream2, cudaStreamNonBlocking));
   CUDA_TRY(cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&t->ev_m2m, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&t->ev_in, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&t->ev_out, cudaEventDisableTiming));
   for (auto& e : t->ev) CUDA_TRY(cudaEventCreate(&e));
@@ -3278,6 +3281,30 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   k_p2m<<<blocks_for(A.n_leaf_cells, 256), 256, 0, st>>>(A, mode);
   CUDA_TRY(cudaGetLastError());
   ++nl;
+  // The same-level leaf pairs need only the leaf masses: their kernel runs on the second stream
+  // from here, beside the level-by-level (latency-bound) upward pass.
+  const int v_ref = sd->mixed_variant % 3, v_leaf = sd->mixed_variant / 3;
+  CUDA_TRY(cudaEventRecord(t->ev_fork, st));
+  CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_fork, 0));
+  if ((rc = record(t, 8, t->stream2))) return rc;
+  if (t->n_work_leaf > 0) {
+    cudaStream_t s2 = t->stream2;
+    if (mixed && v_leaf == 0)
+      k_m2l_leaf4<false><<<unsigned((t->n_work_leaf + 1) / 2), kLeaf4Threads, kLeaf4Smem, s2>>>(
+          A, t->d_work_leaf, t->n_work_leaf);
+    else if (mixed)
+      k_m2l_leaf<float, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), s2>>>(
+          A, t->d_work_leaf);
+    else if (df)
+      k_m2l_leaf<dfloat, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(dfloat), s2>>>(
+          A, t->d_work_leaf);
+    else
+      k_m2l_leaf<double, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(double), s2>>>(
+          A, t->d_work_leaf);
+    CUDA_TRY(cudaGetLastError());
+    ++nl;
+  }
+  if ((rc = record(t, 9, t->stream2))) return rc;
   // octants whose children are leaves need only the leaf masses: every level's in one launch;
   // then the octants with refined children, finest level first
   const int64_t n_walsh = t->oct_leaf_off[h.depth + 1];
@@ -3297,67 +3324,50 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   }
 
   if ((rc = record(t, 1, st))) return rc;
-  // interactions: leaf subgrids of levels >= 1 (same-level leaf partners), then the general
-  // kernel: root chunks, every (refined subgrid, parity) and every (boundary leaf subgrid, parity).
-  // Mixed path, by the launch variant of this tree and theta (kMixedVariants): the refined
-  // subgrids go to k_m2l_stage on a second stream beside the leaf and general kernels (one block
-  // per SM leaves room for theirs), or after them on the same stream, or to k_m2l_ref's
-  // per-parity blocks reading their partners from L2; the leaf pairs to k_m2l_leaf4 or
-  // k_m2l_leaf<float>.
-  const int v_ref = sd->mixed_variant % 3, v_leaf = sd->mixed_variant / 3;
+  // interactions of refined targets, the root level and boundary leaf targets (these add onto
+  // the leaf kernel's output, so they follow it).  Mixed path, by the launch variant of this
+  // tree and theta (kMixedVariants): refined subgrids by k_m2l_stage on this stream while the
+  // root and boundary kernel follows the leaf kernel on the second (one staging block per SM
+  // leaves room for theirs), or both on this stream, or by k_m2l_ref's per-parity blocks
+  // reading their partners from L2; the leaf pairs by k_m2l_leaf4 or k_m2l_leaf<float>.
   const bool staged = mixed && !t->work.empty() && v_ref != 2;
-  const bool fork = staged && v_ref == 0;
-  if (fork) {
-    CUDA_TRY(cudaEventRecord(t->ev_fork, st));
-    CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_fork, 0));
-    if ((rc = record(t, 6, t->stream2))) return rc;
-    k_m2l_stage<false><<<unsigned(t->work.size()), kStageThreads, kStageSmem, t->stream2>>>(A, t->d_work, amc);
-    CUDA_TRY(cudaGetLastError());
-    ++nl;
-    if ((rc = record(t, 7, t->stream2))) return rc;
-    CUDA_TRY(cudaEventRecord(t->ev_join, t->stream2));
-  }
-  if (t->n_work_leaf > 0) {
-    if (mixed && v_leaf == 0)
-      k_m2l_leaf4<false><<<unsigned((t->n_work_leaf + 1) / 2), kLeaf4Threads, kLeaf4Smem, st>>>(
-          A, t->d_work_leaf, t->n_work_leaf);
-    else if (mixed)
-      k_m2l_leaf<float, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), st>>>(
-          A, t->d_work_leaf);
-    else if (df)
-      k_m2l_leaf<dfloat, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(dfloat), st>>>(
-          A, t->d_work_leaf);
-    else
-      k_m2l_leaf<double, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(double), st>>>(
-          A, t->d_work_leaf);
-    CUDA_TRY(cudaGetLastError());
-    ++nl;
-  }
-  if ((rc = record(t, 5, st))) return rc;
-  if (mixed && v_ref == 2) {
-    k_m2l_ref<float, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
-    CUDA_TRY(cudaGetLastError());
-    ++nl;
-  } else if (mixed) {
-    // root and boundary blocks here; refined subgrids on the second stream, or after these
+  const bool split2 = staged && v_ref == 0;  // root and boundary kernel on the second stream
+  if (split2) {
+    CUDA_TRY(cudaEventRecord(t->ev_m2m, st));
+    CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_m2m, 0));
     if (sd->n_blocks_split > 0) {
-      k_m2l_split<float><<<unsigned(sd->n_blocks_split), 64 * kSplitLanes, 0, st>>>(A, sd->d_blocks_split, amc);
+      k_m2l_split<float><<<unsigned(sd->n_blocks_split), 64 * kSplitLanes, 0, t->stream2>>>(
+          A, sd->d_blocks_split, amc);
       CUDA_TRY(cudaGetLastError());
       ++nl;
     }
-    if (staged && !fork) {
-      k_m2l_stage<false><<<unsigned(t->work.size()), kStageThreads, kStageSmem, st>>>(A, t->d_work, amc);
-      CUDA_TRY(cudaGetLastError());
-      ++nl;
-    }
-    if (fork) CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
-  } else {
-    if (df)
-      k_m2l_ref<dfloat, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
-    else
-      k_m2l_ref<double, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
+  }
+  CUDA_TRY(cudaEventRecord(t->ev_join, t->stream2));
+  if (split2) {
+    if ((rc = record(t, 6, st))) return rc;
+    k_m2l_stage<false><<<unsigned(t->work.size()), kStageThreads, kStageSmem, st>>>(A, t->d_work, amc);
     CUDA_TRY(cudaGetLastError());
     ++nl;
+    if ((rc = record(t, 7, st))) return rc;
+    CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
+  } else {
+    CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
+    if (mixed && v_ref == 2) {
+      k_m2l_ref<float, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
+    } else if (mixed) {
+      k_m2l_split<float><<<unsigned(sd->n_blocks_split), 64 * kSplitLanes, 0, st>>>(A, sd->d_blocks_split, amc);
+      if (staged) {
+        CUDA_TRY(cudaGetLastError());
+        ++nl;
+        k_m2l_stage<false><<<unsigned(t->work.size()), kStageThreads, kStageSmem, st>>>(A, t->d_work, amc);
+      }
+    } else if (df) {
+      k_m2l_ref<dfloat, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
+    } else {
+      k_m2l_ref<double, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
+    }
+    CUDA_TRY(cudaGetLastError());
+    ++nl;  // the last (or only) launch of this branch
   }
   if ((rc = record(t, 2, st))) return rc;
   // downward pass: the roots, then per level the refined cells' totals and the leaf cells
@@ -3386,6 +3396,21 @@ static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream
   k_p2m_src<<<blocks_for(A.n_leaf_cells, 256), 256, 0, st>>>(A, mx);
   CUDA_TRY(cudaGetLastError());
   ++*nl;
+  // as in the rho solve: the leaf kernel on the second stream beside the upward pass; the root
+  // and boundary kernel after it (it adds onto its output) and after the upward pass; the
+  // refined subgrids (mixed: the staging kernel) on this stream
+  CUDA_TRY(cudaEventRecord(t->ev_fork, st));
+  CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_fork, 0));
+  if (t->n_work_leaf > 0) {
+    if (mixed)
+      k_m2l_leaf4<true><<<unsigned((t->n_work_leaf + 1) / 2), kLeaf4Threads, kLeaf4Smem, t->stream2>>>(
+          A, t->d_work_leaf, t->n_work_leaf);
+    else
+      k_m2l_leaf<double, true><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(double),
+                                 t->stream2>>>(A, t->d_work_leaf);
+    CUDA_TRY(cudaGetLastError());
+    ++*nl;
+  }
   for (int l = h.depth - 1; l >= 0; --l) {
     const int64_t nw = t->oct_leaf_off[l + 1] - t->oct_leaf_off[l];
     const int64_t nr = t->oct_ref_off[l + 1] - t->oct_ref_off[l];
@@ -3395,32 +3420,27 @@ static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream
     CUDA_TRY(cudaGetLastError());
     ++*nl;
   }
-  // mixed path: the refined subgrids by the staging kernel on the second stream, the leaf and
-  // the root and boundary kernels on this one (as in the rho solve)
-  const bool fork = mixed && !t->work.empty();
-  if (fork) {
-    CUDA_TRY(cudaEventRecord(t->ev_fork, st));
-    CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_fork, 0));
-    k_m2l_stage<true><<<unsigned(t->work.size()), kStageThreads, kStageSmemSrc, t->stream2>>>(A, t->d_work, 0);
+  if (mixed) {
+    CUDA_TRY(cudaEventRecord(t->ev_m2m, st));
+    CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_m2m, 0));
+    k_m2l_split_src<float><<<unsigned(sd->n_blocks_split), 64 * kSplitLanes, 0, t->stream2>>>(
+        A, sd->d_blocks_split);
     CUDA_TRY(cudaGetLastError());
     ++*nl;
     CUDA_TRY(cudaEventRecord(t->ev_join, t->stream2));
-  }
-  if (t->n_work_leaf > 0) {
-    if (mixed)
-      k_m2l_leaf4<true><<<unsigned((t->n_work_leaf + 1) / 2), kLeaf4Threads, kLeaf4Smem, st>>>(
-          A, t->d_work_leaf, t->n_work_leaf);
-    else
-      k_m2l_leaf<double, true><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(double), st>>>(
-          A, t->d_work_leaf);
+    if (!t->work.empty()) {
+      k_m2l_stage<true><<<unsigned(t->work.size()), kStageThreads, kStageSmemSrc, st>>>(A, t->d_work, 0);
+      CUDA_TRY(cudaGetLastError());
+      ++*nl;
+    }
+    CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
+  } else {
+    CUDA_TRY(cudaEventRecord(t->ev_join, t->stream2));
+    CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
+    k_m2l_ref_src<double, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks);
     CUDA_TRY(cudaGetLastError());
     ++*nl;
   }
-  if (mixed) k_m2l_split_src<float><<<unsigned(sd->n_blocks_split), 64 * kSplitLanes, 0, st>>>(A, sd->d_blocks_split);
-  else k_m2l_ref_src<double, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks);
-  CUDA_TRY(cudaGetLastError());
-  ++*nl;
-  if (fork) CUDA_TRY(cudaStreamWaitEvent(st, t->ev_join, 0));
   if (mixed) k_root_total<true, true><<<blocks_for(int64_t(h.n_trees) * kRootComps * kCells, 128), 128, 0, st>>>(A);
   else k_root_total<false, true><<<blocks_for(int64_t(h.n_trees) * kRootComps * kCells, 128), 128, 0, st>>>(A);
   CUDA_TRY(cudaGetLastError());
@@ -3501,7 +3521,7 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
   CUDA_TRY(cudaStreamWaitEvent(caller, t->ev_out, 0));
   t->ev_recorded = t->profiling;
-  t->ev_stage = t->profiling && mixed && !t->work.empty() && sd->mixed_variant % 3 == 0;
+  t->ev_stage = t->profiling && mixed && !t->work.empty() && sd->mixed_variant % 3 == 0;  // ev[6], ev[7]
   t->launches = n_io + n_solve;
   return FMM_OK;
 }
@@ -3615,6 +3635,7 @@ void fmm_destroy(fmm_tree* t) {
   }
   if (t->ev_fork) cudaEventDestroy(t->ev_fork);
   if (t->ev_join) cudaEventDestroy(t->ev_join);
+  if (t->ev_m2m) cudaEventDestroy(t->ev_m2m);
   for (void* p : t->allocs) cudaFree(p);
   for (auto& e : t->ev)
     if (e) cudaEventDestroy(e);
@@ -3949,9 +3970,10 @@ int fmm_phase_times(fmm_tree* t, float* ms, int n) {
   if (!t->ev_recorded) return fail(FMM_ERR_STATE, "no profiled solve recorded");
   CUDA_TRY(cudaEventSynchronize(t->ev[4]));
   for (int k = 0; k < n && k < 4; ++k) CUDA_TRY(cudaEventElapsedTime(&ms[k], t->ev[k], t->ev[k + 1]));
-  // [4] general interaction kernel (root, refined targets, boundary leaves), [5] leaf kernel
-  if (n > 4) CUDA_TRY(cudaEventElapsedTime(&ms[4], t->ev[5], t->ev[2]));
-  if (n > 5) CUDA_TRY(cudaEventElapsedTime(&ms[5], t->ev[1], t->ev[5]));
+  // [4] from the end of the leaf kernel (second stream) to the end of the interactions, [5] the
+  // leaf kernel, which starts beside the upward pass
+  if (n > 4) CUDA_TRY(cudaEventElapsedTime(&ms[4], t->ev[9], t->ev[2]));
+  if (n > 5) CUDA_TRY(cudaEventElapsedTime(&ms[5], t->ev[8], t->ev[9]));
   // [6] the staged refined-target kernel of a mixed solve (0 for the other precisions)
   if (n > 6) {
     ms[6] = 0.0f;

@@ -82,7 +82,10 @@ def test_graph_on_a_side_stream_and_profiled():
     tree.set_profiling(False)
     assert np.array_equal(phi.cpu().numpy(), ref[0]) and np.array_equal(g.cpu().numpy(), ref[1])
     assert (ms > 0).all()
-    assert abs(ms[1] - (ms[4] + ms[5])) <= 0.05 * ms[1] + 0.01
+    # the leaf kernel starts beside the upward pass and ends inside the interaction phase; the
+    # staging kernel runs inside the interaction phase
+    assert ms[5] <= ms[0] + ms[1] + 0.01 and ms[4] <= ms[1] + 0.01
+    assert ms[6] <= ms[1] + 0.01
 
 
 def test_batch_in_place_through_graph():
