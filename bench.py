@@ -248,6 +248,25 @@ def measure_batched(tree_api, synth, torch, dev, stream, steps):
     return out
 
 
+def cpu_model():
+    """The host CPU's name as the OS reports it (x86: "model name"; Arm: implementer/part ids)."""
+    try:
+        fields = {}
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip(), v.strip())
+        if "model name" in fields:
+            return fields["model name"]
+        if "CPU part" in fields:
+            return f"Arm implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(seconds_target=15.0):
     """The oracle, as it stands, on a bounded sample of the same workload: phi and g at randomly
     chosen leaf cells, each with its ancestors' expansions and its direct sums."""
@@ -267,7 +286,7 @@ def cpu_baseline(seconds_target=15.0):
             break
         ns = min(rho.size // 4, int(ns * max(2.0, seconds_target / max(dt, 1e-3))))
     return {"value": c["m2l"] / dt, "unit": "interactions/s", "cores": O.max_threads(),
-            "kind": "oracle",
+            "cpu": cpu_model(), "kind": "oracle",
             "sample": f"{ns} random leaf cells of the same tree (their own and their ancestors' "
                       f"{c['m2l']} multipole interactions and {c['p2p_same'] + c['p2p_mixed']} "
                       f"direct pairs), {dt:.1f} s"}
@@ -301,6 +320,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "levels": LEVELS, "theta": THETA},
             "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": O.max_threads(),
+                             "cpu": cpu_model(),
                              "kind": "oracle",
                              "sample": f"each step: {ns} random leaf cells of the same tree"},
             "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
