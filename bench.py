@@ -267,7 +267,7 @@ def cpu_model():
     return platform.processor() or platform.machine()
 
 
-def cpu_baseline(seconds_target=15.0):
+def cpu_baseline(seconds_target=20.0):
     """The oracle, as it stands, on a bounded sample of the same workload: phi and g at randomly
     chosen leaf cells, each with its ancestors' expansions and its direct sums."""
     import oracle as O
