@@ -282,9 +282,9 @@ def cpu_baseline(seconds_target=20.0):
         t0 = time.perf_counter()
         _, _, c = O.sample(t, rho, THETA, idx, with_counts=True)
         dt = time.perf_counter() - t0
-        if dt >= seconds_target / 4 or ns >= rho.size // 4:
+        if dt >= seconds_target / 4 or ns >= rho.size // 2:
             break
-        ns = min(rho.size // 4, int(ns * max(2.0, seconds_target / max(dt, 1e-3))))
+        ns = min(rho.size // 2, int(ns * max(2.0, seconds_target / max(dt, 1e-3))))
     return {"value": c["m2l"] / dt, "unit": "interactions/s", "cores": O.max_threads(),
             "cpu": cpu_model(), "kind": "oracle",
             "sample": f"{ns} random leaf cells of the same tree (their own and their ancestors' "
