@@ -177,7 +177,7 @@ def test_host_entry_point_equals_device_entry_point():
     assert np.array_equal(net, n1)
 
 
-@pytest.mark.parametrize("levels,precision", [(5, "fp64"), (5, "mixed"), (7, "fp64")])
+@pytest.mark.parametrize("levels,precision", [(5, "fp64"), (5, "mixed"), (7, "fp64"), (7, "mixed")])
 def test_full_size_sampled(levels, precision):
     """The 5-level q = 0.7 binary (about 0.9M cells) and the 7-level q = 0.6 binary (13.5M
     cells): the oracle evaluates a sample of leaf cells one by one."""
