@@ -186,6 +186,23 @@ int fmm_binary_diagnostics(fmm_tree* tree, const double* rho_dev, const double* 
                            double omega, const double* x1, const double* x2, double rc1,
                            double rc2, double* out_dev, int8_t* member_dev, void* stream);
 
+/* The diagnostics' fixed-point iteration (Sec. 4: the stars' centres are found by repeating the
+ * classification), n_iter >= 1 passes of fmm_binary_diagnostics enqueued back to back, each pass's
+ * parameters computed on the device from the previous pass's sums: every star's centre moves to
+ * its centre of mass (sum m x / M; a star that received no mass keeps its centre), and the
+ * critical radii become a quarter of Eggleton's (1983) volume-equivalent Roche-lobe radius of
+ * each star, 0.49 q^(2/3) / (0.6 q^(2/3) + ln(1 + q^(1/3))) a with q = M_star / M_other and a the
+ * distance of the new centres (once both stars have mass; the first pass uses none).
+ * x1, x2: host double[3], the starting centres.  After the last pass: out_dev (22 doubles, as
+ * fmm_binary_diagnostics) holds its sums, centres_dev (6 doubles, device) the centres it used
+ * (x_1 then x_2), torque_dev (3 doubles, device) the orbital torque x_1 x F_1 + x_2 x F_2 about
+ * the origin with those centres, member_dev (optional, int8 [n_leaf]) its membership.  Omega,
+ * rho_dev, g_dev as for fmm_binary_diagnostics.  Asynchronous, ordered on `stream`; a forest is
+ * rejected (FMM_ERR_ARG), as are null pointers and n_iter < 1. */
+int fmm_binary_iterate(fmm_tree* tree, const double* rho_dev, const double* g_dev, double omega,
+                       const double* x1, const double* x2, int n_iter, double* out_dev,
+                       double* centres_dev, double* torque_dev, int8_t* member_dev, void* stream);
+
 /* Launch variants of the mixed path (FMM_MIXED), per tree and theta: variant = r + 3 l with
  *   r = 0: refined targets by the shared-memory staging kernel on a second stream, beside the
  *          leaf and boundary kernels (the default);
@@ -242,9 +259,11 @@ int fmm_last_launches(const fmm_tree* tree, int32_t* n);
  * x_dev: [n][3] positions, m_dev: [n] masses, g_dev: [n][3] accelerations (device pointers);
  * net_dev: 7 doubles (F_x, F_y, F_z, T_x, T_y, T_z, S) as for fmm_solve, with F = sum m g,
  * T = sum x cross m g, S = sum |x| |m g| (FP64 sums; the terms of S formed in FP32).  Partial sums live in a fixed 112 KiB device array of
- * this library, so n may not exceed FMM_NET_STATIC_MAX_POINTS (FMM_ERR_ARG otherwise).  The first
- * call on a device looks up that array's address; make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race and must be serialised
+ * this library, so n may not exceed FMM_NET_STATIC_MAX_POINTS (FMM_ERR_ARG otherwise); n = 0
+ * gives seven zeros.  The first call on a device looks up that array's address and caches it for
+ * the life of the process; make that first call before any stream capture.  The cached address
+ * belongs to the device's primary context (the one the CUDA runtime uses): it is not valid in
+ * another context made current on the same device, nor after cudaDeviceReset.  All calls share the array: calls that overlap on the GPU race and must be serialised
  * by the caller (one stream, or events).  Asynchronous on `stream`. */
 #define FMM_NET_STATIC_MAX_POINTS (2048LL * 4096LL)
 int fmm_net_force_torque_points_static(int64_t n, const double* x_dev, const double* m_dev,

@@ -3,7 +3,6 @@ of the solve runs in the library's CUDA kernels."""
 from __future__ import annotations
 
 import ctypes as C
-import math
 from typing import Optional, Tuple
 
 import numpy as np
@@ -23,12 +22,6 @@ def _stream_handle(stream) -> Optional[int]:
         import torch
         return torch.cuda.current_stream().cuda_stream
     return getattr(stream, "cuda_stream", stream)
-
-
-def _roche_lobe(q: float, a: float) -> float:
-    # Eggleton (1983) volume-equivalent Roche-lobe radius, mass ratio q = M_star / M_other
-    q23 = q ** (2.0 / 3.0)
-    return a * 0.49 * q23 / (0.6 * q23 + math.log(1.0 + q ** (1.0 / 3.0)))
 
 
 def stencil(theta: float, parity: int) -> np.ndarray:
@@ -160,27 +153,25 @@ class Tree:
         res = out.cpu().numpy().reshape(2, 11)
         return (res, mem) if member else res
 
-    def binary_iterate(self, rho, g, omega: float, x1, x2, n_iter: int = 5):
-        """The diagnostics' fixed-point iteration (Sec. 4): classify with the current centres,
-        move each centre to its star's centre of mass; critical radii a quarter of the
-        point-mass Roche lobes (Eggleton) of the previous iteration's masses, none at first.
-        Returns (sums, membership, centres used, orbital torque x_1 x F_1 + x_2 x F_2)."""
-        x1 = np.asarray(x1, dtype=np.float64)
-        x2 = np.asarray(x2, dtype=np.float64)
-        rc1 = rc2 = 0.0
-        for _ in range(n_iter):
-            sums, mem = self.binary_diagnostics(rho, g, omega, x1, x2, rc1, rc2, member=True)
-            c1, c2 = x1, x2
-            if sums[0, 0] > 0:
-                x1 = sums[0, 1:4] / sums[0, 0]
-            if sums[1, 0] > 0:
-                x2 = sums[1, 1:4] / sums[1, 0]
-            a = float(np.linalg.norm(x1 - x2))
-            if sums[0, 0] > 0 and sums[1, 0] > 0:
-                rc1 = 0.25 * _roche_lobe(sums[0, 0] / sums[1, 0], a)
-                rc2 = 0.25 * _roche_lobe(sums[1, 0] / sums[0, 0], a)
-        t_orb = np.cross(c1, sums[0, 4:7]) + np.cross(c2, sums[1, 4:7])
-        return sums, mem, (c1, c2), t_orb
+    def binary_iterate(self, rho, g, omega: float, x1, x2, n_iter: int = 5, stream=None):
+        """fmm_binary_iterate: n_iter diagnostics passes, each with the centres and critical radii
+        the library derives on the device from the previous pass.  Returns the last pass's (2, 11)
+        sums, its membership tensor, the centres it used and the orbital torque, as host arrays."""
+        import torch
+        n = self.n_leaf_cells
+        assert rho.numel() == n and g.numel() == 3 * n
+        dev = rho.device
+        out = torch.empty(22, dtype=torch.float64, device=dev)
+        cen = torch.empty(6, dtype=torch.float64, device=dev)
+        torb = torch.empty(3, dtype=torch.float64, device=dev)
+        mem = torch.empty(n, dtype=torch.int8, device=dev)
+        c1 = (C.c_double * 3)(*[float(v) for v in x1])
+        c2 = (C.c_double * 3)(*[float(v) for v in x2])
+        check(lib().fmm_binary_iterate(self._h, rho.data_ptr(), g.data_ptr(), float(omega), c1, c2,
+                                       int(n_iter), out.data_ptr(), cen.data_ptr(), torb.data_ptr(),
+                                       mem.data_ptr(), _stream_handle(stream)))
+        cen = cen.cpu().numpy()
+        return (out.cpu().numpy().reshape(2, 11), mem, (cen[:3], cen[3:]), torb.cpu().numpy())
 
     def sync_status(self, stream=None):
         check(lib().fmm_sync_status(self._h, _stream_handle(stream)))

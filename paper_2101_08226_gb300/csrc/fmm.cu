@@ -2442,8 +2442,10 @@ __device__ __forceinline__ double q_of(double gex, double gey, double gez, doubl
 }
 
 __global__ void __launch_bounds__(kDiagThreads)
-    k_binary_partial(DevArgs A, BinaryParams P, double* __restrict__ partials, int8_t* member) {
+    k_binary_partial(DevArgs A, const BinaryParams* __restrict__ Pdev, double* __restrict__ partials,
+                     int8_t* member) {
   __shared__ double sh[kDiagVals][kDiagThreads];
+  const BinaryParams P = *Pdev;
   double v[kDiagVals];
 #pragma unroll
   for (int k = 0; k < kDiagVals; ++k) v[k] = 0.0;
@@ -2500,14 +2502,60 @@ __global__ void __launch_bounds__(kDiagThreads)
   if (t < kDiagVals) partials[int64_t(blockIdx.x) * kDiagVals + t] = sh[t][0];
 }
 
-// One block: the partials of all blocks in a fixed order.
+// Eggleton's (1983) volume-equivalent Roche-lobe radius of a star of mass ratio
+// q = M_star / M_other at separation a (within 1 % of the exact lobe volume for all q).
+__device__ __forceinline__ double roche_lobe(double q, double a) {
+  const double q23 = pow(q, 2.0 / 3.0);
+  return a * 0.49 * q23 / (0.6 * q23 + log(1.0 + pow(q, 1.0 / 3.0)));
+}
+
+// Sets the parameters of the first pass.
+__global__ void k_binary_init(BinaryParams P, BinaryParams* __restrict__ state) { *state = P; }
+
+// One block: the partials of all blocks in a fixed order.  With `update`, thread 0 then takes
+// one step of the diagnostics' fixed-point iteration on the parameters of the next pass: the
+// centres used by this pass and the orbital torque x_1 x F_1 + x_2 x F_2 go to centres_out (6)
+// and torque_out (3); each star's centre moves to its centre of mass, and the critical radii
+// become a quarter of the Roche-lobe radii of the two masses at the new separation.  A star that
+// received no mass keeps its centre, and both radii stay as they were until both stars have mass.
 __global__ void __launch_bounds__(kDiagThreads)
-    k_binary_final(const double* __restrict__ partials, int n_blocks, double* __restrict__ out) {
+    k_binary_final(const double* __restrict__ partials, int n_blocks, double* __restrict__ out,
+                   BinaryParams* __restrict__ state, double* __restrict__ centres_out,
+                   double* __restrict__ torque_out, int update) {
+  __shared__ double sums[kDiagVals];
   const int t = threadIdx.x;
-  if (t >= kDiagVals) return;
-  double v = 0.0;
-  for (int b = 0; b < n_blocks; ++b) v += partials[int64_t(b) * kDiagVals + t];
-  out[t] = v;
+  if (t < kDiagVals) {
+    double v = 0.0;
+    for (int b = 0; b < n_blocks; ++b) v += partials[int64_t(b) * kDiagVals + t];
+    out[t] = v;
+    sums[t] = v;
+  }
+  __syncthreads();
+  if (!update || t != 0) return;
+  BinaryParams& P = *state;
+  const double* F1 = sums + 4;
+  const double* F2 = sums + 15;
+  const double* c1 = P.c[0];
+  const double* c2 = P.c[1];
+  for (int k = 0; k < 3; ++k) {
+    centres_out[k] = c1[k];
+    centres_out[3 + k] = c2[k];
+  }
+  torque_out[0] = (c1[1] * F1[2] - c1[2] * F1[1]) + (c2[1] * F2[2] - c2[2] * F2[1]);
+  torque_out[1] = (c1[2] * F1[0] - c1[0] * F1[2]) + (c2[2] * F2[0] - c2[0] * F2[2]);
+  torque_out[2] = (c1[0] * F1[1] - c1[1] * F1[0]) + (c2[0] * F2[1] - c2[1] * F2[0]);
+  const double M1 = sums[0], M2 = sums[11];
+  for (int k = 0; k < 3; ++k) {
+    if (M1 > 0.0) P.c[0][k] = sums[1 + k] / M1;
+    if (M2 > 0.0) P.c[1][k] = sums[12 + k] / M2;
+  }
+  if (M1 > 0.0 && M2 > 0.0) {
+    const double dx = P.c[0][0] - P.c[1][0], dy = P.c[0][1] - P.c[1][1], dz = P.c[0][2] - P.c[1][2];
+    const double a = sqrt(dx * dx + dy * dy + dz * dz);
+    const double r1 = 0.25 * roche_lobe(M1 / M2, a), r2 = 0.25 * roche_lobe(M2 / M1, a);
+    P.rc2[0] = r1 * r1;
+    P.rc2[1] = r2 * r2;
+  }
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -2585,6 +2633,7 @@ struct fmm_tree {
   // time-derivative solve workspace (allocated on first use)
   bool src_ready = false, src32_ready = false;
   double* d_diag_partials = nullptr;  // binary diagnostics: [blocks][kDiagVals]
+  BinaryParams* d_diag_state = nullptr;  // the parameters of the next diagnostics pass
   bool df_ready = false;
   dfloat *d_momff = nullptr, *d_massff = nullptr;
   double *d_smom = nullptr, *d_smtl = nullptr, *d_sloc = nullptr;
@@ -3838,6 +3887,37 @@ int fmm_net_force_torque(fmm_tree* t, const double* rho_dev, const double* g_dev
   }
 }
 
+// Enqueues n_pass diagnostics passes on the tree's stream, the parameters of the first written
+// by a small kernel and, with `iterate`, those of each later pass updated on the device by the
+// previous pass's final kernel.
+static int enqueue_binary(fmm_tree* t, const double* rho_dev, const double* g_dev, const BinaryParams& P,
+                          int n_pass, bool iterate, double* out_dev, double* centres_dev,
+                          double* torque_dev, int8_t* member_dev, cudaStream_t caller) {
+  const int nb = 2 * t->n_sms;
+  if (!t->d_diag_partials) CUDA_TRY(dalloc(t, &t->d_diag_partials, sizeof(double) * nb * kDiagVals));
+  if (!t->d_diag_state) CUDA_TRY(dalloc(t, &t->d_diag_state, sizeof(BinaryParams)));
+  std::vector<TreeIo> io = contiguous_io(t, rho_dev, nullptr, const_cast<double*>(g_dev));
+  CUDA_TRY(cudaEventRecord(t->ev_in, caller));
+  CUDA_TRY(cudaStreamWaitEvent(t->stream, t->ev_in, 0));
+  int32_t n_io = 0;
+  int rc = set_io(t, io, nullptr, t->stream, &n_io);
+  if (rc) return rc;
+  k_binary_init<<<1, 1, 0, t->stream>>>(P, t->d_diag_state);
+  CUDA_TRY(cudaGetLastError());
+  DevArgs A = make_args(t, nullptr);
+  for (int k = 0; k < n_pass; ++k) {
+    k_binary_partial<<<nb, kDiagThreads, 0, t->stream>>>(A, t->d_diag_state, t->d_diag_partials, member_dev);
+    CUDA_TRY(cudaGetLastError());
+    k_binary_final<<<1, kDiagThreads, 0, t->stream>>>(t->d_diag_partials, nb, out_dev, t->d_diag_state,
+                                                      centres_dev, torque_dev, iterate ? 1 : 0);
+    CUDA_TRY(cudaGetLastError());
+  }
+  CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
+  CUDA_TRY(cudaStreamWaitEvent(caller, t->ev_out, 0));
+  t->launches = n_io + 1 + 2 * n_pass;
+  return FMM_OK;
+}
+
 int fmm_binary_diagnostics(fmm_tree* t, const double* rho_dev, const double* g_dev, double omega,
                            const double* x1, const double* x2, double rc1, double rc2,
                            double* out_dev, int8_t* member_dev, void* stream) {
@@ -3847,8 +3927,6 @@ int fmm_binary_diagnostics(fmm_tree* t, const double* rho_dev, const double* g_d
   int rc = ensure_device(t);
   if (rc) return rc;
   try {
-    const int nb = 2 * t->n_sms;
-    if (!t->d_diag_partials) CUDA_TRY(dalloc(t, &t->d_diag_partials, sizeof(double) * nb * kDiagVals));
     BinaryParams P;
     P.w2 = omega * omega;
     for (int a = 0; a < 3; ++a) {
@@ -3857,20 +3935,32 @@ int fmm_binary_diagnostics(fmm_tree* t, const double* rho_dev, const double* g_d
     }
     P.rc2[0] = rc1 * rc1;
     P.rc2[1] = rc2 * rc2;
-    cudaStream_t caller = static_cast<cudaStream_t>(stream);
-    std::vector<TreeIo> io = contiguous_io(t, rho_dev, nullptr, const_cast<double*>(g_dev));
-    CUDA_TRY(cudaEventRecord(t->ev_in, caller));
-    CUDA_TRY(cudaStreamWaitEvent(t->stream, t->ev_in, 0));
-    int32_t n_io = 0;
-    if ((rc = set_io(t, io, nullptr, t->stream, &n_io))) return rc;
-    DevArgs A = make_args(t, nullptr);
-    k_binary_partial<<<nb, kDiagThreads, 0, t->stream>>>(A, P, t->d_diag_partials, member_dev);
-    CUDA_TRY(cudaGetLastError());
-    k_binary_final<<<1, kDiagThreads, 0, t->stream>>>(t->d_diag_partials, nb, out_dev);
-    CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
-    CUDA_TRY(cudaStreamWaitEvent(caller, t->ev_out, 0));
-    return FMM_OK;
+    return enqueue_binary(t, rho_dev, g_dev, P, 1, false, out_dev, nullptr, nullptr, member_dev,
+                          static_cast<cudaStream_t>(stream));
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+int fmm_binary_iterate(fmm_tree* t, const double* rho_dev, const double* g_dev, double omega,
+                       const double* x1, const double* x2, int n_iter, double* out_dev,
+                       double* centres_dev, double* torque_dev, int8_t* member_dev, void* stream) {
+  if (!t || !rho_dev || !g_dev || !x1 || !x2 || !out_dev || !centres_dev || !torque_dev)
+    return fail(FMM_ERR_ARG, "null argument");
+  if (n_iter < 1) return fail(FMM_ERR_ARG, "n_iter must be >= 1");
+  if (t->h.n_trees != 1) return fail(FMM_ERR_ARG, "diagnostics take a single tree");
+  int rc = ensure_device(t);
+  if (rc) return rc;
+  try {
+    BinaryParams P;
+    P.w2 = omega * omega;
+    for (int a = 0; a < 3; ++a) {
+      P.c[0][a] = x1[a];
+      P.c[1][a] = x2[a];
+    }
+    P.rc2[0] = P.rc2[1] = 0.0;  // the first pass uses no critical radius
+    return enqueue_binary(t, rho_dev, g_dev, P, n_iter, true, out_dev, centres_dev, torque_dev,
+                          member_dev, static_cast<cudaStream_t>(stream));
   } catch (...) {
     return fail(FMM_ERR_NOMEM, "host allocation failed");
   }

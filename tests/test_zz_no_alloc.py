@@ -61,6 +61,36 @@ def test_static_scratch_net_matches_workspace_net(which):
         got = out.cpu().numpy()
         assert abs(got[6] - ref[6]) <= NORM_TOL * ref[6]
         assert np.abs(got[:6] - ref[:6]).max() <= FP64_TOL * ref[6]
+        # and against plain FP64 sums of the same points, formed on the host by numpy
+        f = (rho * dx ** 3)[:, None] * g.cpu().numpy()
+        host = np.concatenate([f.sum(0), np.cross(x, f).sum(0),
+                               [(np.linalg.norm(x, axis=1) * np.linalg.norm(f, axis=1)).sum()]])
+        assert abs(got[6] - host[6]) <= NORM_TOL * host[6]
+        assert np.abs(got[:6] - host[:6]).max() <= FP64_TOL * host[6]
+
+
+def test_static_scratch_empty_point_set():
+    """n = 0 launches no partial-sum block; the sums are exact zeros, also right after a call that
+    left partial sums in the shared array."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    stream = torch.cuda.current_stream().cuda_stream
+    n = 5000
+    rng = np.random.default_rng(3)
+    x = torch.from_numpy(rng.uniform(-0.5, 0.5, (n, 3))).cuda()
+    m = torch.from_numpy(rng.uniform(0.0, 1.0, n)).cuda()
+    g = torch.from_numpy(rng.normal(size=(n, 3))).cuda()
+    out = torch.empty(7, dtype=torch.float64, device="cuda")
+    assert _lib.lib().fmm_net_force_torque_points_static(n, x.data_ptr(), m.data_ptr(), g.data_ptr(),
+                                                         out.data_ptr(), stream) == _lib.FMM_OK
+    for _ in range(2):
+        out.fill_(float("nan"))
+        rc = _lib.lib().fmm_net_force_torque_points_static(0, x.data_ptr(), m.data_ptr(), g.data_ptr(),
+                                                           out.data_ptr(), stream)
+        assert rc == _lib.FMM_OK, _lib.lib().fmm_last_error()
+        torch.cuda.synchronize()
+        assert (out.cpu().numpy() == 0.0).all()
 
 
 def test_static_scratch_rejects_sizes_beyond_its_capacity():
