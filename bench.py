@@ -1,15 +1,21 @@
 #!/usr/bin/env python
 """Benchmark of the octree FMM gravity solve (Sec. 2.2) on GB300.
 
-Workload: the AMR binary of two n = 3/2 polytropes (mass ratio 0.7, radii 0.1 and 0.085,
-separation 0.35, density floor 1e-10, subgrids refined where the density exceeds 1e-4 of the
-peak, 5 refinement levels: 1961 subgrids, 878,592 leaf cells), theta = 0.5, angular-momentum
+Headline workload: the 7-level AMR binary of two n = 3/2 polytropes (mass ratio 0.6, radii 0.1
+and 0.085, separation 0.3, density floor 1e-10 of the peak, subgrids refined where the density
+exceeds 1e-4 of the peak: 30,089 subgrids, 13,479,936 leaf cells), theta = 0.5, angular-momentum
 correction on.  One step = one whole solve (multipoles up, multipole interactions and near field,
-expansions down, net force and torque) on that step's density, perturbed by seeded 1e-3 noise.
+expansions down, net force and torque) on that step's density rho0 (1 + 1e-3 u_k), the per-step
+re-solve of an evolving star with the tree held fixed.
 
 Metric: directed cell-cell multipole interactions per second (direct near-field pairs are
-reported separately), and ms per solve, for the FP64 path (`value`) and the mixed FP32/FP64 path
-(`mixed`), each with its error against the FP64 path on the same input.
+reported separately), and ms per solve, for the FP64 path (`value`), the mixed FP32/FP64 path
+(`mixed`) and the double-float path (`df64`), each with its error against the FP64 path on the same
+input.  Beside it: the 0.9M-cell 5-level binary (`small`: the three paths, the mixed path's errors
+and residual torque at theta 0.35 / 0.5 / 0.7, the time-derivative solve, the binary diagnostics),
+the 64-tree forest (`batched`) and the 9-level merger binary at theta = 0.34 (`paper_binary`).
+The rooflines divide by FMA rates measured on the same GPU in the same run
+(fmm_measure_fma_rate).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -30,10 +36,25 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 THETA = 0.5
-LEVELS = 5
-WORKLOAD = ("AMR binary: two n=3/2 polytropes, q=0.7, R=0.1/0.085, a=0.35, floor 1e-10, "
-            "refine where rho > 1e-4 rho_peak, 5 levels, theta=0.5, AMC on")
+# the headline workload: the 7-level binary (the largest single-GPU configuration)
+BIG = {"levels": 7, "q": 0.6, "a": 0.3}
+WORKLOAD = ("AMR binary: two n=3/2 polytropes, q=0.6, R=0.1/0.085, a=0.3, floor 1e-10 (density "
+            "contrast 1e10), refine where rho > 1e-4 rho_peak, 7 levels, theta=0.5, AMC on; each "
+            "step solves rho0 (1 + 1e-3 u_k), u_k ~ U[-1, 1] per cell, seed 20210120 + k")
+# the 0.9M-cell binary: FP64, mixed at three opening angles, the time derivative, diagnostics
+SMALL = {"levels": 5, "q": 0.7, "a": 0.35}
+SMALL_WORKLOAD = ("AMR binary: two n=3/2 polytropes, q=0.7, R=0.1/0.085, a=0.35, floor 1e-10, "
+                  "refine where rho > 1e-4 rho_peak, 5 levels, theta=0.5, AMC on")
 METRIC = "FMM cell-cell interactions/s (directed M2L pairs) and gravity-solve ms per solve"
+
+
+def big_workload(synth):
+    return synth.workload_binary(BIG["levels"], q=BIG["q"], a=BIG["a"])
+
+
+def small_workload(synth):
+    return synth.workload_binary(SMALL["levels"], q=SMALL["q"], a=SMALL["a"])
+
 
 # Algorithmic flops per directed interaction, counted from the kernels' formulas (an FMA counts
 # 2, a multiply or add 1, a reciprocal square root 1).  Same-level leaf pairs (multipole or
@@ -61,15 +82,17 @@ def root_pairs(theta):
     return int((mult * ws).sum())
 
 
+# nominal rates (152 SMs, 2 FP64 or 128 FP32 FMA per clock per SM, 2.07 GHz), context only: the
+# rooflines divide by the rates fmm_measure_fma_rate measures
 SMS = 152
 SM_MAX_GHZ = 2.07
-FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1e3    # 2 FP64 FMA / clock / SM
-FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MAX_GHZ / 1e3  # 128 FP32 FMA / clock / SM
+NOMINAL_TFLOPS = {64: SMS * 2 * 2 * SM_MAX_GHZ / 1e3, 32: SMS * 128 * 2 * SM_MAX_GHZ / 1e3}
 
 
-def measured_traffic():
-    """Per-launch DRAM bytes of the interaction kernels from the committed ncu summary, if the
-    kernel sources are the ones it was captured from (else nothing: the counters are stale)."""
+def measured_traffic(workload: str):
+    """Per-launch DRAM bytes of the interaction kernels on one workload from the committed ncu
+    summary, if the kernel sources are the ones it was captured from (else nothing: the counters
+    are stale).  Lines: `workload kernel read_bytes write_bytes`."""
     import hashlib
     here = os.path.dirname(os.path.abspath(__file__))
     csrc = os.path.join(here, "paper_2101_08226_gb300", "csrc")
@@ -86,8 +109,8 @@ def measured_traffic():
                     continue
                 if parts[0] == "sha256":
                     sha = parts[1]
-                else:
-                    out[parts[0]] = int(parts[1]) + int(parts[2])
+                elif parts[0] == workload and len(parts) == 4:
+                    out[parts[1]] = int(parts[2]) + int(parts[3])
     except OSError:
         return {}
     return out if sha == h.hexdigest() else {}
@@ -268,44 +291,57 @@ def cpu_model():
 
 
 def cpu_baseline(seconds_target=20.0):
-    """The oracle, as it stands, on a bounded sample of the same workload: phi and g at randomly
-    chosen leaf cells, each with its ancestors' expansions and its direct sums."""
+    """The oracle, as it stands, on a bounded sample of the headline workload: phi and g at
+    randomly chosen leaf cells, each with its ancestors' expansions and its direct sums.  A call
+    has a fixed cost (the oracle's moments of every cell, from their definition) and a cost per
+    sampled cell; two probe calls size the timed sample to about `seconds_target`."""
     import oracle as O
     from paper_2101_08226_gb300 import synth
-    w = synth.workload_binary(LEVELS)
+    w = big_workload(synth)
     t = O.Tree(w.max_level, w.flags)
     rho = synth.leaf_density(w.field, t.leaves())
     rng = np.random.default_rng(20210120)
-    ns = 512
-    while True:
+
+    def run(ns):
         idx = rng.choice(rho.size, ns, replace=False)
         t0 = time.perf_counter()
         _, _, c = O.sample(t, rho, THETA, idx, with_counts=True)
-        dt = time.perf_counter() - t0
-        if dt >= seconds_target / 4 or ns >= rho.size // 2:
-            break
-        ns = min(rho.size // 2, int(ns * max(2.0, seconds_target / max(dt, 1e-3))))
+        return time.perf_counter() - t0, c
+
+    n0, n1 = 256, 4096
+    d0, _ = run(n0)
+    d1, c = run(n1)
+    ns, dt = n1, d1
+    per_cell = max((d1 - d0) / (n1 - n0), 1e-6)
+    if d1 < 0.5 * seconds_target:
+        ns = int(min(rho.size // 2, max(n1, (seconds_target - (d0 - n0 * per_cell)) / per_cell)))
+        dt, c = run(ns)
     return {"value": c["m2l"] / dt, "unit": "interactions/s", "cores": O.max_threads(),
             "cpu": cpu_model(), "kind": "oracle",
-            "sample": f"{ns} random leaf cells of the same tree (their own and their ancestors' "
-                      f"{c['m2l']} multipole interactions and {c['p2p_same'] + c['p2p_mixed']} "
-                      f"direct pairs), {dt:.1f} s"}
+            "sample": f"{ns} random leaf cells of the 13.5M-cell headline tree (their own and their "
+                      f"ancestors' {c['m2l']} multipole interactions and "
+                      f"{c['p2p_same'] + c['p2p_mixed']} direct pairs), {dt:.1f} s including the "
+                      "oracle's moments of every cell"}
 
 
 def run_reference(args):
+    """The oracle on the headline workload: each step evaluates a bounded sample of leaf cells
+    (a fresh random set of 512 per step) on the host cores; value = multipole interactions / s."""
     rank, _, world = dist_env()
     if rank != 0:
         return
     import oracle as O
     from paper_2101_08226_gb300 import synth
-    w = synth.workload_binary(LEVELS)
+    w = big_workload(synth)
     t = O.Tree(w.max_level, w.flags)
-    rho = synth.leaf_density(w.field, t.leaves())
+    rho0 = synth.leaf_density(w.field, t.leaves())
+    floor = w.field.floor * w.field.rho_peak
     rng = np.random.default_rng(7)
-    ns = 2048
-    rates, times = [], []
+    ns = 512
+    times = []
     total_m2l = 0
     for step in range(args.warmup + args.steps):
+        rho = synth.perturbed_density(rho0, replica_seed(0, step), floor_value=floor)
         idx = rng.choice(rho.size, ns, replace=False)
         t0 = time.perf_counter()
         _, _, c = O.sample(t, rho, THETA, idx, with_counts=True)
@@ -318,36 +354,238 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "levels": LEVELS, "theta": THETA},
+            "config": {"workload": WORKLOAD, "levels": BIG["levels"], "theta": THETA},
             "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": O.max_threads(),
                              "cpu": cpu_model(),
                              "kind": "oracle",
-                             "sample": f"each step: {ns} random leaf cells of the same tree"},
+                             "sample": f"each step: {ns} random leaf cells of the 13.5M-cell tree, "
+                                       "the step's perturbed density"},
             "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 def run_solve_only(args):
-    """Profiling driver: the benchmark tree, `--warmup` untimed solves then `--steps` more in the
+    """Profiling driver: one workload's tree, `--warmup` untimed solves then `--steps` more in the
     given precision (graph-replayed, as in the timed run), nothing else -- a small, fixed launch
     sequence to run under ncu."""
     import torch
     from paper_2101_08226_gb300 import api, build, synth
     build.build()
+    theta = THETA
     if args.solve_workload == "paper9":
         w = synth.workload_paper_binary()
         theta = w.theta
+    elif args.solve_workload == "binary7":
+        w = big_workload(synth)
     else:
-        w = synth.workload_binary(LEVELS)
-        theta = THETA
+        w = small_workload(synth)
     tree = api.Tree(w.max_level, w.flags)
     rho = torch.from_numpy(synth.leaf_density(w.field, tree.leaves())).cuda()
     for _ in range(args.warmup + args.steps):
         phi, g, net = tree.solve(rho, theta, args.solve_only, True)
     torch.cuda.synchronize()
-    print(json.dumps({"solve_only": args.solve_only, "solves": args.warmup + args.steps,
+    print(json.dumps({"solve_only": args.solve_only, "workload": args.solve_workload,
+                      "solves": args.warmup + args.steps,
                       "launches_per_solve": tree.last_launches(), "net": net.cpu().tolist()}))
+
+
+class Timer:
+    """Times whole solves of one tree on one stream with CUDA events, after W untimed solves, an
+    L2 flush (a 256 MiB write, larger than the 129 MB L2) before each timed one, and the library's
+    per-phase events recorded inside the solve's graph."""
+
+    def __init__(self, torch, dist, world, dev, stream):
+        self.torch, self.dist, self.world, self.dev, self.stream = torch, dist, world, dev, stream
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def solves(self, tree, rhos, theta, precision, warmup, steps, out, call=None):
+        torch = self.torch
+        call = call or (lambda r: tree.solve(r, theta, precision, True, *out, self.stream,
+                                             check_status=False))
+        tree.set_profiling(True)
+        for k in range(warmup):
+            call(rhos[k % len(rhos)])
+        torch.cuda.synchronize()
+        tree.sync_status(self.stream)
+        if self.world > 1:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+        step_ms, phases = [], []
+        for k in range(warmup, warmup + steps):
+            self.flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            call(rhos[k % len(rhos)])
+            e1.record(self.stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            phases.append(tree.phase_times())
+        torch.cuda.synchronize()
+        tree.sync_status(self.stream)
+        tree.set_profiling(False)
+        total = reduce_max(float(np.sum(step_ms)), self.dist, self.world, self.dev)
+        return {"total_ms": total, "step_ms": step_ms, "phases": np.mean(np.array(phases), axis=0),
+                "launches": tree.last_launches() * steps}
+
+
+def kernel_flops_of(counts, depth):
+    kf = {k: sum(FLOPS[c] * counts[c] for c in cs) for k, cs in KERNEL_PAIRS.items()}
+    if depth > 0:
+        kf["k_m2l_stage"] -= FLOPS["m2l_refined_refined"] * root_pairs(THETA)
+    return kf
+
+
+def roofline(ph, precision, kernel_flops, peaks, traffic):
+    """The dominant interaction kernel of this precision, timed with CUDA events on the stream it
+    runs on, inside the timed region: FP64 / df64, the general kernel (refined and boundary
+    targets, root) or the leaf kernel; mixed, the refined targets' staging kernel."""
+    if precision == "mixed" and float(ph[6]) > 0:
+        ms = {"k_m2l_stage": float(ph[6]), "k_m2l_leaf": float(ph[5])}
+        k = "k_m2l_stage"
+    else:
+        ms = {"k_m2l_ref": float(ph[4]), "k_m2l_leaf": float(ph[5])}
+        k = max(ms, key=ms.get)
+    bits = 64 if precision == "fp64" else 32
+    ach = kernel_flops[k] / (ms[k] * 1e-3) / 1e12
+    tname = {"fp64": "double", "df64": "dfloat", "mixed": "float"}[precision]
+    kname = k if k == "k_m2l_stage" else f"{k}<{tname}>"
+    if precision == "mixed" and k == "k_m2l_ref":
+        kname = "k_m2l_ref<float> or k_m2l_split<float> + k_m2l_stage (one stream)"
+    peak = peaks[bits]
+    return {"bound": "alu", "kernel": kname, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": traffic.get(kname),
+            "traffic_unit": "DRAM bytes per launch (ncu)",
+            "kernel_ms": ms[k], "kernel_flops": kernel_flops[k],
+            "other_kernel_ms": {kk: v for kk, v in ms.items() if kk != k},
+            "peak_source": f"measured: FP{bits} FMA rate, fmm_measure_fma_rate on this GPU in this "
+                           "run (2 flops per FMA)",
+            "frac_of_nominal": ach / NOMINAL_TFLOPS[bits]}
+
+
+def phases_of(ph, precision="fp64"):
+    out = {"upward": float(ph[0]), "interactions": float(ph[1]), "downward": float(ph[2]),
+           "reductions": float(ph[3])}
+    # the leaf kernel runs on the tree's second stream from the end of the first upward step (it
+    # overlaps "upward"); "after_leaf_kernel" runs from its end to the end of the interactions
+    if precision == "mixed":
+        out.update({"k_m2l_leaf": float(ph[5]), "after_leaf_kernel": float(ph[4]),
+                    "k_m2l_stage": float(ph[6])})
+    else:
+        out.update({"k_m2l_ref": float(ph[4]), "k_m2l_leaf": float(ph[5])})
+    return out
+
+
+def field_errors(torch, phi, g, net, phi64, g64, net64, m):
+    """Errors of a solve against the FP64 path's solve of the same input: infinity norms over the
+    largest reference value, mass-weighted RMS of the per-cell relative error, the worst per-cell
+    relative error with a floor of 1e-3 of the largest value, and net force and torque over the
+    normalisation S."""
+    gn = g64.norm(dim=1)
+    wgt = m / m.sum()
+    dg = (g - g64).norm(dim=1)
+    dphi = (phi - phi64).abs()
+    return {
+        "g_inf_rel": float(((g - g64).abs().max() / g64.abs().max()).item()),
+        "g_rms_mass_weighted": float(torch.sqrt((wgt * (dg / gn) ** 2).sum()).item()),
+        "g_max_cell_rel_floor1e-3": float((dg / torch.clamp(gn, min=1e-3 * float(gn.max()))).max().item()),
+        "phi_inf_rel": float((dphi.max() / phi64.abs().max()).item()),
+        "phi_rms_mass_weighted": float(torch.sqrt((wgt * (dphi / phi64.abs()) ** 2).sum()).item()),
+        "phi_max_cell_rel": float((dphi / phi64.abs()).max().item()),
+        "force_over_norm": float((net[:3].abs().max() / net[6]).item()),
+        "torque_over_norm": float((net[3:6].abs().max() / net[6]).item()),
+        "force_over_norm_fp64": float((net64[:3].abs().max() / net64[6]).item()),
+        "torque_over_norm_fp64": float((net64[3:6].abs().max() / net64[6]).item()),
+    }
+
+
+def leaf_mass(torch, tree, rho):
+    dx3 = np.repeat(1.0 / (8 * 2.0 ** tree.leaves()[:, 0]) ** 3, 512)
+    return rho * torch.from_numpy(dx3).to(rho.device)
+
+
+def measure_small(api, synth, torch, timer, dev, steps, peaks, rank):
+    """The 0.9M-cell 5-level binary: the three paths; the mixed path's errors and residual
+    torque against the FP64 path at theta = 0.35, 0.5, 0.7; the time-derivative solve; the
+    binary diagnostics."""
+    stream = timer.stream
+    w = small_workload(synth)
+    tree = api.Tree(w.max_level, w.flags)
+    n_sub, n_leaf_sub, depth = tree.info()
+    n = n_leaf_sub * 512
+    rho0 = synth.leaf_density(w.field, tree.leaves())
+    floor = w.field.floor * w.field.rho_peak
+    rhos = [torch.from_numpy(synth.perturbed_density(rho0, replica_seed(rank, k), floor_value=floor)).to(dev)
+            for k in range(3 + steps)]
+    counts = tree.counts_by_type(THETA)
+    n_m2l = sum(v for k, v in counts.items() if k.startswith("m2l"))
+    kflops = kernel_flops_of(counts, depth)
+    traffic = measured_traffic("binary_q0.7_L5")
+    phi = torch.empty(n, dtype=torch.float64, device=dev)
+    g = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    net = torch.empty(7, dtype=torch.float64, device=dev)
+    out = {"workload": SMALL_WORKLOAD, "subgrids": n_sub, "leaf_cells": n, "m2l_pairs": n_m2l,
+           "pair_types": counts, "unit": "interactions/s"}
+    tree.autotune(rhos[0], THETA, "mixed", reps=3, stream=stream)
+    for precision in ("fp64", "mixed", "df64"):
+        r = timer.solves(tree, rhos, THETA, precision, 3, steps, (phi, g, net))
+        tm = r["total_ms"] / steps
+        out[precision] = {"value": n_m2l / (tm * 1e-3), "ms_per_solve": tm,
+                          "roofline": roofline(r["phases"], precision, kflops, peaks, traffic),
+                          "phases_ms": phases_of(r["phases"], precision),
+                          "gpu_launches": tree.last_launches()}
+    # the mixed path against the FP64 path at the three opening angles (the same input)
+    m = leaf_mass(torch, tree, rhos[0])
+    sweep = {}
+    for theta in (0.35, 0.5, 0.7):
+        phi64, g64, net64 = tree.solve(rhos[0], theta, "fp64", True, stream=stream)
+        phi32, g32, net32 = tree.solve(rhos[0], theta, "mixed", True, stream=stream)
+        c = tree.counts(theta)
+        sweep[str(theta)] = dict(field_errors(torch, phi32, g32, net32, phi64, g64, net64, m),
+                                 m2l_pairs=c["m2l"])
+    out["mixed_vs_fp64_by_theta"] = sweep
+    # the time-derivative solve: rho and d rho / dt in one call (Sec. 2.1)
+    rhodot = torch.from_numpy(rho0 * np.random.default_rng(31).uniform(-1.0, 1.0, rho0.size)).to(dev)
+    phidot = torch.empty(n, dtype=torch.float64, device=dev)
+    dt_out = {"what": "fmm_solve_dt: the rho solve plus dphi/dt (same operator, source with a "
+                      "dipole); d rho/dt = rho u, u ~ U[-1, 1]"}
+    for precision in ("fp64", "mixed"):
+        r = timer.solves(tree, rhos, THETA, precision, 2, min(steps, 5), None,
+                         call=lambda x: tree.solve_dt(x, rhodot, THETA, precision, True, phi, g,
+                                                      phidot, net, stream, check_status=False))
+        tm = r["total_ms"] / min(steps, 5)
+        base = out[precision]["ms_per_solve"]
+        dt_out[precision] = {"ms_per_solve": tm, "ms_rho_solve_alone": base,
+                             "added_ms_for_dphi_dt": tm - base, "ratio_to_rho_solve": tm / base,
+                             "gpu_launches": tree.last_launches()}
+    out["dphi_dt"] = dt_out
+    # binary diagnostics (Sec. 4): five passes of the fixed-point iteration on the device
+    s1, s2 = w.field.stars
+    sep = float(np.linalg.norm(np.subtract(s2.center, s1.center)))
+    _, g, _ = tree.solve(rhos[-1], THETA, "fp64", True, stream=stream)
+    diag_ms = []
+    for k in range(2 + min(steps, 5)):
+        timer.flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sums, _, _, _ = tree.binary_iterate(rhos[-1], g, (1.7 / sep ** 3) ** 0.5, s1.center,
+                                            s2.center, 5, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 2:
+            diag_ms.append(e0.elapsed_time(e1))
+    tdiag = float(np.mean(diag_ms))
+    out["binary_diagnostics"] = {
+        "what": "fmm_binary_iterate: 5 passes of star membership by the effective acceleration "
+                "and per-star M, sum m x, F, T, each pass's centres and critical radii computed on "
+                "the device from the previous pass",
+        "ms_per_iteration_of_5_passes": tdiag, "leaf_cells": n,
+        "input_gb_per_s": 5 * 32 * n / (tdiag * 1e-3) / 1e9,
+        "stars": [{"M": float(r[0]), "cells": int(r[10])} for r in sums]}
+    tree.close()
+    return out
 
 
 def run_ours(args):
@@ -360,17 +598,22 @@ def run_ours(args):
     from paper_2101_08226_gb300 import api, build, synth
     build.build()
     dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    timer = Timer(torch, dist, world, dev, stream)
 
-    w = synth.workload_binary(LEVELS)
+    # roofline denominators, measured on this GPU
+    peaks, peak_ms = {}, {}
+    for bits in (64, 32):
+        peaks[bits], peak_ms[bits] = api.measure_fma_rate(bits, 5, stream=stream)
+
+    w = big_workload(synth)
     tree = api.Tree(w.max_level, w.flags)
     n_sub, n_leaf_sub, depth = tree.info()
     n = n_leaf_sub * 512
     rho0 = synth.leaf_density(w.field, tree.leaves())
     counts = tree.counts_by_type(THETA)
     n_m2l = sum(v for k, v in counts.items() if k.startswith("m2l"))
-    kernel_flops = {k: sum(FLOPS[c] * counts[c] for c in cs) for k, cs in KERNEL_PAIRS.items()}
-    if depth > 0:
-        kernel_flops["k_m2l_stage"] -= FLOPS["m2l_refined_refined"] * root_pairs(THETA)
+    kflops = kernel_flops_of(counts, depth)
     floor = w.field.floor * w.field.rho_peak
     n_steps = args.warmup + args.steps
     rhos = [torch.from_numpy(synth.perturbed_density(rho0, replica_seed(rank, k), floor_value=floor)).to(dev)
@@ -378,222 +621,112 @@ def run_ours(args):
     phi = torch.empty(n, dtype=torch.float64, device=dev)
     g = torch.empty((n, 3), dtype=torch.float64, device=dev)
     net = torch.empty(7, dtype=torch.float64, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
-    stream = torch.cuda.current_stream(dev)
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         pass
-
-    def timed(precision, sampler=None):
-        tree.set_profiling(True)
-        for k in range(args.warmup):
-            tree.solve(rhos[k], THETA, precision, True, phi, g, net, stream, check_status=False)
-        torch.cuda.synchronize()
-        tree.sync_status(stream)
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        step_ms, phases = [], []
-        for k in range(args.warmup, n_steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            tree.solve(rhos[k], THETA, precision, True, phi, g, net, stream, check_status=False)
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-            phases.append(tree.phase_times())
-        torch.cuda.synchronize()
-        tree.sync_status(stream)
-        total = reduce_max(float(np.sum(step_ms)), dist, world, dev)
-        launches = tree.last_launches() * args.steps
-        return total, np.mean(np.array(phases), axis=0), launches
+    traffic = measured_traffic("binary_q0.6_L7")
 
     # the library's autotuner picks the mixed path's launch variant for this tree (untimed)
     tuned_variant, tuned_ms, _, _ = tree.autotune(rhos[0], THETA, "mixed", reps=3, stream=stream)
     sampler = ClockSampler(uuid) if (uuid and rank == 0) else None
-    t64, ph64, l64 = timed("fp64")
+    r64 = timer.solves(tree, rhos, THETA, "fp64", args.warmup, args.steps, (phi, g, net))
     phi64, g64, net64 = phi.clone(), g.clone(), net.clone()
-    t32, ph32, l32 = timed("mixed")
-    # FP64 results with the pair arithmetic in double-float on the FP32 pipes
-    tdf, phdf, ldf = timed("df64")
-    df_err = {"phi_max_rel_vs_fp64": float(((phi - phi64).abs() / phi64.abs()).max().item()),
-              "g_max_rel_vs_fp64": float(((g - g64).norm(dim=1) / g64.norm(dim=1)).max().item()),
-              "force_over_norm": float((net[:3].abs().max() / net[6]).item()),
-              "torque_over_norm": float((net[3:6].abs().max() / net[6]).item())}
+    r32 = timer.solves(tree, rhos, THETA, "mixed", args.warmup, args.steps, (phi, g, net))
+    err32 = field_errors(torch, phi, g, net, phi64, g64, net64, leaf_mass(torch, tree, rhos[-1]))
+    rdf = timer.solves(tree, rhos, THETA, "df64", args.warmup, args.steps, (phi, g, net))
+    errdf = field_errors(torch, phi, g, net, phi64, g64, net64, leaf_mass(torch, tree, rhos[-1]))
     # the same mixed solve with its kernels launched one by one instead of one graph replay
     tree.set_graphs(False)
-    t32d, _, _ = timed("mixed")
+    r32d = timer.solves(tree, rhos, THETA, "mixed", 1, min(args.steps, 5), (phi, g, net))
     tree.set_graphs(True)
     clocks = sampler.stop() if sampler else None
-    # mixed-path error against the FP64 path on the same (last) input
-    gn = g64.norm(dim=1)
-    m = rhos[-1] * torch.from_numpy(np.repeat(1.0 / (8 * 2.0 ** tree.leaves()[:, 0]) ** 3, 512)).to(dev)
-    wgt = m / m.sum()
-    err = {
-        "g_inf_rel": float(((g - g64).abs().max() / g64.abs().max()).item()),
-        "g_rms_mass_weighted": float(torch.sqrt((wgt * ((g - g64).norm(dim=1) / gn) ** 2).sum()).item()),
-        "phi_max_rel": float(((phi - phi64).abs() / phi64.abs()).max().item()),
-        "torque_over_norm": float((net[3:6].abs().max() / net[6]).item()),
-        "torque_over_norm_fp64": float((net64[3:6].abs().max() / net64[6]).item()),
-        "force_over_norm_fp64": float((net64[:3].abs().max() / net64[6]).item()),
-    }
 
     # end to end through the C ABI with pinned host buffers, copies inside the timed region
-    rho_h = torch.empty(n, dtype=torch.float64).pin_memory()
-    rho_h.copy_(rhos[-1].cpu())
+    rho_h = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(2)]
+    for k in range(2):
+        rho_h[k].copy_(rhos[-1 - k].cpu())
     phi_h = torch.empty(n, dtype=torch.float64).pin_memory()
     g_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
     net_h = torch.empty(7, dtype=torch.float64).pin_memory()
-    for _ in range(2):
-        tree.solve_host(rho_h.numpy(), THETA, "fp64", True, phi_h.numpy(), g_h.numpy(), net_h.numpy(), stream)
+    for k in range(2):
+        tree.solve_host(rho_h[k].numpy(), THETA, "fp64", True, phi_h.numpy(), g_h.numpy(),
+                        net_h.numpy(), stream)
     if world > 1:
         dist.barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        tree.solve_host(rho_h.numpy(), THETA, "fp64", True, phi_h.numpy(), g_h.numpy(), net_h.numpy(), stream)
+    for k in range(args.steps):
+        tree.solve_host(rho_h[k % 2].numpy(), THETA, "fp64", True, phi_h.numpy(), g_h.numpy(),
+                        net_h.numpy(), stream)
     e2e_s = reduce_max(time.perf_counter() - t0, dist, world, dev)
+    tree.close()
+    del rhos, rho_h, phi, g, net, phi64, g64, net64
+    torch.cuda.empty_cache()
 
-    # the time-derivative solve on the same tree: rho and d rho/dt in one call (Sec. 2.1)
-    rhodot = torch.from_numpy(rho0 * np.random.default_rng(31).uniform(-1.0, 1.0, rho0.size)).to(dev)
-    phidot = torch.empty(n, dtype=torch.float64, device=dev)
-    dt_out = {"workload": WORKLOAD + "; d rho/dt = rho u, u ~ U[-1, 1]",
-              "what": "fmm_solve_dt: the rho solve plus dphi/dt (same operator, source with a dipole)"}
-    tree.set_profiling(False)
-    for precision in ("fp64", "mixed"):
-        for k in range(2):
-            tree.solve_dt(rhos[k], rhodot, THETA, precision, True, phi, g, phidot, net, stream,
-                          check_status=False)
-        torch.cuda.synchronize()
-        ms = []
-        for k in range(min(args.steps, 5)):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            tree.solve_dt(rhos[k], rhodot, THETA, precision, True, phi, g, phidot, net, stream,
-                          check_status=False)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        tree.sync_status(stream)
-        tm = float(np.mean(ms))
-        base = t64 / args.steps if precision == "fp64" else t32 / args.steps
-        dt_out[precision] = {"ms_per_solve": tm, "ms_rho_solve_alone": base,
-                             "added_ms_for_dphi_dt": tm - base,
-                             "gpu_launches": tree.last_launches()}
-    # binary diagnostics (Sec. 4): one fused membership + per-star reduction pass over phi's g
-    s1, s2 = w.field.stars
-    sep = float(np.linalg.norm(np.subtract(s2.center, s1.center)))
-    diag_ms = []
-    for k in range(2 + min(args.steps, 5)):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sums = tree.binary_diagnostics(rhos[-1], g, (1.7 / sep ** 3) ** 0.5, s1.center, s2.center,
-                                       0.08 * sep, 0.07 * sep, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        if k >= 2:
-            diag_ms.append(e0.elapsed_time(e1))
-    tdiag = float(np.mean(diag_ms))
-    diag = {"what": "star membership by the effective acceleration and per-star M, sum m x, F, T "
-                    "(fmm_binary_diagnostics, one pass, sums copied to the host)",
-            "ms_per_pass": tdiag, "leaf_cells": n,
-            "input_bytes": 32 * n, "input_gb_per_s": 32 * n / (tdiag * 1e-3) / 1e9,
-            "stars": [{"M": float(r[0]), "cells": int(r[10])} for r in sums]}
+    small = measure_small(api, synth, torch, timer, dev, min(args.steps, 10), peaks, rank)
     batched = measure_batched(api, synth, torch, dev, stream, min(args.steps, 3))
-    paper = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), flush)
+    paper = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), timer.flush)
     if rank != 0:
         if world > 1:
             dist.barrier()
             dist.destroy_process_group()
         return
     cpu = cpu_baseline() if world == 1 else None
-    value64 = whole_job_rate(world, n_m2l, args.steps, t64)
-    value32 = whole_job_rate(world, n_m2l, args.steps, t32)
+    t64, t32, tdf = r64["total_ms"], r32["total_ms"], rdf["total_ms"]
 
-    traffic = measured_traffic()
+    def med(r):
+        return float(np.median(r["step_ms"]))
 
-    def roofline(ph, precision):
-        # the dominant interaction kernel of this precision, timed with CUDA events on the
-        # stream it runs on, inside the timed region.  FP64: the general kernel (refined and
-        # boundary targets, root) or the leaf kernel; mixed: the refined targets' kernel, which
-        # runs on the tree's second stream beside the leaf and boundary kernels
-        if precision == "mixed" and float(ph[6]) > 0:
-            ms = {"k_m2l_stage": float(ph[6]), "k_m2l_leaf": float(ph[5])}
-            k = "k_m2l_stage"
-        else:
-            ms = {"k_m2l_ref": float(ph[4]), "k_m2l_leaf": float(ph[5])}
-            k = max(ms, key=ms.get)
-        ach = kernel_flops[k] / (ms[k] * 1e-3) / 1e12
-        peak = FP64_PEAK_TFLOPS if precision == "fp64" else FP32_PEAK_TFLOPS
-        unit = "FP64" if precision == "fp64" else "FP32"
-        kname = k if k == "k_m2l_stage" else f"{k}<{'double' if precision == 'fp64' else 'float'}>"
-        if precision == "mixed" and k == "k_m2l_ref":
-            kname = "k_m2l_ref<float> or k_m2l_split<float> + k_m2l_stage (one stream)"
-        return {"bound": "alu", "kernel": kname,
-                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": traffic.get(kname), "traffic_unit": "bytes per launch (ncu)",
-                "kernel_ms": ms[k], "kernel_flops": kernel_flops[k],
-                "other_kernel_ms": {kk: v for kk, v in ms.items() if kk != k},
-                "peak_source": f"derived: 152 SMs x {2 if unit == 'FP64' else 128} {unit} FMA/clk "
-                               "x 2 flop x 2.07 GHz"}
-
-    def phases(ph, precision="fp64"):
-        out = {"upward": float(ph[0]), "interactions": float(ph[1]), "downward": float(ph[2]),
-               "reductions": float(ph[3])}
-        # the leaf kernel runs on the tree's second stream from the end of the first upward step
-        # (it overlaps "upward"); "after_leaf_kernel" runs from its end to the end of the
-        # interactions
-        if precision == "mixed":
-            # refined targets (k_m2l_stage) on the tree's stream after the upward pass, the root
-            # and boundary kernel on the second stream after the leaf kernel
-            out.update({"k_m2l_leaf": float(ph[5]), "after_leaf_kernel": float(ph[4]),
-                        "k_m2l_stage": float(ph[6])})
-        else:
-            out.update({"k_m2l_ref": float(ph[4]), "k_m2l_leaf": float(ph[5])})
-        return out
     line = {
-        "metric": METRIC, "value": value64, "unit": "interactions/s", "n_gpus": world,
+        "metric": METRIC, "value": whole_job_rate(world, n_m2l, args.steps, t64),
+        "unit": "interactions/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t64 / args.steps,
+        "ms_per_step_median": med(r64),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "levels": LEVELS, "theta": THETA, "subgrids": n_sub,
-                   "leaf_cells": n, "m2l_pairs": n_m2l, "p2p_pairs": counts["p2p_same"],
-                   "p2p_mixed_pairs": counts["p2p_mixed"], "pair_types": counts,
-                   "l2": "flushed (256 MiB write) before every timed step",
+        "config": {"workload": WORKLOAD, "levels": BIG["levels"], "theta": THETA,
+                   "subgrids": n_sub, "leaf_cells": n, "m2l_pairs": n_m2l,
+                   "p2p_pairs": counts["p2p_same"], "p2p_mixed_pairs": counts["p2p_mixed"],
+                   "pair_types": counts,
+                   "l2": "flushed (256 MiB write) before every timed step; inputs and workspace "
+                         "(about 10 GB) far larger than L2",
                    "launch": "one CUDA graph replay per step, after one pointer-table kernel",
                    "parallelism": f"{world} independent replicas"},
-        "roofline": roofline(ph64, "fp64"),
-        "phases_ms": phases(ph64),
-        "df64": {"value": whole_job_rate(world, n_m2l, args.steps, tdf), "ms_per_step": tdf / args.steps,
-                 "dtype": "double-float (2 x f32) pair arithmetic, f64 rest",
-                 "speedup_vs_fp64": t64 / tdf, "err_vs_fp64_path": df_err,
-                 "phases_ms": phases(phdf), "gpu_launches": ldf},
-        "mixed": {"value": value32, "ms_per_step": t32 / args.steps, "dtype": "f32 pairs, f64 rest",
-                  "speedup_vs_fp64": t64 / t32, "err_vs_fp64": err,
-                  "roofline": roofline(ph32, "mixed"),
-                  "phases_ms": phases(ph32, "mixed"),
-                  "ms_per_step_direct_launches": t32d / args.steps,
+        "roofline": roofline(r64["phases"], "fp64", kflops, peaks, traffic),
+        "phases_ms": phases_of(r64["phases"]),
+        "mixed": {"value": whole_job_rate(world, n_m2l, args.steps, t32),
+                  "ms_per_step": t32 / args.steps, "ms_per_step_median": med(r32),
+                  "dtype": "f32 pairs, f64 rest", "speedup_vs_fp64": t64 / t32,
+                  "err_vs_fp64": err32,
+                  "roofline": roofline(r32["phases"], "mixed", kflops, peaks, traffic),
+                  "phases_ms": phases_of(r32["phases"], "mixed"),
+                  "ms_per_step_direct_launches": r32d["total_ms"] / min(args.steps, 5),
                   "autotune": {"variant": int(tuned_variant),
                                "median_ms_per_variant": [round(float(x), 4) for x in tuned_ms],
-                               "variants": "r + 3 l; r: refined targets 0 staged on a second stream, "
-                                           "1 staged on one stream, 2 per-parity blocks from L2; "
-                                           "l: leaf kernel 0 four targets per lane, 1 two per thread"},
-                  "gpu_launches": l32},
+                               "variants": "r + 3 l; r: refined targets 0 staged on a second "
+                                           "stream, 1 staged on one stream, 2 per-parity blocks "
+                                           "from L2; l: leaf kernel 0 four targets per lane, 1 "
+                                           "two per thread"},
+                  "gpu_launches": r32["launches"]},
+        "df64": {"value": whole_job_rate(world, n_m2l, args.steps, tdf),
+                 "ms_per_step": tdf / args.steps, "ms_per_step_median": med(rdf),
+                 "dtype": "double-float (2 x f32) pair arithmetic, f64 rest",
+                 "speedup_vs_fp64": t64 / tdf, "err_vs_fp64": errdf,
+                 "roofline": roofline(rdf["phases"], "df64", kflops, peaks, traffic),
+                 "phases_ms": phases_of(rdf["phases"]), "gpu_launches": rdf["launches"]},
+        "peaks": {"fp64_tflops": peaks[64], "fp32_tflops": peaks[32],
+                  "ms_per_launch": {"fp64": peak_ms[64], "fp32": peak_ms[32]},
+                  "nominal_tflops": {"fp64": NOMINAL_TFLOPS[64], "fp32": NOMINAL_TFLOPS[32]},
+                  "how": "fmm_measure_fma_rate: 8 independent FMA chains per thread, 2048 threads "
+                         "per SM, about 40 ms per launch, fastest of 5"},
         "e2e": {"value": world * n_m2l * args.steps / e2e_s, "unit": "interactions/s",
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n + 24 * n + 56,
-                "precision": "fp64"},
-        "gpu_launches": l64,
+                "precision": "fp64", "api": "fmm_solve_host (pinned host buffers)"},
+        "gpu_launches": r64["launches"],
+        "small": small,
         "batched": batched,
         "paper_binary": paper,
-        "dphi_dt": dt_out,
-        "binary_diagnostics": diag,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
@@ -606,12 +739,12 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--solve-workload", choices=["binary5", "paper9"], default="binary5",
-                    help="with --solve-only: the 5-level binary (default) or the 9-level merger "
-                         "binary in the paper's proportions")
+    ap.add_argument("--solve-workload", choices=["binary5", "binary7", "paper9"], default="binary5",
+                    help="with --solve-only: the 5-level binary (default), the 7-level headline "
+                         "binary or the 9-level merger binary in the paper's proportions")
     ap.add_argument("--solve-only", choices=["fp64", "mixed", "df64"], default=None,
                     help="profiling driver: run warmup + steps solves of the benchmark tree, no timing")
     args = ap.parse_args()

@@ -269,6 +269,16 @@ int fmm_last_launches(const fmm_tree* tree, int32_t* n);
 int fmm_net_force_torque_points_static(int64_t n, const double* x_dev, const double* m_dev,
                                        const double* g_dev, double* net_dev, void* stream);
 
+/* Measured rate of the FP64 (bits = 64) or FP32 (bits = 32) fused multiply-add pipes of the
+ * current device, the denominator of the roofline of the interaction kernels (they are bound by
+ * arithmetic, Sec. 2.2's multipole interactions evaluated pair by pair).  Every thread of a fully
+ * occupied grid (8 blocks of 256 threads per SM) runs 8 independent FMA chains; the trip count is
+ * calibrated to about 40 ms per launch, and the fastest of `reps` launches, timed with CUDA events
+ * on `stream`, gives *tflops = 2 x FMAs / s / 1e12 (and *ms_per_launch, optional).  Allocates and
+ * frees a small output buffer; synchronises with the stream.  FMM_ERR_ARG for other bits, reps < 1
+ * or a null tflops. */
+int fmm_measure_fma_rate(int bits, int reps, double* tflops, double* ms_per_launch, void* stream);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char* fmm_last_error(void);
 

@@ -24,6 +24,15 @@ def _stream_handle(stream) -> Optional[int]:
     return getattr(stream, "cuda_stream", stream)
 
 
+def measure_fma_rate(bits: int, reps: int = 5, stream=None) -> Tuple[float, float]:
+    """fmm_measure_fma_rate: (TFLOP/s of fused multiply-adds at 2 flops each, ms per launch) of the
+    FP64 (bits = 64) or FP32 (bits = 32) pipes of the current device."""
+    tf, ms = C.c_double(), C.c_double()
+    check(lib().fmm_measure_fma_rate(int(bits), int(reps), C.byref(tf), C.byref(ms),
+                                     _stream_handle(stream)))
+    return tf.value, ms.value
+
+
 def stencil(theta: float, parity: int) -> np.ndarray:
     n = C.c_int32(0)
     check(lib().fmm_stencil(float(theta), int(parity), None, 0, C.byref(n)))

@@ -46,6 +46,8 @@ static int fail(int code, const std::string& msg) {
   return code;
 }
 
+int fmm_record_error(int code, const char* msg) { return fail(code, msg); }
+
 #define CUDA_TRY(expr)                                                                   \
   do {                                                                                   \
     cudaError_t _e = (expr);                                                             \

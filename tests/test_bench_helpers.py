@@ -19,13 +19,14 @@ def test_root_pairs_equal_library_count(theta):
 
 
 def test_traffic_table_parses():
-    tr = bench.measured_traffic()
-    assert isinstance(tr, dict)
-    # empty once the kernel sources differ from the captured ones; otherwise every kernel the
-    # rooflines name is there
-    if tr:
-        for k in ("k_m2l_ref<double>", "k_m2l_stage", "k_m2l_leaf<double>"):
-            assert tr[k] > 0
+    for workload in ("binary_q0.7_L5", "binary_q0.6_L7"):
+        tr = bench.measured_traffic(workload)
+        assert isinstance(tr, dict)
+        # empty once the kernel sources differ from the captured ones; otherwise every kernel
+        # the rooflines name is there
+        if tr:
+            for k in ("k_m2l_ref<double>", "k_m2l_stage", "k_m2l_leaf<double>"):
+                assert tr[k] > 0
 
 
 def test_cpu_model_is_named():
