@@ -269,6 +269,59 @@ int fmm_last_launches(const fmm_tree* tree, int32_t* n);
 int fmm_net_force_torque_points_static(int64_t n, const double* x_dev, const double* m_dev,
                                        const double* g_dev, double* net_dev, void* stream);
 
+/* Self-consistent-field (SCF) construction of a synchronously rotating binary of two polytropes
+ * (Sec. 4.1, "The Initial Stellar Model"), every step on the device around this library's gravity
+ * solve.  The stars lie on the x axis, the accretor (star 1) at smaller x than the donor (star 2);
+ * a star is the material denser than rho_floor on its side of the plane x = x_L1 through the inner
+ * Lagrange point.  An iteration: (1) each star's density scaled to its prescribed mass; the solve
+ * of the scaled density; (2) the rotation axis through the centre of mass (x_cm, y_cm), parallel
+ * to z; (3) Omega = J0 (M1 + M2) / (M1 M2 a^2), a the distance of the stars' centres of mass;
+ * (4) with phi_eff = phi - Omega^2 ((x - x_cm)^2 + (y - y_cm)^2) / 2: L1 = the leaf cell touching
+ * the x axis between the centres with the largest phi_eff, C2 = (1 - f) phi_C + f phi_L1 (phi_C at
+ * the donor's densest cell); (5) K = (C2 - phi_C) / ((n + 1) rho_2^(1/n)) (rho_2 the donor's
+ * largest density), C1 = K (1 + n) rho_1^(1/n) + phi_1 (the accretor's largest density and
+ * phi_eff there); (6) rho = ((C - phi_eff) / (K (n + 1)))^n inside each star's ball about its
+ * centre of mass up to the plane of L1 where positive, rho_floor elsewhere.  Ties (densest cell,
+ * L1) go to the first cell in canonical leaf order.  Where the printed equations are garbled this
+ * follows a reading: Omega squared in phi_eff, K from C2 - phi_C (the printed product does not
+ * balance dimensionally), C - phi_eff in step (6), the axis through the centre of mass instead of
+ * advecting the grid, and the solve placed after the mass scaling (the printed order diverges).
+ * The gravity solves take theta and precision (FMM_FP64, FMM_MIXED or FMM_DF64) with the
+ * correction on.  A single tree only (FMM_ERR_ARG for a forest); the tree stays fixed. */
+typedef struct {
+  double M1, M2;    /* prescribed masses of the accretor and the donor (> 0) */
+  double n;         /* polytropic index (> 0) */
+  double f;         /* the donor's Roche filling factor, (phi_edge - phi_C) / (phi_L1 - phi_C), in (0, 1] */
+  double J0;        /* orbital angular momentum, held fixed (> 0) */
+  double rho_floor; /* atmosphere density (>= 0) */
+  double theta;     /* opening criterion of the solves */
+  int precision;    /* FMM_FP64, FMM_MIXED or FMM_DF64 */
+} fmm_scf_params;
+
+/* The state of the iteration, FMM_SCF_STATE doubles: K, Omega, C1, C2, x_L1, phi_L1 (phi_eff at
+ * L1), the accretor's and the donor's centres of mass (3 + 3), the system's centre of mass (3), the
+ * separation a, the stars' masses before the last scaling (2), their largest densities after it
+ * (rho_1, rho_2), phi_eff at the densest cells (phi_1, phi_C).  K is NaN once a star lost all its
+ * material or no axis cell lay between the centres (the iteration then leaves rho alone). */
+#define FMM_SCF_STATE 22
+
+/* The solve before the iterations and the initial state: the centres of mass of the material at
+ * x < 0 and x >= 0, Omega of the Kepler orbit at their separation, L1 from the solved potential,
+ * K = K0 (> 0).  rho_dev [n_leaf]: the initial density (two stars); phi_dev, g_dev: the solve's
+ * outputs.  Asynchronous on `stream`.  Must precede fmm_scf_iterate on this tree. */
+int fmm_scf_init(fmm_tree* tree, const fmm_scf_params* params, const double* rho_dev, double K0,
+                 double* phi_dev, double* g_dev, void* stream);
+
+/* n_iter >= 0 iterations from the state fmm_scf_init or the previous call left: rho_dev [n_leaf]
+ * holds the current density on entry and the new density (step (6)) on return; phi_dev, g_dev
+ * hold the last solve's potential and acceleration (of the last scaled density).  state_dev
+ * (optional, FMM_SCF_STATE doubles, device) receives the final state, history_dev (optional,
+ * n_iter x FMM_SCF_STATE doubles, device) the state after every iteration.  Asynchronous on
+ * `stream`: no host synchronisation inside; FMM_ERR_STATE without a prior fmm_scf_init. */
+int fmm_scf_iterate(fmm_tree* tree, const fmm_scf_params* params, int n_iter, double* rho_dev,
+                    double* phi_dev, double* g_dev, double* state_dev, double* history_dev,
+                    void* stream);
+
 /* Measured rate of the FP64 (bits = 64) or FP32 (bits = 32) fused multiply-add pipes of the
  * current device, the denominator of the roofline of the interaction kernels (they are bound by
  * arithmetic, Sec. 2.2's multipole interactions evaluated pair by pair).  Every thread of a fully

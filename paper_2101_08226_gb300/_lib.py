@@ -18,6 +18,7 @@ FMM_ERR_STATE = -8
 FMM_ERR_TIMEOUT = -9
 FMM_MIXED_VARIANTS = 6
 FMM_NET_STATIC_MAX_POINTS = 2048 * 4096
+FMM_SCF_STATE = 22
 FMM_FP64 = 0
 FMM_MIXED = 1
 FMM_DF64 = 2
@@ -25,10 +26,17 @@ FMM_DF64 = 2
 EXPORTS = [
     "fmm_build_tree", "fmm_destroy", "fmm_build_forest", "fmm_forest_info", "fmm_solve_batch", "fmm_tree_info", "fmm_tree_subgrids", "fmm_stencil",
     "fmm_interaction_counts", "fmm_interaction_counts_by_type", "fmm_last_launches", "fmm_solve", "fmm_solve_dt", "fmm_sync_status", "fmm_solve_host",
-    "fmm_net_force_torque", "fmm_net_force_torque_points_static", "fmm_set_profiling", "fmm_set_graphs", "fmm_set_wait_limit", "fmm_set_variant", "fmm_autotune", "fmm_binary_diagnostics", "fmm_binary_iterate", "fmm_phase_times", "fmm_measure_fma_rate", "fmm_last_error",
+    "fmm_net_force_torque", "fmm_net_force_torque_points_static", "fmm_set_profiling", "fmm_set_graphs", "fmm_set_wait_limit", "fmm_set_variant", "fmm_autotune", "fmm_binary_diagnostics", "fmm_binary_iterate", "fmm_phase_times", "fmm_measure_fma_rate", "fmm_scf_init", "fmm_scf_iterate", "fmm_last_error",
 ]
 
 _lib = None
+
+
+class ScfParams(C.Structure):
+    """fmm_scf_params"""
+    _fields_ = [("M1", C.c_double), ("M2", C.c_double), ("n", C.c_double), ("f", C.c_double),
+                ("J0", C.c_double), ("rho_floor", C.c_double), ("theta", C.c_double),
+                ("precision", C.c_int)]
 
 
 class FmmError(RuntimeError):
@@ -74,6 +82,8 @@ def lib():
             "fmm_binary_iterate": (i32, [vp, vp, vp, dbl, vp, vp, i32, vp, vp, vp, vp, vp]),
             "fmm_phase_times": (i32, [vp, vp, i32]),
             "fmm_measure_fma_rate": (i32, [i32, i32, vp, vp, vp]),
+            "fmm_scf_init": (i32, [vp, vp, vp, dbl, vp, vp, vp]),
+            "fmm_scf_iterate": (i32, [vp, vp, i32, vp, vp, vp, vp, vp, vp]),
             "fmm_last_error": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():

@@ -24,6 +24,18 @@ def _stream_handle(stream) -> Optional[int]:
     return getattr(stream, "cuda_stream", stream)
 
 
+# the entries of the SCF state (octo_fmm.h, FMM_SCF_STATE), in order
+SCF_STATE_KEYS = ("K", "Omega", "C1", "C2", "x_L1", "phi_L1", "X1x", "X1y", "X1z", "X2x", "X2y",
+                  "X2z", "Xcmx", "Xcmy", "Xcmz", "a", "M1_raw", "M2_raw", "rho1", "rho2", "phi1",
+                  "phiC")
+
+
+def _scf_params(p: dict):
+    return _lib.ScfParams(float(p["M1"]), float(p["M2"]), float(p["n"]), float(p["f"]),
+                          float(p["J0"]), float(p["rho_floor"]), float(p.get("theta", 0.5)),
+                          PRECISIONS[p.get("precision", "fp64")])
+
+
 def measure_fma_rate(bits: int, reps: int = 5, stream=None) -> Tuple[float, float]:
     """fmm_measure_fma_rate: (TFLOP/s of fused multiply-adds at 2 flops each, ms per launch) of the
     FP64 (bits = 64) or FP32 (bits = 32) pipes of the current device."""
@@ -181,6 +193,36 @@ class Tree:
                                        mem.data_ptr(), _stream_handle(stream)))
         cen = cen.cpu().numpy()
         return (out.cpu().numpy().reshape(2, 11), mem, (cen[:3], cen[3:]), torb.cpu().numpy())
+
+    def scf_init(self, params: dict, rho, K0: float, stream=None):
+        """fmm_scf_init: the solve of the initial density and the initial SCF state.  params:
+        M1, M2, n, f, J0, rho_floor, theta, precision ("fp64" / "mixed" / "df64").  Returns
+        (phi, g) of the initial solve."""
+        import torch
+        n = self.n_leaf_cells
+        assert rho.is_cuda and rho.dtype == torch.float64 and rho.numel() == n
+        phi = torch.empty(n, dtype=torch.float64, device=rho.device)
+        g = torch.empty((n, 3), dtype=torch.float64, device=rho.device)
+        check(lib().fmm_scf_init(self._h, C.byref(_scf_params(params)), rho.data_ptr(), float(K0),
+                                 phi.data_ptr(), g.data_ptr(), _stream_handle(stream)))
+        return phi, g
+
+    def scf_iterate(self, params: dict, rho, n_iter: int, phi=None, g=None, stream=None):
+        """fmm_scf_iterate: n_iter SCF iterations on the CUDA float64 density rho (updated in
+        place).  Returns (state dict, history array (n_iter, FMM_SCF_STATE), phi, g)."""
+        import torch
+        n = self.n_leaf_cells
+        assert rho.is_cuda and rho.dtype == torch.float64 and rho.numel() == n
+        dev = rho.device
+        phi = torch.empty(n, dtype=torch.float64, device=dev) if phi is None else phi
+        g = torch.empty((n, 3), dtype=torch.float64, device=dev) if g is None else g
+        state = torch.empty(_lib.FMM_SCF_STATE, dtype=torch.float64, device=dev)
+        hist = torch.empty((max(n_iter, 1), _lib.FMM_SCF_STATE), dtype=torch.float64, device=dev)
+        check(lib().fmm_scf_iterate(self._h, C.byref(_scf_params(params)), int(n_iter),
+                                    rho.data_ptr(), phi.data_ptr(), g.data_ptr(), state.data_ptr(),
+                                    hist.data_ptr(), _stream_handle(stream)))
+        st = state.cpu().numpy()
+        return dict(zip(SCF_STATE_KEYS, (float(v) for v in st))), hist.cpu().numpy()[:n_iter], phi, g
 
     def sync_status(self, stream=None):
         check(lib().fmm_sync_status(self._h, _stream_handle(stream)))

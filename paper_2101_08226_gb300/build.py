@@ -10,7 +10,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libocto_fmm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fmm.cu", "tree.cpp", "peaks.cu"]
+SOURCES = ["fmm.cu", "tree.cpp", "peaks.cu", "scf.cu"]
 
 
 def _nvcc() -> str:

@@ -32,6 +32,7 @@
 
 #include "../../include/octo_fmm.h"
 #include "fmm_kernels.cuh"
+#include "scf.cuh"
 #include "tree.hpp"
 
 using namespace octofmm;
@@ -2636,6 +2637,13 @@ struct fmm_tree {
   bool src_ready = false, src32_ready = false;
   double* d_diag_partials = nullptr;  // binary diagnostics: [blocks][kDiagVals]
   BinaryParams* d_diag_state = nullptr;  // the parameters of the next diagnostics pass
+  // self-consistent-field iteration (allocated on first use)
+  int64_t* d_scf_axis = nullptr;           // leaf cells touching the x axis
+  int64_t n_scf_axis = 0;
+  ScfState* d_scf_state = nullptr;
+  ScfPartial* d_scf_part = nullptr;
+  ScfAxisPartial* d_scf_apart = nullptr;
+  bool scf_started = false;               // fmm_scf_init has enqueued an initial state
   bool df_ready = false;
   dfloat *d_momff = nullptr, *d_massff = nullptr;
   double *d_smom = nullptr, *d_smtl = nullptr, *d_sloc = nullptr;
@@ -3648,6 +3656,62 @@ static int static_net_scratch(double** out) {
 }
 
 // ----------------------------------------------------------------------------------------------
+// self-consistent-field iteration (Sec. 4.1): the host side (kernels in scf.cu)
+// ----------------------------------------------------------------------------------------------
+// The leaf cells whose closure touches the x axis: cells with y and z centres at +-dx / 2, i.e.
+// global cell indices n/2 - 1 and n/2 of n = 8 2^l cells per axis.
+static int ensure_scf(fmm_tree* t) {
+  if (t->d_scf_state) return FMM_OK;
+  const HostTree& h = t->h;
+  std::vector<int64_t> axis;
+  for (int64_t ls = 0; ls < h.n_leaf_sub; ++ls) {
+    const int32_t s = h.leaf_sub[size_t(ls)];
+    const int lev = h.level[s];
+    const int64_t half = int64_t(kSub) << lev >> 1;
+    for (int b = 0; b < kSub; ++b)
+      for (int c = 0; c < kSub; ++c) {
+        const int64_t gy = int64_t(h.ijk[3 * s + 1]) * kSub + b, gz = int64_t(h.ijk[3 * s + 2]) * kSub + c;
+        if ((gy != half - 1 && gy != half) || (gz != half - 1 && gz != half)) continue;
+        for (int a = 0; a < kSub; ++a) axis.push_back(ls * kCells + (a * kSub + b) * kSub + c);
+      }
+  }
+  std::sort(axis.begin(), axis.end());
+  t->n_scf_axis = int64_t(axis.size());
+  CUDA_TRY(upload(t, &t->d_scf_axis, axis));
+  CUDA_TRY(dalloc(t, &t->d_scf_state, sizeof(ScfState)));
+  CUDA_TRY(dalloc(t, &t->d_scf_part, sizeof(ScfPartial) * size_t(scf_blocks(h.n_leaf_sub * kCells))));
+  CUDA_TRY(dalloc(t, &t->d_scf_apart, sizeof(ScfAxisPartial) * size_t(scf_blocks(t->n_scf_axis))));
+  return FMM_OK;
+}
+
+static ScfGeom scf_geom(const fmm_tree* t) {
+  ScfGeom G;
+  G.n_leaf_cells = t->h.n_leaf_sub * kCells;
+  G.leaf_sub = t->d_leaf_sub;
+  G.level = t->d_level;
+  G.ijk = t->d_ijk;
+  G.axis = t->d_scf_axis;
+  G.n_axis = t->n_scf_axis;
+  return G;
+}
+
+static int scf_check(fmm_tree* t, const fmm_scf_params* p, ScfProblem* P) {
+  if (!t || !p) return fail(FMM_ERR_ARG, "null argument");
+  if (t->h.n_trees != 1) return fail(FMM_ERR_ARG, "the SCF iteration takes a single tree");
+  if (!(p->M1 > 0.0) || !(p->M2 > 0.0) || !(p->n > 0.0) || !(p->f > 0.0 && p->f <= 1.0) ||
+      !(p->J0 > 0.0) || !(p->rho_floor >= 0.0))
+    return fail(FMM_ERR_ARG, "SCF parameters: M1, M2, n, J0 > 0, 0 < f <= 1, rho_floor >= 0");
+  *P = ScfProblem{p->M1, p->M2, p->n, p->f, p->J0, p->rho_floor};
+  int rc = ensure_device(t);
+  if (rc) return rc;
+  try {
+    return ensure_scf(t);
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+// ----------------------------------------------------------------------------------------------
 // C ABI
 // ----------------------------------------------------------------------------------------------
 extern "C" {
@@ -4092,6 +4156,53 @@ int fmm_net_force_torque_points_static(int64_t n, const double* x_dev, const dou
   }
   k_net_final<<<1, kReduceThreads, 0, st>>>(scratch, blocks, net_dev, nullptr);
   CUDA_TRY(cudaGetLastError());
+  return FMM_OK;
+}
+
+int fmm_scf_init(fmm_tree* t, const fmm_scf_params* p, const double* rho_dev, double K0,
+                 double* phi_dev, double* g_dev, void* stream) {
+  ScfProblem P;
+  int rc = scf_check(t, p, &P);
+  if (rc) return rc;
+  if (!rho_dev || !phi_dev || !g_dev || !(K0 > 0.0)) return fail(FMM_ERR_ARG, "null pointer or K0 <= 0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  try {
+    // the solve before the iterations
+    rc = solve_impl(t, contiguous_io(t, rho_dev, phi_dev, g_dev), p->theta, p->precision, 1, nullptr, st);
+    if (rc) return rc;
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+  CUDA_TRY(scf_launch_init(scf_geom(t), P, rho_dev, phi_dev, K0, t->d_scf_state, t->d_scf_part,
+                           t->d_scf_apart, st));
+  t->scf_started = true;
+  return FMM_OK;
+}
+
+int fmm_scf_iterate(fmm_tree* t, const fmm_scf_params* p, int n_iter, double* rho_dev,
+                    double* phi_dev, double* g_dev, double* state_dev, double* history_dev,
+                    void* stream) {
+  ScfProblem P;
+  int rc = scf_check(t, p, &P);
+  if (rc) return rc;
+  if (!rho_dev || !phi_dev || !g_dev || n_iter < 0) return fail(FMM_ERR_ARG, "null pointer or n_iter < 0");
+  if (!t->scf_started) return fail(FMM_ERR_STATE, "fmm_scf_init has not been called on this tree");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ScfGeom G = scf_geom(t);
+  try {
+    for (int k = 0; k < n_iter; ++k) {
+      CUDA_TRY(scf_launch_scale(G, P, rho_dev, t->d_scf_state, t->d_scf_part, st));
+      rc = solve_impl(t, contiguous_io(t, rho_dev, phi_dev, g_dev), p->theta, p->precision, 1, nullptr, st);
+      if (rc) return rc;
+      CUDA_TRY(scf_launch_update(G, P, rho_dev, phi_dev, t->d_scf_state, t->d_scf_apart,
+                                 history_dev ? history_dev + int64_t(k) * kScfState : nullptr, st));
+    }
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+  if (state_dev)
+    CUDA_TRY(cudaMemcpyAsync(state_dev, t->d_scf_state, sizeof(double) * kScfState,
+                             cudaMemcpyDeviceToDevice, st));
   return FMM_OK;
 }
 

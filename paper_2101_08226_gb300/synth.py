@@ -328,6 +328,19 @@ def roche_lobe_radius(q: float, a: float) -> float:
     return a * 0.49 * q23 / (0.6 * q23 + math.log(1.0 + q ** (1.0 / 3.0)))
 
 
+def polytrope_k(radius: float, rho_c: float, n: float = 1.5) -> float:
+    """K of the Lane-Emden polytrope p = K rho^(1 + 1/n) of index n with this radius and central
+    density (G = 1): R = xi_1 sqrt((n + 1) K rho_c^(1/n - 1) / (4 pi))."""
+    _, xi1 = lane_emden_table(float(n))
+    return 4.0 * math.pi * radius ** 2 * rho_c ** (1.0 - 1.0 / n) / ((n + 1.0) * xi1 ** 2)
+
+
+def kepler_j0(m1: float, m2: float, a: float) -> float:
+    """Orbital angular momentum of two point masses on a circular Kepler orbit of separation a
+    (G = 1): J = m1 m2 / (m1 + m2) a^2 Omega, Omega^2 = (m1 + m2) / a^3."""
+    return m1 * m2 * math.sqrt(a / (m1 + m2))
+
+
 def workload_paper_binary(levels: int = 9, theta: float = 0.34, refine_frac: float = 1e-4) -> Workload:
     """The merger models' binary in the paper's proportions (Sec. 4): a domain 40 code lengths wide
     mapped to the unit box, 9 refinement levels (finest spacing 1/4096 of the box), accretor 50

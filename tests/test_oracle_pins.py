@@ -640,3 +640,97 @@ def test_roche_lobe_radius_against_the_roche_potential():
         for f in (D.roche_lobe_radius, synth.roche_lobe_radius):
             assert abs(f(q, 1.0) - exact) <= 0.01 * exact, (q, f(q, 1.0), exact)
             assert abs(f(q, 0.37) - 0.37 * f(q, 1.0)) <= 1e-15
+
+
+# ------------------------------------------------------------------------------------------
+# self-consistent-field iteration (Sec. 4.1)
+# ------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def scf_run():
+    import scf_case
+    from oracle import scf as S
+    fld, flags = scf_case.workload()
+    t = O.Tree(scf_case.LEVELS, flags)
+    params, rho0, K0 = scf_case.inputs(fld, t.leaves())
+    P = scf_case.oracle_problem(params, t.leaves())
+    st, out = S.run(t, P, rho0, K0, 10)
+    phi = O.solve(t, out[-1]["rho"], 0.5)[0]   # the potential of the final density
+    return t, P, params, st, out, phi
+
+
+def test_scf_converges(scf_run):
+    """The iteration settles: the relative changes of K, Omega, C1, C2 shrink from iteration to
+    iteration and end below 1e-3; the masses are the prescribed ones after every scaling."""
+    t, P, params, st, out, phi = scf_run
+    keys = ("K", "Omega", "C1", "C2")
+    ch = [max(abs(b["state"][k] / a["state"][k] - 1.0) for k in keys) for a, b in zip(out, out[1:])]
+    assert ch[-1] < 1e-3
+    assert all(y < x for x, y in zip(ch[3:], ch[4:]))
+    # the mass of each star's material, measured on the scaled density with the plane it used
+    for a, b in zip(out, out[1:]):
+        s = b["scaled"]
+        m = s * P.vol
+        star = s > P.rho_floor
+        x_l1 = a["state"]["x_L1"]
+        assert abs(m[star & (P.x[:, 0] < x_l1)].sum() / P.M1 - 1.0) < 1e-12
+        assert abs(m[star & (P.x[:, 0] >= x_l1)].sum() / P.M2 - 1.0) < 1e-12
+
+
+def test_scf_hydrostatic_equilibrium(scf_run):
+    """Inside each star the converged model satisfies the integrated hydrostatic equation with the
+    potential of its own density: K (1 + n) rho^(1/n) + phi_eff = C to 2e-3 of |C| (the change of
+    the potential over the last iteration is what is left)."""
+    from oracle import scf as S
+    t, P, params, st, out, phi = scf_run
+    rho = out[-1]["rho"]
+    pe = S.phi_eff(P, phi, st["Omega"], np.array([st["Xcmx"], st["Xcmy"], st["Xcmz"]]))
+    for C, side in ((st["C1"], P.x[:, 0] < st["x_L1"]), (st["C2"], P.x[:, 0] >= st["x_L1"])):
+        inner = side & (rho > 0.05 * rho[side].max())
+        assert inner.sum() > 100
+        res = st["K"] * (1.0 + P.n) * rho[inner] ** (1.0 / P.n) + pe[inner] - C
+        assert np.abs(res).max() < 2e-3 * abs(C)
+
+
+def test_scf_kepler_orbit_and_filling_factor(scf_run):
+    """Physics of the converged binary, independent of the iteration's formulas: the stars, far
+    apart compared with their radii, orbit like point masses (Omega^2 a^3 = M1 + M2 to 5e-3, with
+    J0 held fixed the separation stays the initial one); and the donor's edge on the axis towards
+    L1 brackets the prescribed Roche filling factor f = (phi_edge - phi_C) / (phi_L1 - phi_C)."""
+    import scf_case
+    from oracle import scf as S
+    t, P, params, st, out, phi = scf_run
+    assert abs(st["Omega"] ** 2 * st["a"] ** 3 / (P.M1 + P.M2) - 1.0) < 5e-3
+    assert abs(st["a"] / scf_case.A0 - 1.0) < 1e-3
+    rho = out[-1]["rho"]
+    pe = S.phi_eff(P, out[-1]["phi"], st["Omega"], np.array([st["Xcmx"], st["Xcmy"], st["Xcmz"]]))
+    ax = P.axis[(P.x[P.axis, 0] > st["x_L1"]) & (P.x[P.axis, 0] < st["X2x"])]
+    ax = ax[np.argsort(P.x[ax, 0])]
+    inside, outside = ax[rho[ax] > P.rho_floor], ax[rho[ax] <= P.rho_floor]
+    ff = lambda j: (pe[j] - st["phiC"]) / (st["phi_L1"] - st["phiC"])
+    assert outside.size and inside.size
+    assert ff(inside[0]) <= P.f <= ff(outside[-1])
+
+
+def test_scf_effective_potential_l1_of_point_masses():
+    """phi_eff of the SCF (gravity plus the centrifugal potential of the frame rotating at Omega
+    about the centre of mass) peaks, along the axis between two point masses on a Kepler orbit, at
+    the inner Lagrange point: where the two pulls and the centrifugal force balance,
+    M1 / d1^2 - M2 / d2^2 = Omega^2 (x - x_cm).  A wrong factor or sign of the centrifugal term
+    moves the peak by 7e-3 to 1.4e-2 here, far more than the 1e-4 sampling."""
+    from oracle import scf as S
+    M1, M2, a = 2.0, 1.0, 0.45
+    X1, X2 = -a * M2 / (M1 + M2), a * M1 / (M1 + M2)
+    omega = np.sqrt((M1 + M2) / a ** 3)
+    xs = np.arange(X1 + 0.05, X2 - 0.05, 1e-4)
+    x = np.stack([xs, np.zeros_like(xs), np.zeros_like(xs)], axis=1)
+    phi = -M1 / np.abs(xs - X1) - M2 / np.abs(xs - X2)
+    P = S.ScfProblem(x, np.ones_like(xs), np.arange(xs.size), M1, M2, 1.5, 0.5, 1.0, 0.0)
+    peak = xs[np.argmax(S.phi_eff(P, phi, omega, np.zeros(3)))]
+    lo, hi = X1 + 1e-9, X2 - 1e-9
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if M1 / (mid - X1) ** 2 - M2 / (X2 - mid) ** 2 - omega ** 2 * mid > 0:
+            lo = mid
+        else:
+            hi = mid
+    assert abs(peak - 0.5 * (lo + hi)) <= 1e-4
