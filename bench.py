@@ -437,10 +437,11 @@ def kernel_flops_of(counts, depth):
     return kf
 
 
-def roofline(ph, precision, kernel_flops, peaks, traffic):
+def roofline(ph, precision, kernel_flops, peaks, traffic, variant=0):
     """The dominant interaction kernel of this precision, timed with CUDA events on the stream it
     runs on, inside the timed region: FP64 / df64, the general kernel (refined and boundary
-    targets, root) or the leaf kernel; mixed, the refined targets' staging kernel."""
+    targets, root) or the leaf kernel; mixed, the refined targets' staging kernel (that of the
+    tree's launch variant: k_m2l_stage_pipe for r = 3)."""
     if precision == "mixed" and float(ph[6]) > 0:
         ms = {"k_m2l_stage": float(ph[6]), "k_m2l_leaf": float(ph[5])}
         k = "k_m2l_stage"
@@ -451,6 +452,8 @@ def roofline(ph, precision, kernel_flops, peaks, traffic):
     ach = kernel_flops[k] / (ms[k] * 1e-3) / 1e12
     tname = {"fp64": "double", "df64": "dfloat", "mixed": "float"}[precision]
     kname = k if k == "k_m2l_stage" else f"{k}<{tname}>"
+    if k == "k_m2l_stage" and variant % 4 == 3:
+        kname = "k_m2l_stage_pipe"
     if precision == "mixed" and k == "k_m2l_ref":
         kname = "k_m2l_ref<float> or k_m2l_split<float> + k_m2l_stage (one stream)"
     peak = peaks[bits]
@@ -527,12 +530,14 @@ def measure_small(api, synth, torch, timer, dev, steps, peaks, rank):
     net = torch.empty(7, dtype=torch.float64, device=dev)
     out = {"workload": SMALL_WORKLOAD, "subgrids": n_sub, "leaf_cells": n, "m2l_pairs": n_m2l,
            "pair_types": counts, "unit": "interactions/s"}
-    tree.autotune(rhos[0], THETA, "mixed", reps=3, stream=stream)
+    variant, _, _, _ = tree.autotune(rhos[0], THETA, "mixed", reps=3, stream=stream)
+    out["mixed_variant"] = int(variant)
     for precision in ("fp64", "mixed", "df64"):
         r = timer.solves(tree, rhos, THETA, precision, 3, steps, (phi, g, net))
         tm = r["total_ms"] / steps
         out[precision] = {"value": n_m2l / (tm * 1e-3), "ms_per_solve": tm,
-                          "roofline": roofline(r["phases"], precision, kflops, peaks, traffic),
+                          "roofline": roofline(r["phases"], precision, kflops, peaks, traffic,
+                                               variant),
                           "phases_ms": phases_of(r["phases"], precision),
                           "gpu_launches": tree.last_launches()}
     # the mixed path against the FP64 path at the three opening angles (the same input)
@@ -699,15 +704,17 @@ def run_ours(args):
                   "ms_per_step": t32 / args.steps, "ms_per_step_median": med(r32),
                   "dtype": "f32 pairs, f64 rest", "speedup_vs_fp64": t64 / t32,
                   "err_vs_fp64": err32,
-                  "roofline": roofline(r32["phases"], "mixed", kflops, peaks, traffic),
+                  "roofline": roofline(r32["phases"], "mixed", kflops, peaks, traffic,
+                                       tuned_variant),
                   "phases_ms": phases_of(r32["phases"], "mixed"),
                   "ms_per_step_direct_launches": r32d["total_ms"] / min(args.steps, 5),
                   "autotune": {"variant": int(tuned_variant),
                                "median_ms_per_variant": [round(float(x), 4) for x in tuned_ms],
-                               "variants": "r + 3 l; r: refined targets 0 staged on a second "
+                               "variants": "r + 4 l; r: refined targets 0 staged on a second "
                                            "stream, 1 staged on one stream, 2 per-parity blocks "
-                                           "from L2; l: leaf kernel 0 four targets per lane, 1 "
-                                           "two per thread"},
+                                           "from L2, 3 staged with a copy-issuing warp and "
+                                           "full / empty barriers; l: leaf kernel 0 four targets "
+                                           "per lane, 1 two per thread"},
                   "gpu_launches": r32["launches"]},
         "df64": {"value": whole_job_rate(world, n_m2l, args.steps, tdf),
                  "ms_per_step": tdf / args.steps, "ms_per_step_median": med(rdf),

@@ -203,18 +203,20 @@ int fmm_binary_iterate(fmm_tree* tree, const double* rho_dev, const double* g_de
                        const double* x1, const double* x2, int n_iter, double* out_dev,
                        double* centres_dev, double* torque_dev, int8_t* member_dev, void* stream);
 
-/* Launch variants of the mixed path (FMM_MIXED), per tree and theta: variant = r + 3 l with
+/* Launch variants of the mixed path (FMM_MIXED), per tree and theta: variant = r + 4 l with
  *   r = 0: refined targets by the shared-memory staging kernel on a second stream, beside the
  *          leaf and boundary kernels (the default);
  *   r = 1: the same kernel after them, on one stream;
  *   r = 2: refined targets by per-parity blocks that read their partners from L2;
+ *   r = 3: as r = 0 with the staging pipelined: a separate warp issues the copies and each buffer
+ *          has its own full and empty barriers, so the evaluating warps never meet;
  *   l = 0: leaf pairs by the four-targets-per-lane FP32 kernel (the default);
  *   l = 1: leaf pairs by the two-targets-per-thread kernel.
- * r = 0 and 1 give the same results bit for bit, and so do l = 0 and 1; r = 2 sums the refined
+ * r = 0, 1 and 3 give the same results bit for bit, and so do l = 0 and 1; r = 2 sums the refined
  * targets' pairs in another order (results differ at FP32 rounding, within the mixed path's
  * tolerance).  FMM_ERR_ARG for a variant outside [0, FMM_MIXED_VARIANTS), FMM_ERR_THETA for a
  * theta outside [0.34, 1).  The FP64 and df64 paths have one launch configuration. */
-#define FMM_MIXED_VARIANTS 6
+#define FMM_MIXED_VARIANTS 8
 int fmm_set_variant(fmm_tree* tree, double theta, int variant);
 
 /* Autotuner: times every launch variant of `precision` (FMM_MIXED: FMM_MIXED_VARIANTS; FP64,

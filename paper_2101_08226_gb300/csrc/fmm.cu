@@ -157,7 +157,7 @@ constexpr int kLeafThreads = 256;    // one block = one leaf subgrid, two target
 constexpr int kRootChunks = 8;       // root sources split into 8 chunks of 64 cells
 constexpr int kM2LThreads = 64;      // one block = the 64 cells of one parity of one subgrid
 constexpr int kSplitLanes = 4;       // lanes per target in k_m2l_split's long-list blocks
-constexpr int kMixedVariants = 6;    // mixed path launch variants: refined (3) x leaf kernel (2)
+constexpr int kMixedVariants = 8;    // mixed path launch variants: refined (4) x leaf kernel (2)
 constexpr int kReduceThreads = 256;
 constexpr int kReduceBlocks = 1216;  // 8 per SM
 
@@ -1390,6 +1390,144 @@ __global__ void __launch_bounds__(kStageThreads, 1) k_m2l_stage(DevArgs A, const
     finish_rr(S);
     store_own<float, true>(A, S, iA);
   }
+}
+
+// The same work as k_m2l_stage with the staging decoupled from the evaluation: a 17th warp only
+// issues the copies, and each of the two buffers has a "full" barrier (the class's copies have
+// landed) and an "empty" barrier (all 16 evaluating warps are done with it).  The producer issues
+// class c + 2 into a buffer as soon as every warp has finished class c, so a warp that is done
+// with a class moves on to the next one at once; it waits only when it gets a whole class ahead
+// of the slowest warp.  (k_m2l_stage makes all warps meet at the end of every class, and the
+// uneven split of a parity's stencil over the 8 partner classes makes them wait for each other.)
+// Every wait is bounded: a wait that runs out records FMM_ERR_TIMEOUT; the producer then waits
+// (bounded) for the copies it issued before it leaves, so no copy lands after the block is gone.
+constexpr int kStagePipeThreads = kStageThreads + 32;
+
+template <int W>
+__device__ __forceinline__ void stage_issue_warp(const float* __restrict__ arr, const int32_t* nb, int c,
+                                                 float* buf, uint64_t* bar, int lane) {
+  // lane takes runs lane, lane + 32, ...; it zero-fills its runs in absent neighbours, then
+  // announces the bytes of its bulk copies with one arrive, then issues them
+  uint32_t bytes = 0;
+  for (int j = lane; j < kStageRuns; j += 32) {
+    const int rx = (c >> 2) & 1, ry = (c >> 1) & 1, rz = c & 1;
+    const int lx = j / 27, ly = (j / 3) % 9, run = j % 3;
+    const int x = 2 * lx + rx - 5, y = 2 * ly + ry - 5;
+    const int z1 = rz ? 2 : 3, z2 = rz ? 6 : 7;
+    const int lz0 = run == 0 ? 0 : (run == 1 ? z1 : z2);
+    const int lz1 = run == 0 ? z1 : (run == 1 ? z2 : 9);
+    const int z = 2 * lz0 + rz - 5;
+    const int32_t sB = nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)];
+    const uint32_t n = uint32_t(lz1 - lz0) * uint32_t(W * 4);
+    if (sB >= 0) {
+      bytes += n;
+    } else {
+      float* dst = buf + (lx * kStageSX + ly * kStageSY + lz0) * W;
+      for (int k = 0; k < int(n / 4); ++k) dst[k] = 0.0f;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_arrive_tx(bar, bytes);
+  for (int j = lane; j < kStageRuns; j += 32) {
+    const int rx = (c >> 2) & 1, ry = (c >> 1) & 1, rz = c & 1;
+    const int lx = j / 27, ly = (j / 3) % 9, run = j % 3;
+    const int x = 2 * lx + rx - 5, y = 2 * ly + ry - 5;
+    const int z1 = rz ? 2 : 3, z2 = rz ? 6 : 7;
+    const int lz0 = run == 0 ? 0 : (run == 1 ? z1 : z2);
+    const int lz1 = run == 0 ? z1 : (run == 1 ? z2 : 9);
+    const int z = 2 * lz0 + rz - 5;
+    const int32_t sB = nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)];
+    if (sB < 0) continue;
+    const int64_t row = int64_t(sB) * kCells + cidx(x & 7, y & 7, z & 7);
+    bulk_g2s(buf + (lx * kStageSX + ly * kStageSY + lz0) * W, arr + row * W,
+             uint32_t(lz1 - lz0) * uint32_t(W * 4), bar);
+  }
+}
+
+__global__ void __launch_bounds__(kStagePipeThreads, 1) k_m2l_stage_pipe(DevArgs A, const int32_t* __restrict__ subs,
+                                                                         int amc) {
+  constexpr int W = 20;
+  extern __shared__ __align__(128) unsigned char stage_smem[];
+  float* const buf0 = reinterpret_cast<float*>(stage_smem);
+  constexpr int kBufFloats = StageW<false>::kBufBytes / 4;  // buffer b starts at buf0 + b kBufFloats
+  __shared__ __align__(8) uint64_t full[2], empty[2];
+  __shared__ int32_t nb[27];
+  const int32_t s = subs[blockIdx.x];
+  const int t = threadIdx.x;
+  if (t < 27) nb[t] = A.nbr[27 * s + t];
+  if (t == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&full[b], 32);                      // one arrival per producer lane
+      mbar_init(&empty[b], kStageThreads / 32);     // one arrival per evaluating warp
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int w = t >> 5, lane = t & 31;
+  if (w == kStageThreads / 32) {
+    // producer: classes 0 and 1 at once, class c >= 2 once class c - 2 is done with
+    int last = -1;  // the last class issued
+    for (int cl = 0; cl < 8; ++cl) {
+      const int b = cl & 1;
+      if (cl >= 2 && !mbar_wait_bounded(&empty[b], uint32_t(((cl - 2) >> 1) & 1), A.wait_cycles)) {
+        if (lane == 0) atomicOr(A.status, 4);
+        break;
+      }
+      stage_issue_warp<W>(A.mom32, nb, cl, buf0 + b * kBufFloats, &full[b], lane);
+      last = cl;
+    }
+    // every copy this warp issued has landed before the block's shared memory is released: the
+    // last class issued into each buffer (earlier ones were waited for before it was reissued)
+    for (int cl = last; cl >= 0 && cl >= last - 1; --cl)
+      mbar_wait_bounded(&full[cl & 1], uint32_t((cl >> 1) & 1), kStageWaitCycles);
+    return;
+  }
+  const int parity = w >> 1;
+  const int ia = ((w & 1) << 1) | ((lane >> 2) & 1), ib = lane >> 3, ic = lane & 3;
+  const int a = 2 * ia + ((parity >> 2) & 1), b_ = 2 * ib + ((parity >> 1) & 1), c = 2 * ic + (parity & 1);
+  const int64_t iA = int64_t(s) * kCells + cidx(a, b_, c);
+  Target<float, true> S;
+  load_target<float, true>(S, A, A.mom32, iA, amc != 0);
+  const float h = cell_h<float>(A.level[s]);
+  const int base = (ia * kStageSX + ib * kStageSY + ic) * W;
+  const float4* __restrict__ tab = A.stage_tab + parity * kLeafCap;
+  const int32_t* __restrict__ seg = A.stage_seg + parity * 9;
+  for (int cl = 0; cl < 8; ++cl) {
+    const int bi = cl & 1;
+    // every lane waits (the wait is also what makes the producer's zero fills visible)
+    if (!mbar_wait_bounded(&full[bi], uint32_t((cl >> 1) & 1), A.wait_cycles)) {
+      atomicOr(A.status, 4);
+      return;  // the producer waits for its own copies before the block ends
+    }
+    const float* __restrict__ B = buf0 + bi * kBufFloats + base;
+    const int q1 = __ldg(seg + cl + 1);
+    const int qb = __ldg(seg + cl);
+    float4 e_next = __ldg(tab + min(qb, kLeafCap - 1));
+    for (int q0 = qb; q0 < q1; q0 += kFlush) {
+      const int qe = min(q0 + kFlush, q1);
+      for (int q = q0; q < qe; ++q) {
+        const float4 e = e_next;
+        e_next = __ldg(tab + min(q + 1, q1 - 1));
+        const float4* m = reinterpret_cast<const float4*>(B + __float_as_int(e.w) * W);
+        float Mv[W];
+#pragma unroll
+        for (int k = 0; k < W / 4; ++k) {
+          const float4 v = m[k];
+          Mv[4 * k] = v.x;
+          Mv[4 * k + 1] = v.y;
+          Mv[4 * k + 2] = v.z;
+          Mv[4 * k + 3] = v.w;
+        }
+        const float x = fmaf(-e.x, h, S.dAx), y = fmaf(-e.y, h, S.dAy), z = fmaf(-e.z, h, S.dAz);
+        interact_rr_v<float>(S, Mv, x, y, z);
+      }
+      flush(S);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[bi]);
+  }
+  finish_rr(S);
+  store_own<float, true>(A, S, iA);
 }
 
 // Four consecutive table values (16-byte aligned) in vector loads.
@@ -2798,8 +2936,14 @@ static int ensure_device(fmm_tree* t) {
   CUDA_TRY(upload(t, &t->d_leaf_tree, leaf_tree));
   CUDA_TRY(dalloc(t, &t->d_io, sizeof(TreeIo) * size_t(nr)));
   CUDA_TRY(dalloc(t, &t->d_io_net, sizeof(double*)));
-  CUDA_TRY(cudaStreamCreateWithFlags(&t->stream, cudaStreamNonBlocking));
-  CUDA_TRY(cudaStreamCreateWithFlags(&t->stream2, cudaStreamNonBlocking));
+  // The tree's stream carries the level-by-level passes, short launches on the critical path;
+  // the second stream carries the leaf and boundary kernels, which only need to finish before the
+  // downward pass.  With the first at the higher priority, the blocks of a pass are scheduled
+  // ahead of the waiting blocks of the long kernel beside it.
+  int prio_low = 0, prio_high = 0;
+  CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  CUDA_TRY(cudaStreamCreateWithPriority(&t->stream, cudaStreamNonBlocking, prio_high));
+  CUDA_TRY(cudaStreamCreateWithPriority(&t->stream2, cudaStreamNonBlocking, prio_low));
   CUDA_TRY(cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&t->ev_join, cudaEventDisableTiming));
   CUDA_TRY(cudaEventCreateWithFlags(&t->ev_m2m, cudaEventDisableTiming));
@@ -2822,6 +2966,7 @@ static int ensure_mixed(fmm_tree* t) {
   CUDA_TRY(dalloc(t, &t->d_root_part_ac, sizeof(double) * nr * kRootChunks * 3 * kCells));
   CUDA_TRY(cudaFuncSetAttribute(k_m2l_stage<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageSmem));
   CUDA_TRY(cudaFuncSetAttribute(k_m2l_stage<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageSmemSrc));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_stage_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageSmem));
   t->mixed_ready = true;
   return FMM_OK;
 }
@@ -3342,7 +3487,7 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   ++nl;
   // The same-level leaf pairs need only the leaf masses: their kernel runs on the second stream
   // from here, beside the level-by-level (latency-bound) upward pass.
-  const int v_ref = sd->mixed_variant % 3, v_leaf = sd->mixed_variant / 3;
+  const int v_ref = sd->mixed_variant % 4, v_leaf = sd->mixed_variant / 4;
   CUDA_TRY(cudaEventRecord(t->ev_fork, st));
   CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_fork, 0));
   if ((rc = record(t, 8, t->stream2))) return rc;
@@ -3390,7 +3535,7 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   // leaves room for theirs), or both on this stream, or by k_m2l_ref's per-parity blocks
   // reading their partners from L2; the leaf pairs by k_m2l_leaf4 or k_m2l_leaf<float>.
   const bool staged = mixed && !t->work.empty() && v_ref != 2;
-  const bool split2 = staged && v_ref == 0;  // root and boundary kernel on the second stream
+  const bool split2 = staged && (v_ref == 0 || v_ref == 3);  // root and boundary kernel on the second stream
   if (split2) {
     CUDA_TRY(cudaEventRecord(t->ev_m2m, st));
     CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_m2m, 0));
@@ -3404,7 +3549,10 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   CUDA_TRY(cudaEventRecord(t->ev_join, t->stream2));
   if (split2) {
     if ((rc = record(t, 6, st))) return rc;
-    k_m2l_stage<false><<<unsigned(t->work.size()), kStageThreads, kStageSmem, st>>>(A, t->d_work, amc);
+    if (v_ref == 3)
+      k_m2l_stage_pipe<<<unsigned(t->work.size()), kStagePipeThreads, kStageSmem, st>>>(A, t->d_work, amc);
+    else
+      k_m2l_stage<false><<<unsigned(t->work.size()), kStageThreads, kStageSmem, st>>>(A, t->d_work, amc);
     CUDA_TRY(cudaGetLastError());
     ++nl;
     if ((rc = record(t, 7, st))) return rc;
@@ -3580,7 +3728,8 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
   CUDA_TRY(cudaStreamWaitEvent(caller, t->ev_out, 0));
   t->ev_recorded = t->profiling;
-  t->ev_stage = t->profiling && mixed && !t->work.empty() && sd->mixed_variant % 3 == 0;  // ev[6], ev[7]
+  t->ev_stage = t->profiling && mixed && !t->work.empty() &&
+                (sd->mixed_variant % 4 == 0 || sd->mixed_variant % 4 == 3);  // ev[6], ev[7]
   t->launches = n_io + n_solve;
   return FMM_OK;
 }
