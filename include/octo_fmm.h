@@ -271,6 +271,26 @@ int fmm_last_launches(const fmm_tree* tree, int32_t* n);
 int fmm_net_force_torque_points_static(int64_t n, const double* x_dev, const double* m_dev,
                                        const double* g_dev, double* net_dev, void* stream);
 
+/* Spatial decomposition of one tree over n_ranks GPUs (Sec. 5: the large runs split one tree
+ * over many nodes), host-only.  The subgrids of level cut_level (each with its whole subtree) and
+ * the leaf subgrids coarser than it are ordered by the Morton key of their first corner at the cut
+ * level and split into n_ranks contiguous runs of about equal leaf-cell count; owner_host
+ * [n_subgrids] receives each subgrid's rank, or -1 for a refined subgrid coarser than the cut,
+ * which every rank keeps: its moments are the sum over the ranks of the moments of each rank's
+ * own leaves (an all-reduce), and every rank evaluates its interactions.  FMM_ERR_ARG for a forest,
+ * n_ranks < 1 or a cut level outside [0, depth]. */
+int fmm_partition(const fmm_tree* tree, int n_ranks, int cut_level, int32_t* owner_host);
+
+/* The ghost subgrids of `rank` under an owner array from fmm_partition: the subgrids owned by
+ * other ranks whose data this rank's solve reads -- for each subgrid it owns or keeps, the 26
+ * same-level neighbours (every multipole partner lies among them for theta >= 0.34); for each leaf
+ * it owns, also the leaf children of its refined neighbours and the leaf neighbours of each of its
+ * ancestors (direct partners one level finer and coarser).  A leaf ghost is sent as its 512
+ * densities, a refined ghost as its cells' moments.  Writes up to `capacity` subgrid indices,
+ * ascending, into ghosts_host and their number into *count.  Host-only. */
+int fmm_ghosts(const fmm_tree* tree, const int32_t* owner_host, int rank, int32_t* ghosts_host,
+               int64_t capacity, int64_t* count);
+
 /* Self-consistent-field (SCF) construction of a synchronously rotating binary of two polytropes
  * (Sec. 4.1, "The Initial Stellar Model"), every step on the device around this library's gravity
  * solve.  The stars lie on the x axis, the accretor (star 1) at smaller x than the donor (star 2);

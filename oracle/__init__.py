@@ -42,6 +42,8 @@ def lib():
         L.oracle_fmm_solve.restype = None
         L.oracle_fmm_sample.argtypes = [vp, vp, dbl, i32, i32, i64, vp, vp, vp, vp]
         L.oracle_fmm_sample.restype = None
+        L.oracle_fmm_sample_given.argtypes = [vp, vp, vp, dbl, i32, i32, i64, vp, vp, vp]
+        L.oracle_fmm_sample_given.restype = None
         L.oracle_inner_moments.argtypes = [vp, vp, i32, vp]
         L.oracle_inner_moments.restype = None
         L.oracle_direct.argtypes = [i64, vp, vp, i32, vp, vp]
@@ -142,6 +144,20 @@ def sample(tree: Tree, rho: np.ndarray, theta: float, idx: np.ndarray, amc: bool
                             int(idx.size), _p(idx), _p(phi), _p(g), _p(cnt))
     if with_counts:
         return phi, g, {"m2l": int(cnt[0]), "p2p_same": int(cnt[1]), "p2p_mixed": int(cnt[2])}
+    return phi, g
+
+
+def sample_given(tree: Tree, rho: np.ndarray, inner_mom: np.ndarray, theta: float,
+                 idx: np.ndarray, amc: bool = True, nthreads: int = 0):
+    """phi, g at the listed leaf cells with the refined cells' multipoles taken from inner_mom
+    ((n_refined_cells, 40), as inner_moments returns them) instead of formed from rho."""
+    rho = _f64(rho)
+    inner_mom = _f64(inner_mom)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    phi = np.empty(idx.size)
+    g = np.empty((idx.size, 3))
+    lib().oracle_fmm_sample_given(tree._h, _p(rho), _p(inner_mom), float(theta), int(bool(amc)),
+                                  int(nthreads), int(idx.size), _p(idx), _p(phi), _p(g))
     return phi, g
 
 

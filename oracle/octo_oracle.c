@@ -794,6 +794,25 @@ void oracle_fmm_sample(const otree *t, const double *rho, double theta, int amc,
   free(C.inner_mom);
 }
 
+/* The same evaluation with the multipoles of the refined cells given by the caller (inner_mom,
+ * in the layout of oracle_inner_moments) instead of formed from rho: a rank of a decomposed solve
+ * evaluates its cells from its own moments, the summed moments of the shared coarse cells and
+ * the moments and densities it received from other ranks.  Entries the evaluation should never
+ * read may hold NaN. */
+void oracle_fmm_sample_given(const otree *t, const double *rho, const double *inner_mom, double theta,
+                             int amc, int nthreads, int64_t ns, const int64_t *idx, double *phi,
+                             double *g) {
+  nthreads = resolve_threads(nthreads);
+  ctx_t C = {t, rho, (double *)inner_mom};
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+  for (int64_t q = 0; q < ns; ++q) {
+    int lev = 0;
+    int64_t gc[3] = {0, 0, 0};
+    leaf_cell_coords(t, idx[q], &lev, gc);
+    leaf_solve(&C, lev, gc, theta, amc, NULL, phi + q, g + 3 * q, NULL);
+  }
+}
+
 /* Multipoles (m, X[3], M2[9], M3[27]) of every cell of every refined subgrid, in canonical
  * refined-subgrid order, from the definition. */
 void oracle_inner_moments(const otree *t, const double *rho, int nthreads, double *out) {

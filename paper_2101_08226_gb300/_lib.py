@@ -26,7 +26,7 @@ FMM_DF64 = 2
 EXPORTS = [
     "fmm_build_tree", "fmm_destroy", "fmm_build_forest", "fmm_forest_info", "fmm_solve_batch", "fmm_tree_info", "fmm_tree_subgrids", "fmm_stencil",
     "fmm_interaction_counts", "fmm_interaction_counts_by_type", "fmm_last_launches", "fmm_solve", "fmm_solve_dt", "fmm_sync_status", "fmm_solve_host",
-    "fmm_net_force_torque", "fmm_net_force_torque_points_static", "fmm_set_profiling", "fmm_set_graphs", "fmm_set_wait_limit", "fmm_set_variant", "fmm_autotune", "fmm_binary_diagnostics", "fmm_binary_iterate", "fmm_phase_times", "fmm_measure_fma_rate", "fmm_scf_init", "fmm_scf_iterate", "fmm_last_error",
+    "fmm_net_force_torque", "fmm_net_force_torque_points_static", "fmm_set_profiling", "fmm_set_graphs", "fmm_set_wait_limit", "fmm_set_variant", "fmm_autotune", "fmm_binary_diagnostics", "fmm_binary_iterate", "fmm_phase_times", "fmm_measure_fma_rate", "fmm_scf_init", "fmm_scf_iterate", "fmm_partition", "fmm_ghosts", "fmm_last_error",
 ]
 
 _lib = None
@@ -83,6 +83,8 @@ def lib():
             "fmm_phase_times": (i32, [vp, vp, i32]),
             "fmm_measure_fma_rate": (i32, [i32, i32, vp, vp, vp]),
             "fmm_scf_init": (i32, [vp, vp, vp, dbl, vp, vp, vp]),
+            "fmm_partition": (i32, [vp, i32, i32, vp]),
+            "fmm_ghosts": (i32, [vp, vp, i32, vp, i64, vp]),
             "fmm_scf_iterate": (i32, [vp, vp, i32, vp, vp, vp, vp, vp, vp]),
             "fmm_last_error": (C.c_char_p, []),
         }

@@ -111,6 +111,21 @@ class Tree:
                 "p2p_same", "p2p_mixed")
         return dict(zip(keys, (int(v) for v in out)))
 
+    def partition(self, n_ranks: int, cut_level: int) -> np.ndarray:
+        """fmm_partition: the rank of every subgrid (-1: kept by every rank)."""
+        out = np.empty(self.info()[0], dtype=np.int32)
+        check(lib().fmm_partition(self._h, int(n_ranks), int(cut_level), _p(out)))
+        return out
+
+    def ghosts(self, owner: np.ndarray, rank: int) -> np.ndarray:
+        """fmm_ghosts: the subgrids other ranks own whose data `rank` reads."""
+        owner = np.ascontiguousarray(owner, dtype=np.int32)
+        n = C.c_int64()
+        check(lib().fmm_ghosts(self._h, _p(owner), int(rank), None, 0, C.byref(n)))
+        out = np.empty(max(n.value, 1), dtype=np.int32)
+        check(lib().fmm_ghosts(self._h, _p(owner), int(rank), _p(out), n.value, C.byref(n)))
+        return out[:n.value]
+
     def last_launches(self) -> int:
         n = C.c_int32()
         check(lib().fmm_last_launches(self._h, C.byref(n)))

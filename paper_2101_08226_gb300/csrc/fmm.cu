@@ -4308,6 +4308,35 @@ int fmm_net_force_torque_points_static(int64_t n, const double* x_dev, const dou
   return FMM_OK;
 }
 
+int fmm_partition(const fmm_tree* t, int n_ranks, int cut_level, int32_t* owner_host) {
+  if (!t || !owner_host) return fail(FMM_ERR_ARG, "null argument");
+  try {
+    std::vector<int32_t> owner;
+    std::string err = partition_tree(t->h, n_ranks, cut_level, owner);
+    if (!err.empty()) return fail(FMM_ERR_ARG, err);
+    std::copy(owner.begin(), owner.end(), owner_host);
+    return FMM_OK;
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+}
+
+int fmm_ghosts(const fmm_tree* t, const int32_t* owner_host, int rank, int32_t* ghosts_host,
+               int64_t capacity, int64_t* count) {
+  if (!t || !owner_host || !count || capacity < 0 || (capacity > 0 && !ghosts_host))
+    return fail(FMM_ERR_ARG, "null argument or negative capacity");
+  try {
+    std::vector<int32_t> owner(owner_host, owner_host + t->h.n_sub), out;
+    std::string err = ghost_subgrids(t->h, owner, rank, out);
+    if (!err.empty()) return fail(FMM_ERR_ARG, err);
+    *count = int64_t(out.size());
+    for (int64_t k = 0; k < int64_t(out.size()) && k < capacity; ++k) ghosts_host[k] = out[size_t(k)];
+    return FMM_OK;
+  } catch (...) {
+    return fail(FMM_ERR_NOMEM, "host allocation failed");
+  }
+}
+
 int fmm_scf_init(fmm_tree* t, const fmm_scf_params* p, const double* rho_dev, double K0,
                  double* phi_dev, double* g_dev, void* stream) {
   ScfProblem P;

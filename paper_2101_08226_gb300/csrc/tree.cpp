@@ -336,3 +336,97 @@ void interaction_counts(const HostTree& t, const Stencil& st, int64_t out[3]) {
 }
 
 }  // namespace octofmm
+
+namespace octofmm {
+
+// Spatial decomposition of one tree (the multi-node runs of Sec. 5 split one tree over nodes).
+// Units in Morton order at the cut level: every subgrid of the cut level (with its whole
+// subtree) and every leaf subgrid coarser than the cut (a leaf at level l < c stands at the cut
+// level's key of its first corner, (i, j, k) << (c - l)).  The ordered units are split into
+// n_ranks contiguous runs of about equal leaf-cell count; a subgrid finer than the cut belongs to
+// the rank of its cut-level ancestor.  Refined subgrids coarser than the cut are every rank's
+// (owner -1): each rank forms their moments from its share of the leaves, the shares are summed
+// over the ranks, and each rank evaluates their interactions itself.
+std::string partition_tree(const HostTree& t, int n_ranks, int cut, std::vector<int32_t>& owner) {
+  if (t.n_trees != 1) return "the decomposition takes a single tree";
+  if (n_ranks < 1) return "n_ranks must be >= 1";
+  if (cut < 0 || cut > t.depth) return "cut level outside the tree";
+  owner.assign(size_t(t.n_sub), -1);
+  struct Unit {
+    uint64_t key;
+    int32_t s;
+    int64_t weight;
+  };
+  std::vector<Unit> units;
+  std::vector<int64_t> leaves_below(size_t(t.n_sub), 0);
+  for (int l = t.depth; l >= 0; --l)
+    for (int64_t s = t.lev_off[l]; s < t.lev_off[l + 1]; ++s) {
+      if (t.leaf[s]) {
+        leaves_below[s] = 1;
+      } else {
+        for (int o = 0; o < 8; ++o) leaves_below[s] += leaves_below[t.child[8 * s + o]];
+      }
+    }
+  for (int l = 0; l <= cut; ++l)
+    for (int64_t s = t.lev_off[l]; s < t.lev_off[l + 1]; ++s) {
+      if (l < cut && !t.leaf[s]) continue;
+      const int sh = cut - l;
+      units.push_back(Unit{morton(cut, int64_t(t.ijk[3 * s]) << sh, int64_t(t.ijk[3 * s + 1]) << sh,
+                                  int64_t(t.ijk[3 * s + 2]) << sh),
+                           int32_t(s), leaves_below[s] * kCells});
+    }
+  std::stable_sort(units.begin(), units.end(), [](const Unit& a, const Unit& b) { return a.key < b.key; });
+  int64_t total = 0;
+  for (const Unit& u : units) total += u.weight;
+  // rank r takes the units whose cumulative weight midpoint falls in [r, r + 1) total / n_ranks
+  int64_t acc = 0;
+  std::vector<int32_t> unit_rank(units.size());
+  for (size_t k = 0; k < units.size(); ++k) {
+    const double mid = double(acc) + 0.5 * double(units[k].weight);
+    int r = int(mid * n_ranks / double(total > 0 ? total : 1));
+    unit_rank[k] = std::min(r, n_ranks - 1);
+    acc += units[k].weight;
+  }
+  for (size_t k = 0; k < units.size(); ++k) owner[size_t(units[k].s)] = unit_rank[k];
+  for (int l = cut + 1; l <= t.depth; ++l)
+    for (int64_t s = t.lev_off[l]; s < t.lev_off[l + 1]; ++s) owner[s] = owner[size_t(t.parent[s])];
+  return "";
+}
+
+// The subgrids whose data rank `rank` reads but another rank owns (ghosts): for every subgrid the
+// rank owns or shares (owner -1), its 26 same-level neighbours (multipole partners lie within one
+// subgrid for theta >= 0.34); for every leaf it owns, also the leaf children of its refined
+// neighbours (direct partners across the level jump) and the leaf neighbours of each of its
+// ancestors (direct partners at coarser levels).  A leaf ghost is read as its densities, a refined
+// ghost as its cells' moments.  Sorted, without repeats.
+std::string ghost_subgrids(const HostTree& t, const std::vector<int32_t>& owner, int rank,
+                           std::vector<int32_t>& out) {
+  if (owner.size() != size_t(t.n_sub)) return "owner array of the wrong size";
+  std::vector<uint8_t> need(size_t(t.n_sub), 0);
+  auto mark = [&](int32_t q) {
+    if (q >= 0 && owner[size_t(q)] >= 0 && owner[size_t(q)] != rank) need[size_t(q)] = 1;
+  };
+  for (int64_t s = 0; s < t.n_sub; ++s) {
+    const int32_t o = owner[size_t(s)];
+    if (o != rank && o != -1) continue;
+    for (int k = 0; k < 27; ++k) mark(t.nbr[27 * s + k]);
+    if (o != rank || !t.leaf[s]) continue;
+    for (int k = 0; k < 27; ++k) {
+      const int32_t q = t.nbr[27 * s + k];
+      if (q < 0 || t.leaf[q]) continue;
+      for (int c = 0; c < 8; ++c)
+        if (t.leaf[t.child[8 * q + c]]) mark(t.child[8 * q + c]);
+    }
+    for (int32_t a = t.parent[s]; a >= 0; a = t.parent[a])
+      for (int k = 0; k < 27; ++k) {
+        const int32_t q = t.nbr[27 * a + k];
+        if (q >= 0 && t.leaf[q]) mark(q);
+      }
+  }
+  out.clear();
+  for (int64_t s = 0; s < t.n_sub; ++s)
+    if (need[size_t(s)]) out.push_back(int32_t(s));
+  return "";
+}
+
+}  // namespace octofmm

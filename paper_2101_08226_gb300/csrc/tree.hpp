@@ -59,6 +59,12 @@ void interaction_counts(const HostTree& t, const Stencil& s, int64_t out[3]);
 // out[6]: M2L leaf<-leaf, leaf<-refined, refined<-leaf, refined<-refined, direct same, mixed.
 void interaction_counts_by_type(const HostTree& t, const Stencil& s, int64_t out[6]);
 
+// Spatial decomposition of a single tree over n_ranks (Morton-contiguous below the cut level,
+// refined subgrids above it shared) and the ghost subgrids a rank reads from other ranks.
+std::string partition_tree(const HostTree& t, int n_ranks, int cut, std::vector<int32_t>& owner);
+std::string ghost_subgrids(const HostTree& t, const std::vector<int32_t>& owner, int rank,
+                           std::vector<int32_t>& out);
+
 OCTO_HD inline int32_t pack_offset(int dx, int dy, int dz) {
   return ((dx + 16) << 10) | ((dy + 16) << 5) | (dz + 16);
 }
