@@ -28,6 +28,7 @@
 #include <string>
 #include <tuple>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/octo_fmm.h"
@@ -1243,6 +1244,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (clock64() - t0 > limit) return false;
   return true;
 }
+// Waits like mbar_wait_bounded, but suspended in the barrier (try_wait with a 20 us hint) rather
+// than spinning, so a waiting warp takes no issue slots from the warps still computing.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_sleep_bounded(uint64_t* bar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
 // Global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16), completing
 // `bytes` transactions on the mbarrier.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -1469,7 +1489,7 @@ __global__ void __launch_bounds__(kStagePipeThreads, 1) k_m2l_stage_pipe(DevArgs
     int last = -1;  // the last class issued
     for (int cl = 0; cl < 8; ++cl) {
       const int b = cl & 1;
-      if (cl >= 2 && !mbar_wait_bounded(&empty[b], uint32_t(((cl - 2) >> 1) & 1), A.wait_cycles)) {
+      if (cl >= 2 && !mbar_sleep_bounded(&empty[b], uint32_t(((cl - 2) >> 1) & 1), A.wait_cycles)) {
         if (lane == 0) atomicOr(A.status, 4);
         break;
       }
@@ -1479,7 +1499,7 @@ __global__ void __launch_bounds__(kStagePipeThreads, 1) k_m2l_stage_pipe(DevArgs
     // every copy this warp issued has landed before the block's shared memory is released: the
     // last class issued into each buffer (earlier ones were waited for before it was reissued)
     for (int cl = last; cl >= 0 && cl >= last - 1; --cl)
-      mbar_wait_bounded(&full[cl & 1], uint32_t((cl >> 1) & 1), kStageWaitCycles);
+      mbar_sleep_bounded(&full[cl & 1], uint32_t((cl >> 1) & 1), kStageWaitCycles);
     return;
   }
   const int parity = w >> 1;
@@ -1495,7 +1515,7 @@ __global__ void __launch_bounds__(kStagePipeThreads, 1) k_m2l_stage_pipe(DevArgs
   for (int cl = 0; cl < 8; ++cl) {
     const int bi = cl & 1;
     // every lane waits (the wait is also what makes the producer's zero fills visible)
-    if (!mbar_wait_bounded(&full[bi], uint32_t((cl >> 1) & 1), A.wait_cycles)) {
+    if (!mbar_sleep_bounded(&full[bi], uint32_t((cl >> 1) & 1), A.wait_cycles)) {
       atomicOr(A.status, 4);
       return;  // the producer waits for its own copies before the block ends
     }
@@ -2782,6 +2802,7 @@ struct fmm_tree {
   ScfPartial* d_scf_part = nullptr;
   ScfAxisPartial* d_scf_apart = nullptr;
   bool scf_started = false;               // fmm_scf_init has enqueued an initial state
+  int prio_high = 0;                      // the device's highest stream priority
   bool df_ready = false;
   dfloat *d_momff = nullptr, *d_massff = nullptr;
   double *d_smom = nullptr, *d_smtl = nullptr, *d_sloc = nullptr;
@@ -2942,6 +2963,7 @@ static int ensure_device(fmm_tree* t) {
   // ahead of the waiting blocks of the long kernel beside it.
   int prio_low = 0, prio_high = 0;
   CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  t->prio_high = prio_high;
   CUDA_TRY(cudaStreamCreateWithPriority(&t->stream, cudaStreamNonBlocking, prio_high));
   CUDA_TRY(cudaStreamCreateWithPriority(&t->stream2, cudaStreamNonBlocking, prio_low));
   CUDA_TRY(cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming));
@@ -3408,6 +3430,25 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   return A;
 }
 
+// Launches kernel k on stream st with a scheduling priority given as a launch attribute (captured
+// graphs keep it as the kernel node's priority, which a stream's own priority does not reliably
+// become).
+template <typename... P, typename... Args>
+static cudaError_t launch_prio(int prio, void (*k)(P...), dim3 grid, dim3 block, size_t smem,
+                               cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = prio;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 static inline unsigned blocks_for(int64_t n, int threads) {
   return unsigned((n + threads - 1) / threads);
 }
@@ -3513,16 +3554,16 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   // then the octants with refined children, finest level first
   const int64_t n_walsh = t->oct_leaf_off[h.depth + 1];
   if (n_walsh > 0) {
-    k_m2m<<<unsigned(n_walsh), kM2MThreads, 0, st>>>(A, t->d_oct_leaf, int(n_walsh), nullptr, mode);
-    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(launch_prio(t->prio_high, k_m2m, dim3(unsigned(n_walsh)), dim3(kM2MThreads), 0, st, A,
+                         (const int32_t*)t->d_oct_leaf, int(n_walsh), (const int32_t*)nullptr, mode));
     ++nl;
   }
   for (int l = h.depth - 1; l >= 0; --l) {
     const int64_t nr_oct = t->oct_ref_off[l + 1] - t->oct_ref_off[l];
     if (nr_oct > 0) {
-      k_m2m<<<unsigned(nr_oct * 8), kM2MThreads, 0, st>>>(A, nullptr, 0, t->d_oct_ref + t->oct_ref_off[l],
-                                                          mode);
-      CUDA_TRY(cudaGetLastError());
+      CUDA_TRY(launch_prio(t->prio_high, k_m2m, dim3(unsigned(nr_oct * 8)), dim3(kM2MThreads), 0, st, A,
+                           (const int32_t*)nullptr, 0, (const int32_t*)(t->d_oct_ref + t->oct_ref_off[l]),
+                           mode));
       ++nl;
     }
   }
@@ -3550,9 +3591,11 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   if (split2) {
     if ((rc = record(t, 6, st))) return rc;
     if (v_ref == 3)
-      k_m2l_stage_pipe<<<unsigned(t->work.size()), kStagePipeThreads, kStageSmem, st>>>(A, t->d_work, amc);
+      CUDA_TRY(launch_prio(t->prio_high, k_m2l_stage_pipe, dim3(unsigned(t->work.size())),
+                           dim3(kStagePipeThreads), kStageSmem, st, A, (const int32_t*)t->d_work, amc));
     else
-      k_m2l_stage<false><<<unsigned(t->work.size()), kStageThreads, kStageSmem, st>>>(A, t->d_work, amc);
+      CUDA_TRY(launch_prio(t->prio_high, k_m2l_stage<false>, dim3(unsigned(t->work.size())),
+                           dim3(kStageThreads), kStageSmem, st, A, (const int32_t*)t->d_work, amc));
     CUDA_TRY(cudaGetLastError());
     ++nl;
     if ((rc = record(t, 7, st))) return rc;
