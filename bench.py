@@ -193,10 +193,13 @@ def algorithmic_flops(counts):
     return sum(FLOPS[k] * v for k, v in counts.items())
 
 
-def measure_paper_binary(tree_api, synth, torch, dev, stream, steps, flush):
+def measure_paper_binary(tree_api, synth, torch, dev, stream, steps, flush, graded=False):
     """The merger binary in the paper's proportions (9 levels, theta = 0.34, 2.07M leaf cells):
-    the same metric on the paper's deepest tree and smallest opening angle."""
-    w = synth.workload_paper_binary()
+    the same metric on the paper's deepest tree and smallest opening angle.  graded: the same
+    binary refined by the mass-based reading of the density criterion (one level per factor 8 in
+    density below rho_peak / 8; leaves on every level from 2 to 9)."""
+    w = (synth.workload_paper_binary(graded=True, refine_frac=0.125) if graded
+         else synth.workload_paper_binary())
     t = tree_api.Tree(w.max_level, w.flags)
     n_sub, n_leaf_sub, _ = t.info()
     rho0 = synth.leaf_density(w.field, t.leaves())
@@ -205,9 +208,11 @@ def measure_paper_binary(tree_api, synth, torch, dev, stream, steps, flush):
             for k in range(steps + 2)]
     counts = t.counts_by_type(w.theta)
     n_m2l = sum(v for k, v in counts.items() if k.startswith("m2l"))
+    rule = ("graded refinement: level 9 above rho_peak/8, one level less per factor 8 in density"
+            if graded else "refine_frac 1e-4")
     out = {"workload": "merger binary in the paper's proportions: q=0.5, accretor 50 finest cells "
-                       "across, donor filling its Roche lobe, a=0.024 of the box, 9 levels, "
-                       "refine_frac 1e-4, theta=0.34",
+                       f"across, donor filling its Roche lobe, a=0.024 of the box, 9 levels, {rule}, "
+                       "theta=0.34",
            "subgrids": n_sub, "leaf_cells": n_leaf_sub * 512, "m2l_pairs": n_m2l,
            "pair_types": counts, "l2": "flushed before every timed solve"}
     for precision in ("fp64", "mixed"):
@@ -382,6 +387,8 @@ def run_solve_only(args):
         w = small_workload(synth)
     tree = api.Tree(w.max_level, w.flags)
     rho = torch.from_numpy(synth.leaf_density(w.field, tree.leaves())).cuda()
+    if args.variant is not None:
+        tree.set_variant(theta, args.variant)
     for _ in range(args.warmup + args.steps):
         phi, g, net = tree.solve(rho, theta, args.solve_only, True)
     torch.cuda.synchronize()
@@ -672,6 +679,8 @@ def run_ours(args):
     small = measure_small(api, synth, torch, timer, dev, min(args.steps, 10), peaks, rank)
     batched = measure_batched(api, synth, torch, dev, stream, min(args.steps, 3))
     paper = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), timer.flush)
+    graded = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), timer.flush,
+                                  graded=True)
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -710,11 +719,12 @@ def run_ours(args):
                   "ms_per_step_direct_launches": r32d["total_ms"] / min(args.steps, 5),
                   "autotune": {"variant": int(tuned_variant),
                                "median_ms_per_variant": [round(float(x), 4) for x in tuned_ms],
-                               "variants": "r + 4 l; r: refined targets 0 staged on a second "
-                                           "stream, 1 staged on one stream, 2 per-parity blocks "
-                                           "from L2, 3 staged with a copy-issuing warp and "
+                               "variants": "r + 4 l + 8 p; r: refined targets 0 staged on a "
+                                           "second stream, 1 staged on one stream, 2 per-parity "
+                                           "blocks from L2, 3 staged with a copy-issuing warp and "
                                            "full / empty barriers; l: leaf kernel 0 four targets "
-                                           "per lane, 1 two per thread"},
+                                           "per lane, 1 two per thread; p: leaf kernel 0 beside "
+                                           "the upward pass, 1 after it"},
                   "gpu_launches": r32["launches"]},
         "df64": {"value": whole_job_rate(world, n_m2l, args.steps, tdf),
                  "ms_per_step": tdf / args.steps, "ms_per_step_median": med(rdf),
@@ -734,6 +744,7 @@ def run_ours(args):
         "small": small,
         "batched": batched,
         "paper_binary": paper,
+        "paper_binary_graded": graded,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
@@ -752,6 +763,8 @@ def main():
     ap.add_argument("--solve-workload", choices=["binary5", "binary7", "paper9"], default="binary5",
                     help="with --solve-only: the 5-level binary (default), the 7-level headline "
                          "binary or the 9-level merger binary in the paper's proportions")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="with --solve-only mixed: the launch variant (fmm_set_variant)")
     ap.add_argument("--solve-only", choices=["fp64", "mixed", "df64"], default=None,
                     help="profiling driver: run warmup + steps solves of the benchmark tree, no timing")
     args = ap.parse_args()

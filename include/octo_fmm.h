@@ -47,6 +47,10 @@ extern "C" {
 #define FMM_ERR_STATE (-8)     /* tree not usable (destroyed or built on another device) */
 #define FMM_ERR_TIMEOUT (-9)   /* a kernel's bounded wait for its shared-memory copies gave up
                                   (found on the device; that block's results are missing) */
+#define FMM_ERR_BOUNDS (-10)   /* an index read from the library's tables failed its range check;
+                                  only the bounds-checked build of the library
+                                  (libocto_fmm_bc.so, compiled with -DFMM_BOUNDS_CHECK) checks,
+                                  skipping the access instead of making it */
 
 #define FMM_FP64 0  /* every step in FP64 */
 #define FMM_MIXED 1 /* multipole interactions and direct sums in FP32, expansions in FP32;
@@ -203,7 +207,7 @@ int fmm_binary_iterate(fmm_tree* tree, const double* rho_dev, const double* g_de
                        const double* x1, const double* x2, int n_iter, double* out_dev,
                        double* centres_dev, double* torque_dev, int8_t* member_dev, void* stream);
 
-/* Launch variants of the mixed path (FMM_MIXED), per tree and theta: variant = r + 4 l with
+/* Launch variants of the mixed path (FMM_MIXED), per tree and theta: variant = r + 4 l + 8 p with
  *   r = 0: refined targets by the shared-memory staging kernel on a second stream, beside the
  *          leaf and boundary kernels (the default);
  *   r = 1: the same kernel after them, on one stream;
@@ -211,12 +215,15 @@ int fmm_binary_iterate(fmm_tree* tree, const double* rho_dev, const double* g_de
  *   r = 3: as r = 0 with the staging pipelined: a separate warp issues the copies and each buffer
  *          has its own full and empty barriers, so the evaluating warps never meet;
  *   l = 0: leaf pairs by the four-targets-per-lane FP32 kernel (the default);
- *   l = 1: leaf pairs by the two-targets-per-thread kernel.
- * r = 0, 1 and 3 give the same results bit for bit, and so do l = 0 and 1; r = 2 sums the refined
- * targets' pairs in another order (results differ at FP32 rounding, within the mixed path's
- * tolerance).  FMM_ERR_ARG for a variant outside [0, FMM_MIXED_VARIANTS), FMM_ERR_THETA for a
- * theta outside [0.34, 1).  The FP64 and df64 paths have one launch configuration. */
-#define FMM_MIXED_VARIANTS 8
+ *   l = 1: leaf pairs by the two-targets-per-thread kernel;
+ *   p = 0: the leaf-pair kernel starts beside the upward pass (the default);
+ *   p = 1: it starts after the upward pass, beside the refined targets' kernel.
+ * Variants that differ in r among 0, 1, 3, in l, or in p give the same results bit for bit; r = 2
+ * sums the refined targets' pairs in another order (results differ at FP32 rounding, within the
+ * mixed path's tolerance).  FMM_ERR_ARG for a variant outside [0, FMM_MIXED_VARIANTS),
+ * FMM_ERR_THETA for a theta outside [0.34, 1).  The FP64 and df64 paths have one launch
+ * configuration. */
+#define FMM_MIXED_VARIANTS 16
 int fmm_set_variant(fmm_tree* tree, double theta, int variant);
 
 /* Autotuner: times every launch variant of `precision` (FMM_MIXED: FMM_MIXED_VARIANTS; FP64,

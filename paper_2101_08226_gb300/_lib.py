@@ -16,7 +16,8 @@ FMM_ERR_NONFINITE = -6
 FMM_ERR_NOMEM = -7
 FMM_ERR_STATE = -8
 FMM_ERR_TIMEOUT = -9
-FMM_MIXED_VARIANTS = 8
+FMM_ERR_BOUNDS = -10
+FMM_MIXED_VARIANTS = 16
 FMM_NET_STATIC_MAX_POINTS = 2048 * 4096
 FMM_SCF_STATE = 22
 FMM_FP64 = 0
@@ -45,54 +46,58 @@ class FmmError(RuntimeError):
         self.code = code
 
 
+def load(path: str):
+    """The library at `path` with the C ABI's signatures (the normal or the bounds-checked build)."""
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library {path} is missing: run paper_2101_08226_gb300.build.build() "
+            "(there is no CPU fallback)")
+    L = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    sig = {
+        "fmm_build_tree": (i32, [i32, vp, i64, C.POINTER(vp)]),
+        "fmm_destroy": (None, [vp]),
+        "fmm_build_forest": (i32, [vp, i32, C.POINTER(vp)]),
+        "fmm_forest_info": (i32, [vp, vp, vp]),
+        "fmm_solve_batch": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
+        "fmm_solve_dt": (i32, [vp, vp, vp, dbl, i32, i32, vp, vp, vp, vp, vp]),
+        "fmm_tree_info": (i32, [vp, vp, vp, vp]),
+        "fmm_tree_subgrids": (i32, [vp, vp]),
+        "fmm_stencil": (i32, [dbl, i32, vp, i32, vp]),
+        "fmm_interaction_counts": (i32, [vp, dbl, vp]),
+        "fmm_interaction_counts_by_type": (i32, [vp, dbl, vp]),
+        "fmm_last_launches": (i32, [vp, vp]),
+        "fmm_solve": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
+        "fmm_sync_status": (i32, [vp, vp]),
+        "fmm_solve_host": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
+        "fmm_net_force_torque": (i32, [vp, vp, vp, vp, vp]),
+        "fmm_net_force_torque_points_static": (i32, [i64, vp, vp, vp, vp, vp]),
+        "fmm_set_profiling": (i32, [vp, i32]),
+        "fmm_set_graphs": (i32, [vp, i32]),
+        "fmm_set_wait_limit": (i32, [vp, C.c_longlong]),
+        "fmm_set_variant": (i32, [vp, dbl, i32]),
+        "fmm_autotune": (i32, [vp, vp, dbl, i32, i32, vp, vp, i32, vp, vp, vp]),
+        "fmm_binary_diagnostics": (i32, [vp, vp, vp, dbl, vp, vp, dbl, dbl, vp, vp, vp]),
+        "fmm_binary_iterate": (i32, [vp, vp, vp, dbl, vp, vp, i32, vp, vp, vp, vp, vp]),
+        "fmm_phase_times": (i32, [vp, vp, i32]),
+        "fmm_measure_fma_rate": (i32, [i32, i32, vp, vp, vp]),
+        "fmm_scf_init": (i32, [vp, vp, vp, dbl, vp, vp, vp]),
+        "fmm_partition": (i32, [vp, i32, i32, vp]),
+        "fmm_ghosts": (i32, [vp, vp, i32, vp, i64, vp]),
+        "fmm_scf_iterate": (i32, [vp, vp, i32, vp, vp, vp, vp, vp, vp]),
+        "fmm_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        path = _build.LIB
-        if not os.path.exists(path):
-            raise RuntimeError(
-                f"CUDA library {path} is missing: run paper_2101_08226_gb300.build.build() "
-                "(there is no CPU fallback)")
-        L = C.CDLL(path)
-        vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
-        sig = {
-            "fmm_build_tree": (i32, [i32, vp, i64, C.POINTER(vp)]),
-            "fmm_destroy": (None, [vp]),
-            "fmm_build_forest": (i32, [vp, i32, C.POINTER(vp)]),
-            "fmm_forest_info": (i32, [vp, vp, vp]),
-            "fmm_solve_batch": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
-            "fmm_solve_dt": (i32, [vp, vp, vp, dbl, i32, i32, vp, vp, vp, vp, vp]),
-            "fmm_tree_info": (i32, [vp, vp, vp, vp]),
-            "fmm_tree_subgrids": (i32, [vp, vp]),
-            "fmm_stencil": (i32, [dbl, i32, vp, i32, vp]),
-            "fmm_interaction_counts": (i32, [vp, dbl, vp]),
-            "fmm_interaction_counts_by_type": (i32, [vp, dbl, vp]),
-            "fmm_last_launches": (i32, [vp, vp]),
-            "fmm_solve": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
-            "fmm_sync_status": (i32, [vp, vp]),
-            "fmm_solve_host": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
-            "fmm_net_force_torque": (i32, [vp, vp, vp, vp, vp]),
-            "fmm_net_force_torque_points_static": (i32, [i64, vp, vp, vp, vp, vp]),
-            "fmm_set_profiling": (i32, [vp, i32]),
-            "fmm_set_graphs": (i32, [vp, i32]),
-            "fmm_set_wait_limit": (i32, [vp, C.c_longlong]),
-            "fmm_set_variant": (i32, [vp, dbl, i32]),
-            "fmm_autotune": (i32, [vp, vp, dbl, i32, i32, vp, vp, i32, vp, vp, vp]),
-            "fmm_binary_diagnostics": (i32, [vp, vp, vp, dbl, vp, vp, dbl, dbl, vp, vp, vp]),
-            "fmm_binary_iterate": (i32, [vp, vp, vp, dbl, vp, vp, i32, vp, vp, vp, vp, vp]),
-            "fmm_phase_times": (i32, [vp, vp, i32]),
-            "fmm_measure_fma_rate": (i32, [i32, i32, vp, vp, vp]),
-            "fmm_scf_init": (i32, [vp, vp, vp, dbl, vp, vp, vp]),
-            "fmm_partition": (i32, [vp, i32, i32, vp]),
-            "fmm_ghosts": (i32, [vp, vp, i32, vp, i64, vp]),
-            "fmm_scf_iterate": (i32, [vp, vp, i32, vp, vp, vp, vp, vp, vp]),
-            "fmm_last_error": (C.c_char_p, []),
-        }
-        for name, (res, args) in sig.items():
-            f = getattr(L, name)
-            f.restype = res
-            f.argtypes = args
-        _lib = L
+        _lib = load(_build.LIB)
     return _lib
 
 

@@ -8,6 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libocto_fmm.so")
+LIB_BC = os.path.join(OUT_DIR, "libocto_fmm_bc.so")  # index checks on (FMM_BOUNDS_CHECK)
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["fmm.cu", "tree.cpp", "peaks.cu", "scf.cu"]
@@ -24,18 +25,25 @@ def _deps():
     return files
 
 
+def _up_to_date(lib: str) -> bool:
+    return os.path.exists(lib) and all(os.path.getmtime(lib) >= os.path.getmtime(f) for f in _deps())
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    if (not force and os.path.exists(LIB)
-            and all(os.path.getmtime(LIB) >= os.path.getmtime(f) for f in _deps())):
+    """Builds libocto_fmm.so and, from the same sources with -DFMM_BOUNDS_CHECK, the index-checked
+    libocto_fmm_bc.so (used by its own tests), compiling every translation unit of both in
+    parallel.  Returns the path of libocto_fmm.so."""
+    if not force and _up_to_date(LIB) and _up_to_date(LIB_BC):
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
     common = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
-    objs = []
 
-    def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(job):
+        src, checked = job
+        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ("_bc" if checked else "") + ".o")
+        cmd = [nvcc] + common + (["-DFMM_BOUNDS_CHECK"] if checked else []) + \
+            ["-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-c",
                    os.path.join(CSRC, src), "-o", obj]
@@ -44,11 +52,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
         subprocess.run(cmd, check=True)
         return obj
 
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
-    os.replace(tmp, LIB)
+    # the host-only tree code is shared; the CUDA sources are compiled twice
+    jobs = [(src, False) for src in SOURCES] + [(src, True) for src in SOURCES if src.endswith(".cu")]
+    with ThreadPoolExecutor(len(jobs)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    plain = objs[:len(SOURCES)]
+    checked = objs[len(SOURCES):] + [o for o, (src, _) in zip(plain, jobs) if src.endswith(".cpp")]
+    for lib, parts in ((LIB, plain), (LIB_BC, checked)):
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + parts, check=True)
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -57,6 +57,18 @@ int fmm_record_error(int code, const char* msg) { return fail(code, msg); }
       return fail(FMM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));    \
   } while (0)
 
+// Index checks of the bounds-checked build (-DFMM_BOUNDS_CHECK, libocto_fmm_bc.so): before an
+// access through an index read from a table (neighbours, children, leaf ordinals, work lists,
+// pair lists, stencil tables), the index is tested against its array; a failed test records
+// status bit 8 (FMM_ERR_BOUNDS) and the access is skipped (FMM_SKIP: the thread leaves the kernel
+// or the loop iteration; FMM_CLAMP: the index is replaced by a safe one where the thread must
+// stay for a barrier or a warp shuffle).  Nothing traps.  The normal build compiles none of it.
+#ifdef FMM_BOUNDS_CHECK
+#define FMM_BAD(A, cond) (!(cond) ? (atomicOr((A).status, 8), true) : false)
+#else
+#define FMM_BAD(A, cond) false
+#endif
+
 // ----------------------------------------------------------------------------------------------
 // device-side tree and workspace
 // ----------------------------------------------------------------------------------------------
@@ -158,7 +170,8 @@ constexpr int kLeafThreads = 256;    // one block = one leaf subgrid, two target
 constexpr int kRootChunks = 8;       // root sources split into 8 chunks of 64 cells
 constexpr int kM2LThreads = 64;      // one block = the 64 cells of one parity of one subgrid
 constexpr int kSplitLanes = 4;       // lanes per target in k_m2l_split's long-list blocks
-constexpr int kMixedVariants = 8;    // mixed path launch variants: refined (4) x leaf kernel (2)
+constexpr int kMixedVariants = 16;   // mixed path launch variants: refined (4) x leaf kernel (2)
+                                     // x leaf kernel placement (2)
 constexpr int kReduceThreads = 256;
 constexpr int kReduceBlocks = 1216;  // 8 per SM
 
@@ -211,10 +224,11 @@ __global__ void k_p2m(DevArgs A, int mixed) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= A.n_leaf_cells) return;
   int32_t s = A.leaf_sub[i >> 9];
+  const int k = A.leaf_tree[i >> 9];
+  if (FMM_BAD(A, s >= 0 && int64_t(s) * kCells < A.n_cell && k >= 0 && k < A.n_roots)) return;
   int lev = A.level[s];
   const int u = int(i & 511);
   int64_t cell = int64_t(s) * kCells + cidx(u >> 6, (u >> 3) & 7, u & 7);
-  const int k = A.leaf_tree[i >> 9];
   double r = A.io[k].rho[i - A.tree_leaf_off[k] * kCells];
   // finite and >= 0, tested on the bit pattern (a double compare runs on the FP64 pipe): +0 up to
   // the largest finite value lie below the exponent mask, and -0 is the sign bit alone
@@ -304,6 +318,9 @@ __device__ __forceinline__ void m2m_walsh(const DevArgs& A, const int32_t* __res
   const int o = code & 7, u = int(threadIdx.x);
   int a, b, c;
   octant_cell(o, u, a, b, c);
+  if (FMM_BAD(A, s >= 0 && int64_t(s) * kCells < A.n_cell && A.child[8 * s + o] >= 0 &&
+                    int64_t(A.child[8 * s + o]) * kCells < A.n_cell))
+    return;
   const int64_t c0 = int64_t(A.child[8 * s + o]) * kCells + u;  // child e at c0 + (e << 6)
   double v[8];
 #pragma unroll
@@ -371,7 +388,9 @@ __device__ __forceinline__ void m2m_lanes(const DevArgs& A, const int32_t* __res
   octant_cell(o, u, a, b, c);
   const int64_t N = A.n_cell;
   const double hc = cell_dx(A.level[s] + 1);
-  const int64_t ci = int64_t(A.child[8 * s + o]) * kCells + u + (e << 6);
+  int64_t ci = int64_t(A.child[8 * s + o]) * kCells + u + (e << 6);
+  const bool bad = FMM_BAD(A, A.child[8 * s + o] >= 0 && ci < N);
+  if (bad) ci = 0;  // stays for the shuffles; nothing is stored
   // this child's centre of mass relative to the parent cell's geometric centre
   const double m = A.mom[ci];
   const double ux = (((e >> 2) & 1) ? 0.5 : -0.5) * hc + A.mom[N + ci],
@@ -450,7 +469,7 @@ __device__ __forceinline__ void m2m_lanes(const DevArgs& A, const int32_t* __res
     const int owner = ((j >> 3) & 1) << 2 | ((j >> 2) & 1) << 1 | ((j >> 1) & 1);
     R[j] = __shfl_sync(0xffffffffu, F[j & 1], lead + owner);
   }
-  if (e != 0) return;
+  if (e != 0 || bad) return;
   store_moments(A, int64_t(s) * kCells + cidx(a, b, c), mt, dx, dy, dz, R, R + 6, mixed);
 }
 
@@ -947,6 +966,7 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool a
       int32_t sB = nb[slot];
       if (sB < 0) continue;  // only without proper nesting
       int64_t iB = int64_t(sB) * kCells + cidx(px & 7, py & 7, pz & 7);
+      if (FMM_BAD(A, iB < N && slot >= 0 && slot < 27)) continue;
       interact_rr<T>(S, M, N, iB, S.dAx - ldg_t(td + 4 * q) * h, S.dAy - ldg_t(td + 4 * q + 1) * h,
                      S.dAz - ldg_t(td + 4 * q + 2) * h);
     }
@@ -1066,7 +1086,7 @@ __device__ void m2l_boundary(const DevArgs& A, int64_t first, int64_t end, int c
   for (int i = threadIdx.x; i <= 2 * kCodeMax; i += blockDim.x) quarter[i] = T(i - kCodeMax) * T(0.25);
   __syncthreads();
   const int64_t k = first + int64_t(chunk) * 64 + t;
-  const bool valid = k < end;
+  const bool valid = k < end && !FMM_BAD(A, A.bt_cell[k] >= 0 && A.bt_cell[k] < A.n_cell);
   if (LANES == 1 && !valid) return;
   const int64_t iA = valid ? A.bt_cell[k] : 0;
   const int parity = int(iA & 511) >> 6;
@@ -1096,6 +1116,7 @@ __device__ void m2l_boundary(const DevArgs& A, int64_t first, int64_t end, int c
         q_next = __ldg(A.bm_q + j + LANES);
         src_next = __ldg(A.bm_src + j + LANES);
       }
+      if (FMM_BAD(A, src >= 0 && src < N && q >= 0 && q < kLeafCap)) continue;
       interact_lr<T>(S, M, N, src, -ldg_t(td + 4 * q) * h, -ldg_t(td + 4 * q + 1) * h,
                      -ldg_t(td + 4 * q + 2) * h);
     }
@@ -1113,6 +1134,10 @@ __device__ void m2l_boundary(const DevArgs& A, int64_t first, int64_t end, int c
       code_next = __ldg(A.bp_code + j + LANES);
       psrc_next = __ldg(A.bp_src + j + LANES);
     }
+    if (FMM_BAD(A, src >= 0 && src < N && unsigned(((code >> 20) & 1023) - 512 + kCodeMax) <= 2u * kCodeMax &&
+                       unsigned(((code >> 10) & 1023) - 512 + kCodeMax) <= 2u * kCodeMax &&
+                       unsigned((code & 1023) - 512 + kCodeMax) <= 2u * kCodeMax))
+      continue;
     const T x = quarter[((code >> 20) & 1023) - 512 + kCodeMax] * h;
     const T y = quarter[((code >> 10) & 1023) - 512 + kCodeMax] * h;
     const T z = quarter[(code & 1023) - 512 + kCodeMax] * h;
@@ -1277,8 +1302,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // j / 3 % 9), z run j % 3 (halo z < 0, 0 <= z < 8, z >= 8), from the neighbour subgrid that
 // holds it; an absent neighbour (only without proper nesting) gives zeros.  W floats per cell.
 template <int W>
-__device__ __forceinline__ void stage_issue(const float* __restrict__ arr, const int32_t* nb, int c, float* buf,
-                                            uint64_t* bar, int j) {
+__device__ __forceinline__ void stage_issue(const DevArgs& A, const float* __restrict__ arr, const int32_t* nb,
+                                            int c, float* buf, uint64_t* bar, int j) {
   if (j >= kStageRuns) return;
   const int rx = (c >> 2) & 1, ry = (c >> 1) & 1, rz = c & 1;
   const int lx = j / 27, ly = (j / 3) % 9, run = j % 3;
@@ -1291,7 +1316,7 @@ __device__ __forceinline__ void stage_issue(const float* __restrict__ arr, const
   const int32_t sB = nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)];
   float* dst = buf + (lx * kStageSX + ly * kStageSY + lz0) * W;
   const uint32_t bytes = uint32_t(lz1 - lz0) * uint32_t(W * 4);
-  if (sB >= 0) {
+  if (sB >= 0 && !FMM_BAD(A, int64_t(sB) * kCells < A.n_cell)) {
     // the run's cells are consecutive in the neighbour's parity-major order (cidx)
     const int64_t row = int64_t(sB) * kCells + cidx(x & 7, y & 7, z & 7);
     mbar_arrive_tx(bar, bytes);
@@ -1361,7 +1386,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) k_m2l_stage(DevArgs A, const
   const float4* __restrict__ tab = A.stage_tab + parity * kLeafCap;
   const int32_t* __restrict__ seg = A.stage_seg + parity * 9;
   __syncthreads();
-  stage_issue<W>(arr, nb, 0, buf0, &bar[0], t);
+  stage_issue<W>(A, arr, nb, 0, buf0, &bar[0], t);
   for (int cl = 0; cl < 8; ++cl) {
     const bool ok = mbar_wait_bounded(&bar[cl & 1], uint32_t((cl >> 1) & 1), A.wait_cycles);
     // block-uniform decision; also makes the zero fills of class cl visible and frees the other
@@ -1373,7 +1398,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) k_m2l_stage(DevArgs A, const
       mbar_wait_bounded(&bar[cl & 1], uint32_t((cl >> 1) & 1), kStageWaitCycles);
       return;
     }
-    if (cl < 7) stage_issue<W>(arr, nb, cl + 1, (cl & 1) ? buf0 : buf1, &bar[(cl + 1) & 1], t);
+    if (cl < 7) stage_issue<W>(A, arr, nb, cl + 1, (cl & 1) ? buf0 : buf1, &bar[(cl + 1) & 1], t);
     const float* __restrict__ B = ((cl & 1) ? buf1 : buf0) + base;
     const int q1 = __ldg(seg + cl + 1);
     const int qb = __ldg(seg + cl);
@@ -1383,6 +1408,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) k_m2l_stage(DevArgs A, const
       for (int q = q0; q < qe; ++q) {
         const float4 e = e_next;
         e_next = __ldg(tab + min(q + 1, q1 - 1));
+        if (FMM_BAD(A, unsigned(base / W + __float_as_int(e.w)) < unsigned(kStageCells))) continue;
         const float4* m = reinterpret_cast<const float4*>(B + __float_as_int(e.w) * W);
         float Mv[W];
 #pragma unroll
@@ -1424,8 +1450,9 @@ __global__ void __launch_bounds__(kStageThreads, 1) k_m2l_stage(DevArgs A, const
 constexpr int kStagePipeThreads = kStageThreads + 32;
 
 template <int W>
-__device__ __forceinline__ void stage_issue_warp(const float* __restrict__ arr, const int32_t* nb, int c,
-                                                 float* buf, uint64_t* bar, int lane) {
+__device__ __forceinline__ void stage_issue_warp(const DevArgs& A, const float* __restrict__ arr,
+                                                 const int32_t* nb, int c, float* buf, uint64_t* bar,
+                                                 int lane) {
   // lane takes runs lane, lane + 32, ...; it zero-fills its runs in absent neighbours, then
   // announces the bytes of its bulk copies with one arrive, then issues them
   uint32_t bytes = 0;
@@ -1439,7 +1466,7 @@ __device__ __forceinline__ void stage_issue_warp(const float* __restrict__ arr, 
     const int z = 2 * lz0 + rz - 5;
     const int32_t sB = nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)];
     const uint32_t n = uint32_t(lz1 - lz0) * uint32_t(W * 4);
-    if (sB >= 0) {
+    if (sB >= 0 && !FMM_BAD(A, int64_t(sB) * kCells < A.n_cell)) {
       bytes += n;
     } else {
       float* dst = buf + (lx * kStageSX + ly * kStageSY + lz0) * W;
@@ -1457,7 +1484,7 @@ __device__ __forceinline__ void stage_issue_warp(const float* __restrict__ arr, 
     const int lz1 = run == 0 ? z1 : (run == 1 ? z2 : 9);
     const int z = 2 * lz0 + rz - 5;
     const int32_t sB = nb[((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)];
-    if (sB < 0) continue;
+    if (sB < 0 || int64_t(sB) * kCells >= A.n_cell) continue;  // (the first pass zero-filled it)
     const int64_t row = int64_t(sB) * kCells + cidx(x & 7, y & 7, z & 7);
     bulk_g2s(buf + (lx * kStageSX + ly * kStageSY + lz0) * W, arr + row * W,
              uint32_t(lz1 - lz0) * uint32_t(W * 4), bar);
@@ -1493,7 +1520,7 @@ __global__ void __launch_bounds__(kStagePipeThreads, 1) k_m2l_stage_pipe(DevArgs
         if (lane == 0) atomicOr(A.status, 4);
         break;
       }
-      stage_issue_warp<W>(A.mom32, nb, cl, buf0 + b * kBufFloats, &full[b], lane);
+      stage_issue_warp<W>(A, A.mom32, nb, cl, buf0 + b * kBufFloats, &full[b], lane);
       last = cl;
     }
     // every copy this warp issued has landed before the block's shared memory is released: the
@@ -1528,6 +1555,7 @@ __global__ void __launch_bounds__(kStagePipeThreads, 1) k_m2l_stage_pipe(DevArgs
       for (int q = q0; q < qe; ++q) {
         const float4 e = e_next;
         e_next = __ldg(tab + min(q + 1, q1 - 1));
+        if (FMM_BAD(A, unsigned(base / W + __float_as_int(e.w)) < unsigned(kStageCells))) continue;
         const float4* m = reinterpret_cast<const float4*>(B + __float_as_int(e.w) * W);
         float Mv[W];
 #pragma unroll
@@ -1627,7 +1655,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
       dst[u] = i < kH3 ? ((hx & 1) << 2 | (hy & 1) << 1 | (hz & 1)) * kHaloPar + (hx >> 1) * kHaloSX +
                              (hy >> 1) * kHaloSY + (hz >> 1)
                        : -1;
-      v[u] = q >= 0 ? M[int64_t(q) * kCells + cidx(x & 7, y & 7, z & 7)] : T(0);
+      v[u] = q >= 0 && !FMM_BAD(A, int64_t(q) * kCells < N) ? M[int64_t(q) * kCells + cidx(x & 7, y & 7, z & 7)] : T(0);
     }
 #pragma unroll
     for (int u = 0; u < kFill; ++u)
@@ -1649,6 +1677,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
 #pragma unroll 4
   for (int q = 0; q < n_tab; ++q) {
     const int off = __ldg(toff + q);
+    if (FMM_BAD(A, off >= 0 && base1 + off < kHaloWords)) continue;
     T k0, kx, ky, kz;
     load4(tk + 4 * q, k0, kx, ky, kz);
     const T m0 = hm[base0 + off], m1 = hm[base1 + off];
@@ -1745,7 +1774,9 @@ __global__ void __launch_bounds__(kLeaf4Threads) k_m2l_leaf4(DevArgs A, const in
       dst[u] = i < 2 * kH3 ? h * (kHaloWords + 1) + ((hx & 1) << 2 | (hy & 1) << 1 | (hz & 1)) * kHaloPar +
                                  (hx >> 1) * kHaloSX + (hy >> 1) * kHaloSY + (hz >> 1)
                            : -1;
-      v[u] = q >= 0 ? __ldg(M + int64_t(q) * kCells + cidx(x & 7, y & 7, z & 7)) : 0.0f;
+      v[u] = q >= 0 && !FMM_BAD(A, int64_t(q) * kCells < A.n_cell)
+                 ? __ldg(M + int64_t(q) * kCells + cidx(x & 7, y & 7, z & 7))
+                 : 0.0f;
     }
 #pragma unroll
     for (int u = 0; u < kFill; ++u)
@@ -1772,7 +1803,11 @@ __global__ void __launch_bounds__(kLeaf4Threads) k_m2l_leaf4(DevArgs A, const in
     float4 kn[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) kn[u] = __ldg(tk + 4 * qn + u);
-    const int off[4] = {o.x, o.y, o.z, o.w};
+    int off[4] = {o.x, o.y, o.z, o.w};
+#ifdef FMM_BOUNDS_CHECK
+    for (int u = 0; u < 4; ++u)
+      if (FMM_BAD(A, off[u] >= 0 && li * kHaloSX + lj * kHaloSY + off[u] + 3 < kHaloWords)) off[u] = 0;
+#endif
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
 #pragma unroll
@@ -1862,7 +1897,9 @@ struct Down {
 __device__ __forceinline__ void store_leaf(const DevArgs& A, int32_t s, int a, int b, int c,
                                            double phi_v, double gx, double gy, double gz) {
   const int32_t ls = A.leaf_ord[s];
+  if (FMM_BAD(A, ls >= 0 && int64_t(ls) * kCells < A.n_leaf_cells)) return;
   const int k = A.leaf_tree[ls];
+  if (FMM_BAD(A, k >= 0 && k < A.n_roots)) return;
   const int64_t o = (int64_t(ls) - A.tree_leaf_off[k]) * kCells + (a * 8 + b) * 8 + c;
   double* __restrict__ phi = A.io[k].phi;
   double* __restrict__ g = A.io[k].g;
@@ -1944,6 +1981,7 @@ __global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* 
   const int64_t N = A.n_cell;
   if (int(blockIdx.x) < n_ref_blocks) {
     const int32_t s = ref[blockIdx.x >> 3];
+    if (FMM_BAD(A, s >= 0 && int64_t(s) * kCells < N && A.parent[s] >= 0)) return;
     const int loc = int(blockIdx.x & 7) * 64 + int(threadIdx.x);
     const int64_t i = int64_t(s) * kCells + loc;
     const int32_t Pn = A.parent[s];
@@ -1976,6 +2014,9 @@ __global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* 
   const int32_t code = octs[blockIdx.x - n_ref_blocks];
   const int32_t Pn = code >> 3;
   const int o = code & 7, u = int(threadIdx.x);
+  if (FMM_BAD(A, Pn >= 0 && int64_t(Pn) * kCells < N && A.child[8 * Pn + o] >= 0 &&
+                     int64_t(A.child[8 * Pn + o]) * kCells < N))
+    return;
   int pa, pb, pc;
   octant_cell(o, u, pa, pb, pc);
   const int64_t ip = int64_t(Pn) * kCells + cidx(pa, pb, pc);
@@ -3526,30 +3567,36 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   k_p2m<<<blocks_for(A.n_leaf_cells, 256), 256, 0, st>>>(A, mode);
   CUDA_TRY(cudaGetLastError());
   ++nl;
-  // The same-level leaf pairs need only the leaf masses: their kernel runs on the second stream
-  // from here, beside the level-by-level (latency-bound) upward pass.
-  const int v_ref = sd->mixed_variant % 4, v_leaf = sd->mixed_variant / 4;
-  CUDA_TRY(cudaEventRecord(t->ev_fork, st));
-  CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_fork, 0));
-  if ((rc = record(t, 8, t->stream2))) return rc;
-  if (t->n_work_leaf > 0) {
-    cudaStream_t s2 = t->stream2;
-    if (mixed && v_leaf == 0)
-      k_m2l_leaf4<false><<<unsigned((t->n_work_leaf + 1) / 2), kLeaf4Threads, kLeaf4Smem, s2>>>(
-          A, t->d_work_leaf, t->n_work_leaf);
-    else if (mixed)
-      k_m2l_leaf<float, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), s2>>>(
-          A, t->d_work_leaf);
-    else if (df)
-      k_m2l_leaf<dfloat, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(dfloat), s2>>>(
-          A, t->d_work_leaf);
-    else
-      k_m2l_leaf<double, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(double), s2>>>(
-          A, t->d_work_leaf);
-    CUDA_TRY(cudaGetLastError());
-    ++nl;
-  }
-  if ((rc = record(t, 9, t->stream2))) return rc;
+  // The same-level leaf pairs need only the leaf masses: their kernel runs on the second stream,
+  // forked from here, beside the level-by-level (latency-bound) upward pass, or (mixed launch
+  // variants with p = 1) forked after the upward pass, beside the refined targets' kernel.
+  const int v_ref = sd->mixed_variant % 4, v_leaf = (sd->mixed_variant / 4) % 2,
+            v_place = mixed ? sd->mixed_variant / 8 : 0;
+  auto launch_leaf = [&]() -> int {
+    CUDA_TRY(cudaEventRecord(t->ev_fork, st));
+    CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_fork, 0));
+    int rc2 = record(t, 8, t->stream2);
+    if (rc2) return rc2;
+    if (t->n_work_leaf > 0) {
+      cudaStream_t s2 = t->stream2;
+      if (mixed && v_leaf == 0)
+        k_m2l_leaf4<false><<<unsigned((t->n_work_leaf + 1) / 2), kLeaf4Threads, kLeaf4Smem, s2>>>(
+            A, t->d_work_leaf, t->n_work_leaf);
+      else if (mixed)
+        k_m2l_leaf<float, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), s2>>>(
+            A, t->d_work_leaf);
+      else if (df)
+        k_m2l_leaf<dfloat, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(dfloat), s2>>>(
+            A, t->d_work_leaf);
+      else
+        k_m2l_leaf<double, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(double), s2>>>(
+            A, t->d_work_leaf);
+      CUDA_TRY(cudaGetLastError());
+      ++nl;
+    }
+    return record(t, 9, t->stream2);
+  };
+  if (v_place == 0 && (rc = launch_leaf())) return rc;
   // octants whose children are leaves need only the leaf masses: every level's in one launch;
   // then the octants with refined children, finest level first
   const int64_t n_walsh = t->oct_leaf_off[h.depth + 1];
@@ -3569,6 +3616,7 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   }
 
   if ((rc = record(t, 1, st))) return rc;
+  if (v_place == 1 && (rc = launch_leaf())) return rc;
   // interactions of refined targets, the root level and boundary leaf targets (these add onto
   // the leaf kernel's output, so they follow it).  Mixed path, by the launch variant of this
   // tree and theta (kMixedVariants): refined subgrids by k_m2l_stage on this stream while the
@@ -4094,6 +4142,7 @@ int fmm_sync_status(fmm_tree* t, void* stream) {
   if (status & 1) return fail(FMM_ERR_NONFINITE, "a density was negative, NaN or infinite");
   if (status & 2) return fail(FMM_ERR_NONFINITE, "a density time derivative was NaN or infinite");
   if (status & 4) return fail(FMM_ERR_TIMEOUT, "a shared-memory staging wait timed out");
+  if (status & 8) return fail(FMM_ERR_BOUNDS, "an index check of the bounds-checked build failed");
   return FMM_OK;
 }
 

@@ -222,17 +222,22 @@ def leaf_density(fld: Field, leaves: np.ndarray) -> np.ndarray:
     return out
 
 
-def refinement_flags(fld: Field, max_level: int, refine_frac: float) -> np.ndarray:
+def refinement_flags(fld: Field, max_level: int, refine_frac: float, graded: bool = False) -> np.ndarray:
     """Dense flags: position p at level l (< max_level) is flagged iff the density exceeds
     refine_frac * rho_peak somewhere in the subgrid's volume.  Each star's profile is radial and
     non-increasing, so its maximum over the box is its value at the box point closest to the
     star's centre; the flag tests that maximum star by star (and the floor).  Point samples at
     coarse cell centres would miss a star that lies between them, while in an evolved field the
-    coarse cells carry the mass of the finer ones."""
+    coarse cells carry the mass of the finer ones.
+
+    graded: the mass-based form of the density criterion (Sec. 2.7) -- a cell of density rho
+    belongs at the deepest level l with rho > rho_r 8^(l - max_level), rho_r = refine_frac *
+    rho_peak (cells of about equal mass: one level per factor 8 in density), so a level-l subgrid
+    is refined iff its maximum density exceeds rho_r 8^(l + 1 - max_level)."""
     out = np.zeros(flags_size(max_level), dtype=np.uint8)
-    thr = refine_frac * fld.rho_peak
-    floor_hit = fld.floor * fld.rho_peak > thr
     for lev in range(max_level):
+        thr = refine_frac * fld.rho_peak * (8.0 ** (lev + 1 - max_level) if graded else 1.0)
+        floor_hit = fld.floor * fld.rho_peak > thr
         n = 1 << lev
         ii, jj, kk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
         ijk = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1)
@@ -341,20 +346,23 @@ def kepler_j0(m1: float, m2: float, a: float) -> float:
     return m1 * m2 * math.sqrt(a / (m1 + m2))
 
 
-def workload_paper_binary(levels: int = 9, theta: float = 0.34, refine_frac: float = 1e-4) -> Workload:
+def workload_paper_binary(levels: int = 9, theta: float = 0.34, refine_frac: float = 1e-4,
+                          graded: bool = False) -> Workload:
     """The merger models' binary in the paper's proportions (Sec. 4): a domain 40 code lengths wide
     mapped to the unit box, 9 refinement levels (finest spacing 1/4096 of the box), accretor 50
     finest cells across, donor of half the accretor's mass filling its Roche lobe (spherical
     stand-in of the lobe's volume-equivalent radius), separation 0.96 code lengths (6e-2 solar
     radii), theta = 0.34 as for the paper's interacting binaries.  Refinement: every subgrid whose
-    volume reaches a density above refine_frac * rho_peak is refined, to the deepest level."""
+    volume reaches a density above refine_frac * rho_peak is refined, to the deepest level; with
+    graded, one level per factor 8 in density below refine_frac * rho_peak (refinement_flags)."""
     a = 0.96 / 40.0
     q = 0.5
     r1 = 25.0 / 4096.0
     r2 = roche_lobe_radius(q, a)
     fld = binary_field(q, r1, r2, a)
-    return Workload(f"paper_binary_L{levels}", levels, refinement_flags(fld, levels, refine_frac),
-                    fld, theta, {"q": q, "r1": r1, "r2": r2, "a": a, "refine_frac": refine_frac})
+    name = f"paper_binary_{'graded_' if graded else ''}L{levels}"
+    return Workload(name, levels, refinement_flags(fld, levels, refine_frac, graded), fld, theta,
+                    {"q": q, "r1": r1, "r2": r2, "a": a, "refine_frac": refine_frac, "graded": graded})
 
 
 def workload_uniform_sphere(depth: int, theta: float = 0.5) -> Workload:

@@ -43,9 +43,9 @@ def test_every_mixed_variant_matches_oracle():
         phi, g, _ = a.solve(r, 0.5, "mixed")
         out[v] = (phi.cpu().numpy(), g.cpu().numpy())
         assert _inf(out[v][0], phi_o) <= MIXED_TOL and _inf(out[v][1], g_o) <= MIXED_TOL, v
-    # same arithmetic in the same order: streams and staging pipelines (r = 0, 1, 3) and leaf
-    # layouts (l = 0, 1); variant = r + 4 l
-    for v, w in ((0, 1), (0, 3), (0, 4), (0, 5), (0, 7), (2, 6)):
+    # same arithmetic in the same order: streams and staging pipelines (r = 0, 1, 3), leaf
+    # layouts (l = 0, 1) and leaf kernel placements (p = 0, 1); variant = r + 4 l + 8 p
+    for v, w in ((0, 1), (0, 3), (0, 4), (0, 5), (0, 7), (2, 6), (0, 8), (0, 11), (0, 15), (2, 10)):
         assert np.array_equal(out[v][0], out[w][0]) and np.array_equal(out[v][1], out[w][1]), (v, w)
 
 

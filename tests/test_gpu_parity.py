@@ -221,11 +221,14 @@ def test_full_size_sampled(levels, precision):
         mixed_per_cell(phi, g, net, ps, gs, idx)
 
 
+@pytest.mark.parametrize("graded", [False, True])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_paper_binary_sampled(precision):
-    """The merger binary in the paper's proportions: 9 levels, theta = 0.34, 2.07M leaf cells;
-    the oracle evaluates sampled leaf cells one by one."""
-    w = synth.workload_paper_binary()
+def test_paper_binary_sampled(precision, graded):
+    """The merger binary in the paper's proportions: 9 levels, theta = 0.34, 2.07M leaf cells
+    (graded: the mass-based refinement, leaves on levels 2 to 9, 1.04M cells); the oracle
+    evaluates sampled leaf cells one by one."""
+    w = (synth.workload_paper_binary(graded=True, refine_frac=0.125) if graded
+         else synth.workload_paper_binary())
     a, b = both_trees(w.max_level, w.flags)
     rho = synth.leaf_density(w.field, b.leaves())
     phi, g, net = gpu_solve(a, rho, w.theta, precision)

@@ -101,3 +101,27 @@ def test_roche_lobe_and_paper_binary():
     assert abs(m1 * s1.center[0] + m2 * s2.center[0]) < 1e-15 * m1
     # the accretor spans 50 finest cells
     assert abs(2 * s1.radius * 4096 - 50) < 1e-9
+
+
+def test_graded_refinement_levels_follow_density():
+    """The mass-based refinement (Sec. 2.7's criterion read as one level per factor 8 in density):
+    every leaf cell's density is below the threshold of the next finer level, and a flagged
+    subgrid's densest point exceeds it."""
+    from paper_2101_08226_gb300 import api
+    w = synth.workload_paper_binary(graded=True, refine_frac=0.125)
+    t = api.Tree(w.max_level, w.flags)
+    rows = t.subgrids()
+    leaves = rows[rows[:, 4] == 1]
+    rho = synth.leaf_density(w.field, leaves[:, :4])
+    lev = np.repeat(leaves[:, 0], 512)
+    thr = 0.125 * w.field.rho_peak * 8.0 ** (lev + 1 - w.max_level)
+    # a leaf cell below the deepest level is not denser than its next level's threshold
+    assert (rho[lev < w.max_level] <= thr[lev < w.max_level]).all()
+    assert len(np.unique(leaves[:, 0])) >= 6      # leaves spread over many levels
+    # its thresholds are the volume rule's at the deepest level and lower above it: it refines
+    # at least where the volume rule with the same rho_r does (on these steep polytrope edges
+    # proper nesting already makes the two trees the same)
+    lit = synth.workload_paper_binary(refine_frac=0.125)
+    assert (w.flags >= lit.flags).all()
+    lt = api.Tree(lit.max_level, lit.flags)
+    assert t.info()[1] >= lt.info()[1]
