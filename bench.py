@@ -515,6 +515,39 @@ def leaf_mass(torch, tree, rho):
     return rho * torch.from_numpy(dx3).to(rho.device)
 
 
+def measure_scf(api, synth, torch, timer, dev, n_iter=10):
+    """The self-consistent-field construction of the binary (Sec. 4.1) on the device: the
+    5-level starting model (two equal-K n = 3/2 polytropes, q = 0.5, a = 0.45), fmm_scf_init and
+    n_iter iterations (each: mass scaling, a gravity solve, L1, C1, C2, K, the new density), timed
+    with CUDA events around the iterations, FP64 and mixed solves."""
+    w = synth.workload_scf_binary(5)
+    tree = api.Tree(w.max_level, w.flags)
+    params, rho0, K0 = synth.scf_inputs(w, tree.leaves())
+    out = {"workload": "SCF binary: n=3/2, q=0.5, accretor radius 0.1, donor 0.126 (equal K), "
+                       "a0=0.45, f=0.8385, 5 levels, theta=0.5", "leaf_cells": int(rho0.size),
+           "iterations": n_iter}
+    for precision in ("fp64", "mixed"):
+        p = dict(params, precision=precision)
+        rho = torch.from_numpy(rho0.copy()).to(dev)
+        tree.scf_init(p, rho, K0, stream=timer.stream)
+        tree.scf_iterate(p, rho, 1, stream=timer.stream)  # captures the solve's graph
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(timer.stream)
+        st, hist, _, _ = tree.scf_iterate(p, rho, n_iter, stream=timer.stream)
+        e1.record(timer.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        dK = abs(hist[-1][0] / hist[-2][0] - 1.0) if n_iter > 1 else None
+        out[precision] = {"ms_per_iteration": ms / n_iter, "K": st["K"], "Omega": st["Omega"],
+                          "last_relative_change_of_K": dK,
+                          "kepler_omega2_a3_over_M": st["Omega"] ** 2 * st["a"] ** 3 /
+                          (params["M1"] + params["M2"])}
+    tree.close()
+    return out
+
+
 def measure_small(api, synth, torch, timer, dev, steps, peaks, rank):
     """The 0.9M-cell 5-level binary: the three paths; the mixed path's errors and residual
     torque against the FP64 path at theta = 0.35, 0.5, 0.7; the time-derivative solve; the
@@ -681,6 +714,7 @@ def run_ours(args):
     paper = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), timer.flush)
     graded = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), timer.flush,
                                   graded=True)
+    scf = measure_scf(api, synth, torch, timer, dev)
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -719,12 +753,17 @@ def run_ours(args):
                   "ms_per_step_direct_launches": r32d["total_ms"] / min(args.steps, 5),
                   "autotune": {"variant": int(tuned_variant),
                                "median_ms_per_variant": [round(float(x), 4) for x in tuned_ms],
-                               "variants": "r + 4 l + 8 p; r: refined targets 0 staged on a "
-                                           "second stream, 1 staged on one stream, 2 per-parity "
-                                           "blocks from L2, 3 staged with a copy-issuing warp and "
-                                           "full / empty barriers; l: leaf kernel 0 four targets "
-                                           "per lane, 1 two per thread; p: leaf kernel 0 beside "
-                                           "the upward pass, 1 after it"},
+                               "variants": "r + 4 l + 12 p + 24 c; r: refined targets 0 staged "
+                                           "on a second stream, 1 staged on one stream, 2 "
+                                           "per-parity blocks from L2, 3 staged with a "
+                                           "copy-issuing warp and full / empty barriers; l: leaf "
+                                           "kernel 0 four targets per lane and 2 subgrids per "
+                                           "block, 1 two targets per thread and 1 subgrid per "
+                                           "block, 2 four targets per lane and 4 subgrids per "
+                                           "block; p: leaf kernel 0 beside the upward pass, 1 "
+                                           "after it; c: boundary lists split over four lanes "
+                                           "above an estimated cost of 6000, 1500, 24000, never; "
+                                           "-1: not timed (coordinate search)"},
                   "gpu_launches": r32["launches"]},
         "df64": {"value": whole_job_rate(world, n_m2l, args.steps, tdf),
                  "ms_per_step": tdf / args.steps, "ms_per_step_median": med(rdf),
@@ -745,6 +784,7 @@ def run_ours(args):
         "batched": batched,
         "paper_binary": paper,
         "paper_binary_graded": graded,
+        "scf": scf,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }

@@ -207,31 +207,38 @@ int fmm_binary_iterate(fmm_tree* tree, const double* rho_dev, const double* g_de
                        const double* x1, const double* x2, int n_iter, double* out_dev,
                        double* centres_dev, double* torque_dev, int8_t* member_dev, void* stream);
 
-/* Launch variants of the mixed path (FMM_MIXED), per tree and theta: variant = r + 4 l + 8 p with
+/* Launch variants of the mixed path (FMM_MIXED), per tree and theta: variant = r + 4 l + 12 p + 24 c
+ * with
  *   r = 0: refined targets by the shared-memory staging kernel on a second stream, beside the
  *          leaf and boundary kernels (the default);
  *   r = 1: the same kernel after them, on one stream;
  *   r = 2: refined targets by per-parity blocks that read their partners from L2;
  *   r = 3: as r = 0 with the staging pipelined: a separate warp issues the copies and each buffer
  *          has its own full and empty barriers, so the evaluating warps never meet;
- *   l = 0: leaf pairs by the four-targets-per-lane FP32 kernel (the default);
- *   l = 1: leaf pairs by the two-targets-per-thread kernel;
- *   p = 0: the leaf-pair kernel starts beside the upward pass (the default);
- *   p = 1: it starts after the upward pass, beside the refined targets' kernel.
- * Variants that differ in r among 0, 1, 3, in l, or in p give the same results bit for bit; r = 2
- * sums the refined targets' pairs in another order (results differ at FP32 rounding, within the
- * mixed path's tolerance).  FMM_ERR_ARG for a variant outside [0, FMM_MIXED_VARIANTS),
- * FMM_ERR_THETA for a theta outside [0.34, 1).  The FP64 and df64 paths have one launch
- * configuration. */
-#define FMM_MIXED_VARIANTS 16
+ *   l = 0: leaf pairs by the four-targets-per-lane FP32 kernel, two leaf subgrids per block (the
+ *          default); l = 1: by the two-targets-per-thread kernel, one subgrid per block;
+ *          l = 2: by the four-targets-per-lane kernel with four subgrids per block;
+ *   p = 0: the leaf-pair kernel starts beside the upward pass (the default); p = 1: after it,
+ *          beside the refined targets' kernel;
+ *   c = 0..3: boundary targets whose estimated list cost exceeds 6000, 1500, 24000 or (c = 3)
+ *          nothing split their lists over four lanes (the default c = 0).
+ * Variants with the same c that differ only in r among 0, 1, 3, in l or in p give the same results
+ * bit for bit; r = 2 and other c sum some pairs in another order (results differ at FP32
+ * rounding, within the mixed path's tolerance).  FMM_ERR_ARG for a variant outside
+ * [0, FMM_MIXED_VARIANTS), FMM_ERR_THETA for a theta outside [0.34, 1).  The FP64 and df64 paths
+ * have one launch configuration. */
+#define FMM_MIXED_VARIANTS 96
 int fmm_set_variant(fmm_tree* tree, double theta, int variant);
 
-/* Autotuner: times every launch variant of `precision` (FMM_MIXED: FMM_MIXED_VARIANTS; FP64,
- * df64: one) on the caller's density, `reps` timed solves each after one warm-up solve (CUDA
- * events on `stream`, the median kept), keeps the fastest for this tree and theta, writes its
- * number to *variant_out and the medians (ms) to ms_host[variant] when ms_host is not null, and
- * leaves that variant's phi and g in the output buffers.  Blocks the calling thread until done.
- * rho_dev, phi_dev, g_dev as for fmm_solve.  FMM_ERR_ARG for a null pointer or reps < 1. */
+/* Autotuner: times launch variants of `precision` on the caller's density, `reps` timed solves
+ * each after one warm-up solve (CUDA events on `stream`, the median kept), and keeps the fastest
+ * for this tree and theta (part of the graph key).  FMM_MIXED: a coordinate search -- the 24
+ * variants with c = 0, then the other three split thresholds c with the best of them; FP64 and
+ * df64: their one configuration.  Writes the chosen variant to *variant_out and, when ms_host is
+ * not null, each timed variant's median (ms) to ms_host[variant] (FMM_MIXED_VARIANTS floats; -1
+ * for variants not timed), and leaves the chosen variant's phi and g in the output buffers.
+ * Blocks the calling thread until done.  rho_dev, phi_dev, g_dev as for fmm_solve.  FMM_ERR_ARG
+ * for a null pointer or reps < 1. */
 int fmm_autotune(fmm_tree* tree, const double* rho_dev, double theta, int precision, int amc,
                  double* phi_dev, double* g_dev, int reps, float* ms_host, int32_t* variant_out,
                  void* stream);

@@ -17,7 +17,7 @@ FMM_ERR_NOMEM = -7
 FMM_ERR_STATE = -8
 FMM_ERR_TIMEOUT = -9
 FMM_ERR_BOUNDS = -10
-FMM_MIXED_VARIANTS = 16
+FMM_MIXED_VARIANTS = 96
 FMM_NET_STATIC_MAX_POINTS = 2048 * 4096
 FMM_SCF_STATE = 22
 FMM_FP64 = 0

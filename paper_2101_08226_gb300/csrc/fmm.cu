@@ -170,8 +170,10 @@ constexpr int kLeafThreads = 256;    // one block = one leaf subgrid, two target
 constexpr int kRootChunks = 8;       // root sources split into 8 chunks of 64 cells
 constexpr int kM2LThreads = 64;      // one block = the 64 cells of one parity of one subgrid
 constexpr int kSplitLanes = 4;       // lanes per target in k_m2l_split's long-list blocks
-constexpr int kMixedVariants = 16;   // mixed path launch variants: refined (4) x leaf kernel (2)
-                                     // x leaf kernel placement (2)
+// mixed path launch variants: refined kernel (4) x leaf kernel (3) x leaf kernel placement (2)
+// x split threshold of the boundary lists (4)
+constexpr int kMixedVariants = 96;
+constexpr int kSplitChoices = 4;
 constexpr int kReduceThreads = 256;
 constexpr int kReduceBlocks = 1216;  // 8 per SM
 
@@ -1738,21 +1740,26 @@ __global__ void __launch_bounds__(kLeafThreads) k_m2l_leaf(DevArgs A, const int3
 // table entry; the offsets come four to a 16-byte load (the tables are zero-padded, so the loop
 // runs to a multiple of four).  The second halo starts one word past the first, so the two half
 // warps fall on the even and the odd banks: lattice offsets 120 i + 10 j are the 16 even banks.
-constexpr int kLeaf4Threads = 256;
-constexpr int kLeaf4Smem = (2 * kHaloWords + 1) * 4;
-template <bool SRC>
-__global__ void __launch_bounds__(kLeaf4Threads) k_m2l_leaf4(DevArgs A, const int32_t* __restrict__ work,
-                                                            int64_t n_work) {
+// NSUB leaf subgrids per block (2 or 4, a tile parameter of the autotuner): warp w takes parity
+// class w % 8 of the pair of subgrids 2 (w / 8), 2 (w / 8) + 1, one per half warp.
+constexpr int kLeaf4Threads = 256;  // per pair of subgrids
+template <int NSUB>
+constexpr int leaf4_smem() { return (NSUB * kHaloWords + NSUB - 1) * 4; }
+constexpr int kLeaf4Smem = leaf4_smem<2>();
+template <bool SRC, int NSUB = 2>
+__global__ void __launch_bounds__(kLeaf4Threads * NSUB / 2) k_m2l_leaf4(DevArgs A, const int32_t* __restrict__ work,
+                                                                       int64_t n_work) {
+  constexpr int NT = kLeaf4Threads * NSUB / 2;
   extern __shared__ __align__(16) float leaf4_smem[];
-  __shared__ int32_t nb[2][27];
-  __shared__ int32_t sub[2];
+  __shared__ int32_t nb[NSUB][27];
+  __shared__ int32_t sub[NSUB];
   const int t = threadIdx.x;
-  if (t < 2) {
-    const int64_t w = 2 * int64_t(blockIdx.x) + t;
+  if (t < NSUB) {
+    const int64_t w = NSUB * int64_t(blockIdx.x) + t;
     sub[t] = w < n_work ? work[w] : -1;
   }
   __syncthreads();
-  if (t < 54) {
+  if (t < 27 * NSUB) {
     const int h = t / 27, k = t % 27;
     int32_t q = sub[h] >= 0 ? A.nbr[27 * sub[h] + k] : -1;
     nb[h][k] = (q >= 0 && A.leaf[q]) ? q : -1;
@@ -1761,19 +1768,19 @@ __global__ void __launch_bounds__(kLeaf4Threads) k_m2l_leaf4(DevArgs A, const in
   const float* __restrict__ M = SRC ? A.smom32 : A.m32;
   constexpr int kH3 = kHalo * kHalo * kHalo;
   constexpr int kFill = 8;  // halo loads in flight per thread
-  for (int i0 = t; i0 < 2 * kH3; i0 += kFill * kLeaf4Threads) {
+  for (int i0 = t; i0 < NSUB * kH3; i0 += kFill * NT) {
     float v[kFill];
     int dst[kFill];
 #pragma unroll
     for (int u = 0; u < kFill; ++u) {
-      const int i = i0 + u * kLeaf4Threads;
-      const int h = i >= kH3, j = i - h * kH3;
+      const int i = i0 + u * NT;
+      const int h = i / kH3, j = i - h * kH3;
       const int hx = j / (kHalo * kHalo), r = j - hx * (kHalo * kHalo), hy = r / kHalo, hz = r - hy * kHalo;
       const int x = hx - 5, y = hy - 5, z = hz - 5;
-      const int32_t q = i < 2 * kH3 ? nb[h][((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)] : -1;
-      dst[u] = i < 2 * kH3 ? h * (kHaloWords + 1) + ((hx & 1) << 2 | (hy & 1) << 1 | (hz & 1)) * kHaloPar +
-                                 (hx >> 1) * kHaloSX + (hy >> 1) * kHaloSY + (hz >> 1)
-                           : -1;
+      const int32_t q = i < NSUB * kH3 ? nb[h][((x >> 3) + 1) * 9 + ((y >> 3) + 1) * 3 + ((z >> 3) + 1)] : -1;
+      dst[u] = i < NSUB * kH3 ? h * (kHaloWords + 1) + ((hx & 1) << 2 | (hy & 1) << 1 | (hz & 1)) * kHaloPar +
+                                    (hx >> 1) * kHaloSX + (hy >> 1) * kHaloSY + (hz >> 1)
+                              : -1;
       v[u] = q >= 0 && !FMM_BAD(A, int64_t(q) * kCells < A.n_cell)
                  ? __ldg(M + int64_t(q) * kCells + cidx(x & 7, y & 7, z & 7))
                  : 0.0f;
@@ -1783,11 +1790,12 @@ __global__ void __launch_bounds__(kLeaf4Threads) k_m2l_leaf4(DevArgs A, const in
       if (dst[u] >= 0) leaf4_smem[dst[u]] = v[u];
   }
   __syncthreads();
-  const int parity = t >> 5, lane = t & 31, half = lane >> 4;
-  const int32_t s = sub[half];
+  const int warp = t >> 5, parity = warp & 7, lane = t & 31;
+  const int hsub = 2 * (warp >> 3) + (lane >> 4);
+  const int32_t s = sub[hsub];
   const int px = (parity >> 2) & 1, py = (parity >> 1) & 1, pz = parity & 1;
   const int li = (lane >> 2) & 3, lj = lane & 3;
-  const float* __restrict__ hm = leaf4_smem + half * (kHaloWords + 1) + li * kHaloSX + lj * kHaloSY;
+  const float* __restrict__ hm = leaf4_smem + hsub * (kHaloWords + 1) + li * kHaloSX + lj * kHaloSY;
   const int4* __restrict__ toff = reinterpret_cast<const int4*>(A.ltab_off + parity * kLeafCap);
   const float4* __restrict__ tk = reinterpret_cast<const float4*>(A.ltab_k32 + int64_t(parity) * kLeafCap * 4);
   const int n4 = (A.n_stencil + A.n_near + 3) >> 2;
@@ -2794,9 +2802,12 @@ struct StencilDev {
   int32_t* d_blocks = nullptr;     // general-kernel blocks (one parity each) for this tree, theta
   int64_t n_blocks = 0;
   int mixed_variant = 0;              // mixed path launch variant (fmm_set_variant, fmm_autotune)
-  int32_t* d_blocks_split = nullptr;  // mixed path: k_m2l_split's blocks (root, boundary)
-  int64_t n_blocks_split = 0;
-  int64_t n_bt_long = 0;              // boundary targets [0, n_bt_long) take four lanes
+  // mixed path: k_m2l_split's blocks (root, boundary) for each choice of the threshold above which
+  // a boundary target's lists are split over four lanes (built when first used)
+  int32_t* d_blocks_split[kSplitChoices] = {};
+  int64_t n_blocks_split[kSplitChoices] = {};
+  int64_t n_bt_long[kSplitChoices] = {};  // boundary targets [0, n_bt_long) take four lanes
+  std::vector<double> bnd_cost;           // estimated cost of each boundary target (sorted)
   float* d_stage_tab = nullptr;    // [8][kLeafCap][4] (DevArgs::stage_tab)
   int32_t* d_stage_seg = nullptr;  // [8][9]
   // boundary pair lists (see DevArgs)
@@ -2923,8 +2934,10 @@ static int ensure_device(fmm_tree* t) {
                                 int(kHaloWords * sizeof(double))));
   CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 int(kHaloWords * sizeof(float))));
-  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLeaf4Smem));
-  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLeaf4Smem));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf4<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLeaf4Smem));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf4<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLeaf4Smem));
+  CUDA_TRY(cudaFuncSetAttribute(k_m2l_leaf4<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                leaf4_smem<4>()));
   const HostTree& h = t->h;
   const int64_t nc = h.n_sub * kCells;
   CUDA_TRY(upload(t, &t->d_level, h.level));
@@ -3263,20 +3276,23 @@ static std::vector<int32_t> general_blocks(const HostTree& h, const Stencil& st,
 // only add per-target overhead.  The choice depends on the target's own lists alone, so a tree
 // gives the same results alone and inside a forest.  Largest per-lane work first.
 constexpr double kSplitCost = 6000;  // about 40 multipole partners
-static std::vector<int32_t> split_blocks(const HostTree& h, const BoundaryLists& bnd, int64_t* n_long) {
+// the thresholds of the split-lane choices: kSplitCost, a quarter, four times, never split
+constexpr double kSplitCosts[kSplitChoices] = {kSplitCost, kSplitCost / 4, kSplitCost * 4, 1e300};
+static std::vector<int32_t> split_blocks(const HostTree& h, const std::vector<double>& cost,
+                                         double split_cost, int64_t* n_long) {
   const double c_rr = 230, root_lane = 64.0 * c_rr / kSplitLanes;
   std::vector<std::pair<double, int32_t>> items;
   for (int r = 0; r < h.n_trees; ++r)
     for (int ch = 0; ch < kRootChunks; ++ch)
       for (int p = 0; p < 8; ++p) items.push_back({root_lane, block_code(0, p, uint32_t(r * 8 + ch))});
-  const int64_t n = int64_t(bnd.cell.size());
+  const int64_t n = int64_t(cost.size());
   int64_t nl = 0;
-  while (nl < n && bnd.cost[size_t(nl)] > kSplitCost) ++nl;  // targets are sorted by cost
+  while (nl < n && cost[size_t(nl)] > split_cost) ++nl;  // targets are sorted by cost
   *n_long = nl;
   for (int64_t c = 0; c * 64 < nl; ++c)
-    items.push_back({bnd.cost[size_t(c * 64)] / kSplitLanes, block_code(2, 0, uint32_t(c))});
+    items.push_back({cost[size_t(c * 64)] / kSplitLanes, block_code(2, 0, uint32_t(c))});
   for (int64_t c = 0; nl + c * 64 < n; c += 4)
-    items.push_back({bnd.cost[size_t(nl + c * 64)], block_code(3, 0, uint32_t(c))});
+    items.push_back({cost[size_t(nl + c * 64)], block_code(3, 0, uint32_t(c))});
   std::stable_sort(items.begin(), items.end(),
                    [](const std::pair<double, int32_t>& x, const std::pair<double, int32_t>& y) {
                      return x.first > y.first;
@@ -3285,6 +3301,17 @@ static std::vector<int32_t> split_blocks(const HostTree& h, const BoundaryLists&
   out.reserve(items.size());
   for (auto& it : items) out.push_back(it.second);
   return out;
+}
+
+// The split-lane choice of a stencil's current mixed launch variant, and its block list.
+static inline int split_choice(const StencilDev* sd) { return (sd->mixed_variant / 24) % kSplitChoices; }
+static int ensure_split(fmm_tree* t, StencilDev* sd) {
+  const int c = split_choice(sd);
+  if (sd->d_blocks_split[c]) return FMM_OK;
+  std::vector<int32_t> blocks = split_blocks(t->h, sd->bnd_cost, kSplitCosts[c], &sd->n_bt_long[c]);
+  sd->n_blocks_split[c] = int64_t(blocks.size());
+  CUDA_TRY(upload(t, &sd->d_blocks_split[c], blocks));
+  return FMM_OK;
 }
 
 static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
@@ -3357,9 +3384,7 @@ static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
     std::vector<int32_t> blocks = general_blocks(t->h, st, t->work, bl, false);
     sd.n_blocks = int64_t(blocks.size());
     CUDA_TRY(upload(t, &sd.d_blocks, blocks));
-    std::vector<int32_t> blocks_split = split_blocks(t->h, bl, &sd.n_bt_long);
-    sd.n_blocks_split = int64_t(blocks_split.size());
-    CUDA_TRY(upload(t, &sd.d_blocks_split, blocks_split));
+    sd.bnd_cost = bl.cost;
     // staged refined targets: per parity, the stencil entries grouped by partner class, with
     // the partner's lattice offset from a target at lattice cell (0, 0, 0) of that parity
     std::vector<float> stab(8 * kLeafCap * 4, 0.0f);
@@ -3449,7 +3474,7 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.status = t->d_status;
   A.stage_tab = sd ? reinterpret_cast<const float4*>(sd->d_stage_tab) : nullptr;
   A.stage_seg = sd ? sd->d_stage_seg : nullptr;
-  A.n_bt_long = sd ? sd->n_bt_long : 0;
+  A.n_bt_long = sd ? sd->n_bt_long[split_choice(sd)] : 0;
   A.wait_cycles = t->wait_cycles > 0 ? t->wait_cycles : kStageWaitCycles;
   A.smom = t->d_smom;
   A.smtl = t->d_smtl;
@@ -3570,8 +3595,8 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   // The same-level leaf pairs need only the leaf masses: their kernel runs on the second stream,
   // forked from here, beside the level-by-level (latency-bound) upward pass, or (mixed launch
   // variants with p = 1) forked after the upward pass, beside the refined targets' kernel.
-  const int v_ref = sd->mixed_variant % 4, v_leaf = (sd->mixed_variant / 4) % 2,
-            v_place = mixed ? sd->mixed_variant / 8 : 0;
+  const int v_ref = sd->mixed_variant % 4, v_leaf = (sd->mixed_variant / 4) % 3,
+            v_place = mixed ? (sd->mixed_variant / 12) % 2 : 0;
   auto launch_leaf = [&]() -> int {
     CUDA_TRY(cudaEventRecord(t->ev_fork, st));
     CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_fork, 0));
@@ -3580,7 +3605,10 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
     if (t->n_work_leaf > 0) {
       cudaStream_t s2 = t->stream2;
       if (mixed && v_leaf == 0)
-        k_m2l_leaf4<false><<<unsigned((t->n_work_leaf + 1) / 2), kLeaf4Threads, kLeaf4Smem, s2>>>(
+        k_m2l_leaf4<false, 2><<<unsigned((t->n_work_leaf + 1) / 2), kLeaf4Threads, kLeaf4Smem, s2>>>(
+            A, t->d_work_leaf, t->n_work_leaf);
+      else if (mixed && v_leaf == 2)
+        k_m2l_leaf4<false, 4><<<unsigned((t->n_work_leaf + 3) / 4), 2 * kLeaf4Threads, leaf4_smem<4>(), s2>>>(
             A, t->d_work_leaf, t->n_work_leaf);
       else if (mixed)
         k_m2l_leaf<float, false><<<unsigned(t->n_work_leaf), kLeafThreads, kHaloWords * sizeof(float), s2>>>(
@@ -3628,9 +3656,10 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   if (split2) {
     CUDA_TRY(cudaEventRecord(t->ev_m2m, st));
     CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_m2m, 0));
-    if (sd->n_blocks_split > 0) {
-      k_m2l_split<float><<<unsigned(sd->n_blocks_split), 64 * kSplitLanes, 0, t->stream2>>>(
-          A, sd->d_blocks_split, amc);
+    const int sc = split_choice(sd);
+    if (sd->n_blocks_split[sc] > 0) {
+      k_m2l_split<float><<<unsigned(sd->n_blocks_split[sc]), 64 * kSplitLanes, 0, t->stream2>>>(
+          A, sd->d_blocks_split[sc], amc);
       CUDA_TRY(cudaGetLastError());
       ++nl;
     }
@@ -3653,7 +3682,8 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
     if (mixed && v_ref == 2) {
       k_m2l_ref<float, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
     } else if (mixed) {
-      k_m2l_split<float><<<unsigned(sd->n_blocks_split), 64 * kSplitLanes, 0, st>>>(A, sd->d_blocks_split, amc);
+      k_m2l_split<float><<<unsigned(sd->n_blocks_split[split_choice(sd)]), 64 * kSplitLanes, 0, st>>>(
+          A, sd->d_blocks_split[split_choice(sd)], amc);
       if (staged) {
         CUDA_TRY(cudaGetLastError());
         ++nl;
@@ -3721,8 +3751,8 @@ static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream
   if (mixed) {
     CUDA_TRY(cudaEventRecord(t->ev_m2m, st));
     CUDA_TRY(cudaStreamWaitEvent(t->stream2, t->ev_m2m, 0));
-    k_m2l_split_src<float><<<unsigned(sd->n_blocks_split), 64 * kSplitLanes, 0, t->stream2>>>(
-        A, sd->d_blocks_split);
+    k_m2l_split_src<float><<<unsigned(sd->n_blocks_split[split_choice(sd)]), 64 * kSplitLanes, 0,
+                              t->stream2>>>(A, sd->d_blocks_split[split_choice(sd)]);
     CUDA_TRY(cudaGetLastError());
     ++*nl;
     CUDA_TRY(cudaEventRecord(t->ev_join, t->stream2));
@@ -3793,6 +3823,7 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   if (src && (rc = ensure_src(t, mixed))) return rc;
   StencilDev* sd = nullptr;
   if ((rc = get_stencil(t, theta, &sd))) return rc;
+  if ((rc = ensure_split(t, sd))) return rc;
   amc = amc ? 1 : 0;
   fmm_tree::Graph* gr = nullptr;
   if (t->use_graphs) {
@@ -4299,7 +4330,6 @@ int fmm_autotune(fmm_tree* t, const double* rho_dev, double theta, int precision
   try {
     cudaStream_t caller = static_cast<cudaStream_t>(stream);
     const std::vector<TreeIo> io = contiguous_io(t, rho_dev, phi_dev, g_dev);
-    const int n_var = precision == FMM_MIXED ? kMixedVariants : 1;
     int rc = solve_impl(t, io, theta, precision, amc, nullptr, caller);  // builds the lists
     if (rc) return rc;
     StencilDev* sd = nullptr;
@@ -4307,34 +4337,56 @@ int fmm_autotune(fmm_tree* t, const double* rho_dev, double theta, int precision
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    int best = 0;
-    float best_ms = 0.0f;
-    for (int v = 0; v < n_var && rc == FMM_OK; ++v) {
-      sd->mixed_variant = v;
-      rc = solve_impl(t, io, theta, precision, amc, nullptr, caller);  // warm-up (captures its graph)
+    if (ms_host)
+      for (int v = 0; v < (precision == FMM_MIXED ? kMixedVariants : 1); ++v) ms_host[v] = -1.0f;
+    // median time of `reps` solves of variant v after a warm-up solve (which captures its graph)
+    auto time_variant = [&](int v, float* med) -> int {
+      if (precision == FMM_MIXED) sd->mixed_variant = v;
+      int r = solve_impl(t, io, theta, precision, amc, nullptr, caller);
       std::vector<float> ms;
-      for (int r = 0; r < reps && rc == FMM_OK; ++r) {
+      for (int k = 0; k < reps && r == FMM_OK; ++k) {
         float x = 0.0f;
-        if (cudaEventRecord(e0, caller) != cudaSuccess) rc = fail(FMM_ERR_CUDA, "event record");
-        if (!rc) rc = solve_impl(t, io, theta, precision, amc, nullptr, caller);
-        if (!rc && (cudaEventRecord(e1, caller) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                    cudaEventElapsedTime(&x, e0, e1) != cudaSuccess))
-          rc = fail(FMM_ERR_CUDA, "event timing");
+        if (cudaEventRecord(e0, caller) != cudaSuccess) r = fail(FMM_ERR_CUDA, "event record");
+        if (!r) r = solve_impl(t, io, theta, precision, amc, nullptr, caller);
+        if (!r && (cudaEventRecord(e1, caller) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                   cudaEventElapsedTime(&x, e0, e1) != cudaSuccess))
+          r = fail(FMM_ERR_CUDA, "event timing");
         ms.push_back(x);
       }
-      if (rc) break;
+      if (r) return r;
       std::sort(ms.begin(), ms.end());
-      const float med = ms[ms.size() / 2];
-      if (ms_host) ms_host[v] = med;
-      if (v == 0 || med < best_ms) {
+      *med = ms[ms.size() / 2];
+      if (ms_host) ms_host[v] = *med;
+      return FMM_OK;
+    };
+    // coordinate search: every kernel / leaf layout / placement combination at the default split
+    // threshold, then the split thresholds with the best of those
+    int best = 0;
+    float best_ms = 0.0f;
+    const int n_first = precision == FMM_MIXED ? 24 : 1;
+    for (int v = 0; v < n_first && rc == FMM_OK; ++v) {
+      float m = 0.0f;
+      rc = time_variant(v, &m);
+      if (!rc && (v == 0 || m < best_ms)) {
         best = v;
-        best_ms = med;
+        best_ms = m;
+      }
+    }
+    if (precision == FMM_MIXED) {
+      const int base = best;
+      for (int c = 1; c < kSplitChoices && rc == FMM_OK; ++c) {
+        float m = 0.0f;
+        rc = time_variant(base + 24 * c, &m);
+        if (!rc && m < best_ms) {
+          best = base + 24 * c;
+          best_ms = m;
+        }
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    sd->mixed_variant = precision == FMM_MIXED ? best : sd->mixed_variant;
+    if (precision == FMM_MIXED) sd->mixed_variant = best;
     *variant_out = best;
     // leave the outputs of the chosen variant in phi and g
     return solve_impl(t, io, theta, precision, amc, nullptr, caller);

@@ -365,6 +365,34 @@ def workload_paper_binary(levels: int = 9, theta: float = 0.34, refine_frac: flo
                     {"q": q, "r1": r1, "r2": r2, "a": a, "refine_frac": refine_frac, "graded": graded})
 
 
+def workload_scf_binary(levels: int = 3, q: float = 0.5, r1: float = 0.1, a0: float = 0.45,
+                        n: float = 1.5, f: float = 0.8385) -> Workload:
+    """The starting model of the self-consistent-field iteration (Sec. 4.1): two n = 3/2
+    polytropes of equal polytropic constant on the x axis (donor radius r1 q^(-1/3), the equal-K
+    mass-radius relation of n = 3/2), mass ratio q, separation a0, density floor 1e-10 of the
+    accretor's central density, refined where the density exceeds 1e-4 of the peak; f is the
+    donor's Roche filling factor as placed (0.8385 for these stars at this separation)."""
+    fld = binary_field(q, r1, r1 * q ** (-1.0 / 3.0), a0, n=n)
+    return Workload(f"scf_binary_L{levels}", levels, refinement_flags(fld, levels, 1e-4), fld, 0.5,
+                    {"q": q, "r1": r1, "a0": a0, "n": n, "f": f})
+
+
+def scf_inputs(w: Workload, leaves: np.ndarray):
+    """(fmm_scf_params as a dict, the initial density, K0) for workload_scf_binary: prescribed
+    masses = the initial stars' masses on the grid (material at x < 0 and x >= 0), J0 of the
+    Kepler orbit at the initial separation, K0 of the initial accretor."""
+    x, dx = leaf_cell_centres(leaves)
+    rho0 = leaf_density(w.field, leaves)
+    floor = w.field.floor * w.field.rho_peak
+    m = rho0 * dx ** 3
+    star = rho0 > floor
+    M1 = float(m[star & (x[:, 0] < 0)].sum())
+    M2 = float(m[star & (x[:, 0] >= 0)].sum())
+    params = {"M1": M1, "M2": M2, "n": w.meta["n"], "f": w.meta["f"],
+              "J0": kepler_j0(M1, M2, w.meta["a0"]), "rho_floor": floor, "theta": w.theta}
+    return params, rho0, polytrope_k(w.meta["r1"], 1.0, w.meta["n"])
+
+
 def workload_uniform_sphere(depth: int, theta: float = 0.5) -> Workload:
     return Workload(f"uniform_sphere_d{depth}", depth, uniform_flags(depth),
                     uniform_sphere_field(), theta, {"depth": depth})

@@ -1,32 +1,21 @@
-"""The binary of the SCF tests (Sec. 4.1): two n = 3/2 polytropes of equal polytropic constant on
-the x axis, mass ratio 0.5, accretor radius 0.1 (donor 0.1 * 0.5^(-1/3), the equal-K mass-radius
-relation of n = 3/2), separation 0.45, density floor 1e-10 of the accretor's central density, on
-the 3-level tree refined where the density exceeds 1e-4 of the peak (75,776 leaf cells).  The
-prescribed masses are the initial stars' masses on the grid, J0 that of the Kepler orbit at the
-initial separation, K0 the accretor's polytropic constant, and the filling factor 0.8385, the
-donor's as initially placed.  Inputs only: no step of the iteration is computed here."""
+"""The binary of the SCF tests (Sec. 4.1): synth.workload_scf_binary at 3 levels (75,776 leaf
+cells) -- two n = 3/2 polytropes of equal polytropic constant, mass ratio 0.5, accretor radius
+0.1, separation 0.45 -- with synth.scf_inputs (prescribed masses of the initial stars, J0 of the
+Kepler orbit, K0 of the initial accretor, filling factor 0.8385).  Inputs only."""
 from paper_2101_08226_gb300 import synth
 
-LEVELS, Q, R1, A0, N, F = 3, 0.5, 0.1, 0.45, 1.5, 0.8385
+LEVELS = 3
+_W = synth.workload_scf_binary(LEVELS)
+A0 = _W.meta["a0"]
 
 
 def workload():
-    fld = synth.binary_field(Q, R1, R1 * Q ** (-1.0 / 3.0), A0)
-    return fld, synth.refinement_flags(fld, LEVELS, 1e-4)
+    return _W.field, _W.flags
 
 
 def inputs(fld, leaves):
     """(params dict of fmm_scf_params, the initial density, K0)."""
-    x, dx = synth.leaf_cell_centres(leaves)
-    rho0 = synth.leaf_density(fld, leaves)
-    floor = fld.floor * fld.rho_peak
-    m = rho0 * dx ** 3
-    star = rho0 > floor
-    M1 = float(m[star & (x[:, 0] < 0)].sum())
-    M2 = float(m[star & (x[:, 0] >= 0)].sum())
-    params = {"M1": M1, "M2": M2, "n": N, "f": F, "J0": synth.kepler_j0(M1, M2, A0),
-              "rho_floor": floor, "theta": 0.5}
-    return params, rho0, synth.polytrope_k(R1, 1.0, N)
+    return synth.scf_inputs(_W, leaves)
 
 
 def oracle_problem(params, leaves):

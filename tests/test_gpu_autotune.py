@@ -44,9 +44,14 @@ def test_every_mixed_variant_matches_oracle():
         out[v] = (phi.cpu().numpy(), g.cpu().numpy())
         assert _inf(out[v][0], phi_o) <= MIXED_TOL and _inf(out[v][1], g_o) <= MIXED_TOL, v
     # same arithmetic in the same order: streams and staging pipelines (r = 0, 1, 3), leaf
-    # layouts (l = 0, 1) and leaf kernel placements (p = 0, 1); variant = r + 4 l + 8 p
-    for v, w in ((0, 1), (0, 3), (0, 4), (0, 5), (0, 7), (2, 6), (0, 8), (0, 11), (0, 15), (2, 10)):
-        assert np.array_equal(out[v][0], out[w][0]) and np.array_equal(out[v][1], out[w][1]), (v, w)
+    # layouts (l = 0, 1, 2) and leaf kernel placements (p = 0, 1) at one split threshold c;
+    # variant = r + 4 l + 12 p + 24 c
+    for c in range(4):
+        o = 24 * c
+        for v, w in ((0, 1), (0, 3), (0, 4), (0, 8), (0, 12), (0, 15), (0, 20), (0, 23), (2, 6),
+                     (2, 10), (2, 14), (2, 22)):
+            assert np.array_equal(out[o + v][0], out[o + w][0]), (o + v, o + w)
+            assert np.array_equal(out[o + v][1], out[o + w][1]), (o + v, o + w)
 
 
 def test_autotune_picks_a_variant_and_keeps_it():
@@ -54,8 +59,12 @@ def test_autotune_picks_a_variant_and_keeps_it():
     r = torch.from_numpy(rho).cuda()
     v, ms, phi, g = a.autotune(r, 0.5, "mixed", reps=3)
     assert 0 <= v < _lib.FMM_MIXED_VARIANTS
-    assert ms.shape == (_lib.FMM_MIXED_VARIANTS,) and (ms > 0).all()
-    assert ms[v] == ms.min()
+    assert ms.shape == (_lib.FMM_MIXED_VARIANTS,)
+    # the coordinate search times the 24 variants of the default split threshold, then the other
+    # thresholds with the best of those; the rest are marked -1
+    timed = ms > 0
+    assert timed[:24].all() and timed.sum() == 27 and (ms[~timed] == -1).all()
+    assert ms[v] == ms[timed].min()
     phi2, g2, _ = a.solve(r, 0.5, "mixed")  # uses the chosen variant
     a.set_variant(0.5, v)
     phi3, g3, _ = a.solve(r, 0.5, "mixed")

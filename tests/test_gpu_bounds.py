@@ -79,7 +79,8 @@ def test_no_check_fires_and_results_agree(checked, case):
         rho = torch.from_numpy(synth.leaf_density(fld, leaves)).cuda()
         rhodot = rho * torch.from_numpy(np.random.default_rng(2).uniform(-1, 1, rho.numel())).cuda()
         runs = [(p, th, None, None) for p in ("fp64", "df64", "mixed") for th in (0.34, 0.5, 0.7)]
-        runs += [("mixed", 0.5, v, None) for v in range(_lib.FMM_MIXED_VARIANTS)]
+        variants = range(_lib.FMM_MIXED_VARIANTS) if case == "tiny_amr" else range(0, _lib.FMM_MIXED_VARIANTS, 7)
+        runs += [("mixed", 0.5, v, None) for v in variants]
         runs += [("fp64", 0.5, None, rhodot), ("mixed", 0.5, None, rhodot)]
         for precision, theta, variant, rd in runs:
             got = _solve(checked, hc, rho, theta, precision, variant, rd)
