@@ -1271,16 +1271,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (clock64() - t0 > limit) return false;
   return true;
 }
-// Waits like mbar_wait_bounded, but suspended in the barrier (try_wait with a 20 us hint) rather
-// than spinning, so a waiting warp takes no issue slots from the warps still computing.
+// Waits like mbar_wait_bounded, but in try_wait (the thread may be suspended in the barrier until
+// the phase completes, for the hardware's own time limit) rather than in a test loop, so a
+// waiting warp takes few issue slots from the warps still computing.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+      : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return done != 0;
 }
