@@ -302,3 +302,31 @@ def test_df64_rejected_for_time_derivative():
     r = torch.ones(a.n_leaf_cells, dtype=torch.float64, device="cuda")
     with pytest.raises(_lib.FmmError):
         a.solve_dt(r, r, 0.5, "df64")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "df64", "mixed"])
+def test_massless_field_gives_exact_zeros(precision):
+    """The degenerate input: no mass anywhere.  Every cell's centre of mass falls back to its
+    geometric centre, every moment and expansion is zero, and phi, g and the net sums come out
+    as exact zeros (no NaN from a 0/0 centre of mass or a zero correction weight)."""
+    max_level, flags, _ = CASES["tiny_amr"]()
+    a = api.Tree(max_level, flags)
+    n = a.n_leaf_cells
+    for theta in (0.34, 0.5):
+        phi, g, net = gpu_solve(a, np.zeros(n), theta, precision)
+        assert (phi == 0.0).all() and (g == 0.0).all() and (net == 0.0).all()
+
+
+def test_one_leaf_level_tree_and_forest_of_one():
+    """Small degenerate shapes: a tree whose root is its only subgrid (no refined cell, no
+    multipole partner beyond the root's own cells) and a forest holding one tree solve as the
+    tree alone does, bit for bit."""
+    a = api.Tree(0, np.zeros(0, np.uint8))
+    b = O.Tree(0, np.zeros(0, np.uint8))
+    rho = synth.leaf_density(synth.single_polytrope_field(0.3), b.leaves())
+    phi, g, net = gpu_solve(a, rho, 0.5)
+    phi_o, g_o, _ = O.solve(b, rho, 0.5)
+    assert rel_err(phi, phi_o) <= FP64_TOL and rel_err(g, g_o) <= FP64_TOL
+    f = api.Forest([a])
+    p2, g2, n2 = gpu_solve(f, rho, 0.5)
+    assert np.array_equal(p2, phi) and np.array_equal(g2, g) and np.array_equal(n2, net)
