@@ -240,7 +240,8 @@ def measure_paper_binary(tree_api, synth, torch, dev, stream, steps, flush, grad
 
 def measure_batched(tree_api, synth, torch, dev, stream, steps):
     """The 64 seeded trees of uneven depth (levels 2..5, single stars or binaries) as one forest:
-    every level of every tree in one set of launches.  Same metric as the headline."""
+    every level of every tree in one set of launches, replayed as one CUDA graph, the mixed path's
+    launch variant chosen by the autotuner.  Same metric as the headline."""
     ws = synth.batched_workloads(64)
     trees = [tree_api.Tree(w.max_level, w.flags) for w in ws]
     f = tree_api.Forest(trees)
@@ -252,6 +253,9 @@ def measure_batched(tree_api, synth, torch, dev, stream, steps):
                        "(q ~ U[0.3,1], a ~ U[0.25,0.5]), seeds 20210120+t, theta=0.5",
            "subgrids": n_sub, "leaf_cells": n_leaf_sub * 512, "m2l_pairs": counts["m2l"],
            "p2p_pairs": counts["p2p_same"] + counts["p2p_mixed"]}
+    # the autotuner picks the forest's mixed launch variant (untimed)
+    v, _, _, _ = f.autotune(rho, THETA, "mixed", reps=3, stream=stream)
+    out["mixed_variant"] = int(v)
     for precision in ("fp64", "mixed"):
         for _ in range(2):
             f.solve(rho, THETA, precision, True, stream=stream, check_status=False)
