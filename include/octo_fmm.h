@@ -159,7 +159,8 @@ int fmm_solve_batch(fmm_tree* forest, const double* const* rho_dev, double theta
                     int amc, double* const* phi_dev, double* const* g_dev, double* net_dev,
                     void* stream);
 
-/* Waits for `stream`, then returns FMM_OK, or FMM_ERR_NONFINITE if a solve since the last call
+/* Waits for `stream` (and for the tree's pipelined host solves), then returns FMM_OK, or
+ * FMM_ERR_NONFINITE if a solve since the last call
  * met an invalid density, FMM_ERR_TIMEOUT if one of its bounded waits gave up, or FMM_ERR_CUDA;
  * clears the recorded status. */
 int fmm_sync_status(fmm_tree* tree, void* stream);
@@ -169,6 +170,18 @@ int fmm_sync_status(fmm_tree* tree, void* stream);
  * are owned by the tree.  Returns the solve's status. */
 int fmm_solve_host(fmm_tree* tree, const double* rho_host, double theta, int precision, int amc,
                    double* phi_host, double* g_host, double* net_host, void* stream);
+
+/* Pipelined form of fmm_solve_host for a sequence of solves: enqueues, without waiting, the copy
+ * of rho_host into one of two device slots owned by the tree, the solve, and the copies of phi, g
+ * and (if net_host is not NULL) the 7 net sums into the host buffers, each on a stream of its own,
+ * so that one call's copies overlap the neighbouring calls' solves.  The copy in is ordered after
+ * the work enqueued on `stream` before the call; `stream` is not made to wait for anything.  The
+ * host buffers must stay valid, and rho_host unchanged, until the work is done: call
+ * fmm_sync_status (which waits for every pipelined call) before reading the outputs or reusing the
+ * buffers.  Pinned host memory is needed for the copies to overlap.  Errors of the solve itself
+ * are reported by fmm_sync_status. */
+int fmm_solve_host_async(fmm_tree* tree, const double* rho_host, double theta, int precision,
+                         int amc, double* phi_host, double* g_host, double* net_host, void* stream);
 
 /* Net force, torque and normalisation (as net_dev above) of an arbitrary acceleration field g_dev
  * for the masses given by rho_dev on this tree's leaf cells.  Uses the tree's workspace. */

@@ -26,7 +26,7 @@ FMM_DF64 = 2
 
 EXPORTS = [
     "fmm_build_tree", "fmm_destroy", "fmm_build_forest", "fmm_forest_info", "fmm_solve_batch", "fmm_tree_info", "fmm_tree_subgrids", "fmm_stencil",
-    "fmm_interaction_counts", "fmm_interaction_counts_by_type", "fmm_last_launches", "fmm_solve", "fmm_solve_dt", "fmm_sync_status", "fmm_solve_host",
+    "fmm_interaction_counts", "fmm_interaction_counts_by_type", "fmm_last_launches", "fmm_solve", "fmm_solve_dt", "fmm_sync_status", "fmm_solve_host", "fmm_solve_host_async",
     "fmm_net_force_torque", "fmm_net_force_torque_points_static", "fmm_set_profiling", "fmm_set_graphs", "fmm_set_wait_limit", "fmm_set_variant", "fmm_autotune", "fmm_binary_diagnostics", "fmm_binary_iterate", "fmm_phase_times", "fmm_measure_fma_rate", "fmm_scf_init", "fmm_scf_iterate", "fmm_partition", "fmm_ghosts", "fmm_last_error",
 ]
 
@@ -70,6 +70,7 @@ def load(path: str):
         "fmm_solve": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
         "fmm_sync_status": (i32, [vp, vp]),
         "fmm_solve_host": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
+        "fmm_solve_host_async": (i32, [vp, vp, dbl, i32, i32, vp, vp, vp, vp]),
         "fmm_net_force_torque": (i32, [vp, vp, vp, vp, vp]),
         "fmm_net_force_torque_points_static": (i32, [i64, vp, vp, vp, vp, vp]),
         "fmm_set_profiling": (i32, [vp, i32]),

@@ -257,6 +257,20 @@ class Tree:
                                    _stream_handle(stream)))
         return phi, g, net
 
+    def solve_host_async(self, rho: np.ndarray, theta: float, precision: str, phi: np.ndarray,
+                         g: np.ndarray, net: Optional[np.ndarray] = None, amc: bool = True,
+                         stream=None):
+        """fmm_solve_host_async: enqueue one host-buffer solve of a pipelined sequence; the buffers
+        (pinned, contiguous float64) must stay untouched until sync_status()."""
+        n = self.n_leaf_cells
+        assert rho.size == n and phi.size == n and g.size == 3 * n
+        for a in (rho, phi, g) + ((net,) if net is not None else ()):
+            assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+        check(lib().fmm_solve_host_async(self._h, _p(rho), float(theta), PRECISIONS[precision],
+                                         int(bool(amc)), _p(phi), _p(g),
+                                         _p(net) if net is not None else None,
+                                         _stream_handle(stream)))
+
     def net_force_torque(self, rho, g, stream=None):
         import torch
         net = torch.empty(7 * self.forest_info()[0], dtype=torch.float64, device=rho.device)

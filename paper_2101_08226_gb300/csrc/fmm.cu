@@ -2844,6 +2844,14 @@ struct fmm_tree {
   int* d_status = nullptr;
   int64_t* d_tree_leaf_off = nullptr;
   double *d_rho = nullptr, *d_phi = nullptr, *d_g = nullptr, *d_net = nullptr;
+  // pipelined host solves (fmm_solve_host_async): two device slots, a stream for the copies in, one
+  // for the solves, one for the copies out, and per slot the events that order them
+  struct HostPipe {
+    double *rho[2] = {}, *phi[2] = {}, *g[2] = {}, *net[2] = {};
+    cudaStream_t in = nullptr, solve = nullptr, out = nullptr;
+    cudaEvent_t copied_in[2] = {}, solved[2] = {}, copied_out[2] = {}, caller = nullptr;
+    int slot = 0;
+  } hp;
   // time-derivative solve workspace (allocated on first use)
   bool src_ready = false, src32_ready = false;
   double* d_diag_partials = nullptr;  // binary diagnostics: [blocks][kDiagVals]
@@ -4028,6 +4036,15 @@ void fmm_destroy(fmm_tree* t) {
     if (e) cudaEventDestroy(e);
   if (t->ev_in) cudaEventDestroy(t->ev_in);
   if (t->ev_out) cudaEventDestroy(t->ev_out);
+  for (cudaStream_t q : {t->hp.in, t->hp.solve, t->hp.out})
+    if (q) {
+      cudaStreamSynchronize(q);
+      cudaStreamDestroy(q);
+    }
+  for (int k = 0; k < 2; ++k)
+    for (cudaEvent_t e : {t->hp.copied_in[k], t->hp.solved[k], t->hp.copied_out[k]})
+      if (e) cudaEventDestroy(e);
+  if (t->hp.caller) cudaEventDestroy(t->hp.caller);
   if (switched) cudaSetDevice(cur);
   delete t;
 }
@@ -4168,6 +4185,8 @@ int fmm_sync_status(fmm_tree* t, void* stream) {
   if (!t->dev_ready) return FMM_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CUDA_TRY(cudaStreamSynchronize(st));
+  for (cudaStream_t q : {t->hp.in, t->hp.solve, t->hp.out})
+    if (q) CUDA_TRY(cudaStreamSynchronize(q));
   int status = 0;
   CUDA_TRY(cudaMemcpy(&status, t->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   CUDA_TRY(cudaMemset(t->d_status, 0, sizeof(int)));
@@ -4201,6 +4220,54 @@ int fmm_solve_host(fmm_tree* t, const double* rho_host, double theta, int precis
     CUDA_TRY(cudaMemcpyAsync(net_host, t->d_net, sizeof(double) * 7 * t->h.n_trees,
                              cudaMemcpyDeviceToHost, st));
   return fmm_sync_status(t, stream);
+}
+
+int fmm_solve_host_async(fmm_tree* t, const double* rho_host, double theta, int precision, int amc,
+                         double* phi_host, double* g_host, double* net_host, void* stream) {
+  if (!t || !rho_host || !phi_host || !g_host) return fail(FMM_ERR_ARG, "null argument");
+  int rc = ensure_device(t);
+  if (rc) return rc;
+  fmm_tree::HostPipe& P = t->hp;
+  const int64_t n = t->h.n_leaf_sub * kCells;
+  if (!P.in) {
+    for (int k = 0; k < 2; ++k) {
+      CUDA_TRY(dalloc(t, &P.rho[k], sizeof(double) * n));
+      CUDA_TRY(dalloc(t, &P.phi[k], sizeof(double) * n));
+      CUDA_TRY(dalloc(t, &P.g[k], sizeof(double) * 3 * n));
+      CUDA_TRY(dalloc(t, &P.net[k], sizeof(double) * 7 * t->h.n_trees));
+      CUDA_TRY(cudaEventCreateWithFlags(&P.copied_in[k], cudaEventDisableTiming));
+      CUDA_TRY(cudaEventCreateWithFlags(&P.solved[k], cudaEventDisableTiming));
+      CUDA_TRY(cudaEventCreateWithFlags(&P.copied_out[k], cudaEventDisableTiming));
+    }
+    CUDA_TRY(cudaEventCreateWithFlags(&P.caller, cudaEventDisableTiming));
+    CUDA_TRY(cudaStreamCreateWithFlags(&P.in, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&P.solve, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&P.out, cudaStreamNonBlocking));
+  }
+  const int k = P.slot;
+  // copy in: after the caller's work so far, and after the solve two calls back read this slot
+  CUDA_TRY(cudaEventRecord(P.caller, static_cast<cudaStream_t>(stream)));
+  CUDA_TRY(cudaStreamWaitEvent(P.in, P.caller, 0));
+  CUDA_TRY(cudaStreamWaitEvent(P.in, P.solved[k], 0));
+  CUDA_TRY(cudaMemcpyAsync(P.rho[k], rho_host, sizeof(double) * n, cudaMemcpyHostToDevice, P.in));
+  CUDA_TRY(cudaEventRecord(P.copied_in[k], P.in));
+  // solve: after the copy in, and after the copies out two calls back emptied this slot
+  CUDA_TRY(cudaStreamWaitEvent(P.solve, P.copied_in[k], 0));
+  CUDA_TRY(cudaStreamWaitEvent(P.solve, P.copied_out[k], 0));
+  rc = fmm_solve(t, P.rho[k], theta, precision, amc, P.phi[k], P.g[k], net_host ? P.net[k] : nullptr,
+                 P.solve);
+  if (rc) return rc;
+  CUDA_TRY(cudaEventRecord(P.solved[k], P.solve));
+  // copy out
+  CUDA_TRY(cudaStreamWaitEvent(P.out, P.solved[k], 0));
+  CUDA_TRY(cudaMemcpyAsync(phi_host, P.phi[k], sizeof(double) * n, cudaMemcpyDeviceToHost, P.out));
+  CUDA_TRY(cudaMemcpyAsync(g_host, P.g[k], sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, P.out));
+  if (net_host)
+    CUDA_TRY(cudaMemcpyAsync(net_host, P.net[k], sizeof(double) * 7 * t->h.n_trees,
+                             cudaMemcpyDeviceToHost, P.out));
+  CUDA_TRY(cudaEventRecord(P.copied_out[k], P.out));
+  P.slot = 1 - k;
+  return FMM_OK;
 }
 
 int fmm_net_force_torque(fmm_tree* t, const double* rho_dev, const double* g_dev, double* net_dev,

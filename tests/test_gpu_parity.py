@@ -330,3 +330,28 @@ def test_one_leaf_level_tree_and_forest_of_one():
     f = api.Forest([a])
     p2, g2, n2 = gpu_solve(f, rho, 0.5)
     assert np.array_equal(p2, phi) and np.array_equal(g2, g) and np.array_equal(n2, net)
+
+
+def test_pipelined_host_solves_equal_device_solves():
+    """fmm_solve_host_async: a sequence of host-buffer solves on different densities, pipelined over
+    two device slots and three streams, gives every step's phi, g and net sums bit for bit as the
+    device entry point does, whichever slot the step used."""
+    w = synth.workload_binary(4)
+    a = api.Tree(w.max_level, w.flags)
+    rho0 = synth.leaf_density(w.field, a.leaves())
+    floor = w.field.floor * w.field.rho_peak
+    steps = [np.ascontiguousarray(synth.perturbed_density(rho0, k, floor_value=floor)) for k in range(5)]
+    n = rho0.size
+    outs = [(np.empty(n), np.empty((n, 3)), np.empty(7)) for _ in steps]
+    pinned = [torch.from_numpy(r).pin_memory() for r in steps]
+    pins = [(torch.empty(n, dtype=torch.float64).pin_memory(),
+             torch.empty((n, 3), dtype=torch.float64).pin_memory(),
+             torch.empty(7, dtype=torch.float64).pin_memory()) for _ in steps]
+    for k in range(len(steps)):
+        a.solve_host_async(pinned[k].numpy(), 0.5, "fp64", pins[k][0].numpy(), pins[k][1].numpy(),
+                           pins[k][2].numpy())
+    a.sync_status()
+    for k, r in enumerate(steps):
+        phi, g, net = gpu_solve(a, r, 0.5)
+        assert np.array_equal(pins[k][0].numpy(), phi) and np.array_equal(pins[k][1].numpy(), g)
+        assert np.array_equal(pins[k][2].numpy(), net)
