@@ -244,10 +244,13 @@ int fmm_binary_iterate(fmm_tree* tree, const double* rho_dev, const double* g_de
 int fmm_set_variant(fmm_tree* tree, double theta, int variant);
 
 /* Autotuner: times launch variants of `precision` on the caller's density, `reps` timed solves
- * each after one warm-up solve (CUDA events on `stream`, the median kept), and keeps the fastest
- * for this tree and theta (part of the graph key).  FMM_MIXED: a coordinate search -- the 24
- * variants with c = 0, then the other three split thresholds c with the best of them; FP64 and
- * df64: their one configuration.  Writes the chosen variant to *variant_out and, when ms_host is
+ * each after one warm-up solve (CUDA events on `stream`, the median kept; before every timed
+ * solve a scratch buffer of twice the L2's size is overwritten, so that each starts with cold
+ * caches as a solve inside a time step does), and keeps the fastest for this tree and theta (part
+ * of the graph key); a variant displaces the one kept so far only when it is at least 1 % faster.
+ * FMM_MIXED: a coordinate search -- the 24 variants with c = 0 (variant 0 first), then the other
+ * three split thresholds c with the best of them; FP64 and df64: their one configuration.  The
+ * scratch buffer is allocated and freed by the call.  Writes the chosen variant to *variant_out and, when ms_host is
  * not null, each timed variant's median (ms) to ms_host[variant] (FMM_MIXED_VARIANTS floats; -1
  * for variants not timed), and leaves the chosen variant's phi and g in the output buffers.
  * Blocks the calling thread until done.  rho_dev, phi_dev, g_dev as for fmm_solve.  FMM_ERR_ARG

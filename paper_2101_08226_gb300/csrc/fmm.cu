@@ -3696,7 +3696,10 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
       if (staged) {
         CUDA_TRY(cudaGetLastError());
         ++nl;
+        if ((rc = record(t, 6, st))) return rc;
         k_m2l_stage<false><<<unsigned(t->work.size()), kStageThreads, kStageSmem, st>>>(A, t->d_work, amc);
+        CUDA_TRY(cudaGetLastError());
+        if ((rc = record(t, 7, st))) return rc;
       }
     } else if (df) {
       k_m2l_ref<dfloat, kM2LThreads><<<unsigned(sd->n_blocks), kM2LThreads, 0, st>>>(A, sd->d_blocks, amc);
@@ -3859,8 +3862,7 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   CUDA_TRY(cudaEventRecord(t->ev_out, t->stream));
   CUDA_TRY(cudaStreamWaitEvent(caller, t->ev_out, 0));
   t->ev_recorded = t->profiling;
-  t->ev_stage = t->profiling && mixed && !t->work.empty() &&
-                (sd->mixed_variant % 4 == 0 || sd->mixed_variant % 4 == 3);  // ev[6], ev[7]
+  t->ev_stage = t->profiling && mixed && !t->work.empty() && sd->mixed_variant % 4 != 2;  // ev[6], ev[7]
   t->launches = n_io + n_solve;
   return FMM_OK;
 }
@@ -4405,6 +4407,13 @@ int fmm_autotune(fmm_tree* t, const double* rho_dev, double theta, int precision
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
+    // each timed solve starts with cold caches, as a solve does inside a time step: a buffer of
+    // twice the L2's size is overwritten before it (outside the timed interval)
+    int l2 = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, t->device));
+    const size_t flush_bytes = size_t(2) * size_t(l2 > 0 ? l2 : (64 << 20));
+    void* flush = nullptr;
+    CUDA_TRY(cudaMalloc(&flush, flush_bytes));
     if (ms_host)
       for (int v = 0; v < (precision == FMM_MIXED ? kMixedVariants : 1); ++v) ms_host[v] = -1.0f;
     // median time of `reps` solves of variant v after a warm-up solve (which captures its graph)
@@ -4414,7 +4423,8 @@ int fmm_autotune(fmm_tree* t, const double* rho_dev, double theta, int precision
       std::vector<float> ms;
       for (int k = 0; k < reps && r == FMM_OK; ++k) {
         float x = 0.0f;
-        if (cudaEventRecord(e0, caller) != cudaSuccess) r = fail(FMM_ERR_CUDA, "event record");
+        if (cudaMemsetAsync(flush, k & 0xff, flush_bytes, caller) != cudaSuccess) r = fail(FMM_ERR_CUDA, "L2 flush");
+        if (!r && cudaEventRecord(e0, caller) != cudaSuccess) r = fail(FMM_ERR_CUDA, "event record");
         if (!r) r = solve_impl(t, io, theta, precision, amc, nullptr, caller);
         if (!r && (cudaEventRecord(e1, caller) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                    cudaEventElapsedTime(&x, e0, e1) != cudaSuccess))
@@ -4428,14 +4438,16 @@ int fmm_autotune(fmm_tree* t, const double* rho_dev, double theta, int precision
       return FMM_OK;
     };
     // coordinate search: every kernel / leaf layout / placement combination at the default split
-    // threshold, then the split thresholds with the best of those
+    // threshold, then the split thresholds with the best of those.  A variant displaces the one
+    // kept so far only when it is at least 1 % faster, so that timing noise does not move the
+    // choice away from the default
     int best = 0;
     float best_ms = 0.0f;
     const int n_first = precision == FMM_MIXED ? 24 : 1;
     for (int v = 0; v < n_first && rc == FMM_OK; ++v) {
       float m = 0.0f;
       rc = time_variant(v, &m);
-      if (!rc && (v == 0 || m < best_ms)) {
+      if (!rc && (v == 0 || m < 0.99f * best_ms)) {
         best = v;
         best_ms = m;
       }
@@ -4445,7 +4457,7 @@ int fmm_autotune(fmm_tree* t, const double* rho_dev, double theta, int precision
       for (int c = 1; c < kSplitChoices && rc == FMM_OK; ++c) {
         float m = 0.0f;
         rc = time_variant(base + 24 * c, &m);
-        if (!rc && m < best_ms) {
+        if (!rc && m < 0.99f * best_ms) {
           best = base + 24 * c;
           best_ms = m;
         }
@@ -4453,6 +4465,7 @@ int fmm_autotune(fmm_tree* t, const double* rho_dev, double theta, int precision
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaFree(flush);
     if (rc) return rc;
     if (precision == FMM_MIXED) sd->mixed_variant = best;
     *variant_out = best;

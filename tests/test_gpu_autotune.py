@@ -64,7 +64,9 @@ def test_autotune_picks_a_variant_and_keeps_it():
     # thresholds with the best of those; the rest are marked -1
     timed = ms > 0
     assert timed[:24].all() and timed.sum() == 27 and (ms[~timed] == -1).all()
-    assert ms[v] == ms[timed].min()
+    # the choice is within 1 % of the fastest variant timed (a variant displaces the kept one
+    # only when it is 1 % faster)
+    assert ms[v] <= ms[timed].min() / 0.99 ** 2
     phi2, g2, _ = a.solve(r, 0.5, "mixed")  # uses the chosen variant
     a.set_variant(0.5, v)
     phi3, g3, _ = a.solve(r, 0.5, "mixed")
