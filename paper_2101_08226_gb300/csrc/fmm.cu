@@ -143,9 +143,9 @@ struct DevArgs {
   int64_t n_bt;
   int64_t n_bt_long;       // k_m2l_split: the targets [0, n_bt_long) with four lanes each
   const int32_t* bt_cell;  // [n_bt] internal cell index of each target
-  const int32_t* bm_off;   // [n_bt + 1] its multipole partners: bm_src / bm_q [bm_off[k], ..)
-  const int32_t* bm_src;   // partner cell (in a refined same-level neighbour)
-  const int32_t* bm_q;     // stencil entry of the partner (offset d in the target's parity table)
+  const int32_t* bm_off;   // [n_bt + 1] its multipole partners: bm_e [bm_off[k], ..)
+  const uint16_t* bm_e;    // a partner in 16 bits: the neighbour slot of the target's subgrid that
+                           // holds it (bits 9-13) and its internal cell index there (bits 0-8)
   const int32_t* bp_off;   // [n_bt + 1] its point-mass partners: bp_src / bp_code
   const int32_t* bp_src;
   const int32_t* bp_code;  // x_A - x_B in units of dx / 4, three 10-bit fields biased by 512
@@ -1071,6 +1071,35 @@ struct LeafMass<dfloat> {
   static __device__ __forceinline__ const dfloat* get(const DevArgs& A) { return A.massff; }
 };
 
+// A multipole partner of a boundary target from its 16-bit list entry: the neighbour slot of the
+// target's subgrid s (slot = (sx * 3 + sy) * 3 + sz, s itself at 13) and the partner's internal
+// cell index there; also the partner's offset from the target cell (a, b, c) in cells.
+__device__ __forceinline__ int64_t boundary_partner(const DevArgs& A, int32_t s, int a, int b, int c,
+                                                    uint32_t e, int& dx, int& dy, int& dz) {
+  const int slot = int(e >> 9), loc = int(e & 511);
+  int la, lb, lc;
+  cdecode(loc, la, lb, lc);
+  dx = (slot / 9 - 1) * kSub + la - a;
+  dy = ((slot / 3) % 3 - 1) * kSub + lb - b;
+  dz = (slot % 3 - 1) * kSub + lc - c;
+  const int32_t q = A.nbr[27 * s + slot];
+  return int64_t(q) * kCells + loc;
+}
+// -d h for an integer offset d and a cell width h = 2^-(lev + 3), exact and without FP64-pipe
+// arithmetic in the FP64 path (the double is assembled from integer bits).
+template <typename T>
+__device__ __forceinline__ T neg_offset(int d, int lev);
+template <>
+__device__ __forceinline__ double neg_offset<double>(int d, int lev) {
+  return __longlong_as_double(d == 0 ? 0ll : __double_as_longlong(dyadic(-d, lev + 3)));
+}
+template <>
+__device__ __forceinline__ float neg_offset<float>(int d, int lev) { return float(-d) * cell_dx32(lev); }
+template <>
+__device__ __forceinline__ dfloat neg_offset<dfloat>(int d, int lev) {
+  return dfloat(float(-d) * cell_dx32(lev), 0.0f);
+}
+
 // Leaf targets at a refinement boundary, 64 per block, from the pair lists built on the host:
 // multipole interactions with the cells of refined same-level neighbours, then direct sums with
 // point masses (the leaf children of refined near cells, and leaves one level coarser near the
@@ -1091,36 +1120,32 @@ __device__ void m2l_boundary(const DevArgs& A, int64_t first, int64_t end, int c
   const bool valid = k < end && !FMM_BAD(A, A.bt_cell[k] >= 0 && A.bt_cell[k] < A.n_cell);
   if (LANES == 1 && !valid) return;
   const int64_t iA = valid ? A.bt_cell[k] : 0;
-  const int parity = int(iA & 511) >> 6;
   const T* __restrict__ M = MomView<T>::get(A);
   const int64_t N = A.n_cell;
   Target<T, false> S;
   load_target<T, false>(S, A, M, iA, amc);
-  const T h = cell_h<T>(A.level[iA >> 9]);
-  const T* __restrict__ td = LeafOffsets<T>::get(A) + int64_t(parity) * kLeafCap * 4;
-  // each list entry's indices are loaded one entry ahead, so that a pair waits for its partner's
-  // moments only, not for the index that locates them first; point partners' masses come from
-  // the contiguous mass array (the same values as component 0 of the moments)
+  const int32_t sA = int32_t(iA >> 9);
+  const int lev = A.level[sA];
+  const T h = cell_h<T>(lev);
+  int a, b, c;
+  cdecode(int(iA & 511), a, b, c);
+  // each list entry is loaded and decoded one entry ahead, so that a pair waits for its
+  // partner's moments only, not for the index that locates them first; point partners' masses
+  // come from the contiguous mass array (the same values as component 0 of the moments)
   const T* __restrict__ Mass = LeafMass<T>::get(A);
   const int32_t m0 = (valid ? A.bm_off[k] : 0) + r, m1 = valid ? A.bm_off[k + 1] : 0;
-  int q_next = 0;
-  int32_t src_next = 0;
-  if (m0 < m1) {
-    q_next = __ldg(A.bm_q + m0);
-    src_next = __ldg(A.bm_src + m0);
-  }
+  int dx_next = 0, dy_next = 0, dz_next = 0;
+  int64_t src_next = 0;
+  if (m0 < m1) src_next = boundary_partner(A, sA, a, b, c, __ldg(A.bm_e + m0), dx_next, dy_next, dz_next);
   for (int32_t j0 = m0; j0 < m1; j0 += LANES * kFlush) {
     const int32_t j1 = min(j0 + LANES * kFlush, m1);
     for (int32_t j = j0; j < j1; j += LANES) {
-      const int q = q_next;
-      const int32_t src = src_next;
-      if (j + LANES < m1) {
-        q_next = __ldg(A.bm_q + j + LANES);
-        src_next = __ldg(A.bm_src + j + LANES);
-      }
-      if (FMM_BAD(A, src >= 0 && src < N && q >= 0 && q < kLeafCap)) continue;
-      interact_lr<T>(S, M, N, src, -ldg_t(td + 4 * q) * h, -ldg_t(td + 4 * q + 1) * h,
-                     -ldg_t(td + 4 * q + 2) * h);
+      const int64_t src = src_next;
+      const int dx = dx_next, dy = dy_next, dz = dz_next;
+      if (j + LANES < m1)
+        src_next = boundary_partner(A, sA, a, b, c, __ldg(A.bm_e + j + LANES), dx_next, dy_next, dz_next);
+      if (FMM_BAD(A, src >= 0 && src < N)) continue;
+      interact_lr<T>(S, M, N, src, neg_offset<T>(dx, lev), neg_offset<T>(dy, lev), neg_offset<T>(dz, lev));
     }
     flush(S);
   }
@@ -2469,18 +2494,21 @@ __device__ void m2l_boundary_src(const DevArgs& A, int64_t first, int64_t end, i
   const bool valid = k < end;
   if (LANES == 1 && !valid) return;
   const int64_t iA = valid ? A.bt_cell[k] : 0;
-  const int parity = int(iA & 511) >> 6;
   const T* __restrict__ G = MomView<T>::get(A);
   const T* __restrict__ Sm = SrcView<T>::get(A);
   const int64_t N = A.n_cell;
-  const T h = cell_h<T>(A.level[iA >> 9]);
-  const T* __restrict__ td = LeafOffsets<T>::get(A) + int64_t(parity) * kLeafCap * 4;
+  const int32_t sA = int32_t(iA >> 9);
+  const int lev = A.level[sA];
+  const T h = cell_h<T>(lev);
+  int a, b, c;
+  cdecode(int(iA & 511), a, b, c);
   T L[1] = {T(0)};
   const int32_t m1 = valid ? A.bm_off[k + 1] : 0;
   for (int32_t j = (valid ? A.bm_off[k] : 0) + r; j < m1; j += LANES) {
-    const int q = __ldg(A.bm_q + j);
-    interact_src<T, false, true>(L, Sm, G, N, __ldg(A.bm_src + j), -ldg_t(td + 4 * q) * h,
-                                 -ldg_t(td + 4 * q + 1) * h, -ldg_t(td + 4 * q + 2) * h);
+    int dx, dy, dz;
+    const int64_t src = boundary_partner(A, sA, a, b, c, __ldg(A.bm_e + j), dx, dy, dz);
+    interact_src<T, false, true>(L, Sm, G, N, src, neg_offset<T>(dx, lev), neg_offset<T>(dy, lev),
+                                 neg_offset<T>(dz, lev));
   }
   const int32_t p1 = valid ? A.bp_off[k + 1] : 0;
   for (int32_t j = (valid ? A.bp_off[k] : 0) + r; j < p1; j += LANES) {
@@ -2813,7 +2841,8 @@ struct StencilDev {
   int32_t* d_stage_seg = nullptr;  // [8][9]
   // boundary pair lists (see DevArgs)
   int64_t n_bt = 0;
-  int32_t *d_bt_cell = nullptr, *d_bm_off = nullptr, *d_bm_src = nullptr, *d_bm_q = nullptr,
+  uint16_t* d_bm_e = nullptr;
+  int32_t *d_bt_cell = nullptr, *d_bm_off = nullptr,
           *d_bp_off = nullptr, *d_bp_src = nullptr, *d_bp_code = nullptr;
 
   int n_stencil = 0, n_near = 0;
@@ -3104,7 +3133,8 @@ static inline int slot_of(int p) { return p < 0 ? 0 : (p < 8 ? 1 : 2); }
 //     neighbour, and the near entries of the parent cell that land in a leaf one level coarser.
 // Targets without partners are dropped; the rest are sorted by estimated work, largest first.
 struct BoundaryLists {
-  std::vector<int32_t> cell, m_off, m_src, m_q, p_off, p_src, p_code;
+  std::vector<int32_t> cell, m_off, p_off, p_src, p_code;
+  std::vector<uint16_t> m_e;  // multipole partners: neighbour slot << 9 | internal cell index
   std::vector<double> cost;  // per target, in the order of `cell`
 };
 
@@ -3117,7 +3147,8 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
   // first pass: every target's lists in subgrid order, flat
   std::vector<int32_t> cell;
   std::vector<int64_t> moff{0}, poff{0};
-  std::vector<int32_t> ms, mq, ps, pc;
+  std::vector<int32_t> ps, pc;
+  std::vector<uint16_t> ms;
   for (int32_t s : work_bnd) {
     int32_t nb[27], pnb[27];
     bool nb_ref[27], pnb_leaf[27];
@@ -3140,8 +3171,7 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
             const int px = a + dx, py = b + dy, pz = c + dz;
             const int sl = slot_of(px) * 9 + slot_of(py) * 3 + slot_of(pz);
             if (!nb_ref[sl]) continue;
-            ms.push_back(int32_t(int64_t(nb[sl]) * kCells + host_cidx(px & 7, py & 7, pz & 7)));
-            mq.push_back(int32_t(q));
+            ms.push_back(uint16_t((sl << 9) | host_cidx(px & 7, py & 7, pz & 7)));
           }
           for (int32_t code : st.near) {
             int dx, dy, dz;
@@ -3200,8 +3230,7 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
   out.cost.resize(n);
   out.m_off.resize(n + 1);
   out.p_off.resize(n + 1);
-  out.m_src.resize(ms.size());
-  out.m_q.resize(mq.size());
+  out.m_e.resize(ms.size());
   out.p_src.resize(ps.size());
   out.p_code.resize(pc.size());
   int64_t mo = 0, po = 0;
@@ -3210,8 +3239,7 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
     const size_t k = order[r];
     out.cell[r] = cell[k];
     out.cost[r] = cost[k];
-    std::copy(ms.begin() + moff[k], ms.begin() + moff[k + 1], out.m_src.begin() + mo);
-    std::copy(mq.begin() + moff[k], mq.begin() + moff[k + 1], out.m_q.begin() + mo);
+    std::copy(ms.begin() + moff[k], ms.begin() + moff[k + 1], out.m_e.begin() + mo);
     std::copy(ps.begin() + poff[k], ps.begin() + poff[k + 1], out.p_src.begin() + po);
     std::copy(pc.begin() + poff[k], pc.begin() + poff[k + 1], out.p_code.begin() + po);
     mo += moff[k + 1] - moff[k];
@@ -3385,8 +3413,7 @@ static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
     sd.n_bt = int64_t(bl.cell.size());
     CUDA_TRY(upload(t, &sd.d_bt_cell, bl.cell));
     CUDA_TRY(upload(t, &sd.d_bm_off, bl.m_off));
-    CUDA_TRY(upload(t, &sd.d_bm_src, bl.m_src));
-    CUDA_TRY(upload(t, &sd.d_bm_q, bl.m_q));
+    CUDA_TRY(upload(t, &sd.d_bm_e, bl.m_e));
     CUDA_TRY(upload(t, &sd.d_bp_off, bl.p_off));
     CUDA_TRY(upload(t, &sd.d_bp_src, bl.p_src));
     CUDA_TRY(upload(t, &sd.d_bp_code, bl.p_code));
@@ -3494,8 +3521,7 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.n_bt = sd ? sd->n_bt : 0;
   A.bt_cell = sd ? sd->d_bt_cell : nullptr;
   A.bm_off = sd ? sd->d_bm_off : nullptr;
-  A.bm_src = sd ? sd->d_bm_src : nullptr;
-  A.bm_q = sd ? sd->d_bm_q : nullptr;
+  A.bm_e = sd ? sd->d_bm_e : nullptr;
   A.bp_off = sd ? sd->d_bp_off : nullptr;
   A.bp_src = sd ? sd->d_bp_src : nullptr;
   A.bp_code = sd ? sd->d_bp_code : nullptr;
