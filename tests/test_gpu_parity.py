@@ -342,7 +342,6 @@ def test_pipelined_host_solves_equal_device_solves():
     floor = w.field.floor * w.field.rho_peak
     steps = [np.ascontiguousarray(synth.perturbed_density(rho0, k, floor_value=floor)) for k in range(5)]
     n = rho0.size
-    outs = [(np.empty(n), np.empty((n, 3)), np.empty(7)) for _ in steps]
     pinned = [torch.from_numpy(r).pin_memory() for r in steps]
     pins = [(torch.empty(n, dtype=torch.float64).pin_memory(),
              torch.empty((n, 3), dtype=torch.float64).pin_memory(),
