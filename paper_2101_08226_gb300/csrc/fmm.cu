@@ -146,9 +146,9 @@ struct DevArgs {
   const int32_t* bm_off;   // [n_bt + 1] its multipole partners: bm_e [bm_off[k], ..)
   const uint16_t* bm_e;    // a partner in 16 bits: the neighbour slot of the target's subgrid that
                            // holds it (bits 9-13) and its internal cell index there (bits 0-8)
-  const int32_t* bp_off;   // [n_bt + 1] its point-mass partners: bp_src / bp_code
-  const int32_t* bp_src;
-  const int32_t* bp_code;  // x_A - x_B in units of dx / 4, three 10-bit fields biased by 512
+  const int32_t* bp_off;   // [n_bt + 1] its point-mass partner entries: bp_e [bp_off[k], ..)
+  const uint16_t* bp_e;    // an entry in 16 bits: kind (bit 15), neighbour slot (bits 9-13) and
+                           // internal cell index (bits 0-8); see point_partner
   const int32_t* leaf_tree;  // [n_leaf_sub] tree of each leaf subgrid
   const TreeIo* io;          // [n_roots] the caller's arrays of each tree
   double* const* io_net;     // the caller's net array (7 numbers per tree), or null
@@ -1085,6 +1085,45 @@ __device__ __forceinline__ int64_t boundary_partner(const DevArgs& A, int32_t s,
   const int32_t q = A.nbr[27 * s + slot];
   return int64_t(q) * kCells + loc;
 }
+// A point-mass partner entry of a boundary target (kind << 15 | slot << 9 | internal cell index).
+// Kind 0: a near cell (offset d in cells from the target cell (a, b, c)) in the refined
+// same-level neighbour at `slot` of the target's subgrid s.  It stands for the near cell's 8
+// leaf children, which the parity-major order puts 64 apart: child o = ox << 2 | oy << 1 | oz
+// is cell first + 64 o, and x_A - x_child = (1 - 2 o_x - 4 d_x, ...) dx / 4.
+// Kind 1: a leaf cell one level coarser, in the neighbour at `slot` of the parent subgrid, at
+// offset d in coarse cells from the target's parent cell: one partner at first, with
+// x_A - x_i = (4 (a & 1) - 2 - 8 d_x, ...) dx / 4.
+// Returns the number of point masses (8 or 1) and q = x_A - x_first in units of dx / 4; -1 when
+// a bounds check fails (the bounds-checked build).
+__device__ __forceinline__ int point_partner(const DevArgs& A, int32_t s, int a, int b, int c,
+                                             uint32_t e, int64_t& first, int& qx, int& qy, int& qz) {
+  const int slot = int((e >> 9) & 31), loc = int(e & 511);
+  int la, lb, lc;
+  cdecode(loc, la, lb, lc);
+  const int px = (slot / 9 - 1) * kSub + la, py = ((slot / 3) % 3 - 1) * kSub + lb,
+            pz = (slot % 3 - 1) * kSub + lc;
+  if (!(e >> 15)) {
+    const int32_t q = A.nbr[27 * s + slot];
+    if (FMM_BAD(A, slot < 27 && q >= 0 && int64_t(q) * kCells < A.n_cell)) return -1;
+    const int32_t cs = A.child[8 * q + ((la >> 2) << 2 | (lb >> 2) << 1 | (lc >> 2))];
+    if (FMM_BAD(A, cs >= 0 && int64_t(cs) * kCells < A.n_cell)) return -1;
+    first = int64_t(cs) * kCells + ((la & 3) << 4 | (lb & 3) << 2 | (lc & 3));
+    qx = 1 - 4 * (px - a);
+    qy = 1 - 4 * (py - b);
+    qz = 1 - 4 * (pz - c);
+    return 8;
+  }
+  const int32_t P = A.parent[s];
+  if (FMM_BAD(A, slot < 27 && P >= 0 && int64_t(P) * kCells < A.n_cell)) return -1;
+  const int32_t q = A.nbr[27 * P + slot];
+  if (FMM_BAD(A, q >= 0 && int64_t(q) * kCells < A.n_cell)) return -1;
+  first = int64_t(q) * kCells + loc;
+  // the target's parent cell in the parent subgrid: (a >> 1) + 4 (the subgrid's octant bit)
+  qx = 4 * (a & 1) - 2 - 8 * (px - ((A.ijk[3 * s] & 1) << 2) - (a >> 1));
+  qy = 4 * (b & 1) - 2 - 8 * (py - ((A.ijk[3 * s + 1] & 1) << 2) - (b >> 1));
+  qz = 4 * (c & 1) - 2 - 8 * (pz - ((A.ijk[3 * s + 2] & 1) << 2) - (c >> 1));
+  return 1;
+}
 // -d h for an integer offset d and a cell width h = 2^-(lev + 3), exact and without FP64-pipe
 // arithmetic in the FP64 path (the double is assembled from integer bits).
 template <typename T>
@@ -1150,25 +1189,28 @@ __device__ void m2l_boundary(const DevArgs& A, int64_t first, int64_t end, int c
     flush(S);
   }
   const int32_t p0 = (valid ? A.bp_off[k] : 0) + r, p1 = valid ? A.bp_off[k + 1] : 0;
-  int32_t code_next = 0, psrc_next = 0;
-  if (p0 < p1) {
-    code_next = __ldg(A.bp_code + p0);
-    psrc_next = __ldg(A.bp_src + p0);
-  }
+  int64_t first_next = 0;
+  int n_next = 0, qx_next = 0, qy_next = 0, qz_next = 0;
+  if (p0 < p1) n_next = point_partner(A, sA, a, b, c, __ldg(A.bp_e + p0), first_next, qx_next, qy_next, qz_next);
   for (int32_t j = p0; j < p1; j += LANES) {
-    const int32_t code = code_next, src = psrc_next;
-    if (j + LANES < p1) {
-      code_next = __ldg(A.bp_code + j + LANES);
-      psrc_next = __ldg(A.bp_src + j + LANES);
-    }
-    if (FMM_BAD(A, src >= 0 && src < N && unsigned(((code >> 20) & 1023) - 512 + kCodeMax) <= 2u * kCodeMax &&
-                       unsigned(((code >> 10) & 1023) - 512 + kCodeMax) <= 2u * kCodeMax &&
-                       unsigned((code & 1023) - 512 + kCodeMax) <= 2u * kCodeMax))
+    const int64_t first = first_next;
+    const int n = n_next, qx = qx_next, qy = qy_next, qz = qz_next;
+    if (j + LANES < p1)
+      n_next = point_partner(A, sA, a, b, c, __ldg(A.bp_e + j + LANES), first_next, qx_next, qy_next, qz_next);
+    if (FMM_BAD(A, n > 0 && first + 64 * (n - 1) < N && unsigned(qx + kCodeMax - 2) <= 2u * kCodeMax - 2 &&
+                       unsigned(qy + kCodeMax - 2) <= 2u * kCodeMax - 2 &&
+                       unsigned(qz + kCodeMax - 2) <= 2u * kCodeMax - 2))
       continue;
-    const T x = quarter[((code >> 20) & 1023) - 512 + kCodeMax] * h;
-    const T y = quarter[((code >> 10) & 1023) - 512 + kCodeMax] * h;
-    const T z = quarter[(code & 1023) - 512 + kCodeMax] * h;
-    interact_point<T, false>(S, Mass[src], x, y, z);
+    if (n == 8) {
+#pragma unroll
+      for (int o = 0; o < 8; ++o)
+        interact_point<T, false>(S, Mass[first + 64 * o], quarter[qx - 2 * (o >> 2) + kCodeMax] * h,
+                                 quarter[qy - 2 * ((o >> 1) & 1) + kCodeMax] * h,
+                                 quarter[qz - 2 * (o & 1) + kCodeMax] * h);
+    } else {
+      interact_point<T, false>(S, Mass[first], quarter[qx + kCodeMax] * h, quarter[qy + kCodeMax] * h,
+                               quarter[qz + kCodeMax] * h);
+    }
   }
   if constexpr (LANES > 1) {
     lane_reduce<LANES>(S);  // the correction partials were flushed after the multipole pairs
@@ -2512,11 +2554,18 @@ __device__ void m2l_boundary_src(const DevArgs& A, int64_t first, int64_t end, i
   }
   const int32_t p1 = valid ? A.bp_off[k + 1] : 0;
   for (int32_t j = (valid ? A.bp_off[k] : 0) + r; j < p1; j += LANES) {
-    const int32_t code = __ldg(A.bp_code + j);
-    interact_src<T, false, false>(L, Sm, G, N, __ldg(A.bp_src + j),
-                                  quarter[((code >> 20) & 1023) - 512 + kCodeMax] * h,
-                                  quarter[((code >> 10) & 1023) - 512 + kCodeMax] * h,
-                                  quarter[(code & 1023) - 512 + kCodeMax] * h);
+    int64_t first;
+    int qx, qy, qz;
+    const int n = point_partner(A, sA, a, b, c, __ldg(A.bp_e + j), first, qx, qy, qz);
+    if (FMM_BAD(A, n > 0 && first + 64 * (n - 1) < N && unsigned(qx + kCodeMax - 2) <= 2u * kCodeMax - 2 &&
+                       unsigned(qy + kCodeMax - 2) <= 2u * kCodeMax - 2 &&
+                       unsigned(qz + kCodeMax - 2) <= 2u * kCodeMax - 2))
+      continue;
+    for (int o = 0; o < n; ++o)
+      interact_src<T, false, false>(L, Sm, G, N, first + 64 * o,
+                                    quarter[qx - (n == 8 ? 2 * (o >> 2) : 0) + kCodeMax] * h,
+                                    quarter[qy - (n == 8 ? 2 * ((o >> 1) & 1) : 0) + kCodeMax] * h,
+                                    quarter[qz - (n == 8 ? 2 * (o & 1) : 0) + kCodeMax] * h);
   }
   if constexpr (LANES > 1) {
 #pragma unroll
@@ -2843,7 +2892,8 @@ struct StencilDev {
   int64_t n_bt = 0;
   uint16_t* d_bm_e = nullptr;
   int32_t *d_bt_cell = nullptr, *d_bm_off = nullptr,
-          *d_bp_off = nullptr, *d_bp_src = nullptr, *d_bp_code = nullptr;
+          *d_bp_off = nullptr;
+  uint16_t* d_bp_e = nullptr;
 
   int n_stencil = 0, n_near = 0;
   int ws_d2 = 0;
@@ -3133,22 +3183,27 @@ static inline int slot_of(int p) { return p < 0 ? 0 : (p < 8 ? 1 : 2); }
 //     neighbour, and the near entries of the parent cell that land in a leaf one level coarser.
 // Targets without partners are dropped; the rest are sorted by estimated work, largest first.
 struct BoundaryLists {
-  std::vector<int32_t> cell, m_off, p_off, p_src, p_code;
+  std::vector<int32_t> cell, m_off, p_off;
   std::vector<uint16_t> m_e;  // multipole partners: neighbour slot << 9 | internal cell index
+  std::vector<uint16_t> p_e;  // point-mass partners: kind << 15 | neighbour slot << 9 | cell index
   std::vector<double> cost;  // per target, in the order of `cell`
 };
 
 static std::string boundary_lists(const HostTree& h, const Stencil& st,
                                   const std::vector<int32_t>& work_bnd, BoundaryLists& out) {
   const double c_m = 150, c_p = 20;
-  auto code3 = [](int x, int y, int z) {
-    return int32_t((uint32_t(x + 512) << 20) | (uint32_t(y + 512) << 10) | uint32_t(z + 512));
+  // an entry's offsets x_A - x_first in units of dx / 4 (the kernel forms the same numbers, and
+  // kind 0 lowers each by up to 2 for the children): all must index the kernel's table
+  bool code_ok = true;
+  auto check = [&](int qx, int qy, int qz) {
+    for (int v : {qx, qy, qz}) code_ok = code_ok && v <= kCodeMax && v - 2 >= -kCodeMax;
   };
   // first pass: every target's lists in subgrid order, flat
   std::vector<int32_t> cell;
   std::vector<int64_t> moff{0}, poff{0};
-  std::vector<int32_t> ps, pc;
-  std::vector<uint16_t> ms;
+  std::vector<uint16_t> ms, ps;
+  std::vector<int64_t> npt{0};  // point masses per target, running
+  int64_t n_points = 0;
   for (int32_t s : work_bnd) {
     int32_t nb[27], pnb[27];
     bool nb_ref[27], pnb_leaf[27];
@@ -3179,15 +3234,11 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
             const int px = a + dx, py = b + dy, pz = c + dz;
             const int sl = slot_of(px) * 9 + slot_of(py) * 3 + slot_of(pz);
             if (!nb_ref[sl]) continue;
-            const int lx = px & 7, ly = py & 7, lz = pz & 7;
-            const int32_t cs = h.child[8 * nb[sl] + ((lx >> 2) << 2 | (ly >> 2) << 1 | (lz >> 2))];
-            for (int o = 0; o < 8; ++o) {
-              const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-              ps.push_back(int32_t(int64_t(cs) * kCells +
-                                   host_cidx((lx & 3) * 2 + ox, (ly & 3) * 2 + oy, (lz & 3) * 2 + oz)));
-              // x_A - x_C = (1/2 - o - 2 d) dx_(l+1) = (1 - 2 o - 4 d) dx_l / 4
-              pc.push_back(code3(1 - 2 * ox - 4 * dx, 1 - 2 * oy - 4 * dy, 1 - 2 * oz - 4 * dz));
-            }
+            // the 8 leaf children C (o = 0..7) of the near cell: x_A - x_C = (1/2 - o - 2 d) dx_(l+1)
+            // = (1 - 2 o - 4 d) dx_l / 4
+            ps.push_back(uint16_t((sl << 9) | host_cidx(px & 7, py & 7, pz & 7)));
+            check(1 - 4 * dx, 1 - 4 * dy, 1 - 4 * dz);
+            n_points += 8;
           }
           const int ga = h.ijk[3 * s] * 8 + a, gb = h.ijk[3 * s + 1] * 8 + b, gc = h.ijk[3 * s + 2] * 8 + c;
           const int ja = (ga >> 1) - h.ijk[3 * P] * 8, jb = (gb >> 1) - h.ijk[3 * P + 1] * 8,
@@ -3198,22 +3249,20 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
             const int px = ja + dx, py = jb + dy, pz = jc + dz;
             const int sl = slot_of(px) * 9 + slot_of(py) * 3 + slot_of(pz);
             if (!pnb_leaf[sl]) continue;
-            ps.push_back(int32_t(int64_t(pnb[sl]) * kCells + host_cidx(px & 7, py & 7, pz & 7)));
-            // x_A - x_i = ((g_A & 1) - 1/2 - 2 d) dx_l = (4 (g_A & 1) - 2 - 8 d) dx_l / 4
-            pc.push_back(code3(4 * (ga & 1) - 2 - 8 * dx, 4 * (gb & 1) - 2 - 8 * dy,
-                               4 * (gc & 1) - 2 - 8 * dz));
+            // a leaf i one level coarser: x_A - x_i = ((g_A & 1) - 1/2 - 2 d) dx_l
+            // = (4 (g_A & 1) - 2 - 8 d) dx_l / 4
+            ps.push_back(uint16_t(0x8000 | (sl << 9) | host_cidx(px & 7, py & 7, pz & 7)));
+            check(4 * (ga & 1) - 2 - 8 * dx, 4 * (gb & 1) - 2 - 8 * dy, 4 * (gc & 1) - 2 - 8 * dz);
+            n_points += 1;
           }
           if (ms.size() == m0 && ps.size() == p0) continue;  // no partners
           cell.push_back(int32_t(int64_t(s) * kCells + host_cidx(a, b, c)));
           moff.push_back(int64_t(ms.size()));
           poff.push_back(int64_t(ps.size()));
+          npt.push_back(n_points);
         }
   }
-  for (int32_t code : pc)
-    for (int f = 0; f < 3; ++f) {
-      const int v = int((uint32_t(code) >> (20 - 10 * f)) & 1023u) - 512;
-      if (v < -kCodeMax || v > kCodeMax) return "point-pair offset outside the table";
-    }
+  if (!code_ok) return "point-pair offset outside the table";
   if (ms.size() > size_t(INT32_MAX) || ps.size() > size_t(INT32_MAX))
     return "boundary pair lists exceed 2^31 entries";
   // second pass: targets by estimated work, largest first
@@ -3221,7 +3270,7 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
   std::vector<double> cost(n);
   std::vector<size_t> order(n);
   for (size_t k = 0; k < n; ++k) {
-    cost[k] = c_m * double(moff[k + 1] - moff[k]) + c_p * double(poff[k + 1] - poff[k]);
+    cost[k] = c_m * double(moff[k + 1] - moff[k]) + c_p * double(npt[k + 1] - npt[k]);
     order[k] = k;
   }
   std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
@@ -3231,8 +3280,7 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
   out.m_off.resize(n + 1);
   out.p_off.resize(n + 1);
   out.m_e.resize(ms.size());
-  out.p_src.resize(ps.size());
-  out.p_code.resize(pc.size());
+  out.p_e.resize(ps.size());
   int64_t mo = 0, po = 0;
   out.m_off[0] = out.p_off[0] = 0;
   for (size_t r = 0; r < n; ++r) {
@@ -3240,8 +3288,7 @@ static std::string boundary_lists(const HostTree& h, const Stencil& st,
     out.cell[r] = cell[k];
     out.cost[r] = cost[k];
     std::copy(ms.begin() + moff[k], ms.begin() + moff[k + 1], out.m_e.begin() + mo);
-    std::copy(ps.begin() + poff[k], ps.begin() + poff[k + 1], out.p_src.begin() + po);
-    std::copy(pc.begin() + poff[k], pc.begin() + poff[k + 1], out.p_code.begin() + po);
+    std::copy(ps.begin() + poff[k], ps.begin() + poff[k + 1], out.p_e.begin() + po);
     mo += moff[k + 1] - moff[k];
     po += poff[k + 1] - poff[k];
     out.m_off[r + 1] = int32_t(mo);
@@ -3415,8 +3462,7 @@ static int get_stencil(fmm_tree* t, double theta, StencilDev** out) {
     CUDA_TRY(upload(t, &sd.d_bm_off, bl.m_off));
     CUDA_TRY(upload(t, &sd.d_bm_e, bl.m_e));
     CUDA_TRY(upload(t, &sd.d_bp_off, bl.p_off));
-    CUDA_TRY(upload(t, &sd.d_bp_src, bl.p_src));
-    CUDA_TRY(upload(t, &sd.d_bp_code, bl.p_code));
+    CUDA_TRY(upload(t, &sd.d_bp_e, bl.p_e));
     std::vector<int32_t> blocks = general_blocks(t->h, st, t->work, bl, false);
     sd.n_blocks = int64_t(blocks.size());
     CUDA_TRY(upload(t, &sd.d_blocks, blocks));
@@ -3523,8 +3569,7 @@ static DevArgs make_args(fmm_tree* t, const StencilDev* sd) {
   A.bm_off = sd ? sd->d_bm_off : nullptr;
   A.bm_e = sd ? sd->d_bm_e : nullptr;
   A.bp_off = sd ? sd->d_bp_off : nullptr;
-  A.bp_src = sd ? sd->d_bp_src : nullptr;
-  A.bp_code = sd ? sd->d_bp_code : nullptr;
+  A.bp_e = sd ? sd->d_bp_e : nullptr;
   A.leaf_tree = t->d_leaf_tree;
   A.io = t->d_io;
   A.io_net = t->d_io_net;
