@@ -469,12 +469,15 @@ def roofline(ph, precision, kernel_flops, peaks, traffic, variant=0):
     if precision == "mixed" and k == "k_m2l_ref":
         kname = "k_m2l_ref<float> or k_m2l_split<float> + k_m2l_stage (one stream)"
     peak = peaks[bits]
+    how = f"FP{bits} FMA rate"
+    if bits == 32 and peaks.get(-32, 0.0) > peak:  # packed FP32 pairs retire FMAs faster
+        peak, how = peaks[-32], "FP32 FMA rate in packed pairs (fma.rn.f32x2)"
     return {"bound": "alu", "kernel": kname, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": ach / peak, "traffic": traffic.get(kname),
             "traffic_unit": "DRAM bytes per launch (ncu)",
             "kernel_ms": ms[k], "kernel_flops": kernel_flops[k],
             "other_kernel_ms": {kk: v for kk, v in ms.items() if kk != k},
-            "peak_source": f"measured: FP{bits} FMA rate, fmm_measure_fma_rate on this GPU in this "
+            "peak_source": f"measured: {how}, fmm_measure_fma_rate on this GPU in this "
                            "run (2 flops per FMA)",
             "frac_of_nominal": ach / NOMINAL_TFLOPS[bits]}
 
@@ -653,7 +656,7 @@ def run_ours(args):
 
     # roofline denominators, measured on this GPU
     peaks, peak_ms = {}, {}
-    for bits in (64, 32):
+    for bits in (64, 32, -32):  # -32: FP32 in packed pairs
         peaks[bits], peak_ms[bits] = api.measure_fma_rate(bits, 5, stream=stream)
 
     w = big_workload(synth)
@@ -787,8 +790,8 @@ def run_ours(args):
                  "speedup_vs_fp64": t64 / tdf, "err_vs_fp64": errdf,
                  "roofline": roofline(rdf["phases"], "df64", kflops, peaks, traffic),
                  "phases_ms": phases_of(rdf["phases"]), "gpu_launches": rdf["launches"]},
-        "peaks": {"fp64_tflops": peaks[64], "fp32_tflops": peaks[32],
-                  "ms_per_launch": {"fp64": peak_ms[64], "fp32": peak_ms[32]},
+        "peaks": {"fp64_tflops": peaks[64], "fp32_tflops": peaks[32], "fp32x2_tflops": peaks[-32],
+                  "ms_per_launch": {"fp64": peak_ms[64], "fp32": peak_ms[32], "fp32x2": peak_ms[-32]},
                   "nominal_tflops": {"fp64": NOMINAL_TFLOPS[64], "fp32": NOMINAL_TFLOPS[32]},
                   "how": "fmm_measure_fma_rate: 8 independent FMA chains per thread, 2048 threads "
                          "per SM, about 40 ms per launch, fastest of 5"},

@@ -374,8 +374,12 @@ int fmm_scf_iterate(fmm_tree* tree, const fmm_scf_params* params, int n_iter, do
                     double* phi_dev, double* g_dev, double* state_dev, double* history_dev,
                     void* stream);
 
-/* Measured rate of the FP64 (bits = 64) or FP32 (bits = 32) fused multiply-add pipes of the
- * current device, the denominator of the roofline of the interaction kernels (they are bound by
+/* `bits` of fmm_measure_fma_rate for FP32 fused multiply-adds in packed pairs (fma.rn.f32x2, one
+ * instruction per two FMAs, sm_100 and later). */
+#define FMM_FMA_F32X2 (-32)
+
+/* Measured rate of the FP64 (bits = 64) or FP32 (bits = 32; FMM_FMA_F32X2: packed pairs) fused
+ * multiply-add pipes of the current device, the denominator of the roofline of the interaction kernels (they are bound by
  * arithmetic, Sec. 2.2's multipole interactions evaluated pair by pair).  Every thread of a fully
  * occupied grid (8 blocks of 256 threads per SM) runs 8 independent FMA chains; the trip count is
  * calibrated to about 40 ms per launch, and the fastest of `reps` launches, timed with CUDA events

@@ -17,6 +17,7 @@ FMM_ERR_NOMEM = -7
 FMM_ERR_STATE = -8
 FMM_ERR_TIMEOUT = -9
 FMM_ERR_BOUNDS = -10
+FMM_FMA_F32X2 = -32  # fmm_measure_fma_rate: packed FP32 pairs
 FMM_MIXED_VARIANTS = 96
 FMM_NET_STATIC_MAX_POINTS = 2048 * 4096
 FMM_SCF_STATE = 22

@@ -38,7 +38,8 @@ def _scf_params(p: dict):
 
 def measure_fma_rate(bits: int, reps: int = 5, stream=None) -> Tuple[float, float]:
     """fmm_measure_fma_rate: (TFLOP/s of fused multiply-adds at 2 flops each, ms per launch) of the
-    FP64 (bits = 64) or FP32 (bits = 32) pipes of the current device."""
+    FP64 (bits = 64) or FP32 (bits = 32; _lib.FMM_FMA_F32X2: packed pairs, one instruction per
+    two FMAs) pipes of the current device."""
     tf, ms = C.c_double(), C.c_double()
     check(lib().fmm_measure_fma_rate(int(bits), int(reps), C.byref(tf), C.byref(ms),
                                      _stream_handle(stream)))
