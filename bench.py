@@ -238,7 +238,7 @@ def measure_paper_binary(tree_api, synth, torch, dev, stream, steps, flush, grad
     return out
 
 
-def measure_batched(tree_api, synth, torch, dev, stream, steps):
+def measure_batched(tree_api, synth, torch, dev, stream, steps, timer):
     """The 64 seeded trees of uneven depth (levels 2..5, single stars or binaries) as one forest:
     every level of every tree in one set of launches, replayed as one CUDA graph, the mixed path's
     launch variant chosen by the autotuner.  Same metric as the headline."""
@@ -274,6 +274,7 @@ def measure_batched(tree_api, synth, torch, dev, stream, steps):
         out[precision] = {"value": counts["m2l"] / (t * 1e-3), "ms_per_solve": t,
                           "gpu_launches": f.last_launches()}
     out["unit"] = "interactions/s"
+    out["persistent_level_passes"] = persistent_vs_launches(timer, f, [rho], ("fp64", "mixed"), steps)
     f.close()
     for t in trees:
         t.close()
@@ -442,6 +443,25 @@ class Timer:
                 "launches": tree.last_launches() * steps}
 
 
+def persistent_vs_launches(timer, tree, rhos, precisions, steps):
+    """ms per solve with the level passes (upward octant phases, downward level phases) as one
+    launch per phase and as one persistent, level-ordered launch per direction
+    (fmm_set_persistent): the same inputs, flushes and events."""
+    res = {}
+    for precision in precisions:
+        row = {}
+        for name, on in (("per_phase_launches", False), ("persistent", True)):
+            tree.set_persistent(on)
+            r = timer.solves(tree, rhos, THETA, precision, 2, steps, None,
+                             call=lambda x: tree.solve(x, THETA, precision, True, stream=timer.stream,
+                                                       check_status=False))
+            row[name] = {"ms_per_solve": r["total_ms"] / steps, "gpu_launches": tree.last_launches(),
+                         "upward_ms": float(r["phases"][0]), "downward_ms": float(r["phases"][2])}
+        res[precision] = row
+    tree.set_persistent(False)
+    return res
+
+
 def kernel_flops_of(counts, depth):
     kf = {k: sum(FLOPS[c] * counts[c] for c in cs) for k, cs in KERNEL_PAIRS.items()}
     if depth > 0:
@@ -578,8 +598,12 @@ def measure_small(api, synth, torch, timer, dev, steps, peaks, rank):
     net = torch.empty(7, dtype=torch.float64, device=dev)
     out = {"workload": SMALL_WORKLOAD, "subgrids": n_sub, "leaf_cells": n, "m2l_pairs": n_m2l,
            "pair_types": counts, "unit": "interactions/s"}
-    variant, _, _, _ = tree.autotune(rhos[0], THETA, "mixed", reps=3, stream=stream)
+    # tuned in the configuration the timer runs (per-phase events on), which moves kernels a little
+    tree.set_profiling(True)
+    variant, tuned_ms, _, _ = tree.autotune(rhos[0], THETA, "mixed", reps=3, stream=stream)
+    tree.set_profiling(False)
     out["mixed_variant"] = int(variant)
+    out["autotune_median_ms"] = {str(v): round(float(x), 4) for v, x in enumerate(tuned_ms) if x > 0}
     for precision in ("fp64", "mixed", "df64"):
         r = timer.solves(tree, rhos, THETA, precision, 3, steps, (phi, g, net))
         tm = r["total_ms"] / steps
@@ -588,6 +612,13 @@ def measure_small(api, synth, torch, timer, dev, steps, peaks, rank):
                                                variant),
                           "phases_ms": phases_of(r["phases"], precision),
                           "gpu_launches": tree.last_launches()}
+    out["persistent_level_passes"] = persistent_vs_launches(timer, tree, rhos, ("fp64", "mixed"),
+                                                            min(steps, 10))
+    if variant != 0:  # the default launch variant, timed the same way, beside the tuner's choice
+        tree.set_variant(THETA, 0)
+        r = timer.solves(tree, rhos, THETA, "mixed", 3, steps, (phi, g, net))
+        out["mixed"]["ms_per_solve_variant_0"] = r["total_ms"] / steps
+        tree.set_variant(THETA, variant)
     # the mixed path against the FP64 path at the three opening angles (the same input)
     m = leaf_mass(torch, tree, rhos[0])
     sweep = {}
@@ -682,7 +713,10 @@ def run_ours(args):
     traffic = measured_traffic("binary_q0.6_L7")
 
     # the library's autotuner picks the mixed path's launch variant for this tree (untimed)
+    # (tuned with the per-phase events on, as the timed solves run)
+    tree.set_profiling(True)
     tuned_variant, tuned_ms, _, _ = tree.autotune(rhos[0], THETA, "mixed", reps=3, stream=stream)
+    tree.set_profiling(False)
     sampler = ClockSampler(uuid) if (uuid and rank == 0) else None
     r64 = timer.solves(tree, rhos, THETA, "fp64", args.warmup, args.steps, (phi, g, net))
     phi64, g64, net64 = phi.clone(), g.clone(), net.clone()
@@ -694,6 +728,7 @@ def run_ours(args):
     tree.set_graphs(False)
     r32d = timer.solves(tree, rhos, THETA, "mixed", 1, min(args.steps, 5), (phi, g, net))
     tree.set_graphs(True)
+    pers = persistent_vs_launches(timer, tree, rhos, ("fp64", "mixed"), min(args.steps, 5))
     clocks = sampler.stop() if sampler else None
 
     # end to end through the C ABI with pinned host buffers, copies inside the timed region: every
@@ -729,7 +764,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
 
     small = measure_small(api, synth, torch, timer, dev, min(args.steps, 10), peaks, rank)
-    batched = measure_batched(api, synth, torch, dev, stream, min(args.steps, 3))
+    batched = measure_batched(api, synth, torch, dev, stream, min(args.steps, 3), timer)
     paper = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), timer.flush)
     graded = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), timer.flush,
                                   graded=True)
@@ -801,6 +836,7 @@ def run_ours(args):
                 "api": "fmm_solve_host_async (pinned host buffers, steps pipelined), wall clock",
                 "synchronous_fmm_solve_host_ms_per_step": 1e3 * e2e_sync_s},
         "gpu_launches": r64["launches"],
+        "persistent_level_passes": pers,
         "small": small,
         "batched": batched,
         "paper_binary": paper,

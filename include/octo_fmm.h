@@ -262,13 +262,25 @@ int fmm_autotune(fmm_tree* tree, const double* rho_dev, double theta, int precis
 /* Mixed-precision refined targets stage their partners' moments in shared memory with bulk
  * asynchronous copies; each wait for a parity class's copies gives up after `cycles` SM clock
  * cycles (0, the default: 2^31, about a second), records FMM_ERR_TIMEOUT in the status word and
- * leaves that subgrid's expansions unset.  A small limit exercises this path; the solve's
+ * leaves that subgrid's expansions unset.  The same limit bounds each grid-barrier wait of the
+ * persistent level passes (fmm_set_persistent).  A small limit exercises this path; the solve's
  * results are then invalid.  FMM_ERR_ARG for a negative limit. */
 int fmm_set_wait_limit(fmm_tree* tree, long long cycles);
 
 /* on != 0 (the default): replay one captured CUDA graph per solve configuration; on == 0:
  * enqueue the kernels one by one on every call.  The results are the same bit for bit. */
 int fmm_set_graphs(fmm_tree* tree, int on);
+
+/* Level passes of the rho solve (Sec. 2.2's upward M2M after P2M -- the octants with leaf
+ * children, then those with refined children level by level -- and the downward pass below the
+ * root -- the refined subgrids level by level, then every leaf octant): on == 0 (the default),
+ * one launch per phase; on != 0, one persistent, level-ordered cooperative launch per direction,
+ * whose resident blocks take each phase's work items in turn and meet at a grid-wide barrier
+ * between phases (part of the graph key).  Each barrier wait is bounded by the fmm_set_wait_limit
+ * limit; a wait that runs out records FMM_ERR_TIMEOUT (fmm_sync_status) and the launch leaves
+ * its remaining phases undone.  The results are the same bit for bit.  The time-derivative
+ * solve's source pass keeps its per-phase launches.  FMM_ERR_ARG for a null tree. */
+int fmm_set_persistent(fmm_tree* tree, int on);
 
 /* Per-phase device times (ms) of the most recent solve on this tree, measured with CUDA events
  * when profiling is on: [0] upward pass, [1] interactions after the upward pass, [2] downward

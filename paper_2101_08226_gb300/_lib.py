@@ -28,7 +28,7 @@ FMM_DF64 = 2
 EXPORTS = [
     "fmm_build_tree", "fmm_destroy", "fmm_build_forest", "fmm_forest_info", "fmm_solve_batch", "fmm_tree_info", "fmm_tree_subgrids", "fmm_stencil",
     "fmm_interaction_counts", "fmm_interaction_counts_by_type", "fmm_last_launches", "fmm_solve", "fmm_solve_dt", "fmm_sync_status", "fmm_solve_host", "fmm_solve_host_async",
-    "fmm_net_force_torque", "fmm_net_force_torque_points_static", "fmm_set_profiling", "fmm_set_graphs", "fmm_set_wait_limit", "fmm_set_variant", "fmm_autotune", "fmm_binary_diagnostics", "fmm_binary_iterate", "fmm_phase_times", "fmm_measure_fma_rate", "fmm_scf_init", "fmm_scf_iterate", "fmm_partition", "fmm_ghosts", "fmm_last_error",
+    "fmm_net_force_torque", "fmm_net_force_torque_points_static", "fmm_set_profiling", "fmm_set_graphs", "fmm_set_persistent", "fmm_set_wait_limit", "fmm_set_variant", "fmm_autotune", "fmm_binary_diagnostics", "fmm_binary_iterate", "fmm_phase_times", "fmm_measure_fma_rate", "fmm_scf_init", "fmm_scf_iterate", "fmm_partition", "fmm_ghosts", "fmm_last_error",
 ]
 
 _lib = None
@@ -76,6 +76,7 @@ def load(path: str):
         "fmm_net_force_torque_points_static": (i32, [i64, vp, vp, vp, vp, vp]),
         "fmm_set_profiling": (i32, [vp, i32]),
         "fmm_set_graphs": (i32, [vp, i32]),
+        "fmm_set_persistent": (i32, [vp, i32]),
         "fmm_set_wait_limit": (i32, [vp, C.c_longlong]),
         "fmm_set_variant": (i32, [vp, dbl, i32]),
         "fmm_autotune": (i32, [vp, vp, dbl, i32, i32, vp, vp, i32, vp, vp, vp]),

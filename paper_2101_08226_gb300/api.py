@@ -288,6 +288,11 @@ class Tree:
         kernels one by one."""
         check(lib().fmm_set_graphs(self._h, int(bool(on))))
 
+    def set_persistent(self, on: bool = True):
+        """Level passes as one persistent, level-ordered launch per direction, or one launch per
+        phase (the default) (fmm_set_persistent)."""
+        check(lib().fmm_set_persistent(self._h, int(bool(on))))
+
     def set_variant(self, theta: float, variant: int):
         """Launch variant of the mixed path for this tree and theta (fmm_set_variant)."""
         check(lib().fmm_set_variant(self._h, float(theta), int(variant)))

@@ -2049,16 +2049,17 @@ __global__ void k_root_total(DevArgs A) {
 //              + w^2 sum_(a<b) s_a s_b L2_ab + w^3 s_x s_y s_z L3_xyz,
 //   dphi/dr_a (s w) = [L1_a + w^2 t_a / 2] + w sum_b s_b L2_ab + w^2 sum_(b<c) s_b s_c L3_abc,
 // each evaluated at all 8 children by an inverse 8-point Walsh-Hadamard transform.
+// One 64-thread work item of the downward pass (blk: the item's index, blockIdx.x of k_down).
 template <bool MIXED, bool SRC>
-__global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* __restrict__ ref,
-                                             int n_ref_blocks, const int32_t* __restrict__ octs) {
+__device__ __forceinline__ void down_item(const DevArgs& A, int lev, const int32_t* __restrict__ ref,
+                                          int n_ref_blocks, const int32_t* __restrict__ octs, int blk) {
   using T = typename Down<MIXED>::T;
   using D = Down<MIXED, SRC>;
   const int64_t N = A.n_cell;
-  if (int(blockIdx.x) < n_ref_blocks) {
-    const int32_t s = ref[blockIdx.x >> 3];
+  if (blk < n_ref_blocks) {
+    const int32_t s = ref[blk >> 3];
     if (FMM_BAD(A, s >= 0 && int64_t(s) * kCells < N && A.parent[s] >= 0)) return;
-    const int loc = int(blockIdx.x & 7) * 64 + int(threadIdx.x);
+    const int loc = (blk & 7) * 64 + int(threadIdx.x);
     const int64_t i = int64_t(s) * kCells + loc;
     const int32_t Pn = A.parent[s];
     int a, b, c;
@@ -2087,7 +2088,7 @@ __global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* 
     A.ac[2 * N + i] += A.ac[2 * N + ip];
     return;
   }
-  const int32_t code = octs[blockIdx.x - n_ref_blocks];
+  const int32_t code = octs[blk - n_ref_blocks];
   const int32_t Pn = code >> 3;
   const int o = code & 7, u = int(threadIdx.x);
   if (FMM_BAD(A, Pn >= 0 && int64_t(Pn) * kCells < N && A.child[8 * Pn + o] >= 0 &&
@@ -2184,6 +2185,77 @@ __global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* 
     const double ax = A.ac[i] + apx, ay = A.ac[N + i] + apy, az = A.ac[2 * N + i] + apz;
     store_leaf(A, s, 2 * (pa & 3) + ((e >> 2) & 1), 2 * (pb & 3) + ((e >> 1) & 1), 2 * (pc & 3) + (e & 1),
                double(phi), -double(l1x) + ax, -double(l1y) + ay, -double(l1z) + az);
+  }
+}
+template <bool MIXED, bool SRC>
+__global__ void __launch_bounds__(64) k_down(DevArgs A, int lev, const int32_t* __restrict__ ref,
+                                             int n_ref_blocks, const int32_t* __restrict__ octs) {
+  down_item<MIXED, SRC>(A, lev, ref, n_ref_blocks, octs, int(blockIdx.x));
+}
+
+// ----------------------------------------------------------------------------------------------
+// the level passes as one persistent launch per direction
+// ----------------------------------------------------------------------------------------------
+// The upward pass after P2M (the octants with leaf children, then the octants with refined
+// children level by level, finest first) and the downward pass below the root (the refined
+// subgrids level by level, then every leaf octant) are sequences of phases, each of which needs
+// the one before it complete on the whole tree.  Instead of one launch per phase, k_levels runs
+// a whole sequence in one cooperative launch whose blocks stay resident: block b takes the
+// phase's 64-thread work items b, b + gridDim.x, ..., and the blocks meet at a grid-wide barrier
+// between phases.  The items are the same device functions as those of k_m2m and k_down, so the
+// results are the same bit for bit.
+constexpr int kMaxPhases = 40;
+struct LevelPlan {
+  int n;                               // phases
+  int kind[kMaxPhases];                // 0 m2m_walsh, 1 m2m_lanes, 2 down (refined), 3 down (leaf octants)
+  int lev[kMaxPhases];                 // kind 2: the level
+  int items[kMaxPhases];               // 64-thread work items of the phase
+  const int32_t* list[kMaxPhases];     // its octant or subgrid list
+};
+
+// Grid-wide barrier of a cooperative launch (all blocks resident): every block arrives with one
+// atomic add on bar[0]; the last to arrive resets it and starts the next generation (bar[1]); the
+// others wait for that for at most `limit` SM cycles.  The fences around the arrival make each
+// block's writes before the barrier visible to every block after it.  False on time-out.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, long long limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;  // read before arriving: the generation cannot move until we have
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+      ok = 1;
+    } else {
+      const long long t0 = clock64();
+      bool done = false;
+      while (!(done = *gen != g) && clock64() - t0 <= limit) __nanosleep(32);
+      ok = done ? 1 : 0;
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(64) k_levels(DevArgs A, LevelPlan P, int mode, unsigned* bar) {
+  for (int p = 0; p < P.n; ++p) {
+    if (p > 0 && !grid_barrier(bar, A.wait_cycles)) {
+      if (threadIdx.x == 0) atomicOr(A.status, 16);  // FMM_ERR_TIMEOUT; the other blocks time out too
+      return;
+    }
+    const int n = P.items[p], kind = P.kind[p];
+    const int32_t* list = P.list[p];
+    for (int b = int(blockIdx.x); b < n; b += int(gridDim.x)) {
+      if (kind == 0) m2m_walsh(A, list, b, mode);
+      else if (kind == 1) m2m_lanes(A, list, b, mode);
+      else if (kind == 2) down_item<MIXED, false>(A, P.lev[p], list, n, nullptr, b);
+      else down_item<MIXED, false>(A, 0, nullptr, 0, list, b);
+    }
   }
 }
 
@@ -2919,6 +2991,9 @@ struct fmm_tree {
   double *d_mom = nullptr, *d_mtl = nullptr, *d_loc = nullptr, *d_ac = nullptr, *d_root_part = nullptr,
          *d_root_part_ac = nullptr, *d_partials = nullptr;
   unsigned* d_net_count = nullptr;  // k_net_partial's finished-block counters, one per tree
+  unsigned* d_bar = nullptr;        // k_levels' grid barrier: arrivals, generation
+  int persistent = 0;               // level passes as persistent launches (fmm_set_persistent)
+  int levels_cap[2] = {0, 0};       // co-resident blocks of k_levels<false>, k_levels<true>
   float *d_mom32 = nullptr, *d_m32 = nullptr, *d_loc32 = nullptr, *d_root_part32 = nullptr;
   int* d_status = nullptr;
   int64_t* d_tree_leaf_off = nullptr;
@@ -2975,7 +3050,7 @@ struct fmm_tree {
     int32_t launches = 0;
   };
   // one instantiated graph per (theta, precision, correction, net output, profiling, dphi/dt)
-  std::map<std::tuple<double, int, int, int, int, int, long long, int>, Graph> graphs;
+  std::map<std::tuple<double, int, int, int, int, int, long long, int, int>, Graph> graphs;
 };
 
 // blocks per tree of the net reduction: about 512 in all
@@ -3089,6 +3164,7 @@ static int ensure_device(fmm_tree* t) {
   CUDA_TRY(dalloc(t, &t->d_root_part, sizeof(double) * nr * kRootChunks * 23 * kCells));
   CUDA_TRY(dalloc(t, &t->d_partials, sizeof(double) * 7 * net_blocks(nr) * nr));
   CUDA_TRY(dalloc(t, &t->d_net_count, sizeof(unsigned) * size_t(nr)));
+  CUDA_TRY(dalloc(t, &t->d_bar, sizeof(unsigned) * 2));
   CUDA_TRY(cudaMemset(t->d_net_count, 0, sizeof(unsigned) * size_t(nr)));
   CUDA_TRY(upload(t, &t->d_tree_leaf_off, h.tree_leaf_off));
   CUDA_TRY(dalloc(t, &t->d_status, sizeof(int)));
@@ -3657,6 +3733,54 @@ static int launch_down(fmm_tree* t, const DevArgs& A, bool mixed, cudaStream_t s
   return FMM_OK;
 }
 
+// The level passes of one direction as one cooperative launch of k_levels (fmm_set_persistent):
+// a grid of at most the blocks that fit on the device at once, and never more than the largest
+// phase has items.  The barrier words are cleared before every launch, so a launch that timed out
+// leaves nothing behind.
+static int launch_levels(fmm_tree* t, const DevArgs& A, const LevelPlan& P, bool mixed, int mode,
+                         int prio, cudaStream_t st, int32_t* nl) {
+  if (P.n == 0) return FMM_OK;
+  int& cap = t->levels_cap[mixed ? 1 : 0];
+  if (cap == 0) {
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (mixed) CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels<true>, 64, 0));
+    else CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_levels<false>, 64, 0));
+    if (!coop || per_sm < 1) return fail(FMM_ERR_CUDA, "persistent level passes: no cooperative launch");
+    cap = per_sm * sms;
+  }
+  int most = 1;
+  for (int p = 0; p < P.n; ++p) most = std::max(most, P.items[p]);
+  CUDA_TRY(cudaMemsetAsync(t->d_bar, 0, 2 * sizeof(unsigned), st));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(std::min(cap, most)));
+  cfg.blockDim = dim3(64);
+  cfg.stream = st;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = prio;
+  at[1].id = cudaLaunchAttributeCooperative;
+  at[1].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
+  if (mixed) CUDA_TRY(cudaLaunchKernelEx(&cfg, k_levels<true>, A, P, mode, t->d_bar));
+  else CUDA_TRY(cudaLaunchKernelEx(&cfg, k_levels<false>, A, P, mode, t->d_bar));
+  ++*nl;
+  return FMM_OK;
+}
+static bool add_phase(LevelPlan& P, int kind, int lev, int64_t items, const int32_t* list) {
+  if (items <= 0) return true;
+  if (P.n == kMaxPhases || items > INT32_MAX) return false;
+  P.kind[P.n] = kind;
+  P.lev[P.n] = lev;
+  P.items[P.n] = int(items);
+  P.list[P.n] = list;
+  ++P.n;
+  return true;
+}
+
 // All launches of one solve, in order, on stream st (which may be capturing).
 static int enqueue_src(fmm_tree* t, const StencilDev* sd, bool mixed, cudaStream_t st, int32_t* nl);
 
@@ -3706,14 +3830,25 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   };
   if (v_place == 0 && (rc = launch_leaf())) return rc;
   // octants whose children are leaves need only the leaf masses: every level's in one launch;
-  // then the octants with refined children, finest level first
+  // then the octants with refined children, finest level first (or all of it in one persistent
+  // launch)
   const int64_t n_walsh = t->oct_leaf_off[h.depth + 1];
-  if (n_walsh > 0) {
+  LevelPlan up = {}, down = {};
+  bool persistent = t->persistent != 0 && add_phase(up, 0, 0, n_walsh, t->d_oct_leaf);
+  for (int l = h.depth - 1; persistent && l >= 0; --l)
+    persistent = add_phase(up, 1, l, (t->oct_ref_off[l + 1] - t->oct_ref_off[l]) * 8,
+                           t->d_oct_ref + t->oct_ref_off[l]);
+  for (int l = 1; persistent && l <= h.depth; ++l)
+    persistent = add_phase(down, 2, l, (t->ref_off[l + 1] - t->ref_off[l]) * 8, t->d_ref_sub + t->ref_off[l]);
+  persistent = persistent && add_phase(down, 3, 0, t->oct_leaf_off[h.depth + 1], t->d_oct_leaf);
+  if (persistent) {
+    if ((rc = launch_levels(t, A, up, mixed, mode, t->prio_high, st, &nl))) return rc;
+  } else if (n_walsh > 0) {
     CUDA_TRY(launch_prio(t->prio_high, k_m2m, dim3(unsigned(n_walsh)), dim3(kM2MThreads), 0, st, A,
                          (const int32_t*)t->d_oct_leaf, int(n_walsh), (const int32_t*)nullptr, mode));
     ++nl;
   }
-  for (int l = h.depth - 1; l >= 0; --l) {
+  for (int l = h.depth - 1; !persistent && l >= 0; --l) {
     const int64_t nr_oct = t->oct_ref_off[l + 1] - t->oct_ref_off[l];
     if (nr_oct > 0) {
       CUDA_TRY(launch_prio(t->prio_high, k_m2m, dim3(unsigned(nr_oct * 8)), dim3(kM2MThreads), 0, st, A,
@@ -3786,7 +3921,11 @@ static int enqueue_solve(fmm_tree* t, const StencilDev* sd, int mode, int amc, b
   else k_root_total<false, false><<<blocks_for(int64_t(h.n_trees) * kRootComps * kCells, 128), 128, 0, st>>>(A);
   CUDA_TRY(cudaGetLastError());
   ++nl;
-  if ((rc = launch_down<false>(t, A, mixed, st, &nl))) return rc;
+  if (persistent) {
+    if ((rc = launch_levels(t, A, down, mixed, mode, 0, st, &nl))) return rc;
+  } else if ((rc = launch_down<false>(t, A, mixed, st, &nl))) {
+    return rc;
+  }
   if ((rc = record(t, 3, st))) return rc;
   if (net) {
     if ((rc = launch_net(t, A, st))) return rc;
@@ -3911,7 +4050,8 @@ static int solve_impl(fmm_tree* t, const std::vector<TreeIo>& io, double theta, 
   fmm_tree::Graph* gr = nullptr;
   if (t->use_graphs) {
     auto key = std::make_tuple(theta, precision, amc, net ? 1 : 0, t->profiling ? 1 : 0, src ? 1 : 0,
-                               t->wait_cycles, precision == FMM_MIXED ? sd->mixed_variant : 0);
+                               t->wait_cycles, precision == FMM_MIXED ? sd->mixed_variant : 0,
+                               t->persistent);
     auto it = t->graphs.find(key);
     if (it == t->graphs.end()) {
       fmm_tree::Graph fresh;
@@ -4267,6 +4407,7 @@ int fmm_sync_status(fmm_tree* t, void* stream) {
   if (status & 2) return fail(FMM_ERR_NONFINITE, "a density time derivative was NaN or infinite");
   if (status & 4) return fail(FMM_ERR_TIMEOUT, "a shared-memory staging wait timed out");
   if (status & 8) return fail(FMM_ERR_BOUNDS, "an index check of the bounds-checked build failed");
+  if (status & 16) return fail(FMM_ERR_TIMEOUT, "a grid barrier of a persistent level pass timed out");
   return FMM_OK;
 }
 
@@ -4458,6 +4599,12 @@ int fmm_set_variant(fmm_tree* t, double theta, int variant) {
     return fail(FMM_ERR_NOMEM, "host allocation failed");
   }
   sd->mixed_variant = variant;
+  return FMM_OK;
+}
+
+int fmm_set_persistent(fmm_tree* t, int on) {
+  if (!t) return fail(FMM_ERR_ARG, "tree is null");
+  t->persistent = on ? 1 : 0;
   return FMM_OK;
 }
 

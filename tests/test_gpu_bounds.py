@@ -3,7 +3,7 @@ kernels read from the library's tables (neighbours, children, leaf ordinals, wor
 lists, stencil and staging tables) is range-checked before the access it leads to, and a failed
 check is reported as FMM_ERR_BOUNDS instead of being made.  On valid trees no check may fire: the
 solves of every precision, every mixed launch variant, the time-derivative solve and a forest
-report FMM_OK and give the normal build's results."""
+report FMM_OK and give the normal build's results; so do the persistent level passes."""
 import ctypes as C
 
 import numpy as np
@@ -46,8 +46,9 @@ def _tree(L, max_level, flags):
     return h
 
 
-def _solve(L, h, rho, theta, precision, variant=None, rhodot=None):
+def _solve(L, h, rho, theta, precision, variant=None, rhodot=None, persistent=False):
     n = rho.numel()
+    assert L.fmm_set_persistent(h, int(persistent)) == 0
     phi = torch.empty(n, dtype=torch.float64, device="cuda")
     g = torch.empty((n, 3), dtype=torch.float64, device="cuda")
     net = torch.empty(7, dtype=torch.float64, device="cuda")
@@ -78,13 +79,14 @@ def test_no_check_fires_and_results_agree(checked, case):
         leaves = api.Tree(max_level, flags).leaves()
         rho = torch.from_numpy(synth.leaf_density(fld, leaves)).cuda()
         rhodot = rho * torch.from_numpy(np.random.default_rng(2).uniform(-1, 1, rho.numel())).cuda()
-        runs = [(p, th, None, None) for p in ("fp64", "df64", "mixed") for th in (0.34, 0.5, 0.7)]
+        runs = [(p, th, None, None, False) for p in ("fp64", "df64", "mixed") for th in (0.34, 0.5, 0.7)]
         variants = range(_lib.FMM_MIXED_VARIANTS) if case == "tiny_amr" else range(0, _lib.FMM_MIXED_VARIANTS, 7)
-        runs += [("mixed", 0.5, v, None) for v in variants]
-        runs += [("fp64", 0.5, None, rhodot), ("mixed", 0.5, None, rhodot)]
-        for precision, theta, variant, rd in runs:
-            got = _solve(checked, hc, rho, theta, precision, variant, rd)
-            ref = _solve(plain, hp, rho, theta, precision, variant, rd)
+        runs += [("mixed", 0.5, v, None, False) for v in variants]
+        runs += [("fp64", 0.5, None, rhodot, False), ("mixed", 0.5, None, rhodot, False)]
+        runs += [(p, 0.5, None, None, True) for p in ("fp64", "df64", "mixed")]  # persistent level passes
+        for precision, theta, variant, rd, pers in runs:
+            got = _solve(checked, hc, rho, theta, precision, variant, rd, pers)
+            ref = _solve(plain, hp, rho, theta, precision, variant, rd, pers)
             for a, b in zip(got, ref):
                 assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), (precision, theta, variant)
     finally:
