@@ -195,6 +195,11 @@ __device__ __forceinline__ double dyadic(int n, int k) {
   const uint64_t bits = (uint64_t(n < 0) << 63) | (uint64_t(1023 + e - k) << 52) | mant;
   return __longlong_as_double(int64_t(bits));
 }
+// A value as a double: exact either way; a float is widened with
+// integer operations (a float-to-double conversion runs on the FP64 pipe).
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return df_f2d(x); }
+
 template <typename T>
 __device__ __forceinline__ T cell_h(int lev);
 template <>
@@ -242,7 +247,7 @@ __global__ void k_p2m(DevArgs A, int mixed) {
   // the other 19 moments of a leaf cell stay zero from the workspace initialisation
   const double m = r * cell_vol(lev);
   A.mom[cell] = m;
-  A.mtl[cell] = m;
+  if (mixed == 0) A.mtl[cell] = m;  // the FP64 detraced set is read by the FP64 path only
   if (mixed == 1) {
     A.mom32[cell * 20] = float(m);
     A.m32[cell] = float(m);
@@ -255,8 +260,9 @@ __global__ void k_p2m(DevArgs A, int mixed) {
 // ----------------------------------------------------------------------------------------------
 // m2m: moments of a refined cell from its 8 children (exact shift to the parent's centre of mass)
 // ----------------------------------------------------------------------------------------------
-// Writes the moments of one refined cell: raw (m, delta, M2, M3), detraced, and the FP32 copy of
-// the detraced set (mixed path).
+// Writes the moments of one refined cell: raw (m, delta, M2, M3) in FP64, and the detraced set
+// its path's interactions read: FP64 (mtl), the FP32 copy (mixed path: detraced in FP32 from the
+// FP64 moments; its pair arithmetic is FP32) or the double-float copy (df64 path).
 __device__ __forceinline__ void store_moments(const DevArgs& A, int64_t cell, double mt, double dx,
                                               double dy, double dz, const double* M2,
                                               const double* M3, int mixed) {
@@ -269,21 +275,34 @@ __device__ __forceinline__ void store_moments(const DevArgs& A, int64_t cell, do
   for (int k = 0; k < 6; ++k) A.mom[(4 + k) * N + cell] = M2[k];
 #pragma unroll
   for (int k = 0; k < 10; ++k) A.mom[(10 + k) * N + cell] = M3[k];
+  if (mixed == 1) {
+    float q[6], p[10];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q[k] = float(M2[k]);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) p[k] = float(M3[k]);
+    const float tr3 = (q[0] + q[3] + q[5]) * (1.0f / 3.0f);
+    const float tx = (p[0] + p[3] + p[5]) * 0.2f, ty = (p[1] + p[6] + p[8]) * 0.2f,
+                tz = (p[2] + p[7] + p[9]) * 0.2f;
+    float4* o = reinterpret_cast<float4*>(A.mom32 + cell * 20);
+    o[0] = make_float4(float(mt), float(dx), float(dy), float(dz));
+    o[1] = make_float4(q[0] - tr3, q[1], q[2], q[3] - tr3);
+    o[2] = make_float4(q[4], q[5] - tr3, p[0] - 3.0f * tx, p[1] - ty);
+    o[3] = make_float4(p[2] - tz, p[3] - tx, p[4], p[5] - tx);
+    o[4] = make_float4(p[6] - 3.0f * ty, p[7] - tz, p[8] - ty, p[9] - 3.0f * tz);
+    A.m32[cell] = float(mt);
+    return;
+  }
   const double tr3 = (M2[0] + M2[3] + M2[5]) * (1.0 / 3.0);
   const double tx = (M3[0] + M3[3] + M3[5]) * 0.2, ty = (M3[1] + M3[6] + M3[8]) * 0.2,
                tz = (M3[2] + M3[7] + M3[9]) * 0.2;
   const double T[20] = {mt, dx, dy, dz, M2[0] - tr3, M2[1], M2[2], M2[3] - tr3, M2[4],
                         M2[5] - tr3, M3[0] - 3 * tx, M3[1] - ty, M3[2] - tz, M3[3] - tx, M3[4],
                         M3[5] - tx, M3[6] - 3 * ty, M3[7] - tz, M3[8] - ty, M3[9] - 3 * tz};
+  if (mixed == 0) {
 #pragma unroll
-  for (int k = 0; k < 20; ++k) A.mtl[k * N + cell] = T[k];
-  if (mixed == 1) {
-#pragma unroll
-    for (int q = 0; q < 5; ++q)
-      reinterpret_cast<float4*>(A.mom32 + cell * 20)[q] =
-          make_float4(float(T[4 * q]), float(T[4 * q + 1]), float(T[4 * q + 2]), float(T[4 * q + 3]));
-    A.m32[cell] = float(mt);
-  } else if (mixed == 2) {
+    for (int k = 0; k < 20; ++k) A.mtl[k * N + cell] = T[k];
+  } else {
 #pragma unroll
     for (int q = 0; q < 10; ++q) {
       const dfloat u = df_from_double(T[2 * q]), v = df_from_double(T[2 * q + 1]);
@@ -808,9 +827,15 @@ __device__ __forceinline__ void finish_rr(Target<T, true>& S) {
 // pair terms in FP32 before each flush).
 template <typename T, bool AREF>
 __device__ __forceinline__ void flush(Target<T, AREF>& S) {
-  S.ax += double(S.px);
-  S.ay += double(S.py);
-  S.az += double(S.pz);
+  if constexpr (std::is_same<T, float>::value) {
+    S.ax += to_f64(S.px);
+    S.ay += to_f64(S.py);
+    S.az += to_f64(S.pz);
+  } else {
+    S.ax += double(S.px);
+    S.ay += double(S.py);
+    S.az += double(S.pz);
+  }
   S.px = S.py = S.pz = T(0);
 }
 
@@ -2135,7 +2160,7 @@ __device__ __forceinline__ void down_item(const DevArgs& A, int lev, const int32
 #pragma unroll
     for (int e = 0; e < 8; ++e)
       store_leaf_dt(A, s, 2 * (pa & 3) + ((e >> 2) & 1), 2 * (pb & 3) + ((e >> 1) & 1),
-                    2 * (pc & 3) + (e & 1), double(D::ld(A, 0, c0 + (e << 6)) + f[e]));
+                    2 * (pc & 3) + (e & 1), to_f64(D::ld(A, 0, c0 + (e << 6)) + f[e]));
     return;
   }
   gxv[0] = L[1] + T(0.5) * w2 * tx;
@@ -2184,7 +2209,7 @@ __device__ __forceinline__ void down_item(const DevArgs& A, int lev, const int32
             l1z = D::ld(A, 3, i) + gzv[e];
     const double ax = A.ac[i] + apx, ay = A.ac[N + i] + apy, az = A.ac[2 * N + i] + apz;
     store_leaf(A, s, 2 * (pa & 3) + ((e >> 2) & 1), 2 * (pb & 3) + ((e >> 1) & 1), 2 * (pc & 3) + (e & 1),
-               double(phi), -double(l1x) + ax, -double(l1y) + ay, -double(l1z) + az);
+               to_f64(phi), ax - to_f64(l1x), ay - to_f64(l1y), az - to_f64(l1z));
   }
 }
 template <bool MIXED, bool SRC>
