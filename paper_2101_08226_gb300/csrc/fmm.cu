@@ -2295,11 +2295,16 @@ __global__ void __launch_bounds__(64) k_levels(DevArgs A, LevelPlan P, int mode,
 
 // index of (a, b) in the 6 stored components of a symmetric 2-tensor (xx xy xz yy yz zz)
 __host__ __device__ constexpr int sym2_index(int a, int b) {
-  return a > b ? sym2_index(b, a) : (a == 0 ? b : (a == 1 ? 2 + b : 5));
+  return (a < b ? a : b) == 0 ? (a < b ? b : a) : ((a < b ? a : b) == 1 ? 2 + (a < b ? b : a) : 5);
 }
-// the (a <= b <= c) triples of the 10 stored components of a symmetric 3-tensor
-__device__ constexpr int kSym3[10][3] = {{0, 0, 0}, {0, 0, 1}, {0, 0, 2}, {0, 1, 1}, {0, 1, 2},
-                                         {0, 2, 2}, {1, 1, 1}, {1, 1, 2}, {1, 2, 2}, {2, 2, 2}};
+// axis j (0..2) of the (a <= b <= c) triple of stored component k (0..9) of a symmetric
+// 3-tensor (xxx xxy xxz xyy xyz xzz yyy yyz yzz zzz); a function rather than a device table, so
+// that in unrolled loops the indices are compile-time constants and the operands stay in
+// registers
+__host__ __device__ constexpr int sym3_axis(int k, int j) {
+  // component k's triple as the base-3 number 9 a + 3 b + c, six bits per component
+  return int((0x69138d205102040ull >> (6 * k)) & 63u) / (j == 0 ? 9 : (j == 1 ? 3 : 1)) % 3;
+}
 
 // Exact shift of raw source moments c about X_c to the point X_c - r (r = X_c - X_new), added
 // onto S:  S0 += c0,  S1 += c1 + c0 r,  S2 += c2 + r c1 + c1 r + c0 r r,
@@ -2316,7 +2321,7 @@ __device__ __forceinline__ void src_shift_add(const double* c, const double* r, 
                                  c[0] * r[a] * r[b];
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
-    const int a = kSym3[k][0], b = kSym3[k][1], cc = kSym3[k][2];
+    const int a = sym3_axis(k, 0), b = sym3_axis(k, 1), cc = sym3_axis(k, 2);
     S[10 + k] += c[10 + k] + r[a] * c[4 + sym2_index(b, cc)] + r[b] * c[4 + sym2_index(a, cc)] +
                  r[cc] * c[4 + sym2_index(a, b)] + r[a] * r[b] * c[1 + cc] + r[a] * r[cc] * c[1 + b] +
                  r[b] * r[cc] * c[1 + a] + c[0] * r[a] * r[b] * r[cc];
@@ -2426,7 +2431,7 @@ __global__ void __launch_bounds__(64) k_m2m_src(DevArgs A, const int32_t* __rest
         S[4 + sym2_index(p, q)] = P2[sym2_index(p, q)] - d[p] * P1[q] - d[q] * P1[p] + S0 * d[p] * d[q];
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
-      const int p = kSym3[k][0], q = kSym3[k][1], r = kSym3[k][2];
+      const int p = sym3_axis(k, 0), q = sym3_axis(k, 1), r = sym3_axis(k, 2);
       S[10 + k] = P3[k] - (d[p] * P2[sym2_index(q, r)] + d[q] * P2[sym2_index(p, r)] +
                            d[r] * P2[sym2_index(p, q)]) +
                   (d[p] * d[q] * P1[r] + d[p] * d[r] * P1[q] + d[q] * d[r] * P1[p]) -
