@@ -616,20 +616,20 @@ struct Target {
   bool amc;
 };
 
-// Interaction of target A with one source cell B (same level) at separation R = X_A - X_B; BREF:
-// B is refined (full moments), else a point mass.
+// Interaction of target A with one source cell B (same level) at separation
+// R = X_A - X_B = (delta_A - delta_B) + o, with o = (o_x, o_y, o_z) the exact offset of A's cell
+// centre from B's (an integer multiple of the cell width); BREF: B is refined (full moments),
+// else a point mass.
 template <typename T, bool AREF, bool BREF>
 __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict__ M, int64_t N,
-                                         int64_t iB, T x, T y, T z) {
+                                         int64_t iB, T ox, T oy, T oz) {
   T mB;
   Radial<T> g;
   if constexpr (BREF) {
     T Mv[20];
     mom_load20(M, N, iB, Mv);
     mB = Mv[0];
-    x -= Mv[1];
-    y -= Mv[2];
-    z -= Mv[3];
+    const T x = (S.dAx - Mv[1]) + ox, y = (S.dAy - Mv[2]) + oy, z = (S.dAz - Mv[3]) + oz;
     const T* M2 = Mv + 4;
     const T* M3 = Mv + 10;
     g.set(x, y, z, 4);
@@ -661,6 +661,7 @@ __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict
     }
   } else {
     mB = mom_get(M, N, iB, 0);
+    const T x = S.dAx + ox, y = S.dAy + oy, z = S.dAz + oz;
     g.set(x, y, z, AREF ? 4 : 1);
     m2l_mono<T>(x, y, z, g, mB, S.L);
     if constexpr (AREF) {
@@ -685,12 +686,15 @@ __device__ __forceinline__ void interact(Target<T, AREF>& S, const T* __restrict
 // "L -= a b + c d" on its own: the same expansion and correction as interact<T, true, true>.
 // M3'(R,R) uses the tracelessness of the stored M3' (T_xzz = -T_xxx - T_xyy, ...) on the shared
 // monomials xx - zz, yy - zz, 2xy, 2xz, 2yz; the correction's Q(R,R,R) is contracted directly.
+// The partner lies at offset d (in cells, ex ey ez) from the target, cell width h:
+// R = X_A - X_B = (delta_A - delta_B) - d h.  The centre-of-mass offsets' difference is rounded
+// once and d h is exact, so R of the pair (B, A) is exactly -R in any precision: both halves of
+// a pair see the same |R| and opposite directions, and FP32 rounding of R leaves no systematic
+// net force.
 template <typename T>
-__device__ __forceinline__ void interact_rr_v(Target<T, true>& S, const T* Mv, T x, T y, T z) {
+__device__ __forceinline__ void interact_rr_v(Target<T, true>& S, const T* Mv, T ex, T ey, T ez, T h) {
   const T mB = Mv[0];
-  x -= Mv[1];
-  y -= Mv[2];
-  z -= Mv[3];
+  const T x = (S.dAx - Mv[1]) - ex * h, y = (S.dAy - Mv[2]) - ey * h, z = (S.dAz - Mv[3]) - ez * h;
   const T* M2 = Mv + 4;
   const T* M3 = Mv + 10;  // zzz is not needed
   Radial<T> g;
@@ -758,10 +762,10 @@ __device__ __forceinline__ void interact_rr_v(Target<T, true>& S, const T* Mv, T
 
 template <typename T>
 __device__ __forceinline__ void interact_rr(Target<T, true>& S, const T* __restrict__ M, int64_t N,
-                                            int64_t iB, T x, T y, T z) {
+                                            int64_t iB, T ex, T ey, T ez, T h) {
   T Mv[20];
   mom_load20(M, N, iB, Mv);
-  interact_rr_v<T>(S, Mv, x, y, z);
+  interact_rr_v<T>(S, Mv, ex, ey, ez, h);
 }
 
 // A leaf target (a point mass at its centre: only L0, L1; no M3 of its own, so the correction
@@ -994,8 +998,7 @@ __device__ void m2l_level(const DevArgs& A, int32_t s, int parity, int t, bool a
       if (sB < 0) continue;  // only without proper nesting
       int64_t iB = int64_t(sB) * kCells + cidx(px & 7, py & 7, pz & 7);
       if (FMM_BAD(A, iB < N && slot >= 0 && slot < 27)) continue;
-      interact_rr<T>(S, M, N, iB, S.dAx - ldg_t(td + 4 * q) * h, S.dAy - ldg_t(td + 4 * q + 1) * h,
-                     S.dAz - ldg_t(td + 4 * q + 2) * h);
+      interact_rr<T>(S, M, N, iB, ldg_t(td + 4 * q), ldg_t(td + 4 * q + 1), ldg_t(td + 4 * q + 2), h);
     }
     flush(S);
   }
@@ -1036,22 +1039,24 @@ __device__ void m2l_root(const DevArgs& A, int root, int parity, int t, int chun
   load_target<T, AREF>(S, A, M, base + iloc, amc);
   const T h = cell_h<T>(0);
   const bool root_leaf = A.leaf[root] != 0;
-  // chunk = source x index; source offsets kept as floating-point counters (no conversions)
+  // chunk = source x index; the exact offsets of the target's cell centre from the source's,
+  // kept as floating-point counters (no conversions; small multiples of h, so exact)
   const int dx = chunk - a;
-  const T rx0 = S.dAx - T(dx) * h;
+  const T ox = -T(dx) * h;
   constexpr int kRows = 8 / LANES;
   const int jy0 = r * kRows;
-  // X_A - x_B for a source at y = jy0, z = 0
-  T ry = S.dAy + T(b - jy0) * h, rz0 = S.dAz + T(c) * h;
-  for (int jy = jy0; jy < jy0 + kRows; ++jy, ry -= h) {
-    T rz = rz0;
-    for (int jz = 0; jz < 8; ++jz, rz -= h) {
+  // for a source at y = jy0, z = 0
+  T oy = T(b - jy0) * h;
+  const T oz0 = T(c) * h;
+  for (int jy = jy0; jy < jy0 + kRows; ++jy, oy -= h) {
+    T oz = oz0;
+    for (int jz = 0; jz < 8; ++jz, oz -= h) {
       const int j = cidx(chunk, jy, jz);
       if (j == iloc) continue;
       const int dy = jy - b, dz = jz - c;
       const bool ws = dx * dx + dy * dy + dz * dz > A.ws_d2;
       if (!ws && !root_leaf) continue;
-      interact<T, AREF, AREF>(S, M, N, base + j, rx0, ry, rz);  // AREF: the root is refined
+      interact<T, AREF, AREF>(S, M, N, base + j, ox, oy, oz);  // AREF: the root is refined
     }
     if (jy & 1) flush(S);
   }
@@ -1514,12 +1519,13 @@ __global__ void __launch_bounds__(kStageThreads, 1) k_m2l_stage(DevArgs A, const
           Mv[4 * k + 2] = v.z;
           Mv[4 * k + 3] = v.w;
         }
-        const float x = fmaf(-e.x, h, S.dAx), y = fmaf(-e.y, h, S.dAy), z = fmaf(-e.z, h, S.dAz);
-        if constexpr (SRC)
+        if constexpr (SRC) {
+          const float x = fmaf(-e.x, h, S.dAx), y = fmaf(-e.y, h, S.dAy), z = fmaf(-e.z, h, S.dAz);
           src_far<float, true>(Ls, Mv[0], Mv[1], Mv[2], Mv[3], Mv + 4, Mv + 10, x - Mv[20], y - Mv[21],
                                z - Mv[22]);
-        else
-          interact_rr_v<float>(S, Mv, x, y, z);
+        } else {
+          interact_rr_v<float>(S, Mv, e.x, e.y, e.z, h);
+        }
       }
       if constexpr (!SRC) flush(S);
     }
@@ -1661,8 +1667,7 @@ __global__ void __launch_bounds__(kStagePipeThreads, 1) k_m2l_stage_pipe(DevArgs
           Mv[4 * k + 2] = v.z;
           Mv[4 * k + 3] = v.w;
         }
-        const float x = fmaf(-e.x, h, S.dAx), y = fmaf(-e.y, h, S.dAy), z = fmaf(-e.z, h, S.dAz);
-        interact_rr_v<float>(S, Mv, x, y, z);
+        interact_rr_v<float>(S, Mv, e.x, e.y, e.z, h);
       }
       flush(S);
     }
