@@ -614,11 +614,12 @@ def measure_small(api, synth, torch, timer, dev, steps, peaks, rank):
                           "gpu_launches": tree.last_launches()}
     out["persistent_level_passes"] = persistent_vs_launches(timer, tree, rhos, ("fp64", "mixed"),
                                                             min(steps, 10))
-    if variant != 0:  # the default launch variant, timed the same way, beside the tuner's choice
-        tree.set_variant(THETA, 0)
-        r = timer.solves(tree, rhos, THETA, "mixed", 3, steps, (phi, g, net))
-        out["mixed"]["ms_per_solve_variant_0"] = r["total_ms"] / steps
-        tree.set_variant(THETA, variant)
+    # the default launch variant, timed the same way, beside the tuner's choice (on every rank,
+    # whatever each rank's tuner chose: the timer synchronises the ranks)
+    tree.set_variant(THETA, 0)
+    r = timer.solves(tree, rhos, THETA, "mixed", 3, steps, (phi, g, net))
+    out["mixed"]["ms_per_solve_variant_0"] = r["total_ms"] / steps
+    tree.set_variant(THETA, variant)
     # the mixed path against the FP64 path at the three opening angles (the same input)
     m = leaf_mass(torch, tree, rhos[0])
     sweep = {}
