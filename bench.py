@@ -238,6 +238,45 @@ def measure_paper_binary(tree_api, synth, torch, dev, stream, steps, flush, grad
     return out
 
 
+def measure_binary6(tree_api, synth, torch, dev, stream, steps, flush):
+    """The 5-level binary's field refined one level deeper (6 levels, about 2M leaf cells): the
+    size between the 0.9M-cell and the 13.5M-cell binaries, FP64 and mixed (autotuned)."""
+    w = synth.workload_binary(6, q=SMALL["q"], a=SMALL["a"])
+    t = tree_api.Tree(w.max_level, w.flags)
+    n_sub, n_leaf_sub, _ = t.info()
+    rho0 = synth.leaf_density(w.field, t.leaves())
+    floor = w.field.floor * w.field.rho_peak
+    rhos = [torch.from_numpy(synth.perturbed_density(rho0, 600 + k, floor_value=floor)).to(dev)
+            for k in range(steps + 2)]
+    counts = t.counts_by_type(THETA)
+    n_m2l = sum(v for k, v in counts.items() if k.startswith("m2l"))
+    out = {"workload": SMALL_WORKLOAD.replace("5 levels", "6 levels"), "subgrids": n_sub,
+           "leaf_cells": n_leaf_sub * 512, "m2l_pairs": n_m2l, "l2": "flushed before every timed solve"}
+    v, _, _, _ = t.autotune(rhos[0], THETA, "mixed", reps=3, stream=stream)
+    out["mixed_variant"] = int(v)
+    for precision in ("fp64", "mixed"):
+        for k in range(2):
+            t.solve(rhos[k], THETA, precision, True, stream=stream, check_status=False)
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t.solve(rhos[2 + k], THETA, precision, True, stream=stream, check_status=False)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t.sync_status(stream)
+        tm = float(np.mean(ms))
+        out[precision] = {"value": n_m2l / (tm * 1e-3), "ms_per_solve": tm,
+                          "gpu_launches": t.last_launches()}
+    out["unit"] = "interactions/s"
+    t.close()
+    return out
+
+
 def measure_batched(tree_api, synth, torch, dev, stream, steps, timer):
     """The 64 seeded trees of uneven depth (levels 2..5, single stars or binaries) as one forest:
     every level of every tree in one set of launches, replayed as one CUDA graph, the mixed path's
@@ -765,6 +804,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
 
     small = measure_small(api, synth, torch, timer, dev, min(args.steps, 10), peaks, rank)
+    six = measure_binary6(api, synth, torch, dev, stream, min(args.steps, 5), timer.flush)
     batched = measure_batched(api, synth, torch, dev, stream, min(args.steps, 3), timer)
     paper = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), timer.flush)
     graded = measure_paper_binary(api, synth, torch, dev, stream, min(args.steps, 3), timer.flush,
@@ -839,6 +879,7 @@ def run_ours(args):
         "gpu_launches": r64["launches"],
         "persistent_level_passes": pers,
         "small": small,
+        "binary_6_levels": six,
         "batched": batched,
         "paper_binary": paper,
         "paper_binary_graded": graded,

@@ -194,10 +194,12 @@ def mixed_per_cell(phi, g, net, ps, gs, idx):
     assert np.abs(net[3:6]).max() <= MIXED_TORQUE_TOL * net[6]
 
 
-@pytest.mark.parametrize("levels,precision", [(5, "fp64"), (5, "mixed"), (7, "fp64"), (7, "mixed")])
+@pytest.mark.parametrize("levels,precision", [(5, "fp64"), (5, "mixed"), (6, "fp64"), (6, "mixed"),
+                                              (7, "fp64"), (7, "mixed")])
 def test_full_size_sampled(levels, precision):
-    """The 5-level q = 0.7 binary (about 0.9M cells) and the 7-level q = 0.6 binary (13.5M
-    cells): the oracle evaluates a sample of leaf cells one by one."""
+    """The 5-level q = 0.7 binary (about 0.9M cells), the same field refined to 6 levels, and the
+    7-level q = 0.6 binary (13.5M cells): the oracle evaluates a sample of leaf cells one by
+    one."""
     if levels == 7:
         w = synth.workload_binary(7, q=0.6, a=0.3)
     else:
