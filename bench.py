@@ -428,10 +428,19 @@ def run_solve_only(args):
         theta = w.theta
     elif args.solve_workload == "binary7":
         w = big_workload(synth)
-    else:
+    elif args.solve_workload == "binary6":
+        w = synth.workload_binary(6, q=SMALL["q"], a=SMALL["a"])
+    elif args.solve_workload != "forest64":
         w = small_workload(synth)
-    tree = api.Tree(w.max_level, w.flags)
-    rho = torch.from_numpy(synth.leaf_density(w.field, tree.leaves())).cuda()
+    if args.solve_workload == "forest64":  # the 64 seeded trees of uneven depth as one forest
+        ws = synth.batched_workloads(64)
+        trees = [api.Tree(x.max_level, x.flags) for x in ws]
+        tree = api.Forest(trees)
+        rho = torch.from_numpy(np.concatenate([synth.leaf_density(x.field, t.leaves())
+                                               for x, t in zip(ws, trees)])).cuda()
+    else:
+        tree = api.Tree(w.max_level, w.flags)
+        rho = torch.from_numpy(synth.leaf_density(w.field, tree.leaves())).cuda()
     if args.variant is not None:
         tree.set_variant(theta, args.variant)
     for _ in range(args.warmup + args.steps):
@@ -899,9 +908,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--solve-workload", choices=["binary5", "binary7", "paper9"], default="binary5",
-                    help="with --solve-only: the 5-level binary (default), the 7-level headline "
-                         "binary or the 9-level merger binary in the paper's proportions")
+    ap.add_argument("--solve-workload", choices=["binary5", "binary6", "binary7", "paper9", "forest64"],
+                    default="binary5",
+                    help="with --solve-only: the 5-level binary (default), the same at 6 levels, "
+                         "the 7-level headline binary, the 9-level merger binary in the paper's "
+                         "proportions, or the 64-tree forest")
     ap.add_argument("--variant", type=int, default=None,
                     help="with --solve-only mixed: the launch variant (fmm_set_variant)")
     ap.add_argument("--solve-only", choices=["fp64", "mixed", "df64"], default=None,

@@ -2735,24 +2735,29 @@ __device__ __forceinline__ void block_sum7(double* v, double (*sh)[kReduceThread
   }
 }
 
-// blockIdx.y = tree; its leaf cells are reduced by gridDim.x blocks in a fixed order, and the
-// last of them to finish (a counter per tree, reset by that block) adds the gridDim.x partial
-// sums in block order into the tree's 7 numbers.  The FP64 work per cell is m, m g, F and the
+// Block b reduces chunk plan[2 b + 1] of tree k = plan[2 b]: tree k's leaf cells are shared by
+// its nb = tree_plan[2 k] blocks in a fixed order (each tree's share of the blocks is in
+// proportion to its leaf cells, so that the trees of a forest finish together), and the last of
+// them to finish (a counter per tree, reset by that block) adds the nb partial sums, stored from
+// partials[7 tree_plan[2 k + 1]] on, in block order into the tree's 7 numbers.  The FP64 work per cell is m, m g, F and the
 // torque (13 operations); the normalisation S, a scale, is formed in FP32 from values converted
 // with integer operations.
 __global__ void __launch_bounds__(kReduceThreads)
-    k_net_partial(DevArgs A, double* __restrict__ partials, unsigned* __restrict__ counters) {
+    k_net_partial(DevArgs A, double* __restrict__ partials, unsigned* __restrict__ counters,
+                  const int32_t* __restrict__ plan, const int32_t* __restrict__ tree_plan) {
   __shared__ double sh[7][kReduceThreads];
   double v[6] = {0, 0, 0, 0, 0, 0};
   float sn = 0.0f;  // this thread's share of the normalisation S, formed and summed in FP32
-  const int64_t stride = int64_t(gridDim.x) * kReduceThreads;
-  const int64_t base = A.tree_leaf_off[blockIdx.y] * kCells;
-  const int64_t end = A.tree_leaf_off[blockIdx.y + 1] * kCells;
-  const double* __restrict__ rho = A.io[blockIdx.y].rho;
-  const double* __restrict__ g = A.io[blockIdx.y].g;
+  const int tree = plan[2 * blockIdx.x], chunk = plan[2 * blockIdx.x + 1];
+  if (FMM_BAD(A, tree >= 0 && tree < A.n_roots)) return;  // (no block waits for another)
+  const int nb = tree_plan[2 * tree];
+  const int64_t stride = int64_t(nb) * kReduceThreads;
+  const int64_t base = A.tree_leaf_off[tree] * kCells;
+  const int64_t end = A.tree_leaf_off[tree + 1] * kCells;
+  const double* __restrict__ rho = A.io[tree].rho;
+  const double* __restrict__ g = A.io[tree].g;
 #pragma unroll 4
-  for (int64_t i = base + int64_t(blockIdx.x) * kReduceThreads + threadIdx.x; i < end;
-       i += stride) {
+  for (int64_t i = base + int64_t(chunk) * kReduceThreads + threadIdx.x; i < end; i += stride) {
     const int32_t s = A.leaf_sub[i >> 9];
     const int lev = A.level[s];
     const int loc = int(i & 511);
@@ -2778,22 +2783,22 @@ __global__ void __launch_bounds__(kReduceThreads)
   }
   double w[7] = {v[0], v[1], v[2], v[3], v[4], v[5], df_f2d(sn)};
   block_sum7(w, sh);
-  double* P = partials + int64_t(blockIdx.y) * gridDim.x * 7;
-  if (threadIdx.x < 7) P[int64_t(blockIdx.x) * 7 + threadIdx.x] = sh[threadIdx.x][0];
+  double* P = partials + int64_t(tree_plan[2 * tree + 1]) * 7;
+  if (threadIdx.x < 7) P[int64_t(chunk) * 7 + threadIdx.x] = sh[threadIdx.x][0];
   __shared__ bool last;
   __threadfence();  // this block's partial sums are visible before it is counted
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&counters[blockIdx.y], 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) last = atomicAdd(&counters[tree], 1u) == unsigned(nb) - 1u;
   __syncthreads();
   if (!last) return;
   __threadfence();
   double u[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int b = threadIdx.x; b < int(gridDim.x); b += kReduceThreads)
+  for (int b = threadIdx.x; b < nb; b += kReduceThreads)
 #pragma unroll
     for (int k = 0; k < 7; ++k) u[k] += P[int64_t(b) * 7 + k];
   block_sum7(u, sh);
-  if (threadIdx.x < 7) (*A.io_net)[int64_t(blockIdx.y) * 7 + threadIdx.x] = sh[threadIdx.x][0];
-  if (threadIdx.x == 0) counters[blockIdx.y] = 0u;  // ready for the next solve
+  if (threadIdx.x < 7) (*A.io_net)[int64_t(tree) * 7 + threadIdx.x] = sh[threadIdx.x][0];
+  if (threadIdx.x == 0) counters[tree] = 0u;  // ready for the next solve
 }
 
 // blockIdx.x = tree (or set of partials): sums n_blocks partials in a fixed order into out[7 x];
@@ -3026,6 +3031,8 @@ struct fmm_tree {
   double *d_mom = nullptr, *d_mtl = nullptr, *d_loc = nullptr, *d_ac = nullptr, *d_root_part = nullptr,
          *d_root_part_ac = nullptr, *d_partials = nullptr;
   unsigned* d_net_count = nullptr;  // k_net_partial's finished-block counters, one per tree
+  int32_t *d_net_plan = nullptr, *d_net_tree_plan = nullptr;  // its blocks' trees and chunks
+  int64_t net_blocks = 0;
   unsigned* d_bar = nullptr;        // k_levels' grid barrier: arrivals, generation
   int persistent = 0;               // level passes as persistent launches (fmm_set_persistent)
   int levels_cap[2] = {0, 0};       // co-resident blocks of k_levels<false>, k_levels<true>
@@ -3088,10 +3095,28 @@ struct fmm_tree {
   std::map<std::tuple<double, int, int, int, int, int, long long, int, int>, Graph> graphs;
 };
 
-// blocks per tree of the net reduction: about 512 in all
-static inline int net_blocks(int64_t n_trees) {
-  int64_t b = kReduceBlocks / (n_trees > 0 ? n_trees : 1);
-  return int(b < 8 ? 8 : b);
+// The net reduction's blocks: about kReduceBlocks in all, each tree's share in proportion to its
+// leaf cells (at least one).  plan: (tree, chunk) per block; tree_plan: (blocks, first partial)
+// per tree.  Returns the number of blocks.
+static int64_t net_plan(const std::vector<int64_t>& tree_leaf_off, std::vector<int32_t>& plan,
+                        std::vector<int32_t>& tree_plan) {
+  const int64_t nr = int64_t(tree_leaf_off.size()) - 1;
+  const int64_t total = tree_leaf_off[size_t(nr)] - tree_leaf_off[0];
+  plan.clear();
+  tree_plan.assign(size_t(2 * nr), 0);
+  int64_t first = 0;
+  for (int64_t k = 0; k < nr; ++k) {
+    const int64_t cells = tree_leaf_off[size_t(k + 1)] - tree_leaf_off[size_t(k)];
+    const int64_t nb = std::max<int64_t>(1, total > 0 ? (kReduceBlocks * cells) / total : 1);
+    tree_plan[size_t(2 * k)] = int32_t(nb);
+    tree_plan[size_t(2 * k + 1)] = int32_t(first);
+    for (int64_t c = 0; c < nb; ++c) {
+      plan.push_back(int32_t(k));
+      plan.push_back(int32_t(c));
+    }
+    first += nb;
+  }
+  return first;
 }
 
 template <typename P>
@@ -3197,7 +3222,13 @@ static int ensure_device(fmm_tree* t) {
   CUDA_TRY(dalloc(t, &t->d_ac, sizeof(double) * 3 * nc));
   const int64_t nr = h.n_trees;
   CUDA_TRY(dalloc(t, &t->d_root_part, sizeof(double) * nr * kRootChunks * 23 * kCells));
-  CUDA_TRY(dalloc(t, &t->d_partials, sizeof(double) * 7 * net_blocks(nr) * nr));
+  {
+    std::vector<int32_t> plan, tree_plan;
+    t->net_blocks = net_plan(h.tree_leaf_off, plan, tree_plan);
+    CUDA_TRY(dalloc(t, &t->d_partials, sizeof(double) * 7 * size_t(t->net_blocks)));
+    CUDA_TRY(upload(t, &t->d_net_plan, plan));
+    CUDA_TRY(upload(t, &t->d_net_tree_plan, tree_plan));
+  }
   CUDA_TRY(dalloc(t, &t->d_net_count, sizeof(unsigned) * size_t(nr)));
   CUDA_TRY(dalloc(t, &t->d_bar, sizeof(unsigned) * 2));
   CUDA_TRY(cudaMemset(t->d_net_count, 0, sizeof(unsigned) * size_t(nr)));
@@ -3736,9 +3767,8 @@ static int set_io(fmm_tree* t, const std::vector<TreeIo>& io, double* net, cudaS
 }
 
 static int launch_net(fmm_tree* t, const DevArgs& A, cudaStream_t st) {
-  const int nb = net_blocks(t->h.n_trees);
-  k_net_partial<<<dim3(unsigned(nb), unsigned(t->h.n_trees)), kReduceThreads, 0, st>>>(
-      A, t->d_partials, t->d_net_count);
+  k_net_partial<<<unsigned(t->net_blocks), kReduceThreads, 0, st>>>(
+      A, t->d_partials, t->d_net_count, t->d_net_plan, t->d_net_tree_plan);
   CUDA_TRY(cudaGetLastError());
   return FMM_OK;
 }
