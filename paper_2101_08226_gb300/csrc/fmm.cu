@@ -1284,8 +1284,11 @@ __global__ void __launch_bounds__(NT) k_m2l_ref(DevArgs A, const int32_t* __rest
 // [0, n_bt_long)): 4 lanes per target -- these threads would run long serial lists of partners
 // read from L2, so each list is split four ways and the partial sums are added with warp
 // shuffles.  Kind 3: the targets n_bt_long + 64 (idx .. idx + 3) + t, one lane each.
+// (at most 64 registers, four blocks per SM: this kernel waits on scattered gathers, and the
+// extra warps hide more of that latency than the few spilled registers cost -- measured 1.5-2.5 %
+// off the mixed solve on the 5- and 7-level binaries and the 64-tree forest)
 template <typename T>
-__global__ void __launch_bounds__(64 * kSplitLanes) k_m2l_split(DevArgs A, const int32_t* __restrict__ blocks,
+__global__ void __launch_bounds__(64 * kSplitLanes, 4) k_m2l_split(DevArgs A, const int32_t* __restrict__ blocks,
                                                                  int amc) {
   const int32_t code = blocks[blockIdx.x];
   const int kind = (code >> 30) & 3, idx = code & ((1 << 27) - 1);
